@@ -1,0 +1,167 @@
+"""Seeded synthetic initial conditions and run configurations.
+
+This module holds the workloads only (grids, boxes, time steps, seeded
+phase-space distributions).  It contains none of the solver's arithmetic and
+imports nothing else from the package, so the CUDA path and the FP64 oracle
+can both be fed from it.
+
+Workloads, shaped after the paper's tests (Sec. 3.2):
+  * isothermal (Spitzer) sheet, the stationary solution used as the paper's
+    first test, normalised to total mass 1 with G = 1;
+  * a sum of warm Gaussian halos, standing in for the paper's random set of
+    stationary clouds (whose exact construction is not given in the paper);
+  * a free-streaming (G = 0) run on the Spitzer grid.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+ALPHA = math.sqrt(3.0) / 4.0            # Sec. 2.3.3, alpha = sqrt(3)/4
+BETA = 0.5 * (1.0 - math.sqrt(3.0) / 2.0)  # Sec. 2.3.3, beta = (1 - sqrt(3)/2)/2
+
+
+@dataclass(frozen=True)
+class RunConfig:
+    """One solve: grid, box, element stride, time step, remap period, G."""
+    name: str
+    nx: int
+    nv: int
+    x_lo: float
+    x_hi: float
+    v_lo: float
+    v_hi: float
+    s: int
+    dt: float
+    n_s: int
+    G: float
+    steps: int
+    ic: str = "spitzer"          # "spitzer" | "halos"
+    ic_params: dict = field(default_factory=dict)
+    seed: int = 0
+
+    @property
+    def dx(self) -> float:
+        return (self.x_hi - self.x_lo) / (self.nx - 1)
+
+    @property
+    def dv(self) -> float:
+        return (self.v_hi - self.v_lo) / (self.nv - 1)
+
+    def x(self) -> np.ndarray:
+        return self.x_lo + np.arange(self.nx, dtype=np.float64) * self.dx
+
+    def v(self) -> np.ndarray:
+        return self.v_lo + np.arange(self.nv, dtype=np.float64) * self.dv
+
+    def with_(self, **kw) -> "RunConfig":
+        return replace(self, **kw)
+
+
+# ---- initial conditions ------------------------------------------------------
+
+def spitzer(x: np.ndarray, v: np.ndarray, sigma: float = 0.5, G: float = 1.0,
+            mass: float = 1.0) -> np.ndarray:
+    """Isothermal sheet f = rho0/(sqrt(2 pi) sigma) sech^2(x/x0) exp(-v^2/2sigma^2).
+
+    For phi'' = 4 pi G rho the self-consistent scale is x0 = sigma^2/(pi G M)
+    with rho0 = M/(2 x0); x and v broadcast against each other.
+    """
+    x0 = sigma * sigma / (math.pi * G * mass) if G != 0 else sigma * sigma / math.pi
+    rho0 = mass / (2.0 * x0)
+    return (rho0 / (math.sqrt(2.0 * math.pi) * sigma)) / np.cosh(x / x0) ** 2 * \
+        np.exp(-0.5 * (v / sigma) ** 2)
+
+
+@dataclass(frozen=True)
+class Halos:
+    """Parameters of a sum of Gaussian phase-space halos."""
+    xc: np.ndarray
+    vc: np.ndarray
+    sx: np.ndarray
+    sv: np.ndarray
+    m: np.ndarray
+
+    def __call__(self, x: np.ndarray, v: np.ndarray) -> np.ndarray:
+        out = np.zeros(np.broadcast(x, v).shape)
+        for k in range(self.m.size):
+            out += self.m[k] / (2.0 * math.pi * self.sx[k] * self.sv[k]) * np.exp(
+                -0.5 * ((x - self.xc[k]) / self.sx[k]) ** 2 - 0.5 * ((v - self.vc[k]) / self.sv[k]) ** 2)
+        return out
+
+
+def draw_halos(seed: int, n: int = 16, centre: float = 0.5, sx=(0.02, 0.1), sv=(0.05, 0.2),
+               mass=(0.1, 1.0)) -> Halos:
+    """Draw halo parameters from numpy's default_rng(seed) in a fixed order:
+    x centres, v centres, log sigma_x, log sigma_v, log masses; masses are
+    normalised to a total of 1."""
+    rng = np.random.default_rng(seed)
+    xc = rng.uniform(-centre, centre, n)
+    vc = rng.uniform(-centre, centre, n)
+    sxs = np.exp(rng.uniform(math.log(sx[0]), math.log(sx[1]), n))
+    svs = np.exp(rng.uniform(math.log(sv[0]), math.log(sv[1]), n))
+    m = np.exp(rng.uniform(math.log(mass[0]), math.log(mass[1]), n))
+    m = m / m.sum()
+    return Halos(xc, vc, sxs, svs, m)
+
+
+def initial_f(cfg: RunConfig) -> np.ndarray:
+    """f0 sampled on the nodes, [nx, nv] float64, v fastest."""
+    X, V = np.meshgrid(cfg.x(), cfg.v(), indexing="ij")
+    if cfg.ic == "spitzer":
+        return spitzer(X, V, sigma=cfg.ic_params.get("sigma", 0.5), G=cfg.G if cfg.G else 1.0)
+    if cfg.ic == "halos":
+        h = draw_halos(cfg.seed, n=cfg.ic_params.get("n", 16))
+        return h(X, V)
+    if cfg.ic == "blob":
+        # a single warm Gaussian well inside the box (free-streaming checks)
+        p = cfg.ic_params
+        return np.exp(-0.5 * ((X - p.get("x0", 0.0)) / p.get("sx", 0.15)) ** 2
+                      - 0.5 * ((V - p.get("v0", 0.0)) / p.get("sv", 0.3)) ** 2)
+    raise ValueError(cfg.ic)
+
+
+def ic_function(cfg: RunConfig):
+    """The initial condition as a callable f0(x, v) (for exact free streaming)."""
+    if cfg.ic == "spitzer":
+        sig = cfg.ic_params.get("sigma", 0.5)
+        return lambda x, v: spitzer(x, v, sigma=sig, G=cfg.G if cfg.G else 1.0)
+    if cfg.ic == "halos":
+        return draw_halos(cfg.seed, n=cfg.ic_params.get("n", 16))
+    if cfg.ic == "blob":
+        p = cfg.ic_params
+        return lambda x, v: np.exp(-0.5 * ((x - p.get("x0", 0.0)) / p.get("sx", 0.15)) ** 2
+                                   - 0.5 * ((v - p.get("v0", 0.0)) / p.get("sv", 0.3)) ** 2)
+    raise ValueError(cfg.ic)
+
+
+# ---- the named workloads -----------------------------------------------------
+
+SPITZER_128 = RunConfig("spitzer-128x128-G1", 128, 128, -1.0, 1.0, -2.5, 2.5, 4, 0.005, 20, 1.0, 200,
+                        "spitzer", {"sigma": 0.5})
+FREE_128 = SPITZER_128.with_(name="free-streaming-128x128-G0", G=0.0)
+HALOS_4096 = RunConfig("halos16-4096x4096", 4096, 4096, -1.0, 1.0, -1.5, 1.5, 8, 0.002, 25, 1.0, 1000,
+                       "halos", {"n": 16}, seed=0)
+HALOS_8192 = HALOS_4096.with_(name="halos16-8192x8192", nx=8192, nv=8192, steps=500)
+
+WORKLOADS = {c.name: c for c in (SPITZER_128, FREE_128, HALOS_4096, HALOS_8192)}
+
+
+def batch_member(index: int, base_seed: int = 1000) -> RunConfig:
+    """One of the many independent solves of the batched workload: sides drawn
+    independently from {64, ..., 1024}, a Spitzer sheet (sigma ~ U[0.3, 0.7],
+    v box +-5 sigma) or 4-16 halos, from a per-instance seed."""
+    rng = np.random.default_rng(base_seed + index)
+    sides = (64, 128, 256, 512, 1024)
+    nx = int(rng.choice(sides))
+    nv = int(rng.choice(sides))
+    s = 4 if max(nx, nv) <= 128 else 8
+    if rng.uniform() < 0.5:
+        sig = float(rng.uniform(0.3, 0.7))
+        return RunConfig(f"batch{index}-spitzer", nx, nv, -1.0, 1.0, -5 * sig, 5 * sig, s, 0.005, 20, 1.0,
+                         500, "spitzer", {"sigma": sig}, seed=base_seed + index)
+    nh = int(rng.integers(4, 17))
+    return RunConfig(f"batch{index}-halos", nx, nv, -1.0, 1.0, -1.5, 1.5, s, 0.002, 20, 1.0, 500,
+                     "halos", {"n": nh}, seed=base_seed + index)
