@@ -1,0 +1,170 @@
+/*
+ * vlamet.h -- C ABI of the GB300 (sm_103a) metric semi-Lagrangian
+ * Vlasov-Poisson solver (Colombi & Alard, "A 'metric' semi-Lagrangian
+ * Vlasov-Poisson solver", 1D space / 2D phase space).
+ *
+ * The library advances one solve (one phase-space grid) per vm_solver.  Every
+ * step of the method runs in the library's own CUDA kernels on the caller's
+ * stream; the host only launches.  Pointers are plain host or device
+ * pointers; no C++ or framework types cross this boundary.
+ *
+ * Grid and storage conventions (fixed for every call):
+ *   - node-centred fixed box: x_i = x_lo + i*dx, dx = (x_hi - x_lo)/(nx - 1),
+ *     v_j = v_lo + j*dv; f, f_ini, eta and the map are [nx][nv], v fastest
+ *     (element (i, j) at offset i*nv + j);
+ *   - elements of metric sit on a lattice centred on the box with spacing
+ *     s*dx by s*dv and one extra layer on every side: Lx = 2*Kx + 3 with
+ *     Kx = ceil(((nx-1)/2)/s), same for v; element m = k*Lv + l;
+ *   - element state exchanged as 12 arrays of ne doubles (structure of
+ *     arrays, row r at offset r*ne): x, v, Txx, Txv, Tvx, Tvv,
+ *     Hx_xx, Hx_xv, Hx_vv, Hv_xx, Hv_xv, Hv_vv, where T_ab = dP_a/dQ_b and
+ *     H_a,bc = d2P_a/dQ_b dQ_c (Sec. 2.1).
+ *
+ * Ownership: the caller provides one device workspace (vm_workspace_bytes)
+ * at vm_create and keeps it alive until vm_destroy; the solver keeps all of
+ * its state there.  Buffers passed to other calls are borrowed for the
+ * duration of the call only.
+ *
+ * Errors: every call returns a vm_status; nothing aborts, throws or traps.
+ * Device-side failures (a percolation that does not converge, a flood-fill
+ * window that overflows) set an error word on the device, which is read and
+ * cleared by the calls that synchronise (vm_sync and every call that copies
+ * results to the host).
+ *
+ * Threads and streams: calls on one solver must not run concurrently; calls
+ * are asynchronous on the solver's stream unless they say they synchronise.
+ * Distinct solvers on distinct streams are independent.
+ */
+#ifndef VLAMET_H
+#define VLAMET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VM_OK = 0,
+  VM_E_INVALID_ARG = 1,
+  VM_E_OOM = 2,            /* workspace too small */
+  VM_E_CUDA = 3,           /* a CUDA runtime call failed */
+  VM_E_NOT_CONVERGED = 4,  /* unexplored-site repair hit its round cap */
+  VM_E_PATCH_OVERFLOW = 5, /* an element's influence region exceeded the largest window */
+  VM_E_BUDGET = 6,         /* admission refused by a memory budget (batch/serve layer) */
+  VM_E_STATE = 7           /* call out of order (e.g. a step before vm_set_f) */
+} vm_status;
+
+typedef enum { VM_FP64 = 0, VM_FP32_MIXED = 1 } vm_precision;
+typedef enum { VM_DTYPE_F64 = 0, VM_DTYPE_F32 = 1 } vm_dtype;
+
+typedef struct {
+  int32_t nx, nv;             /* grid nodes along x and v, each >= 4 */
+  double x_lo, x_hi;          /* box along x */
+  double v_lo, v_hi;          /* box along v */
+  int32_t elem_stride;        /* s: element spacing in grid sites (Sec. 2.3, Delta_m = s*Delta) */
+  double dt;                  /* constant time step (Sec. 2.4) */
+  int32_t n_s;                /* transport steps between remaps (Table 1, n_s) */
+  double G;                   /* gravitational constant: a = 2 pi G (M_right - M_left) (Sec. 2.5) */
+  int32_t precision;          /* vm_precision */
+  double alpha;               /* percolation margin, default sqrt(3)/4 (Sec. 2.3.3) */
+  double beta;                /* Q_r margin, default (1 - sqrt(3)/2)/2 (Sec. 2.3.3) */
+  int32_t pad;                /* connectivity margin around the grid, sites; 0 -> s */
+  int32_t literal_fd;         /* 1: a' = (a(i+1)-a(i-1))/dx as printed; 0: /(2 dx) */
+  int32_t max_hole_rounds;    /* cap on unexplored-site repair rounds; 0 -> nx + nv */
+  int32_t reserved;
+} vm_config;
+
+typedef struct {
+  double mass;      /* sum f dx dv of the last reconstructed f */
+  double energy;    /* 1/2 sum v^2 f dx dv - 1/(8 pi G) sum (a^2 - (2 pi G M)^2) dx (Sec. 3.2) */
+  double detT_min;  /* range of det T over the elements (Sec. 2.1, |T| = 1) */
+  double detT_max;
+  int64_t step;     /* steps taken since vm_set_f */
+  int32_t cycle;    /* steps since the last remap */
+  int32_t holes;    /* unexplored sites repaired by the last map */
+  int32_t hole_rounds;
+  int32_t overflow_elements; /* elements that needed the large flood-fill window */
+} vm_diag;
+
+typedef struct vm_solver vm_solver;
+
+/* Fill *c with the paper's defaults (alpha, beta) and zeros elsewhere. */
+void vm_config_default(vm_config* c);
+
+/* Device bytes the solver needs for config *c (0 if *c is invalid). */
+size_t vm_workspace_bytes(const vm_config* c);
+
+/* Create a solver.  d_workspace: device buffer of at least
+ * vm_workspace_bytes(c) bytes, 256-byte aligned, owned by the caller until
+ * vm_destroy.  cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * Returns VM_E_INVALID_ARG for a bad config, VM_E_OOM if the workspace is too
+ * small.  The state is empty until vm_set_f. */
+vm_status vm_create(const vm_config* c, void* d_workspace, size_t workspace_bytes,
+                    void* cuda_stream, vm_solver** out);
+void vm_destroy(vm_solver* s);
+const char* vm_status_string(vm_status st);
+
+/* Lattice shape: number of elements, Lx and Lv. */
+vm_status vm_lattice(const vm_solver* s, int32_t* ne, int32_t* Lx, int32_t* Lv);
+
+/* New initial condition (Sec. 1 and 2.3): f_ini <- f0 ([nx][nv] doubles,
+ * host if on_device == 0, else device), its cubic B-spline coefficients
+ * (Sec. 2.2.2), and isotropic elements on the lattice (T = I, H = 0). */
+vm_status vm_set_f(vm_solver* s, const double* f0, int32_t on_device);
+
+/* Replace / read the element state (12 x ne doubles, layout above).  Used
+ * to inject identical states into two implementations. */
+vm_status vm_set_elements(vm_solver* s, const double* soa12, int32_t on_device);
+vm_status vm_get_elements(vm_solver* s, double* soa12, int32_t on_device);
+
+/* Influence map of the current elements (Sec. 2.3.1): Taylor terms of the
+ * inverse map, percolation, overlap and unexplored-site rules.  Result read
+ * with vm_read_map. */
+vm_status vm_compute_map(vm_solver* s);
+
+/* Transport-mode f at the current elements (Sec. 2.2.1 with the map of
+ * Sec. 2.3.1), its pixel masses and the force (Sec. 2.5).  Results read with
+ * vm_read_f and vm_density_force. */
+vm_status vm_reconstruct(vm_solver* s);
+
+/* Advance nsteps steps of dt (Sec. 2.4): half drift; map; f(t + dt/2);
+ * pixel masses, mass scan, force, a', a''; kick; half drift; and, after
+ * every n_s-th step of a cycle, a remap (Secs. 2.2.2, 2.3.2).  Asynchronous. */
+vm_status vm_step(vm_solver* s, int32_t nsteps);
+
+/* Remap now, at the current elements: Q_r blend, spline of f_ini at Q_r,
+ * new f_ini and coefficients, isotropic elements.  Asynchronous. */
+vm_status vm_remap(vm_solver* s);
+
+/* Pixel masses M(i) = sum_j f(i,j) dx dv, and a, a', a'' on the x nodes,
+ * from the last reconstruction ([nx] doubles each; any pointer may be
+ * NULL).  Synchronises when on_device == 0. */
+vm_status vm_density_force(vm_solver* s, double* M, double* a, double* da, double* d2a,
+                           int32_t on_device);
+
+/* Copy out [nx][nv] arrays: the last reconstructed f, the current f_ini,
+ * the current spline coefficients eta, the current map (int32).  dtype is a
+ * vm_dtype (conversion happens on the device).  Synchronise when
+ * on_device == 0. */
+vm_status vm_read_f(vm_solver* s, void* out, int32_t dtype, int32_t on_device);
+vm_status vm_read_fini(vm_solver* s, void* out, int32_t dtype, int32_t on_device);
+vm_status vm_read_eta(vm_solver* s, void* out, int32_t dtype, int32_t on_device);
+vm_status vm_read_map(vm_solver* s, int32_t* out, int32_t on_device);
+
+/* Mass, energy and det T range of the last reconstruction (Sec. 3.2, 2.1),
+ * plus step counters and map statistics.  Synchronises. */
+vm_status vm_diagnostics(vm_solver* s, vm_diag* d);
+
+/* Wait for the solver's stream; return and clear any device-side error. */
+vm_status vm_sync(vm_solver* s);
+
+/* Number of kernel launches the solver has issued since creation (a count
+ * kept on the host, for launch accounting). */
+int64_t vm_launch_count(const vm_solver* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,442 @@
+// C ABI of the solver (declared in include/vlamet.h): configuration,
+// workspace layout, and the host-side sequencing of the kernels.  The host
+// never touches grid data; it only launches and copies on request.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Layout {
+  size_t fini, eta, f, tmp, map, keys, holes_a, holes_b, ovf, el, tay, M, a, da, d2a, thx, thv, thxf, thvf,
+      ds, total;
+};
+
+bool valid(const vm_config* c) {
+  if (!c) return false;
+  if (c->nx < 4 || c->nv < 4 || c->elem_stride < 1 || c->n_s < 1) return false;
+  if (!(c->x_hi > c->x_lo) || !(c->v_hi > c->v_lo) || !(c->dt > 0.0) || !isfinite(c->G)) return false;
+  if (c->precision != VM_FP64 && c->precision != VM_FP32_MIXED) return false;
+  if (c->pad < 0 || c->max_hole_rounds < 0) return false;
+  if (!(c->alpha >= 0.0) || !(c->beta >= 0.0)) return false;
+  // 32-bit site and element indices
+  if ((long long)c->nx * (long long)c->nv >= (1ll << 31) / 2) return false;
+  return true;
+}
+
+void lattice(const vm_config* c, int32_t* Kx, int32_t* Kv, int32_t* Lx, int32_t* Lv) {
+  const int s = c->elem_stride;
+  *Kx = (c->nx - 1 + 2 * s - 1) / (2 * s);
+  *Kv = (c->nv - 1 + 2 * s - 1) / (2 * s);
+  *Lx = 2 * *Kx + 3;
+  *Lv = 2 * *Kv + 3;
+}
+
+Layout layout(const vm_config* c) {
+  Layout L{};
+  int32_t Kx, Kv, Lx, Lv;
+  lattice(c, &Kx, &Kv, &Lx, &Lv);
+  const size_t n = (size_t)c->nx * c->nv, ne = (size_t)Lx * Lv;
+  const size_t sr = (c->precision == VM_FP32_MIXED) ? 4 : 8;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align256(o + bytes);
+    return at;
+  };
+  L.fini = take(n * sr);
+  L.eta = take(n * sr);
+  L.f = take(n * sr);
+  L.tmp = take(n * sr);
+  L.map = take(n * 4);
+  L.keys = take(n * 16);
+  L.holes_a = take(n * 4);
+  L.holes_b = take(2 * n * 4);
+  L.ovf = take(ne * 4);
+  L.el = take(12 * ne * 8);
+  L.tay = take(16 * ne * 8);
+  L.M = take(c->nx * 8);
+  L.a = take(c->nx * 8);
+  L.da = take(c->nx * 8);
+  L.d2a = take(c->nx * 8);
+  L.thx = take(2 * c->nx * 8);
+  L.thv = take(2 * c->nv * 8);
+  L.thxf = take(2 * c->nx * 4);
+  L.thvf = take(2 * c->nv * 4);
+  L.ds = take(sizeof(vm::DevState));
+  L.total = o;
+  return L;
+}
+
+// LU factors of the constant spline system (rows (1,4,1), ends (4,2) and
+// (2,4)): c'_i and 1/den_i of the Thomas sweeps.
+void thomas(int n, std::vector<double>& out) {
+  out.assign(2 * (size_t)n, 0.0);
+  double cprev = 0.0;
+  for (int i = 0; i < n; i++) {
+    const double sub = (i == 0) ? 0.0 : ((i == n - 1) ? 2.0 : 1.0);
+    const double sup = (i == n - 1) ? 0.0 : ((i == 0) ? 2.0 : 1.0);
+    const double den = 4.0 - sub * cprev;
+    const double cp = sup / den;
+    out[i] = cp;
+    out[n + i] = 1.0 / den;
+    cprev = cp;
+  }
+}
+
+vm_status check_launch(vm_solver* s) {
+  (void)s;
+  return cudaPeekAtLastError() == cudaSuccess ? VM_OK : VM_E_CUDA;
+}
+
+vm_status remap_internal(vm_solver* s) {
+  vm::launch_taylor(s);
+  vm::launch_map(s);
+  vm::launch_remap_resample(s, s->tmp);
+  void* t = s->fini;
+  s->fini = s->tmp;
+  s->tmp = t;
+  vm::launch_spline_solve(s, s->fini, s->eta);
+  vm::launch_reset_elements(s);
+  s->cyc = 0;
+  return check_launch(s);
+}
+
+// Restore the claim keys after they served as a staging buffer.
+vm_status reset_keys(vm_solver* s) {
+  VM_CUDA_TRY(cudaMemsetAsync(s->keys, 0xFF, s->n * 16, s->stream));
+  return VM_OK;
+}
+
+vm_status read_real(vm_solver* s, const void* src, void* out, int32_t dtype, int32_t on_device) {
+  if (!out || (dtype != VM_DTYPE_F64 && dtype != VM_DTYPE_F32)) return VM_E_INVALID_ARG;
+  const size_t esz = dtype == VM_DTYPE_F64 ? 8 : 4;
+  const bool same = (esz == s->sreal);
+  if (on_device) {
+    if (same) {
+      VM_CUDA_TRY(cudaMemcpyAsync(out, src, s->n * esz, cudaMemcpyDeviceToDevice, s->stream));
+    } else {
+      vm::launch_convert(s, src, out, dtype, s->n);
+    }
+    return check_launch(s);
+  }
+  if (same) {
+    VM_CUDA_TRY(cudaMemcpyAsync(out, src, s->n * esz, cudaMemcpyDeviceToHost, s->stream));
+  } else {
+    vm::launch_convert(s, src, s->keys, dtype, s->n);
+    VM_CUDA_TRY(cudaMemcpyAsync(out, s->keys, s->n * esz, cudaMemcpyDeviceToHost, s->stream));
+    vm_status st = reset_keys(s);
+    if (st != VM_OK) return st;
+  }
+  return vm_sync(s);
+}
+
+}  // namespace
+
+extern "C" {
+
+void vm_config_default(vm_config* c) {
+  if (!c) return;
+  memset(c, 0, sizeof *c);
+  c->alpha = sqrt(3.0) / 4.0;
+  c->beta = 0.5 * (1.0 - sqrt(3.0) / 2.0);
+  c->precision = VM_FP64;
+}
+
+size_t vm_workspace_bytes(const vm_config* c) {
+  if (!valid(c)) return 0;
+  return layout(c).total;
+}
+
+const char* vm_status_string(vm_status st) {
+  switch (st) {
+    case VM_OK: return "ok";
+    case VM_E_INVALID_ARG: return "invalid argument";
+    case VM_E_OOM: return "workspace too small";
+    case VM_E_CUDA: return "CUDA runtime error";
+    case VM_E_NOT_CONVERGED: return "unexplored-site repair did not converge";
+    case VM_E_PATCH_OVERFLOW: return "influence region larger than the largest flood-fill window";
+    case VM_E_BUDGET: return "memory budget exceeded";
+    case VM_E_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+vm_status vm_create(const vm_config* c, void* d_workspace, size_t bytes, void* stream, vm_solver** out) {
+  if (!out) return VM_E_INVALID_ARG;
+  *out = nullptr;
+  if (!valid(c) || !d_workspace || ((uintptr_t)d_workspace & 255)) return VM_E_INVALID_ARG;
+  const Layout L = layout(c);
+  if (bytes < L.total) return VM_E_OOM;
+  vm_solver* s = (vm_solver*)calloc(1, sizeof(vm_solver));
+  if (!s) return VM_E_OOM;
+  s->cfg = *c;
+  if (s->cfg.pad == 0) s->cfg.pad = c->elem_stride;
+  if (s->cfg.max_hole_rounds == 0) s->cfg.max_hole_rounds = c->nx + c->nv;
+  s->stream = (cudaStream_t)stream;
+  s->fp32 = (c->precision == VM_FP32_MIXED);
+  s->sreal = s->fp32 ? 4 : 8;
+  s->n = (size_t)c->nx * c->nv;
+  vm::Grid& g = s->g;
+  g.nx = c->nx;
+  g.nv = c->nv;
+  g.s = c->elem_stride;
+  g.pad = s->cfg.pad;
+  lattice(c, &g.Kx, &g.Kv, &g.Lx, &g.Lv);
+  g.ne = g.Lx * g.Lv;
+  // Derived constants, one operation at a time (no contraction).
+  g.x_lo = c->x_lo;
+  g.v_lo = c->v_lo;
+  g.dx = (c->x_hi - c->x_lo) / (double)(c->nx - 1);
+  g.dv = (c->v_hi - c->v_lo) / (double)(c->nv - 1);
+  g.dxm = (double)c->elem_stride * g.dx;
+  g.dvm = (double)c->elem_stride * g.dv;
+  g.inv_dx = 1.0 / g.dx;
+  g.inv_dv = 1.0 / g.dv;
+  g.inv_dxm = 1.0 / g.dxm;
+  g.inv_dvm = 1.0 / g.dvm;
+  g.cx = 0.5 * (c->x_lo + c->x_hi);
+  g.cv = 0.5 * (c->v_lo + c->v_hi);
+  g.dxdv = g.dx * g.dv;
+  g.alpha = c->alpha;
+  g.beta = c->beta;
+  g.dt = c->dt;
+  g.half_dt = 0.5 * c->dt;
+  g.A = 2.0 * kPi * c->G;
+  g.literal_fd = c->literal_fd;
+  g.max_hole_rounds = s->cfg.max_hole_rounds;
+  char* base = (char*)d_workspace;
+  s->fini = base + L.fini;
+  s->eta = base + L.eta;
+  s->f = base + L.f;
+  s->tmp = base + L.tmp;
+  s->map = (int32_t*)(base + L.map);
+  s->keys = (unsigned long long*)(base + L.keys);
+  s->holes_a = (int32_t*)(base + L.holes_a);
+  s->holes_b = (int32_t*)(base + L.holes_b);
+  s->overflow_list = (int32_t*)(base + L.ovf);
+  s->el = (double*)(base + L.el);
+  s->tay = (double*)(base + L.tay);
+  s->M = (double*)(base + L.M);
+  s->a = (double*)(base + L.a);
+  s->da = (double*)(base + L.da);
+  s->d2a = (double*)(base + L.d2a);
+  s->thomas_x = (double*)(base + L.thx);
+  s->thomas_v = (double*)(base + L.thv);
+  s->thomas_xf = (float*)(base + L.thxf);
+  s->thomas_vf = (float*)(base + L.thvf);
+  s->ds = (vm::DevState*)(base + L.ds);
+  std::vector<double> tx, tv;
+  thomas(c->nx, tx);
+  thomas(c->nv, tv);
+  std::vector<float> txf(tx.begin(), tx.end()), tvf(tv.begin(), tv.end());
+  vm_status st = VM_OK;
+  do {
+    if (cudaMemsetAsync(base, 0, L.total, s->stream) != cudaSuccess) { st = VM_E_CUDA; break; }
+    if (cudaMemsetAsync(s->keys, 0xFF, s->n * 16, s->stream) != cudaSuccess) { st = VM_E_CUDA; break; }
+    if (cudaMemsetAsync(s->map, 0xFF, s->n * 4, s->stream) != cudaSuccess) { st = VM_E_CUDA; break; }
+    if (cudaMemcpyAsync(s->thomas_x, tx.data(), tx.size() * 8, cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+        cudaMemcpyAsync(s->thomas_v, tv.data(), tv.size() * 8, cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+        cudaMemcpyAsync(s->thomas_xf, txf.data(), txf.size() * 4, cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+        cudaMemcpyAsync(s->thomas_vf, tvf.data(), tvf.size() * 4, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) {
+      st = VM_E_CUDA;
+      break;
+    }
+    vm::DevState init{};
+    init.det_min_key = ~0ull;
+    init.det_max_key = 0ull;
+    if (cudaMemcpyAsync(s->ds, &init, sizeof init, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) { st = VM_E_CUDA; break; }
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) { st = VM_E_CUDA; break; }
+  } while (0);
+  if (st != VM_OK) {
+    free(s);
+    return st;
+  }
+  *out = s;
+  return VM_OK;
+}
+
+void vm_destroy(vm_solver* s) { free(s); }
+
+vm_status vm_lattice(const vm_solver* s, int32_t* ne, int32_t* Lx, int32_t* Lv) {
+  if (!s) return VM_E_INVALID_ARG;
+  if (ne) *ne = s->g.ne;
+  if (Lx) *Lx = s->g.Lx;
+  if (Lv) *Lv = s->g.Lv;
+  return VM_OK;
+}
+
+int64_t vm_launch_count(const vm_solver* s) { return s ? s->launches : 0; }
+
+vm_status vm_set_f(vm_solver* s, const double* f0, int32_t on_device) {
+  if (!s || !f0) return VM_E_INVALID_ARG;
+  const size_t bytes = s->n * 8;
+  if (!s->fp32) {
+    VM_CUDA_TRY(cudaMemcpyAsync(s->fini, f0, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                s->stream));
+  } else {
+    const double* src = f0;
+    if (!on_device) {
+      VM_CUDA_TRY(cudaMemcpyAsync(s->keys, f0, bytes, cudaMemcpyHostToDevice, s->stream));
+      src = (const double*)s->keys;
+    }
+    vm::launch_store_real(s, src, s->fini, s->n);
+    if (!on_device) {
+      vm_status st = reset_keys(s);
+      if (st != VM_OK) return st;
+    }
+  }
+  VM_CUDA_TRY(cudaMemcpyAsync(s->f, s->fini, s->n * s->sreal, cudaMemcpyDeviceToDevice, s->stream));
+  vm::launch_spline_solve(s, s->fini, s->eta);
+  vm::launch_reset_elements(s);
+  s->have_f = 1;
+  s->nstep = 0;
+  s->cyc = 0;
+  return check_launch(s);
+}
+
+vm_status vm_set_elements(vm_solver* s, const double* soa12, int32_t on_device) {
+  if (!s || !soa12) return VM_E_INVALID_ARG;
+  VM_CUDA_TRY(cudaMemcpyAsync(s->el, soa12, 12 * (size_t)s->g.ne * 8,
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->stream));
+  if (!on_device) VM_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return VM_OK;
+}
+
+vm_status vm_get_elements(vm_solver* s, double* soa12, int32_t on_device) {
+  if (!s || !soa12) return VM_E_INVALID_ARG;
+  VM_CUDA_TRY(cudaMemcpyAsync(soa12, s->el, 12 * (size_t)s->g.ne * 8,
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream));
+  return on_device ? VM_OK : vm_sync(s);
+}
+
+vm_status vm_compute_map(vm_solver* s) {
+  if (!s) return VM_E_INVALID_ARG;
+  vm::launch_taylor(s);
+  vm::launch_map(s);
+  return check_launch(s);
+}
+
+vm_status vm_reconstruct(vm_solver* s) {
+  if (!s) return VM_E_INVALID_ARG;
+  if (!s->have_f) return VM_E_STATE;
+  vm::launch_taylor(s);
+  vm::launch_map(s);
+  vm::launch_reconstruct(s);
+  vm::launch_scan_force(s);
+  return check_launch(s);
+}
+
+vm_status vm_step(vm_solver* s, int32_t nsteps) {
+  if (!s || nsteps < 0) return VM_E_INVALID_ARG;
+  if (!s->have_f) return VM_E_STATE;
+  for (int32_t it = 0; it < nsteps; it++) {
+    vm::launch_drift(s, true);   // predictor + Taylor terms at t + dt/2
+    vm::launch_map(s);
+    vm::launch_reconstruct(s);   // f(t + dt/2) and M(i)
+    vm::launch_scan_force(s);    // a, a', a''
+    vm::launch_kick_drift(s);    // kick + corrector
+    s->nstep++;
+    s->cyc++;
+    if (s->cyc >= s->cfg.n_s) {
+      vm_status st = remap_internal(s);
+      if (st != VM_OK) return st;
+    }
+  }
+  return check_launch(s);
+}
+
+vm_status vm_remap(vm_solver* s) {
+  if (!s) return VM_E_INVALID_ARG;
+  if (!s->have_f) return VM_E_STATE;
+  return remap_internal(s);
+}
+
+vm_status vm_density_force(vm_solver* s, double* M, double* a, double* da, double* d2a, int32_t on_device) {
+  if (!s) return VM_E_INVALID_ARG;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const size_t b = (size_t)s->g.nx * 8;
+  if (M) VM_CUDA_TRY(cudaMemcpyAsync(M, s->M, b, kind, s->stream));
+  if (a) VM_CUDA_TRY(cudaMemcpyAsync(a, s->a, b, kind, s->stream));
+  if (da) VM_CUDA_TRY(cudaMemcpyAsync(da, s->da, b, kind, s->stream));
+  if (d2a) VM_CUDA_TRY(cudaMemcpyAsync(d2a, s->d2a, b, kind, s->stream));
+  return on_device ? VM_OK : vm_sync(s);
+}
+
+vm_status vm_read_f(vm_solver* s, void* out, int32_t dtype, int32_t on_device) {
+  if (!s) return VM_E_INVALID_ARG;
+  return read_real(s, s->f, out, dtype, on_device);
+}
+
+vm_status vm_read_fini(vm_solver* s, void* out, int32_t dtype, int32_t on_device) {
+  if (!s) return VM_E_INVALID_ARG;
+  return read_real(s, s->fini, out, dtype, on_device);
+}
+
+vm_status vm_read_eta(vm_solver* s, void* out, int32_t dtype, int32_t on_device) {
+  if (!s) return VM_E_INVALID_ARG;
+  return read_real(s, s->eta, out, dtype, on_device);
+}
+
+vm_status vm_read_map(vm_solver* s, int32_t* out, int32_t on_device) {
+  if (!s || !out) return VM_E_INVALID_ARG;
+  VM_CUDA_TRY(cudaMemcpyAsync(out, s->map, s->n * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                              s->stream));
+  return on_device ? VM_OK : vm_sync(s);
+}
+
+vm_status vm_sync(vm_solver* s) {
+  if (!s) return VM_E_INVALID_ARG;
+  int32_t err = 0;
+  VM_CUDA_TRY(cudaMemcpyAsync(&err, &s->ds->err, sizeof err, cudaMemcpyDeviceToHost, s->stream));
+  VM_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  if (err) {
+    VM_CUDA_TRY(cudaMemsetAsync(&s->ds->err, 0, sizeof(int32_t), s->stream));
+    VM_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (err & vm::ERR_PATCH_OVERFLOW) return VM_E_PATCH_OVERFLOW;
+    if (err & vm::ERR_NOT_CONVERGED) return VM_E_NOT_CONVERGED;
+    return VM_E_CUDA;
+  }
+  return VM_OK;
+}
+
+vm_status vm_diagnostics(vm_solver* s, vm_diag* d) {
+  if (!s || !d) return VM_E_INVALID_ARG;
+  // zero the accumulators: sum_mass, sum_kin, sum_pot, and the det keys
+  vm::DevState h{};
+  const size_t off = offsetof(vm::DevState, sum_mass);
+  h.det_min_key = ~0ull;
+  h.det_max_key = 0ull;
+  VM_CUDA_TRY(cudaMemcpyAsync((char*)s->ds + off, (char*)&h + off, sizeof(vm::DevState) - off,
+                              cudaMemcpyHostToDevice, s->stream));
+  vm::launch_diagnostics(s);
+  VM_CUDA_TRY(cudaMemcpyAsync(&h, s->ds, sizeof h, cudaMemcpyDeviceToHost, s->stream));
+  vm_status st = vm_sync(s);
+  if (st != VM_OK) return st;
+  auto decode = [](unsigned long long k) {
+    unsigned long long b = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+    double d;
+    memcpy(&d, &b, 8);
+    return d;
+  };
+  d->mass = h.sum_mass;
+  d->energy = h.sum_kin + (s->cfg.G != 0.0 ? -h.sum_pot / (8.0 * kPi * s->cfg.G) : 0.0);
+  d->detT_min = decode(h.det_min_key);
+  d->detT_max = decode(h.det_max_key);
+  d->step = s->nstep;
+  d->cycle = s->cyc;
+  d->holes = h.holes_found;
+  d->hole_rounds = h.hole_rounds;
+  d->overflow_elements = h.overflow_stat;
+  return VM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,162 @@
+// Internal declarations shared by the CUDA translation units of libvlamet.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/vlamet.h"
+
+namespace vm {
+
+// Device error word bits.
+enum : int32_t {
+  ERR_NOT_CONVERGED = 1,
+  ERR_PATCH_OVERFLOW = 2,
+  ERR_LIST_OVERFLOW = 4,
+};
+
+// Grid, lattice and method constants, passed by value to every kernel.  All
+// derived doubles are computed once on the host in a fixed order (no fused
+// multiply-add), so the percolation decisions see the same operands as any
+// other FP64 restatement of the method that uses this order.
+struct Grid {
+  int32_t nx, nv, s, pad, Kx, Kv, Lx, Lv, ne;
+  double x_lo, v_lo, dx, dv, dxm, dvm, inv_dx, inv_dv, inv_dxm, inv_dvm, cx, cv, dxdv;
+  double alpha, beta;
+  double dt, half_dt, A;  // A = 2 pi G
+  int32_t literal_fd;
+  int32_t max_hole_rounds;
+};
+
+// Small device-resident control block.
+struct DevState {
+  int32_t err;
+  int32_t nholes;        // holes in the working list
+  int32_t holes_found;   // holes left by the claims (statistics)
+  int32_t hole_rounds;   // repair rounds of the last map (statistics)
+  int32_t noverflow;     // elements queued for the large flood-fill window
+  int32_t overflow_stat;
+  int32_t pad0, pad1;
+  double Mtot;           // total mass of the last reconstruction
+  double sum_mass, sum_kin, sum_pot;
+  unsigned long long det_min_key, det_max_key;
+};
+
+// Element state: 12 doubles per element, structure of arrays.
+enum { EL_X = 0, EL_V, EL_TXX, EL_TXV, EL_TVX, EL_TVV, EL_HXXX, EL_HXXV, EL_HXVV, EL_HVXX, EL_HVXV, EL_HVVV, EL_N };
+// Taylor record: 16 doubles (128 bytes) per element, array of structures so
+// that one element's terms are one cache line for the per-site gathers.
+enum { TY_X = 0, TY_V, TY_TI00, TY_TI01, TY_TI10, TY_TI11, TY_GX00, TY_GX01, TY_GX11,
+       TY_GV00, TY_GV01, TY_GV11, TY_QX, TY_QV, TY_N = 16 };
+
+constexpr unsigned long long KEY_EMPTY = ~0ull;
+
+}  // namespace vm
+
+struct vm_solver {
+  vm_config cfg;
+  vm::Grid g;
+  cudaStream_t stream;
+  int32_t fp32;            // 1: f_ini, eta, f stored as float
+  size_t sreal;            // bytes per stored real
+  size_t n;                // nx * nv
+  // device buffers (carved from the caller's workspace)
+  void* fini;
+  void* eta;
+  void* f;
+  void* tmp;
+  int32_t* map;
+  unsigned long long* keys;  // 2 words per site: {element index, bits of d^2}
+  int32_t* holes_a;
+  int32_t* holes_b;
+  int32_t* overflow_list;
+  double* el;               // 12 x ne
+  double* tay;              // ne x 16
+  double* M;                // pixel masses of the last step
+  double* a;
+  double* da;
+  double* d2a;
+  double* thomas_x;         // 2 x nx: c'_i and 1/den_i of the spline system along x
+  double* thomas_v;         // 2 x nv
+  float* thomas_xf;
+  float* thomas_vf;
+  vm::DevState* ds;
+  // host-side bookkeeping
+  int32_t have_f;
+  int64_t nstep;
+  int32_t cyc;
+  int64_t launches;
+};
+
+namespace vm {
+
+// ---- launchers (each in the translation unit of its kernels) ----
+// elements.cu
+void launch_drift(vm_solver* s, bool taylor);
+void launch_taylor(vm_solver* s);
+void launch_kick_drift(vm_solver* s);
+void launch_reset_elements(vm_solver* s);
+void launch_scan_force(vm_solver* s);
+void launch_diagnostics(vm_solver* s);
+// map.cu
+void launch_map(vm_solver* s);
+// recon.cu
+void launch_reconstruct(vm_solver* s);
+void launch_remap_resample(vm_solver* s, void* out);
+void launch_convert(vm_solver* s, const void* src, void* dst, int32_t dst_dtype, size_t count);
+void launch_store_real(vm_solver* s, const double* src, void* dst, size_t count);
+// spline.cu
+void launch_spline_solve(vm_solver* s, const void* src, void* dst);
+
+// ---- exact-order FP64 arithmetic (never contracted into FMA) ----
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+
+// Offset Q - Q_m of the second-order inverse map of one element at P
+// (Sec. 2.1): y = T^-1 dP, s_l = dP^T G_l dP, dQ = y - T^-1 s / 2.
+__device__ __forceinline__ void qofp_exact(const double* t, double Px, double Pv, double& dqx,
+                                           double& dqv) {
+  double dPx = dsub(Px, t[TY_X]), dPv = dsub(Pv, t[TY_V]);
+  double yx = dadd(dmul(t[TY_TI00], dPx), dmul(t[TY_TI01], dPv));
+  double yv = dadd(dmul(t[TY_TI10], dPx), dmul(t[TY_TI11], dPv));
+  double g0 = dadd(dmul(t[TY_GX00], dPx), dmul(t[TY_GX01], dPv));
+  double g1 = dadd(dmul(t[TY_GX01], dPx), dmul(t[TY_GX11], dPv));
+  double sx = dadd(dmul(dPx, g0), dmul(dPv, g1));
+  g0 = dadd(dmul(t[TY_GV00], dPx), dmul(t[TY_GV01], dPv));
+  g1 = dadd(dmul(t[TY_GV01], dPx), dmul(t[TY_GV11], dPv));
+  double sv = dadd(dmul(dPx, g0), dmul(dPv, g1));
+  double cx = dadd(dmul(t[TY_TI00], sx), dmul(t[TY_TI01], sv));
+  double cv = dadd(dmul(t[TY_TI10], sx), dmul(t[TY_TI11], sv));
+  dqx = dsub(yx, dmul(0.5, cx));
+  dqv = dsub(yv, dmul(0.5, cv));
+}
+
+// Squared Lagrangian distance in element spacings (Sec. 2.3.1, d[dQ]).
+__device__ __forceinline__ double dist2_exact(const double* t, const Grid& g, double Px, double Pv,
+                                              double& xi, double& ze) {
+  double dqx, dqv;
+  qofp_exact(t, Px, Pv, dqx, dqv);
+  xi = dmul(dqx, g.inv_dxm);
+  ze = dmul(dqv, g.inv_dvm);
+  return dadd(dmul(xi, xi), dmul(ze, ze));
+}
+
+__device__ __forceinline__ double site_x(const Grid& g, long long i) {
+  return dadd(g.x_lo, dmul((double)i, g.dx));
+}
+__device__ __forceinline__ double site_v(const Grid& g, long long j) {
+  return dadd(g.v_lo, dmul((double)j, g.dv));
+}
+
+__device__ __forceinline__ unsigned long long dkey(double d) {
+  return (unsigned long long)__double_as_longlong(d);
+}
+
+}  // namespace vm
+
+#define VM_CUDA_TRY(expr)                       \
+  do {                                          \
+    cudaError_t e_ = (expr);                    \
+    if (e_ != cudaSuccess) return VM_E_CUDA;    \
+  } while (0)

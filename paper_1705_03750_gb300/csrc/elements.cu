@@ -1,0 +1,324 @@
+// Elements of metric (Sec. 2.1, 2.4) and the 1D force (Sec. 2.5).
+//
+// One thread per element for the drift, kick and Taylor kernels: the
+// element arrays are ~1/s^2 of the grid, so these kernels are small next to
+// the per-site work.  The element arithmetic is written operation by
+// operation in a fixed order with non-contracting intrinsics, so that given
+// the same force arrays the element trajectories are reproducible to the
+// last bit by any FP64 restatement that uses the same order.
+#include "common.cuh"
+
+namespace vm {
+namespace {
+
+__device__ __forceinline__ void taylor_one(const Grid& g, const double* __restrict__ el, int m,
+                                           double* __restrict__ tay) {
+  const int ne = g.ne;
+  double x = el[EL_X * ne + m], v = el[EL_V * ne + m];
+  double Txx = el[EL_TXX * ne + m], Txv = el[EL_TXV * ne + m];
+  double Tvx = el[EL_TVX * ne + m], Tvv = el[EL_TVV * ne + m];
+  double det = dsub(dmul(Txx, Tvv), dmul(Txv, Tvx));
+  double Ti00 = Tvv / det, Ti01 = -Txv / det, Ti10 = -Tvx / det, Ti11 = Txx / det;
+  double* t = tay + (size_t)m * TY_N;
+  t[TY_X] = x;
+  t[TY_V] = v;
+  t[TY_TI00] = Ti00;
+  t[TY_TI01] = Ti01;
+  t[TY_TI10] = Ti10;
+  t[TY_TI11] = Ti11;
+#pragma unroll
+  for (int l = 0; l < 2; l++) {
+    double h0 = el[(EL_HXXX + 3 * l) * ne + m];
+    double h1 = el[(EL_HXXV + 3 * l) * ne + m];
+    double h2 = el[(EL_HXVV + 3 * l) * ne + m];
+    // A = H_l T^-1, G_l = [T^-1]^T A
+    double A00 = dadd(dmul(h0, Ti00), dmul(h1, Ti10));
+    double A01 = dadd(dmul(h0, Ti01), dmul(h1, Ti11));
+    double A10 = dadd(dmul(h1, Ti00), dmul(h2, Ti10));
+    double A11 = dadd(dmul(h1, Ti01), dmul(h2, Ti11));
+    t[TY_GX00 + 3 * l] = dadd(dmul(Ti00, A00), dmul(Ti10, A10));
+    t[TY_GX01 + 3 * l] = dadd(dmul(Ti00, A01), dmul(Ti10, A11));
+    t[TY_GX11 + 3 * l] = dadd(dmul(Ti01, A01), dmul(Ti11, A11));
+  }
+  int k = m / g.Lv, l = m - k * g.Lv;
+  t[TY_QX] = dadd(g.cx, dmul((double)(k - g.Kx - 1), g.dxm));
+  t[TY_QV] = dadd(g.cv, dmul((double)(l - g.Kv - 1), g.dvm));
+  t[14] = 0.0;
+  t[15] = 0.0;
+}
+
+// Half drift (predictor or corrector of Sec. 2.4): x, T_x. and H_x.. move
+// with v, T_v. and H_v..; optionally followed by the Taylor terms.
+__global__ void k_drift(Grid g, double* __restrict__ el, double* __restrict__ tay, int taylor) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= g.ne) return;
+  const int ne = g.ne;
+  double h = g.half_dt;
+  el[EL_X * ne + m] = dadd(el[EL_X * ne + m], dmul(el[EL_V * ne + m], h));
+  el[EL_TXX * ne + m] = dadd(el[EL_TXX * ne + m], dmul(el[EL_TVX * ne + m], h));
+  el[EL_TXV * ne + m] = dadd(el[EL_TXV * ne + m], dmul(el[EL_TVV * ne + m], h));
+#pragma unroll
+  for (int q = 0; q < 3; q++)
+    el[(EL_HXXX + q) * ne + m] = dadd(el[(EL_HXXX + q) * ne + m], dmul(el[(EL_HVXX + q) * ne + m], h));
+  if (taylor) taylor_one(g, el, m, tay);
+}
+
+__global__ void k_taylor(Grid g, const double* __restrict__ el, double* __restrict__ tay) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < g.ne) taylor_one(g, el, m, tay);
+}
+
+// Dual TSC interpolation (Sec. 2.5) at index coordinate u; beyond the grid
+// the values are lo (left) and hi (right).
+__device__ __forceinline__ double tsc(const double* __restrict__ A, int nx, double lo, double hi,
+                                      double u) {
+  if (!(u > -1e9 && u < 1e9)) return (u < 0.0) ? lo : hi;
+  long long i = (long long)floor(dadd(u, 0.5));
+  double w = dsub(u, (double)i);
+  double v0 = (i - 1 < 0) ? lo : ((i - 1 >= nx) ? hi : A[i - 1]);
+  double v1 = (i < 0) ? lo : ((i >= nx) ? hi : A[i]);
+  double v2 = (i + 1 < 0) ? lo : ((i + 1 >= nx) ? hi : A[i + 1]);
+  double a = dsub(0.5, w), b = dadd(0.5, w);
+  double wl = dmul(0.5, dmul(a, a));
+  double wc = dsub(0.75, dmul(w, w));
+  double wr = dmul(0.5, dmul(b, b));
+  return dadd(dadd(dmul(wl, v0), dmul(wc, v1)), dmul(wr, v2));
+}
+
+// Kick with a, a', a'' at the drifted positions, then the corrector drift.
+__global__ void k_kick_drift(Grid g, double* __restrict__ el, const double* __restrict__ a,
+                             const double* __restrict__ da, const double* __restrict__ d2a,
+                             const DevState* __restrict__ ds) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= g.ne) return;
+  const int ne = g.ne;
+  double Mt = ds->Mtot;
+  double alo = dmul(g.A, Mt), ahi = -dmul(g.A, Mt);
+  double x = el[EL_X * ne + m];
+  double u = dmul(dsub(x, g.x_lo), g.inv_dx);
+  double am = tsc(a, g.nx, alo, ahi, u);
+  double dam = tsc(da, g.nx, 0.0, 0.0, u);
+  double d2am = tsc(d2a, g.nx, 0.0, 0.0, u);
+  double dt = g.dt;
+  double v = dadd(el[EL_V * ne + m], dmul(am, dt));
+  double Txx = el[EL_TXX * ne + m], Txv = el[EL_TXV * ne + m];
+  double Tvx = dadd(el[EL_TVX * ne + m], dmul(dmul(dam, Txx), dt));
+  double Tvv = dadd(el[EL_TVV * ne + m], dmul(dmul(dam, Txv), dt));
+  double Hx0 = el[EL_HXXX * ne + m], Hx1 = el[EL_HXXV * ne + m], Hx2 = el[EL_HXVV * ne + m];
+  double Hv0 = dadd(el[EL_HVXX * ne + m], dmul(dadd(dmul(dam, Hx0), dmul(dmul(d2am, Txx), Txx)), dt));
+  double Hv1 = dadd(el[EL_HVXV * ne + m], dmul(dadd(dmul(dam, Hx1), dmul(dmul(d2am, Txx), Txv)), dt));
+  double Hv2 = dadd(el[EL_HVVV * ne + m], dmul(dadd(dmul(dam, Hx2), dmul(dmul(d2am, Txv), Txv)), dt));
+  double h = g.half_dt;
+  el[EL_X * ne + m] = dadd(x, dmul(v, h));
+  el[EL_V * ne + m] = v;
+  el[EL_TXX * ne + m] = dadd(Txx, dmul(Tvx, h));
+  el[EL_TXV * ne + m] = dadd(Txv, dmul(Tvv, h));
+  el[EL_TVX * ne + m] = Tvx;
+  el[EL_TVV * ne + m] = Tvv;
+  el[EL_HXXX * ne + m] = dadd(Hx0, dmul(Hv0, h));
+  el[EL_HXXV * ne + m] = dadd(Hx1, dmul(Hv1, h));
+  el[EL_HXVV * ne + m] = dadd(Hx2, dmul(Hv2, h));
+  el[EL_HVXX * ne + m] = Hv0;
+  el[EL_HVXV * ne + m] = Hv1;
+  el[EL_HVVV * ne + m] = Hv2;
+}
+
+// Isotropic elements on the lattice (remap, Sec. 1): P_m = Q_m, T = I, H = 0.
+__global__ void k_reset(Grid g, double* __restrict__ el) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= g.ne) return;
+  const int ne = g.ne;
+  int k = m / g.Lv, l = m - k * g.Lv;
+  el[EL_X * ne + m] = dadd(g.cx, dmul((double)(k - g.Kx - 1), g.dxm));
+  el[EL_V * ne + m] = dadd(g.cv, dmul((double)(l - g.Kv - 1), g.dvm));
+  el[EL_TXX * ne + m] = 1.0;
+  el[EL_TXV * ne + m] = 0.0;
+  el[EL_TVX * ne + m] = 0.0;
+  el[EL_TVV * ne + m] = 1.0;
+#pragma unroll
+  for (int q = EL_HXXX; q < EL_N; q++) el[q * ne + m] = 0.0;
+}
+
+// ---- double-double helpers for the compensated mass scan ----
+struct dd {
+  double hi, lo;
+};
+__device__ __forceinline__ dd two_sum(double a, double b) {
+  double s = dadd(a, b);
+  double bb = dsub(s, a);
+  double e = dadd(dsub(a, dsub(s, bb)), dsub(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+  dd s = two_sum(a.hi, b.hi);
+  double e = dadd(s.lo, dadd(a.lo, b.lo));
+  double h = dadd(s.hi, e);
+  double l = dsub(e, dsub(h, s.hi));
+  return {h, l};
+}
+__device__ __forceinline__ dd dd_neg(dd a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dd shfl_up_dd(dd v, int d) {
+  return {__shfl_up_sync(0xffffffffu, v.hi, d), __shfl_up_sync(0xffffffffu, v.lo, d)};
+}
+
+constexpr int SCAN_T = 1024;
+
+// Mass scan and force (Sec. 2.5, eq. of a(i)): one block; each thread owns
+// a contiguous chunk of pixels; pixel masses are summed in double-double so
+// that M_left and M_total carry ~30 digits before the final rounding.
+__global__ void __launch_bounds__(SCAN_T) k_scan_force(Grid g, const double* __restrict__ M,
+                                                       double* __restrict__ a, double* __restrict__ da,
+                                                       double* __restrict__ d2a, DevState* ds) {
+  __shared__ double sh_hi[SCAN_T / 32], sh_lo[SCAN_T / 32];
+  __shared__ double tot_hi, tot_lo;
+  const int nx = g.nx, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int C = (nx + SCAN_T - 1) / SCAN_T;
+  const int i0 = min(tid * C, nx), i1 = min(i0 + C, nx);
+  dd loc = {0.0, 0.0};
+  for (int i = i0; i < i1; i++) loc = dd_add(loc, dd{M[i], 0.0});
+  // inclusive warp scan
+  dd inc = loc;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    dd o = shfl_up_dd(inc, d);
+    if (lane >= d) inc = dd_add(o, inc);
+  }
+  if (lane == 31) {
+    sh_hi[wid] = inc.hi;
+    sh_lo[wid] = inc.lo;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    dd w = {sh_hi[lane], sh_lo[lane]};
+    dd wi = w;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      dd o = shfl_up_dd(wi, d);
+      if (lane >= d) wi = dd_add(o, wi);
+    }
+    // exclusive prefix of the warp totals
+    dd ex = shfl_up_dd(wi, 1);
+    if (lane == 0) ex = {0.0, 0.0};
+    sh_hi[lane] = ex.hi;
+    sh_lo[lane] = ex.lo;
+    if (lane == 31) {
+      tot_hi = wi.hi;
+      tot_lo = wi.lo;
+    }
+  }
+  __syncthreads();
+  dd excl = dd_add(dd{sh_hi[wid], sh_lo[wid]}, dd_add(inc, dd_neg(loc)));
+  dd tot = {tot_hi, tot_lo};
+  dd left_prev = excl;
+  for (int i = i0; i < i1; i++) {
+    dd left = dd_add(left_prev, dd{M[i], 0.0});
+    dd r = dd_add(dd_add(tot, dd_neg(left)), dd_neg(left_prev));
+    a[i] = dmul(g.A, dadd(r.hi, r.lo));
+    left_prev = left;
+  }
+  __syncthreads();
+  const double Mt = dadd(tot.hi, tot.lo);
+  const double alo = dmul(g.A, Mt), ahi = -dmul(g.A, Mt);
+  const double twodx = g.literal_fd ? g.dx : dmul(2.0, g.dx);
+  const double dx2 = dmul(g.dx, g.dx);
+  for (int i = i0; i < i1; i++) {
+    double am = (i > 0) ? a[i - 1] : alo;
+    double ap = (i < nx - 1) ? a[i + 1] : ahi;
+    da[i] = dsub(ap, am) / twodx;
+    d2a[i] = dsub(dadd(ap, am), dmul(2.0, a[i])) / dx2;
+  }
+  if (tid == 0) ds->Mtot = Mt;
+}
+
+__device__ __forceinline__ unsigned long long order_key(double d) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+template <typename R>
+__global__ void k_diag(Grid g, const R* __restrict__ f, const double* __restrict__ a,
+                       const double* __restrict__ el, DevState* ds) {
+  __shared__ double red[2][32];
+  double ms = 0.0, ek = 0.0;
+  const size_t n = (size_t)g.nx * g.nv;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
+    int j = (int)(p % g.nv);
+    double v = dadd(g.v_lo, dmul((double)j, g.dv));
+    double fv = (double)f[p];
+    ms += fv * g.dxdv;
+    ek += 0.5 * (v * v) * fv * g.dxdv;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ms += __shfl_down_sync(0xffffffffu, ms, o);
+    ek += __shfl_down_sync(0xffffffffu, ek, o);
+  }
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][wid] = ms;
+    red[1][wid] = ek;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a0 = 0, a1 = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+      a0 += red[0][w];
+      a1 += red[1][w];
+    }
+    atomicAdd(&ds->sum_mass, a0);
+    atomicAdd(&ds->sum_kin, a1);
+  }
+  // potential energy and det T range (grid-stride, atomics)
+  const double a8 = g.A * ds->Mtot;
+  double ep = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.nx; i += gridDim.x * blockDim.x)
+    ep += (a[i] * a[i] - a8 * a8) * g.dx;
+  if (ep != 0.0) atomicAdd(&ds->sum_pot, ep);
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < g.ne; m += gridDim.x * blockDim.x) {
+    const int ne = g.ne;
+    double d = el[EL_TXX * ne + m] * el[EL_TVV * ne + m] - el[EL_TXV * ne + m] * el[EL_TVX * ne + m];
+    unsigned long long k = order_key(d);
+    atomicMin(&ds->det_min_key, k);
+    atomicMax(&ds->det_max_key, k);
+  }
+}
+
+inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+void launch_drift(vm_solver* s, bool taylor) {
+  k_drift<<<blocks_for(s->g.ne, 256), 256, 0, s->stream>>>(s->g, s->el, s->tay, taylor ? 1 : 0);
+  s->launches++;
+}
+
+void launch_taylor(vm_solver* s) {
+  k_taylor<<<blocks_for(s->g.ne, 256), 256, 0, s->stream>>>(s->g, s->el, s->tay);
+  s->launches++;
+}
+
+void launch_kick_drift(vm_solver* s) {
+  k_kick_drift<<<blocks_for(s->g.ne, 256), 256, 0, s->stream>>>(s->g, s->el, s->a, s->da, s->d2a, s->ds);
+  s->launches++;
+}
+
+void launch_reset_elements(vm_solver* s) {
+  k_reset<<<blocks_for(s->g.ne, 256), 256, 0, s->stream>>>(s->g, s->el);
+  s->launches++;
+}
+
+void launch_scan_force(vm_solver* s) {
+  k_scan_force<<<1, SCAN_T, 0, s->stream>>>(s->g, s->M, s->a, s->da, s->d2a, s->ds);
+  s->launches++;
+}
+
+void launch_diagnostics(vm_solver* s) {
+  unsigned nb = blocks_for((long long)s->n, 256);
+  if (nb > 2048) nb = 2048;
+  if (s->fp32)
+    k_diag<float><<<nb, 256, 0, s->stream>>>(s->g, (const float*)s->f, s->a, s->el, s->ds);
+  else
+    k_diag<double><<<nb, 256, 0, s->stream>>>(s->g, (const double*)s->f, s->a, s->el, s->ds);
+  s->launches++;
+}
+
+}  // namespace vm

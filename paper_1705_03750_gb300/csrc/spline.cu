@@ -1,0 +1,120 @@
+// Cubic B-spline coefficients of f_ini (Sec. 2.2.2): for every x row a
+// tridiagonal system along v, then for every v column one along x.  The
+// systems share one constant matrix (rows (1, 4, 1)/6 with the zero-slope
+// ghosts eta_{-1} = eta_1, eta_n = eta_{n-2}), so its LU factors c'_i and
+// 1/den_i are computed once on the host and each system is one forward and
+// one backward sweep.
+//
+// Row systems are contiguous in memory: a warp owns 32 rows and walks them
+// in 32 x 32 tiles staged in shared memory, so global loads and stores stay
+// coalesced while each lane runs the sequential sweep of its own row.  Column
+// systems are strided by nv: one thread per column, so a warp's loads at a
+// given step are 32 consecutive values.
+#include "common.cuh"
+
+namespace vm {
+namespace {
+
+constexpr int RW = 4;  // warps per block for the row sweeps
+
+template <typename R, typename C>
+__global__ void __launch_bounds__(32 * RW) k_rows(Grid g, const R* __restrict__ src, R* __restrict__ dst,
+                                                  const C* __restrict__ th) {
+  __shared__ R tile[RW][32][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int row0 = (blockIdx.x * RW + w) * 32;
+  if (row0 >= g.nx) return;
+  const int nv = g.nv;
+  const C* cp = th;
+  const C* inv = th + nv;
+  const int myrow = row0 + lane;
+  R (*T)[33] = tile[w];
+  // forward sweep: d'_j = (6 f_j - sub_j d'_{j-1}) / den_j
+  R dprev = R(0);
+  for (int c0 = 0; c0 < nv; c0 += 32) {
+    for (int rr = 0; rr < 32; rr++) {
+      const int r = row0 + rr, c = c0 + lane;
+      T[rr][lane] = (r < g.nx && c < nv) ? src[(size_t)r * nv + c] : R(0);
+    }
+    __syncwarp();
+    const int cend = min(32, nv - c0);
+    for (int cc = 0; cc < cend; cc++) {
+      const int j = c0 + cc;
+      const R sub = (j == 0) ? R(0) : ((j == nv - 1) ? R(2) : R(1));
+      const R d = (R(6) * T[lane][cc] - sub * dprev) * (R)inv[j];
+      T[lane][cc] = d;
+      dprev = d;
+    }
+    __syncwarp();
+    for (int rr = 0; rr < 32; rr++) {
+      const int r = row0 + rr, c = c0 + lane;
+      if (r < g.nx && c < nv) dst[(size_t)r * nv + c] = T[rr][lane];
+    }
+    __syncwarp();
+  }
+  // backward sweep: eta_j = d'_j - c'_j eta_{j+1}
+  R enext = R(0);
+  const int last0 = ((nv - 1) / 32) * 32;
+  for (int c0 = last0; c0 >= 0; c0 -= 32) {
+    for (int rr = 0; rr < 32; rr++) {
+      const int r = row0 + rr, c = c0 + lane;
+      T[rr][lane] = (r < g.nx && c < nv) ? dst[(size_t)r * nv + c] : R(0);
+    }
+    __syncwarp();
+    const int cend = min(32, nv - c0);
+    for (int cc = cend - 1; cc >= 0; cc--) {
+      const int j = c0 + cc;
+      const R e = (j == nv - 1) ? T[lane][cc] : (T[lane][cc] - (R)cp[j] * enext);
+      T[lane][cc] = e;
+      enext = e;
+    }
+    __syncwarp();
+    for (int rr = 0; rr < 32; rr++) {
+      const int r = row0 + rr, c = c0 + lane;
+      if (r < g.nx && c < nv) dst[(size_t)r * nv + c] = T[rr][lane];
+    }
+    __syncwarp();
+  }
+  (void)myrow;
+}
+
+template <typename R, typename C>
+__global__ void __launch_bounds__(128) k_cols(Grid g, R* __restrict__ x, const C* __restrict__ th) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= g.nv) return;
+  const int nx = g.nx, nv = g.nv;
+  const C* cp = th;
+  const C* inv = th + nx;
+  R dprev = R(0);
+  for (int i = 0; i < nx; i++) {
+    const R sub = (i == 0) ? R(0) : ((i == nx - 1) ? R(2) : R(1));
+    const size_t p = (size_t)i * nv + j;
+    const R d = (R(6) * x[p] - sub * dprev) * (R)inv[i];
+    x[p] = d;
+    dprev = d;
+  }
+  R enext = x[(size_t)(nx - 1) * nv + j];
+  for (int i = nx - 2; i >= 0; i--) {
+    const size_t p = (size_t)i * nv + j;
+    const R e = x[p] - (R)cp[i] * enext;
+    x[p] = e;
+    enext = e;
+  }
+}
+
+}  // namespace
+
+void launch_spline_solve(vm_solver* s, const void* src, void* dst) {
+  const unsigned rb = (unsigned)((s->g.nx + 32 * RW - 1) / (32 * RW));
+  const unsigned cb = (unsigned)((s->g.nv + 127) / 128);
+  if (s->fp32) {
+    k_rows<float, float><<<rb, 32 * RW, 0, s->stream>>>(s->g, (const float*)src, (float*)dst, s->thomas_vf);
+    k_cols<float, float><<<cb, 128, 0, s->stream>>>(s->g, (float*)dst, s->thomas_xf);
+  } else {
+    k_rows<double, double><<<rb, 32 * RW, 0, s->stream>>>(s->g, (const double*)src, (double*)dst, s->thomas_v);
+    k_cols<double, double><<<cb, 128, 0, s->stream>>>(s->g, (double*)dst, s->thomas_x);
+  }
+  s->launches += 2;
+}
+
+}  // namespace vm

@@ -92,6 +92,17 @@ class Halos:
         return out
 
 
+    def on_grid(self, x: np.ndarray, v: np.ndarray) -> np.ndarray:
+        """The same sum on the tensor grid x (rows) by v (columns), using that
+        each halo is a product of a Gaussian in x and one in v."""
+        out = np.zeros((x.size, v.size))
+        for k in range(self.m.size):
+            gx = self.m[k] / (2.0 * math.pi * self.sx[k] * self.sv[k]) * np.exp(-0.5 * ((x - self.xc[k]) / self.sx[k]) ** 2)
+            gv = np.exp(-0.5 * ((v - self.vc[k]) / self.sv[k]) ** 2)
+            out += np.outer(gx, gv)
+        return out
+
+
 def draw_halos(seed: int, n: int = 16, centre: float = 0.5, sx=(0.02, 0.1), sv=(0.05, 0.2),
                mass=(0.1, 1.0)) -> Halos:
     """Draw halo parameters from numpy's default_rng(seed) in a fixed order:
@@ -114,7 +125,7 @@ def initial_f(cfg: RunConfig) -> np.ndarray:
         return spitzer(X, V, sigma=cfg.ic_params.get("sigma", 0.5), G=cfg.G if cfg.G else 1.0)
     if cfg.ic == "halos":
         h = draw_halos(cfg.seed, n=cfg.ic_params.get("n", 16))
-        return h(X, V)
+        return h.on_grid(cfg.x(), cfg.v())
     if cfg.ic == "blob":
         # a single warm Gaussian well inside the box (free-streaming checks)
         p = cfg.ic_params

@@ -1,0 +1,262 @@
+"""Thin ctypes binding of libvlamet (the C ABI declared in include/vlamet.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  PyTorch provides the device workspace and the stream.  There
+is no fallback: if the library is missing or no GPU is present, constructing
+a Solver raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libvlamet.so")
+
+VM_FP64, VM_FP32_MIXED = 0, 1
+VM_DTYPE_F64, VM_DTYPE_F32 = 0, 1
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "workspace too small", 3: "CUDA runtime error",
+          4: "unexplored-site repair did not converge", 5: "influence region larger than the largest window",
+          6: "memory budget exceeded", 7: "call out of order"}
+
+# Names of every entry point declared in include/vlamet.h.
+EXPORTS = ["vm_config_default", "vm_workspace_bytes", "vm_create", "vm_destroy", "vm_status_string",
+           "vm_lattice", "vm_set_f", "vm_set_elements", "vm_get_elements", "vm_compute_map",
+           "vm_reconstruct", "vm_step", "vm_remap", "vm_density_force", "vm_read_f", "vm_read_fini",
+           "vm_read_eta", "vm_read_map", "vm_diagnostics", "vm_sync", "vm_launch_count"]
+
+
+class VmConfig(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("nv", C.c_int32),
+        ("x_lo", C.c_double), ("x_hi", C.c_double), ("v_lo", C.c_double), ("v_hi", C.c_double),
+        ("elem_stride", C.c_int32), ("dt", C.c_double), ("n_s", C.c_int32), ("G", C.c_double),
+        ("precision", C.c_int32), ("alpha", C.c_double), ("beta", C.c_double),
+        ("pad", C.c_int32), ("literal_fd", C.c_int32), ("max_hole_rounds", C.c_int32),
+        ("reserved", C.c_int32),
+    ]
+
+
+class VmDiag(C.Structure):
+    _fields_ = [("mass", C.c_double), ("energy", C.c_double), ("detT_min", C.c_double),
+                ("detT_max", C.c_double), ("step", C.c_int64), ("cycle", C.c_int32),
+                ("holes", C.c_int32), ("hole_rounds", C.c_int32), ("overflow_elements", C.c_int32)]
+
+
+class VlametError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Open libvlamet.so (built by build.py / __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libvlamet.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, dp = C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_double)
+    sig = {
+        "vm_config_default": (None, [C.POINTER(VmConfig)]),
+        "vm_workspace_bytes": (C.c_size_t, [C.POINTER(VmConfig)]),
+        "vm_create": (i32, [C.POINTER(VmConfig), vp, C.c_size_t, vp, C.POINTER(vp)]),
+        "vm_destroy": (None, [vp]),
+        "vm_status_string": (C.c_char_p, [i32]),
+        "vm_lattice": (i32, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
+        "vm_set_f": (i32, [vp, vp, i32]),
+        "vm_set_elements": (i32, [vp, vp, i32]),
+        "vm_get_elements": (i32, [vp, vp, i32]),
+        "vm_compute_map": (i32, [vp]),
+        "vm_reconstruct": (i32, [vp]),
+        "vm_step": (i32, [vp, i32]),
+        "vm_remap": (i32, [vp]),
+        "vm_density_force": (i32, [vp, vp, vp, vp, vp, i32]),
+        "vm_read_f": (i32, [vp, vp, i32, i32]),
+        "vm_read_fini": (i32, [vp, vp, i32, i32]),
+        "vm_read_eta": (i32, [vp, vp, i32, i32]),
+        "vm_read_map": (i32, [vp, vp, i32]),
+        "vm_diagnostics": (i32, [vp, C.POINTER(VmDiag)]),
+        "vm_sync": (i32, [vp]),
+        "vm_launch_count": (i64, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(st: int, where: str) -> None:
+    if st != 0:
+        raise VlametError(st, where)
+
+
+@dataclass
+class Config:
+    nx: int
+    nv: int
+    x_lo: float
+    x_hi: float
+    v_lo: float
+    v_hi: float
+    s: int
+    dt: float
+    n_s: int
+    G: float
+    precision: int = VM_FP64
+    alpha: float = math.sqrt(3.0) / 4.0
+    beta: float = 0.5 * (1.0 - math.sqrt(3.0) / 2.0)
+    pad: int = 0
+    literal_fd: int = 0
+    max_hole_rounds: int = 0
+
+    @classmethod
+    def from_run(cls, rc, precision: int = VM_FP64) -> "Config":
+        return cls(rc.nx, rc.nv, rc.x_lo, rc.x_hi, rc.v_lo, rc.v_hi, rc.s, rc.dt, rc.n_s, rc.G, precision)
+
+    def c(self) -> VmConfig:
+        return VmConfig(self.nx, self.nv, self.x_lo, self.x_hi, self.v_lo, self.v_hi, self.s, self.dt,
+                        self.n_s, self.G, self.precision, self.alpha, self.beta, self.pad, self.literal_fd,
+                        self.max_hole_rounds, 0)
+
+
+def workspace_bytes(cfg: Config) -> int:
+    c = cfg.c()
+    return int(load().vm_workspace_bytes(C.byref(c)))
+
+
+class Solver:
+    """One solve on the current CUDA device, on a torch stream."""
+
+    def __init__(self, cfg: Config, stream=None, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("Solver needs a CUDA device")
+        self.L = load()
+        self.cfg = cfg
+        self._c = cfg.c()
+        nbytes = int(self.L.vm_workspace_bytes(C.byref(self._c)))
+        if nbytes == 0:
+            raise ValueError("invalid solver configuration")
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) & ~255
+        h = C.c_void_p()
+        _check(self.L.vm_create(C.byref(self._c), C.c_void_p(aligned), nbytes,
+                                C.c_void_p(self.stream.cuda_stream), C.byref(h)), "vm_create")
+        self.h = h
+        ne, lx, lv = C.c_int32(), C.c_int32(), C.c_int32()
+        self.L.vm_lattice(self.h, C.byref(ne), C.byref(lx), C.byref(lv))
+        self.ne, self.Lx, self.Lv = ne.value, lx.value, lv.value
+        self.nx, self.nv = cfg.nx, cfg.nv
+        self.fp32 = cfg.precision == VM_FP32_MIXED
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.vm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- pointers: a torch tensor (device) or a numpy array (host) ----
+    @staticmethod
+    def _ptr(x):
+        if isinstance(x, np.ndarray):
+            assert x.flags.c_contiguous
+            return C.c_void_p(x.ctypes.data), 0
+        assert x.is_contiguous()
+        return C.c_void_p(x.data_ptr()), (1 if x.is_cuda else 0)
+
+    def set_f(self, f0) -> None:
+        if isinstance(f0, np.ndarray):
+            f0 = np.ascontiguousarray(f0, dtype=np.float64)
+        p, dev = self._ptr(f0)
+        _check(self.L.vm_set_f(self.h, p, dev), "vm_set_f")
+
+    def set_elements(self, soa12) -> None:
+        if isinstance(soa12, np.ndarray):
+            soa12 = np.ascontiguousarray(soa12, dtype=np.float64)
+        p, dev = self._ptr(soa12)
+        _check(self.L.vm_set_elements(self.h, p, dev), "vm_set_elements")
+
+    def elements(self) -> np.ndarray:
+        out = np.empty((12, self.ne))
+        _check(self.L.vm_get_elements(self.h, C.c_void_p(out.ctypes.data), 0), "vm_get_elements")
+        return out
+
+    def compute_map(self) -> None:
+        _check(self.L.vm_compute_map(self.h), "vm_compute_map")
+
+    def reconstruct(self) -> None:
+        _check(self.L.vm_reconstruct(self.h), "vm_reconstruct")
+
+    def step(self, n: int = 1) -> None:
+        _check(self.L.vm_step(self.h, int(n)), "vm_step")
+
+    def remap(self) -> None:
+        _check(self.L.vm_remap(self.h), "vm_remap")
+
+    def sync(self) -> None:
+        _check(self.L.vm_sync(self.h), "vm_sync")
+
+    def density_force(self, out=None) -> dict:
+        """M, a, a', a'' ([nx] float64 each) of the last reconstruction.  With
+        ``out`` (a dict of device tensors) the copy stays on the device."""
+        if out is not None:
+            ptrs = [C.c_void_p(out[k].data_ptr()) if k in out else None for k in ("M", "a", "da", "d2a")]
+            _check(self.L.vm_density_force(self.h, *ptrs, 1), "vm_density_force")
+            return out
+        res = {k: np.empty(self.nx) for k in ("M", "a", "da", "d2a")}
+        _check(self.L.vm_density_force(self.h, *(C.c_void_p(res[k].ctypes.data) for k in ("M", "a", "da", "d2a")), 0),
+               "vm_density_force")
+        return res
+
+    def _read(self, fn, name, dtype=np.float64, out=None):
+        code = VM_DTYPE_F64 if dtype == np.float64 else VM_DTYPE_F32
+        if out is not None:
+            p, dev = self._ptr(out)
+            _check(fn(self.h, p, code, dev), name)
+            return out
+        res = np.empty((self.nx, self.nv), dtype=dtype)
+        _check(fn(self.h, C.c_void_p(res.ctypes.data), code, 0), name)
+        return res
+
+    def read_f(self, dtype=np.float64, out=None):
+        return self._read(self.L.vm_read_f, "vm_read_f", dtype, out)
+
+    def read_fini(self, dtype=np.float64, out=None):
+        return self._read(self.L.vm_read_fini, "vm_read_fini", dtype, out)
+
+    def read_eta(self, dtype=np.float64, out=None):
+        return self._read(self.L.vm_read_eta, "vm_read_eta", dtype, out)
+
+    def read_map(self) -> np.ndarray:
+        res = np.empty((self.nx, self.nv), dtype=np.int32)
+        _check(self.L.vm_read_map(self.h, C.c_void_p(res.ctypes.data), 0), "vm_read_map")
+        return res
+
+    def diagnostics(self) -> dict:
+        d = VmDiag()
+        _check(self.L.vm_diagnostics(self.h, C.byref(d)), "vm_diagnostics")
+        return {k: getattr(d, k) for k, _ in VmDiag._fields_}
+
+    @property
+    def launches(self) -> int:
+        return int(self.L.vm_launch_count(self.h))
