@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Benchmark of the metric semi-Lagrangian Vlasov-Poisson step on GB300.
+
+Metric: cell-updates/s (one grid site reconstructed in one time step; the
+remap every n_s steps is inside the timed steps) on the 4096 x 4096 halo
+workload (16 warm Gaussian halos, elements every 8 sites, dt = 0.002,
+remap every 25 steps), FP32-mixed path as the headline and the FP64 path
+beside it.  Synthetic seeded input; working set > L2, so no flush between
+steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Multi-GPU (torchrun): every rank advances its own independent solve (the
+method has no data-parallel exchange for independent problems: replicas,
+weak scaling); the timed region is bracketed by a barrier and a device
+synchronisation on every rank and the max over ranks is reported.
+
+--impl reference times the FP64 CPU oracle (the plain restatement of the
+paper used by the tests) on this machine's host cores on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1705_03750_gb300 import inputs as I  # noqa: E402
+
+METRIC = "cell-updates/s at 4096^2 (FP32 vs FP64 path)"
+WORKLOAD = I.HALOS_4096
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str, path: str | None = None):
+        self.gpu_id, self.path, self.proc = gpu_id, path, None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", self.gpu_id], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.path:
+            with open(self.path, "a") as fh:
+                fh.write(self.out)
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if p[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per kernel launch (see the design notes)
+# ---------------------------------------------------------------------------
+
+def algorithmic(kernel: str, rc, fp32: bool, ne: int):
+    """(bytes, unit count, per-unit description) of one launch: the bytes the
+    method must move at minimum, independent of how the kernel moves them."""
+    n = rc.nx * rc.nv
+    sr = 4 if fp32 else 8
+    tay = 16 * 8
+    if kernel == "reconstruct":
+        # map 4 + f_ini 1x + f 1x per site, Taylor records once per element
+        return n * (4 + 2 * sr) + ne * tay, n, f"{4 + 2 * sr} B/site + 128 B/element"
+    if kernel == "remap_resample":
+        return n * (4 + 2 * sr) + ne * tay, n, f"{4 + 2 * sr} B/site + 128 B/element"
+    if kernel == "claim_small":
+        # Taylor records of the 3x3 neighbourhood, one 16 B key read+write per site
+        return n * 32 + ne * 9 * tay, n, "32 B/site + 1152 B/element"
+    if kernel == "map_finalize":
+        return n * (16 + 16 + 4), n, "36 B/site"
+    if kernel in ("spline_rows", "spline_cols"):
+        return n * 4 * sr, n, f"{4 * sr} B/site (2 sweeps, read+write)"
+    if kernel in ("drift_taylor", "kick_drift"):
+        return ne * (24 * 8 + (tay if kernel == "drift_taylor" else 0)), ne, "element state r+w"
+    return None
+
+
+# ---------------------------------------------------------------------------
+# native arm
+# ---------------------------------------------------------------------------
+
+def run_native(args, rank: int, world: int, dist):
+    import torch
+    from paper_1705_03750_gb300 import vlamet as V
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    rc = WORKLOAD.with_(seed=WORKLOAD.seed + rank)
+    f0 = I.initial_f(rc)
+    f0_dev = torch.from_numpy(f0).to(dev)
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        gpu_id = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        gpu_id = str(dev.index)
+    peaks, peak_kind = _peaks()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    out = {}
+    for name, prec in (("fp32", V.VM_FP32_MIXED), ("fp64", V.VM_FP64)):
+        if args.precision not in ("both", name):
+            continue
+        s = V.Solver(V.Config.from_run(rc, prec))
+        s.set_f(f0_dev)
+        s.step(args.warmup)
+        s.sync()
+        stream = s.stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        launches0 = s.launches
+        barrier()
+        torch.cuda.synchronize(dev)
+        clocks = ClockSampler(gpu_id, os.path.join(ROOT, "gpurun_out", f"clocks_{name}.csv")
+                              if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+        with clocks:
+            e0.record(stream)
+            s.step(args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+        barrier()
+        s.sync()
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        launches = s.launches - launches0
+        # per-kernel device time over the same number of steps (events on the
+        # solver's stream around each launch)
+        s.profile(True)
+        s.step(args.steps)
+        stats = s.profile_read()
+        s.profile(False)
+        s.sync()
+        # end to end through the C ABI with host buffers: a new solve from a
+        # pinned host f0, then every step the density and force read back
+        e2e = None
+        if not args.no_e2e:
+            host_f0 = torch.from_numpy(f0).pin_memory()
+            outs = {k: torch.empty(rc.nx, dtype=torch.float64).pin_memory() for k in ("M", "a", "da", "d2a")}
+            se = V.Solver(V.Config.from_run(rc, prec))
+            se.sync()
+            barrier()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            def ptr(t):
+                return ctypes.c_void_p(t.data_ptr())
+
+            V._check(se.L.vm_set_f(se.h, ptr(host_f0), 0), "vm_set_f")
+            for _ in range(args.steps):
+                V._check(se.L.vm_step(se.h, 1), "vm_step")
+                V._check(se.L.vm_density_force(se.h, ptr(outs["M"]), ptr(outs["a"]), ptr(outs["da"]),
+                                               ptr(outs["d2a"]), 0), "vm_density_force")
+            torch.cuda.synchronize(dev)
+            te = max_over_ranks(time.perf_counter() - t0)
+            barrier()
+            e2e = {"value": world * rc.nx * rc.nv * args.steps / te, "unit": "cell-updates/s",
+                   "h2d_bytes_per_step": f0.nbytes / args.steps, "d2h_bytes_per_step": 4 * rc.nx * 8,
+                   "what": "vm_set_f from pinned host f0, then per step vm_step + vm_density_force to host"}
+            del se
+        out[name] = {"ms": ms, "launches": launches, "stats": stats, "clocks": clocks.summary(), "e2e": e2e,
+                     "ne": s.ne, "fp32": prec == V.VM_FP32_MIXED}
+        del s
+        torch.cuda.synchronize(dev)
+
+    if rank != 0:
+        return None
+    head = out.get("fp32") or out.get("fp64")
+    K = args.steps
+    cells = rc.nx * rc.nv
+    value = world * cells * K / (head["ms"] / 1e3)
+    # dominant kernel and its roofline
+    stats = head["stats"]
+    dom = max(stats, key=lambda k: stats[k][1])
+    nl, tms = stats[dom]
+    avg_s = tms / nl / 1e3
+    alg = algorithmic(dom, rc, head["fp32"], head["ne"])
+    roof = {"kernel": dom, "launches_per_step": nl / K, "avg_ms": tms / nl,
+            "share_of_step": tms / sum(v[1] for v in stats.values())}
+    if alg is not None:
+        b, units, per = alg
+        ach = b / avg_s / 1e9
+        roof.update({"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": ach / peaks["hbm_gbs"], "traffic": None, "per_unit": per, "units": units,
+                     "peak_kind": peak_kind})
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "cell-updates/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": head["ms"] / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64 (f32 f/eta/interpolation, f64 elements, map decisions, mass scan)" if head["fp32"] else "f64",
+        "data": "synthetic (seeded 16-halo initial condition)",
+        "config": {"workload": rc.name, "nx": rc.nx, "nv": rc.nv, "elem_stride": rc.s, "dt": rc.dt,
+                   "n_s": rc.n_s, "G": rc.G, "remaps_in_timed_steps": (args.warmup + K) // rc.n_s - args.warmup // rc.n_s,
+                   "l2": "working set > L2 (129 MB): no flush", "parallelism": f"replicas x{world}"},
+        "clocks": head["clocks"],
+        "e2e": head["e2e"],
+        "gpu_launches": head["launches"],
+        "roofline": roof,
+        "kernels": {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in sorted(stats.items(), key=lambda kv: -kv[1][1])},
+    }
+    if "fp64" in out and head is not out["fp64"]:
+        f64 = out["fp64"]
+        line["fp64_path"] = {"value": world * cells * K / (f64["ms"] / 1e3), "ms_per_step": f64["ms"] / K,
+                             "gpu_launches": f64["launches"], "clocks": f64["clocks"],
+                             "e2e": f64["e2e"],
+                             "top_kernels": {k: round(v[1], 3) for k, v in sorted(f64["stats"].items(), key=lambda kv: -kv[1][1])[:4]}}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(rc, f0)
+    return line
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def _cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(rc, f0, transport_steps: int = 3) -> dict:
+    """The FP64 oracle (OpenMP over sites, all host cores) on a bounded
+    sample of the same workload: `transport_steps` steps and one remap;
+    per-step cost = transport + remap / n_s."""
+    import oracle.oracle as O
+    o = O.Oracle(rc.nx, rc.nv, rc.x_lo, rc.x_hi, rc.v_lo, rc.v_hi, rc.s, rc.dt, 10 ** 9, rc.G)
+    o.set_f(f0)
+    t0 = time.perf_counter()
+    o.step(transport_steps)
+    t1 = time.perf_counter()
+    o.remap()
+    t2 = time.perf_counter()
+    per_step = (t1 - t0) / transport_steps + (t2 - t1) / rc.n_s
+    return {"value": rc.nx * rc.nv / per_step, "unit": "cell-updates/s", "cores": _cores(), "kind": "oracle",
+            "sample": f"{rc.name}: {transport_steps} transport steps + 1 remap timed "
+                      f"({t2 - t0:.1f} s); rate = sites / (step + remap/{rc.n_s})"}
+
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return None
+    rc = WORKLOAD
+    f0 = I.initial_f(rc)
+    import oracle.oracle as O
+    o = O.Oracle(rc.nx, rc.nv, rc.x_lo, rc.x_hi, rc.v_lo, rc.v_hi, rc.s, rc.dt, rc.n_s, rc.G)
+    o.set_f(f0)
+    # one timed step of the full grid costs ~1 s on 16 cores: keep the whole
+    # run to a few minutes by timing at most `cap` of the K steps
+    cap = max(1, min(args.steps, args.ref_cap))
+    o.step(min(args.warmup, 3))
+    t0 = time.perf_counter()
+    o.step(cap)
+    dt = time.perf_counter() - t0
+    value = rc.nx * rc.nv * cap / dt
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / cap * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded 16-halo initial condition)",
+        "config": {"workload": rc.name, "nx": rc.nx, "nv": rc.nv, "elem_stride": rc.s, "dt": rc.dt, "n_s": rc.n_s},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": _cores(), "kind": "oracle",
+                         "sample": f"{cap} consecutive full-grid steps of {rc.name} (remaps at their cadence)"},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default="both", choices=["both", "fp32", "fp64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-cap", type=int, default=20)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        line = run_reference(args, rank)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as D
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+            D.init_process_group("nccl")
+            dist = D
+        from paper_1705_03750_gb300 import build as B
+        B.build()
+        line = run_native(args, rank, world, dist)
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

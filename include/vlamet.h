@@ -164,6 +164,20 @@ vm_status vm_sync(vm_solver* s);
  * kept on the host, for launch accounting). */
 int64_t vm_launch_count(const vm_solver* s);
 
+/* Optional per-kernel timing: when enabled, every launch is bracketed by a
+ * pair of CUDA events on the solver's stream; vm_profile_read waits for
+ * them and returns, per kernel that ran, its launch count and total device
+ * time since the last vm_profile call (at most `max` entries written to
+ * `out`; the return value is the number of kernels that ran, or -1).
+ * Intended for measurement runs; off by default. */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double total_ms;
+} vm_kernel_stat;
+vm_status vm_profile(vm_solver* s, int32_t enable);
+int32_t vm_profile_read(vm_solver* s, vm_kernel_stat* out, int32_t max);
+
 #ifdef __cplusplus
 }
 #endif

@@ -85,6 +85,7 @@ def lib(openmp: bool = True) -> C.CDLL:
             "vo_get_taylor": (None, [C.c_void_p, _D]),
             "vo_compute_map": (C.c_int32, [C.c_void_p, _I32]),
             "vo_map_stats": (C.c_int32, [C.c_void_p, _I64, _I64, _I32]),
+            "vo_component_bbox": (None, [C.c_void_p, _I32]),
             "vo_reconstruct": (C.c_int32, [C.c_void_p, _D]),
             "vo_density_force": (None, [C.c_void_p, _D, _D, _D, _D, _D]),
             "vo_step": (C.c_int32, [C.c_void_p, C.c_int32]),
@@ -246,6 +247,13 @@ class Oracle:
         a, b, c = C.c_int64(), C.c_int64(), C.c_int32()
         self.L.vo_map_stats(self.h, C.byref(a), C.byref(b), C.byref(c))
         return {"multi_claims": a.value, "holes": b.value, "rounds": c.value}
+
+    def component_bbox(self) -> np.ndarray:
+        """[ne, 4]: i_min, i_max, j_min, j_max of each element's component in
+        the last percolation (min > max when empty)."""
+        out = np.empty((self.ne, 4), dtype=np.int32)
+        self.L.vo_component_bbox(self.h, _ip(out))
+        return out
 
     def reconstruct(self) -> np.ndarray:
         out = np.empty((self.nx, self.nv))

@@ -75,6 +75,7 @@ struct vo_state {
   int32_t* prevmap;
   int64_t stat_multi, stat_holes;
   int32_t stat_rounds;
+  int32_t* bbox; /* per element: i_min, i_max, j_min, j_max of its component */
 };
 
 /* ------------------------------------------------------------------ */
@@ -435,6 +436,7 @@ vo_state* vo_create(const vo_config* c) {
   S->bestkey = (uint64_t*)malloc(sizeof(uint64_t) * n);
   S->stamp = (int32_t*)malloc(sizeof(int32_t) * np);
   S->queue = (int32_t*)malloc(sizeof(int32_t) * np);
+  S->bbox = (int32_t*)malloc(sizeof(int32_t) * 4 * (size_t)S->ne);
   S->M = (double*)calloc((size_t)c->nx, sizeof(double));
   S->a = (double*)calloc((size_t)c->nx, sizeof(double));
   S->da = (double*)calloc((size_t)c->nx, sizeof(double));
@@ -455,6 +457,7 @@ void vo_destroy(vo_state* S) {
   free(S->bestkey);
   free(S->stamp);
   free(S->queue);
+  free(S->bbox);
   free(S->M);
   free(S->a);
   free(S->da);
@@ -612,6 +615,9 @@ static int32_t percolate(vo_state* S) {
   for (int64_t p = 0; p < PW * PH; p++) S->stamp[p] = -1;
   S->stat_multi = 0;
   for (int32_t m = 0; m < S->ne; m++) {
+    int32_t* bb = S->bbox + 4 * (size_t)m;
+    bb[0] = bb[2] = 1;
+    bb[1] = bb[3] = 0;
     /* start from the grid site nearest to P_m */
     double us = (S->el[m].x - S->c.x_lo) * S->inv_dx;
     double ws = (S->el[m].v - S->c.v_lo) * S->inv_dv;
@@ -623,6 +629,8 @@ static int32_t percolate(vo_state* S) {
     double d2;
     if (!passes(S, m, site_x(S, i0), site_v(S, j0), &d2)) continue;
     claim(S, i0, j0, m, d2);
+    bb[0] = bb[1] = (int32_t)i0;
+    bb[2] = bb[3] = (int32_t)j0;
     int64_t qh = 0, qt = 0;
     S->queue[qt++] = (int32_t)p0;
     while (qh < qt) {
@@ -637,6 +645,10 @@ static int32_t percolate(vo_state* S) {
         S->stamp[pp] = m;
         if (passes(S, m, site_x(S, ii), site_v(S, jj), &d2)) {
           claim(S, ii, jj, m, d2);
+          if (ii < bb[0]) bb[0] = (int32_t)ii;
+          if (ii > bb[1]) bb[1] = (int32_t)ii;
+          if (jj < bb[2]) bb[2] = (int32_t)jj;
+          if (jj > bb[3]) bb[3] = (int32_t)jj;
           S->queue[qt++] = (int32_t)pp;
         }
       }
@@ -690,6 +702,13 @@ int32_t vo_compute_map(vo_state* S, int32_t* map_out) {
   int32_t st = percolate(S);
   if (map_out) memcpy(map_out, S->map, sizeof(int32_t) * (size_t)S->c.nx * S->c.nv);
   return st;
+}
+
+/* Bounding box (i_min, i_max, j_min, j_max, padded-lattice indices) of each
+ * element's connected component in the last percolation; empty components
+ * have min > max. */
+void vo_component_bbox(const vo_state* S, int32_t* out4xne) {
+  memcpy(out4xne, S->bbox, sizeof(int32_t) * 4 * (size_t)S->ne);
 }
 
 int32_t vo_map_stats(const vo_state* S, int64_t* multi, int64_t* holes, int32_t* rounds) {

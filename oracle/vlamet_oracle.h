@@ -70,6 +70,7 @@ void vo_get_elements(const vo_state* S, double* out12xne_aos);
 void vo_set_elements(vo_state* S, const double* in12xne_aos);
 void vo_get_taylor(vo_state* S, double* out14xne_aos);
 int32_t vo_compute_map(vo_state* S, int32_t* map_out);
+void vo_component_bbox(const vo_state* S, int32_t* out4xne);
 int32_t vo_map_stats(const vo_state* S, int64_t* claimed_multi, int64_t* holes, int32_t* rounds);
 int32_t vo_reconstruct(vo_state* S, double* f_out);
 void vo_density_force(const vo_state* S, double* M, double* a, double* da, double* d2a,

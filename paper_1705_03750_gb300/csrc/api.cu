@@ -60,7 +60,7 @@ Layout layout(const vm_config* c) {
   L.keys = take(n * 16);
   L.holes_a = take(n * 4);
   L.holes_b = take(2 * n * 4);
-  L.ovf = take(ne * 4);
+  L.ovf = take(2 * ne * 8);
   L.el = take(12 * ne * 8);
   L.tay = take(16 * ne * 8);
   L.M = take(c->nx * 8);
@@ -91,6 +91,8 @@ void thomas(int n, std::vector<double>& out) {
     cprev = cp;
   }
 }
+
+size_t ne_total(const vm_solver* s) { return (size_t)s->g.ne; }
 
 vm_status check_launch(vm_solver* s) {
   (void)s;
@@ -139,7 +141,49 @@ vm_status read_real(vm_solver* s, const void* src, void* out, int32_t dtype, int
   return vm_sync(s);
 }
 
+const char* const kKernelNames[vm::KID_N] = {
+    "drift_taylor", "taylor", "kick_drift", "reset_elements", "scan_force", "diagnostics",
+    "map_clear", "claim_small", "claim_large", "map_finalize", "holes",
+    "reconstruct", "remap_resample", "convert", "spline_rows", "spline_cols"};
+
 }  // namespace
+
+namespace vm {
+
+int prof_begin(vm_solver* s, int kid) {
+  if (!s->prof) return -1;
+  if (s->prof_n >= PROF_CAP) prof_flush(s);
+  const int slot = s->prof_n++;
+  if (slot >= s->prof_created) {
+    cudaEventCreate(&s->prof_ev[2 * slot]);
+    cudaEventCreate(&s->prof_ev[2 * slot + 1]);
+    s->prof_created = slot + 1;
+  }
+  s->prof_kind[slot] = kid;
+  cudaEventRecord(s->prof_ev[2 * slot], s->stream);
+  return slot;
+}
+
+void prof_end(vm_solver* s, int slot) {
+  if (slot < 0) return;
+  cudaEventRecord(s->prof_ev[2 * slot + 1], s->stream);
+}
+
+// Wait for the recorded launches and fold their durations into the totals.
+void prof_flush(vm_solver* s) {
+  if (s->prof_n == 0) return;
+  cudaEventSynchronize(s->prof_ev[2 * (s->prof_n - 1) + 1]);
+  for (int i = 0; i < s->prof_n; i++) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, s->prof_ev[2 * i], s->prof_ev[2 * i + 1]) == cudaSuccess) {
+      s->prof_ms[s->prof_kind[i]] += ms;
+      s->prof_count[s->prof_kind[i]]++;
+    }
+  }
+  s->prof_n = 0;
+}
+
+}  // namespace vm
 
 extern "C" {
 
@@ -222,7 +266,8 @@ vm_status vm_create(const vm_config* c, void* d_workspace, size_t bytes, void* s
   s->keys = (unsigned long long*)(base + L.keys);
   s->holes_a = (int32_t*)(base + L.holes_a);
   s->holes_b = (int32_t*)(base + L.holes_b);
-  s->overflow_list = (int32_t*)(base + L.ovf);
+  s->overflow_list = (int2*)(base + L.ovf);
+  s->overflow_list2 = s->overflow_list + ne_total(s);
   s->el = (double*)(base + L.el);
   s->tay = (double*)(base + L.tay);
   s->M = (double*)(base + L.M);
@@ -234,6 +279,10 @@ vm_status vm_create(const vm_config* c, void* d_workspace, size_t bytes, void* s
   s->thomas_xf = (float*)(base + L.thxf);
   s->thomas_vf = (float*)(base + L.thvf);
   s->ds = (vm::DevState*)(base + L.ds);
+  if (!vm::map_prepare(g)) {
+    free(s);
+    return VM_E_INVALID_ARG;
+  }
   std::vector<double> tx, tv;
   thomas(c->nx, tx);
   thomas(c->nv, tv);
@@ -264,7 +313,39 @@ vm_status vm_create(const vm_config* c, void* d_workspace, size_t bytes, void* s
   return VM_OK;
 }
 
-void vm_destroy(vm_solver* s) { free(s); }
+void vm_destroy(vm_solver* s) {
+  if (!s) return;
+  for (int i = 0; i < 2 * s->prof_created; i++) cudaEventDestroy(s->prof_ev[i]);
+  free(s);
+}
+
+vm_status vm_profile(vm_solver* s, int32_t enable) {
+  if (!s) return VM_E_INVALID_ARG;
+  vm::prof_flush(s);
+  for (int k = 0; k < vm::KID_N; k++) {
+    s->prof_ms[k] = 0.0;
+    s->prof_count[k] = 0;
+  }
+  s->prof = enable ? 1 : 0;
+  return VM_OK;
+}
+
+int32_t vm_profile_read(vm_solver* s, vm_kernel_stat* out, int32_t max) {
+  if (!s) return -1;
+  vm::prof_flush(s);
+  int32_t n = 0;
+  for (int k = 0; k < vm::KID_N; k++) {
+    if (s->prof_count[k] == 0) continue;
+    if (out && n < max) {
+      memset(&out[n], 0, sizeof out[n]);
+      strncpy(out[n].name, kKernelNames[k], sizeof out[n].name - 1);
+      out[n].launches = s->prof_count[k];
+      out[n].total_ms = s->prof_ms[k];
+    }
+    n++;
+  }
+  return n;
+}
 
 vm_status vm_lattice(const vm_solver* s, int32_t* ne, int32_t* Lx, int32_t* Lv) {
   if (!s) return VM_E_INVALID_ARG;

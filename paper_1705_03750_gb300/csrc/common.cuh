@@ -34,9 +34,10 @@ struct DevState {
   int32_t nholes;        // holes in the working list
   int32_t holes_found;   // holes left by the claims (statistics)
   int32_t hole_rounds;   // repair rounds of the last map (statistics)
-  int32_t noverflow;     // elements queued for the large flood-fill window
+  int32_t noverflow;     // elements queued for the band / large windows
   int32_t overflow_stat;
-  int32_t pad0, pad1;
+  int32_t noverflow2;    // elements queued for the last-resort window
+  int32_t overflow2_stat;
   double Mtot;           // total mass of the last reconstruction
   double sum_mass, sum_kin, sum_pot;
   unsigned long long det_min_key, det_max_key;
@@ -50,6 +51,14 @@ enum { TY_X = 0, TY_V, TY_TI00, TY_TI01, TY_TI10, TY_TI11, TY_GX00, TY_GX01, TY_
        TY_GV00, TY_GV01, TY_GV11, TY_QX, TY_QV, TY_N = 16 };
 
 constexpr unsigned long long KEY_EMPTY = ~0ull;
+
+// Kernel identities for the optional per-launch timing (vm_profile).
+enum KernelId {
+  KID_DRIFT = 0, KID_TAYLOR, KID_KICK_DRIFT, KID_RESET, KID_SCAN_FORCE, KID_DIAG,
+  KID_MAP_CLEAR, KID_CLAIM_SMALL, KID_CLAIM_LARGE, KID_FINALIZE, KID_HOLES,
+  KID_RECON, KID_REMAP, KID_CONVERT, KID_SPLINE_ROWS, KID_SPLINE_COLS, KID_N
+};
+constexpr int PROF_CAP = 1024;
 
 }  // namespace vm
 
@@ -69,7 +78,8 @@ struct vm_solver {
   unsigned long long* keys;  // 2 words per site: {element index, bits of d^2}
   int32_t* holes_a;
   int32_t* holes_b;
-  int32_t* overflow_list;
+  int2* overflow_list;      // (element, window mode) for the second tier
+  int2* overflow_list2;     // for the last-resort tier
   double* el;               // 12 x ne
   double* tay;              // ne x 16
   double* M;                // pixel masses of the last step
@@ -86,9 +96,22 @@ struct vm_solver {
   int64_t nstep;
   int32_t cyc;
   int64_t launches;
+  // optional per-launch timing: event pairs around each launch
+  int32_t prof;
+  int32_t prof_n;
+  int32_t prof_created;
+  int32_t prof_kind[vm::PROF_CAP];
+  cudaEvent_t prof_ev[2 * vm::PROF_CAP];
+  int64_t prof_count[vm::KID_N];
+  double prof_ms[vm::KID_N];
 };
 
 namespace vm {
+
+// ---- per-launch timing (no-ops unless vm_profile enabled it) ----
+int prof_begin(vm_solver* s, int kid);
+void prof_end(vm_solver* s, int slot);
+void prof_flush(vm_solver* s);
 
 // ---- launchers (each in the translation unit of its kernels) ----
 // elements.cu
@@ -99,6 +122,7 @@ void launch_reset_elements(vm_solver* s);
 void launch_scan_force(vm_solver* s);
 void launch_diagnostics(vm_solver* s);
 // map.cu
+bool map_prepare(const Grid& g);
 void launch_map(vm_solver* s);
 // recon.cu
 void launch_reconstruct(vm_solver* s);

@@ -287,37 +287,39 @@ inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) /
 }  // namespace
 
 void launch_drift(vm_solver* s, bool taylor) {
-  k_drift<<<blocks_for(s->g.ne, 256), 256, 0, s->stream>>>(s->g, s->el, s->tay, taylor ? 1 : 0);
+  { const int ps_ = prof_begin(s, KID_DRIFT); k_drift<<<blocks_for(s->g.ne, 256), 256, 0, s->stream>>>(s->g, s->el, s->tay, taylor ? 1 : 0); prof_end(s, ps_); }
   s->launches++;
 }
 
 void launch_taylor(vm_solver* s) {
-  k_taylor<<<blocks_for(s->g.ne, 256), 256, 0, s->stream>>>(s->g, s->el, s->tay);
+  { const int ps_ = prof_begin(s, KID_TAYLOR); k_taylor<<<blocks_for(s->g.ne, 256), 256, 0, s->stream>>>(s->g, s->el, s->tay); prof_end(s, ps_); }
   s->launches++;
 }
 
 void launch_kick_drift(vm_solver* s) {
-  k_kick_drift<<<blocks_for(s->g.ne, 256), 256, 0, s->stream>>>(s->g, s->el, s->a, s->da, s->d2a, s->ds);
+  { const int ps_ = prof_begin(s, KID_KICK_DRIFT); k_kick_drift<<<blocks_for(s->g.ne, 256), 256, 0, s->stream>>>(s->g, s->el, s->a, s->da, s->d2a, s->ds); prof_end(s, ps_); }
   s->launches++;
 }
 
 void launch_reset_elements(vm_solver* s) {
-  k_reset<<<blocks_for(s->g.ne, 256), 256, 0, s->stream>>>(s->g, s->el);
+  { const int ps_ = prof_begin(s, KID_RESET); k_reset<<<blocks_for(s->g.ne, 256), 256, 0, s->stream>>>(s->g, s->el); prof_end(s, ps_); }
   s->launches++;
 }
 
 void launch_scan_force(vm_solver* s) {
-  k_scan_force<<<1, SCAN_T, 0, s->stream>>>(s->g, s->M, s->a, s->da, s->d2a, s->ds);
+  { const int ps_ = prof_begin(s, KID_SCAN_FORCE); k_scan_force<<<1, SCAN_T, 0, s->stream>>>(s->g, s->M, s->a, s->da, s->d2a, s->ds); prof_end(s, ps_); }
   s->launches++;
 }
 
 void launch_diagnostics(vm_solver* s) {
   unsigned nb = blocks_for((long long)s->n, 256);
   if (nb > 2048) nb = 2048;
+  const int ps_ = prof_begin(s, KID_DIAG);
   if (s->fp32)
     k_diag<float><<<nb, 256, 0, s->stream>>>(s->g, (const float*)s->f, s->a, s->el, s->ds);
   else
     k_diag<double><<<nb, 256, 0, s->stream>>>(s->g, (const double*)s->f, s->a, s->el, s->ds);
+  prof_end(s, ps_);
   s->launches++;
 }
 

@@ -1,22 +1,30 @@
 // Influence map of the elements of metric (Sec. 2.3.1).
 //
-// Element-parallel percolation.  Each element is handled by one thread
-// block that holds, in shared memory, bit masks of a window of the Eulerian
-// grid centred on the element's start site: "evaluated" and "claimed"
-// (the connected component grown so far).  The flood fill is lazy: each
-// round dilates the component by one site in the four directions and runs
-// the percolation test only on the newly reached sites, so the test runs
-// once per site of the component and once per site of its rim, as in a
-// breadth-first search, while the dilation itself is a few word operations
-// per window row.
+// Element-parallel percolation: the claimed set of element m is the
+// 4-connected component, containing the grid site nearest to P_m, of the
+// sites that pass m's test (no investigated neighbour proposes a strictly
+// smaller d).  Each element is flood-filled inside a window of bit masks
+// held in shared memory (evaluated / passing / claimed), with the window
+// sized in three tiers:
 //
-// Claims are resolved with one 128-bit atomic compare-and-swap minimum per
-// claimed site on the key (bits of d^2, element index): the smallest
-// distance wins, ties go to the smaller index.  A finalize pass turns keys
-// into the int32 map, resets them and lists the sites nobody claimed; a
-// single-block pass then repairs those in Jacobi rounds from their
-// 4-neighbours.  Elements whose component reaches the edge of the small
-// window are queued and redone with a 4x larger window.
+//   1. a 64 x 128 window, one warp per element, one percolation test per
+//      newly reached site (lazy breadth-first growth: the test runs once per
+//      site of the component and of its rim);
+//   2. for the elements whose component reached the edge of tier 1: a band
+//      window, 64 sites across and the whole padded lattice along the
+//      direction in which the component escaped, or a 256 x 256 window if
+//      it escaped both ways.  Elements of the outer layer whose neighbours
+//      have moved away claim long thin bands; to cross them in few rounds,
+//      any 64-site word the component reaches is evaluated whole, and the
+//      component is then extended through runs of passing sites inside the
+//      word with one carry-propagating addition;
+//   3. a 256 x 256 window for band elements that outgrew the band.
+//
+// Claims are resolved by one 128-bit atomic compare-and-swap minimum per
+// claimed site on the key (bits of d^2, element index): smallest distance
+// wins, ties go to the smaller index.  A finalize pass turns keys into the
+// int32 map, resets them and lists unclaimed sites; one block repairs those
+// in Jacobi rounds from their 4-neighbours.
 //
 // Every decision (ranges, the d comparisons, the claim order) is taken on
 // FP64 values computed operation by operation in a fixed order.
@@ -39,8 +47,7 @@ __device__ __forceinline__ void alpha_range(double r, double alpha, int& lo, int
 }
 
 // Percolation test of site P for the centre element of a 3x3 block of
-// Taylor records (index 4): it fails if an investigated, existing neighbour
-// proposes a strictly smaller distance.
+// Taylor records (index 4).
 __device__ bool pass_test(const Grid& g, const double (*T9)[TY_N], const int* ex9, double Px,
                           double Pv, double& d2) {
   double xi, ze;
@@ -51,10 +58,10 @@ __device__ bool pass_test(const Grid& g, const double (*T9)[TY_N], const int* ex
   for (int a = a0; a <= a1; a++)
     for (int b = b0; b <= b1; b++) {
       if (a == 0 && b == 0) continue;
-      int q = (a + 1) * 3 + (b + 1);
+      const int q = (a + 1) * 3 + (b + 1);
       if (!ex9[q]) continue;
       double x2, z2;
-      double dn = dist2_exact(T9[q], g, Px, Pv, x2, z2);
+      const double dn = dist2_exact(T9[q], g, Px, Pv, x2, z2);
       if (dn < d2) return false;
     }
   return true;
@@ -77,109 +84,124 @@ __device__ __forceinline__ ulonglong2 cas128(unsigned long long* addr, ulonglong
   return old;
 }
 
-// keys[2p] = element index, keys[2p+1] = bits of d^2 (a 128-bit integer
-// whose order is the claim order).
+// keys[2p] = element index, keys[2p+1] = bits of d^2: as a 128-bit integer
+// its order is the claim order.
 __device__ __forceinline__ void claim_min(unsigned long long* key2, unsigned long long dbits,
                                           unsigned long long idx) {
   ulonglong2 cur = __ldcg(reinterpret_cast<const ulonglong2*>(key2));
-  ulonglong2 val = make_ulonglong2(idx, dbits);
+  const ulonglong2 val = make_ulonglong2(idx, dbits);
   while (dbits < cur.y || (dbits == cur.y && idx < cur.x)) {
-    ulonglong2 prev = cas128(key2, cur, val);
+    const ulonglong2 prev = cas128(key2, cur, val);
     if (prev.x == cur.x && prev.y == cur.y) break;
     cur = prev;
   }
 }
 
+__device__ __forceinline__ void claim_site(const Grid& g, unsigned long long* keys, long long i, long long j,
+                                           double d2, int m) {
+  if (i >= 0 && i < g.nx && j >= 0 && j < g.nv)
+    claim_min(keys + 2 * ((size_t)i * g.nv + j), dkey(d2), (unsigned long long)m);
+}
+
 // Mask of window columns [lo, hi) within word w (64 columns per word).
 __device__ __forceinline__ unsigned long long col_mask(int w, int lo, int hi) {
-  int a = max(lo - 64 * w, 0), b = min(hi - 64 * w, 64);
+  const int a = max(lo - 64 * w, 0), b = min(hi - 64 * w, 64);
   if (b <= a) return 0ull;
-  unsigned long long up = (b >= 64) ? ~0ull : ((1ull << b) - 1ull);
-  unsigned long long dn = (a <= 0) ? 0ull : ((1ull << a) - 1ull);
+  const unsigned long long up = (b >= 64) ? ~0ull : ((1ull << b) - 1ull);
+  const unsigned long long dn = (a <= 0) ? 0ull : ((1ull << a) - 1ull);
   return up & ~dn;
 }
 
-template <int ROWS, int WORDS, int T>
-struct ClaimShared {
+// Bits of P reachable from the seeds S (S inside P) through runs of set
+// bits of P, in both directions along the word.
+__device__ __forceinline__ unsigned long long run_fill(unsigned long long S, unsigned long long P) {
+  S &= P;
+  const unsigned long long up = (((P + S) ^ P) & P) | S;
+  const unsigned long long Pr = __brevll(P), Sr = __brevll(S);
+  const unsigned long long dn = __brevll((((Pr + Sr) ^ Pr) & Pr) | Sr);
+  return up | dn;
+}
+
+enum : int { MODE_BAND_V = 0, MODE_BAND_X = 1, MODE_FAT = 2 };
+
+__device__ __forceinline__ void load_T9(const Grid& g, int m, const double* __restrict__ tay,
+                                        double (*T9)[TY_N], int* ex9) {
+  const int k = m / g.Lv, l = m - k * g.Lv;
+  for (int idx = threadIdx.x; idx < 9 * TY_N; idx += blockDim.x) {
+    const int q = idx / TY_N, c = idx - q * TY_N;
+    const int kk = k + q / 3 - 1, ll = l + q % 3 - 1;
+    const bool ex = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
+    T9[q][c] = ex ? tay[(size_t)(kk * g.Lv + ll) * TY_N + c] : 0.0;
+    if (c == 0) ex9[q] = ex;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// tier 1: 64 x 128 window, one warp per element, lazy per-site growth
+// ---------------------------------------------------------------------------
+
+constexpr int SR = 64, SW = 2, ST = 32;
+
+struct SmallShared {
   double T9[9][TY_N];
   int ex9[9];
-  unsigned long long comp[ROWS][WORDS];
-  unsigned long long eval[ROWS][WORDS];
-  int ok, any, ovf;
+  unsigned long long comp[SR][SW];
+  unsigned long long eval[SR][SW];
+  int ok;
 };
 
-// One element per block.  ROWS window rows along x, WORDS*64 columns along v;
-// T threads, each owning rows tid, tid+T, ...
-template <int ROWS, int WORDS, int T>
-__device__ void claim_element(const Grid& g, int m, const double* __restrict__ tay,
-                              unsigned long long* __restrict__ keys, DevState* ds,
-                              int32_t* __restrict__ ovf_list, bool last_resort,
-                              ClaimShared<ROWS, WORDS, T>& S) {
-  constexpr int COLS = 64 * WORDS;
-  constexpr int RPT = ROWS / T;
-  const int tid = threadIdx.x;
-  const int k = m / g.Lv, l = m - k * g.Lv;
-  for (int idx = tid; idx < 9 * TY_N; idx += T) {
-    int q = idx / TY_N, c = idx - q * TY_N;
-    int kk = k + q / 3 - 1, ll = l + q % 3 - 1;
-    bool ex = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
-    S.T9[q][c] = ex ? tay[(size_t)(kk * g.Lv + ll) * TY_N + c] : 0.0;
-    if (c == 0) S.ex9[q] = ex;
-  }
-  for (int r = tid; r < ROWS; r += T)
+__global__ void __launch_bounds__(ST) k_claim_small(Grid g, const double* __restrict__ tay,
+                                                    unsigned long long* __restrict__ keys, DevState* ds,
+                                                    int2* __restrict__ ovf_list) {
+  constexpr int COLS = 64 * SW, RPT = SR / ST;
+  __shared__ SmallShared S;
+  const int m = blockIdx.x, tid = threadIdx.x;
+  load_T9(g, m, tay, S.T9, S.ex9);
+  for (int r = tid; r < SR; r += ST)
 #pragma unroll
-    for (int w = 0; w < WORDS; w++) {
+    for (int w = 0; w < SW; w++) {
       S.comp[r][w] = 0ull;
       S.eval[r][w] = 0ull;
     }
-  if (tid == 0) {
-    S.ok = 0;
-    S.ovf = 0;
-  }
   __syncthreads();
-  // start: the grid site nearest to P_m
   const double us = dmul(dsub(S.T9[4][TY_X], g.x_lo), g.inv_dx);
   const double ws = dmul(dsub(S.T9[4][TY_V], g.v_lo), g.inv_dv);
   if (!(us > -1e9 && us < 1e9 && ws > -1e9 && ws < 1e9)) return;
   const long long i0 = (long long)floor(dadd(us, 0.5)), j0 = (long long)floor(dadd(ws, 0.5));
   const int pad = g.pad;
   if (i0 < -pad || i0 >= g.nx + pad || j0 < -pad || j0 >= g.nv + pad) return;
-  const long long r0 = i0 - ROWS / 2, c0 = j0 - COLS / 2;
-  // window columns / rows inside the padded lattice
+  const long long r0 = i0 - SR / 2, c0 = j0 - COLS / 2;
   const int clo = (int)max(0ll, (long long)(-pad) - c0);
   const int chi = (int)min((long long)COLS, (long long)(g.nv + pad) - c0);
   const int rlo = (int)max(0ll, (long long)(-pad) - r0);
-  const int rhi = (int)min((long long)ROWS, (long long)(g.nx + pad) - r0);
+  const int rhi = (int)min((long long)SR, (long long)(g.nx + pad) - r0);
   if (tid == 0) {
     double d2;
-    double Px = site_x(g, i0), Pv = site_v(g, j0);
-    bool ok = pass_test(g, S.T9, S.ex9, Px, Pv, d2);
-    const int rs = ROWS / 2, cs = COLS / 2;
-    S.eval[rs][cs >> 6] |= 1ull << (cs & 63);
+    const bool ok = pass_test(g, S.T9, S.ex9, site_x(g, i0), site_v(g, j0), d2);
+    S.eval[SR / 2][(COLS / 2) >> 6] |= 1ull << ((COLS / 2) & 63);
     if (ok) {
-      S.comp[rs][cs >> 6] |= 1ull << (cs & 63);
-      if (i0 >= 0 && i0 < g.nx && j0 >= 0 && j0 < g.nv)
-        claim_min(keys + 2 * ((size_t)i0 * g.nv + j0), dkey(d2), (unsigned long long)m);
+      S.comp[SR / 2][(COLS / 2) >> 6] |= 1ull << ((COLS / 2) & 63);
+      claim_site(g, keys, i0, j0, d2, m);
     }
     S.ok = ok;
   }
   __syncthreads();
   if (!S.ok) return;
-  unsigned long long front[RPT][WORDS];
-  for (int it = 0; it < ROWS * COLS; it++) {
+  unsigned long long front[RPT][SW];
+  for (int it = 0; it < SR * COLS; it++) {
     bool anyf = false;
 #pragma unroll
     for (int q = 0; q < RPT; q++) {
-      const int r = tid + q * T;
+      const int r = tid + q * ST;
 #pragma unroll
-      for (int w = 0; w < WORDS; w++) {
-        unsigned long long c = S.comp[r][w];
+      for (int w = 0; w < SW; w++) {
+        const unsigned long long c = S.comp[r][w];
         unsigned long long d = c | (c << 1) | (c >> 1);
         if (w > 0) d |= S.comp[r][w - 1] >> 63;
-        if (w < WORDS - 1) d |= S.comp[r][w + 1] << 63;
+        if (w < SW - 1) d |= S.comp[r][w + 1] << 63;
         if (r > 0) d |= S.comp[r - 1][w];
-        if (r < ROWS - 1) d |= S.comp[r + 1][w];
-        unsigned long long valid = (r >= rlo && r < rhi) ? col_mask(w, clo, chi) : 0ull;
+        if (r < SR - 1) d |= S.comp[r + 1][w];
+        const unsigned long long valid = (r >= rlo && r < rhi) ? col_mask(w, clo, chi) : 0ull;
         front[q][w] = d & ~S.eval[r][w] & valid;
         anyf |= front[q][w] != 0ull;
       }
@@ -187,23 +209,22 @@ __device__ void claim_element(const Grid& g, int m, const double* __restrict__ t
     if (!__syncthreads_or(anyf)) break;
 #pragma unroll
     for (int q = 0; q < RPT; q++) {
-      const int r = tid + q * T;
+      const int r = tid + q * ST;
       const long long i = r0 + r;
 #pragma unroll
-      for (int w = 0; w < WORDS; w++) {
+      for (int w = 0; w < SW; w++) {
         unsigned long long fr = front[q][w];
         if (!fr) continue;
         S.eval[r][w] |= fr;
         unsigned long long add = 0ull;
         while (fr) {
-          int b = __ffsll((long long)fr) - 1;
+          const int b = __ffsll((long long)fr) - 1;
           fr &= fr - 1ull;
           const long long j = c0 + 64 * w + b;
           double d2;
           if (pass_test(g, S.T9, S.ex9, site_x(g, i), site_v(g, j), d2)) {
             add |= 1ull << b;
-            if (i >= 0 && i < g.nx && j >= 0 && j < g.nv)
-              claim_min(keys + 2 * ((size_t)i * g.nv + j), dkey(d2), (unsigned long long)m);
+            claim_site(g, keys, i, j, d2, m);
           }
         }
         S.comp[r][w] |= add;
@@ -211,51 +232,233 @@ __device__ void claim_element(const Grid& g, int m, const double* __restrict__ t
     }
     __syncthreads();
   }
-  // Did the component reach a window edge beyond which the padded lattice
-  // continues?  Then the window was too small for this element.
-  bool ovf = false;
+  // Escaped the window?  Record on which sides, to pick the next window.
+  bool esc_rows = false, esc_cols = false;
 #pragma unroll
   for (int q = 0; q < RPT; q++) {
-    const int r = tid + q * T;
+    const int r = tid + q * ST;
     unsigned long long rowany = 0ull;
 #pragma unroll
-    for (int w = 0; w < WORDS; w++) rowany |= S.comp[r][w];
+    for (int w = 0; w < SW; w++) rowany |= S.comp[r][w];
     if (!rowany) continue;
-    if (r == 0 && rlo == 0 && r0 - 1 >= -pad) ovf = true;
-    if (r == ROWS - 1 && rhi == ROWS && r0 + ROWS < g.nx + pad) ovf = true;
-    if ((S.comp[r][0] & 1ull) && clo == 0 && c0 - 1 >= -pad) ovf = true;
-    if ((S.comp[r][WORDS - 1] >> 63) && chi == COLS && c0 + COLS < g.nv + pad) ovf = true;
+    if (r == 0 && rlo == 0 && r0 - 1 >= -pad) esc_rows = true;
+    if (r == SR - 1 && rhi == SR && r0 + SR < g.nx + pad) esc_rows = true;
+    if ((S.comp[r][0] & 1ull) && clo == 0 && c0 - 1 >= -pad) esc_cols = true;
+    if ((S.comp[r][SW - 1] >> 63) && chi == COLS && c0 + COLS < g.nv + pad) esc_cols = true;
   }
-  if (__syncthreads_or(ovf) && tid == 0) {
-    if (last_resort) {
-      atomicOr(&ds->err, ERR_PATCH_OVERFLOW);
+  const bool er = __syncthreads_or(esc_rows), ec = __syncthreads_or(esc_cols);
+  if ((er || ec) && tid == 0) {
+    const int mode = (er && ec) ? MODE_FAT : (ec ? MODE_BAND_V : MODE_BAND_X);
+    const int slot = atomicAdd(&ds->noverflow, 1);
+    ovf_list[slot] = make_int2(m, mode);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// tiers 2 and 3: cooperative block, word-granular evaluation
+// ---------------------------------------------------------------------------
+
+constexpr int BT = 256;       // threads
+constexpr int BAND_R = 64;    // band window: rows across the band
+constexpr int FAT_R = 256, FAT_W = 4;
+constexpr int LIST_CAP = 1024;
+
+struct BigHeader {
+  double T9[9][TY_N];
+  int ex9[9];
+  int ok, nlist, active, esc;
+  int list[LIST_CAP];
+};
+
+// Window geometry: "rows" run across, "words" along the bit axis.  For
+// MODE_BAND_X the bit axis is x (transposed window), otherwise v.
+struct Win {
+  bool trans;
+  int R, W;              // rows, 64-bit words per row
+  long long r0, c0;      // lattice coordinate of row 0 / bit 0
+  int rlo, rhi, clo, chi;
+  long long nrow_lat, ncol_lat;  // lattice extent along rows / bits (without pad)
+};
+
+__device__ __forceinline__ void site_of(const Win& W, int r, int c, long long& i, long long& j) {
+  if (W.trans) {
+    j = W.r0 + r;
+    i = W.c0 + c;
+  } else {
+    i = W.r0 + r;
+    j = W.c0 + c;
+  }
+}
+
+__global__ void __launch_bounds__(BT) k_claim_big(Grid g, const double* __restrict__ tay,
+                                                  unsigned long long* __restrict__ keys, DevState* ds,
+                                                  const int2* __restrict__ list_in, int tier,
+                                                  int2* __restrict__ list_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BigHeader& H = *reinterpret_cast<BigHeader*>(smem_raw);
+  unsigned long long* bits = reinterpret_cast<unsigned long long*>(smem_raw + sizeof(BigHeader));
+  const int tid = threadIdx.x;
+  const int pad = g.pad;
+  const int n = (tier == 2) ? ds->noverflow : ds->noverflow2;
+  for (int item = blockIdx.x; item < n; item += gridDim.x) {
+    const int m = list_in[item].x;
+    const int mode = (tier == 2) ? list_in[item].y : MODE_FAT;
+    load_T9(g, m, tay, H.T9, H.ex9);
+    __syncthreads();
+    const double us = dmul(dsub(H.T9[4][TY_X], g.x_lo), g.inv_dx);
+    const double ws = dmul(dsub(H.T9[4][TY_V], g.v_lo), g.inv_dv);
+    const long long i0 = (long long)floor(dadd(us, 0.5)), j0 = (long long)floor(dadd(ws, 0.5));
+    Win W;
+    W.trans = (mode == MODE_BAND_X);
+    const long long along0 = W.trans ? i0 : j0, across0 = W.trans ? j0 : i0;
+    W.nrow_lat = W.trans ? g.nv : g.nx;
+    W.ncol_lat = W.trans ? g.nx : g.nv;
+    if (mode == MODE_FAT) {
+      W.R = FAT_R;
+      W.W = FAT_W;
+      W.r0 = across0 - FAT_R / 2;
+      W.c0 = along0 - 32 * FAT_W;
     } else {
-      int slot = atomicAdd(&ds->noverflow, 1);
-      ovf_list[slot] = m;
+      W.R = BAND_R;
+      W.W = (int)((W.ncol_lat + 2 * pad + 63) / 64);
+      W.r0 = across0 - BAND_R / 2;
+      W.c0 = -pad;
     }
-  }
-}
-
-constexpr int SR = 64, SW = 2, ST = 32;    // small window: 64 x 128 sites, one warp
-constexpr int BR = 256, BW = 4, BT = 256;  // large window: 256 x 256 sites
-
-__global__ void __launch_bounds__(ST) k_claim_small(Grid g, const double* __restrict__ tay,
-                                                    unsigned long long* __restrict__ keys, DevState* ds,
-                                                    int32_t* __restrict__ ovf_list) {
-  __shared__ ClaimShared<SR, SW, ST> S;
-  claim_element<SR, SW, ST>(g, blockIdx.x, tay, keys, ds, ovf_list, false, S);
-}
-
-__global__ void __launch_bounds__(BT) k_claim_large(Grid g, const double* __restrict__ tay,
-                                                    unsigned long long* __restrict__ keys, DevState* ds,
-                                                    int32_t* __restrict__ ovf_list) {
-  __shared__ ClaimShared<BR, BW, BT> S;
-  const int n = ds->noverflow;
-  for (int idx = blockIdx.x; idx < n; idx += gridDim.x) {
-    claim_element<BR, BW, BT>(g, ovf_list[idx], tay, keys, ds, ovf_list, true, S);
+    const int COLS = 64 * W.W;
+    W.clo = (int)max(0ll, (long long)(-pad) - W.c0);
+    W.chi = (int)min((long long)COLS, W.ncol_lat + pad - W.c0);
+    W.rlo = (int)max(0ll, (long long)(-pad) - W.r0);
+    W.rhi = (int)min((long long)W.R, W.nrow_lat + pad - W.r0);
+    const int NW = W.R * W.W;
+    unsigned long long* comp = bits;
+    unsigned long long* eval = bits + NW;
+    unsigned long long* pass = bits + 2 * NW;
+    for (int q = tid; q < 3 * NW; q += BT) bits[q] = 0ull;
+    if (tid == 0) {
+      H.ok = 0;
+      H.esc = 0;
+    }
+    __syncthreads();
+    const int rs = (int)(across0 - W.r0), cs = (int)(along0 - W.c0);
+    if (tid == 0) {
+      double d2;
+      const bool ok = pass_test(g, H.T9, H.ex9, site_x(g, i0), site_v(g, j0), d2);
+      const int q = rs * W.W + (cs >> 6);
+      eval[q] |= 1ull << (cs & 63);
+      if (ok) {
+        pass[q] |= 1ull << (cs & 63);
+        comp[q] |= 1ull << (cs & 63);
+        claim_site(g, keys, i0, j0, d2, m);
+      }
+      H.ok = ok;
+    }
+    __syncthreads();
+    if (H.ok) {
+      for (int it = 0; it < NW * 64; it++) {
+        if (tid == 0) {
+          H.nlist = 0;
+          H.active = 0;
+        }
+        __syncthreads();
+        // A: growth candidates of every word; words needing evaluation are listed
+        bool act = false;
+        for (int q = tid; q < NW; q += BT) {
+          const int r = q / W.W, w = q - r * W.W;
+          const unsigned long long c = comp[q];
+          unsigned long long d = c | (c << 1) | (c >> 1);
+          if (w > 0) d |= comp[q - 1] >> 63;
+          if (w < W.W - 1) d |= comp[q + 1] << 63;
+          if (r > 0) d |= comp[q - W.W];
+          if (r < W.R - 1) d |= comp[q + W.W];
+          const unsigned long long valid = (r >= W.rlo && r < W.rhi) ? col_mask(w, W.clo, W.chi) : 0ull;
+          const unsigned long long gr = d & ~c & valid;
+          if (gr & ~eval[q]) {
+            act = true;
+            const int slot = atomicAdd(&H.nlist, 1);
+            if (slot < LIST_CAP) H.list[slot] = q;
+          } else if (gr & pass[q]) {
+            act = true;
+          }
+        }
+        if (!__syncthreads_or(act)) break;
+        // C: evaluate every still-unevaluated valid site of the listed words
+        const int nl = min(H.nlist, LIST_CAP);
+        for (int e = tid; e < nl * 64; e += BT) {
+          const int q = H.list[e >> 6], b = e & 63;
+          const int r = q / W.W, w = q - r * W.W;
+          const unsigned long long valid = (r >= W.rlo && r < W.rhi) ? col_mask(w, W.clo, W.chi) : 0ull;
+          if (!(((valid & ~eval[q]) >> b) & 1ull)) continue;
+          long long i, j;
+          site_of(W, r, 64 * w + b, i, j);
+          double d2;
+          if (pass_test(g, H.T9, H.ex9, site_x(g, i), site_v(g, j), d2))
+            atomicOr(&pass[q], 1ull << b);
+        }
+        __syncthreads();
+        for (int e = tid; e < nl; e += BT) {
+          const int q = H.list[e];
+          const int r = q / W.W, w = q - r * W.W;
+          eval[q] |= (r >= W.rlo && r < W.rhi) ? col_mask(w, W.clo, W.chi) : 0ull;
+        }
+        __syncthreads();
+        // D: extend the component through passing runs inside each word.  A
+        // word may see its neighbours' growth of this same phase; that only
+        // adds connected passing sites earlier, so the fixed point is the same.
+        for (int q = tid; q < NW; q += BT) {
+          const int r = q / W.W, w = q - r * W.W;
+          const unsigned long long c = comp[q];
+          unsigned long long d = c | (c << 1) | (c >> 1);
+          if (w > 0) d |= comp[q - 1] >> 63;
+          if (w < W.W - 1) d |= comp[q + 1] << 63;
+          if (r > 0) d |= comp[q - W.W];
+          if (r < W.R - 1) d |= comp[q + W.W];
+          const unsigned long long seeds = d & ~c & pass[q];
+          if (!seeds) continue;
+          const unsigned long long nw = run_fill(seeds | c, pass[q]);
+          unsigned long long add = nw & ~c;
+          comp[q] = c | nw;
+          while (add) {
+            const int b = __ffsll((long long)add) - 1;
+            add &= add - 1ull;
+            long long i, j;
+            site_of(W, r, 64 * w + b, i, j);
+            if (i >= 0 && i < g.nx && j >= 0 && j < g.nv) {
+              double xi, ze;
+              const double d2 = dist2_exact(H.T9[4], g, site_x(g, i), site_v(g, j), xi, ze);
+              claim_site(g, keys, i, j, d2, m);
+            }
+          }
+        }
+        __syncthreads();
+      }
+      // escaped this window as well?
+      bool esc = false;
+      for (int q = tid; q < NW; q += BT) {
+        const unsigned long long c = comp[q];
+        if (!c) continue;
+        const int r = q / W.W, w = q - r * W.W;
+        if (r == 0 && W.rlo == 0 && W.r0 - 1 >= -pad) esc = true;
+        if (r == W.R - 1 && W.rhi == W.R && W.r0 + W.R < W.nrow_lat + pad) esc = true;
+        if (w == 0 && (c & 1ull) && W.clo == 0 && W.c0 - 1 >= -pad) esc = true;
+        if (w == W.W - 1 && (c >> 63) && W.chi == COLS && W.c0 + COLS < W.ncol_lat + pad) esc = true;
+      }
+      if (__syncthreads_or(esc) && tid == 0) {
+        if (tier == 2 && mode != MODE_FAT) {
+          const int slot = atomicAdd(&ds->noverflow2, 1);
+          list_out[slot] = make_int2(m, MODE_FAT);
+        } else {
+          atomicOr(&ds->err, ERR_PATCH_OVERFLOW);
+        }
+      }
+    }
     __syncthreads();
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) ds->overflow_stat = n;
+  if (blockIdx.x == 0 && tid == 0) {
+    if (tier == 2)
+      ds->overflow_stat = n;
+    else
+      ds->overflow2_stat = n;
+  }
 }
 
 // Keys -> map; reset keys for the next map; list the unclaimed sites.
@@ -264,10 +467,10 @@ __global__ void k_finalize(Grid g, unsigned long long* __restrict__ keys, int32_
   const size_t n = (size_t)g.nx * g.nv;
   const ulonglong2 empty = make_ulonglong2(KEY_EMPTY, KEY_EMPTY);
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
-    ulonglong2 kv = reinterpret_cast<ulonglong2*>(keys)[p];
+    const ulonglong2 kv = reinterpret_cast<ulonglong2*>(keys)[p];
     int32_t m = -1;
     if (kv.y == KEY_EMPTY && kv.x == KEY_EMPTY) {
-      int slot = atomicAdd(&ds->nholes, 1);
+      const int slot = atomicAdd(&ds->nholes, 1);
       holes[slot] = (int32_t)p;
     } else {
       m = (int32_t)kv.x;
@@ -312,7 +515,7 @@ __global__ void __launch_bounds__(HT) k_holes(Grid g, const double* __restrict__
         const int cand = map[(size_t)ii * g.nv + jj];
         if (cand < 0) continue;
         double xi, ze;
-        unsigned long long key = dkey(dist2_exact(tay + (size_t)cand * TY_N, g, Px, Pv, xi, ze));
+        const unsigned long long key = dkey(dist2_exact(tay + (size_t)cand * TY_N, g, Px, Pv, xi, ze));
         if (best < 0 || key < bestk || (key == bestk && cand < best)) {
           best = cand;
           bestk = key;
@@ -327,7 +530,7 @@ __global__ void __launch_bounds__(HT) k_holes(Grid g, const double* __restrict__
       if (c >= 0) {
         map[la[idx]] = c;
       } else {
-        int slot = atomicAdd(&next_s, 1);
+        const int slot = atomicAdd(&next_s, 1);
         lb[slot] = la[idx];
       }
     }
@@ -345,19 +548,47 @@ __global__ void __launch_bounds__(HT) k_holes(Grid g, const double* __restrict__
   }
 }
 
+size_t big_smem_bytes(const Grid& g) {
+  const long long wv = (g.nv + 2 * g.pad + 63) / 64, wx = (g.nx + 2 * g.pad + 63) / 64;
+  long long nw = FAT_R * FAT_W;
+  nw = max(nw, (long long)BAND_R * wv);
+  nw = max(nw, (long long)BAND_R * wx);
+  return sizeof(BigHeader) + 3 * (size_t)nw * sizeof(unsigned long long);
+}
+
 }  // namespace
 
+// The band window spans the padded lattice along one axis; it must fit in
+// one block's shared memory (grid sides up to about 9400 sites).
+bool map_prepare(const Grid& g) {
+  const size_t need = big_smem_bytes(g);
+  if (need > 227 * 1024) return false;
+  return cudaFuncSetAttribute(k_claim_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need) == cudaSuccess;
+}
+
 void launch_map(vm_solver* s) {
-  // counters: nholes, holes_found, hole_rounds, noverflow
-  cudaMemsetAsync(&s->ds->nholes, 0, 4 * sizeof(int32_t), s->stream);
+  // counters: nholes, holes_found, hole_rounds, noverflow, overflow_stat, noverflow2, overflow2_stat
+  int ps = prof_begin(s, KID_MAP_CLEAR);
+  cudaMemsetAsync(&s->ds->nholes, 0, 7 * sizeof(int32_t), s->stream);
+  prof_end(s, ps);
+  ps = prof_begin(s, KID_CLAIM_SMALL);
   k_claim_small<<<s->g.ne, ST, 0, s->stream>>>(s->g, s->tay, s->keys, s->ds, s->overflow_list);
-  k_claim_large<<<152, BT, 0, s->stream>>>(s->g, s->tay, s->keys, s->ds, s->overflow_list);
+  prof_end(s, ps);
+  const size_t smem = big_smem_bytes(s->g);
+  ps = prof_begin(s, KID_CLAIM_LARGE);
+  k_claim_big<<<2 * 152, BT, smem, s->stream>>>(s->g, s->tay, s->keys, s->ds, s->overflow_list, 2,
+                                                s->overflow_list2);
+  k_claim_big<<<152, BT, smem, s->stream>>>(s->g, s->tay, s->keys, s->ds, s->overflow_list2, 3, nullptr);
+  prof_end(s, ps);
   unsigned nb = (unsigned)((s->n + 255) / 256);
   if (nb > 152 * 16) nb = 152 * 16;
+  ps = prof_begin(s, KID_FINALIZE);
   k_finalize<<<nb, 256, 0, s->stream>>>(s->g, s->keys, s->map, s->holes_a, s->ds);
-  k_holes<<<1, HT, 0, s->stream>>>(s->g, s->tay, s->map, s->holes_a, s->holes_b,
-                                    s->holes_b + s->n, s->ds);
-  s->launches += 4;
+  prof_end(s, ps);
+  ps = prof_begin(s, KID_HOLES);
+  k_holes<<<1, HT, 0, s->stream>>>(s->g, s->tay, s->map, s->holes_a, s->holes_b, s->holes_b + s->n, s->ds);
+  prof_end(s, ps);
+  s->launches += 5;
 }
 
 }  // namespace vm

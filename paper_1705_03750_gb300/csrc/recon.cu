@@ -223,21 +223,25 @@ inline unsigned grid_for(size_t n) {
 
 void launch_reconstruct(vm_solver* s) {
   const int nt = s->g.nv >= 256 ? 256 : ((s->g.nv + 31) / 32) * 32;
+  const int ps_ = prof_begin(s, KID_RECON);
   if (s->fp32)
     k_recon<float><<<s->g.nx, nt, 0, s->stream>>>(s->g, s->map, s->tay, (const float*)s->fini,
                                                    (float*)s->f, s->M);
   else
     k_recon<double><<<s->g.nx, nt, 0, s->stream>>>(s->g, s->map, s->tay, (const double*)s->fini,
                                                     (double*)s->f, s->M);
+  prof_end(s, ps_);
   s->launches++;
 }
 
 void launch_remap_resample(vm_solver* s, void* out) {
   const int nt = s->g.nv >= 256 ? 256 : ((s->g.nv + 31) / 32) * 32;
+  const int ps_ = prof_begin(s, KID_REMAP);
   if (s->fp32)
     k_remap<float><<<s->g.nx, nt, 0, s->stream>>>(s->g, s->map, s->tay, (const float*)s->eta, (float*)out);
   else
     k_remap<double><<<s->g.nx, nt, 0, s->stream>>>(s->g, s->map, s->tay, (const double*)s->eta, (double*)out);
+  prof_end(s, ps_);
   s->launches++;
 }
 

@@ -107,13 +107,18 @@ __global__ void __launch_bounds__(128) k_cols(Grid g, R* __restrict__ x, const C
 void launch_spline_solve(vm_solver* s, const void* src, void* dst) {
   const unsigned rb = (unsigned)((s->g.nx + 32 * RW - 1) / (32 * RW));
   const unsigned cb = (unsigned)((s->g.nv + 127) / 128);
-  if (s->fp32) {
+  int ps = prof_begin(s, KID_SPLINE_ROWS);
+  if (s->fp32)
     k_rows<float, float><<<rb, 32 * RW, 0, s->stream>>>(s->g, (const float*)src, (float*)dst, s->thomas_vf);
-    k_cols<float, float><<<cb, 128, 0, s->stream>>>(s->g, (float*)dst, s->thomas_xf);
-  } else {
+  else
     k_rows<double, double><<<rb, 32 * RW, 0, s->stream>>>(s->g, (const double*)src, (double*)dst, s->thomas_v);
+  prof_end(s, ps);
+  ps = prof_begin(s, KID_SPLINE_COLS);
+  if (s->fp32)
+    k_cols<float, float><<<cb, 128, 0, s->stream>>>(s->g, (float*)dst, s->thomas_xf);
+  else
     k_cols<double, double><<<cb, 128, 0, s->stream>>>(s->g, (double*)dst, s->thomas_x);
-  }
+  prof_end(s, ps);
   s->launches += 2;
 }
 

@@ -28,7 +28,8 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "workspace too small", 3: "CUDA run
 EXPORTS = ["vm_config_default", "vm_workspace_bytes", "vm_create", "vm_destroy", "vm_status_string",
            "vm_lattice", "vm_set_f", "vm_set_elements", "vm_get_elements", "vm_compute_map",
            "vm_reconstruct", "vm_step", "vm_remap", "vm_density_force", "vm_read_f", "vm_read_fini",
-           "vm_read_eta", "vm_read_map", "vm_diagnostics", "vm_sync", "vm_launch_count"]
+           "vm_read_eta", "vm_read_map", "vm_diagnostics", "vm_sync", "vm_launch_count",
+           "vm_profile", "vm_profile_read"]
 
 
 class VmConfig(C.Structure):
@@ -46,6 +47,10 @@ class VmDiag(C.Structure):
     _fields_ = [("mass", C.c_double), ("energy", C.c_double), ("detT_min", C.c_double),
                 ("detT_max", C.c_double), ("step", C.c_int64), ("cycle", C.c_int32),
                 ("holes", C.c_int32), ("hole_rounds", C.c_int32), ("overflow_elements", C.c_int32)]
+
+
+class VmKernelStat(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double)]
 
 
 class VlametError(RuntimeError):
@@ -88,6 +93,8 @@ def load() -> C.CDLL:
         "vm_diagnostics": (i32, [vp, C.POINTER(VmDiag)]),
         "vm_sync": (i32, [vp]),
         "vm_launch_count": (i64, [vp]),
+        "vm_profile": (i32, [vp, i32]),
+        "vm_profile_read": (i32, [vp, C.POINTER(VmKernelStat), i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -256,6 +263,18 @@ class Solver:
         d = VmDiag()
         _check(self.L.vm_diagnostics(self.h, C.byref(d)), "vm_diagnostics")
         return {k: getattr(d, k) for k, _ in VmDiag._fields_}
+
+    def profile(self, enable: bool = True) -> None:
+        """Start (or stop) per-kernel event timing; resets the totals."""
+        _check(self.L.vm_profile(self.h, int(enable)), "vm_profile")
+
+    def profile_read(self) -> dict:
+        """{kernel name: (launches, total device ms)} since profile()."""
+        buf = (VmKernelStat * 32)()
+        n = self.L.vm_profile_read(self.h, buf, 32)
+        if n < 0:
+            raise VlametError(1, "vm_profile_read")
+        return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(min(n, 32))}
 
     @property
     def launches(self) -> int:

@@ -51,6 +51,15 @@ def evolved_state(rc, steps):
     return o.elements(), o.fini()
 
 
+ELEMENT_TOL = {"fp64": (1e-13, 1e-12, 1e-10), "fp32": (1e-8, 1e-6, 1e-4)}
+
+
+def element_errors(eg, eo):
+    """Per state column, max |difference| over elements / max |value|."""
+    scale = np.maximum(np.abs(eo).max(axis=0), 1e-300)
+    return np.abs(eg - eo).max(axis=0) / scale
+
+
 def assert_f_close(fg, fo, tol=F_TOL):
     scale = max(np.abs(fo).max(), 1e-300)
     err = np.abs(fg - fo).max() / scale
@@ -177,8 +186,12 @@ def test_first_step_matches(prec):
     o.step(1)
     assert_f_close(s.read_f(), o.last_f())
     eg, eo = s.elements().T, o.elements()
-    rtol = 1e-12 if prec == "fp64" else 1e-9
-    np.testing.assert_allclose(eg, eo, rtol=rtol, atol=rtol * np.abs(eo).max(axis=0))
+    err = element_errors(eg, eo)
+    # columns: x, v | T (4) | H (6); the force enters v at O(dt a), T through
+    # a' and H through a'' (a second difference of the mass scan)
+    lim = ELEMENT_TOL[prec]
+    for c, e in enumerate(err):
+        assert e <= lim[0 if c < 2 else (1 if c < 6 else 2)], (c, err)
 
 
 @pytest.mark.parametrize("rc", [I.SPITZER_128, I.FREE_128], ids=["spitzer", "free"])
