@@ -36,8 +36,10 @@ struct DevState {
   int32_t hole_rounds;   // repair rounds of the last map (statistics)
   int32_t noverflow;     // elements queued for the band / large windows
   int32_t overflow_stat;
-  int32_t noverflow2;    // elements queued for the last-resort window
+  int32_t noverflow2;    // elements queued for the second large-window attempt
   int32_t overflow2_stat;
+  int32_t noverflow3;    // elements queued for the third attempt
+  int32_t overflow3_stat;
   double Mtot;           // total mass of the last reconstruction
   double sum_mass, sum_kin, sum_pot;
   unsigned long long det_min_key, det_max_key;

@@ -10,15 +10,15 @@
 //   1. a 64 x 128 window, one warp per element, one percolation test per
 //      newly reached site (lazy breadth-first growth: the test runs once per
 //      site of the component and of its rim);
-//   2. for the elements whose component reached the edge of tier 1: a band
-//      window, 64 sites across and the whole padded lattice along the
-//      direction in which the component escaped, or a 256 x 256 window if
-//      it escaped both ways.  Elements of the outer layer whose neighbours
-//      have moved away claim long thin bands; to cross them in few rounds,
-//      any 64-site word the component reaches is evaluated whole, and the
-//      component is then extended through runs of passing sites inside the
-//      word with one carry-propagating addition;
-//   3. a 256 x 256 window for band elements that outgrew the band.
+//   2. for the elements whose component reached the edge of tier 1, up to
+//      three attempts with larger windows, in an order set by the sides it
+//      escaped from: a band window 128 sites across and as long as shared
+//      memory allows along v (the whole padded lattice at 4096^2), the same
+//      along x, and a 256 x 256 window.  Elements of the outer layer whose
+//      neighbours have moved away claim long thin bands; to cross them in
+//      few rounds, any 64-site word the component reaches is evaluated
+//      whole, and the component is then extended through runs of passing
+//      sites inside the word with one carry-propagating addition.
 //
 // Claims are resolved by one 128-bit atomic compare-and-swap minimum per
 // claimed site on the key (bits of d^2, element index): smallest distance
@@ -248,9 +248,9 @@ __global__ void __launch_bounds__(ST) k_claim_small(Grid g, const double* __rest
   }
   const bool er = __syncthreads_or(esc_rows), ec = __syncthreads_or(esc_cols);
   if ((er || ec) && tid == 0) {
-    const int mode = (er && ec) ? MODE_FAT : (ec ? MODE_BAND_V : MODE_BAND_X);
+    const int sides = (er ? 1 : 0) | (ec ? 2 : 0);
     const int slot = atomicAdd(&ds->noverflow, 1);
-    ovf_list[slot] = make_int2(m, mode);
+    ovf_list[slot] = make_int2(m, sides << 4);   // attempt 0
   }
 }
 
@@ -259,9 +259,20 @@ __global__ void __launch_bounds__(ST) k_claim_small(Grid g, const double* __rest
 // ---------------------------------------------------------------------------
 
 constexpr int BT = 256;       // threads
-constexpr int BAND_R = 64;    // band window: rows across the band
+constexpr int BAND_R = 128;   // band window: rows across the band
 constexpr int FAT_R = 256, FAT_W = 4;
 constexpr int LIST_CAP = 1024;
+constexpr size_t SMEM_MAX = 227 * 1024;
+
+// Order of the window modes tried for an element, by the sides its
+// component escaped tier 1 from (1: rows, 2: columns, 3: both).
+__device__ __forceinline__ int mode_for(int sides, int attempt) {
+  const int seq[4][3] = {{MODE_FAT, MODE_BAND_V, MODE_BAND_X},
+                         {MODE_BAND_X, MODE_FAT, MODE_BAND_V},
+                         {MODE_BAND_V, MODE_FAT, MODE_BAND_X},
+                         {MODE_BAND_V, MODE_BAND_X, MODE_FAT}};
+  return seq[sides & 3][attempt];
+}
 
 struct BigHeader {
   double T9[9][TY_N];
@@ -290,19 +301,29 @@ __device__ __forceinline__ void site_of(const Win& W, int r, int c, long long& i
   }
 }
 
+// 64-bit words along a band window for a lattice side n: the whole padded
+// side if it fits in shared memory, else as many as fit.
+__host__ __device__ __forceinline__ int band_words(long long n, int pad) {
+  const long long full = (n + 2 * pad + 63) / 64;
+  const long long fit = (long long)((SMEM_MAX - sizeof(BigHeader)) / (3 * 8 * BAND_R));
+  return (int)(full < fit ? full : fit);
+}
+
 __global__ void __launch_bounds__(BT) k_claim_big(Grid g, const double* __restrict__ tay,
                                                   unsigned long long* __restrict__ keys, DevState* ds,
-                                                  const int2* __restrict__ list_in, int tier,
-                                                  int2* __restrict__ list_out) {
+                                                  const int2* __restrict__ list_in, const int* __restrict__ n_in,
+                                                  int* __restrict__ stat, int2* __restrict__ list_out,
+                                                  int* __restrict__ n_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BigHeader& H = *reinterpret_cast<BigHeader*>(smem_raw);
   unsigned long long* bits = reinterpret_cast<unsigned long long*>(smem_raw + sizeof(BigHeader));
   const int tid = threadIdx.x;
   const int pad = g.pad;
-  const int n = (tier == 2) ? ds->noverflow : ds->noverflow2;
+  const int n = *n_in;
   for (int item = blockIdx.x; item < n; item += gridDim.x) {
     const int m = list_in[item].x;
-    const int mode = (tier == 2) ? list_in[item].y : MODE_FAT;
+    const int sides = list_in[item].y >> 4, attempt = list_in[item].y & 15;
+    const int mode = mode_for(sides, attempt);
     load_T9(g, m, tay, H.T9, H.ex9);
     __syncthreads();
     const double us = dmul(dsub(H.T9[4][TY_X], g.x_lo), g.inv_dx);
@@ -320,9 +341,14 @@ __global__ void __launch_bounds__(BT) k_claim_big(Grid g, const double* __restri
       W.c0 = along0 - 32 * FAT_W;
     } else {
       W.R = BAND_R;
-      W.W = (int)((W.ncol_lat + 2 * pad + 63) / 64);
+      W.W = band_words(W.ncol_lat, pad);
       W.r0 = across0 - BAND_R / 2;
-      W.c0 = -pad;
+      // centred on the start, kept inside the padded lattice
+      long long c0 = along0 - 32ll * W.W;
+      const long long hi = W.ncol_lat + pad - 64ll * W.W;
+      if (c0 > hi) c0 = hi;
+      if (c0 < -pad) c0 = -pad;
+      W.c0 = c0;
     }
     const int COLS = 64 * W.W;
     W.clo = (int)max(0ll, (long long)(-pad) - W.c0);
@@ -443,9 +469,9 @@ __global__ void __launch_bounds__(BT) k_claim_big(Grid g, const double* __restri
         if (w == W.W - 1 && (c >> 63) && W.chi == COLS && W.c0 + COLS < W.ncol_lat + pad) esc = true;
       }
       if (__syncthreads_or(esc) && tid == 0) {
-        if (tier == 2 && mode != MODE_FAT) {
-          const int slot = atomicAdd(&ds->noverflow2, 1);
-          list_out[slot] = make_int2(m, MODE_FAT);
+        if (list_out != nullptr) {
+          const int slot = atomicAdd(n_out, 1);
+          list_out[slot] = make_int2(m, (sides << 4) | (attempt + 1));
         } else {
           atomicOr(&ds->err, ERR_PATCH_OVERFLOW);
         }
@@ -453,12 +479,7 @@ __global__ void __launch_bounds__(BT) k_claim_big(Grid g, const double* __restri
     }
     __syncthreads();
   }
-  if (blockIdx.x == 0 && tid == 0) {
-    if (tier == 2)
-      ds->overflow_stat = n;
-    else
-      ds->overflow2_stat = n;
-  }
+  if (blockIdx.x == 0 && tid == 0) *stat = n;
 }
 
 // Keys -> map; reset keys for the next map; list the unclaimed sites.
@@ -549,36 +570,39 @@ __global__ void __launch_bounds__(HT) k_holes(Grid g, const double* __restrict__
 }
 
 size_t big_smem_bytes(const Grid& g) {
-  const long long wv = (g.nv + 2 * g.pad + 63) / 64, wx = (g.nx + 2 * g.pad + 63) / 64;
   long long nw = FAT_R * FAT_W;
-  nw = max(nw, (long long)BAND_R * wv);
-  nw = max(nw, (long long)BAND_R * wx);
+  nw = max(nw, (long long)BAND_R * band_words(g.nv, g.pad));
+  nw = max(nw, (long long)BAND_R * band_words(g.nx, g.pad));
   return sizeof(BigHeader) + 3 * (size_t)nw * sizeof(unsigned long long);
 }
 
 }  // namespace
 
-// The band window spans the padded lattice along one axis; it must fit in
-// one block's shared memory (grid sides up to about 9400 sites).
+// Opt the large-window kernel in to the shared memory its windows need.
 bool map_prepare(const Grid& g) {
   const size_t need = big_smem_bytes(g);
-  if (need > 227 * 1024) return false;
+  if (need > SMEM_MAX) return false;
   return cudaFuncSetAttribute(k_claim_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need) == cudaSuccess;
 }
 
 void launch_map(vm_solver* s) {
-  // counters: nholes, holes_found, hole_rounds, noverflow, overflow_stat, noverflow2, overflow2_stat
+  // counters: nholes, holes_found, hole_rounds, noverflow, overflow_stat, noverflow2,
+  // overflow2_stat, noverflow3, overflow3_stat
   int ps = prof_begin(s, KID_MAP_CLEAR);
-  cudaMemsetAsync(&s->ds->nholes, 0, 7 * sizeof(int32_t), s->stream);
+  cudaMemsetAsync(&s->ds->nholes, 0, 9 * sizeof(int32_t), s->stream);
   prof_end(s, ps);
   ps = prof_begin(s, KID_CLAIM_SMALL);
   k_claim_small<<<s->g.ne, ST, 0, s->stream>>>(s->g, s->tay, s->keys, s->ds, s->overflow_list);
   prof_end(s, ps);
   const size_t smem = big_smem_bytes(s->g);
   ps = prof_begin(s, KID_CLAIM_LARGE);
-  k_claim_big<<<2 * 152, BT, smem, s->stream>>>(s->g, s->tay, s->keys, s->ds, s->overflow_list, 2,
-                                                s->overflow_list2);
-  k_claim_big<<<152, BT, smem, s->stream>>>(s->g, s->tay, s->keys, s->ds, s->overflow_list2, 3, nullptr);
+  DevState* d = s->ds;
+  k_claim_big<<<2 * 152, BT, smem, s->stream>>>(s->g, s->tay, s->keys, d, s->overflow_list, &d->noverflow,
+                                                &d->overflow_stat, s->overflow_list2, &d->noverflow2);
+  k_claim_big<<<152, BT, smem, s->stream>>>(s->g, s->tay, s->keys, d, s->overflow_list2, &d->noverflow2,
+                                            &d->overflow2_stat, s->overflow_list, &d->noverflow3);
+  k_claim_big<<<152, BT, smem, s->stream>>>(s->g, s->tay, s->keys, d, s->overflow_list, &d->noverflow3,
+                                            &d->overflow3_stat, nullptr, nullptr);
   prof_end(s, ps);
   unsigned nb = (unsigned)((s->n + 255) / 256);
   if (nb > 152 * 16) nb = 152 * 16;
@@ -588,7 +612,7 @@ void launch_map(vm_solver* s) {
   ps = prof_begin(s, KID_HOLES);
   k_holes<<<1, HT, 0, s->stream>>>(s->g, s->tay, s->map, s->holes_a, s->holes_b, s->holes_b + s->n, s->ds);
   prof_end(s, ps);
-  s->launches += 5;
+  s->launches += 6;
 }
 
 }  // namespace vm
