@@ -178,6 +178,32 @@ typedef struct {
 vm_status vm_profile(vm_solver* s, int32_t enable);
 int32_t vm_profile_read(vm_solver* s, vm_kernel_stat* out, int32_t max);
 
+/* Pixel masses and force from a caller's f, allocating nothing.
+ *
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory (a plugin whose host application owns the
+ * device heap and forbids cudaMalloc, or a loop that must never pay the
+ * device-wide synchronisation cudaMalloc and cudaFree can cause).  It
+ * computes what vm_reconstruct + vm_density_force produce for an f given on
+ * the device: M(i) = sum_j f(i,j) dx dv, then a, a', a'' on the x nodes by
+ * the compensated mass scan (same grid conventions as vm_config).
+ *
+ * f: device pointer, [nx][nv], v fastest, dtype a vm_dtype.  M_out (may be
+ * NULL), a, da, d2a: device pointers to [nx] doubles.  cuda_stream: the
+ * stream the work is queued on (asynchronous; nothing is synchronised).
+ * The only scratch is a file-scope device array holding up to
+ * VM_STATIC_FORCE_MAX_NX pixel masses, which every GPU that loads the library
+ * keeps until the process exits; nx above that limit returns
+ * VM_E_INVALID_ARG.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the one array and it keeps the last call's
+ * contents (every entry used is rewritten by each call); calls whose work
+ * overlaps on the GPU race on it, so serialise them (one stream, or events). */
+#define VM_STATIC_FORCE_MAX_NX 16384
+vm_status vm_force_from_f_static(const void* f, int32_t dtype, int32_t nx, int32_t nv, double x_lo, double x_hi,
+                                 double v_lo, double v_hi, double G, int32_t literal_fd, double* M_out, double* a,
+                                 double* da, double* d2a, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

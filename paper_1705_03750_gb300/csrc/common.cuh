@@ -122,6 +122,8 @@ void launch_taylor(vm_solver* s);
 void launch_kick_drift(vm_solver* s);
 void launch_reset_elements(vm_solver* s);
 void launch_scan_force(vm_solver* s);
+void launch_scan_force_raw(const Grid& g, const double* M, double* a, double* da, double* d2a, DevState* ds,
+                           cudaStream_t stream);
 void launch_diagnostics(vm_solver* s);
 // map.cu
 bool map_prepare(const Grid& g);

@@ -311,6 +311,13 @@ void launch_scan_force(vm_solver* s) {
   s->launches++;
 }
 
+// The same mass scan on caller-provided buffers (no solver), for the
+// allocation-free entry point.
+void launch_scan_force_raw(const Grid& g, const double* M, double* a, double* da, double* d2a, DevState* ds,
+                           cudaStream_t stream) {
+  k_scan_force<<<1, SCAN_T, 0, stream>>>(g, M, a, da, d2a, ds);
+}
+
 void launch_diagnostics(vm_solver* s) {
   unsigned nb = blocks_for((long long)s->n, 256);
   if (nb > 2048) nb = 2048;

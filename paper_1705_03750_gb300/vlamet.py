@@ -29,7 +29,9 @@ EXPORTS = ["vm_config_default", "vm_workspace_bytes", "vm_create", "vm_destroy",
            "vm_lattice", "vm_set_f", "vm_set_elements", "vm_get_elements", "vm_compute_map",
            "vm_reconstruct", "vm_step", "vm_remap", "vm_density_force", "vm_read_f", "vm_read_fini",
            "vm_read_eta", "vm_read_map", "vm_diagnostics", "vm_sync", "vm_launch_count",
-           "vm_profile", "vm_profile_read"]
+           "vm_profile", "vm_profile_read", "vm_force_from_f_static"]
+
+VM_STATIC_FORCE_MAX_NX = 16384
 
 
 class VmConfig(C.Structure):
@@ -95,6 +97,8 @@ def load() -> C.CDLL:
         "vm_launch_count": (i64, [vp]),
         "vm_profile": (i32, [vp, i32]),
         "vm_profile_read": (i32, [vp, C.POINTER(VmKernelStat), i32]),
+        "vm_force_from_f_static": (i32, [vp, i32, i32, i32, C.c_double, C.c_double, C.c_double, C.c_double,
+                                         C.c_double, i32, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -141,6 +145,25 @@ class Config:
 def workspace_bytes(cfg: Config) -> int:
     c = cfg.c()
     return int(load().vm_workspace_bytes(C.byref(c)))
+
+
+def force_from_f_static(f, cfg: Config, out: dict, stream=None) -> None:
+    """Pixel masses and force of a device tensor f ([nx, nv], float64 or
+    float32) into the device tensors out["a"], out["da"], out["d2a"] (and
+    out["M"] if present), through the allocation-free entry point: its only
+    scratch is a static device array of at most VM_STATIC_FORCE_MAX_NX pixel
+    masses shared by all calls (serialise calls that could overlap)."""
+    import torch
+    L = load()
+    if cfg.nx > VM_STATIC_FORCE_MAX_NX:
+        raise ValueError(f"nx = {cfg.nx} exceeds the static scratch limit of {VM_STATIC_FORCE_MAX_NX} pixels")
+    assert f.is_cuda and f.is_contiguous() and tuple(f.shape) == (cfg.nx, cfg.nv)
+    dtype = {torch.float64: VM_DTYPE_F64, torch.float32: VM_DTYPE_F32}[f.dtype]
+    st = stream if stream is not None else torch.cuda.current_stream(f.device)
+    ptr = lambda k: C.c_void_p(out[k].data_ptr()) if k in out else None  # noqa: E731
+    _check(L.vm_force_from_f_static(C.c_void_p(f.data_ptr()), dtype, cfg.nx, cfg.nv, cfg.x_lo, cfg.x_hi,
+                                    cfg.v_lo, cfg.v_hi, cfg.G, cfg.literal_fd, ptr("M"), ptr("a"), ptr("da"),
+                                    ptr("d2a"), C.c_void_p(st.cuda_stream)), "vm_force_from_f_static")
 
 
 class Solver:
