@@ -16,8 +16,8 @@ constexpr double kPi = 3.14159265358979323846;
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t fini, eta, f, tmp, map, keys, holes_a, holes_b, ovf, el, tay, M, a, da, d2a, thx, thv, thxf, thvf,
-      ds, total;
+  size_t fini, eta, f, tmp, map, slot1, extras, conflicts, holes_a, holes_b, ovf, el, tay, tayf, M, a, da, d2a,
+      thx, thv, thxf, thvf, ds, total;
 };
 
 bool valid(const vm_config* c) {
@@ -27,8 +27,11 @@ bool valid(const vm_config* c) {
   if (c->precision != VM_FP64 && c->precision != VM_FP32_MIXED) return false;
   if (c->pad < 0 || c->max_hole_rounds < 0) return false;
   if (!(c->alpha >= 0.0) || !(c->beta >= 0.0)) return false;
-  // 32-bit site and element indices
+  // 32-bit site indices; element indices fit the 24-bit field of the owner slots
   if ((long long)c->nx * (long long)c->nv >= (1ll << 31) / 2) return false;
+  const long long s = c->elem_stride;
+  const long long Lx = 2 * ((c->nx - 1 + 2 * s - 1) / (2 * s)) + 3, Lv = 2 * ((c->nv - 1 + 2 * s - 1) / (2 * s)) + 3;
+  if (Lx * Lv >= (1ll << 24)) return false;
   return true;
 }
 
@@ -57,12 +60,15 @@ Layout layout(const vm_config* c) {
   L.f = take(n * sr);
   L.tmp = take(n * sr);
   L.map = take(n * 4);
-  L.keys = take(n * 16);
+  L.slot1 = take(n * 4);
+  L.extras = take(n * 8);
+  L.conflicts = take(n * 4);
   L.holes_a = take(n * 4);
   L.holes_b = take(2 * n * 4);
   L.ovf = take(2 * ne * 8);
   L.el = take(12 * ne * 8);
   L.tay = take(16 * ne * 8);
+  L.tayf = take(32 * ne * 4);
   L.M = take(c->nx * 8);
   L.a = take(c->nx * 8);
   L.da = take(c->nx * 8);
@@ -112,11 +118,9 @@ vm_status remap_internal(vm_solver* s) {
   return check_launch(s);
 }
 
-// Restore the claim keys after they served as a staging buffer.
-vm_status reset_keys(vm_solver* s) {
-  VM_CUDA_TRY(cudaMemsetAsync(s->keys, 0xFF, s->n * 16, s->stream));
-  return VM_OK;
-}
+// 8 bytes per site of scratch for the copy calls: the second hole list,
+// which only lives inside one influence map.
+void* staging(vm_solver* s) { return s->holes_b; }
 
 vm_status read_real(vm_solver* s, const void* src, void* out, int32_t dtype, int32_t on_device) {
   if (!out || (dtype != VM_DTYPE_F64 && dtype != VM_DTYPE_F32)) return VM_E_INVALID_ARG;
@@ -133,17 +137,15 @@ vm_status read_real(vm_solver* s, const void* src, void* out, int32_t dtype, int
   if (same) {
     VM_CUDA_TRY(cudaMemcpyAsync(out, src, s->n * esz, cudaMemcpyDeviceToHost, s->stream));
   } else {
-    vm::launch_convert(s, src, s->keys, dtype, s->n);
-    VM_CUDA_TRY(cudaMemcpyAsync(out, s->keys, s->n * esz, cudaMemcpyDeviceToHost, s->stream));
-    vm_status st = reset_keys(s);
-    if (st != VM_OK) return st;
+    vm::launch_convert(s, src, staging(s), dtype, s->n);
+    VM_CUDA_TRY(cudaMemcpyAsync(out, staging(s), s->n * esz, cudaMemcpyDeviceToHost, s->stream));
   }
   return vm_sync(s);
 }
 
 const char* const kKernelNames[vm::KID_N] = {
     "drift_taylor", "taylor", "kick_drift", "reset_elements", "scan_force", "diagnostics",
-    "map_clear", "claim_small", "claim_large", "map_finalize", "holes",
+    "map_clear", "claim_small", "claim_large", "find_holes", "holes", "resolve", "read_map",
     "reconstruct", "remap_resample", "convert", "spline_rows", "spline_cols"};
 
 }  // namespace
@@ -262,14 +264,17 @@ vm_status vm_create(const vm_config* c, void* d_workspace, size_t bytes, void* s
   s->eta = base + L.eta;
   s->f = base + L.f;
   s->tmp = base + L.tmp;
-  s->map = (int32_t*)(base + L.map);
-  s->keys = (unsigned long long*)(base + L.keys);
+  s->map = (uint32_t*)(base + L.map);
+  s->slot1 = (uint32_t*)(base + L.slot1);
+  s->extras = (int2*)(base + L.extras);
+  s->conflicts = (int32_t*)(base + L.conflicts);
   s->holes_a = (int32_t*)(base + L.holes_a);
   s->holes_b = (int32_t*)(base + L.holes_b);
   s->overflow_list = (int2*)(base + L.ovf);
   s->overflow_list2 = s->overflow_list + ne_total(s);
   s->el = (double*)(base + L.el);
   s->tay = (double*)(base + L.tay);
+  s->tayf = (float*)(base + L.tayf);
   s->M = (double*)(base + L.M);
   s->a = (double*)(base + L.a);
   s->da = (double*)(base + L.da);
@@ -290,8 +295,9 @@ vm_status vm_create(const vm_config* c, void* d_workspace, size_t bytes, void* s
   vm_status st = VM_OK;
   do {
     if (cudaMemsetAsync(base, 0, L.total, s->stream) != cudaSuccess) { st = VM_E_CUDA; break; }
-    if (cudaMemsetAsync(s->keys, 0xFF, s->n * 16, s->stream) != cudaSuccess) { st = VM_E_CUDA; break; }
+    // owner slots start empty (all-ones: an epoch no map uses)
     if (cudaMemsetAsync(s->map, 0xFF, s->n * 4, s->stream) != cudaSuccess) { st = VM_E_CUDA; break; }
+    if (cudaMemsetAsync(s->slot1, 0xFF, s->n * 4, s->stream) != cudaSuccess) { st = VM_E_CUDA; break; }
     if (cudaMemcpyAsync(s->thomas_x, tx.data(), tx.size() * 8, cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
         cudaMemcpyAsync(s->thomas_v, tv.data(), tv.size() * 8, cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
         cudaMemcpyAsync(s->thomas_xf, txf.data(), txf.size() * 4, cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
@@ -366,14 +372,10 @@ vm_status vm_set_f(vm_solver* s, const double* f0, int32_t on_device) {
   } else {
     const double* src = f0;
     if (!on_device) {
-      VM_CUDA_TRY(cudaMemcpyAsync(s->keys, f0, bytes, cudaMemcpyHostToDevice, s->stream));
-      src = (const double*)s->keys;
+      VM_CUDA_TRY(cudaMemcpyAsync(staging(s), f0, bytes, cudaMemcpyHostToDevice, s->stream));
+      src = (const double*)staging(s);
     }
     vm::launch_store_real(s, src, s->fini, s->n);
-    if (!on_device) {
-      vm_status st = reset_keys(s);
-      if (st != VM_OK) return st;
-    }
   }
   VM_CUDA_TRY(cudaMemcpyAsync(s->f, s->fini, s->n * s->sreal, cudaMemcpyDeviceToDevice, s->stream));
   vm::launch_spline_solve(s, s->fini, s->eta);
@@ -469,9 +471,13 @@ vm_status vm_read_eta(vm_solver* s, void* out, int32_t dtype, int32_t on_device)
 
 vm_status vm_read_map(vm_solver* s, int32_t* out, int32_t on_device) {
   if (!s || !out) return VM_E_INVALID_ARG;
-  VM_CUDA_TRY(cudaMemcpyAsync(out, s->map, s->n * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                              s->stream));
-  return on_device ? VM_OK : vm_sync(s);
+  if (on_device) {
+    vm::launch_read_map(s, out);
+    return check_launch(s);
+  }
+  vm::launch_read_map(s, (int32_t*)staging(s));
+  VM_CUDA_TRY(cudaMemcpyAsync(out, staging(s), s->n * 4, cudaMemcpyDeviceToHost, s->stream));
+  return vm_sync(s);
 }
 
 vm_status vm_sync(vm_solver* s) {

@@ -12,7 +12,6 @@ namespace vm {
 enum : int32_t {
   ERR_NOT_CONVERGED = 1,
   ERR_PATCH_OVERFLOW = 2,
-  ERR_LIST_OVERFLOW = 4,
 };
 
 // Grid, lattice and method constants, passed by value to every kernel.  All
@@ -31,26 +30,47 @@ struct Grid {
 // Small device-resident control block.
 struct DevState {
   int32_t err;
+  // counters of one influence map (cleared together at its start)
   int32_t nholes;        // holes in the working list
   int32_t holes_found;   // holes left by the claims (statistics)
   int32_t hole_rounds;   // repair rounds of the last map (statistics)
-  int32_t noverflow;     // elements queued for the band / large windows
+  int32_t noverflow;     // elements queued for the first large-window attempt
   int32_t overflow_stat;
-  int32_t noverflow2;    // elements queued for the second large-window attempt
+  int32_t noverflow2;    // ... second attempt
   int32_t overflow2_stat;
-  int32_t noverflow3;    // elements queued for the third attempt
+  int32_t noverflow3;    // ... third attempt
   int32_t overflow3_stat;
+  int32_t nconflict;     // sites claimed by two or more elements
+  int32_t nextra;        // claims beyond the second one on a site
   double Mtot;           // total mass of the last reconstruction
   double sum_mass, sum_kin, sum_pot;
   unsigned long long det_min_key, det_max_key;
 };
+constexpr int kMapCounters = 11;  // int32 fields from nholes to nextra
+
+// Owner slots of the influence map: (epoch << 24) | element index.  A slot
+// whose epoch is not the current map's is empty; every site is rewritten
+// each map (claimed or repaired), so stale values are never more than one
+// map old, and the second slot is cleared when its conflict is resolved.
+constexpr uint32_t SLOT_EMPTY = 0xFFFFFFFFu;
+constexpr uint32_t SLOT_MASK = 0x00FFFFFFu;
+constexpr int kEpochs = 255;  // epochs 0..254; 255 never current
 
 // Element state: 12 doubles per element, structure of arrays.
 enum { EL_X = 0, EL_V, EL_TXX, EL_TXV, EL_TVX, EL_TVV, EL_HXXX, EL_HXXV, EL_HXVV, EL_HVXX, EL_HVXV, EL_HVVV, EL_N };
 // Taylor record: 16 doubles (128 bytes) per element, array of structures so
 // that one element's terms are one cache line for the per-site gathers.
 enum { TY_X = 0, TY_V, TY_TI00, TY_TI01, TY_TI10, TY_TI11, TY_GX00, TY_GX01, TY_GX11,
-       TY_GV00, TY_GV01, TY_GV11, TY_QX, TY_QV, TY_N = 16 };
+       TY_GV00, TY_GV01, TY_GV11, TY_QX, TY_QV, TY_U, TY_W, TY_N = 16 };
+// FP32 record of the inverse map in element units (32 words = 128 bytes):
+// with p = (P - P_m)/Delta_m and q = (Q - Q_m)/Delta_m,
+//   q_a = sum_b T[a][b] p_b - 1/2 sum_l K[a][l] s_l,  s_l = p^T G_l p,
+// and |each term| of q_a bounded by C1_a |p|_inf + C2_a |p|_inf^2 (the
+// coefficients of the bound are rounded up).  UF/WF and UI/WI split the
+// element's index position u_m = (x_m - x_lo)/dx into integer and fraction.
+enum { TF_T00 = 0, TF_T01, TF_T10, TF_T11, TF_GX00, TF_GX01, TF_GX11, TF_GV00, TF_GV01, TF_GV11,
+       TF_K00, TF_K01, TF_K10, TF_K11, TF_C1X, TF_C2X, TF_C1V, TF_C2V, TF_UF, TF_WF, TF_UI, TF_WI,
+       TF_N = 32 };
 
 constexpr unsigned long long KEY_EMPTY = ~0ull;
 
@@ -58,6 +78,7 @@ constexpr unsigned long long KEY_EMPTY = ~0ull;
 enum KernelId {
   KID_DRIFT = 0, KID_TAYLOR, KID_KICK_DRIFT, KID_RESET, KID_SCAN_FORCE, KID_DIAG,
   KID_MAP_CLEAR, KID_CLAIM_SMALL, KID_CLAIM_LARGE, KID_FINALIZE, KID_HOLES,
+  KID_RESOLVE, KID_READ_MAP,
   KID_RECON, KID_REMAP, KID_CONVERT, KID_SPLINE_ROWS, KID_SPLINE_COLS, KID_N
 };
 constexpr int PROF_CAP = 1024;
@@ -76,14 +97,17 @@ struct vm_solver {
   void* eta;
   void* f;
   void* tmp;
-  int32_t* map;
-  unsigned long long* keys;  // 2 words per site: {element index, bits of d^2}
+  uint32_t* map;            // owner slot 0: the influence map (epoch-tagged)
+  uint32_t* slot1;          // owner slot 1 (second claimant of a site)
+  int2* extras;             // (site, element) of further claimants
+  int32_t* conflicts;       // sites with two or more claimants
   int32_t* holes_a;
-  int32_t* holes_b;
+  int32_t* holes_b;         // also the 8 B/site staging buffer of the copy calls
   int2* overflow_list;      // (element, window mode) for the second tier
   int2* overflow_list2;     // for the last-resort tier
   double* el;               // 12 x ne
   double* tay;              // ne x 16
+  float* tayf;              // ne x 32 (FP32 record, element units)
   double* M;                // pixel masses of the last step
   double* a;
   double* da;
@@ -95,6 +119,7 @@ struct vm_solver {
   vm::DevState* ds;
   // host-side bookkeeping
   int32_t have_f;
+  uint32_t epoch;           // epoch of the current influence map
   int64_t nstep;
   int32_t cyc;
   int64_t launches;
@@ -128,6 +153,7 @@ void launch_diagnostics(vm_solver* s);
 // map.cu
 bool map_prepare(const Grid& g);
 void launch_map(vm_solver* s);
+void launch_read_map(vm_solver* s, int32_t* dst);
 // recon.cu
 void launch_reconstruct(vm_solver* s);
 void launch_remap_resample(vm_solver* s, void* out);

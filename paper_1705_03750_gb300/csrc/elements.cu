@@ -6,13 +6,59 @@
 // operation in a fixed order with non-contracting intrinsics, so that given
 // the same force arrays the element trajectories are reproducible to the
 // last bit by any FP64 restatement that uses the same order.
+#include <climits>
+
 #include "common.cuh"
 
 namespace vm {
 namespace {
 
+__device__ __forceinline__ float up32(double x) {
+  // float >= x (for bound coefficients, x >= 0)
+  float f = __double2float_ru(x);
+  return f;
+}
+
+// FP32 record of element m (see TF_* in common.cuh) from its FP64 terms.
+__device__ __forceinline__ void taylor_f32(const Grid& g, const double* t, float* __restrict__ F) {
+  const double dxm = g.dxm, dvm = g.dvm;
+  const double T00 = t[TY_TI00], T01 = t[TY_TI01] * dvm / dxm, T10 = t[TY_TI10] * dxm / dvm, T11 = t[TY_TI11];
+  F[TF_T00] = (float)T00;
+  F[TF_T01] = (float)T01;
+  F[TF_T10] = (float)T10;
+  F[TF_T11] = (float)T11;
+  double gs[2];
+#pragma unroll
+  for (int l = 0; l < 2; l++) {
+    const double g00 = t[TY_GX00 + 3 * l] * dxm * dxm;
+    const double g01 = t[TY_GX01 + 3 * l] * dxm * dvm;
+    const double g11 = t[TY_GX11 + 3 * l] * dvm * dvm;
+    F[TF_GX00 + 3 * l] = (float)g00;
+    F[TF_GX01 + 3 * l] = (float)g01;
+    F[TF_GX11 + 3 * l] = (float)g11;
+    gs[l] = fabs(g00) + 2.0 * fabs(g01) + fabs(g11);
+  }
+  const double K00 = t[TY_TI00] / dxm, K01 = t[TY_TI01] / dxm, K10 = t[TY_TI10] / dvm, K11 = t[TY_TI11] / dvm;
+  F[TF_K00] = (float)K00;
+  F[TF_K01] = (float)K01;
+  F[TF_K10] = (float)K10;
+  F[TF_K11] = (float)K11;
+  const double slack = 1.0 + 1e-6;
+  F[TF_C1X] = up32((fabs(T00) + fabs(T01)) * slack);
+  F[TF_C2X] = up32(0.5 * (fabs(K00) * gs[0] + fabs(K01) * gs[1]) * slack);
+  F[TF_C1V] = up32((fabs(T10) + fabs(T11)) * slack);
+  F[TF_C2V] = up32(0.5 * (fabs(K10) * gs[0] + fabs(K11) * gs[1]) * slack);
+  const double u = t[TY_U], w = t[TY_W];
+  const double ui = floor(u), wi = floor(w);
+  const bool ok = (u > -1e9 && u < 1e9 && w > -1e9 && w < 1e9);
+  F[TF_UF] = ok ? (float)(u - ui) : 0.f;
+  F[TF_WF] = ok ? (float)(w - wi) : 0.f;
+  reinterpret_cast<int*>(F)[TF_UI] = ok ? (int)ui : INT_MIN / 2;
+  reinterpret_cast<int*>(F)[TF_WI] = ok ? (int)wi : INT_MIN / 2;
+}
+
 __device__ __forceinline__ void taylor_one(const Grid& g, const double* __restrict__ el, int m,
-                                           double* __restrict__ tay) {
+                                           double* __restrict__ tay, float* __restrict__ tayf) {
   const int ne = g.ne;
   double x = el[EL_X * ne + m], v = el[EL_V * ne + m];
   double Txx = el[EL_TXX * ne + m], Txv = el[EL_TXV * ne + m];
@@ -43,13 +89,16 @@ __device__ __forceinline__ void taylor_one(const Grid& g, const double* __restri
   int k = m / g.Lv, l = m - k * g.Lv;
   t[TY_QX] = dadd(g.cx, dmul((double)(k - g.Kx - 1), g.dxm));
   t[TY_QV] = dadd(g.cv, dmul((double)(l - g.Kv - 1), g.dvm));
-  t[14] = 0.0;
-  t[15] = 0.0;
+  // index position of P_m, as the start site of the percolation uses it
+  t[TY_U] = dmul(dsub(x, g.x_lo), g.inv_dx);
+  t[TY_W] = dmul(dsub(v, g.v_lo), g.inv_dv);
+  taylor_f32(g, t, tayf + (size_t)m * TF_N);
 }
 
 // Half drift (predictor or corrector of Sec. 2.4): x, T_x. and H_x.. move
 // with v, T_v. and H_v..; optionally followed by the Taylor terms.
-__global__ void k_drift(Grid g, double* __restrict__ el, double* __restrict__ tay, int taylor) {
+__global__ void k_drift(Grid g, double* __restrict__ el, double* __restrict__ tay, float* __restrict__ tayf,
+                        int taylor) {
   int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= g.ne) return;
   const int ne = g.ne;
@@ -60,12 +109,12 @@ __global__ void k_drift(Grid g, double* __restrict__ el, double* __restrict__ ta
 #pragma unroll
   for (int q = 0; q < 3; q++)
     el[(EL_HXXX + q) * ne + m] = dadd(el[(EL_HXXX + q) * ne + m], dmul(el[(EL_HVXX + q) * ne + m], h));
-  if (taylor) taylor_one(g, el, m, tay);
+  if (taylor) taylor_one(g, el, m, tay, tayf);
 }
 
-__global__ void k_taylor(Grid g, const double* __restrict__ el, double* __restrict__ tay) {
+__global__ void k_taylor(Grid g, const double* __restrict__ el, double* __restrict__ tay, float* __restrict__ tayf) {
   int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m < g.ne) taylor_one(g, el, m, tay);
+  if (m < g.ne) taylor_one(g, el, m, tay, tayf);
 }
 
 // Dual TSC interpolation (Sec. 2.5) at index coordinate u; beyond the grid
@@ -287,12 +336,12 @@ inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) /
 }  // namespace
 
 void launch_drift(vm_solver* s, bool taylor) {
-  { const int ps_ = prof_begin(s, KID_DRIFT); k_drift<<<blocks_for(s->g.ne, 256), 256, 0, s->stream>>>(s->g, s->el, s->tay, taylor ? 1 : 0); prof_end(s, ps_); }
+  { const int ps_ = prof_begin(s, KID_DRIFT); k_drift<<<blocks_for(s->g.ne, 256), 256, 0, s->stream>>>(s->g, s->el, s->tay, s->tayf, taylor ? 1 : 0); prof_end(s, ps_); }
   s->launches++;
 }
 
 void launch_taylor(vm_solver* s) {
-  { const int ps_ = prof_begin(s, KID_TAYLOR); k_taylor<<<blocks_for(s->g.ne, 256), 256, 0, s->stream>>>(s->g, s->el, s->tay); prof_end(s, ps_); }
+  { const int ps_ = prof_begin(s, KID_TAYLOR); k_taylor<<<blocks_for(s->g.ne, 256), 256, 0, s->stream>>>(s->g, s->el, s->tay, s->tayf); prof_end(s, ps_); }
   s->launches++;
 }
 

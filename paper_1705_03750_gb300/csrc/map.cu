@@ -4,34 +4,46 @@
 // 4-connected component, containing the grid site nearest to P_m, of the
 // sites that pass m's test (no investigated neighbour proposes a strictly
 // smaller d).  Each element is flood-filled inside a window of bit masks
-// held in shared memory (evaluated / passing / claimed), with the window
-// sized in three tiers:
+// held in shared memory (evaluated / passing / claimed), sized in tiers:
 //
-//   1. a 64 x 128 window, one warp per element, one percolation test per
-//      newly reached site (lazy breadth-first growth: the test runs once per
-//      site of the component and of its rim);
+//   1. a 64 x 128 window, one warp per element.  Each round dilates the
+//      component by one site and tests only the newly reached sites, which
+//      are compacted into a list so that all 32 lanes share the tests;
 //   2. for the elements whose component reached the edge of tier 1, up to
 //      three attempts with larger windows, in an order set by the sides it
 //      escaped from: a band window 128 sites across and as long as shared
 //      memory allows along v (the whole padded lattice at 4096^2), the same
-//      along x, and a 256 x 256 window.  Elements of the outer layer whose
-//      neighbours have moved away claim long thin bands; to cross them in
-//      few rounds, any 64-site word the component reaches is evaluated
-//      whole, and the component is then extended through runs of passing
-//      sites inside the word with one carry-propagating addition.
+//      along x, and a 256 x 256 window.  Outer-layer elements whose
+//      neighbours moved away claim long thin bands; to cross them in few
+//      rounds, any 64-site word the component reaches is tested whole and
+//      the component is extended through runs of passing sites inside the
+//      word with one carry-propagating addition.
 //
-// Claims are resolved by one 128-bit atomic compare-and-swap minimum per
-// claimed site on the key (bits of d^2, element index): smallest distance
-// wins, ties go to the smaller index.  A finalize pass turns keys into the
-// int32 map, resets them and lists unclaimed sites; one block repairs those
-// in Jacobi rounds from their 4-neighbours.
+// Decisions.  The percolation's outcome is fixed by FP64 values evaluated in
+// one operation order (the exact test).  Each test is first run in FP32 in
+// element units together with a rigorous bound on the distance between the
+// FP32 value and the FP64 one (forward error of the evaluation, <= gamma_k
+// times the same expression on absolute values, bounded per element by
+// C1 |p| + C2 |p|^2); the FP32 result is used only when every range and
+// distance comparison clears its bound, otherwise the exact FP64 test runs.
+// The outcome is therefore identical to the all-FP64 evaluation.
 //
-// Every decision (ranges, the d comparisons, the claim order) is taken on
-// FP64 values computed operation by operation in a fixed order.
+// Claims.  A claimed site's owner slot takes (epoch << 24 | m) with one
+// atomic exchange; a displaced current-epoch owner moves to the second
+// slot (the site is then listed as a conflict) or to the extras list.
+// Conflicts are resolved afterwards by the exact FP64 key (bits of d^2,
+// element index), smallest first.  Unclaimed sites are repaired in Jacobi
+// rounds from their 4-neighbours.
+#include <math.h>
+
 #include "common.cuh"
 
 namespace vm {
 namespace {
+
+// ---------------------------------------------------------------------------
+// exact FP64 test
+// ---------------------------------------------------------------------------
 
 __device__ __forceinline__ void alpha_range(double r, double alpha, int& lo, int& hi) {
   if (r < -alpha) {
@@ -46,12 +58,11 @@ __device__ __forceinline__ void alpha_range(double r, double alpha, int& lo, int
   }
 }
 
-// Percolation test of site P for the centre element of a 3x3 block of
+// Percolation test of site P for the centre element of a 3x3 block of FP64
 // Taylor records (index 4).
-__device__ bool pass_test(const Grid& g, const double (*T9)[TY_N], const int* ex9, double Px,
-                          double Pv, double& d2) {
+__device__ bool pass_exact(const Grid& g, const double (*T9)[TY_N], const int* ex9, double Px, double Pv) {
   double xi, ze;
-  d2 = dist2_exact(T9[4], g, Px, Pv, xi, ze);
+  const double d2 = dist2_exact(T9[4], g, Px, Pv, xi, ze);
   int a0, a1, b0, b1;
   alpha_range(xi, g.alpha, a0, a1);
   alpha_range(ze, g.alpha, b0, b1);
@@ -67,40 +78,103 @@ __device__ bool pass_test(const Grid& g, const double (*T9)[TY_N], const int* ex
   return true;
 }
 
-// 128-bit compare-and-swap on global memory (sm_90 and later).
-__device__ __forceinline__ ulonglong2 cas128(unsigned long long* addr, ulonglong2 cmp, ulonglong2 val) {
-  ulonglong2 old;
-  asm volatile(
-      "{\n\t"
-      ".reg .b128 c, v, r;\n\t"
-      "mov.b128 c, {%2, %3};\n\t"
-      "mov.b128 v, {%4, %5};\n\t"
-      "atom.global.cas.b128 r, [%6], c, v;\n\t"
-      "mov.b128 {%0, %1}, r;\n\t"
-      "}"
-      : "=l"(old.x), "=l"(old.y)
-      : "l"(cmp.x), "l"(cmp.y), "l"(val.x), "l"(val.y), "l"(addr)
-      : "memory");
-  return old;
+// ---------------------------------------------------------------------------
+// FP32 test with certified decisions
+// ---------------------------------------------------------------------------
+
+// Bound constants: the FP32 evaluation of q has at most ~15 rounding factors
+// per monomial (inputs rounded to FP32, products and sums), d^2 at most ~31;
+// gamma_31(2^-24) < 1.9e-6.  The constants carry a factor ~2 of margin, and
+// the absolute term covers the last-bit differences between the FP32 inputs'
+// source values and the FP64 evaluation's own inputs.
+constexpr float kRelQ = 2.0e-6f, kRelD = 4.0e-6f, kAbs = 1.0e-9f;
+
+struct QF {
+  float qx, qv, ax, av;  // offset in element units and bounds of |terms|
+};
+
+__device__ __forceinline__ QF qeval(const float* __restrict__ F, float px, float pv) {
+  QF r;
+  const float yx = F[TF_T00] * px + F[TF_T01] * pv;
+  const float yv = F[TF_T10] * px + F[TF_T11] * pv;
+  const float sx = px * (F[TF_GX00] * px + F[TF_GX01] * pv) + pv * (F[TF_GX01] * px + F[TF_GX11] * pv);
+  const float sv = px * (F[TF_GV00] * px + F[TF_GV01] * pv) + pv * (F[TF_GV01] * px + F[TF_GV11] * pv);
+  r.qx = yx - 0.5f * (F[TF_K00] * sx + F[TF_K01] * sv);
+  r.qv = yv - 0.5f * (F[TF_K10] * sx + F[TF_K11] * sv);
+  const float P = fmaxf(fabsf(px), fabsf(pv));
+  r.ax = F[TF_C1X] * P + F[TF_C2X] * (P * P);
+  r.av = F[TF_C1V] * P + F[TF_C2V] * (P * P);
+  return r;
 }
 
-// keys[2p] = element index, keys[2p+1] = bits of d^2: as a 128-bit integer
-// its order is the claim order.
-__device__ __forceinline__ void claim_min(unsigned long long* key2, unsigned long long dbits,
-                                          unsigned long long idx) {
-  ulonglong2 cur = __ldcg(reinterpret_cast<const ulonglong2*>(key2));
-  const ulonglong2 val = make_ulonglong2(idx, dbits);
-  while (dbits < cur.y || (dbits == cur.y && idx < cur.x)) {
-    const ulonglong2 prev = cas128(key2, cur, val);
-    if (prev.x == cur.x && prev.y == cur.y) break;
-    cur = prev;
+// Range of one axis from q with |q - r| <= e, r the FP64 value: 1 = {-1,0},
+// 2 = {0}, 3 = {0,1}, 0 = cannot tell.
+__device__ __forceinline__ int range_f(float q, float e, float alo, float ahi) {
+  if (q + e < -ahi) return 1;
+  if (q - e >= -alo && q + e < alo) return 2;
+  if (q - e >= ahi) return 3;
+  return 0;
+}
+
+struct Ctx9 {
+  const float (*F9)[TF_N];
+  const int* ex9;
+  const float* offu;  // (i0 - u_m') for the 9 elements, i0 the window's start site
+  const float* offv;
+  float inv_s, alo, ahi;
+};
+
+// 1: passes, 0: fails, -1: the bound does not settle it (run the exact test).
+__device__ __forceinline__ int pass_f32(const Ctx9& c, float di, float dj) {
+  const QF m = qeval(c.F9[4], (di + c.offu[4]) * c.inv_s, (dj + c.offv[4]) * c.inv_s);
+  const float ex = kRelQ * m.ax + kAbs * (1.f + m.ax), ev = kRelQ * m.av + kAbs * (1.f + m.av);
+  const int ra = range_f(m.qx, ex, c.alo, c.ahi), rb = range_f(m.qv, ev, c.alo, c.ahi);
+  if (!ra || !rb) return -1;
+  const float d2 = m.qx * m.qx + m.qv * m.qv;
+  const float A2 = m.ax * m.ax + m.av * m.av;
+  const float e2 = kRelD * A2 + kAbs * (1.f + A2);
+  const int a0 = (ra == 1) ? -1 : 0, a1 = (ra == 3) ? 1 : 0;
+  const int b0 = (rb == 1) ? -1 : 0, b1 = (rb == 3) ? 1 : 0;
+  for (int a = a0; a <= a1; a++)
+    for (int b = b0; b <= b1; b++) {
+      if (a == 0 && b == 0) continue;
+      const int q = (a + 1) * 3 + (b + 1);
+      if (!c.ex9[q]) continue;
+      const QF n = qeval(c.F9[q], (di + c.offu[q]) * c.inv_s, (dj + c.offv[q]) * c.inv_s);
+      const float d2n = n.qx * n.qx + n.qv * n.qv;
+      const float An = n.ax * n.ax + n.av * n.av;
+      const float en = kRelD * An + kAbs * (1.f + An);
+      if (d2n + en < d2 - e2) return 0;
+      if (!(d2n - en >= d2 + e2)) return -1;
+    }
+  return 1;
+}
+
+// ---------------------------------------------------------------------------
+// claims
+// ---------------------------------------------------------------------------
+
+struct Slots {
+  uint32_t* slot0;
+  uint32_t* slot1;
+  int2* extras;
+  int32_t* conflicts;
+  DevState* ds;
+  uint32_t epoch;
+};
+
+__device__ __forceinline__ void claim(const Slots& S, const Grid& g, long long i, long long j, int m) {
+  if (i < 0 || i >= g.nx || j < 0 || j >= g.nv) return;
+  const size_t p = (size_t)i * g.nv + j;
+  const uint32_t tag = (S.epoch << 24) | (uint32_t)m;
+  const uint32_t old = atomicExch(&S.slot0[p], tag);
+  if ((old >> 24) != S.epoch) return;                // first claimant this map
+  const uint32_t old1 = atomicExch(&S.slot1[p], old);  // keep the displaced one
+  if ((old1 >> 24) != S.epoch) {
+    S.conflicts[atomicAdd(&S.ds->nconflict, 1)] = (int32_t)p;
+    return;
   }
-}
-
-__device__ __forceinline__ void claim_site(const Grid& g, unsigned long long* keys, long long i, long long j,
-                                           double d2, int m) {
-  if (i >= 0 && i < g.nx && j >= 0 && j < g.nv)
-    claim_min(keys + 2 * ((size_t)i * g.nv + j), dkey(d2), (unsigned long long)m);
+  S.extras[atomicAdd(&S.ds->nextra, 1)] = make_int2((int)p, (int)(old1 & SLOT_MASK));
 }
 
 // Mask of window columns [lo, hi) within word w (64 columns per word).
@@ -124,138 +198,200 @@ __device__ __forceinline__ unsigned long long run_fill(unsigned long long S, uns
 
 enum : int { MODE_BAND_V = 0, MODE_BAND_X = 1, MODE_FAT = 2 };
 
-__device__ __forceinline__ void load_T9(const Grid& g, int m, const double* __restrict__ tay,
-                                        double (*T9)[TY_N], int* ex9) {
+// Shared part of every window: the element's 3x3 neighbourhood in FP64 and
+// FP32, and the FP32 offsets of their positions from the start site.
+struct Elem9 {
+  double T9[9][TY_N];
+  float F9[9][TF_N];
+  int ex9[9];
+  float offu[9], offv[9];
+};
+
+__device__ __forceinline__ void load_elem9(const Grid& g, int m, const double* __restrict__ tay,
+                                           const float* __restrict__ tayf, Elem9& E) {
   const int k = m / g.Lv, l = m - k * g.Lv;
   for (int idx = threadIdx.x; idx < 9 * TY_N; idx += blockDim.x) {
     const int q = idx / TY_N, c = idx - q * TY_N;
     const int kk = k + q / 3 - 1, ll = l + q % 3 - 1;
     const bool ex = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
-    T9[q][c] = ex ? tay[(size_t)(kk * g.Lv + ll) * TY_N + c] : 0.0;
-    if (c == 0) ex9[q] = ex;
+    E.T9[q][c] = ex ? tay[(size_t)(kk * g.Lv + ll) * TY_N + c] : 0.0;
+    if (c == 0) E.ex9[q] = ex;
+  }
+  for (int idx = threadIdx.x; idx < 9 * TF_N; idx += blockDim.x) {
+    const int q = idx / TF_N, c = idx - q * TF_N;
+    const int kk = k + q / 3 - 1, ll = l + q % 3 - 1;
+    const bool ex = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
+    E.F9[q][c] = ex ? tayf[(size_t)(kk * g.Lv + ll) * TF_N + c] : 0.f;
   }
 }
 
+__device__ __forceinline__ bool start_site(const Grid& g, const Elem9& E, long long& i0, long long& j0) {
+  const double us = E.T9[4][TY_U], ws = E.T9[4][TY_W];
+  if (!(us > -1e9 && us < 1e9 && ws > -1e9 && ws < 1e9)) return false;
+  i0 = (long long)floor(dadd(us, 0.5));
+  j0 = (long long)floor(dadd(ws, 0.5));
+  return !(i0 < -g.pad || i0 >= g.nx + g.pad || j0 < -g.pad || j0 >= g.nv + g.pad);
+}
+
+// Offsets i0 - u_m' of the neighbourhood (FP64 difference, then FP32).
+__device__ __forceinline__ void set_offsets(Elem9& E, long long i0, long long j0) {
+  const int q = threadIdx.x;
+  if (q < 9) {
+    E.offu[q] = E.ex9[q] ? (float)((double)i0 - E.T9[q][TY_U]) : 0.f;
+    E.offv[q] = E.ex9[q] ? (float)((double)j0 - E.T9[q][TY_W]) : 0.f;
+  }
+}
+
+__device__ __forceinline__ Ctx9 ctx_of(const Grid& g, const Elem9& E, float alo, float ahi) {
+  Ctx9 c;
+  c.F9 = E.F9;
+  c.ex9 = E.ex9;
+  c.offu = E.offu;
+  c.offv = E.offv;
+  c.inv_s = 1.0f / (float)g.s;
+  c.alo = alo;
+  c.ahi = ahi;
+  return c;
+}
+
+__device__ __forceinline__ bool test_site(const Grid& g, const Elem9& E, const Ctx9& c, long long i0, long long j0,
+                                          long long i, long long j) {
+  const int r = pass_f32(c, (float)(i - i0), (float)(j - j0));
+  if (r >= 0) return r == 1;
+  return pass_exact(g, E.T9, E.ex9, site_x(g, i), site_v(g, j));
+}
+
 // ---------------------------------------------------------------------------
-// tier 1: 64 x 128 window, one warp per element, lazy per-site growth
+// tier 1: 64 x 128 window, one warp per element, compacted frontier
 // ---------------------------------------------------------------------------
 
-constexpr int SR = 64, SW = 2, ST = 32;
+constexpr int SR = 64, SW = 2, ST = 32, SCAP = 256;
 
 struct SmallShared {
-  double T9[9][TY_N];
-  int ex9[9];
+  Elem9 E;
   unsigned long long comp[SR][SW];
   unsigned long long eval[SR][SW];
-  int ok;
+  unsigned short item[SCAP];
 };
 
 __global__ void __launch_bounds__(ST) k_claim_small(Grid g, const double* __restrict__ tay,
-                                                    unsigned long long* __restrict__ keys, DevState* ds,
+                                                    const float* __restrict__ tayf, Slots S, float alo, float ahi,
                                                     int2* __restrict__ ovf_list) {
   constexpr int COLS = 64 * SW, RPT = SR / ST;
-  __shared__ SmallShared S;
-  const int m = blockIdx.x, tid = threadIdx.x;
-  load_T9(g, m, tay, S.T9, S.ex9);
-  for (int r = tid; r < SR; r += ST)
+  __shared__ SmallShared sh;
+  const int m = blockIdx.x, lane = threadIdx.x;
+  load_elem9(g, m, tay, tayf, sh.E);
+  for (int r = lane; r < SR; r += ST)
 #pragma unroll
     for (int w = 0; w < SW; w++) {
-      S.comp[r][w] = 0ull;
-      S.eval[r][w] = 0ull;
+      sh.comp[r][w] = 0ull;
+      sh.eval[r][w] = 0ull;
     }
-  __syncthreads();
-  const double us = dmul(dsub(S.T9[4][TY_X], g.x_lo), g.inv_dx);
-  const double ws = dmul(dsub(S.T9[4][TY_V], g.v_lo), g.inv_dv);
-  if (!(us > -1e9 && us < 1e9 && ws > -1e9 && ws < 1e9)) return;
-  const long long i0 = (long long)floor(dadd(us, 0.5)), j0 = (long long)floor(dadd(ws, 0.5));
+  __syncwarp();
+  long long i0, j0;
+  if (!start_site(g, sh.E, i0, j0)) return;
+  set_offsets(sh.E, i0, j0);
+  __syncwarp();
+  const Ctx9 c = ctx_of(g, sh.E, alo, ahi);
   const int pad = g.pad;
-  if (i0 < -pad || i0 >= g.nx + pad || j0 < -pad || j0 >= g.nv + pad) return;
   const long long r0 = i0 - SR / 2, c0 = j0 - COLS / 2;
   const int clo = (int)max(0ll, (long long)(-pad) - c0);
   const int chi = (int)min((long long)COLS, (long long)(g.nv + pad) - c0);
   const int rlo = (int)max(0ll, (long long)(-pad) - r0);
   const int rhi = (int)min((long long)SR, (long long)(g.nx + pad) - r0);
-  if (tid == 0) {
-    double d2;
-    const bool ok = pass_test(g, S.T9, S.ex9, site_x(g, i0), site_v(g, j0), d2);
-    S.eval[SR / 2][(COLS / 2) >> 6] |= 1ull << ((COLS / 2) & 63);
+  bool ok = false;
+  if (lane == 0) {
+    ok = test_site(g, sh.E, c, i0, j0, i0, j0);
+    sh.eval[SR / 2][(COLS / 2) >> 6] |= 1ull << ((COLS / 2) & 63);
     if (ok) {
-      S.comp[SR / 2][(COLS / 2) >> 6] |= 1ull << ((COLS / 2) & 63);
-      claim_site(g, keys, i0, j0, d2, m);
+      sh.comp[SR / 2][(COLS / 2) >> 6] |= 1ull << ((COLS / 2) & 63);
+      claim(S, g, i0, j0, m);
     }
-    S.ok = ok;
   }
-  __syncthreads();
-  if (!S.ok) return;
-  unsigned long long front[RPT][SW];
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __syncwarp();
+  if (!ok) return;
   for (int it = 0; it < SR * COLS; it++) {
-    bool anyf = false;
+    unsigned long long front[RPT][SW];
+    int cnt = 0;
 #pragma unroll
     for (int q = 0; q < RPT; q++) {
-      const int r = tid + q * ST;
+      const int r = lane + q * ST;
 #pragma unroll
       for (int w = 0; w < SW; w++) {
-        const unsigned long long c = S.comp[r][w];
-        unsigned long long d = c | (c << 1) | (c >> 1);
-        if (w > 0) d |= S.comp[r][w - 1] >> 63;
-        if (w < SW - 1) d |= S.comp[r][w + 1] << 63;
-        if (r > 0) d |= S.comp[r - 1][w];
-        if (r < SR - 1) d |= S.comp[r + 1][w];
+        const unsigned long long cw = sh.comp[r][w];
+        unsigned long long d = cw | (cw << 1) | (cw >> 1);
+        if (w > 0) d |= sh.comp[r][w - 1] >> 63;
+        if (w < SW - 1) d |= sh.comp[r][w + 1] << 63;
+        if (r > 0) d |= sh.comp[r - 1][w];
+        if (r < SR - 1) d |= sh.comp[r + 1][w];
         const unsigned long long valid = (r >= rlo && r < rhi) ? col_mask(w, clo, chi) : 0ull;
-        front[q][w] = d & ~S.eval[r][w] & valid;
-        anyf |= front[q][w] != 0ull;
+        front[q][w] = d & ~sh.eval[r][w] & valid;
+        cnt += __popcll(front[q][w]);
       }
     }
-    if (!__syncthreads_or(anyf)) break;
+    // exclusive scan of the counts: each lane's items go to [base, base + cnt)
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) break;
+    int base = incl - cnt;
 #pragma unroll
     for (int q = 0; q < RPT; q++) {
-      const int r = tid + q * ST;
-      const long long i = r0 + r;
+      const int r = lane + q * ST;
 #pragma unroll
       for (int w = 0; w < SW; w++) {
         unsigned long long fr = front[q][w];
-        if (!fr) continue;
-        S.eval[r][w] |= fr;
-        unsigned long long add = 0ull;
         while (fr) {
           const int b = __ffsll((long long)fr) - 1;
           fr &= fr - 1ull;
-          const long long j = c0 + 64 * w + b;
-          double d2;
-          if (pass_test(g, S.T9, S.ex9, site_x(g, i), site_v(g, j), d2)) {
-            add |= 1ull << b;
-            claim_site(g, keys, i, j, d2, m);
-          }
+          if (base < SCAP) sh.item[base] = (unsigned short)((r << 7) | (w << 6) | b);
+          base++;
         }
-        S.comp[r][w] |= add;
       }
     }
-    __syncthreads();
+    __syncwarp();
+    const int nitems = min(total, SCAP);
+    for (int e = lane; e < nitems; e += ST) {
+      const int code = sh.item[e];
+      const int r = code >> 7, w = (code >> 6) & 1, b = code & 63;
+      const long long i = r0 + r, j = c0 + 64 * w + b;
+      const unsigned long long bit = 1ull << b;
+      atomicOr(&sh.eval[r][w], bit);
+      if (test_site(g, sh.E, c, i0, j0, i, j)) {
+        atomicOr(&sh.comp[r][w], bit);
+        claim(S, g, i, j, m);
+      }
+    }
+    __syncwarp();
   }
   // Escaped the window?  Record on which sides, to pick the next window.
   bool esc_rows = false, esc_cols = false;
 #pragma unroll
   for (int q = 0; q < RPT; q++) {
-    const int r = tid + q * ST;
+    const int r = lane + q * ST;
     unsigned long long rowany = 0ull;
 #pragma unroll
-    for (int w = 0; w < SW; w++) rowany |= S.comp[r][w];
+    for (int w = 0; w < SW; w++) rowany |= sh.comp[r][w];
     if (!rowany) continue;
     if (r == 0 && rlo == 0 && r0 - 1 >= -pad) esc_rows = true;
     if (r == SR - 1 && rhi == SR && r0 + SR < g.nx + pad) esc_rows = true;
-    if ((S.comp[r][0] & 1ull) && clo == 0 && c0 - 1 >= -pad) esc_cols = true;
-    if ((S.comp[r][SW - 1] >> 63) && chi == COLS && c0 + COLS < g.nv + pad) esc_cols = true;
+    if ((sh.comp[r][0] & 1ull) && clo == 0 && c0 - 1 >= -pad) esc_cols = true;
+    if ((sh.comp[r][SW - 1] >> 63) && chi == COLS && c0 + COLS < g.nv + pad) esc_cols = true;
   }
-  const bool er = __syncthreads_or(esc_rows), ec = __syncthreads_or(esc_cols);
-  if ((er || ec) && tid == 0) {
+  const bool er = __any_sync(0xffffffffu, esc_rows), ec = __any_sync(0xffffffffu, esc_cols);
+  if ((er || ec) && lane == 0) {
     const int sides = (er ? 1 : 0) | (ec ? 2 : 0);
-    const int slot = atomicAdd(&ds->noverflow, 1);
-    ovf_list[slot] = make_int2(m, sides << 4);   // attempt 0
+    ovf_list[atomicAdd(&S.ds->noverflow, 1)] = make_int2(m, sides << 4);  // attempt 0
   }
 }
 
 // ---------------------------------------------------------------------------
-// tiers 2 and 3: cooperative block, word-granular evaluation
+// tier 2: larger windows, cooperative block, word-granular tests
 // ---------------------------------------------------------------------------
 
 constexpr int BT = 256;       // threads
@@ -263,6 +399,12 @@ constexpr int BAND_R = 128;   // band window: rows across the band
 constexpr int FAT_R = 256, FAT_W = 4;
 constexpr int LIST_CAP = 1024;
 constexpr size_t SMEM_MAX = 227 * 1024;
+
+struct BigHeader {
+  Elem9 E;
+  int nlist, ok;
+  int list[LIST_CAP];
+};
 
 // Order of the window modes tried for an element, by the sides its
 // component escaped tier 1 from (1: rows, 2: columns, 3: both).
@@ -274,12 +416,13 @@ __device__ __forceinline__ int mode_for(int sides, int attempt) {
   return seq[sides & 3][attempt];
 }
 
-struct BigHeader {
-  double T9[9][TY_N];
-  int ex9[9];
-  int ok, nlist, active, esc;
-  int list[LIST_CAP];
-};
+// 64-bit words along a band window for a lattice side n: the whole padded
+// side if it fits in shared memory, else as many as fit.
+__host__ __device__ __forceinline__ int band_words(long long n, int pad) {
+  const long long full = (n + 2 * pad + 63) / 64;
+  const long long fit = (long long)((SMEM_MAX - sizeof(BigHeader)) / (3 * 8 * BAND_R));
+  return (int)(full < fit ? full : fit);
+}
 
 // Window geometry: "rows" run across, "words" along the bit axis.  For
 // MODE_BAND_X the bit axis is x (transposed window), otherwise v.
@@ -301,16 +444,19 @@ __device__ __forceinline__ void site_of(const Win& W, int r, int c, long long& i
   }
 }
 
-// 64-bit words along a band window for a lattice side n: the whole padded
-// side if it fits in shared memory, else as many as fit.
-__host__ __device__ __forceinline__ int band_words(long long n, int pad) {
-  const long long full = (n + 2 * pad + 63) / 64;
-  const long long fit = (long long)((SMEM_MAX - sizeof(BigHeader)) / (3 * 8 * BAND_R));
-  return (int)(full < fit ? full : fit);
+__device__ __forceinline__ unsigned long long dilate(const unsigned long long* comp, const Win& W, int q) {
+  const int r = q / W.W, w = q - r * W.W;
+  const unsigned long long c = comp[q];
+  unsigned long long d = c | (c << 1) | (c >> 1);
+  if (w > 0) d |= comp[q - 1] >> 63;
+  if (w < W.W - 1) d |= comp[q + 1] << 63;
+  if (r > 0) d |= comp[q - W.W];
+  if (r < W.R - 1) d |= comp[q + W.W];
+  return d;
 }
 
 __global__ void __launch_bounds__(BT) k_claim_big(Grid g, const double* __restrict__ tay,
-                                                  unsigned long long* __restrict__ keys, DevState* ds,
+                                                  const float* __restrict__ tayf, Slots S, float alo, float ahi,
                                                   const int2* __restrict__ list_in, const int* __restrict__ n_in,
                                                   int* __restrict__ stat, int2* __restrict__ list_out,
                                                   int* __restrict__ n_out) {
@@ -324,11 +470,11 @@ __global__ void __launch_bounds__(BT) k_claim_big(Grid g, const double* __restri
     const int m = list_in[item].x;
     const int sides = list_in[item].y >> 4, attempt = list_in[item].y & 15;
     const int mode = mode_for(sides, attempt);
-    load_T9(g, m, tay, H.T9, H.ex9);
+    load_elem9(g, m, tay, tayf, H.E);
     __syncthreads();
-    const double us = dmul(dsub(H.T9[4][TY_X], g.x_lo), g.inv_dx);
-    const double ws = dmul(dsub(H.T9[4][TY_V], g.v_lo), g.inv_dv);
-    const long long i0 = (long long)floor(dadd(us, 0.5)), j0 = (long long)floor(dadd(ws, 0.5));
+    long long i0 = 0, j0 = 0;
+    start_site(g, H.E, i0, j0);  // inside the padded lattice: tier 1 checked it
+    set_offsets(H.E, i0, j0);
     Win W;
     W.trans = (mode == MODE_BAND_X);
     const long long along0 = W.trans ? i0 : j0, across0 = W.trans ? j0 : i0;
@@ -360,44 +506,31 @@ __global__ void __launch_bounds__(BT) k_claim_big(Grid g, const double* __restri
     unsigned long long* eval = bits + NW;
     unsigned long long* pass = bits + 2 * NW;
     for (int q = tid; q < 3 * NW; q += BT) bits[q] = 0ull;
-    if (tid == 0) {
-      H.ok = 0;
-      H.esc = 0;
-    }
     __syncthreads();
+    const Ctx9 c = ctx_of(g, H.E, alo, ahi);
     const int rs = (int)(across0 - W.r0), cs = (int)(along0 - W.c0);
     if (tid == 0) {
-      double d2;
-      const bool ok = pass_test(g, H.T9, H.ex9, site_x(g, i0), site_v(g, j0), d2);
+      const bool ok = test_site(g, H.E, c, i0, j0, i0, j0);
       const int q = rs * W.W + (cs >> 6);
       eval[q] |= 1ull << (cs & 63);
       if (ok) {
         pass[q] |= 1ull << (cs & 63);
         comp[q] |= 1ull << (cs & 63);
-        claim_site(g, keys, i0, j0, d2, m);
+        claim(S, g, i0, j0, m);
       }
       H.ok = ok;
     }
     __syncthreads();
     if (H.ok) {
       for (int it = 0; it < NW * 64; it++) {
-        if (tid == 0) {
-          H.nlist = 0;
-          H.active = 0;
-        }
+        if (tid == 0) H.nlist = 0;
         __syncthreads();
-        // A: growth candidates of every word; words needing evaluation are listed
+        // A: growth candidates; words needing tests are listed
         bool act = false;
         for (int q = tid; q < NW; q += BT) {
           const int r = q / W.W, w = q - r * W.W;
-          const unsigned long long c = comp[q];
-          unsigned long long d = c | (c << 1) | (c >> 1);
-          if (w > 0) d |= comp[q - 1] >> 63;
-          if (w < W.W - 1) d |= comp[q + 1] << 63;
-          if (r > 0) d |= comp[q - W.W];
-          if (r < W.R - 1) d |= comp[q + W.W];
           const unsigned long long valid = (r >= W.rlo && r < W.rhi) ? col_mask(w, W.clo, W.chi) : 0ull;
-          const unsigned long long gr = d & ~c & valid;
+          const unsigned long long gr = dilate(comp, W, q) & ~comp[q] & valid;
           if (gr & ~eval[q]) {
             act = true;
             const int slot = atomicAdd(&H.nlist, 1);
@@ -407,7 +540,7 @@ __global__ void __launch_bounds__(BT) k_claim_big(Grid g, const double* __restri
           }
         }
         if (!__syncthreads_or(act)) break;
-        // C: evaluate every still-unevaluated valid site of the listed words
+        // B: test every still-untested valid site of the listed words
         const int nl = min(H.nlist, LIST_CAP);
         for (int e = tid; e < nl * 64; e += BT) {
           const int q = H.list[e >> 6], b = e & 63;
@@ -416,9 +549,7 @@ __global__ void __launch_bounds__(BT) k_claim_big(Grid g, const double* __restri
           if (!(((valid & ~eval[q]) >> b) & 1ull)) continue;
           long long i, j;
           site_of(W, r, 64 * w + b, i, j);
-          double d2;
-          if (pass_test(g, H.T9, H.ex9, site_x(g, i), site_v(g, j), d2))
-            atomicOr(&pass[q], 1ull << b);
+          if (test_site(g, H.E, c, i0, j0, i, j)) atomicOr(&pass[q], 1ull << b);
         }
         __syncthreads();
         for (int e = tid; e < nl; e += BT) {
@@ -427,32 +558,23 @@ __global__ void __launch_bounds__(BT) k_claim_big(Grid g, const double* __restri
           eval[q] |= (r >= W.rlo && r < W.rhi) ? col_mask(w, W.clo, W.chi) : 0ull;
         }
         __syncthreads();
-        // D: extend the component through passing runs inside each word.  A
+        // C: extend the component through passing runs inside each word.  A
         // word may see its neighbours' growth of this same phase; that only
         // adds connected passing sites earlier, so the fixed point is the same.
         for (int q = tid; q < NW; q += BT) {
-          const int r = q / W.W, w = q - r * W.W;
-          const unsigned long long c = comp[q];
-          unsigned long long d = c | (c << 1) | (c >> 1);
-          if (w > 0) d |= comp[q - 1] >> 63;
-          if (w < W.W - 1) d |= comp[q + 1] << 63;
-          if (r > 0) d |= comp[q - W.W];
-          if (r < W.R - 1) d |= comp[q + W.W];
-          const unsigned long long seeds = d & ~c & pass[q];
+          const unsigned long long cw = comp[q];
+          const unsigned long long seeds = dilate(comp, W, q) & ~cw & pass[q];
           if (!seeds) continue;
-          const unsigned long long nw = run_fill(seeds | c, pass[q]);
-          unsigned long long add = nw & ~c;
-          comp[q] = c | nw;
+          const unsigned long long nw = run_fill(seeds | cw, pass[q]);
+          unsigned long long add = nw & ~cw;
+          comp[q] = cw | nw;
+          const int r = q / W.W, w = q - r * W.W;
           while (add) {
             const int b = __ffsll((long long)add) - 1;
             add &= add - 1ull;
             long long i, j;
             site_of(W, r, 64 * w + b, i, j);
-            if (i >= 0 && i < g.nx && j >= 0 && j < g.nv) {
-              double xi, ze;
-              const double d2 = dist2_exact(H.T9[4], g, site_x(g, i), site_v(g, j), xi, ze);
-              claim_site(g, keys, i, j, d2, m);
-            }
+            claim(S, g, i, j, m);
           }
         }
         __syncthreads();
@@ -460,21 +582,19 @@ __global__ void __launch_bounds__(BT) k_claim_big(Grid g, const double* __restri
       // escaped this window as well?
       bool esc = false;
       for (int q = tid; q < NW; q += BT) {
-        const unsigned long long c = comp[q];
-        if (!c) continue;
+        const unsigned long long cw = comp[q];
+        if (!cw) continue;
         const int r = q / W.W, w = q - r * W.W;
         if (r == 0 && W.rlo == 0 && W.r0 - 1 >= -pad) esc = true;
         if (r == W.R - 1 && W.rhi == W.R && W.r0 + W.R < W.nrow_lat + pad) esc = true;
-        if (w == 0 && (c & 1ull) && W.clo == 0 && W.c0 - 1 >= -pad) esc = true;
-        if (w == W.W - 1 && (c >> 63) && W.chi == COLS && W.c0 + COLS < W.ncol_lat + pad) esc = true;
+        if (w == 0 && (cw & 1ull) && W.clo == 0 && W.c0 - 1 >= -pad) esc = true;
+        if (w == W.W - 1 && (cw >> 63) && W.chi == COLS && W.c0 + COLS < W.ncol_lat + pad) esc = true;
       }
       if (__syncthreads_or(esc) && tid == 0) {
-        if (list_out != nullptr) {
-          const int slot = atomicAdd(n_out, 1);
-          list_out[slot] = make_int2(m, (sides << 4) | (attempt + 1));
-        } else {
-          atomicOr(&ds->err, ERR_PATCH_OVERFLOW);
-        }
+        if (list_out != nullptr)
+          list_out[atomicAdd(n_out, 1)] = make_int2(m, (sides << 4) | (attempt + 1));
+        else
+          atomicOr(&S.ds->err, ERR_PATCH_OVERFLOW);
       }
     }
     __syncthreads();
@@ -482,23 +602,50 @@ __global__ void __launch_bounds__(BT) k_claim_big(Grid g, const double* __restri
   if (blockIdx.x == 0 && tid == 0) *stat = n;
 }
 
-// Keys -> map; reset keys for the next map; list the unclaimed sites.
-__global__ void k_finalize(Grid g, unsigned long long* __restrict__ keys, int32_t* __restrict__ map,
-                           int32_t* __restrict__ holes, DevState* ds) {
-  const size_t n = (size_t)g.nx * g.nv;
-  const ulonglong2 empty = make_ulonglong2(KEY_EMPTY, KEY_EMPTY);
-  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
-    const ulonglong2 kv = reinterpret_cast<ulonglong2*>(keys)[p];
-    int32_t m = -1;
-    if (kv.y == KEY_EMPTY && kv.x == KEY_EMPTY) {
-      const int slot = atomicAdd(&ds->nholes, 1);
-      holes[slot] = (int32_t)p;
-    } else {
-      m = (int32_t)kv.x;
-      reinterpret_cast<ulonglong2*>(keys)[p] = empty;
-    }
-    map[p] = m;
+// ---------------------------------------------------------------------------
+// conflicts, extra claimants, holes
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned long long exact_key(const Grid& g, const double* __restrict__ tay, int m,
+                                                        double Px, double Pv) {
+  double xi, ze;
+  return dkey(dist2_exact(tay + (size_t)m * TY_N, g, Px, Pv, xi, ze));
+}
+
+// Two claimants: keep the one with the smaller (d^2, index).
+__global__ void k_resolve(Grid g, const double* __restrict__ tay, Slots S) {
+  const int n = S.ds->nconflict;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    const int p = S.conflicts[idx];
+    const int i = p / g.nv, j = p - i * g.nv;
+    const double Px = site_x(g, i), Pv = site_v(g, j);
+    const int m0 = (int)(S.slot0[p] & SLOT_MASK), m1 = (int)(S.slot1[p] & SLOT_MASK);
+    const unsigned long long k0 = exact_key(g, tay, m0, Px, Pv), k1 = exact_key(g, tay, m1, Px, Pv);
+    const int win = (k1 < k0 || (k1 == k0 && m1 < m0)) ? m1 : m0;
+    S.slot0[p] = (S.epoch << 24) | (uint32_t)win;
+    S.slot1[p] = SLOT_EMPTY;
   }
+}
+
+// Third and further claimants, one after another (rare).
+__global__ void k_resolve_extras(Grid g, const double* __restrict__ tay, Slots S) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const int n = S.ds->nextra;
+  for (int idx = 0; idx < n; idx++) {
+    const int p = S.extras[idx].x, m = S.extras[idx].y;
+    const int i = p / g.nv, j = p - i * g.nv;
+    const double Px = site_x(g, i), Pv = site_v(g, j);
+    const int cur = (int)(S.slot0[p] & SLOT_MASK);
+    const unsigned long long kc = exact_key(g, tay, cur, Px, Pv), km = exact_key(g, tay, m, Px, Pv);
+    if (km < kc || (km == kc && m < cur)) S.slot0[p] = (S.epoch << 24) | (uint32_t)m;
+  }
+}
+
+__global__ void k_find_holes(Grid g, const uint32_t* __restrict__ slot0, uint32_t epoch, int32_t* __restrict__ holes,
+                             DevState* ds) {
+  const size_t n = (size_t)g.nx * g.nv;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
+    if ((slot0[p] >> 24) != epoch) holes[atomicAdd(&ds->nholes, 1)] = (int32_t)p;
 }
 
 constexpr int HT = 1024;
@@ -507,9 +654,9 @@ constexpr int HT = 1024;
 // hole takes, among the elements its in-grid 4-neighbours held at the end of
 // the previous round, the one with the smallest d at the hole, then the
 // smaller index.
-__global__ void __launch_bounds__(HT) k_holes(Grid g, const double* __restrict__ tay,
-                                              int32_t* __restrict__ map, int32_t* la, int32_t* lb,
-                                              int32_t* cho, DevState* ds) {
+__global__ void __launch_bounds__(HT) k_holes(Grid g, const double* __restrict__ tay, uint32_t* __restrict__ slot0,
+                                              uint32_t epoch, int32_t* la, int32_t* lb, int32_t* cho,
+                                              DevState* ds) {
   __shared__ int n_s, next_s;
   if (threadIdx.x == 0) {
     n_s = ds->nholes;
@@ -533,10 +680,10 @@ __global__ void __launch_bounds__(HT) k_holes(Grid g, const double* __restrict__
       for (int q = 0; q < 4; q++) {
         const int ii = i + di[q], jj = j + dj[q];
         if (ii < 0 || ii >= g.nx || jj < 0 || jj >= g.nv) continue;
-        const int cand = map[(size_t)ii * g.nv + jj];
-        if (cand < 0) continue;
-        double xi, ze;
-        const unsigned long long key = dkey(dist2_exact(tay + (size_t)cand * TY_N, g, Px, Pv, xi, ze));
+        const uint32_t t = slot0[(size_t)ii * g.nv + jj];
+        if ((t >> 24) != epoch) continue;
+        const int cand = (int)(t & SLOT_MASK);
+        const unsigned long long key = exact_key(g, tay, cand, Px, Pv);
         if (best < 0 || key < bestk || (key == bestk && cand < best)) {
           best = cand;
           bestk = key;
@@ -547,13 +694,11 @@ __global__ void __launch_bounds__(HT) k_holes(Grid g, const double* __restrict__
     if (threadIdx.x == 0) next_s = 0;
     __syncthreads();
     for (int idx = threadIdx.x; idx < n; idx += HT) {
-      const int c = cho[idx];
-      if (c >= 0) {
-        map[la[idx]] = c;
-      } else {
-        const int slot = atomicAdd(&next_s, 1);
-        lb[slot] = la[idx];
-      }
+      const int ch = cho[idx];
+      if (ch >= 0)
+        slot0[la[idx]] = (epoch << 24) | (uint32_t)ch;
+      else
+        lb[atomicAdd(&next_s, 1)] = la[idx];
     }
     __syncthreads();
     int32_t* t = la;
@@ -569,11 +714,25 @@ __global__ void __launch_bounds__(HT) k_holes(Grid g, const double* __restrict__
   }
 }
 
+__global__ void k_read_map(const uint32_t* __restrict__ slot0, uint32_t epoch, int32_t* __restrict__ out, size_t n) {
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t t = slot0[p];
+    out[p] = ((t >> 24) == epoch) ? (int32_t)(t & SLOT_MASK) : -1;
+  }
+}
+
 size_t big_smem_bytes(const Grid& g) {
   long long nw = FAT_R * FAT_W;
   nw = max(nw, (long long)BAND_R * band_words(g.nv, g.pad));
   nw = max(nw, (long long)BAND_R * band_words(g.nx, g.pad));
   return sizeof(BigHeader) + 3 * (size_t)nw * sizeof(unsigned long long);
+}
+
+// alpha rounded down and up to FP32
+void alpha_bounds(double alpha, float& lo, float& hi) {
+  const float f = (float)alpha;
+  lo = ((double)f <= alpha) ? f : nextafterf(f, -INFINITY);
+  hi = ((double)f >= alpha) ? f : nextafterf(f, INFINITY);
 }
 
 }  // namespace
@@ -586,33 +745,49 @@ bool map_prepare(const Grid& g) {
 }
 
 void launch_map(vm_solver* s) {
-  // counters: nholes, holes_found, hole_rounds, noverflow, overflow_stat, noverflow2,
-  // overflow2_stat, noverflow3, overflow3_stat
+  s->epoch = (s->epoch + 1) % kEpochs;
+  Slots S{s->map, s->slot1, s->extras, s->conflicts, s->ds, s->epoch};
+  float alo, ahi;
+  alpha_bounds(s->g.alpha, alo, ahi);
   int ps = prof_begin(s, KID_MAP_CLEAR);
-  cudaMemsetAsync(&s->ds->nholes, 0, 9 * sizeof(int32_t), s->stream);
+  cudaMemsetAsync(&s->ds->nholes, 0, kMapCounters * sizeof(int32_t), s->stream);
   prof_end(s, ps);
   ps = prof_begin(s, KID_CLAIM_SMALL);
-  k_claim_small<<<s->g.ne, ST, 0, s->stream>>>(s->g, s->tay, s->keys, s->ds, s->overflow_list);
+  k_claim_small<<<s->g.ne, ST, 0, s->stream>>>(s->g, s->tay, s->tayf, S, alo, ahi, s->overflow_list);
   prof_end(s, ps);
   const size_t smem = big_smem_bytes(s->g);
-  ps = prof_begin(s, KID_CLAIM_LARGE);
   DevState* d = s->ds;
-  k_claim_big<<<2 * 152, BT, smem, s->stream>>>(s->g, s->tay, s->keys, d, s->overflow_list, &d->noverflow,
-                                                &d->overflow_stat, s->overflow_list2, &d->noverflow2);
-  k_claim_big<<<152, BT, smem, s->stream>>>(s->g, s->tay, s->keys, d, s->overflow_list2, &d->noverflow2,
+  ps = prof_begin(s, KID_CLAIM_LARGE);
+  k_claim_big<<<2 * 152, BT, smem, s->stream>>>(s->g, s->tay, s->tayf, S, alo, ahi, s->overflow_list,
+                                                &d->noverflow, &d->overflow_stat, s->overflow_list2, &d->noverflow2);
+  k_claim_big<<<152, BT, smem, s->stream>>>(s->g, s->tay, s->tayf, S, alo, ahi, s->overflow_list2, &d->noverflow2,
                                             &d->overflow2_stat, s->overflow_list, &d->noverflow3);
-  k_claim_big<<<152, BT, smem, s->stream>>>(s->g, s->tay, s->keys, d, s->overflow_list, &d->noverflow3,
+  k_claim_big<<<152, BT, smem, s->stream>>>(s->g, s->tay, s->tayf, S, alo, ahi, s->overflow_list, &d->noverflow3,
                                             &d->overflow3_stat, nullptr, nullptr);
+  prof_end(s, ps);
+  ps = prof_begin(s, KID_RESOLVE);
+  k_resolve<<<152, 256, 0, s->stream>>>(s->g, s->tay, S);
+  k_resolve_extras<<<1, 32, 0, s->stream>>>(s->g, s->tay, S);
   prof_end(s, ps);
   unsigned nb = (unsigned)((s->n + 255) / 256);
   if (nb > 152 * 16) nb = 152 * 16;
   ps = prof_begin(s, KID_FINALIZE);
-  k_finalize<<<nb, 256, 0, s->stream>>>(s->g, s->keys, s->map, s->holes_a, s->ds);
+  k_find_holes<<<nb, 256, 0, s->stream>>>(s->g, s->map, s->epoch, s->holes_a, s->ds);
   prof_end(s, ps);
   ps = prof_begin(s, KID_HOLES);
-  k_holes<<<1, HT, 0, s->stream>>>(s->g, s->tay, s->map, s->holes_a, s->holes_b, s->holes_b + s->n, s->ds);
+  k_holes<<<1, HT, 0, s->stream>>>(s->g, s->tay, s->map, s->epoch, s->holes_a, s->holes_b, s->holes_b + s->n,
+                                    s->ds);
   prof_end(s, ps);
-  s->launches += 6;
+  s->launches += 9;
+}
+
+void launch_read_map(vm_solver* s, int32_t* dst) {
+  unsigned nb = (unsigned)((s->n + 255) / 256);
+  if (nb > 152 * 16) nb = 152 * 16;
+  const int ps = prof_begin(s, KID_READ_MAP);
+  k_read_map<<<nb, 256, 0, s->stream>>>(s->map, s->epoch, dst, s->n);
+  prof_end(s, ps);
+  s->launches++;
 }
 
 }  // namespace vm

@@ -6,10 +6,15 @@
 // Q_r blended over the beta set of elements with the Monaghan kernel, then
 // the cubic B-spline of f_ini at Q_r.
 //
-// Q, the interpolation node choice and the weights' arguments are FP64 in
-// both precisions, evaluated in a fixed operation order; only the storage
-// of f_ini / eta / f and the final interpolation sums follow the stored
-// precision R.
+// FP64 path: Q, the node choice and the interpolation in FP64, evaluated in
+// a fixed operation order.  FP32-mixed path: Q from the element's FP32
+// record in element units, anchored on the exact lattice position of Q_m, so
+// that only the small offset carries FP32 rounding; the integer decisions
+// (nearest node, containing square, beta ranges) are taken from the FP32
+// value only when it clears a rigorous bound on its distance to the FP64
+// value, and otherwise from the FP64 evaluation, so they are the FP64 path's.
+#include <math.h>
+
 #include "common.cuh"
 
 namespace vm {
@@ -37,19 +42,6 @@ __device__ __forceinline__ double qinterp(const double* __restrict__ F, const Gr
   return dadd(f, dmul(dmul(cross, dqx), dqv));
 }
 
-// FP32 storage: nodes and weights as above (FP64), sums in float.
-__device__ __forceinline__ double qinterp(const float* __restrict__ F, const Grid& g, double u, double w) {
-  if (!(u > -2.0 && u < (double)g.nx + 1.0 && w > -2.0 && w < (double)g.nv + 1.0)) return 0.0;
-  const long long in = (long long)floor(dadd(u, 0.5)), jn = (long long)floor(dadd(w, 0.5));
-  const long long ic = (long long)floor(u), jc = (long long)floor(w);
-  const float x = (float)dsub(u, (double)in), y = (float)dsub(w, (double)jn);
-  float f = F_at(F, g, in, jn) * (1.0f - x * x - y * y);
-  f += 0.5f * x * (F_at(F, g, in + 1, jn) * (1.0f + x) + F_at(F, g, in - 1, jn) * (x - 1.0f));
-  f += 0.5f * y * (F_at(F, g, in, jn + 1) * (1.0f + y) + F_at(F, g, in, jn - 1) * (y - 1.0f));
-  f += (F_at(F, g, ic + 1, jc + 1) + F_at(F, g, ic, jc) - F_at(F, g, ic + 1, jc) - F_at(F, g, ic, jc + 1)) * x * y;
-  return (double)f;
-}
-
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -63,17 +55,22 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 // Transport reconstruction of one x row per block, fused with M(i).
-template <typename R>
-__global__ void __launch_bounds__(256) k_recon(Grid g, const int32_t* __restrict__ map,
-                                               const double* __restrict__ tay, const R* __restrict__ fini,
-                                               R* __restrict__ f, double* __restrict__ M) {
+__device__ __forceinline__ int owner(const uint32_t* __restrict__ map, size_t p, uint32_t epoch) {
+  const uint32_t t = map[p];
+  return ((t >> 24) == epoch) ? (int)(t & SLOT_MASK) : -1;
+}
+
+__global__ void __launch_bounds__(256) k_recon64(Grid g, const uint32_t* __restrict__ map, uint32_t epoch,
+                                                 const double* __restrict__ tay, const double* __restrict__ fini,
+                                                 double* __restrict__ f, double* __restrict__ M) {
+  using R = double;
   __shared__ double sh[32];
   const int i = blockIdx.x;
   const double Px = site_x(g, i);
   double acc = 0.0;
   for (int j = threadIdx.x; j < g.nv; j += blockDim.x) {
     const size_t p = (size_t)i * g.nv + j;
-    const int m = map[p];
+    const int m = owner(map, p, epoch);
     double val = 0.0;
     if (m >= 0) {
       const double* t = tay + (size_t)m * TY_N;
@@ -187,15 +184,15 @@ __device__ __forceinline__ double spline_eval(const R* __restrict__ eta, const G
   return (double)sum;
 }
 
-template <typename R>
-__global__ void __launch_bounds__(256) k_remap(Grid g, const int32_t* __restrict__ map,
-                                               const double* __restrict__ tay, const R* __restrict__ eta,
-                                               R* __restrict__ out) {
+__global__ void __launch_bounds__(256) k_remap64(Grid g, const uint32_t* __restrict__ map, uint32_t epoch,
+                                                 const double* __restrict__ tay, const double* __restrict__ eta,
+                                                 double* __restrict__ out) {
+  using R = double;
   const int i = blockIdx.x;
   const double Px = site_x(g, i);
   for (int j = threadIdx.x; j < g.nv; j += blockDim.x) {
     const size_t p = (size_t)i * g.nv + j;
-    const int m = map[p];
+    const int m = owner(map, p, epoch);
     double val = 0.0;
     if (m >= 0) {
       double Qx, Qv;
@@ -205,6 +202,257 @@ __global__ void __launch_bounds__(256) k_remap(Grid g, const int32_t* __restrict
       val = spline_eval(eta, g, u, w);
     }
     out[p] = (R)val;
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// FP32-mixed path
+// ---------------------------------------------------------------------------
+
+constexpr float kRelQ = 2.0e-6f, kAbs = 1.0e-9f;
+
+struct QF {
+  float qx, qv, ex, ev;  // offset in element units and its bounds
+};
+
+__device__ __forceinline__ QF qeval(const float* __restrict__ F, float px, float pv) {
+  QF r;
+  const float yx = F[TF_T00] * px + F[TF_T01] * pv;
+  const float yv = F[TF_T10] * px + F[TF_T11] * pv;
+  const float sx = px * (F[TF_GX00] * px + F[TF_GX01] * pv) + pv * (F[TF_GX01] * px + F[TF_GX11] * pv);
+  const float sv = px * (F[TF_GV00] * px + F[TF_GV01] * pv) + pv * (F[TF_GV01] * px + F[TF_GV11] * pv);
+  r.qx = yx - 0.5f * (F[TF_K00] * sx + F[TF_K01] * sv);
+  r.qv = yv - 0.5f * (F[TF_K10] * sx + F[TF_K11] * sv);
+  const float P = fmaxf(fabsf(px), fabsf(pv));
+  const float ax = F[TF_C1X] * P + F[TF_C2X] * (P * P);
+  const float av = F[TF_C1V] * P + F[TF_C2V] * (P * P);
+  r.ex = kRelQ * ax + kAbs * (1.f + ax);
+  r.ev = kRelQ * av + kAbs * (1.f + av);
+  return r;
+}
+
+// p = (P - P_m)/Delta_m of site (i, j) for the element with record F.
+__device__ __forceinline__ void p_of(const float* __restrict__ F, int i, int j, float inv_s, float& px, float& pv) {
+  const int* Fi = reinterpret_cast<const int*>(F);
+  px = ((float)(i - Fi[TF_UI]) - F[TF_UF]) * inv_s;
+  pv = ((float)(j - Fi[TF_WI]) - F[TF_WF]) * inv_s;
+}
+
+// The lattice index position of Q_m (a multiple of 1/2): integer part and
+// half flag, exactly.
+__device__ __forceinline__ void anchor(const Grid& g, int m, int& Bu, float& bu, int& Bw, float& bw) {
+  const int k = m / g.Lv, l = m - k * g.Lv;
+  const int u2 = (g.nx - 1) + 2 * (k - g.Kx - 1) * g.s;  // 2 * index of Q_m,x
+  const int w2 = (g.nv - 1) + 2 * (l - g.Kv - 1) * g.s;
+  Bu = u2 >> 1;  // floor
+  bu = (u2 & 1) ? 0.5f : 0.f;
+  Bw = w2 >> 1;
+  bw = (w2 & 1) ? 0.5f : 0.f;
+}
+
+// Is floor(x) certain for every value within e of x?
+__device__ __forceinline__ bool floor_sure(float x, float e) {
+  const float f = floorf(x);
+  return (x - e > f) && (x + e < f + 1.f);
+}
+
+__device__ __forceinline__ float F_at32(const float* __restrict__ F, const Grid& g, int i, int j) {
+  if (i < 0 || j < 0 || i >= g.nx || j >= g.nv) return 0.f;
+  return __ldg(F + (size_t)i * g.nv + j);
+}
+
+// Six-point quadratic interpolation from the node choice and the offsets.
+__device__ __forceinline__ float qinterp32(const float* __restrict__ F, const Grid& g, int in, int jn, int ic, int jc,
+                                           float x, float y) {
+  float f = F_at32(F, g, in, jn) * (1.0f - x * x - y * y);
+  f += 0.5f * x * (F_at32(F, g, in + 1, jn) * (1.0f + x) + F_at32(F, g, in - 1, jn) * (x - 1.0f));
+  f += 0.5f * y * (F_at32(F, g, in, jn + 1) * (1.0f + y) + F_at32(F, g, in, jn - 1) * (y - 1.0f));
+  f += (F_at32(F, g, ic + 1, jc + 1) + F_at32(F, g, ic, jc) - F_at32(F, g, ic + 1, jc) - F_at32(F, g, ic, jc + 1)) *
+       x * y;
+  return f;
+}
+
+__global__ void __launch_bounds__(256) k_recon32(Grid g, const uint32_t* __restrict__ map, uint32_t epoch,
+                                                 const double* __restrict__ tay, const float* __restrict__ tayf,
+                                                 const float* __restrict__ fini, float* __restrict__ f,
+                                                 double* __restrict__ M) {
+  __shared__ double sh[32];
+  const int i = blockIdx.x;
+  const float inv_s = 1.0f / (float)g.s, fs = (float)g.s;
+  double acc = 0.0;
+  for (int j = threadIdx.x; j < g.nv; j += blockDim.x) {
+    const size_t p = (size_t)i * g.nv + j;
+    const int m = owner(map, p, epoch);
+    float val = 0.f;
+    if (m >= 0) {
+      const float* F = tayf + (size_t)m * TF_N;
+      float px, pv;
+      p_of(F, i, j, inv_s, px, pv);
+      const QF q = qeval(F, px, pv);
+      int Bu, Bw;
+      float bu, bw;
+      anchor(g, m, Bu, bu, Bw, bw);
+      // index coordinates of Q relative to the anchor
+      const float ru = bu + fs * q.qx, rw = bw + fs * q.qv;
+      const float eu = fs * q.ex + 1e-6f * (1.f + fabsf(ru)), ew = fs * q.ev + 1e-6f * (1.f + fabsf(rw));
+      int in, jn, ic, jc;
+      float x, y;
+      if (!(fabsf(ru) < 1e7f && fabsf(rw) < 1e7f)) {
+        // far outside the grid (or not a number): no node of the stencil exists
+        in = jn = ic = jc = -1000000;
+        x = y = 0.f;
+      } else if (floor_sure(ru + 0.5f, eu) && floor_sure(ru, eu) && floor_sure(rw + 0.5f, ew) && floor_sure(rw, ew)) {
+        const float nu = floorf(ru + 0.5f), nw = floorf(rw + 0.5f);
+        in = Bu + (int)nu;
+        jn = Bw + (int)nw;
+        ic = Bu + (int)floorf(ru);
+        jc = Bw + (int)floorf(rw);
+        x = ru - nu;
+        y = rw - nw;
+      } else {
+        // FP64 evaluation, as the FP64 path takes these decisions
+        const double* t = tay + (size_t)m * TY_N;
+        double dqx, dqv;
+        qofp_exact(t, site_x(g, i), site_v(g, j), dqx, dqv);
+        const double u = dmul(dsub(dadd(t[TY_QX], dqx), g.x_lo), g.inv_dx);
+        const double w = dmul(dsub(dadd(t[TY_QV], dqv), g.v_lo), g.inv_dv);
+        if (!(u > -2.0 && u < (double)g.nx + 1.0 && w > -2.0 && w < (double)g.nv + 1.0)) {
+          in = jn = ic = jc = -1000000;
+          x = y = 0.f;
+        } else {
+          in = (int)floor(dadd(u, 0.5));
+          jn = (int)floor(dadd(w, 0.5));
+          ic = (int)floor(u);
+          jc = (int)floor(w);
+          x = (float)dsub(u, (double)in);
+          y = (float)dsub(w, (double)jn);
+        }
+      }
+      if (in > -2 && in < g.nx + 2 && jn > -2 && jn < g.nv + 2) val = qinterp32(fini, g, in, jn, ic, jc, x, y);
+    }
+    f[p] = val;
+    acc += (double)val;
+  }
+  const double rowsum = block_sum(acc, sh);
+  if (threadIdx.x == 0) M[i] = dmul(rowsum, g.dxdv);
+}
+
+__device__ __forceinline__ float W4f(float x) {
+  if (x <= 1.f) return 1.f - 1.5f * x * x + 0.75f * x * x * x;
+  if (x <= 2.f) {
+    const float r = 2.f - x;
+    return 0.25f * r * r * r;
+  }
+  return 0.f;
+}
+
+// beta range of one axis, 1: {-1,0}, 2: {-1,0,1}, 3: {0,1}, 0: cannot tell.
+__device__ __forceinline__ int beta_range_f(float q, float e, float blo, float bhi) {
+  if (q + e < -bhi) return 1;
+  if (q - e >= -blo && q + e < blo) return 2;
+  if (q - e >= bhi) return 3;
+  return 0;
+}
+
+// Cubic B-spline at index coordinates (B + r) along each axis.
+__device__ __forceinline__ float spline32(const float* __restrict__ eta, const Grid& g, int Bu, float ru, int Bw,
+                                          float rw) {
+  if (!(fabsf(ru) < 1e7f && fabsf(rw) < 1e7f)) return 0.f;
+  const float fu = floorf(ru), fw = floorf(rw);
+  const long long ku = (long long)Bu + (long long)fu, kw = (long long)Bw + (long long)fw;
+  if (ku < -4 || ku > g.nx + 2 || kw < -4 || kw > g.nv + 2) return 0.f;
+  const float tu = ru - fu, tw = rw - fw;
+  float bu4[4], bw4[4];
+  float s_ = 1.f - tu;
+  bu4[0] = s_ * s_ * s_ * (1.f / 6.f);
+  bu4[1] = (2.f / 3.f) - tu * tu + 0.5f * tu * tu * tu;
+  bu4[2] = (2.f / 3.f) - s_ * s_ + 0.5f * s_ * s_ * s_;
+  bu4[3] = tu * tu * tu * (1.f / 6.f);
+  s_ = 1.f - tw;
+  bw4[0] = s_ * s_ * s_ * (1.f / 6.f);
+  bw4[1] = (2.f / 3.f) - tw * tw + 0.5f * tw * tw * tw;
+  bw4[2] = (2.f / 3.f) - s_ * s_ + 0.5f * s_ * s_ * s_;
+  bw4[3] = tw * tw * tw * (1.f / 6.f);
+  float sum = 0.f;
+#pragma unroll
+  for (int a = 0; a < 4; a++) {
+    const long long gk = ghost(ku - 1 + a, g.nx);
+    if (gk < 0) continue;
+    float row = 0.f;
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+      const long long gl = ghost(kw - 1 + b, g.nv);
+      if (gl < 0) continue;
+      row += __ldg(eta + gk * g.nv + gl) * bw4[b];
+    }
+    sum += row * bu4[a];
+  }
+  return sum;
+}
+
+__global__ void __launch_bounds__(256) k_remap32(Grid g, const uint32_t* __restrict__ map, uint32_t epoch,
+                                                 const double* __restrict__ tay, const float* __restrict__ tayf,
+                                                 const float* __restrict__ eta, float* __restrict__ out, float blo,
+                                                 float bhi) {
+  const int i = blockIdx.x;
+  const float inv_s = 1.0f / (float)g.s, fs = (float)g.s;
+  for (int j = threadIdx.x; j < g.nv; j += blockDim.x) {
+    const size_t p = (size_t)i * g.nv + j;
+    const int m = owner(map, p, epoch);
+    float val = 0.f;
+    if (m >= 0) {
+      const float* F = tayf + (size_t)m * TF_N;
+      float px, pv;
+      p_of(F, i, j, inv_s, px, pv);
+      const QF q = qeval(F, px, pv);
+      const int ra = beta_range_f(q.qx, q.ex, blo, bhi), rb = beta_range_f(q.qv, q.ev, blo, bhi);
+      int Bu, Bw;
+      float bu, bw;
+      anchor(g, m, Bu, bu, Bw, bw);
+      float ru, rw;
+      if (ra && rb) {
+        // Q_r - Q_m in element units, blended over the beta set (Sec. 2.3.2)
+        const int a0 = (ra == 3) ? 0 : -1, a1 = (ra == 1) ? 0 : 1;
+        const int b0 = (rb == 3) ? 0 : -1, b1 = (rb == 1) ? 0 : 1;
+        const bool full = (ra == 2) || (rb == 2);
+        const int k = m / g.Lv, l = m - k * g.Lv;
+        float nx_ = 0.f, nv_ = 0.f, den = 0.f;
+        for (int a = a0; a <= a1; a++)
+          for (int b = b0; b <= b1; b++) {
+            if (full && a != 0 && b != 0) continue;
+            const int kk = k + a, ll = l + b;
+            if (kk < 0 || kk >= g.Lx || ll < 0 || ll >= g.Lv) continue;
+            const float* Fn = tayf + (size_t)(kk * g.Lv + ll) * TF_N;
+            float pxn, pvn;
+            p_of(Fn, i, j, inv_s, pxn, pvn);
+            const QF qn = (a == 0 && b == 0) ? q : qeval(Fn, pxn, pvn);
+            const float wgt = W4f(2.f * sqrtf(qn.qx * qn.qx + qn.qv * qn.qv));
+            nx_ += wgt * ((float)a + qn.qx);
+            nv_ += wgt * ((float)b + qn.qv);
+            den += wgt;
+          }
+        const float dx_ = (den > 0.f) ? nx_ / den : q.qx;
+        const float dv_ = (den > 0.f) ? nv_ / den : q.qv;
+        ru = bu + fs * dx_;
+        rw = bw + fs * dv_;
+      } else {
+        double Qx, Qv;
+        blended_q(g, tay, m, site_x(g, i), site_v(g, j), Qx, Qv);
+        const double u = dmul(dsub(Qx, g.x_lo), g.inv_dx), w = dmul(dsub(Qv, g.v_lo), g.inv_dv);
+        if (!(u > -3.0 && u < (double)(g.nx + 2) && w > -3.0 && w < (double)(g.nv + 2))) {
+          out[p] = 0.f;
+          continue;
+        }
+        const double fu = floor(u), fw = floor(w);
+        Bu = (int)fu;
+        Bw = (int)fw;
+        ru = (float)(u - fu);
+        rw = (float)(w - fw);
+      }
+      val = spline32(eta, g, Bu, ru, Bw, rw);
+    }
+    out[p] = val;
   }
 }
 
@@ -225,11 +473,11 @@ void launch_reconstruct(vm_solver* s) {
   const int nt = s->g.nv >= 256 ? 256 : ((s->g.nv + 31) / 32) * 32;
   const int ps_ = prof_begin(s, KID_RECON);
   if (s->fp32)
-    k_recon<float><<<s->g.nx, nt, 0, s->stream>>>(s->g, s->map, s->tay, (const float*)s->fini,
-                                                   (float*)s->f, s->M);
+    k_recon32<<<s->g.nx, nt, 0, s->stream>>>(s->g, s->map, s->epoch, s->tay, s->tayf, (const float*)s->fini,
+                                              (float*)s->f, s->M);
   else
-    k_recon<double><<<s->g.nx, nt, 0, s->stream>>>(s->g, s->map, s->tay, (const double*)s->fini,
-                                                    (double*)s->f, s->M);
+    k_recon64<<<s->g.nx, nt, 0, s->stream>>>(s->g, s->map, s->epoch, s->tay, (const double*)s->fini,
+                                              (double*)s->f, s->M);
   prof_end(s, ps_);
   s->launches++;
 }
@@ -237,10 +485,16 @@ void launch_reconstruct(vm_solver* s) {
 void launch_remap_resample(vm_solver* s, void* out) {
   const int nt = s->g.nv >= 256 ? 256 : ((s->g.nv + 31) / 32) * 32;
   const int ps_ = prof_begin(s, KID_REMAP);
-  if (s->fp32)
-    k_remap<float><<<s->g.nx, nt, 0, s->stream>>>(s->g, s->map, s->tay, (const float*)s->eta, (float*)out);
-  else
-    k_remap<double><<<s->g.nx, nt, 0, s->stream>>>(s->g, s->map, s->tay, (const double*)s->eta, (double*)out);
+  if (s->fp32) {
+    const float fb = (float)s->g.beta;
+    const float blo = ((double)fb <= s->g.beta) ? fb : nextafterf(fb, -INFINITY);
+    const float bhi = ((double)fb >= s->g.beta) ? fb : nextafterf(fb, INFINITY);
+    k_remap32<<<s->g.nx, nt, 0, s->stream>>>(s->g, s->map, s->epoch, s->tay, s->tayf, (const float*)s->eta,
+                                              (float*)out, blo, bhi);
+  } else {
+    k_remap64<<<s->g.nx, nt, 0, s->stream>>>(s->g, s->map, s->epoch, s->tay, (const double*)s->eta,
+                                              (double*)out);
+  }
   prof_end(s, ps_);
   s->launches++;
 }
