@@ -16,7 +16,7 @@ constexpr double kPi = 3.14159265358979323846;
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t fini, eta, f, tmp, map, slot1, extras, conflicts, holes_a, holes_b, ovf, el, tay, tayf, M, a, da, d2a,
+  size_t fini, eta, f, tmp, map, slot1, rec_key, rec_site, holes_a, holes_b, ovf, el, tay, tayf, M, a, da, d2a,
       thx, thv, thxf, thvf, ds, total;
 };
 
@@ -61,8 +61,8 @@ Layout layout(const vm_config* c) {
   L.tmp = take(n * sr);
   L.map = take(n * 4);
   L.slot1 = take(n * 4);
-  L.extras = take(n * 8);
-  L.conflicts = take(n * 4);
+  L.rec_key = take(n * 16);  // at most one record per site (plus rare lost races)
+  L.rec_site = take(n * 4);
   L.holes_a = take(n * 4);
   L.holes_b = take(2 * n * 4);
   L.ovf = take(2 * ne * 8);
@@ -99,6 +99,7 @@ void thomas(int n, std::vector<double>& out) {
 }
 
 size_t ne_total(const vm_solver* s) { return (size_t)s->g.ne; }
+using vm::SLOT_MASK;
 
 vm_status check_launch(vm_solver* s) {
   (void)s;
@@ -266,8 +267,10 @@ vm_status vm_create(const vm_config* c, void* d_workspace, size_t bytes, void* s
   s->tmp = base + L.tmp;
   s->map = (uint32_t*)(base + L.map);
   s->slot1 = (uint32_t*)(base + L.slot1);
-  s->extras = (int2*)(base + L.extras);
-  s->conflicts = (int32_t*)(base + L.conflicts);
+  s->rec_key = (unsigned long long*)(base + L.rec_key);
+  s->rec_site = (int32_t*)(base + L.rec_site);
+  // record indices travel in the 24-bit field of the second slot
+  s->rec_cap = (int32_t)(s->n < (size_t)SLOT_MASK ? s->n : (size_t)SLOT_MASK);
   s->holes_a = (int32_t*)(base + L.holes_a);
   s->holes_b = (int32_t*)(base + L.holes_b);
   s->overflow_list = (int2*)(base + L.ovf);

@@ -11,7 +11,7 @@ namespace vm {
 // Device error word bits.
 enum : int32_t {
   ERR_NOT_CONVERGED = 1,
-  ERR_PATCH_OVERFLOW = 2,
+  ERR_PATCH_OVERFLOW = 2,  // an element outgrew every window, or the contested-site records ran out
 };
 
 // Grid, lattice and method constants, passed by value to every kernel.  All
@@ -40,18 +40,19 @@ struct DevState {
   int32_t overflow2_stat;
   int32_t noverflow3;    // ... third attempt
   int32_t overflow3_stat;
-  int32_t nconflict;     // sites claimed by two or more elements
-  int32_t nextra;        // claims beyond the second one on a site
+  int32_t nrec;          // records of sites claimed by two or more elements
+  int32_t pad_;
   double Mtot;           // total mass of the last reconstruction
   double sum_mass, sum_kin, sum_pot;
   unsigned long long det_min_key, det_max_key;
 };
-constexpr int kMapCounters = 11;  // int32 fields from nholes to nextra
+constexpr int kMapCounters = 11;  // int32 fields from nholes to nrec
 
 // Owner slots of the influence map: (epoch << 24) | element index.  A slot
 // whose epoch is not the current map's is empty; every site is rewritten
 // each map (claimed or repaired), so stale values are never more than one
-// map old, and the second slot is cleared when its conflict is resolved.
+// map old.  The second slot of a contested site holds (epoch << 24) | index
+// of its record and is cleared when the record is resolved.
 constexpr uint32_t SLOT_EMPTY = 0xFFFFFFFFu;
 constexpr uint32_t SLOT_MASK = 0x00FFFFFFu;
 constexpr int kEpochs = 255;  // epochs 0..254; 255 never current
@@ -98,9 +99,10 @@ struct vm_solver {
   void* f;
   void* tmp;
   uint32_t* map;            // owner slot 0: the influence map (epoch-tagged)
-  uint32_t* slot1;          // owner slot 1 (second claimant of a site)
-  int2* extras;             // (site, element) of further claimants
-  int32_t* conflicts;       // sites with two or more claimants
+  uint32_t* slot1;          // record index of a contested site
+  unsigned long long* rec_key;  // per record: {element index, bits of d^2}, 128-bit minimum
+  int32_t* rec_site;        // per record: its site (-1: unused)
+  int32_t rec_cap;
   int32_t* holes_a;
   int32_t* holes_b;         // also the 8 B/site staging buffer of the copy calls
   int2* overflow_list;      // (element, window mode) for the second tier

@@ -29,11 +29,13 @@
 // The outcome is therefore identical to the all-FP64 evaluation.
 //
 // Claims.  A claimed site's owner slot takes (epoch << 24 | m) with one
-// atomic exchange; a displaced current-epoch owner moves to the second
-// slot (the site is then listed as a conflict) or to the extras list.
-// Conflicts are resolved afterwards by the exact FP64 key (bits of d^2,
-// element index), smallest first.  Unclaimed sites are repaired in Jacobi
-// rounds from their 4-neighbours.
+// atomic exchange.  A claim that displaces a current-epoch owner makes sure
+// the site has a record (a 128-bit key, published through the second slot)
+// and folds into it, by a 128-bit compare-and-swap minimum, the exact FP64
+// keys (bits of d^2, element index) of the displaced owner and of itself:
+// every claimant of a contested site reaches the record, so its minimum is
+// the exact winner, and FP64 work is spent only on contested sites.
+// Unclaimed sites are repaired in Jacobi rounds from their 4-neighbours.
 #include <math.h>
 
 #include "common.cuh"
@@ -154,27 +156,84 @@ __device__ __forceinline__ int pass_f32(const Ctx9& c, float di, float dj) {
 // claims
 // ---------------------------------------------------------------------------
 
+// 128-bit compare-and-swap on global memory (sm_90 and later).
+__device__ __forceinline__ ulonglong2 cas128(unsigned long long* addr, ulonglong2 cmp, ulonglong2 val) {
+  ulonglong2 old;
+  asm volatile(
+      "{\n\t"
+      ".reg .b128 c, v, r;\n\t"
+      "mov.b128 c, {%2, %3};\n\t"
+      "mov.b128 v, {%4, %5};\n\t"
+      "atom.global.cas.b128 r, [%6], c, v;\n\t"
+      "mov.b128 {%0, %1}, r;\n\t"
+      "}"
+      : "=l"(old.x), "=l"(old.y)
+      : "l"(cmp.x), "l"(cmp.y), "l"(val.x), "l"(val.y), "l"(addr)
+      : "memory");
+  return old;
+}
+
+// key2[0] = element index, key2[1] = bits of d^2: as a 128-bit integer its
+// order is the claim order (smaller d, then smaller index).
+__device__ __forceinline__ void key_min(unsigned long long* key2, unsigned long long dbits, unsigned long long idx) {
+  ulonglong2 cur = __ldcg(reinterpret_cast<const ulonglong2*>(key2));
+  const ulonglong2 val = make_ulonglong2(idx, dbits);
+  while (dbits < cur.y || (dbits == cur.y && idx < cur.x)) {
+    const ulonglong2 prev = cas128(key2, cur, val);
+    if (prev.x == cur.x && prev.y == cur.y) break;
+    cur = prev;
+  }
+}
+
 struct Slots {
   uint32_t* slot0;
   uint32_t* slot1;
-  int2* extras;
-  int32_t* conflicts;
+  unsigned long long* rec_key;
+  int32_t* rec_site;
+  int rec_cap;
+  const double* tay;
   DevState* ds;
   uint32_t epoch;
 };
 
+__device__ __noinline__ void contest(const Slots& S, const Grid& g, long long i, long long j, size_t p, int m,
+                                     uint32_t displaced) {
+  const uint32_t E = S.epoch;
+  uint32_t rs = __ldcg(&S.slot1[p]);
+  if ((rs >> 24) != E) {
+    // create the site's record; publish it only once initialised
+    const int r = atomicAdd(&S.ds->nrec, 1);
+    if (r >= S.rec_cap) {
+      atomicOr(&S.ds->err, ERR_PATCH_OVERFLOW);
+      return;
+    }
+    S.rec_key[2 * (size_t)r] = KEY_EMPTY;
+    S.rec_key[2 * (size_t)r + 1] = KEY_EMPTY;
+    S.rec_site[r] = (int32_t)p;
+    __threadfence();
+    const uint32_t mine = (E << 24) | (uint32_t)r;
+    const uint32_t prev = atomicCAS(&S.slot1[p], rs, mine);
+    if (prev == rs) {
+      rs = mine;
+    } else {
+      S.rec_site[r] = -1;  // another claim published first: use its record
+      rs = prev;
+    }
+  }
+  unsigned long long* key = S.rec_key + 2 * (size_t)(rs & SLOT_MASK);
+  const double Px = site_x(g, i), Pv = site_v(g, j);
+  double xi, ze;
+  const int mo = (int)(displaced & SLOT_MASK);
+  key_min(key, dkey(dist2_exact(S.tay + (size_t)mo * TY_N, g, Px, Pv, xi, ze)), (unsigned long long)mo);
+  key_min(key, dkey(dist2_exact(S.tay + (size_t)m * TY_N, g, Px, Pv, xi, ze)), (unsigned long long)m);
+}
+
 __device__ __forceinline__ void claim(const Slots& S, const Grid& g, long long i, long long j, int m) {
   if (i < 0 || i >= g.nx || j < 0 || j >= g.nv) return;
   const size_t p = (size_t)i * g.nv + j;
-  const uint32_t tag = (S.epoch << 24) | (uint32_t)m;
-  const uint32_t old = atomicExch(&S.slot0[p], tag);
-  if ((old >> 24) != S.epoch) return;                // first claimant this map
-  const uint32_t old1 = atomicExch(&S.slot1[p], old);  // keep the displaced one
-  if ((old1 >> 24) != S.epoch) {
-    S.conflicts[atomicAdd(&S.ds->nconflict, 1)] = (int32_t)p;
-    return;
-  }
-  S.extras[atomicAdd(&S.ds->nextra, 1)] = make_int2((int)p, (int)(old1 & SLOT_MASK));
+  const uint32_t old = atomicExch(&S.slot0[p], (S.epoch << 24) | (uint32_t)m);
+  if ((old >> 24) != S.epoch) return;  // first claimant this map
+  contest(S, g, i, j, p, m, old);
 }
 
 // Mask of window columns [lo, hi) within word w (64 columns per word).
@@ -413,7 +472,7 @@ __device__ __forceinline__ int mode_for(int sides, int attempt) {
                          {MODE_BAND_X, MODE_FAT, MODE_BAND_V},
                          {MODE_BAND_V, MODE_FAT, MODE_BAND_X},
                          {MODE_BAND_V, MODE_BAND_X, MODE_FAT}};
-  return seq[sides & 3][attempt];
+  return seq[sides & 3][attempt < 0 ? 0 : (attempt > 2 ? 2 : attempt)];
 }
 
 // 64-bit words along a band window for a lattice side n: the whole padded
@@ -468,6 +527,7 @@ __global__ void __launch_bounds__(BT) k_claim_big(Grid g, const double* __restri
   const int n = *n_in;
   for (int item = blockIdx.x; item < n; item += gridDim.x) {
     const int m = list_in[item].x;
+    if (m < 0 || m >= g.ne) continue;  // (never expected; keeps every index in bounds)
     const int sides = list_in[item].y >> 4, attempt = list_in[item].y & 15;
     const int mode = mode_for(sides, attempt);
     load_elem9(g, m, tay, tayf, H.E);
@@ -612,32 +672,15 @@ __device__ __forceinline__ unsigned long long exact_key(const Grid& g, const dou
   return dkey(dist2_exact(tay + (size_t)m * TY_N, g, Px, Pv, xi, ze));
 }
 
-// Two claimants: keep the one with the smaller (d^2, index).
-__global__ void k_resolve(Grid g, const double* __restrict__ tay, Slots S) {
-  const int n = S.ds->nconflict;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-    const int p = S.conflicts[idx];
-    const int i = p / g.nv, j = p - i * g.nv;
-    const double Px = site_x(g, i), Pv = site_v(g, j);
-    const int m0 = (int)(S.slot0[p] & SLOT_MASK), m1 = (int)(S.slot1[p] & SLOT_MASK);
-    const unsigned long long k0 = exact_key(g, tay, m0, Px, Pv), k1 = exact_key(g, tay, m1, Px, Pv);
-    const int win = (k1 < k0 || (k1 == k0 && m1 < m0)) ? m1 : m0;
+// Contested sites: the record's minimum is the owner.
+__global__ void k_resolve(Grid g, Slots S) {
+  const int n = min(S.ds->nrec, S.rec_cap);
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const int p = S.rec_site[r];
+    if (p < 0) continue;
+    const unsigned long long win = S.rec_key[2 * (size_t)r];
     S.slot0[p] = (S.epoch << 24) | (uint32_t)win;
     S.slot1[p] = SLOT_EMPTY;
-  }
-}
-
-// Third and further claimants, one after another (rare).
-__global__ void k_resolve_extras(Grid g, const double* __restrict__ tay, Slots S) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  const int n = S.ds->nextra;
-  for (int idx = 0; idx < n; idx++) {
-    const int p = S.extras[idx].x, m = S.extras[idx].y;
-    const int i = p / g.nv, j = p - i * g.nv;
-    const double Px = site_x(g, i), Pv = site_v(g, j);
-    const int cur = (int)(S.slot0[p] & SLOT_MASK);
-    const unsigned long long kc = exact_key(g, tay, cur, Px, Pv), km = exact_key(g, tay, m, Px, Pv);
-    if (km < kc || (km == kc && m < cur)) S.slot0[p] = (S.epoch << 24) | (uint32_t)m;
   }
 }
 
@@ -681,7 +724,7 @@ __global__ void __launch_bounds__(HT) k_holes(Grid g, const double* __restrict__
         const int ii = i + di[q], jj = j + dj[q];
         if (ii < 0 || ii >= g.nx || jj < 0 || jj >= g.nv) continue;
         const uint32_t t = slot0[(size_t)ii * g.nv + jj];
-        if ((t >> 24) != epoch) continue;
+        if ((t >> 24) != epoch || (int)(t & SLOT_MASK) >= g.ne) continue;
         const int cand = (int)(t & SLOT_MASK);
         const unsigned long long key = exact_key(g, tay, cand, Px, Pv);
         if (best < 0 || key < bestk || (key == bestk && cand < best)) {
@@ -746,7 +789,7 @@ bool map_prepare(const Grid& g) {
 
 void launch_map(vm_solver* s) {
   s->epoch = (s->epoch + 1) % kEpochs;
-  Slots S{s->map, s->slot1, s->extras, s->conflicts, s->ds, s->epoch};
+  Slots S{s->map, s->slot1, s->rec_key, s->rec_site, s->rec_cap, s->tay, s->ds, s->epoch};
   float alo, ahi;
   alpha_bounds(s->g.alpha, alo, ahi);
   int ps = prof_begin(s, KID_MAP_CLEAR);
@@ -766,8 +809,7 @@ void launch_map(vm_solver* s) {
                                             &d->overflow3_stat, nullptr, nullptr);
   prof_end(s, ps);
   ps = prof_begin(s, KID_RESOLVE);
-  k_resolve<<<152, 256, 0, s->stream>>>(s->g, s->tay, S);
-  k_resolve_extras<<<1, 32, 0, s->stream>>>(s->g, s->tay, S);
+  k_resolve<<<152, 256, 0, s->stream>>>(s->g, S);
   prof_end(s, ps);
   unsigned nb = (unsigned)((s->n + 255) / 256);
   if (nb > 152 * 16) nb = 152 * 16;
@@ -778,7 +820,7 @@ void launch_map(vm_solver* s) {
   k_holes<<<1, HT, 0, s->stream>>>(s->g, s->tay, s->map, s->epoch, s->holes_a, s->holes_b, s->holes_b + s->n,
                                     s->ds);
   prof_end(s, ps);
-  s->launches += 9;
+  s->launches += 8;
 }
 
 void launch_read_map(vm_solver* s, int32_t* dst) {

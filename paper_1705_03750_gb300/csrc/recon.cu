@@ -55,9 +55,10 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 // Transport reconstruction of one x row per block, fused with M(i).
-__device__ __forceinline__ int owner(const uint32_t* __restrict__ map, size_t p, uint32_t epoch) {
+__device__ __forceinline__ int owner(const uint32_t* __restrict__ map, size_t p, uint32_t epoch, int ne) {
   const uint32_t t = map[p];
-  return ((t >> 24) == epoch) ? (int)(t & SLOT_MASK) : -1;
+  const int m = (int)(t & SLOT_MASK);
+  return ((t >> 24) == epoch && m < ne) ? m : -1;
 }
 
 __global__ void __launch_bounds__(256) k_recon64(Grid g, const uint32_t* __restrict__ map, uint32_t epoch,
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(256) k_recon64(Grid g, const uint32_t* __restr
   double acc = 0.0;
   for (int j = threadIdx.x; j < g.nv; j += blockDim.x) {
     const size_t p = (size_t)i * g.nv + j;
-    const int m = owner(map, p, epoch);
+    const int m = owner(map, p, epoch, g.ne);
     double val = 0.0;
     if (m >= 0) {
       const double* t = tay + (size_t)m * TY_N;
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(256) k_remap64(Grid g, const uint32_t* __restr
   const double Px = site_x(g, i);
   for (int j = threadIdx.x; j < g.nv; j += blockDim.x) {
     const size_t p = (size_t)i * g.nv + j;
-    const int m = owner(map, p, epoch);
+    const int m = owner(map, p, epoch, g.ne);
     double val = 0.0;
     if (m >= 0) {
       double Qx, Qv;
@@ -283,7 +284,7 @@ __global__ void __launch_bounds__(256) k_recon32(Grid g, const uint32_t* __restr
   double acc = 0.0;
   for (int j = threadIdx.x; j < g.nv; j += blockDim.x) {
     const size_t p = (size_t)i * g.nv + j;
-    const int m = owner(map, p, epoch);
+    const int m = owner(map, p, epoch, g.ne);
     float val = 0.f;
     if (m >= 0) {
       const float* F = tayf + (size_t)m * TF_N;
@@ -399,7 +400,7 @@ __global__ void __launch_bounds__(256) k_remap32(Grid g, const uint32_t* __restr
   const float inv_s = 1.0f / (float)g.s, fs = (float)g.s;
   for (int j = threadIdx.x; j < g.nv; j += blockDim.x) {
     const size_t p = (size_t)i * g.nv + j;
-    const int m = owner(map, p, epoch);
+    const int m = owner(map, p, epoch, g.ne);
     float val = 0.f;
     if (m >= 0) {
       const float* F = tayf + (size_t)m * TF_N;
