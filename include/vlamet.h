@@ -178,6 +178,26 @@ typedef struct {
 vm_status vm_profile(vm_solver* s, int32_t enable);
 int32_t vm_profile_read(vm_solver* s, vm_kernel_stat* out, int32_t max);
 
+/* ---- many independent solves (batching) ----
+ *
+ * A batch advances many solves together (Sec. 2.4 for each; the solves are
+ * independent problems).  vm_batch_create records one time step of every
+ * solve into a CUDA graph, spreading the solves over nstreams streams so
+ * that their kernels overlap on the device, plus a second graph for a step
+ * followed by a remap; vm_batch_step then launches one graph per step on
+ * cuda_stream.  The solvers stay owned by the caller and must outlive the
+ * batch; they must all have received vm_set_f, share n_s and their position
+ * in the remap cycle (VM_E_STATE otherwise), and must not be profiling.
+ * Creation synchronises each solver's stream; vm_batch_step orders itself
+ * after work queued on the solvers' streams and before later work on them.
+ * Results are read per solver with the single-solve calls. */
+typedef struct vm_batch vm_batch;
+vm_status vm_batch_create(vm_solver* const* solvers, int32_t n, int32_t nstreams, void* cuda_stream,
+                          vm_batch** out);
+vm_status vm_batch_step(vm_batch* b, int32_t nsteps);
+int64_t vm_batch_launches_per_step(const vm_batch* b, int32_t with_remap);
+void vm_batch_destroy(vm_batch* b);
+
 /* Pixel masses and force from a caller's f, allocating nothing.
  *
  * The paper has no counterpart to this call; it exists for callers that

@@ -106,15 +106,41 @@ vm_status check_launch(vm_solver* s) {
   return cudaPeekAtLastError() == cudaSuccess ? VM_OK : VM_E_CUDA;
 }
 
+}  // namespace
+
+namespace vm {
+
+// One transport step t -> t + dt (Sec. 2.4): predictor drift + Taylor terms
+// at t + dt/2, map, f(t + dt/2) and M(i), force, kick + corrector.  Only
+// enqueues work (safe inside a stream capture); host counters untouched.
+void step_transport(vm_solver* s) {
+  launch_drift(s, true);
+  launch_map(s);
+  launch_reconstruct(s);
+  launch_scan_force(s);
+  launch_kick_drift(s);
+}
+
+// Remap at the current elements (Secs. 2.2.2, 2.3.2); enqueue only.
+cudaError_t step_remap(vm_solver* s) {
+  launch_taylor(s);
+  launch_map(s);
+  launch_remap_resample(s, s->tmp);
+  // the resampled f becomes f_ini (a copy, not a pointer swap, so that a
+  // captured step keeps its buffers)
+  const cudaError_t e = cudaMemcpyAsync(s->fini, s->tmp, s->n * s->sreal, cudaMemcpyDeviceToDevice, s->stream);
+  if (e != cudaSuccess) return e;
+  launch_spline_solve(s, s->fini, s->eta);
+  launch_reset_elements(s);
+  return cudaSuccess;
+}
+
+}  // namespace vm
+
+namespace {
+
 vm_status remap_internal(vm_solver* s) {
-  vm::launch_taylor(s);
-  vm::launch_map(s);
-  vm::launch_remap_resample(s, s->tmp);
-  void* t = s->fini;
-  s->fini = s->tmp;
-  s->tmp = t;
-  vm::launch_spline_solve(s, s->fini, s->eta);
-  vm::launch_reset_elements(s);
+  if (vm::step_remap(s) != cudaSuccess) return VM_E_CUDA;
   s->cyc = 0;
   return check_launch(s);
 }
@@ -146,7 +172,7 @@ vm_status read_real(vm_solver* s, const void* src, void* out, int32_t dtype, int
 
 const char* const kKernelNames[vm::KID_N] = {
     "drift_taylor", "taylor", "kick_drift", "reset_elements", "scan_force", "diagnostics",
-    "map_clear", "claim_small", "claim_large", "find_holes", "holes", "resolve", "read_map",
+    "map_begin", "claim_small", "claim_large", "find_holes", "holes", "resolve", "read_map",
     "reconstruct", "remap_resample", "convert", "spline_rows", "spline_cols"};
 
 }  // namespace
@@ -425,11 +451,7 @@ vm_status vm_step(vm_solver* s, int32_t nsteps) {
   if (!s || nsteps < 0) return VM_E_INVALID_ARG;
   if (!s->have_f) return VM_E_STATE;
   for (int32_t it = 0; it < nsteps; it++) {
-    vm::launch_drift(s, true);   // predictor + Taylor terms at t + dt/2
-    vm::launch_map(s);
-    vm::launch_reconstruct(s);   // f(t + dt/2) and M(i)
-    vm::launch_scan_force(s);    // a, a', a''
-    vm::launch_kick_drift(s);    // kick + corrector
+    vm::step_transport(s);
     s->nstep++;
     s->cyc++;
     if (s->cyc >= s->cfg.n_s) {

@@ -41,12 +41,12 @@ struct DevState {
   int32_t noverflow3;    // ... third attempt
   int32_t overflow3_stat;
   int32_t nrec;          // records of sites claimed by two or more elements
-  int32_t pad_;
+  uint32_t epoch;        // epoch of the current influence map (0..kEpochs-1)
   double Mtot;           // total mass of the last reconstruction
   double sum_mass, sum_kin, sum_pot;
   unsigned long long det_min_key, det_max_key;
 };
-constexpr int kMapCounters = 11;  // int32 fields from nholes to nrec
+constexpr int kMapCounters = 10;  // int32 fields from nholes to nrec
 
 // Owner slots of the influence map: (epoch << 24) | element index.  A slot
 // whose epoch is not the current map's is empty; every site is rewritten
@@ -121,7 +121,6 @@ struct vm_solver {
   vm::DevState* ds;
   // host-side bookkeeping
   int32_t have_f;
-  uint32_t epoch;           // epoch of the current influence map
   int64_t nstep;
   int32_t cyc;
   int64_t launches;
@@ -141,6 +140,10 @@ namespace vm {
 int prof_begin(vm_solver* s, int kid);
 void prof_end(vm_solver* s, int slot);
 void prof_flush(vm_solver* s);
+
+// ---- one step, enqueue only (api.cu) ----
+void step_transport(vm_solver* s);
+cudaError_t step_remap(vm_solver* s);
 
 // ---- launchers (each in the translation unit of its kernels) ----
 // elements.cu

@@ -62,7 +62,7 @@ __device__ __forceinline__ void alpha_range(double r, double alpha, int& lo, int
 
 // Percolation test of site P for the centre element of a 3x3 block of FP64
 // Taylor records (index 4).
-__device__ bool pass_exact(const Grid& g, const double (*T9)[TY_N], const int* ex9, double Px, double Pv) {
+__device__ __noinline__ bool pass_exact(const Grid& g, const double (*T9)[TY_N], const int* ex9, double Px, double Pv) {
   double xi, ze;
   const double d2 = dist2_exact(T9[4], g, Px, Pv, xi, ze);
   int a0, a1, b0, b1;
@@ -193,8 +193,26 @@ struct Slots {
   int rec_cap;
   const double* tay;
   DevState* ds;
-  uint32_t epoch;
+  uint32_t epoch;  // filled in on the device from ds->epoch
 };
+
+// The map's epoch lives on the device (so that a captured step replays
+// correctly): every map kernel reads it once.
+__device__ __forceinline__ Slots with_epoch(Slots S) {
+  S.epoch = *(volatile uint32_t*)&S.ds->epoch;
+  return S;
+}
+
+// Start of a map: next epoch, counters cleared.
+__global__ void k_map_begin(DevState* ds) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    ds->epoch = (ds->epoch + 1) % kEpochs;
+    ds->nholes = ds->holes_found = ds->hole_rounds = 0;
+    ds->noverflow = ds->overflow_stat = ds->noverflow2 = ds->overflow2_stat = 0;
+    ds->noverflow3 = ds->overflow3_stat = 0;
+    ds->nrec = 0;
+  }
+}
 
 __device__ __noinline__ void contest(const Slots& S, const Grid& g, long long i, long long j, size_t p, int m,
                                      uint32_t displaced) {
@@ -231,8 +249,11 @@ __device__ __noinline__ void contest(const Slots& S, const Grid& g, long long i,
 __device__ __forceinline__ void claim(const Slots& S, const Grid& g, long long i, long long j, int m) {
   if (i < 0 || i >= g.nx || j < 0 || j >= g.nv) return;
   const size_t p = (size_t)i * g.nv + j;
-  const uint32_t old = atomicExch(&S.slot0[p], (S.epoch << 24) | (uint32_t)m);
-  if ((old >> 24) != S.epoch) return;  // first claimant this map
+  const uint32_t tag = (S.epoch << 24) | (uint32_t)m;
+  const uint32_t old = atomicExch(&S.slot0[p], tag);
+  // first claimant this map, or the same element again (a larger window
+  // redoing it): nothing to resolve
+  if ((old >> 24) != S.epoch || old == tag) return;
   contest(S, g, i, j, p, m, old);
 }
 
@@ -321,35 +342,64 @@ __device__ __forceinline__ bool test_site(const Grid& g, const Elem9& E, const C
 }
 
 // ---------------------------------------------------------------------------
-// tier 1: 64 x 128 window, one warp per element, compacted frontier
+// tier 1: 64 x 128 window, one warp per element, four elements per block
 // ---------------------------------------------------------------------------
 
-constexpr int SR = 64, SW = 2, ST = 32, SCAP = 256;
+constexpr int SR = 64, SW = 2, ST = 32, SCAP = 256, SE = 4;
 
 struct SmallShared {
   Elem9 E;
   unsigned long long comp[SR][SW];
   unsigned long long eval[SR][SW];
+  unsigned long long pass[SR][SW];
   unsigned short item[SCAP];
 };
 
-__global__ void __launch_bounds__(ST) k_claim_small(Grid g, const double* __restrict__ tay,
-                                                    const float* __restrict__ tayf, Slots S, float alo, float ahi,
-                                                    int2* __restrict__ ovf_list) {
+// One element per warp.  First every site within one element spacing of the
+// start is tested at once (the component's usual extent); the component then
+// grows through known passing sites (whole runs inside a word per round) and,
+// past the tested box, by testing the newly reached sites as a compacted list.
+__global__ void __launch_bounds__(ST * SE, 6) k_claim_small(Grid g, const double* __restrict__ tay,
+                                                         const float* __restrict__ tayf, Slots Sin, float alo,
+                                                         float ahi, int2* __restrict__ ovf_list) {
   constexpr int COLS = 64 * SW, RPT = SR / ST;
-  __shared__ SmallShared sh;
-  const int m = blockIdx.x, lane = threadIdx.x;
-  load_elem9(g, m, tay, tayf, sh.E);
+  __shared__ SmallShared shs[SE];
+  const Slots S = with_epoch(Sin);
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  const int m = blockIdx.x * SE + wq;
+  if (m >= g.ne) return;
+  SmallShared& sh = shs[wq];
+  // per-warp loads (the block's warps work independently)
+  {
+    const int k = m / g.Lv, l = m - k * g.Lv;
+    for (int idx = lane; idx < 9 * TY_N; idx += ST) {
+      const int q = idx / TY_N, c2 = idx - q * TY_N;
+      const int kk = k + q / 3 - 1, ll = l + q % 3 - 1;
+      const bool ex = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
+      sh.E.T9[q][c2] = ex ? tay[(size_t)(kk * g.Lv + ll) * TY_N + c2] : 0.0;
+      if (c2 == 0) sh.E.ex9[q] = ex;
+    }
+    for (int idx = lane; idx < 9 * TF_N; idx += ST) {
+      const int q = idx / TF_N, c2 = idx - q * TF_N;
+      const int kk = k + q / 3 - 1, ll = l + q % 3 - 1;
+      const bool ex = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
+      sh.E.F9[q][c2] = ex ? tayf[(size_t)(kk * g.Lv + ll) * TF_N + c2] : 0.f;
+    }
+  }
   for (int r = lane; r < SR; r += ST)
 #pragma unroll
     for (int w = 0; w < SW; w++) {
       sh.comp[r][w] = 0ull;
       sh.eval[r][w] = 0ull;
+      sh.pass[r][w] = 0ull;
     }
   __syncwarp();
   long long i0, j0;
   if (!start_site(g, sh.E, i0, j0)) return;
-  set_offsets(sh.E, i0, j0);
+  if (lane < 9) {
+    sh.E.offu[lane] = sh.E.ex9[lane] ? (float)((double)i0 - sh.E.T9[lane][TY_U]) : 0.f;
+    sh.E.offv[lane] = sh.E.ex9[lane] ? (float)((double)j0 - sh.E.T9[lane][TY_W]) : 0.f;
+  }
   __syncwarp();
   const Ctx9 c = ctx_of(g, sh.E, alo, ahi);
   const int pad = g.pad;
@@ -358,21 +408,32 @@ __global__ void __launch_bounds__(ST) k_claim_small(Grid g, const double* __rest
   const int chi = (int)min((long long)COLS, (long long)(g.nv + pad) - c0);
   const int rlo = (int)max(0ll, (long long)(-pad) - r0);
   const int rhi = (int)min((long long)SR, (long long)(g.nx + pad) - r0);
+  // the start site decides whether there is a component at all
   bool ok = false;
-  if (lane == 0) {
-    ok = test_site(g, sh.E, c, i0, j0, i0, j0);
-    sh.eval[SR / 2][(COLS / 2) >> 6] |= 1ull << ((COLS / 2) & 63);
-    if (ok) {
-      sh.comp[SR / 2][(COLS / 2) >> 6] |= 1ull << ((COLS / 2) & 63);
-      claim(S, g, i0, j0, m);
-    }
-  }
+  if (lane == 0) ok = test_site(g, sh.E, c, i0, j0, i0, j0);
   ok = __shfl_sync(0xffffffffu, ok, 0);
-  __syncwarp();
   if (!ok) return;
+  // speculative box: rows and columns within s of the start
+  const int B = min(g.s, 15);
+  const int bw = 2 * B + 1, nbox = bw * bw;
+  for (int e = lane; e < nbox; e += ST) {
+    const int r = SR / 2 - B + e / bw, cc = COLS / 2 - B + e % bw;
+    if (r < rlo || r >= rhi || cc < clo || cc >= chi) continue;
+    const int w = cc >> 6, b = cc & 63;
+    const unsigned long long bit = 1ull << b;
+    atomicOr(&sh.eval[r][w], bit);
+    if (test_site(g, sh.E, c, i0, j0, r0 + r, c0 + cc)) atomicOr(&sh.pass[r][w], bit);
+  }
+  __syncwarp();
+  if (lane == 0) {
+    sh.comp[SR / 2][(COLS / 2) >> 6] |= 1ull << ((COLS / 2) & 63);
+    claim(S, g, i0, j0, m);
+  }
+  __syncwarp();
   for (int it = 0; it < SR * COLS; it++) {
     unsigned long long front[RPT][SW];
     int cnt = 0;
+    bool grew = false;
 #pragma unroll
     for (int q = 0; q < RPT; q++) {
       const int r = lane + q * ST;
@@ -385,11 +446,40 @@ __global__ void __launch_bounds__(ST) k_claim_small(Grid g, const double* __rest
         if (r > 0) d |= sh.comp[r - 1][w];
         if (r < SR - 1) d |= sh.comp[r + 1][w];
         const unsigned long long valid = (r >= rlo && r < rhi) ? col_mask(w, clo, chi) : 0ull;
-        front[q][w] = d & ~sh.eval[r][w] & valid;
+        const unsigned long long gr = d & ~cw & valid;
+        front[q][w] = gr & ~sh.eval[r][w];  // reached, not tested yet
         cnt += __popcll(front[q][w]);
+        grew |= (gr & sh.pass[r][w]) != 0ull;  // reached, known to pass
       }
     }
-    // exclusive scan of the counts: each lane's items go to [base, base + cnt)
+    __syncwarp();
+    // known passing neighbours join now, with the passing runs they reach
+    // (a lane may already see another lane's growth of this phase; that only
+    // adds connected passing sites earlier)
+#pragma unroll
+    for (int q = 0; q < RPT; q++) {
+      const int r = lane + q * ST;
+#pragma unroll
+      for (int w = 0; w < SW; w++) {
+        const unsigned long long cw = sh.comp[r][w];
+        unsigned long long d = cw | (cw << 1) | (cw >> 1);
+        if (w > 0) d |= sh.comp[r][w - 1] >> 63;
+        if (w < SW - 1) d |= sh.comp[r][w + 1] << 63;
+        if (r > 0) d |= sh.comp[r - 1][w];
+        if (r < SR - 1) d |= sh.comp[r + 1][w];
+        const unsigned long long seeds = d & ~cw & sh.pass[r][w];
+        if (!seeds) continue;
+        const unsigned long long nw = run_fill(seeds | cw, sh.pass[r][w] | cw);
+        unsigned long long add = nw & ~cw;
+        atomicOr(&sh.comp[r][w], add);
+        while (add) {
+          const int b = __ffsll((long long)add) - 1;
+          add &= add - 1ull;
+          claim(S, g, r0 + r, c0 + 64 * w + b, m);
+        }
+      }
+    }
+    // exclusive scan of the untested counts: each lane's items go to [base, base + cnt)
     int incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -397,7 +487,8 @@ __global__ void __launch_bounds__(ST) k_claim_small(Grid g, const double* __rest
       if (lane >= o) incl += v;
     }
     const int total = __shfl_sync(0xffffffffu, incl, 31);
-    if (total == 0) break;
+    const bool any_grew = __any_sync(0xffffffffu, grew);
+    if (total == 0 && !any_grew) break;
     int base = incl - cnt;
 #pragma unroll
     for (int q = 0; q < RPT; q++) {
@@ -418,12 +509,11 @@ __global__ void __launch_bounds__(ST) k_claim_small(Grid g, const double* __rest
     for (int e = lane; e < nitems; e += ST) {
       const int code = sh.item[e];
       const int r = code >> 7, w = (code >> 6) & 1, b = code & 63;
-      const long long i = r0 + r, j = c0 + 64 * w + b;
       const unsigned long long bit = 1ull << b;
       atomicOr(&sh.eval[r][w], bit);
-      if (test_site(g, sh.E, c, i0, j0, i, j)) {
-        atomicOr(&sh.comp[r][w], bit);
-        claim(S, g, i, j, m);
+      if (test_site(g, sh.E, c, i0, j0, r0 + r, c0 + 64 * w + b)) {
+        atomicOr(&sh.pass[r][w], bit);
+        if (!(atomicOr(&sh.comp[r][w], bit) & bit)) claim(S, g, r0 + r, c0 + 64 * w + b, m);
       }
     }
     __syncwarp();
@@ -462,6 +552,7 @@ constexpr size_t SMEM_MAX = 227 * 1024;
 struct BigHeader {
   Elem9 E;
   int nlist, ok;
+  int rmin, rmax, wmin, wmax;  // rows / words holding component bits
   int list[LIST_CAP];
 };
 
@@ -515,10 +606,11 @@ __device__ __forceinline__ unsigned long long dilate(const unsigned long long* c
 }
 
 __global__ void __launch_bounds__(BT) k_claim_big(Grid g, const double* __restrict__ tay,
-                                                  const float* __restrict__ tayf, Slots S, float alo, float ahi,
+                                                  const float* __restrict__ tayf, Slots Sin, float alo, float ahi,
                                                   const int2* __restrict__ list_in, const int* __restrict__ n_in,
                                                   int* __restrict__ stat, int2* __restrict__ list_out,
                                                   int* __restrict__ n_out) {
+  const Slots S = with_epoch(Sin);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BigHeader& H = *reinterpret_cast<BigHeader*>(smem_raw);
   unsigned long long* bits = reinterpret_cast<unsigned long long*>(smem_raw + sizeof(BigHeader));
@@ -572,6 +664,8 @@ __global__ void __launch_bounds__(BT) k_claim_big(Grid g, const double* __restri
     if (tid == 0) {
       const bool ok = test_site(g, H.E, c, i0, j0, i0, j0);
       const int q = rs * W.W + (cs >> 6);
+      H.rmin = H.rmax = rs;
+      H.wmin = H.wmax = cs >> 6;
       eval[q] |= 1ull << (cs & 63);
       if (ok) {
         pass[q] |= 1ull << (cs & 63);
@@ -584,11 +678,15 @@ __global__ void __launch_bounds__(BT) k_claim_big(Grid g, const double* __restri
     if (H.ok) {
       for (int it = 0; it < NW * 64; it++) {
         if (tid == 0) H.nlist = 0;
+        // only the words within one word/row of the component can change
+        const int ra = max(H.rmin - 1, 0), rb = min(H.rmax + 1, W.R - 1);
+        const int wa = max(H.wmin - 1, 0), wb = min(H.wmax + 1, W.W - 1);
+        const int bw = wb - wa + 1, nbox = (rb - ra + 1) * bw;
         __syncthreads();
         // A: growth candidates; words needing tests are listed
         bool act = false;
-        for (int q = tid; q < NW; q += BT) {
-          const int r = q / W.W, w = q - r * W.W;
+        for (int e = tid; e < nbox; e += BT) {
+          const int r = ra + e / bw, w = wa + e % bw, q = r * W.W + w;
           const unsigned long long valid = (r >= W.rlo && r < W.rhi) ? col_mask(w, W.clo, W.chi) : 0ull;
           const unsigned long long gr = dilate(comp, W, q) & ~comp[q] & valid;
           if (gr & ~eval[q]) {
@@ -621,7 +719,8 @@ __global__ void __launch_bounds__(BT) k_claim_big(Grid g, const double* __restri
         // C: extend the component through passing runs inside each word.  A
         // word may see its neighbours' growth of this same phase; that only
         // adds connected passing sites earlier, so the fixed point is the same.
-        for (int q = tid; q < NW; q += BT) {
+        for (int e = tid; e < nbox; e += BT) {
+          const int q = (ra + e / bw) * W.W + wa + e % bw;
           const unsigned long long cw = comp[q];
           const unsigned long long seeds = dilate(comp, W, q) & ~cw & pass[q];
           if (!seeds) continue;
@@ -629,6 +728,10 @@ __global__ void __launch_bounds__(BT) k_claim_big(Grid g, const double* __restri
           unsigned long long add = nw & ~cw;
           comp[q] = cw | nw;
           const int r = q / W.W, w = q - r * W.W;
+          atomicMin(&H.rmin, r);
+          atomicMax(&H.rmax, r);
+          atomicMin(&H.wmin, w);
+          atomicMax(&H.wmax, w);
           while (add) {
             const int b = __ffsll((long long)add) - 1;
             add &= add - 1ull;
@@ -673,7 +776,8 @@ __device__ __forceinline__ unsigned long long exact_key(const Grid& g, const dou
 }
 
 // Contested sites: the record's minimum is the owner.
-__global__ void k_resolve(Grid g, Slots S) {
+__global__ void k_resolve(Grid g, Slots Sin) {
+  const Slots S = with_epoch(Sin);
   const int n = min(S.ds->nrec, S.rec_cap);
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     const int p = S.rec_site[r];
@@ -684,8 +788,8 @@ __global__ void k_resolve(Grid g, Slots S) {
   }
 }
 
-__global__ void k_find_holes(Grid g, const uint32_t* __restrict__ slot0, uint32_t epoch, int32_t* __restrict__ holes,
-                             DevState* ds) {
+__global__ void k_find_holes(Grid g, const uint32_t* __restrict__ slot0, int32_t* __restrict__ holes, DevState* ds) {
+  const uint32_t epoch = *(volatile uint32_t*)&ds->epoch;
   const size_t n = (size_t)g.nx * g.nv;
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
     if ((slot0[p] >> 24) != epoch) holes[atomicAdd(&ds->nholes, 1)] = (int32_t)p;
@@ -698,8 +802,8 @@ constexpr int HT = 1024;
 // the previous round, the one with the smallest d at the hole, then the
 // smaller index.
 __global__ void __launch_bounds__(HT) k_holes(Grid g, const double* __restrict__ tay, uint32_t* __restrict__ slot0,
-                                              uint32_t epoch, int32_t* la, int32_t* lb, int32_t* cho,
-                                              DevState* ds) {
+                                              int32_t* la, int32_t* lb, int32_t* cho, DevState* ds) {
+  const uint32_t epoch = *(volatile uint32_t*)&ds->epoch;
   __shared__ int n_s, next_s;
   if (threadIdx.x == 0) {
     n_s = ds->nholes;
@@ -757,7 +861,9 @@ __global__ void __launch_bounds__(HT) k_holes(Grid g, const double* __restrict__
   }
 }
 
-__global__ void k_read_map(const uint32_t* __restrict__ slot0, uint32_t epoch, int32_t* __restrict__ out, size_t n) {
+__global__ void k_read_map(const uint32_t* __restrict__ slot0, const DevState* ds, int32_t* __restrict__ out,
+                           size_t n) {
+  const uint32_t epoch = *(const volatile uint32_t*)&ds->epoch;
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
     const uint32_t t = slot0[p];
     out[p] = ((t >> 24) == epoch) ? (int32_t)(t & SLOT_MASK) : -1;
@@ -788,15 +894,15 @@ bool map_prepare(const Grid& g) {
 }
 
 void launch_map(vm_solver* s) {
-  s->epoch = (s->epoch + 1) % kEpochs;
-  Slots S{s->map, s->slot1, s->rec_key, s->rec_site, s->rec_cap, s->tay, s->ds, s->epoch};
+  Slots S{s->map, s->slot1, s->rec_key, s->rec_site, s->rec_cap, s->tay, s->ds, 0u};
   float alo, ahi;
   alpha_bounds(s->g.alpha, alo, ahi);
   int ps = prof_begin(s, KID_MAP_CLEAR);
-  cudaMemsetAsync(&s->ds->nholes, 0, kMapCounters * sizeof(int32_t), s->stream);
+  k_map_begin<<<1, 32, 0, s->stream>>>(s->ds);
   prof_end(s, ps);
   ps = prof_begin(s, KID_CLAIM_SMALL);
-  k_claim_small<<<s->g.ne, ST, 0, s->stream>>>(s->g, s->tay, s->tayf, S, alo, ahi, s->overflow_list);
+  k_claim_small<<<(s->g.ne + SE - 1) / SE, ST * SE, 0, s->stream>>>(s->g, s->tay, s->tayf, S, alo, ahi,
+                                                                    s->overflow_list);
   prof_end(s, ps);
   const size_t smem = big_smem_bytes(s->g);
   DevState* d = s->ds;
@@ -814,20 +920,19 @@ void launch_map(vm_solver* s) {
   unsigned nb = (unsigned)((s->n + 255) / 256);
   if (nb > 152 * 16) nb = 152 * 16;
   ps = prof_begin(s, KID_FINALIZE);
-  k_find_holes<<<nb, 256, 0, s->stream>>>(s->g, s->map, s->epoch, s->holes_a, s->ds);
+  k_find_holes<<<nb, 256, 0, s->stream>>>(s->g, s->map, s->holes_a, s->ds);
   prof_end(s, ps);
   ps = prof_begin(s, KID_HOLES);
-  k_holes<<<1, HT, 0, s->stream>>>(s->g, s->tay, s->map, s->epoch, s->holes_a, s->holes_b, s->holes_b + s->n,
-                                    s->ds);
+  k_holes<<<1, HT, 0, s->stream>>>(s->g, s->tay, s->map, s->holes_a, s->holes_b, s->holes_b + s->n, s->ds);
   prof_end(s, ps);
-  s->launches += 8;
+  s->launches += 9;
 }
 
 void launch_read_map(vm_solver* s, int32_t* dst) {
   unsigned nb = (unsigned)((s->n + 255) / 256);
   if (nb > 152 * 16) nb = 152 * 16;
   const int ps = prof_begin(s, KID_READ_MAP);
-  k_read_map<<<nb, 256, 0, s->stream>>>(s->map, s->epoch, dst, s->n);
+  k_read_map<<<nb, 256, 0, s->stream>>>(s->map, s->ds, dst, s->n);
   prof_end(s, ps);
   s->launches++;
 }

@@ -55,13 +55,15 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 // Transport reconstruction of one x row per block, fused with M(i).
+__device__ __forceinline__ uint32_t ds_epoch(const DevState* ds) { return *(const volatile uint32_t*)&ds->epoch; }
+
 __device__ __forceinline__ int owner(const uint32_t* __restrict__ map, size_t p, uint32_t epoch, int ne) {
   const uint32_t t = map[p];
   const int m = (int)(t & SLOT_MASK);
   return ((t >> 24) == epoch && m < ne) ? m : -1;
 }
 
-__global__ void __launch_bounds__(256) k_recon64(Grid g, const uint32_t* __restrict__ map, uint32_t epoch,
+__global__ void __launch_bounds__(256) k_recon64(Grid g, const uint32_t* __restrict__ map, const DevState* ds,
                                                  const double* __restrict__ tay, const double* __restrict__ fini,
                                                  double* __restrict__ f, double* __restrict__ M) {
   using R = double;
@@ -71,7 +73,7 @@ __global__ void __launch_bounds__(256) k_recon64(Grid g, const uint32_t* __restr
   double acc = 0.0;
   for (int j = threadIdx.x; j < g.nv; j += blockDim.x) {
     const size_t p = (size_t)i * g.nv + j;
-    const int m = owner(map, p, epoch, g.ne);
+    const int m = owner(map, p, ds_epoch(ds), g.ne);
     double val = 0.0;
     if (m >= 0) {
       const double* t = tay + (size_t)m * TY_N;
@@ -185,7 +187,7 @@ __device__ __forceinline__ double spline_eval(const R* __restrict__ eta, const G
   return (double)sum;
 }
 
-__global__ void __launch_bounds__(256) k_remap64(Grid g, const uint32_t* __restrict__ map, uint32_t epoch,
+__global__ void __launch_bounds__(256) k_remap64(Grid g, const uint32_t* __restrict__ map, const DevState* ds,
                                                  const double* __restrict__ tay, const double* __restrict__ eta,
                                                  double* __restrict__ out) {
   using R = double;
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(256) k_remap64(Grid g, const uint32_t* __restr
   const double Px = site_x(g, i);
   for (int j = threadIdx.x; j < g.nv; j += blockDim.x) {
     const size_t p = (size_t)i * g.nv + j;
-    const int m = owner(map, p, epoch, g.ne);
+    const int m = owner(map, p, ds_epoch(ds), g.ne);
     double val = 0.0;
     if (m >= 0) {
       double Qx, Qv;
@@ -274,7 +276,7 @@ __device__ __forceinline__ float qinterp32(const float* __restrict__ F, const Gr
   return f;
 }
 
-__global__ void __launch_bounds__(256) k_recon32(Grid g, const uint32_t* __restrict__ map, uint32_t epoch,
+__global__ void __launch_bounds__(256) k_recon32(Grid g, const uint32_t* __restrict__ map, const DevState* ds,
                                                  const double* __restrict__ tay, const float* __restrict__ tayf,
                                                  const float* __restrict__ fini, float* __restrict__ f,
                                                  double* __restrict__ M) {
@@ -284,7 +286,7 @@ __global__ void __launch_bounds__(256) k_recon32(Grid g, const uint32_t* __restr
   double acc = 0.0;
   for (int j = threadIdx.x; j < g.nv; j += blockDim.x) {
     const size_t p = (size_t)i * g.nv + j;
-    const int m = owner(map, p, epoch, g.ne);
+    const int m = owner(map, p, ds_epoch(ds), g.ne);
     float val = 0.f;
     if (m >= 0) {
       const float* F = tayf + (size_t)m * TF_N;
@@ -392,7 +394,7 @@ __device__ __forceinline__ float spline32(const float* __restrict__ eta, const G
   return sum;
 }
 
-__global__ void __launch_bounds__(256) k_remap32(Grid g, const uint32_t* __restrict__ map, uint32_t epoch,
+__global__ void __launch_bounds__(256) k_remap32(Grid g, const uint32_t* __restrict__ map, const DevState* ds,
                                                  const double* __restrict__ tay, const float* __restrict__ tayf,
                                                  const float* __restrict__ eta, float* __restrict__ out, float blo,
                                                  float bhi) {
@@ -400,7 +402,7 @@ __global__ void __launch_bounds__(256) k_remap32(Grid g, const uint32_t* __restr
   const float inv_s = 1.0f / (float)g.s, fs = (float)g.s;
   for (int j = threadIdx.x; j < g.nv; j += blockDim.x) {
     const size_t p = (size_t)i * g.nv + j;
-    const int m = owner(map, p, epoch, g.ne);
+    const int m = owner(map, p, ds_epoch(ds), g.ne);
     float val = 0.f;
     if (m >= 0) {
       const float* F = tayf + (size_t)m * TF_N;
@@ -474,10 +476,10 @@ void launch_reconstruct(vm_solver* s) {
   const int nt = s->g.nv >= 256 ? 256 : ((s->g.nv + 31) / 32) * 32;
   const int ps_ = prof_begin(s, KID_RECON);
   if (s->fp32)
-    k_recon32<<<s->g.nx, nt, 0, s->stream>>>(s->g, s->map, s->epoch, s->tay, s->tayf, (const float*)s->fini,
+    k_recon32<<<s->g.nx, nt, 0, s->stream>>>(s->g, s->map, s->ds, s->tay, s->tayf, (const float*)s->fini,
                                               (float*)s->f, s->M);
   else
-    k_recon64<<<s->g.nx, nt, 0, s->stream>>>(s->g, s->map, s->epoch, s->tay, (const double*)s->fini,
+    k_recon64<<<s->g.nx, nt, 0, s->stream>>>(s->g, s->map, s->ds, s->tay, (const double*)s->fini,
                                               (double*)s->f, s->M);
   prof_end(s, ps_);
   s->launches++;
@@ -490,10 +492,10 @@ void launch_remap_resample(vm_solver* s, void* out) {
     const float fb = (float)s->g.beta;
     const float blo = ((double)fb <= s->g.beta) ? fb : nextafterf(fb, -INFINITY);
     const float bhi = ((double)fb >= s->g.beta) ? fb : nextafterf(fb, INFINITY);
-    k_remap32<<<s->g.nx, nt, 0, s->stream>>>(s->g, s->map, s->epoch, s->tay, s->tayf, (const float*)s->eta,
+    k_remap32<<<s->g.nx, nt, 0, s->stream>>>(s->g, s->map, s->ds, s->tay, s->tayf, (const float*)s->eta,
                                               (float*)out, blo, bhi);
   } else {
-    k_remap64<<<s->g.nx, nt, 0, s->stream>>>(s->g, s->map, s->epoch, s->tay, (const double*)s->eta,
+    k_remap64<<<s->g.nx, nt, 0, s->stream>>>(s->g, s->map, s->ds, s->tay, (const double*)s->eta,
                                               (double*)out);
   }
   prof_end(s, ps_);

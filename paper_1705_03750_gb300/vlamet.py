@@ -29,7 +29,8 @@ EXPORTS = ["vm_config_default", "vm_workspace_bytes", "vm_create", "vm_destroy",
            "vm_lattice", "vm_set_f", "vm_set_elements", "vm_get_elements", "vm_compute_map",
            "vm_reconstruct", "vm_step", "vm_remap", "vm_density_force", "vm_read_f", "vm_read_fini",
            "vm_read_eta", "vm_read_map", "vm_diagnostics", "vm_sync", "vm_launch_count",
-           "vm_profile", "vm_profile_read", "vm_force_from_f_static"]
+           "vm_profile", "vm_profile_read", "vm_force_from_f_static",
+           "vm_batch_create", "vm_batch_step", "vm_batch_launches_per_step", "vm_batch_destroy"]
 
 VM_STATIC_FORCE_MAX_NX = 16384
 
@@ -99,6 +100,10 @@ def load() -> C.CDLL:
         "vm_profile_read": (i32, [vp, C.POINTER(VmKernelStat), i32]),
         "vm_force_from_f_static": (i32, [vp, i32, i32, i32, C.c_double, C.c_double, C.c_double, C.c_double,
                                          C.c_double, i32, vp, vp, vp, vp, vp]),
+        "vm_batch_create": (i32, [C.POINTER(vp), i32, i32, vp, C.POINTER(vp)]),
+        "vm_batch_step": (i32, [vp, i32]),
+        "vm_batch_launches_per_step": (i64, [vp, i32]),
+        "vm_batch_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -302,3 +307,38 @@ class Solver:
     @property
     def launches(self) -> int:
         return int(self.L.vm_launch_count(self.h))
+
+
+class Batch:
+    """Many independent solves advanced together, one CUDA graph launch per
+    step (the solves' kernels spread over ``nstreams`` streams inside the
+    graph).  All solvers must have had set_f and share their remap phase."""
+
+    def __init__(self, solvers, nstreams: int = 16, stream=None):
+        import torch
+        self.L = load()
+        self.solvers = list(solvers)
+        dev = self.solvers[0].device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        arr = (C.c_void_p * len(self.solvers))(*[s.h for s in self.solvers])
+        h = C.c_void_p()
+        _check(self.L.vm_batch_create(arr, len(self.solvers), int(nstreams), C.c_void_p(self.stream.cuda_stream),
+                                      C.byref(h)), "vm_batch_create")
+        self.h = h
+
+    def step(self, n: int = 1) -> None:
+        _check(self.L.vm_batch_step(self.h, int(n)), "vm_batch_step")
+
+    def launches_per_step(self, with_remap: bool = False) -> int:
+        return int(self.L.vm_batch_launches_per_step(self.h, int(with_remap)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.vm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,109 @@
+"""Scheduling of the serving layer with a fake device backend (no GPU)."""
+import math
+
+import pytest
+
+from paper_1705_03750_gb300.serve import Request, Server, poisson_requests
+
+
+class FakeClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+
+class FakeBackend:
+    """Each request's footprint is nx*nv bytes; a step of a request takes one
+    tick; the clock advances 1 per tick."""
+
+    def __init__(self, clock):
+        self.clock = clock
+        self.log = []
+
+    def footprint(self, cfg):
+        return cfg[0] * cfg[1]
+
+    def start(self, req, f0):
+        self.log.append(("start", req.rid, self.clock.t))
+        return {"left": req.steps, "rid": req.rid}
+
+    def advance(self, h, n):
+        h["left"] -= n
+        self.clock.t += 0.001
+
+    def done(self, h):
+        return h["left"] == 0
+
+    def result(self, h):
+        return {"rid": h["rid"]}
+
+    def release(self, h):
+        self.log.append(("end", h["rid"], self.clock.t))
+
+
+def test_budget_and_slots_bound_the_active_set():
+    clock = FakeClock()
+    be = FakeBackend(clock)
+    srv = Server(be, budget_bytes=100, max_active=3, clock=clock)
+    reqs = [Request(i, (5, 10), steps=3 + i, arrival=0.0) for i in range(8)]   # 50 B each
+    rep = srv.run(reqs)
+    assert rep["requests"] == 8
+    assert srv.peak_used <= 100 and srv.peak_active <= 2       # the budget binds before the slots
+    assert all(r.result["rid"] == r.rid for r in srv.done)
+    # first come, first served
+    starts = [rid for kind, rid, _ in be.log if kind == "start"]
+    assert starts == sorted(starts)
+
+
+def test_arrivals_wait_for_their_time_and_latency_counts_from_arrival():
+    clock = FakeClock()
+    be = FakeBackend(clock)
+
+    class TickingBackend(FakeBackend):
+        pass
+
+    srv = Server(be, budget_bytes=10 ** 6, max_active=8, clock=clock)
+    reqs = [Request(0, (4, 4), steps=5, arrival=0.0), Request(1, (4, 4), steps=5, arrival=0.003)]
+
+    # advance the clock while idle so that the second arrival comes due
+    orig = srv._admit
+
+    def admit():
+        if not srv.active and srv.waiting:
+            clock.t += 0.001
+        orig()
+    srv._admit = admit
+    srv.run(reqs)
+    r0, r1 = sorted(srv.done, key=lambda r: r.rid)
+    assert r1.admitted >= 0.003 - 1e-12
+    assert r0.latency > 0 and r1.latency > 0
+    assert r1.latency == pytest.approx(r1.finished - 0.003)
+
+
+def test_request_larger_than_the_budget_is_refused():
+    clock = FakeClock()
+    srv = Server(FakeBackend(clock), budget_bytes=10, clock=clock)
+    with pytest.raises(ValueError):
+        srv.submit(Request(0, (10, 10), steps=1, arrival=0.0))
+
+
+def test_report_percentiles():
+    clock = FakeClock()
+    be = FakeBackend(clock)
+    srv = Server(be, budget_bytes=10 ** 9, max_active=100, clock=clock)
+    reqs = [Request(i, (8, 8), steps=1 + (i % 10), arrival=0.0) for i in range(100)]
+    rep = srv.run(reqs)
+    lat = sorted(r.latency for r in srv.done)
+    assert rep["p50_latency_s"] == lat[49] and rep["p99_latency_s"] == lat[98]
+    assert rep["cell_updates_per_s"] > 0
+
+
+def test_poisson_requests_are_seeded():
+    a = poisson_requests(20, rate=3.0, seed=7)
+    b = poisson_requests(20, rate=3.0, seed=7)
+    assert [(r.config, r.steps, r.arrival) for r in a] == [(r.config, r.steps, r.arrival) for r in b]
+    assert all(256 <= nx <= 2048 and nx % 32 == 0 for nx, _ in (r.config for r in a))
+    arr = [r.arrival for r in a]
+    assert arr == sorted(arr) and not math.isnan(arr[-1])
