@@ -332,6 +332,141 @@ def run_reference(args, rank: int):
     }
 
 
+# ---------------------------------------------------------------------------
+# other workloads (their own JSON lines; not the headline)
+# ---------------------------------------------------------------------------
+
+def run_precision(args):
+    """8192^2 halos: FP32-mixed vs FP64 GPU paths over many steps (f
+    difference, mass and energy), and one step of each against the oracle."""
+    import torch
+    from paper_1705_03750_gb300 import vlamet as V
+    rc = I.HALOS_8192
+    f0 = I.initial_f(rc)
+    dev = torch.device("cuda", 0)
+    f0d = torch.from_numpy(f0).to(dev)
+    sol = {}
+    for name, prec in (("fp32", V.VM_FP32_MIXED), ("fp64", V.VM_FP64)):
+        s = V.Solver(V.Config.from_run(rc, prec))
+        s.set_f(f0d)
+        sol[name] = s
+    steps = args.steps
+    hist = []
+    t_ms = {"fp32": 0.0, "fp64": 0.0}
+    for k in range(0, steps, rc.n_s):
+        n = min(rc.n_s, steps - k)
+        for name, s in sol.items():
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s.stream)
+            s.step(n)
+            e1.record(s.stream)
+            torch.cuda.synchronize()
+            t_ms[name] += e0.elapsed_time(e1)
+        a = sol["fp32"].read_f(dtype=np.float32, out=torch.empty((rc.nx, rc.nv), dtype=torch.float32, device=dev))
+        b = sol["fp64"].read_f(out=torch.empty((rc.nx, rc.nv), dtype=torch.float64, device=dev))
+        diff = float((a.double() - b).abs().max() / b.abs().max())
+        d32, d64 = sol["fp32"].diagnostics(), sol["fp64"].diagnostics()
+        hist.append({"step": k + n, "f32_vs_f64_max_rel": diff, "mass32": d32["mass"], "mass64": d64["mass"],
+                     "energy32": d32["energy"], "energy64": d64["energy"]})
+    out = {"workload": rc.name, "steps": steps, "history": hist,
+           "cell_updates_per_s": {n: rc.nx * rc.nv * steps / (t / 1e3) for n, t in t_ms.items()}}
+    if not args.no_cpu_baseline:
+        import oracle.oracle as O
+        o = O.Oracle(rc.nx, rc.nv, rc.x_lo, rc.x_hi, rc.v_lo, rc.v_hi, rc.s, rc.dt, rc.n_s, rc.G)
+        o.set_f(f0)
+        o.step(1)
+        fo = o.last_f()
+        for name, prec in (("fp32", V.VM_FP32_MIXED), ("fp64", V.VM_FP64)):
+            s = V.Solver(V.Config.from_run(rc, prec))
+            s.set_f(f0d)
+            s.step(1)
+            out[f"{name}_vs_oracle_step1_max_rel"] = float(np.abs(s.read_f() - fo).max() / np.abs(fo).max())
+            dg = s.density_force()
+            do = o.density_force()
+            out[f"{name}_vs_oracle_step1_mass_rel"] = abs(dg["M"].sum() - do["M"].sum()) / do["M"].sum()
+    return out
+
+
+def run_batch(args):
+    """Many uneven independent solves: one graph launch per step (Batch)
+    against the plain path (each solve's vm_step on one stream)."""
+    import torch
+    from paper_1705_03750_gb300 import vlamet as V
+    n = args.batch
+    cfgs = [I.batch_member(i) for i in range(n)]
+    cells = sum(rc.nx * rc.nv for rc in cfgs)
+    prec = V.VM_FP32_MIXED
+    f0s = [torch.from_numpy(I.initial_f(rc)).cuda() for rc in cfgs]
+    stream = torch.cuda.current_stream()
+
+    def fresh():
+        ss = [V.Solver(V.Config.from_run(rc, prec), stream=stream) for rc in cfgs]
+        for s, f in zip(ss, f0s):
+            s.set_f(f)
+        return ss
+    res = {"workload": f"batch{n}-uneven-64..1024", "solves": n, "sites": cells, "steps": args.steps}
+    ss = fresh()
+    b = V.Batch(ss, nstreams=args.streams, stream=stream)
+    b.step(args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    res["graph"] = {"cell_updates_per_s": cells * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
+                    "graph_nodes_per_step": b.launches_per_step(False), "streams": args.streams}
+    b.close()
+    del ss
+    # plain path: every solve stepped by its own vm_step call, one stream
+    ss = fresh()
+    for s in ss:
+        s.step(args.warmup)
+    torch.cuda.synchronize()
+    k = max(1, min(args.steps, 20))
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(k):
+        for s in ss:
+            s.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    res["plain"] = {"cell_updates_per_s": cells * k / (ms / 1e3), "ms_per_step": ms / k, "steps_timed": k,
+                    "host_s": time.perf_counter() - t0}
+    return res
+
+
+def run_serve(args):
+    """Open-loop Poisson arrivals of seeded halo solves on a device-memory
+    budget; p50/p99 latency and throughput at fractions of saturation."""
+    import torch
+    from paper_1705_03750_gb300.serve import GpuBackend, Server, poisson_requests
+    budget = int(args.budget_gb * (1 << 30))
+
+    def make(i, nx, nv):
+        return I.HALOS_4096.with_(name=f"req{i}", nx=nx, nv=nv, seed=10_000 + i)
+    base = poisson_requests(args.requests, rate=0.0, seed=args.seed, make_config=make,
+                            steps=(args.min_steps, args.max_steps))
+    ics = {r.rid: I.initial_f(r.config) for r in base}
+    ic = lambda rc: ics[int(rc.name[3:])]  # noqa: E731
+    srv = Server(GpuBackend(), budget_bytes=budget, max_active=args.max_active, steps_per_tick=args.tick, ic_fn=ic)
+    sat = srv.run(base)
+    sat_rate = sat["requests"] / sat["wall_s"]
+    out = {"workload": "serve-halos-256..2048", "requests": args.requests, "budget_gb": args.budget_gb,
+           "saturation": {**sat, "requests_per_s": sat_rate}, "rates": []}
+    for frac in (0.25, 0.5, 0.75, 0.9, 1.1):
+        reqs = poisson_requests(args.requests, rate=frac * sat_rate, seed=args.seed, make_config=make,
+                                steps=(args.min_steps, args.max_steps))
+        srv = Server(GpuBackend(), budget_bytes=budget, max_active=args.max_active, steps_per_tick=args.tick,
+                     ic_fn=ic)
+        rep = srv.run(reqs)
+        out["rates"].append({"fraction_of_saturation": frac, "rate_per_s": frac * sat_rate, **rep})
+        torch.cuda.synchronize()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -342,7 +477,23 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-cap", type=int, default=20)
+    ap.add_argument("--workload", default="halos4096", choices=["halos4096", "precision8192", "batch", "serve"])
+    ap.add_argument("--batch", type=int, default=512)
+    ap.add_argument("--streams", type=int, default=16)
+    ap.add_argument("--requests", type=int, default=48)
+    ap.add_argument("--min-steps", type=int, default=200)
+    ap.add_argument("--max-steps", type=int, default=2000)
+    ap.add_argument("--tick", type=int, default=5)
+    ap.add_argument("--max-active", type=int, default=32)
+    ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--seed", type=int, default=0)
     args = ap.parse_args()
+    if args.workload != "halos4096":
+        from paper_1705_03750_gb300 import build as B
+        B.build()
+        fn = {"precision8192": run_precision, "batch": run_batch, "serve": run_serve}[args.workload]
+        print(json.dumps(fn(args)))
+        return
     if args.warmup < 3:
         args.warmup = 3
     world = int(os.environ.get("WORLD_SIZE", "1"))

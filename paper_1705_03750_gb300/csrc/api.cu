@@ -101,9 +101,11 @@ void thomas(int n, std::vector<double>& out) {
 size_t ne_total(const vm_solver* s) { return (size_t)s->g.ne; }
 using vm::SLOT_MASK;
 
+// Launch errors of this call (cleared, so that one failed launch does not
+// make every later call report it).
 vm_status check_launch(vm_solver* s) {
   (void)s;
-  return cudaPeekAtLastError() == cudaSuccess ? VM_OK : VM_E_CUDA;
+  return cudaGetLastError() == cudaSuccess ? VM_OK : VM_E_CUDA;
 }
 
 }  // namespace

@@ -886,11 +886,13 @@ void alpha_bounds(double alpha, float& lo, float& hi) {
 
 }  // namespace
 
-// Opt the large-window kernel in to the shared memory its windows need.
+// Opt the large-window kernel in to shared memory.  The limit is a property
+// of the kernel, shared by every solver of the process, so it is set to the
+// largest size any grid can ask for rather than to this grid's need.
 bool map_prepare(const Grid& g) {
-  const size_t need = big_smem_bytes(g);
-  if (need > SMEM_MAX) return false;
-  return cudaFuncSetAttribute(k_claim_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need) == cudaSuccess;
+  if (big_smem_bytes(g) > SMEM_MAX) return false;
+  return cudaFuncSetAttribute(k_claim_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX) ==
+         cudaSuccess;
 }
 
 void launch_map(vm_solver* s) {
