@@ -225,10 +225,11 @@ double vo_spline_eval(const double* eta, int32_t nx, int32_t nv, double u, doubl
 /* ------------------------------------------------------------------ */
 
 static void taylor_of(const elem_t* e, double Qx, double Qv, taylor_t* t) {
-  /* det T (eq. of |T|), inverse by the adjugate */
+  /* det T (eq. of |T|), inverse by the adjugate times 1/det T */
   double det = e->Txx * e->Tvv - e->Txv * e->Tvx;
-  double Ti00 = e->Tvv / det, Ti01 = -e->Txv / det;
-  double Ti10 = -e->Tvx / det, Ti11 = e->Txx / det;
+  double id = 1.0 / det;
+  double Ti00 = e->Tvv * id, Ti01 = -e->Txv * id;
+  double Ti10 = -e->Tvx * id, Ti11 = e->Txx * id;
   t->x = e->x;
   t->v = e->v;
   t->Ti[0] = Ti00;

@@ -278,6 +278,8 @@ vm_status vm_create(const vm_config* c, void* d_workspace, size_t bytes, void* s
   g.inv_dv = 1.0 / g.dv;
   g.inv_dxm = 1.0 / g.dxm;
   g.inv_dvm = 1.0 / g.dvm;
+  g.r_vx = g.dvm / g.dxm;
+  g.r_xv = g.dxm / g.dvm;
   g.cx = 0.5 * (c->x_lo + c->x_hi);
   g.cv = 0.5 * (c->v_lo + c->v_hi);
   g.dxdv = g.dx * g.dv;

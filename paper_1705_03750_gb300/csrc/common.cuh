@@ -23,6 +23,7 @@ struct Grid {
   double x_lo, v_lo, dx, dv, dxm, dvm, inv_dx, inv_dv, inv_dxm, inv_dvm, cx, cv, dxdv;
   double alpha, beta;
   double dt, half_dt, A;  // A = 2 pi G
+  double r_vx, r_xv;      // dv_m/dx_m and dx_m/dv_m
   int32_t literal_fd;
   int32_t max_hole_rounds;
 };

@@ -22,7 +22,7 @@ __device__ __forceinline__ float up32(double x) {
 // FP32 record of element m (see TF_* in common.cuh) from its FP64 terms.
 __device__ __forceinline__ void taylor_f32(const Grid& g, const double* t, float* __restrict__ F) {
   const double dxm = g.dxm, dvm = g.dvm;
-  const double T00 = t[TY_TI00], T01 = t[TY_TI01] * dvm / dxm, T10 = t[TY_TI10] * dxm / dvm, T11 = t[TY_TI11];
+  const double T00 = t[TY_TI00], T01 = t[TY_TI01] * g.r_vx, T10 = t[TY_TI10] * g.r_xv, T11 = t[TY_TI11];
   F[TF_T00] = (float)T00;
   F[TF_T01] = (float)T01;
   F[TF_T10] = (float)T10;
@@ -38,7 +38,8 @@ __device__ __forceinline__ void taylor_f32(const Grid& g, const double* t, float
     F[TF_GX11 + 3 * l] = (float)g11;
     gs[l] = fabs(g00) + 2.0 * fabs(g01) + fabs(g11);
   }
-  const double K00 = t[TY_TI00] / dxm, K01 = t[TY_TI01] / dxm, K10 = t[TY_TI10] / dvm, K11 = t[TY_TI11] / dvm;
+  const double K00 = t[TY_TI00] * g.inv_dxm, K01 = t[TY_TI01] * g.inv_dxm;
+  const double K10 = t[TY_TI10] * g.inv_dvm, K11 = t[TY_TI11] * g.inv_dvm;
   F[TF_K00] = (float)K00;
   F[TF_K01] = (float)K01;
   F[TF_K10] = (float)K10;
@@ -63,8 +64,10 @@ __device__ __forceinline__ void taylor_one(const Grid& g, const double* __restri
   double x = el[EL_X * ne + m], v = el[EL_V * ne + m];
   double Txx = el[EL_TXX * ne + m], Txv = el[EL_TXV * ne + m];
   double Tvx = el[EL_TVX * ne + m], Tvv = el[EL_TVV * ne + m];
-  double det = dsub(dmul(Txx, Tvv), dmul(Txv, Tvx));
-  double Ti00 = Tvv / det, Ti01 = -Txv / det, Ti10 = -Tvx / det, Ti11 = Txx / det;
+  // T^-1 = adj(T) (1/det T): one division (FP64 division is slow here)
+  const double det = dsub(dmul(Txx, Tvv), dmul(Txv, Tvx));
+  const double id = 1.0 / det;
+  const double Ti00 = dmul(Tvv, id), Ti01 = dmul(-Txv, id), Ti10 = dmul(-Tvx, id), Ti11 = dmul(Txx, id);
   double* t = tay + (size_t)m * TY_N;
   t[TY_X] = x;
   t[TY_V] = v;
