@@ -131,6 +131,31 @@ def algorithmic(kernel: str, rc, fp32: bool, ne: int):
 
 
 # ---------------------------------------------------------------------------
+# replicas over ranks (one independent solve per GPU)
+# ---------------------------------------------------------------------------
+
+def rank_workload(rank: int):
+    """Rank r advances its own solve of the workload, seeded seed + r."""
+    return WORKLOAD.with_(seed=WORKLOAD.seed + rank)
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """Slowest rank's value (all ranks get it); identity without a process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(world: int, sites: int, steps: int, ms_max: float) -> float:
+    """Whole-job cell updates per second: every rank's sites over the slowest
+    rank's time."""
+    return world * sites * steps / (ms_max / 1e3)
+
+
+# ---------------------------------------------------------------------------
 # native arm
 # ---------------------------------------------------------------------------
 
@@ -140,7 +165,7 @@ def run_native(args, rank: int, world: int, dist):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    rc = WORKLOAD.with_(seed=WORKLOAD.seed + rank)
+    rc = rank_workload(rank)
     f0 = I.initial_f(rc)
     f0_dev = torch.from_numpy(f0).to(dev)
     try:
@@ -154,12 +179,8 @@ def run_native(args, rank: int, world: int, dist):
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def max_ranks(x: float) -> float:
+        return max_over_ranks(x, dist, dev)
 
     out = {}
     for name, prec in (("fp32", V.VM_FP32_MIXED), ("fp64", V.VM_FP64)):
@@ -183,7 +204,7 @@ def run_native(args, rank: int, world: int, dist):
             torch.cuda.synchronize(dev)
         barrier()
         s.sync()
-        ms = max_over_ranks(e0.elapsed_time(e1))
+        ms = max_ranks(e0.elapsed_time(e1))
         launches = s.launches - launches0
         # per-kernel device time over the same number of steps (events on the
         # solver's stream around each launch)
@@ -212,7 +233,7 @@ def run_native(args, rank: int, world: int, dist):
                 V._check(se.L.vm_density_force(se.h, ptr(outs["M"]), ptr(outs["a"]), ptr(outs["da"]),
                                                ptr(outs["d2a"]), 0), "vm_density_force")
             torch.cuda.synchronize(dev)
-            te = max_over_ranks(time.perf_counter() - t0)
+            te = max_ranks(time.perf_counter() - t0)
             barrier()
             e2e = {"value": world * rc.nx * rc.nv * args.steps / te, "unit": "cell-updates/s",
                    "h2d_bytes_per_step": f0.nbytes / args.steps, "d2h_bytes_per_step": 4 * rc.nx * 8,
@@ -228,7 +249,7 @@ def run_native(args, rank: int, world: int, dist):
     head = out.get("fp32") or out.get("fp64")
     K = args.steps
     cells = rc.nx * rc.nv
-    value = world * cells * K / (head["ms"] / 1e3)
+    value = replica_rate(world, cells, K, head["ms"])
     # dominant kernel and its roofline
     stats = head["stats"]
     dom = max(stats, key=lambda k: stats[k][1])
@@ -267,7 +288,7 @@ def run_native(args, rank: int, world: int, dist):
     }
     if "fp64" in out and head is not out["fp64"]:
         f64 = out["fp64"]
-        line["fp64_path"] = {"value": world * cells * K / (f64["ms"] / 1e3), "ms_per_step": f64["ms"] / K,
+        line["fp64_path"] = {"value": replica_rate(world, cells, K, f64["ms"]), "ms_per_step": f64["ms"] / K,
                              "gpu_launches": f64["launches"], "clocks": f64["clocks"],
                              "e2e": f64["e2e"],
                              "top_kernels": {k: round(v[1], 3) for k, v in sorted(f64["stats"].items(), key=lambda kv: -kv[1][1])[:4]}}

@@ -13,7 +13,7 @@
 //      three attempts with larger windows, in an order set by the sides it
 //      escaped from: a band window 128 sites across and as long as shared
 //      memory allows along v (the whole padded lattice at 4096^2), the same
-//      along x, and a 256 x 256 window.  Outer-layer elements whose
+//      along x, and a 640 x 640 window.  Outer-layer elements whose
 //      neighbours moved away claim long thin bands; to cross them in few
 //      rounds, any 64-site word the component reaches is tested whole and
 //      the component is extended through runs of passing sites inside the
@@ -545,7 +545,7 @@ __global__ void __launch_bounds__(ST * SE, 6) k_claim_small(Grid g, const double
 
 constexpr int BT = 256;       // threads
 constexpr int BAND_R = 128;   // band window: rows across the band
-constexpr int FAT_R = 256, FAT_W = 4;
+constexpr int FAT_R = 640, FAT_W = 10;  // 640 x 640 sites
 constexpr int LIST_CAP = 1024;
 constexpr size_t SMEM_MAX = 227 * 1024;
 
@@ -562,7 +562,7 @@ __device__ __forceinline__ int mode_for(int sides, int attempt) {
   const int seq[4][3] = {{MODE_FAT, MODE_BAND_V, MODE_BAND_X},
                          {MODE_BAND_X, MODE_FAT, MODE_BAND_V},
                          {MODE_BAND_V, MODE_FAT, MODE_BAND_X},
-                         {MODE_BAND_V, MODE_BAND_X, MODE_FAT}};
+                         {MODE_FAT, MODE_BAND_V, MODE_BAND_X}};
   return seq[sides & 3][attempt < 0 ? 0 : (attempt > 2 ? 2 : attempt)];
 }
 
