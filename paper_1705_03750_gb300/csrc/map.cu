@@ -6,9 +6,10 @@
 // smaller d).  Each element is flood-filled inside a window of bit masks
 // held in shared memory (evaluated / passing / claimed), sized in tiers:
 //
-//   1. a 64 x 128 window, one warp per element.  Each round dilates the
-//      component by one site and tests only the newly reached sites, which
-//      are compacted into a list so that all 32 lanes share the tests;
+//   1. a 32 x 64 window held in registers (one 64-bit row per lane), one
+//      warp per element.  Each round adds the known passing runs the
+//      component reaches and tests only the newly reached sites, compacted
+//      into a list so that all 32 lanes share the tests;
 //   2. for the elements whose component reached the edge of tier 1, up to
 //      three attempts with larger windows, in an order set by the sides it
 //      escaped from: a band window 128 sites across and as long as shared
@@ -342,144 +343,122 @@ __device__ __forceinline__ bool test_site(const Grid& g, const Elem9& E, const C
 }
 
 // ---------------------------------------------------------------------------
-// tier 1: 64 x 128 window, one warp per element, four elements per block
+// tier 1: 32 x 64 window held in registers, one warp per element
 // ---------------------------------------------------------------------------
 
-constexpr int SR = 64, SW = 2, ST = 32, SCAP = 256, SE = 4;
+constexpr int TR = 32, TCAP = 256, TE = 4;  // rows (one per lane), list capacity, elements per block
 
-struct SmallShared {
-  Elem9 E;
-  unsigned long long comp[SR][SW];
-  unsigned long long eval[SR][SW];
-  unsigned long long pass[SR][SW];
-  unsigned short item[SCAP];
+// The exact test of site (i, j) for element (k, l), FP64 records read from
+// global memory (the rare fallback of the FP32 test).
+__device__ __noinline__ bool pass_exact_g(const Grid& g, const double* __restrict__ tay, int k, int l, double Px,
+                                          double Pv) {
+  double xi, ze;
+  const double d2 = dist2_exact(tay + (size_t)(k * g.Lv + l) * TY_N, g, Px, Pv, xi, ze);
+  int a0, a1, b0, b1;
+  alpha_range(xi, g.alpha, a0, a1);
+  alpha_range(ze, g.alpha, b0, b1);
+  for (int a = a0; a <= a1; a++)
+    for (int b = b0; b <= b1; b++) {
+      if (a == 0 && b == 0) continue;
+      const int kk = k + a, ll = l + b;
+      if (kk < 0 || kk >= g.Lx || ll < 0 || ll >= g.Lv) continue;
+      double x2, z2;
+      if (dist2_exact(tay + (size_t)(kk * g.Lv + ll) * TY_N, g, Px, Pv, x2, z2) < d2) return false;
+    }
+  return true;
+}
+
+struct WarpShared {
+  float F9[9][TF_N];
+  int ex9[9];
+  float offu[9], offv[9];
+  unsigned long long tested[TR], passed[TR];  // results of one round, per window row
+  unsigned short item[TCAP];
 };
 
-// One element per warp.  First every site within one element spacing of the
-// start is tested at once (the component's usual extent); the component then
-// grows through known passing sites (whole runs inside a word per round) and,
-// past the tested box, by testing the newly reached sites as a compacted list.
-__global__ void __launch_bounds__(ST * SE, 6) k_claim_small(Grid g, const double* __restrict__ tay,
+// Lane r owns window row r: its claimed / tested / passing bits are three
+// 64-bit registers; rows above and below come by shuffle.  Each round adds
+// the known passing runs the component reaches, then tests the newly
+// reached sites, compacted into a list shared by the 32 lanes.
+__global__ void __launch_bounds__(32 * TE, 6) k_claim_small(Grid g, const double* __restrict__ tay,
                                                          const float* __restrict__ tayf, Slots Sin, float alo,
                                                          float ahi, int2* __restrict__ ovf_list) {
-  constexpr int COLS = 64 * SW, RPT = SR / ST;
-  __shared__ SmallShared shs[SE];
+  __shared__ WarpShared shw[TE];
   const Slots S = with_epoch(Sin);
   const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
-  const int m = blockIdx.x * SE + wq;
+  const int m = blockIdx.x * TE + wq;
   if (m >= g.ne) return;
-  SmallShared& sh = shs[wq];
-  // per-warp loads (the block's warps work independently)
-  {
-    const int k = m / g.Lv, l = m - k * g.Lv;
-    for (int idx = lane; idx < 9 * TY_N; idx += ST) {
-      const int q = idx / TY_N, c2 = idx - q * TY_N;
-      const int kk = k + q / 3 - 1, ll = l + q % 3 - 1;
-      const bool ex = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
-      sh.E.T9[q][c2] = ex ? tay[(size_t)(kk * g.Lv + ll) * TY_N + c2] : 0.0;
-      if (c2 == 0) sh.E.ex9[q] = ex;
-    }
-    for (int idx = lane; idx < 9 * TF_N; idx += ST) {
-      const int q = idx / TF_N, c2 = idx - q * TF_N;
-      const int kk = k + q / 3 - 1, ll = l + q % 3 - 1;
-      const bool ex = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
-      sh.E.F9[q][c2] = ex ? tayf[(size_t)(kk * g.Lv + ll) * TF_N + c2] : 0.f;
-    }
+  WarpShared& sh = shw[wq];
+  const int k = m / g.Lv, l = m - k * g.Lv;
+  for (int idx = lane; idx < 9 * TF_N; idx += 32) {
+    const int q = idx / TF_N, c2 = idx - q * TF_N;
+    const int kk = k + q / 3 - 1, ll = l + q % 3 - 1;
+    const bool ex = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
+    sh.F9[q][c2] = (ex && c2 < TF_UI) ? tayf[(size_t)(kk * g.Lv + ll) * TF_N + c2] : 0.f;
+    if (c2 == 0) sh.ex9[q] = ex;
   }
-  for (int r = lane; r < SR; r += ST)
-#pragma unroll
-    for (int w = 0; w < SW; w++) {
-      sh.comp[r][w] = 0ull;
-      sh.eval[r][w] = 0ull;
-      sh.pass[r][w] = 0ull;
-    }
-  __syncwarp();
-  long long i0, j0;
-  if (!start_site(g, sh.E, i0, j0)) return;
-  if (lane < 9) {
-    sh.E.offu[lane] = sh.E.ex9[lane] ? (float)((double)i0 - sh.E.T9[lane][TY_U]) : 0.f;
-    sh.E.offv[lane] = sh.E.ex9[lane] ? (float)((double)j0 - sh.E.T9[lane][TY_W]) : 0.f;
-  }
-  __syncwarp();
-  const Ctx9 c = ctx_of(g, sh.E, alo, ahi);
+  // start site (FP64 index position of P_m)
+  const double* tm = tay + (size_t)m * TY_N;
+  const double us = tm[TY_U], ws = tm[TY_W];
+  if (!(us > -1e9 && us < 1e9 && ws > -1e9 && ws < 1e9)) return;
+  const long long i0 = (long long)floor(dadd(us, 0.5)), j0 = (long long)floor(dadd(ws, 0.5));
   const int pad = g.pad;
-  const long long r0 = i0 - SR / 2, c0 = j0 - COLS / 2;
-  const int clo = (int)max(0ll, (long long)(-pad) - c0);
-  const int chi = (int)min((long long)COLS, (long long)(g.nv + pad) - c0);
-  const int rlo = (int)max(0ll, (long long)(-pad) - r0);
-  const int rhi = (int)min((long long)SR, (long long)(g.nx + pad) - r0);
-  // the start site decides whether there is a component at all
-  bool ok = false;
-  if (lane == 0) ok = test_site(g, sh.E, c, i0, j0, i0, j0);
-  ok = __shfl_sync(0xffffffffu, ok, 0);
-  if (!ok) return;
-  // speculative box: rows and columns within s of the start
-  const int B = min(g.s, 15);
-  const int bw = 2 * B + 1, nbox = bw * bw;
-  for (int e = lane; e < nbox; e += ST) {
-    const int r = SR / 2 - B + e / bw, cc = COLS / 2 - B + e % bw;
-    if (r < rlo || r >= rhi || cc < clo || cc >= chi) continue;
-    const int w = cc >> 6, b = cc & 63;
-    const unsigned long long bit = 1ull << b;
-    atomicOr(&sh.eval[r][w], bit);
-    if (test_site(g, sh.E, c, i0, j0, r0 + r, c0 + cc)) atomicOr(&sh.pass[r][w], bit);
+  if (i0 < -pad || i0 >= g.nx + pad || j0 < -pad || j0 >= g.nv + pad) return;
+  if (lane < 9) {
+    const int kk = k + lane / 3 - 1, ll = l + lane % 3 - 1;
+    const bool ex = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
+    const double* tq = tay + (size_t)(kk * g.Lv + ll) * TY_N;
+    sh.offu[lane] = ex ? (float)((double)i0 - tq[TY_U]) : 0.f;
+    sh.offv[lane] = ex ? (float)((double)j0 - tq[TY_W]) : 0.f;
   }
   __syncwarp();
-  if (lane == 0) {
-    sh.comp[SR / 2][(COLS / 2) >> 6] |= 1ull << ((COLS / 2) & 63);
+  Ctx9 c;
+  c.F9 = sh.F9;
+  c.ex9 = sh.ex9;
+  c.offu = sh.offu;
+  c.offv = sh.offv;
+  c.inv_s = 1.0f / (float)g.s;
+  c.alo = alo;
+  c.ahi = ahi;
+  const long long r0 = i0 - TR / 2, c0 = j0 - 32;
+  const long long irow = r0 + lane;
+  const int clo = (int)max(0ll, (long long)(-pad) - c0);
+  const int chi = (int)min(64ll, (long long)(g.nv + pad) - c0);
+  const unsigned long long valid = (irow >= -pad && irow < g.nx + pad) ? col_mask(0, clo, chi) : 0ull;
+  auto test = [&](long long i, long long j) -> bool {
+    const int r = pass_f32(c, (float)(i - i0), (float)(j - j0));
+    if (r >= 0) return r == 1;
+    return pass_exact_g(g, tay, k, l, site_x(g, i), site_v(g, j));
+  };
+  // the start decides whether there is a component at all
+  bool ok = false;
+  if (lane == TR / 2) ok = test(i0, j0);
+  ok = __shfl_sync(0xffffffffu, ok, TR / 2);
+  if (!ok) return;
+  unsigned long long comp = 0ull, tested = 0ull, passing = 0ull;
+  if (lane == TR / 2) {
+    comp = tested = passing = 1ull << 32;
     claim(S, g, i0, j0, m);
   }
-  __syncwarp();
-  for (int it = 0; it < SR * COLS; it++) {
-    unsigned long long front[RPT][SW];
-    int cnt = 0;
-    bool grew = false;
-#pragma unroll
-    for (int q = 0; q < RPT; q++) {
-      const int r = lane + q * ST;
-#pragma unroll
-      for (int w = 0; w < SW; w++) {
-        const unsigned long long cw = sh.comp[r][w];
-        unsigned long long d = cw | (cw << 1) | (cw >> 1);
-        if (w > 0) d |= sh.comp[r][w - 1] >> 63;
-        if (w < SW - 1) d |= sh.comp[r][w + 1] << 63;
-        if (r > 0) d |= sh.comp[r - 1][w];
-        if (r < SR - 1) d |= sh.comp[r + 1][w];
-        const unsigned long long valid = (r >= rlo && r < rhi) ? col_mask(w, clo, chi) : 0ull;
-        const unsigned long long gr = d & ~cw & valid;
-        front[q][w] = gr & ~sh.eval[r][w];  // reached, not tested yet
-        cnt += __popcll(front[q][w]);
-        grew |= (gr & sh.pass[r][w]) != 0ull;  // reached, known to pass
+  for (int it = 0; it < TR * 64; it++) {
+    // growth through sites already known to pass (whole runs along the row)
+    unsigned long long up = __shfl_up_sync(0xffffffffu, comp, 1), dn = __shfl_down_sync(0xffffffffu, comp, 1);
+    if (lane == 0) up = 0ull;
+    if (lane == TR - 1) dn = 0ull;
+    unsigned long long reach = (comp | (comp << 1) | (comp >> 1) | up | dn) & ~comp & valid;
+    const unsigned long long known = reach & passing;
+    if (known) {
+      const unsigned long long nw = run_fill(known | comp, passing);
+      unsigned long long add = nw & ~comp;
+      comp |= nw;
+      while (add) {
+        const int b = __ffsll((long long)add) - 1;
+        add &= add - 1ull;
+        claim(S, g, irow, c0 + b, m);
       }
     }
-    __syncwarp();
-    // known passing neighbours join now, with the passing runs they reach
-    // (a lane may already see another lane's growth of this phase; that only
-    // adds connected passing sites earlier)
-#pragma unroll
-    for (int q = 0; q < RPT; q++) {
-      const int r = lane + q * ST;
-#pragma unroll
-      for (int w = 0; w < SW; w++) {
-        const unsigned long long cw = sh.comp[r][w];
-        unsigned long long d = cw | (cw << 1) | (cw >> 1);
-        if (w > 0) d |= sh.comp[r][w - 1] >> 63;
-        if (w < SW - 1) d |= sh.comp[r][w + 1] << 63;
-        if (r > 0) d |= sh.comp[r - 1][w];
-        if (r < SR - 1) d |= sh.comp[r + 1][w];
-        const unsigned long long seeds = d & ~cw & sh.pass[r][w];
-        if (!seeds) continue;
-        const unsigned long long nw = run_fill(seeds | cw, sh.pass[r][w] | cw);
-        unsigned long long add = nw & ~cw;
-        atomicOr(&sh.comp[r][w], add);
-        while (add) {
-          const int b = __ffsll((long long)add) - 1;
-          add &= add - 1ull;
-          claim(S, g, r0 + r, c0 + 64 * w + b, m);
-        }
-      }
-    }
-    // exclusive scan of the untested counts: each lane's items go to [base, base + cnt)
+    const unsigned long long front = reach & ~tested;
+    const int cnt = __popcll(front);
     int incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -487,52 +466,47 @@ __global__ void __launch_bounds__(ST * SE, 6) k_claim_small(Grid g, const double
       if (lane >= o) incl += v;
     }
     const int total = __shfl_sync(0xffffffffu, incl, 31);
-    const bool any_grew = __any_sync(0xffffffffu, grew);
-    if (total == 0 && !any_grew) break;
+    if (total == 0) {
+      if (!__any_sync(0xffffffffu, known != 0ull)) break;
+      continue;
+    }
     int base = incl - cnt;
-#pragma unroll
-    for (int q = 0; q < RPT; q++) {
-      const int r = lane + q * ST;
-#pragma unroll
-      for (int w = 0; w < SW; w++) {
-        unsigned long long fr = front[q][w];
-        while (fr) {
-          const int b = __ffsll((long long)fr) - 1;
-          fr &= fr - 1ull;
-          if (base < SCAP) sh.item[base] = (unsigned short)((r << 7) | (w << 6) | b);
-          base++;
-        }
-      }
+    unsigned long long fr = front;
+    while (fr) {
+      const int b = __ffsll((long long)fr) - 1;
+      fr &= fr - 1ull;
+      if (base < TCAP) sh.item[base] = (unsigned short)((lane << 6) | b);
+      base++;
+    }
+    sh.tested[lane] = 0ull;
+    sh.passed[lane] = 0ull;
+    __syncwarp();
+    const int n = min(total, TCAP);
+    for (int e = lane; e < n; e += 32) {
+      const int code = sh.item[e], r = code >> 6, b = code & 63;
+      const unsigned long long bit = 1ull << b;
+      atomicOr(&sh.tested[r], bit);
+      if (test(r0 + r, c0 + b)) atomicOr(&sh.passed[r], bit);
     }
     __syncwarp();
-    const int nitems = min(total, SCAP);
-    for (int e = lane; e < nitems; e += ST) {
-      const int code = sh.item[e];
-      const int r = code >> 7, w = (code >> 6) & 1, b = code & 63;
-      const unsigned long long bit = 1ull << b;
-      atomicOr(&sh.eval[r][w], bit);
-      if (test_site(g, sh.E, c, i0, j0, r0 + r, c0 + 64 * w + b)) {
-        atomicOr(&sh.pass[r][w], bit);
-        if (!(atomicOr(&sh.comp[r][w], bit) & bit)) claim(S, g, r0 + r, c0 + 64 * w + b, m);
-      }
+    tested |= sh.tested[lane];
+    const unsigned long long np = sh.passed[lane];
+    passing |= np;
+    // tested sites that pass were reached this round: they join at once
+    unsigned long long add = np & reach & ~comp;
+    comp |= add;
+    while (add) {
+      const int b = __ffsll((long long)add) - 1;
+      add &= add - 1ull;
+      claim(S, g, irow, c0 + b, m);
     }
     __syncwarp();
   }
   // Escaped the window?  Record on which sides, to pick the next window.
-  bool esc_rows = false, esc_cols = false;
-#pragma unroll
-  for (int q = 0; q < RPT; q++) {
-    const int r = lane + q * ST;
-    unsigned long long rowany = 0ull;
-#pragma unroll
-    for (int w = 0; w < SW; w++) rowany |= sh.comp[r][w];
-    if (!rowany) continue;
-    if (r == 0 && rlo == 0 && r0 - 1 >= -pad) esc_rows = true;
-    if (r == SR - 1 && rhi == SR && r0 + SR < g.nx + pad) esc_rows = true;
-    if ((sh.comp[r][0] & 1ull) && clo == 0 && c0 - 1 >= -pad) esc_cols = true;
-    if ((sh.comp[r][SW - 1] >> 63) && chi == COLS && c0 + COLS < g.nv + pad) esc_cols = true;
-  }
-  const bool er = __any_sync(0xffffffffu, esc_rows), ec = __any_sync(0xffffffffu, esc_cols);
+  const bool er = __any_sync(0xffffffffu, comp != 0ull && ((lane == 0 && r0 - 1 >= -pad) ||
+                                                            (lane == TR - 1 && r0 + TR < g.nx + pad)));
+  const bool ec = __any_sync(0xffffffffu, ((comp & 1ull) && clo == 0 && c0 - 1 >= -pad) ||
+                                             ((comp >> 63) && chi == 64 && c0 + 64 < g.nv + pad));
   if ((er || ec) && lane == 0) {
     const int sides = (er ? 1 : 0) | (ec ? 2 : 0);
     ovf_list[atomicAdd(&S.ds->noverflow, 1)] = make_int2(m, sides << 4);  // attempt 0
@@ -903,7 +877,7 @@ void launch_map(vm_solver* s) {
   k_map_begin<<<1, 32, 0, s->stream>>>(s->ds);
   prof_end(s, ps);
   ps = prof_begin(s, KID_CLAIM_SMALL);
-  k_claim_small<<<(s->g.ne + SE - 1) / SE, ST * SE, 0, s->stream>>>(s->g, s->tay, s->tayf, S, alo, ahi,
+  k_claim_small<<<(s->g.ne + TE - 1) / TE, 32 * TE, 0, s->stream>>>(s->g, s->tay, s->tayf, S, alo, ahi,
                                                                     s->overflow_list);
   prof_end(s, ps);
   const size_t smem = big_smem_bytes(s->g);

@@ -276,6 +276,21 @@ __device__ __forceinline__ float qinterp32(const float* __restrict__ F, const Gr
   return f;
 }
 
+// Per-thread row sum of FP32 values as an unevaluated float pair (hi + lo,
+// Knuth's TwoSum), converted to double once per thread: ~2^-48 relative
+// accuracy with FP32 arithmetic only.
+struct FPair {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 __global__ void __launch_bounds__(256) k_recon32(Grid g, const uint32_t* __restrict__ map, const DevState* ds,
                                                  const double* __restrict__ tay, const float* __restrict__ tayf,
                                                  const float* __restrict__ fini, float* __restrict__ f,
@@ -283,7 +298,7 @@ __global__ void __launch_bounds__(256) k_recon32(Grid g, const uint32_t* __restr
   __shared__ double sh[32];
   const int i = blockIdx.x;
   const float inv_s = 1.0f / (float)g.s, fs = (float)g.s;
-  double acc = 0.0;
+  FPair acc;
   for (int j = threadIdx.x; j < g.nv; j += blockDim.x) {
     const size_t p = (size_t)i * g.nv + j;
     const int m = owner(map, p, ds_epoch(ds), g.ne);
@@ -335,9 +350,9 @@ __global__ void __launch_bounds__(256) k_recon32(Grid g, const uint32_t* __restr
       if (in > -2 && in < g.nx + 2 && jn > -2 && jn < g.nv + 2) val = qinterp32(fini, g, in, jn, ic, jc, x, y);
     }
     f[p] = val;
-    acc += (double)val;
+    acc.add(val);
   }
-  const double rowsum = block_sum(acc, sh);
+  const double rowsum = block_sum(acc.value(), sh);
   if (threadIdx.x == 0) M[i] = dmul(rowsum, g.dxdv);
 }
 
