@@ -474,6 +474,7 @@ def run_serve(args):
     ic = lambda rc: ics[int(rc.name[3:])]  # noqa: E731
     srv = Server(GpuBackend(), budget_bytes=budget, max_active=args.max_active, steps_per_tick=args.tick, ic_fn=ic)
     sat = srv.run(base)
+    sat["errors"] = sorted({r.error for r in srv.done if r.error})[:3]
     sat_rate = sat["requests"] / sat["wall_s"]
     out = {"workload": "serve-halos-256..2048", "requests": args.requests, "budget_gb": args.budget_gb,
            "saturation": {**sat, "requests_per_s": sat_rate}, "rates": []}
@@ -483,7 +484,9 @@ def run_serve(args):
         srv = Server(GpuBackend(), budget_bytes=budget, max_active=args.max_active, steps_per_tick=args.tick,
                      ic_fn=ic)
         rep = srv.run(reqs)
-        out["rates"].append({"fraction_of_saturation": frac, "rate_per_s": frac * sat_rate, **rep})
+        errs = sorted({r.error for r in srv.done if r.error})
+        out["rates"].append({"fraction_of_saturation": frac, "rate_per_s": frac * sat_rate, **rep,
+                             "errors": errs[:3]})
         torch.cuda.synchronize()
     return out
 

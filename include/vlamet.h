@@ -73,7 +73,9 @@ typedef struct {
   int32_t pad;                /* connectivity margin around the grid, sites; 0 -> s */
   int32_t literal_fd;         /* 1: a' = (a(i+1)-a(i-1))/dx as printed; 0: /(2 dx) */
   int32_t max_hole_rounds;    /* cap on unexplored-site repair rounds; 0 -> nx + nv */
-  int32_t reserved;
+  int32_t map_windows;        /* 0: every influence-map tier; 1: components that leave the
+                                 32 x 64 window go straight to the whole-lattice window
+                                 (the last tier), for testing that tier on small grids */
 } vm_config;
 
 typedef struct {
@@ -86,6 +88,9 @@ typedef struct {
   int32_t holes;    /* unexplored sites repaired by the last map */
   int32_t hole_rounds;
   int32_t overflow_elements; /* elements that needed the large flood-fill window */
+  int32_t tier1_more;        /* elements whose small-window fill tested sites beyond
+                                the region predicted from the linear part of the map */
+  int32_t last_tier_elements; /* elements filled in the whole-lattice window */
 } vm_diag;
 
 typedef struct vm_solver vm_solver;
@@ -103,7 +108,7 @@ size_t vm_workspace_bytes(const vm_config* c);
  * small.  The state is empty until vm_set_f. */
 vm_status vm_create(const vm_config* c, void* d_workspace, size_t workspace_bytes,
                     void* cuda_stream, vm_solver** out);
-void vm_destroy(vm_solver* s);
+void vm_destroy(vm_solver* s);  /* waits for the solver's stream first */
 const char* vm_status_string(vm_status st);
 
 /* Lattice shape: number of elements, Lx and Lv. */
@@ -159,6 +164,14 @@ vm_status vm_diagnostics(vm_solver* s, vm_diag* d);
 
 /* Wait for the solver's stream; return and clear any device-side error. */
 vm_status vm_sync(vm_solver* s);
+
+/* The CUDA error code behind the last VM_E_CUDA returned to this host thread
+ * (cudaSuccess = 0 if none), and its name.  Calls that launch work first
+ * drop an error that earlier CUDA calls of other code in the thread left
+ * unread, so VM_E_CUDA reports this library's launches (or a context that an
+ * earlier fault made unusable). */
+int32_t vm_last_cuda_error(void);
+const char* vm_cuda_error_name(int32_t code);
 
 /* Number of kernel launches the solver has issued since creation (a count
  * kept on the host, for launch accounting). */

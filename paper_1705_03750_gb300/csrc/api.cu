@@ -16,7 +16,7 @@ constexpr double kPi = 3.14159265358979323846;
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t fini, eta, f, tmp, map, slot1, rec_key, rec_site, holes_a, holes_b, ovf, el, tay, tayf, M, a, da, d2a,
+  size_t fini, eta, f, tmp, map, slot1, rec_key, rec_site, holes_a, holes_b, ovf, gwin, el, tay, tayf, M, a, da, d2a,
       thx, thv, thxf, thvf, ds, total;
 };
 
@@ -26,6 +26,7 @@ bool valid(const vm_config* c) {
   if (!(c->x_hi > c->x_lo) || !(c->v_hi > c->v_lo) || !(c->dt > 0.0) || !isfinite(c->G)) return false;
   if (c->precision != VM_FP64 && c->precision != VM_FP32_MIXED) return false;
   if (c->pad < 0 || c->max_hole_rounds < 0) return false;
+  if (c->map_windows != 0 && c->map_windows != 1) return false;
   if (!(c->alpha >= 0.0) || !(c->beta >= 0.0)) return false;
   // 32-bit site indices; element indices fit the 24-bit field of the owner slots
   if ((long long)c->nx * (long long)c->nv >= (1ll << 31) / 2) return false;
@@ -61,11 +62,13 @@ Layout layout(const vm_config* c) {
   L.tmp = take(n * sr);
   L.map = take(n * 4);
   L.slot1 = take(n * 4);
-  L.rec_key = take(n * 16);  // at most one record per site (plus rare lost races)
+  L.rec_key = take(n * 16);  // one record per site
   L.rec_site = take(n * 4);
   L.holes_a = take(n * 4);
   L.holes_b = take(2 * n * 4);
   L.ovf = take(2 * ne * 8);
+  const long long pad = c->pad ? c->pad : c->elem_stride;
+  L.gwin = take(vm::kGlobalBlocks * vm::global_window_words(c->nx, c->nv, pad) * 8);
   L.el = take(12 * ne * 8);
   L.tay = take(16 * ne * 8);
   L.tayf = take(32 * ne * 4);
@@ -105,12 +108,26 @@ using vm::SLOT_MASK;
 // make every later call report it).
 vm_status check_launch(vm_solver* s) {
   (void)s;
-  return cudaGetLastError() == cudaSuccess ? VM_OK : VM_E_CUDA;
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return VM_OK;
+  vm::note_cuda(e);
+  return VM_E_CUDA;
 }
 
 }  // namespace
 
 namespace vm {
+
+thread_local cudaError_t t_last_cuda = cudaSuccess;
+
+void note_cuda(cudaError_t e) { t_last_cuda = e; }
+
+// An error that earlier CUDA calls of other code in this thread left unread
+// (a query that found work not yet done, a failed allocation the caller
+// recovered from) is not this call's: drop it before launching, so that the
+// check after the launches sees only ours.  An error that has corrupted the
+// context persists and makes our own launches fail.
+void clear_foreign_error() { (void)cudaGetLastError(); }
 
 // One transport step t -> t + dt (Sec. 2.4): predictor drift + Taylor terms
 // at t + dt/2, map, f(t + dt/2) and M(i), force, kick + corrector.  Only
@@ -299,12 +316,13 @@ vm_status vm_create(const vm_config* c, void* d_workspace, size_t bytes, void* s
   s->slot1 = (uint32_t*)(base + L.slot1);
   s->rec_key = (unsigned long long*)(base + L.rec_key);
   s->rec_site = (int32_t*)(base + L.rec_site);
-  // record indices travel in the 24-bit field of the second slot
-  s->rec_cap = (int32_t)(s->n < (size_t)SLOT_MASK ? s->n : (size_t)SLOT_MASK);
+  // each site is listed at most once per map
+  s->rec_cap = (int32_t)s->n;
   s->holes_a = (int32_t*)(base + L.holes_a);
   s->holes_b = (int32_t*)(base + L.holes_b);
   s->overflow_list = (int2*)(base + L.ovf);
   s->overflow_list2 = s->overflow_list + ne_total(s);
+  s->gwin = (unsigned long long*)(base + L.gwin);
   s->el = (double*)(base + L.el);
   s->tay = (double*)(base + L.tay);
   s->tayf = (float*)(base + L.tayf);
@@ -331,6 +349,8 @@ vm_status vm_create(const vm_config* c, void* d_workspace, size_t bytes, void* s
     // owner slots start empty (all-ones: an epoch no map uses)
     if (cudaMemsetAsync(s->map, 0xFF, s->n * 4, s->stream) != cudaSuccess) { st = VM_E_CUDA; break; }
     if (cudaMemsetAsync(s->slot1, 0xFF, s->n * 4, s->stream) != cudaSuccess) { st = VM_E_CUDA; break; }
+    // contested-site records start (and stay, between maps) empty
+    if (cudaMemsetAsync(s->rec_key, 0xFF, s->n * 16, s->stream) != cudaSuccess) { st = VM_E_CUDA; break; }
     if (cudaMemcpyAsync(s->thomas_x, tx.data(), tx.size() * 8, cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
         cudaMemcpyAsync(s->thomas_v, tv.data(), tv.size() * 8, cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
         cudaMemcpyAsync(s->thomas_xf, txf.data(), txf.size() * 4, cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
@@ -354,6 +374,9 @@ vm_status vm_create(const vm_config* c, void* d_workspace, size_t bytes, void* s
 
 void vm_destroy(vm_solver* s) {
   if (!s) return;
+  // the caller frees the workspace after this returns: no work of this
+  // solver may still be running on it
+  cudaStreamSynchronize(s->stream);
   for (int i = 0; i < 2 * s->prof_created; i++) cudaEventDestroy(s->prof_ev[i]);
   free(s);
 }
@@ -398,6 +421,7 @@ int64_t vm_launch_count(const vm_solver* s) { return s ? s->launches : 0; }
 
 vm_status vm_set_f(vm_solver* s, const double* f0, int32_t on_device) {
   if (!s || !f0) return VM_E_INVALID_ARG;
+  vm::clear_foreign_error();
   const size_t bytes = s->n * 8;
   if (!s->fp32) {
     VM_CUDA_TRY(cudaMemcpyAsync(s->fini, f0, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
@@ -436,6 +460,7 @@ vm_status vm_get_elements(vm_solver* s, double* soa12, int32_t on_device) {
 
 vm_status vm_compute_map(vm_solver* s) {
   if (!s) return VM_E_INVALID_ARG;
+  vm::clear_foreign_error();
   vm::launch_taylor(s);
   vm::launch_map(s);
   return check_launch(s);
@@ -443,6 +468,7 @@ vm_status vm_compute_map(vm_solver* s) {
 
 vm_status vm_reconstruct(vm_solver* s) {
   if (!s) return VM_E_INVALID_ARG;
+  vm::clear_foreign_error();
   if (!s->have_f) return VM_E_STATE;
   vm::launch_taylor(s);
   vm::launch_map(s);
@@ -453,6 +479,7 @@ vm_status vm_reconstruct(vm_solver* s) {
 
 vm_status vm_step(vm_solver* s, int32_t nsteps) {
   if (!s || nsteps < 0) return VM_E_INVALID_ARG;
+  vm::clear_foreign_error();
   if (!s->have_f) return VM_E_STATE;
   for (int32_t it = 0; it < nsteps; it++) {
     vm::step_transport(s);
@@ -468,6 +495,7 @@ vm_status vm_step(vm_solver* s, int32_t nsteps) {
 
 vm_status vm_remap(vm_solver* s) {
   if (!s) return VM_E_INVALID_ARG;
+  vm::clear_foreign_error();
   if (!s->have_f) return VM_E_STATE;
   return remap_internal(s);
 }
@@ -552,7 +580,13 @@ vm_status vm_diagnostics(vm_solver* s, vm_diag* d) {
   d->holes = h.holes_found;
   d->hole_rounds = h.hole_rounds;
   d->overflow_elements = h.overflow_stat;
+  d->tier1_more = h.t1_more;
+  d->last_tier_elements = s->cfg.map_windows == 0 ? h.overflow3_stat : h.overflow_stat;
   return VM_OK;
 }
+
+int32_t vm_last_cuda_error(void) { return (int32_t)vm::t_last_cuda; }
+
+const char* vm_cuda_error_name(int32_t code) { return cudaGetErrorName((cudaError_t)code); }
 
 }  // extern "C"

@@ -42,19 +42,26 @@ struct DevState {
   int32_t noverflow3;    // ... third attempt
   int32_t overflow3_stat;
   int32_t nrec;          // records of sites claimed by two or more elements
+  int32_t t1_more;       // tier-1 elements that needed tests beyond their predicted region
   uint32_t epoch;        // epoch of the current influence map (0..kEpochs-1)
   double Mtot;           // total mass of the last reconstruction
   double sum_mass, sum_kin, sum_pot;
   unsigned long long det_min_key, det_max_key;
 };
-constexpr int kMapCounters = 10;  // int32 fields from nholes to nrec
 
 // Owner slots of the influence map: (epoch << 24) | element index.  A slot
 // whose epoch is not the current map's is empty; every site is rewritten
 // each map (claimed or repaired), so stale values are never more than one
-// map old.  The second slot of a contested site holds (epoch << 24) | index
-// of its record and is cleared when the record is resolved.
+// map old.  The second slot of a contested site holds (epoch << 24) while
+// the site is listed for resolution, and is cleared when it is resolved.
 constexpr uint32_t SLOT_EMPTY = 0xFFFFFFFFu;
+
+// Whole-lattice flood-fill windows of the last map tier: blocks working at
+// once, and 64-bit words of one window (three masks over the padded lattice).
+constexpr int kGlobalBlocks = 16;
+inline size_t global_window_words(long long nx, long long nv, long long pad) {
+  return 3 * (size_t)(nx + 2 * pad) * (size_t)((nv + 2 * pad + 63) / 64);
+}
 constexpr uint32_t SLOT_MASK = 0x00FFFFFFu;
 constexpr int kEpochs = 255;  // epochs 0..254; 255 never current
 
@@ -72,7 +79,7 @@ enum { TY_X = 0, TY_V, TY_TI00, TY_TI01, TY_TI10, TY_TI11, TY_GX00, TY_GX01, TY_
 // element's index position u_m = (x_m - x_lo)/dx into integer and fraction.
 enum { TF_T00 = 0, TF_T01, TF_T10, TF_T11, TF_GX00, TF_GX01, TF_GX11, TF_GV00, TF_GV01, TF_GV11,
        TF_K00, TF_K01, TF_K10, TF_K11, TF_C1X, TF_C2X, TF_C1V, TF_C2V, TF_UF, TF_WF, TF_UI, TF_WI,
-       TF_N = 32 };
+       TF_BU, TF_BW, TF_HU, TF_HW, TF_N = 32 };
 
 constexpr unsigned long long KEY_EMPTY = ~0ull;
 
@@ -100,14 +107,15 @@ struct vm_solver {
   void* f;
   void* tmp;
   uint32_t* map;            // owner slot 0: the influence map (epoch-tagged)
-  uint32_t* slot1;          // record index of a contested site
-  unsigned long long* rec_key;  // per record: {element index, bits of d^2}, 128-bit minimum
-  int32_t* rec_site;        // per record: its site (-1: unused)
+  uint32_t* slot1;          // (epoch << 24): the site is listed as contested in that map
+  unsigned long long* rec_key;  // per site: {element index, bits of d^2}, 128-bit minimum; empty between maps
+  int32_t* rec_site;        // contested sites of the current map
   int32_t rec_cap;
   int32_t* holes_a;
   int32_t* holes_b;         // also the 8 B/site staging buffer of the copy calls
   int2* overflow_list;      // (element, window mode) for the second tier
   int2* overflow_list2;     // for the last-resort tier
+  unsigned long long* gwin; // bit masks of the whole-lattice windows (kGlobalBlocks of them), kept zeroed
   double* el;               // 12 x ne
   double* tay;              // ne x 16
   float* tayf;              // ne x 32 (FP32 record, element units)
@@ -215,8 +223,18 @@ __device__ __forceinline__ unsigned long long dkey(double d) {
 
 }  // namespace vm
 
+namespace vm {
+// The last CUDA error a library call met in this host thread (reported by
+// vm_last_cuda_error), and the clearing of errors left unread by other code.
+void note_cuda(cudaError_t e);
+void clear_foreign_error();
+}  // namespace vm
+
 #define VM_CUDA_TRY(expr)                       \
   do {                                          \
     cudaError_t e_ = (expr);                    \
-    if (e_ != cudaSuccess) return VM_E_CUDA;    \
+    if (e_ != cudaSuccess) {                    \
+      vm::note_cuda(e_);                        \
+      return VM_E_CUDA;                         \
+    }                                           \
   } while (0)

@@ -95,7 +95,15 @@ __device__ __forceinline__ void taylor_one(const Grid& g, const double* __restri
   // index position of P_m, as the start site of the percolation uses it
   t[TY_U] = dmul(dsub(x, g.x_lo), g.inv_dx);
   t[TY_W] = dmul(dsub(v, g.v_lo), g.inv_dv);
-  taylor_f32(g, t, tayf + (size_t)m * TF_N);
+  float* F = tayf + (size_t)m * TF_N;
+  taylor_f32(g, t, F);
+  // lattice index position of Q_m (a multiple of 1/2): integer part and
+  // half, exactly
+  const int u2 = (g.nx - 1) + 2 * (k - g.Kx - 1) * g.s, w2 = (g.nv - 1) + 2 * (l - g.Kv - 1) * g.s;
+  reinterpret_cast<int*>(F)[TF_BU] = u2 >> 1;
+  reinterpret_cast<int*>(F)[TF_BW] = w2 >> 1;
+  F[TF_HU] = (u2 & 1) ? 0.5f : 0.f;
+  F[TF_HW] = (w2 & 1) ? 0.5f : 0.f;
 }
 
 // Half drift (predictor or corrector of Sec. 2.4): x, T_x. and H_x.. move
@@ -191,95 +199,70 @@ __global__ void k_reset(Grid g, double* __restrict__ el) {
   for (int q = EL_HXXX; q < EL_N; q++) el[q * ne + m] = 0.0;
 }
 
-// ---- double-double helpers for the compensated mass scan ----
-struct dd {
-  double hi, lo;
-};
-__device__ __forceinline__ dd two_sum(double a, double b) {
-  double s = dadd(a, b);
-  double bb = dsub(s, a);
-  double e = dadd(dsub(a, dsub(s, bb)), dsub(b, bb));
-  return {s, e};
-}
-__device__ __forceinline__ dd dd_add(dd a, dd b) {
-  dd s = two_sum(a.hi, b.hi);
-  double e = dadd(s.lo, dadd(a.lo, b.lo));
-  double h = dadd(s.hi, e);
-  double l = dsub(e, dsub(h, s.hi));
-  return {h, l};
-}
-__device__ __forceinline__ dd dd_neg(dd a) { return {-a.hi, -a.lo}; }
-__device__ __forceinline__ dd shfl_up_dd(dd v, int d) {
-  return {__shfl_up_sync(0xffffffffu, v.hi, d), __shfl_up_sync(0xffffffffu, v.lo, d)};
-}
+constexpr int SCAN_T = 256;
 
-constexpr int SCAN_T = 1024;
-
-// Mass scan and force (Sec. 2.5, eq. of a(i)): one block; each thread owns
-// a contiguous chunk of pixels; pixel masses are summed in double-double so
-// that M_left and M_total carry ~30 digits before the final rounding.
+// Mass scan and force (Sec. 2.5, eq. of a(i)): one block.  FP64 runs at two
+// lanes per SM per clock on this GPU, so the scan is work-efficient: each
+// thread sums a contiguous chunk of pixels, the chunk totals are scanned
+// across the block, and each thread then walks its chunk once.  a(i) takes
+// the same per-pixel expression as the definition, A ((M_tot - left) -
+// left_prev); only the association of the running sums differs (a tree
+// over chunks instead of one left-to-right sum), which moves them by a few
+// units in the last place of M_tot at most.
 __global__ void __launch_bounds__(SCAN_T) k_scan_force(Grid g, const double* __restrict__ M,
-                                                       double* __restrict__ a, double* __restrict__ da,
-                                                       double* __restrict__ d2a, DevState* ds) {
-  __shared__ double sh_hi[SCAN_T / 32], sh_lo[SCAN_T / 32];
-  __shared__ double tot_hi, tot_lo;
+                                                       double* __restrict__ a, DevState* ds) {
+  __shared__ double sh[SCAN_T / 32];
+  __shared__ double tot_s;
   const int nx = g.nx, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int C = (nx + SCAN_T - 1) / SCAN_T;
   const int i0 = min(tid * C, nx), i1 = min(i0 + C, nx);
-  dd loc = {0.0, 0.0};
-  for (int i = i0; i < i1; i++) loc = dd_add(loc, dd{M[i], 0.0});
-  // inclusive warp scan
-  dd inc = loc;
+  double loc = 0.0;
+  for (int i = i0; i < i1; i++) loc = dadd(loc, M[i]);
+  double inc = loc;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    dd o = shfl_up_dd(inc, d);
-    if (lane >= d) inc = dd_add(o, inc);
+    const double o = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d) inc = dadd(o, inc);
   }
-  if (lane == 31) {
-    sh_hi[wid] = inc.hi;
-    sh_lo[wid] = inc.lo;
-  }
+  if (lane == 31) sh[wid] = inc;
   __syncthreads();
   if (wid == 0) {
-    dd w = {sh_hi[lane], sh_lo[lane]};
-    dd wi = w;
+    const double w = (lane < SCAN_T / 32) ? sh[lane] : 0.0;
+    double wi = w;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      dd o = shfl_up_dd(wi, d);
-      if (lane >= d) wi = dd_add(o, wi);
+    for (int d = 1; d < SCAN_T / 32; d <<= 1) {
+      const double o = __shfl_up_sync(0xffffffffu, wi, d);
+      if (lane >= d) wi = dadd(o, wi);
     }
-    // exclusive prefix of the warp totals
-    dd ex = shfl_up_dd(wi, 1);
-    if (lane == 0) ex = {0.0, 0.0};
-    sh_hi[lane] = ex.hi;
-    sh_lo[lane] = ex.lo;
-    if (lane == 31) {
-      tot_hi = wi.hi;
-      tot_lo = wi.lo;
-    }
+    if (lane < SCAN_T / 32) sh[lane] = dsub(wi, w);  // exclusive prefix of the warp totals
+    if (lane == SCAN_T / 32 - 1) tot_s = wi;
   }
   __syncthreads();
-  dd excl = dd_add(dd{sh_hi[wid], sh_lo[wid]}, dd_add(inc, dd_neg(loc)));
-  dd tot = {tot_hi, tot_lo};
-  dd left_prev = excl;
+  const double tot = tot_s;
+  // sum of the pixels before this thread's chunk
+  double left_prev = dadd(sh[wid], dsub(inc, loc));
   for (int i = i0; i < i1; i++) {
-    dd left = dd_add(left_prev, dd{M[i], 0.0});
-    dd r = dd_add(dd_add(tot, dd_neg(left)), dd_neg(left_prev));
-    a[i] = dmul(g.A, dadd(r.hi, r.lo));
+    const double left = dadd(left_prev, M[i]);
+    a[i] = dmul(g.A, dsub(dsub(tot, left), left_prev));
     left_prev = left;
   }
-  __syncthreads();
-  const double Mt = dadd(tot.hi, tot.lo);
-  const double alo = dmul(g.A, Mt), ahi = -dmul(g.A, Mt);
+  if (tid == 0) ds->Mtot = tot;
+}
+
+// a' and a'' by centred differences (Sec. 2.5); beyond the grid a takes its
+// limits +A M_tot (left) and -A M_tot (right).
+__global__ void k_force_diff(Grid g, const double* __restrict__ a, double* __restrict__ da,
+                             double* __restrict__ d2a, const DevState* __restrict__ ds) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nx = g.nx;
+  if (i >= nx) return;
+  const double Mt = ds->Mtot;
   const double twodx = g.literal_fd ? g.dx : dmul(2.0, g.dx);
   const double dx2 = dmul(g.dx, g.dx);
-  for (int i = i0; i < i1; i++) {
-    double am = (i > 0) ? a[i - 1] : alo;
-    double ap = (i < nx - 1) ? a[i + 1] : ahi;
-    da[i] = dsub(ap, am) / twodx;
-    d2a[i] = dsub(dadd(ap, am), dmul(2.0, a[i])) / dx2;
-  }
-  if (tid == 0) ds->Mtot = Mt;
+  const double am = (i > 0) ? a[i - 1] : dmul(g.A, Mt);
+  const double ap = (i < nx - 1) ? a[i + 1] : -dmul(g.A, Mt);
+  da[i] = dsub(ap, am) / twodx;
+  d2a[i] = dsub(dadd(ap, am), dmul(2.0, a[i])) / dx2;
 }
 
 __device__ __forceinline__ unsigned long long order_key(double d) {
@@ -336,38 +319,45 @@ __global__ void k_diag(Grid g, const R* __restrict__ f, const double* __restrict
 
 inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Element kernels are FP64-bound (two FP64 lanes per SM per clock): small
+// blocks spread a small lattice over many SMs.
+constexpr int ET = 64;
+
 }  // namespace
 
 void launch_drift(vm_solver* s, bool taylor) {
-  { const int ps_ = prof_begin(s, KID_DRIFT); k_drift<<<blocks_for(s->g.ne, 256), 256, 0, s->stream>>>(s->g, s->el, s->tay, s->tayf, taylor ? 1 : 0); prof_end(s, ps_); }
+  { const int ps_ = prof_begin(s, KID_DRIFT); k_drift<<<blocks_for(s->g.ne, ET), ET, 0, s->stream>>>(s->g, s->el, s->tay, s->tayf, taylor ? 1 : 0); prof_end(s, ps_); }
   s->launches++;
 }
 
 void launch_taylor(vm_solver* s) {
-  { const int ps_ = prof_begin(s, KID_TAYLOR); k_taylor<<<blocks_for(s->g.ne, 256), 256, 0, s->stream>>>(s->g, s->el, s->tay, s->tayf); prof_end(s, ps_); }
+  { const int ps_ = prof_begin(s, KID_TAYLOR); k_taylor<<<blocks_for(s->g.ne, ET), ET, 0, s->stream>>>(s->g, s->el, s->tay, s->tayf); prof_end(s, ps_); }
   s->launches++;
 }
 
 void launch_kick_drift(vm_solver* s) {
-  { const int ps_ = prof_begin(s, KID_KICK_DRIFT); k_kick_drift<<<blocks_for(s->g.ne, 256), 256, 0, s->stream>>>(s->g, s->el, s->a, s->da, s->d2a, s->ds); prof_end(s, ps_); }
+  { const int ps_ = prof_begin(s, KID_KICK_DRIFT); k_kick_drift<<<blocks_for(s->g.ne, ET), ET, 0, s->stream>>>(s->g, s->el, s->a, s->da, s->d2a, s->ds); prof_end(s, ps_); }
   s->launches++;
 }
 
 void launch_reset_elements(vm_solver* s) {
-  { const int ps_ = prof_begin(s, KID_RESET); k_reset<<<blocks_for(s->g.ne, 256), 256, 0, s->stream>>>(s->g, s->el); prof_end(s, ps_); }
+  { const int ps_ = prof_begin(s, KID_RESET); k_reset<<<blocks_for(s->g.ne, ET), ET, 0, s->stream>>>(s->g, s->el); prof_end(s, ps_); }
   s->launches++;
 }
 
 void launch_scan_force(vm_solver* s) {
-  { const int ps_ = prof_begin(s, KID_SCAN_FORCE); k_scan_force<<<1, SCAN_T, 0, s->stream>>>(s->g, s->M, s->a, s->da, s->d2a, s->ds); prof_end(s, ps_); }
-  s->launches++;
+  const int ps_ = prof_begin(s, KID_SCAN_FORCE);
+  launch_scan_force_raw(s->g, s->M, s->a, s->da, s->d2a, s->ds, s->stream);
+  prof_end(s, ps_);
+  s->launches += 2;
 }
 
 // The same mass scan on caller-provided buffers (no solver), for the
 // allocation-free entry point.
 void launch_scan_force_raw(const Grid& g, const double* M, double* a, double* da, double* d2a, DevState* ds,
                            cudaStream_t stream) {
-  k_scan_force<<<1, SCAN_T, 0, stream>>>(g, M, a, da, d2a, ds);
+  k_scan_force<<<1, SCAN_T, 0, stream>>>(g, M, a, ds);
+  k_force_diff<<<blocks_for(g.nx, 128), 128, 0, stream>>>(g, a, da, d2a, ds);
 }
 
 void launch_diagnostics(vm_solver* s) {

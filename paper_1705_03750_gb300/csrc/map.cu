@@ -4,12 +4,14 @@
 // 4-connected component, containing the grid site nearest to P_m, of the
 // sites that pass m's test (no investigated neighbour proposes a strictly
 // smaller d).  Each element is flood-filled inside a window of bit masks
-// held in shared memory (evaluated / passing / claimed), sized in tiers:
+// (tested / passing / component), sized in tiers:
 //
 //   1. a 32 x 64 window held in registers (one 64-bit row per lane), one
-//      warp per element.  Each round adds the known passing runs the
-//      component reaches and tests only the newly reached sites, compacted
-//      into a list so that all 32 lanes share the tests;
+//      warp per element.  The first round tests the region predicted by the
+//      linear part of the element's map; the component is then closed
+//      through the passing sites by shuffle scans, and further rounds test
+//      only sites next to it left untested (tests compacted into a list so
+//      that all 32 lanes share them);
 //   2. for the elements whose component reached the edge of tier 1, up to
 //      three attempts with larger windows, in an order set by the sides it
 //      escaped from: a band window 128 sites across and as long as shared
@@ -19,6 +21,10 @@
 //      rounds, any 64-site word the component reaches is tested whole and
 //      the component is extended through runs of passing sites inside the
 //      word with one carry-propagating addition.
+//
+// A window whose component reaches its edge claims nothing: the next, larger
+// window's component contains it.  Claims are made once the component is
+// final, with several atomic exchanges in flight per thread.
 //
 // Decisions.  The percolation's outcome is fixed by FP64 values evaluated in
 // one operation order (the exact test).  Each test is first run in FP32 in
@@ -30,14 +36,17 @@
 // The outcome is therefore identical to the all-FP64 evaluation.
 //
 // Claims.  A claimed site's owner slot takes (epoch << 24 | m) with one
-// atomic exchange.  A claim that displaces a current-epoch owner makes sure
-// the site has a record (a 128-bit key, published through the second slot)
-// and folds into it, by a 128-bit compare-and-swap minimum, the exact FP64
-// keys (bits of d^2, element index) of the displaced owner and of itself:
-// every claimant of a contested site reaches the record, so its minimum is
-// the exact winner, and FP64 work is spent only on contested sites.
+// atomic exchange.  A claim that displaces a current-epoch owner folds into
+// the site's record (a 128-bit key per site, empty between maps), by a
+// 128-bit compare-and-swap minimum, the exact FP64 keys (bits of d^2,
+// element index) of the displaced owner and of itself, and lists the site
+// for resolution if it is the first to flag it (second slot = epoch): every
+// claimant of a contested site reaches the record, so its minimum is the
+// exact winner, and FP64 work is spent only on contested sites.
 // Unclaimed sites are repaired in Jacobi rounds from their 4-neighbours.
 #include <math.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 
@@ -212,34 +221,25 @@ __global__ void k_map_begin(DevState* ds) {
     ds->noverflow = ds->overflow_stat = ds->noverflow2 = ds->overflow2_stat = 0;
     ds->noverflow3 = ds->overflow3_stat = 0;
     ds->nrec = 0;
+    ds->t1_more = 0;
   }
 }
 
 __device__ __noinline__ void contest(const Slots& S, const Grid& g, long long i, long long j, size_t p, int m,
                                      uint32_t displaced) {
   const uint32_t E = S.epoch;
-  uint32_t rs = __ldcg(&S.slot1[p]);
-  if ((rs >> 24) != E) {
-    // create the site's record; publish it only once initialised
+  // The site's record is its own 128-bit key slot, empty between maps.  The
+  // claimant that first flags the site in this map's epoch lists it for the
+  // resolution (each site at most once per map).
+  const uint32_t rs = __ldcg(&S.slot1[p]);
+  if ((rs >> 24) != E && atomicCAS(&S.slot1[p], rs, E << 24) == rs) {
     const int r = atomicAdd(&S.ds->nrec, 1);
-    if (r >= S.rec_cap) {
-      atomicOr(&S.ds->err, ERR_PATCH_OVERFLOW);
-      return;
-    }
-    S.rec_key[2 * (size_t)r] = KEY_EMPTY;
-    S.rec_key[2 * (size_t)r + 1] = KEY_EMPTY;
-    S.rec_site[r] = (int32_t)p;
-    __threadfence();
-    const uint32_t mine = (E << 24) | (uint32_t)r;
-    const uint32_t prev = atomicCAS(&S.slot1[p], rs, mine);
-    if (prev == rs) {
-      rs = mine;
-    } else {
-      S.rec_site[r] = -1;  // another claim published first: use its record
-      rs = prev;
-    }
+    if (r < S.rec_cap)
+      S.rec_site[r] = (int32_t)p;
+    else
+      atomicOr(&S.ds->err, ERR_PATCH_OVERFLOW);  // (cannot happen: rec_cap is the site count)
   }
-  unsigned long long* key = S.rec_key + 2 * (size_t)(rs & SLOT_MASK);
+  unsigned long long* key = S.rec_key + 2 * p;
   const double Px = site_x(g, i), Pv = site_v(g, j);
   double xi, ze;
   const int mo = (int)(displaced & SLOT_MASK);
@@ -247,15 +247,21 @@ __device__ __noinline__ void contest(const Slots& S, const Grid& g, long long i,
   key_min(key, dkey(dist2_exact(S.tay + (size_t)m * TY_N, g, Px, Pv, xi, ze)), (unsigned long long)m);
 }
 
-__device__ __forceinline__ void claim(const Slots& S, const Grid& g, long long i, long long j, int m) {
-  if (i < 0 || i >= g.nx || j < 0 || j >= g.nv) return;
-  const size_t p = (size_t)i * g.nv + j;
+// Claims of up to N sites (pos: row-major site index, or ~0 for none) with
+// all N exchanges issued before any result is looked at.
+template <int N>
+__device__ __forceinline__ void claim_sites(const Slots& S, const Grid& g, const size_t (&pos)[N], int m) {
   const uint32_t tag = (S.epoch << 24) | (uint32_t)m;
-  const uint32_t old = atomicExch(&S.slot0[p], tag);
-  // first claimant this map, or the same element again (a larger window
-  // redoing it): nothing to resolve
-  if ((old >> 24) != S.epoch || old == tag) return;
-  contest(S, g, i, j, p, m, old);
+  uint32_t old[N];
+#pragma unroll
+  for (int u = 0; u < N; u++) old[u] = (pos[u] != ~(size_t)0) ? atomicExch(&S.slot0[pos[u]], tag) : tag;
+#pragma unroll
+  for (int u = 0; u < N; u++) {
+    // first claimant this map, or the same element again: nothing to resolve
+    if ((old[u] >> 24) != S.epoch || old[u] == tag) continue;
+    const long long i = (long long)(pos[u] / (size_t)g.nv), j = (long long)(pos[u] - (size_t)i * g.nv);
+    contest(S, g, i, j, pos[u], m, old[u]);
+  }
 }
 
 // Mask of window columns [lo, hi) within word w (64 columns per word).
@@ -277,7 +283,7 @@ __device__ __forceinline__ unsigned long long run_fill(unsigned long long S, uns
   return up | dn;
 }
 
-enum : int { MODE_BAND_V = 0, MODE_BAND_X = 1, MODE_FAT = 2 };
+enum : int { MODE_BAND_V = 0, MODE_BAND_X = 1, MODE_FAT = 2, MODE_GLOBAL = 3 };
 
 // Shared part of every window: the element's 3x3 neighbourhood in FP64 and
 // FP32, and the FP32 offsets of their positions from the start site.
@@ -347,6 +353,7 @@ __device__ __forceinline__ bool test_site(const Grid& g, const Elem9& E, const C
 // ---------------------------------------------------------------------------
 
 constexpr int TR = 32, TCAP = 256, TE = 4;  // rows (one per lane), list capacity, elements per block
+constexpr unsigned FULL = 0xffffffffu;
 
 // The exact test of site (i, j) for element (k, l), FP64 records read from
 // global memory (the rare fallback of the FP32 test).
@@ -368,18 +375,70 @@ __device__ __noinline__ bool pass_exact_g(const Grid& g, const double* __restric
   return true;
 }
 
-struct WarpShared {
+struct __align__(16) WarpShared {
   float F9[9][TF_N];
   int ex9[9];
   float offu[9], offv[9];
-  unsigned long long tested[TR], passed[TR];  // results of one round, per window row
-  unsigned short item[TCAP];
+  unsigned long long passed[TR];  // passing sites found by one round, per window row
+  unsigned short item[TCAP];      // compacted list (lane << 6 | bit)
 };
 
-// Lane r owns window row r: its claimed / tested / passing bits are three
-// 64-bit registers; rows above and below come by shuffle.  Each round adds
-// the known passing runs the component reaches, then tests the newly
-// reached sites, compacted into a list shared by the 32 lanes.
+// Inclusive sum of v over the lanes of the warp.
+__device__ __forceinline__ int warp_incl(int v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(FULL, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// Bits of `comp` carried along the columns of the window (down and up the
+// lanes) through vertical runs of `pass` (comp inside pass): a segmented
+// OR-scan, log2(32) shuffle steps each way.
+__device__ __forceinline__ unsigned long long vfill(unsigned long long comp, unsigned long long pass, int lane) {
+  unsigned long long gd = comp, ad = pass, gu = comp, au = pass;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned long long g1 = __shfl_up_sync(FULL, gd, d), a1 = __shfl_up_sync(FULL, ad, d);
+    const unsigned long long g2 = __shfl_down_sync(FULL, gu, d), a2 = __shfl_down_sync(FULL, au, d);
+    if (lane >= d) {
+      gd |= g1 & ad;
+      ad &= a1;
+    }
+    if (lane + d < 32) {
+      gu |= g2 & au;
+      au &= a2;
+    }
+  }
+  return gd | gu;
+}
+
+// Write the positions of the set bits of `bits` (one word per lane) with
+// list index in [b0, b0 + TCAP) to the list; excl / incl: the lane's range.
+__device__ __forceinline__ void list_chunk(unsigned short* item, unsigned long long bits, int excl, int incl, int b0,
+                                           int lane) {
+  if (excl >= b0 + TCAP || incl <= b0) return;
+  int idx = excl;
+  while (bits) {
+    const int b = __ffsll((long long)bits) - 1;
+    bits &= bits - 1ull;
+    if (idx >= b0 + TCAP) break;
+    if (idx >= b0) item[idx - b0] = (unsigned short)((lane << 6) | b);
+    idx++;
+  }
+}
+
+// Lane r owns window row r: its component / tested / passing bits are three
+// 64-bit registers.  The first round tests the sites of the region the
+// linear part of the map predicts (its parallelogram, widened by one site
+// and by a bound on the second-order terms); every round then closes the
+// component through all sites known to pass (vertical scan + horizontal
+// runs, to a fixed point) and tests the sites next to it not yet tested.
+// Tests are compacted into a list shared by the 32 lanes.  The order of the
+// tests does not change the result: the component is the connected set of
+// passing sites reached from the start, and the loop ends only when every
+// site next to it has been tested.  Claims are made once at the end.
 __global__ void __launch_bounds__(32 * TE, 6) k_claim_small(Grid g, const double* __restrict__ tay,
                                                          const float* __restrict__ tayf, Slots Sin, float alo,
                                                          float ahi, int2* __restrict__ ovf_list) {
@@ -390,12 +449,15 @@ __global__ void __launch_bounds__(32 * TE, 6) k_claim_small(Grid g, const double
   if (m >= g.ne) return;
   WarpShared& sh = shw[wq];
   const int k = m / g.Lv, l = m - k * g.Lv;
-  for (int idx = lane; idx < 9 * TF_N; idx += 32) {
-    const int q = idx / TF_N, c2 = idx - q * TF_N;
+  // the 3x3 neighbourhood's FP32 records, 16 bytes per lane and load
+  for (int idx = lane; idx < 9 * (TF_N / 4); idx += 32) {
+    const int q = idx >> 3, c4 = idx & 7;
     const int kk = k + q / 3 - 1, ll = l + q % 3 - 1;
     const bool ex = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
-    sh.F9[q][c2] = (ex && c2 < TF_UI) ? tayf[(size_t)(kk * g.Lv + ll) * TF_N + c2] : 0.f;
-    if (c2 == 0) sh.ex9[q] = ex;
+    const float4 v = ex ? __ldg(reinterpret_cast<const float4*>(tayf + (size_t)(kk * g.Lv + ll) * TF_N) + c4)
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+    reinterpret_cast<float4*>(sh.F9[q])[c4] = v;
+    if (c4 == 0) sh.ex9[q] = ex;
   }
   // start site (FP64 index position of P_m)
   const double* tm = tay + (size_t)m * TY_N;
@@ -433,83 +495,131 @@ __global__ void __launch_bounds__(32 * TE, 6) k_claim_small(Grid g, const double
   // the start decides whether there is a component at all
   bool ok = false;
   if (lane == TR / 2) ok = test(i0, j0);
-  ok = __shfl_sync(0xffffffffu, ok, TR / 2);
+  ok = __shfl_sync(FULL, ok, TR / 2);
   if (!ok) return;
   unsigned long long comp = 0ull, tested = 0ull, passing = 0ull;
-  if (lane == TR / 2) {
-    comp = tested = passing = 1ull << 32;
-    claim(S, g, i0, j0, m);
+  if (lane == TR / 2) comp = tested = passing = 1ull << 32;
+
+  // predicted region, row by row: |T p|_x <= hx and |T p|_v <= hv for the
+  // columns of this lane's row (p in element units).  Its inner part (the
+  // sites expected well inside the alpha box, whose tests compare with no
+  // neighbour) is listed first, so that the lanes of one pass of the tests
+  // mostly take the same path.
+  unsigned long long fa, fb;
+  {
+    const float* F = sh.F9[4];
+    const float T00 = F[TF_T00], T01 = F[TF_T01], T10 = F[TF_T10], T11 = F[TF_T11];
+    const float inv_s = c.inv_s, sf = (float)g.s;
+    const float det = fabsf(T00 * T11 - T01 * T10);
+    const float ext = (det > 1e-20f) ? fmaxf(fabsf(T11) + fabsf(T01), fabsf(T10) + fabsf(T00)) * __frcp_rn(det) : 0.f;
+    const float P = 0.6f * ext + inv_s;
+    const float sx = F[TF_C2X] * P * P, sv = F[TF_C2V] * P * P;
+    const float hx = 0.52f + 1.1f * fmaxf(fabsf(T00), fabsf(T01)) * inv_s + sx;
+    const float hv = 0.52f + 1.1f * fmaxf(fabsf(T10), fabsf(T11)) * inv_s + sv;
+    const float ix = alo - 0.02f - sx, iv = alo - 0.02f - sv;
+    const float px = ((float)(lane - TR / 2) + sh.offu[4]) * inv_s;
+    const float r01 = (fabsf(T01) > 1e-20f) ? __frcp_rn(T01) : 0.f, r11 = (fabsf(T11) > 1e-20f) ? __frcp_rn(T11) : 0.f;
+    // columns b with |a + cf * pv(b)| <= h for both rows of T, pv(b) = (b - 32 + offv) / s
+    auto cols = [&](float h1, float h2) -> unsigned long long {
+      float lo = -1e30f, hi = 1e30f;
+      auto cut = [&](float a, float cf, float rcf, float h) {
+        if (rcf != 0.f) {
+          const float t1 = (-h - a) * rcf, t2 = (h - a) * rcf;
+          lo = fmaxf(lo, fminf(t1, t2));
+          hi = fminf(hi, fmaxf(t1, t2));
+        } else if (!(fabsf(a) <= h)) {
+          lo = 1e30f;
+          hi = -1e30f;
+        }
+      };
+      cut(T00 * px, T01, r01, h1);
+      cut(T10 * px, T11, r11, h2);
+      const float blo = fminf(fmaxf(lo * sf - sh.offv[4] + 32.f, -1.f), 65.f);
+      const float bhi = fminf(fmaxf(hi * sf - sh.offv[4] + 32.f, -1.f), 65.f);
+      const int ilo = max((int)ceilf(blo), 0), ihi = min((int)floorf(bhi), 63);
+      return (ihi >= ilo) ? col_mask(0, ilo, ihi + 1) : 0ull;
+    };
+    const unsigned long long pred = cols(hx, hv) & valid & ~tested;
+    const unsigned long long inner = (ix > 0.f && iv > 0.f) ? cols(ix, iv) : 0ull;
+    fa = pred & inner;
+    fb = pred & ~inner;
   }
+  int rounds = 0;
   for (int it = 0; it < TR * 64; it++) {
-    // growth through sites already known to pass (whole runs along the row)
-    unsigned long long up = __shfl_up_sync(0xffffffffu, comp, 1), dn = __shfl_down_sync(0xffffffffu, comp, 1);
-    if (lane == 0) up = 0ull;
-    if (lane == TR - 1) dn = 0ull;
-    unsigned long long reach = (comp | (comp << 1) | (comp >> 1) | up | dn) & ~comp & valid;
-    const unsigned long long known = reach & passing;
-    if (known) {
-      const unsigned long long nw = run_fill(known | comp, passing);
-      unsigned long long add = nw & ~comp;
-      comp |= nw;
-      while (add) {
-        const int b = __ffsll((long long)add) - 1;
-        add &= add - 1ull;
-        claim(S, g, irow, c0 + b, m);
+    // the sites to test: fa's listed before fb's
+    const int ca = __popcll(fa), cb = __popcll(fb);
+    const int inca = warp_incl(ca, lane), incb = warp_incl(cb, lane);
+    const int ta = __shfl_sync(FULL, inca, 31);
+    const int total = ta + __shfl_sync(FULL, incb, 31);
+    if (total == 0) break;
+    rounds++;
+    sh.passed[lane] = 0ull;
+    for (int b0 = 0; b0 < total; b0 += TCAP) {
+      __syncwarp();
+      list_chunk(sh.item, fa, inca - ca, inca, b0, lane);
+      list_chunk(sh.item, fb, ta + incb - cb, ta + incb, b0, lane);
+      __syncwarp();
+      const int n = min(total - b0, TCAP);
+      for (int e = lane; e < n; e += 32) {
+        const int code = sh.item[e], r = code >> 6, b = code & 63;
+        if (test(r0 + r, c0 + b)) atomicOr(&sh.passed[r], 1ull << b);
       }
     }
-    const unsigned long long front = reach & ~tested;
-    const int cnt = __popcll(front);
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += v;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    if (total == 0) {
-      if (!__any_sync(0xffffffffu, known != 0ull)) break;
-      continue;
-    }
-    int base = incl - cnt;
-    unsigned long long fr = front;
-    while (fr) {
-      const int b = __ffsll((long long)fr) - 1;
-      fr &= fr - 1ull;
-      if (base < TCAP) sh.item[base] = (unsigned short)((lane << 6) | b);
-      base++;
-    }
-    sh.tested[lane] = 0ull;
-    sh.passed[lane] = 0ull;
     __syncwarp();
-    const int n = min(total, TCAP);
-    for (int e = lane; e < n; e += 32) {
-      const int code = sh.item[e], r = code >> 6, b = code & 63;
-      const unsigned long long bit = 1ull << b;
-      atomicOr(&sh.tested[r], bit);
-      if (test(r0 + r, c0 + b)) atomicOr(&sh.passed[r], bit);
+    tested |= fa | fb;
+    passing |= sh.passed[lane];
+    // close the component through every site known to pass
+    for (int f = 0; f < TR * 64; f++) {
+      const unsigned long long nc = run_fill(vfill(comp, passing, lane), passing);
+      const bool grew = nc != comp;
+      comp = nc;
+      if (!__any_sync(FULL, grew)) break;
     }
-    __syncwarp();
-    tested |= sh.tested[lane];
-    const unsigned long long np = sh.passed[lane];
-    passing |= np;
-    // tested sites that pass were reached this round: they join at once
-    unsigned long long add = np & reach & ~comp;
-    comp |= add;
-    while (add) {
-      const int b = __ffsll((long long)add) - 1;
-      add &= add - 1ull;
-      claim(S, g, irow, c0 + b, m);
-    }
-    __syncwarp();
+    unsigned long long up = __shfl_up_sync(FULL, comp, 1), dn = __shfl_down_sync(FULL, comp, 1);
+    if (lane == 0) up = 0ull;
+    if (lane == TR - 1) dn = 0ull;
+    fa = 0ull;
+    fb = (comp | (comp << 1) | (comp >> 1) | up | dn) & ~comp & valid & ~tested;
   }
-  // Escaped the window?  Record on which sides, to pick the next window.
-  const bool er = __any_sync(0xffffffffu, comp != 0ull && ((lane == 0 && r0 - 1 >= -pad) ||
-                                                            (lane == TR - 1 && r0 + TR < g.nx + pad)));
-  const bool ec = __any_sync(0xffffffffu, ((comp & 1ull) && clo == 0 && c0 - 1 >= -pad) ||
-                                             ((comp >> 63) && chi == 64 && c0 + 64 < g.nv + pad));
-  if ((er || ec) && lane == 0) {
-    const int sides = (er ? 1 : 0) | (ec ? 2 : 0);
-    ovf_list[atomicAdd(&S.ds->noverflow, 1)] = make_int2(m, sides << 4);  // attempt 0
+  if (rounds > 1 && lane == 0) atomicAdd(&S.ds->t1_more, 1);
+
+  // Escaped the window?  Record on which sides, to pick the next window;
+  // the larger window claims a superset of this component.
+  const bool er = __any_sync(FULL, comp != 0ull && ((lane == 0 && r0 - 1 >= -pad) ||
+                                                    (lane == TR - 1 && r0 + TR < g.nx + pad)));
+  const bool ec = __any_sync(FULL, ((comp & 1ull) && clo == 0 && c0 - 1 >= -pad) ||
+                                       ((comp >> 63) && chi == 64 && c0 + 64 < g.nv + pad));
+  if (er || ec) {
+    if (lane == 0) {
+      const int sides = (er ? 1 : 0) | (ec ? 2 : 0);
+      ovf_list[atomicAdd(&S.ds->noverflow, 1)] = make_int2(m, sides << 4);  // attempt 0
+    }
+    return;
+  }
+  // claims: the component's sites compacted into the list, four exchanges
+  // in flight per lane
+  const int cnt = __popcll(comp);
+  const int incl = warp_incl(cnt, lane);
+  const int total = __shfl_sync(FULL, incl, 31);
+  for (int b0 = 0; b0 < total; b0 += TCAP) {
+    __syncwarp();
+    list_chunk(sh.item, comp, incl - cnt, incl, b0, lane);
+    __syncwarp();
+    const int n = min(total - b0, TCAP);
+    for (int e = lane; e < n; e += 4 * 32) {
+      size_t pos[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int ee = e + 32 * u;
+        pos[u] = ~(size_t)0;
+        if (ee < n) {
+          const int code = sh.item[ee];
+          const long long i = r0 + (code >> 6), j = c0 + (code & 63);
+          if (i >= 0 && i < g.nx && j >= 0 && j < g.nv) pos[u] = (size_t)i * g.nv + j;
+        }
+      }
+      claim_sites(S, g, pos, m);
+    }
   }
 }
 
@@ -517,27 +627,28 @@ __global__ void __launch_bounds__(32 * TE, 6) k_claim_small(Grid g, const double
 // tier 2: larger windows, cooperative block, word-granular tests
 // ---------------------------------------------------------------------------
 
-constexpr int BT = 256;       // threads
+constexpr int BT = 512;       // threads
 constexpr int BAND_R = 128;   // band window: rows across the band
 constexpr int FAT_R = 640, FAT_W = 10;  // 640 x 640 sites
 constexpr int LIST_CAP = 1024;
+constexpr int AHEAD = 4;      // rows tested ahead of the component per round
 constexpr size_t SMEM_MAX = 227 * 1024;
 
 struct BigHeader {
   Elem9 E;
   int nlist, ok;
   int rmin, rmax, wmin, wmax;  // rows / words holding component bits
-  int list[LIST_CAP];
+  int list[LIST_CAP];          // words to test this round
+  unsigned long long lmask[LIST_CAP];  // their untested valid sites
 };
 
-// Order of the window modes tried for an element, by the sides its
-// component escaped tier 1 from (1: rows, 2: columns, 3: both).
+// Window modes of the attempts after tier 1, by the sides its component
+// escaped from (1: rows, 2: columns, 3: both); the last attempt covers the
+// whole padded lattice, its bit masks in global memory.
 __device__ __forceinline__ int mode_for(int sides, int attempt) {
-  const int seq[4][3] = {{MODE_FAT, MODE_BAND_V, MODE_BAND_X},
-                         {MODE_BAND_X, MODE_FAT, MODE_BAND_V},
-                         {MODE_BAND_V, MODE_FAT, MODE_BAND_X},
-                         {MODE_FAT, MODE_BAND_V, MODE_BAND_X}};
-  return seq[sides & 3][attempt < 0 ? 0 : (attempt > 2 ? 2 : attempt)];
+  const int seq[4][2] = {{MODE_FAT, MODE_BAND_V}, {MODE_BAND_X, MODE_FAT}, {MODE_BAND_V, MODE_FAT},
+                         {MODE_FAT, MODE_BAND_V}};
+  return attempt >= 2 ? MODE_GLOBAL : seq[sides & 3][attempt < 0 ? 0 : attempt];
 }
 
 // 64-bit words along a band window for a lattice side n: the whole padded
@@ -546,6 +657,27 @@ __host__ __device__ __forceinline__ int band_words(long long n, int pad) {
   const long long full = (n + 2 * pad + 63) / 64;
   const long long fit = (long long)((SMEM_MAX - sizeof(BigHeader)) / (3 * 8 * BAND_R));
   return (int)(full < fit ? full : fit);
+}
+
+// Rows and words of a window mode on a lattice (nrow x ncol sites before
+// the pad, rows across and words along the bit axis): never more than the
+// padded lattice holds.
+__host__ __device__ __forceinline__ void window_dims(int mode, long long nrow, long long ncol, int pad, int& R,
+                                                     int& W) {
+  const long long rows_pad = nrow + 2 * pad, words_pad = (ncol + 2 * pad + 63) / 64;
+  long long r, w;
+  if (mode == MODE_GLOBAL) {
+    r = rows_pad;
+    w = words_pad;
+  } else if (mode == MODE_FAT) {
+    r = FAT_R < rows_pad ? FAT_R : rows_pad;
+    w = FAT_W < words_pad ? FAT_W : words_pad;
+  } else {
+    r = BAND_R < rows_pad ? BAND_R : rows_pad;
+    w = band_words(ncol, pad);
+  }
+  R = (int)r;
+  W = (int)w;
 }
 
 // Window geometry: "rows" run across, "words" along the bit axis.  For
@@ -558,6 +690,28 @@ struct Win {
   long long nrow_lat, ncol_lat;  // lattice extent along rows / bits (without pad)
 };
 
+// Centred on the start site, moved inside the padded lattice.
+__device__ __forceinline__ Win make_window(int mode, const Grid& g, long long i0, long long j0) {
+  Win W;
+  const int pad = g.pad;
+  W.trans = (mode == MODE_BAND_X);
+  W.nrow_lat = W.trans ? g.nv : g.nx;
+  W.ncol_lat = W.trans ? g.nx : g.nv;
+  window_dims(mode, W.nrow_lat, W.ncol_lat, pad, W.R, W.W);
+  const long long across0 = W.trans ? j0 : i0, along0 = W.trans ? i0 : j0;
+  long long r0 = across0 - W.R / 2, c0 = along0 - 32ll * W.W;
+  r0 = min(r0, W.nrow_lat + pad - W.R);
+  c0 = min(c0, W.ncol_lat + pad - 64ll * W.W);
+  W.r0 = max(r0, (long long)(-pad));
+  W.c0 = max(c0, (long long)(-pad));
+  const long long COLS = 64ll * W.W;
+  W.clo = (int)max(0ll, (long long)(-pad) - W.c0);
+  W.chi = (int)min(COLS, W.ncol_lat + pad - W.c0);
+  W.rlo = (int)max(0ll, (long long)(-pad) - W.r0);
+  W.rhi = (int)min((long long)W.R, W.nrow_lat + pad - W.r0);
+  return W;
+}
+
 __device__ __forceinline__ void site_of(const Win& W, int r, int c, long long& i, long long& j) {
   if (W.trans) {
     j = W.r0 + r;
@@ -566,6 +720,10 @@ __device__ __forceinline__ void site_of(const Win& W, int r, int c, long long& i
     i = W.r0 + r;
     j = W.c0 + c;
   }
+}
+
+__device__ __forceinline__ unsigned long long valid_mask(const Win& W, int r, int w) {
+  return (r >= W.rlo && r < W.rhi) ? col_mask(w, W.clo, W.chi) : 0ull;
 }
 
 __device__ __forceinline__ unsigned long long dilate(const unsigned long long* comp, const Win& W, int q) {
@@ -579,15 +737,39 @@ __device__ __forceinline__ unsigned long long dilate(const unsigned long long* c
   return d;
 }
 
+// Sites worth testing ahead of the component in word q: the word's column
+// within AHEAD rows of it, the whole word if its row neighbours hold some.
+__device__ __forceinline__ unsigned long long ahead(const unsigned long long* comp, const Win& W, int q) {
+  const int r = q / W.W, w = q - r * W.W;
+  unsigned long long d = dilate(comp, W, q);
+  for (int k = 2; k <= AHEAD; k++) {
+    if (r - k >= 0) d |= comp[q - k * W.W];
+    if (r + k < W.R) d |= comp[q + k * W.W];
+  }
+  if ((w > 0 && comp[q - 1]) || (w < W.W - 1 && comp[q + 1])) d = ~0ull;
+  return d;
+}
+
+// Flood fill of the elements queued by the previous tier, one element per
+// block at a time.  Each round lists the words near the component that hold
+// untested sites (AHEAD rows ahead, so that a component growing across the
+// rows needs few rounds), tests them whole, and closes the component through
+// the passing sites to a fixed point.  The loop ends when no site next to
+// the component is untested or passing outside it.  kGlobal: the window is
+// the whole padded lattice, its masks in a zeroed global scratch of the
+// block, cleared again (over the touched box) before the next element.
+template <bool kGlobal>
 __global__ void __launch_bounds__(BT) k_claim_big(Grid g, const double* __restrict__ tay,
                                                   const float* __restrict__ tayf, Slots Sin, float alo, float ahi,
                                                   const int2* __restrict__ list_in, const int* __restrict__ n_in,
                                                   int* __restrict__ stat, int2* __restrict__ list_out,
-                                                  int* __restrict__ n_out) {
+                                                  int* __restrict__ n_out, unsigned long long* __restrict__ gwin,
+                                                  size_t gwin_words) {
   const Slots S = with_epoch(Sin);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BigHeader& H = *reinterpret_cast<BigHeader*>(smem_raw);
-  unsigned long long* bits = reinterpret_cast<unsigned long long*>(smem_raw + sizeof(BigHeader));
+  unsigned long long* bits = kGlobal ? gwin + (size_t)blockIdx.x * gwin_words
+                                     : reinterpret_cast<unsigned long long*>(smem_raw + sizeof(BigHeader));
   const int tid = threadIdx.x;
   const int pad = g.pad;
   const int n = *n_in;
@@ -595,45 +777,23 @@ __global__ void __launch_bounds__(BT) k_claim_big(Grid g, const double* __restri
     const int m = list_in[item].x;
     if (m < 0 || m >= g.ne) continue;  // (never expected; keeps every index in bounds)
     const int sides = list_in[item].y >> 4, attempt = list_in[item].y & 15;
-    const int mode = mode_for(sides, attempt);
+    const int mode = kGlobal ? MODE_GLOBAL : mode_for(sides, attempt);
     load_elem9(g, m, tay, tayf, H.E);
     __syncthreads();
     long long i0 = 0, j0 = 0;
     start_site(g, H.E, i0, j0);  // inside the padded lattice: tier 1 checked it
     set_offsets(H.E, i0, j0);
-    Win W;
-    W.trans = (mode == MODE_BAND_X);
-    const long long along0 = W.trans ? i0 : j0, across0 = W.trans ? j0 : i0;
-    W.nrow_lat = W.trans ? g.nv : g.nx;
-    W.ncol_lat = W.trans ? g.nx : g.nv;
-    if (mode == MODE_FAT) {
-      W.R = FAT_R;
-      W.W = FAT_W;
-      W.r0 = across0 - FAT_R / 2;
-      W.c0 = along0 - 32 * FAT_W;
-    } else {
-      W.R = BAND_R;
-      W.W = band_words(W.ncol_lat, pad);
-      W.r0 = across0 - BAND_R / 2;
-      // centred on the start, kept inside the padded lattice
-      long long c0 = along0 - 32ll * W.W;
-      const long long hi = W.ncol_lat + pad - 64ll * W.W;
-      if (c0 > hi) c0 = hi;
-      if (c0 < -pad) c0 = -pad;
-      W.c0 = c0;
-    }
-    const int COLS = 64 * W.W;
-    W.clo = (int)max(0ll, (long long)(-pad) - W.c0);
-    W.chi = (int)min((long long)COLS, W.ncol_lat + pad - W.c0);
-    W.rlo = (int)max(0ll, (long long)(-pad) - W.r0);
-    W.rhi = (int)min((long long)W.R, W.nrow_lat + pad - W.r0);
+    const Win W = make_window(mode, g, i0, j0);
     const int NW = W.R * W.W;
     unsigned long long* comp = bits;
     unsigned long long* eval = bits + NW;
     unsigned long long* pass = bits + 2 * NW;
-    for (int q = tid; q < 3 * NW; q += BT) bits[q] = 0ull;
+    if (!kGlobal) {
+      for (int q = tid; q < 3 * NW; q += BT) bits[q] = 0ull;
+    }
     __syncthreads();
     const Ctx9 c = ctx_of(g, H.E, alo, ahi);
+    const long long across0 = W.trans ? j0 : i0, along0 = W.trans ? i0 : j0;
     const int rs = (int)(across0 - W.r0), cs = (int)(along0 - W.c0);
     if (tid == 0) {
       const bool ok = test_site(g, H.E, c, i0, j0, i0, j0);
@@ -644,94 +804,135 @@ __global__ void __launch_bounds__(BT) k_claim_big(Grid g, const double* __restri
       if (ok) {
         pass[q] |= 1ull << (cs & 63);
         comp[q] |= 1ull << (cs & 63);
-        claim(S, g, i0, j0, m);
       }
       H.ok = ok;
     }
     __syncthreads();
+    bool escaped = false;
     if (H.ok) {
       for (int it = 0; it < NW * 64; it++) {
         if (tid == 0) H.nlist = 0;
-        // only the words within one word/row of the component can change
-        const int ra = max(H.rmin - 1, 0), rb = min(H.rmax + 1, W.R - 1);
+        const int ra = max(H.rmin - AHEAD, 0), rb = min(H.rmax + AHEAD, W.R - 1);
         const int wa = max(H.wmin - 1, 0), wb = min(H.wmax + 1, W.W - 1);
         const int bw = wb - wa + 1, nbox = (rb - ra + 1) * bw;
         __syncthreads();
-        // A: growth candidates; words needing tests are listed
-        bool act = false;
+        // A: is the component open (an untested or passing site next to
+        // it)?  List the words with untested sites near it, marking them
+        // evaluated now (the list keeps which sites to test).
+        bool open = false;
         for (int e = tid; e < nbox; e += BT) {
           const int r = ra + e / bw, w = wa + e % bw, q = r * W.W + w;
-          const unsigned long long valid = (r >= W.rlo && r < W.rhi) ? col_mask(w, W.clo, W.chi) : 0ull;
-          const unsigned long long gr = dilate(comp, W, q) & ~comp[q] & valid;
-          if (gr & ~eval[q]) {
-            act = true;
+          const unsigned long long valid = valid_mask(W, r, w);
+          const unsigned long long ev = eval[q];
+          const unsigned long long near = dilate(comp, W, q) & ~comp[q] & valid;
+          if (near & (~ev | pass[q])) open = true;
+          const unsigned long long todo = ahead(comp, W, q) & valid & ~ev;
+          if (todo) {
             const int slot = atomicAdd(&H.nlist, 1);
-            if (slot < LIST_CAP) H.list[slot] = q;
-          } else if (gr & pass[q]) {
-            act = true;
+            if (slot < LIST_CAP) {
+              H.list[slot] = q;
+              H.lmask[slot] = todo;
+              eval[q] = ev | todo;
+            }
           }
         }
-        if (!__syncthreads_or(act)) break;
-        // B: test every still-untested valid site of the listed words
+        if (!__syncthreads_or(open)) break;
+        // B: the listed sites' tests
         const int nl = min(H.nlist, LIST_CAP);
         for (int e = tid; e < nl * 64; e += BT) {
-          const int q = H.list[e >> 6], b = e & 63;
+          const int s = e >> 6, b = e & 63;
+          if (!((H.lmask[s] >> b) & 1ull)) continue;
+          const int q = H.list[s];
           const int r = q / W.W, w = q - r * W.W;
-          const unsigned long long valid = (r >= W.rlo && r < W.rhi) ? col_mask(w, W.clo, W.chi) : 0ull;
-          if (!(((valid & ~eval[q]) >> b) & 1ull)) continue;
           long long i, j;
           site_of(W, r, 64 * w + b, i, j);
           if (test_site(g, H.E, c, i0, j0, i, j)) atomicOr(&pass[q], 1ull << b);
         }
         __syncthreads();
-        for (int e = tid; e < nl; e += BT) {
-          const int q = H.list[e];
-          const int r = q / W.W, w = q - r * W.W;
-          eval[q] |= (r >= W.rlo && r < W.rhi) ? col_mask(w, W.clo, W.chi) : 0ull;
+        // C: close the component through the passing sites (runs inside a
+        // word at once, one row or word boundary per pass).  A word may see
+        // its neighbours' growth of the same pass; that only adds connected
+        // passing sites earlier, so the fixed point is the same.
+        for (int p = 0; p < NW * 64; p++) {
+          const int ca = max(H.rmin - 1, 0), cb = min(H.rmax + 1, W.R - 1);
+          const int da = max(H.wmin - 1, 0), db = min(H.wmax + 1, W.W - 1);
+          const int cw_ = db - da + 1, cbox = (cb - ca + 1) * cw_;
+          __syncthreads();
+          bool grew = false;
+          for (int e = tid; e < cbox; e += BT) {
+            const int r = ca + e / cw_, w = da + e % cw_, q = r * W.W + w;
+            const unsigned long long cw = comp[q];
+            const unsigned long long seeds = dilate(comp, W, q) & ~cw & pass[q];
+            if (!seeds) continue;
+            comp[q] = cw | run_fill(seeds | cw, pass[q]);
+            grew = true;
+            atomicMin(&H.rmin, r);
+            atomicMax(&H.rmax, r);
+            atomicMin(&H.wmin, w);
+            atomicMax(&H.wmax, w);
+          }
+          if (!__syncthreads_or(grew)) break;
         }
-        __syncthreads();
-        // C: extend the component through passing runs inside each word.  A
-        // word may see its neighbours' growth of this same phase; that only
-        // adds connected passing sites earlier, so the fixed point is the same.
+      }
+      // escaped this window?  (component bits on an edge that is not the
+      // padded lattice's)
+      bool esc = false;
+      if (!kGlobal) {
+        if (tid == 0) {
+          esc = (H.rmin == 0 && W.rlo == 0 && W.r0 - 1 >= -pad) ||
+                (H.rmax == W.R - 1 && W.rhi == W.R && W.r0 + W.R < W.nrow_lat + pad);
+        }
+        const bool left = H.wmin == 0 && W.clo == 0 && W.c0 - 1 >= -pad;
+        const bool right = H.wmax == W.W - 1 && W.chi == 64 * W.W && W.c0 + 64ll * W.W < W.ncol_lat + pad;
+        for (int r = H.rmin + tid; r <= H.rmax; r += BT) {
+          if (left && (comp[r * W.W] & 1ull)) esc = true;
+          if (right && (comp[r * W.W + W.W - 1] >> 63)) esc = true;
+        }
+      }
+      escaped = __syncthreads_or(esc);
+      if (escaped) {
+        // the next, larger window claims a superset of this component
+        if (tid == 0) {
+          if (list_out != nullptr)
+            list_out[atomicAdd(n_out, 1)] = make_int2(m, (sides << 4) | (attempt + 1));
+          else
+            atomicOr(&S.ds->err, ERR_PATCH_OVERFLOW);
+        }
+      } else {
+        // claims, a word per thread, several exchanges in flight
+        const int bw = H.wmax - H.wmin + 1, nbox = (H.rmax - H.rmin + 1) * bw;
         for (int e = tid; e < nbox; e += BT) {
-          const int q = (ra + e / bw) * W.W + wa + e % bw;
-          const unsigned long long cw = comp[q];
-          const unsigned long long seeds = dilate(comp, W, q) & ~cw & pass[q];
-          if (!seeds) continue;
-          const unsigned long long nw = run_fill(seeds | cw, pass[q]);
-          unsigned long long add = nw & ~cw;
-          comp[q] = cw | nw;
-          const int r = q / W.W, w = q - r * W.W;
-          atomicMin(&H.rmin, r);
-          atomicMax(&H.rmax, r);
-          atomicMin(&H.wmin, w);
-          atomicMax(&H.wmax, w);
-          while (add) {
-            const int b = __ffsll((long long)add) - 1;
-            add &= add - 1ull;
-            long long i, j;
-            site_of(W, r, 64 * w + b, i, j);
-            claim(S, g, i, j, m);
+          const int r = H.rmin + e / bw, w = H.wmin + e % bw;
+          unsigned long long cb = comp[r * W.W + w];
+          while (cb) {
+            size_t pos[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+              pos[u] = ~(size_t)0;
+              if (cb) {
+                const int b = __ffsll((long long)cb) - 1;
+                cb &= cb - 1ull;
+                long long i, j;
+                site_of(W, r, 64 * w + b, i, j);
+                if (i >= 0 && i < g.nx && j >= 0 && j < g.nv) pos[u] = (size_t)i * g.nv + j;
+              }
+            }
+            claim_sites(S, g, pos, m);
           }
         }
-        __syncthreads();
       }
-      // escaped this window as well?
-      bool esc = false;
-      for (int q = tid; q < NW; q += BT) {
-        const unsigned long long cw = comp[q];
-        if (!cw) continue;
-        const int r = q / W.W, w = q - r * W.W;
-        if (r == 0 && W.rlo == 0 && W.r0 - 1 >= -pad) esc = true;
-        if (r == W.R - 1 && W.rhi == W.R && W.r0 + W.R < W.nrow_lat + pad) esc = true;
-        if (w == 0 && (cw & 1ull) && W.clo == 0 && W.c0 - 1 >= -pad) esc = true;
-        if (w == W.W - 1 && (cw >> 63) && W.chi == COLS && W.c0 + COLS < W.ncol_lat + pad) esc = true;
-      }
-      if (__syncthreads_or(esc) && tid == 0) {
-        if (list_out != nullptr)
-          list_out[atomicAdd(n_out, 1)] = make_int2(m, (sides << 4) | (attempt + 1));
-        else
-          atomicOr(&S.ds->err, ERR_PATCH_OVERFLOW);
+    }
+    if (kGlobal) {
+      // every word written lies within AHEAD rows and one word of the box
+      __syncthreads();
+      const int ra = max(H.rmin - AHEAD, 0), rb = min(H.rmax + AHEAD, W.R - 1);
+      const int wa = max(H.wmin - 1, 0), wb = min(H.wmax + 1, W.W - 1);
+      const int bw = wb - wa + 1, nbox = (rb - ra + 1) * bw;
+      for (int e = tid; e < nbox; e += BT) {
+        const int q = (ra + e / bw) * W.W + wa + e % bw;
+        comp[q] = 0ull;
+        eval[q] = 0ull;
+        pass[q] = 0ull;
       }
     }
     __syncthreads();
@@ -749,15 +950,17 @@ __device__ __forceinline__ unsigned long long exact_key(const Grid& g, const dou
   return dkey(dist2_exact(tay + (size_t)m * TY_N, g, Px, Pv, xi, ze));
 }
 
-// Contested sites: the record's minimum is the owner.
+// Contested sites: the record's minimum is the owner; the record and the
+// flag are emptied for the next map.
 __global__ void k_resolve(Grid g, Slots Sin) {
   const Slots S = with_epoch(Sin);
   const int n = min(S.ds->nrec, S.rec_cap);
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-    const int p = S.rec_site[r];
-    if (p < 0) continue;
-    const unsigned long long win = S.rec_key[2 * (size_t)r];
+    const size_t p = (size_t)S.rec_site[r];
+    const unsigned long long win = S.rec_key[2 * p];
     S.slot0[p] = (S.epoch << 24) | (uint32_t)win;
+    S.rec_key[2 * p] = KEY_EMPTY;
+    S.rec_key[2 * p + 1] = KEY_EMPTY;
     S.slot1[p] = SLOT_EMPTY;
   }
 }
@@ -845,9 +1048,14 @@ __global__ void k_read_map(const uint32_t* __restrict__ slot0, const DevState* d
 }
 
 size_t big_smem_bytes(const Grid& g) {
-  long long nw = FAT_R * FAT_W;
-  nw = max(nw, (long long)BAND_R * band_words(g.nv, g.pad));
-  nw = max(nw, (long long)BAND_R * band_words(g.nx, g.pad));
+  long long nw = 0;
+  int R, W;
+  window_dims(MODE_FAT, g.nx, g.nv, g.pad, R, W);
+  nw = max(nw, (long long)R * W);
+  window_dims(MODE_BAND_V, g.nx, g.nv, g.pad, R, W);
+  nw = max(nw, (long long)R * W);
+  window_dims(MODE_BAND_X, g.nv, g.nx, g.pad, R, W);
+  nw = max(nw, (long long)R * W);
   return sizeof(BigHeader) + 3 * (size_t)nw * sizeof(unsigned long long);
 }
 
@@ -865,7 +1073,7 @@ void alpha_bounds(double alpha, float& lo, float& hi) {
 // largest size any grid can ask for rather than to this grid's need.
 bool map_prepare(const Grid& g) {
   if (big_smem_bytes(g) > SMEM_MAX) return false;
-  return cudaFuncSetAttribute(k_claim_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX) ==
+  return cudaFuncSetAttribute(k_claim_big<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX) ==
          cudaSuccess;
 }
 
@@ -882,16 +1090,29 @@ void launch_map(vm_solver* s) {
   prof_end(s, ps);
   const size_t smem = big_smem_bytes(s->g);
   DevState* d = s->ds;
+  // Blocks of the large windows: the elements that can escape tier 1 are
+  // few on a small lattice, and an idle block still takes a whole SM.
+  const unsigned big1 = (unsigned)std::min<long long>(2 * 152, std::max<long long>(16, s->g.ne / 16));
+  const unsigned big2 = (unsigned)std::min<long long>(152, big1);
+  const unsigned bigG = (unsigned)std::min<long long>(kGlobalBlocks, big1);
   ps = prof_begin(s, KID_CLAIM_LARGE);
-  k_claim_big<<<2 * 152, BT, smem, s->stream>>>(s->g, s->tay, s->tayf, S, alo, ahi, s->overflow_list,
-                                                &d->noverflow, &d->overflow_stat, s->overflow_list2, &d->noverflow2);
-  k_claim_big<<<152, BT, smem, s->stream>>>(s->g, s->tay, s->tayf, S, alo, ahi, s->overflow_list2, &d->noverflow2,
-                                            &d->overflow2_stat, s->overflow_list, &d->noverflow3);
-  k_claim_big<<<152, BT, smem, s->stream>>>(s->g, s->tay, s->tayf, S, alo, ahi, s->overflow_list, &d->noverflow3,
-                                            &d->overflow3_stat, nullptr, nullptr);
+  if (s->cfg.map_windows == 0) {
+    k_claim_big<false><<<big1, BT, smem, s->stream>>>(s->g, s->tay, s->tayf, S, alo, ahi, s->overflow_list,
+                                                         &d->noverflow, &d->overflow_stat, s->overflow_list2,
+                                                         &d->noverflow2, nullptr, 0);
+    k_claim_big<false><<<big2, BT, smem, s->stream>>>(s->g, s->tay, s->tayf, S, alo, ahi, s->overflow_list2,
+                                                     &d->noverflow2, &d->overflow2_stat, s->overflow_list,
+                                                     &d->noverflow3, nullptr, 0);
+  }
+  // tier-1 escapes go straight here when the shared-memory windows are off
+  int* n_last = s->cfg.map_windows == 0 ? &d->noverflow3 : &d->noverflow;
+  int* stat_last = s->cfg.map_windows == 0 ? &d->overflow3_stat : &d->overflow_stat;
+  k_claim_big<true><<<bigG, BT, sizeof(BigHeader), s->stream>>>(
+      s->g, s->tay, s->tayf, S, alo, ahi, s->overflow_list, n_last, stat_last, nullptr, nullptr, s->gwin,
+      global_window_words(s->g.nx, s->g.nv, s->g.pad));
   prof_end(s, ps);
   ps = prof_begin(s, KID_RESOLVE);
-  k_resolve<<<152, 256, 0, s->stream>>>(s->g, S);
+  k_resolve<<<(unsigned)std::min<size_t>(152, (s->n + 1023) / 1024), 256, 0, s->stream>>>(s->g, S);
   prof_end(s, ps);
   unsigned nb = (unsigned)((s->n + 255) / 256);
   if (nb > 152 * 16) nb = 152 * 16;
@@ -901,7 +1122,7 @@ void launch_map(vm_solver* s) {
   ps = prof_begin(s, KID_HOLES);
   k_holes<<<1, HT, 0, s->stream>>>(s->g, s->tay, s->map, s->holes_a, s->holes_b, s->holes_b + s->n, s->ds);
   prof_end(s, ps);
-  s->launches += 9;
+  s->launches += s->cfg.map_windows == 0 ? 9 : 7;
 }
 
 void launch_read_map(vm_solver* s, int32_t* dst) {

@@ -243,15 +243,13 @@ __device__ __forceinline__ void p_of(const float* __restrict__ F, int i, int j, 
 }
 
 // The lattice index position of Q_m (a multiple of 1/2): integer part and
-// half flag, exactly.
-__device__ __forceinline__ void anchor(const Grid& g, int m, int& Bu, float& bu, int& Bw, float& bw) {
-  const int k = m / g.Lv, l = m - k * g.Lv;
-  const int u2 = (g.nx - 1) + 2 * (k - g.Kx - 1) * g.s;  // 2 * index of Q_m,x
-  const int w2 = (g.nv - 1) + 2 * (l - g.Kv - 1) * g.s;
-  Bu = u2 >> 1;  // floor
-  bu = (u2 & 1) ? 0.5f : 0.f;
-  Bw = w2 >> 1;
-  bw = (w2 & 1) ? 0.5f : 0.f;
+// half, exactly, from the element's FP32 record.
+__device__ __forceinline__ void anchor(const float* __restrict__ F, int& Bu, float& bu, int& Bw, float& bw) {
+  const int* Fi = reinterpret_cast<const int*>(F);
+  Bu = Fi[TF_BU];
+  Bw = Fi[TF_BW];
+  bu = F[TF_HU];
+  bw = F[TF_HW];
 }
 
 // Is floor(x) certain for every value within e of x?
@@ -265,7 +263,21 @@ __device__ __forceinline__ float F_at32(const float* __restrict__ F, const Grid&
   return __ldg(F + (size_t)i * g.nv + j);
 }
 
-// Six-point quadratic interpolation from the node choice and the offsets.
+// Six-point quadratic interpolation from the node choice and the offsets;
+// the stencil entirely inside the grid (1 <= in <= nx-2, 1 <= jn <= nv-2;
+// ic and jc are in-1 or in, jn-1 or jn).
+__device__ __forceinline__ float qinterp32_in(const float* __restrict__ F, const Grid& g, int in, int jn, int ic,
+                                              int jc, float x, float y) {
+  const float* c = F + (size_t)in * g.nv + jn;
+  const float* d = F + (size_t)ic * g.nv + jc;
+  float f = __ldg(c) * (1.0f - x * x - y * y);
+  f += 0.5f * x * (__ldg(c + g.nv) * (1.0f + x) + __ldg(c - g.nv) * (x - 1.0f));
+  f += 0.5f * y * (__ldg(c + 1) * (1.0f + y) + __ldg(c - 1) * (y - 1.0f));
+  f += (__ldg(d + g.nv + 1) + __ldg(d) - __ldg(d + g.nv) - __ldg(d + 1)) * x * y;
+  return f;
+}
+
+// The same with every node checked (outside the grid f is 0).
 __device__ __forceinline__ float qinterp32(const float* __restrict__ F, const Grid& g, int in, int jn, int ic, int jc,
                                            float x, float y) {
   float f = F_at32(F, g, in, jn) * (1.0f - x * x - y * y);
@@ -310,7 +322,7 @@ __global__ void __launch_bounds__(256) k_recon32(Grid g, const uint32_t* __restr
       const QF q = qeval(F, px, pv);
       int Bu, Bw;
       float bu, bw;
-      anchor(g, m, Bu, bu, Bw, bw);
+      anchor(F, Bu, bu, Bw, bw);
       // index coordinates of Q relative to the anchor
       const float ru = bu + fs * q.qx, rw = bw + fs * q.qv;
       const float eu = fs * q.ex + 1e-6f * (1.f + fabsf(ru)), ew = fs * q.ev + 1e-6f * (1.f + fabsf(rw));
@@ -347,7 +359,10 @@ __global__ void __launch_bounds__(256) k_recon32(Grid g, const uint32_t* __restr
           y = (float)dsub(w, (double)jn);
         }
       }
-      if (in > -2 && in < g.nx + 2 && jn > -2 && jn < g.nv + 2) val = qinterp32(fini, g, in, jn, ic, jc, x, y);
+      if (in >= 1 && in <= g.nx - 2 && jn >= 1 && jn <= g.nv - 2)
+        val = qinterp32_in(fini, g, in, jn, ic, jc, x, y);
+      else if (in > -2 && in < g.nx + 2 && jn > -2 && jn < g.nv + 2)
+        val = qinterp32(fini, g, in, jn, ic, jc, x, y);
     }
     f[p] = val;
     acc.add(val);
@@ -427,7 +442,7 @@ __global__ void __launch_bounds__(256) k_remap32(Grid g, const uint32_t* __restr
       const int ra = beta_range_f(q.qx, q.ex, blo, bhi), rb = beta_range_f(q.qv, q.ev, blo, bhi);
       int Bu, Bw;
       float bu, bw;
-      anchor(g, m, Bu, bu, Bw, bw);
+      anchor(F, Bu, bu, Bw, bw);
       float ru, rw;
       if (ra && rb) {
         // Q_r - Q_m in element units, blended over the beta set (Sec. 2.3.2)

@@ -34,6 +34,7 @@ class Request:
     admitted: float = math.nan
     finished: float = math.nan
     result: dict = field(default_factory=dict)
+    error: str = ""           # set if the solve failed (its result is then empty)
 
     @property
     def latency(self) -> float:
@@ -132,12 +133,20 @@ class Server:
     def _tick(self) -> None:
         for req, handle, _ in self.active:
             left = handle["left"]
-            if left > 0:
-                self.backend.advance(handle, min(self.steps_per_tick, left))
+            if left > 0 and not req.error:
+                try:
+                    self.backend.advance(handle, min(self.steps_per_tick, left))
+                except Exception as e:  # noqa: BLE001
+                    req.error = f"{type(e).__name__}: {e}"
         still = []
         for req, handle, need in self.active:
-            if handle["left"] == 0 and self.backend.done(handle):
-                req.result = self.backend.result(handle)
+            if req.error or (handle["left"] == 0 and self.backend.done(handle)):
+                # a failed solve is reported on its request; the others go on
+                if not req.error:
+                    try:
+                        req.result = self.backend.result(handle)
+                    except Exception as e:  # noqa: BLE001
+                        req.error = f"{type(e).__name__}: {e}"
                 req.finished = self.now()
                 self.backend.release(handle)
                 self.used -= need
@@ -169,7 +178,8 @@ class Server:
                 return math.nan
             k = min(len(lat) - 1, max(0, int(math.ceil(p / 100.0 * len(lat))) - 1))
             return lat[k]
-        return {"requests": len(self.done), "wall_s": wall, "cell_updates_per_s": cells / wall if wall > 0 else math.nan,
+        return {"requests": len(self.done), "failed": sum(1 for r in self.done if r.error),
+                "wall_s": wall, "cell_updates_per_s": cells / wall if wall > 0 else math.nan,
                 "p50_latency_s": pct(50), "p99_latency_s": pct(99),
                 "mean_latency_s": statistics.fmean(lat) if lat else math.nan,
                 "peak_active": self.peak_active, "peak_bytes": self.peak_used}

@@ -30,7 +30,8 @@ EXPORTS = ["vm_config_default", "vm_workspace_bytes", "vm_create", "vm_destroy",
            "vm_reconstruct", "vm_step", "vm_remap", "vm_density_force", "vm_read_f", "vm_read_fini",
            "vm_read_eta", "vm_read_map", "vm_diagnostics", "vm_sync", "vm_launch_count",
            "vm_profile", "vm_profile_read", "vm_force_from_f_static",
-           "vm_batch_create", "vm_batch_step", "vm_batch_launches_per_step", "vm_batch_destroy"]
+           "vm_batch_create", "vm_batch_step", "vm_batch_launches_per_step", "vm_batch_destroy",
+           "vm_last_cuda_error", "vm_cuda_error_name"]
 
 VM_STATIC_FORCE_MAX_NX = 16384
 
@@ -42,14 +43,15 @@ class VmConfig(C.Structure):
         ("elem_stride", C.c_int32), ("dt", C.c_double), ("n_s", C.c_int32), ("G", C.c_double),
         ("precision", C.c_int32), ("alpha", C.c_double), ("beta", C.c_double),
         ("pad", C.c_int32), ("literal_fd", C.c_int32), ("max_hole_rounds", C.c_int32),
-        ("reserved", C.c_int32),
+        ("map_windows", C.c_int32),
     ]
 
 
 class VmDiag(C.Structure):
     _fields_ = [("mass", C.c_double), ("energy", C.c_double), ("detT_min", C.c_double),
                 ("detT_max", C.c_double), ("step", C.c_int64), ("cycle", C.c_int32),
-                ("holes", C.c_int32), ("hole_rounds", C.c_int32), ("overflow_elements", C.c_int32)]
+                ("holes", C.c_int32), ("hole_rounds", C.c_int32), ("overflow_elements", C.c_int32),
+                ("tier1_more", C.c_int32), ("last_tier_elements", C.c_int32)]
 
 
 class VmKernelStat(C.Structure):
@@ -104,6 +106,8 @@ def load() -> C.CDLL:
         "vm_batch_step": (i32, [vp, i32]),
         "vm_batch_launches_per_step": (i64, [vp, i32]),
         "vm_batch_destroy": (None, [vp]),
+        "vm_last_cuda_error": (i32, []),
+        "vm_cuda_error_name": (C.c_char_p, [i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -115,6 +119,11 @@ def load() -> C.CDLL:
 
 def _check(st: int, where: str) -> None:
     if st != 0:
+        if st == 3:
+            L = load()
+            code = int(L.vm_last_cuda_error())
+            name = L.vm_cuda_error_name(code)
+            where = f"{where} [{name.decode() if name else code}]"
         raise VlametError(st, where)
 
 
@@ -136,6 +145,7 @@ class Config:
     pad: int = 0
     literal_fd: int = 0
     max_hole_rounds: int = 0
+    map_windows: int = 0
 
     @classmethod
     def from_run(cls, rc, precision: int = VM_FP64) -> "Config":
@@ -144,7 +154,7 @@ class Config:
     def c(self) -> VmConfig:
         return VmConfig(self.nx, self.nv, self.x_lo, self.x_hi, self.v_lo, self.v_hi, self.s, self.dt,
                         self.n_s, self.G, self.precision, self.alpha, self.beta, self.pad, self.literal_fd,
-                        self.max_hole_rounds, 0)
+                        self.max_hole_rounds, self.map_windows)
 
 
 def workspace_bytes(cfg: Config) -> int:

@@ -96,6 +96,31 @@ def test_map_bit_exact_on_injected_elements(prec, steps):
         assert d["overflow_elements"] > 0      # the large-window path ran
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("steps", [40, 150])
+def test_map_bit_exact_with_the_whole_lattice_window_alone(prec, steps):
+    """Components leaving the 32 x 64 window go straight to the last tier
+    (whole padded lattice, masks in global memory)."""
+    rc = I.SPITZER_128
+    s, o = make(rc, prec, map_windows=1)
+    f0 = I.initial_f(rc)
+    s.set_f(f0)
+    o.set_f(f0)
+    el, _ = evolved_state(rc, steps)
+    o.set_elements(el)
+    s.set_elements(np.ascontiguousarray(el.T))
+    for _ in range(2):          # the second map reuses the cleared masks
+        s.compute_map()
+        s.sync()
+        mo, st = o.compute_map()
+        assert st == 0
+        mg = s.read_map()
+        assert (mg == mo).all(), f"{(mg != mo).sum()} sites differ"
+    d = s.diagnostics()
+    if steps == 150:
+        assert d["overflow_elements"] > 0 and d["last_tier_elements"] == d["overflow_elements"]
+
+
 @pytest.mark.parametrize("shape,s_", [((67, 45), 4), ((33, 33), 4), ((4, 4), 1), ((100, 37), 3)])
 def test_map_ragged_and_tie_shapes(shape, s_):
     nx, nv = shape
@@ -279,9 +304,12 @@ def test_halos_4096_first_step_full_grid(prec):
     assert (s.read_map() == mo).all()
 
 
-def test_halos_4096_remap_after_a_cycle_full_grid():
+@pytest.mark.parametrize("windows", [0, 1])
+def test_halos_4096_remap_after_a_cycle_full_grid(windows):
     rc = I.HALOS_4096
-    s = V.Solver(V.Config.from_run(rc.with_(n_s=10 ** 6)))
+    cfg = V.Config.from_run(rc.with_(n_s=10 ** 6))
+    cfg.map_windows = windows
+    s = V.Solver(cfg)
     f0 = I.initial_f(rc)
     s.set_f(f0)
     s.step(rc.n_s - 1)
@@ -297,3 +325,28 @@ def test_halos_4096_remap_after_a_cycle_full_grid():
     s.remap()
     s.sync()
     assert_f_close(s.read_fini(), fo)
+
+
+# ---------------------------------------------------------------------------
+# 8192^2: boundary components longer than every shared-memory window
+# ---------------------------------------------------------------------------
+
+def test_halos_8192_map_after_a_cycle_full_grid():
+    rc = I.HALOS_8192
+    s = V.Solver(V.Config.from_run(rc.with_(n_s=10 ** 6), V.VM_FP32_MIXED))
+    f0 = I.initial_f(rc)
+    s.set_f(f0)
+    s.step(rc.n_s - 1)
+    s.sync()
+    el = s.elements()
+    o = O.Oracle(rc.nx, rc.nv, rc.x_lo, rc.x_hi, rc.v_lo, rc.v_hi, rc.s, rc.dt, rc.n_s, rc.G)
+    o.set_f(f0)
+    o.set_elements(np.ascontiguousarray(el.T))
+    s.compute_map()
+    s.sync()
+    d = s.diagnostics()
+    mo, st = o.compute_map()
+    assert st == 0
+    mg = s.read_map()
+    assert (mg == mo).all(), f"{(mg != mo).sum()} sites differ"
+    assert d["overflow_elements"] > 0

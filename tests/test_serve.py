@@ -107,3 +107,35 @@ def test_poisson_requests_are_seeded():
     assert all(256 <= nx <= 2048 and nx % 32 == 0 for nx, _ in (r.config for r in a))
     arr = [r.arrival for r in a]
     assert arr == sorted(arr) and not math.isnan(arr[-1])
+
+
+def test_a_failed_solve_is_reported_and_the_rest_complete():
+    clock = FakeClock()
+
+    class Failing(FakeBackend):
+        def result(self, h):
+            if h["rid"] == 2:
+                raise RuntimeError("device status 5")
+            return super().result(h)
+
+    srv = Server(Failing(clock), budget_bytes=10 ** 6, max_active=4, clock=clock)
+    rep = srv.run([Request(i, (4, 4), steps=2 + i, arrival=0.0) for i in range(5)])
+    assert rep["requests"] == 5 and rep["failed"] == 1
+    bad = [r for r in srv.done if r.error]
+    assert [r.rid for r in bad] == [2] and "status 5" in bad[0].error and bad[0].result == {}
+    assert srv.used == 0
+
+
+def test_a_solve_that_fails_while_stepping_is_retired():
+    clock = FakeClock()
+
+    class Failing(FakeBackend):
+        def advance(self, h, n):
+            if h["rid"] == 1 and h["left"] < 4:
+                raise RuntimeError("vm_step: CUDA runtime error")
+            super().advance(h, n)
+
+    srv = Server(Failing(clock), budget_bytes=10 ** 6, max_active=2, clock=clock)
+    rep = srv.run([Request(i, (4, 4), steps=6, arrival=0.0) for i in range(4)])
+    assert rep["requests"] == 4 and rep["failed"] == 1
+    assert [r.rid for r in srv.done if r.error] == [1] and srv.used == 0
