@@ -118,16 +118,47 @@ def algorithmic(kernel: str, rc, fp32: bool, ne: int):
         return n * (4 + 2 * sr) + ne * tay, n, f"{4 + 2 * sr} B/site + 128 B/element"
     if kernel == "remap_resample":
         return n * (4 + 2 * sr) + ne * tay, n, f"{4 + 2 * sr} B/site + 128 B/element"
-    if kernel == "claim_small":
-        # Taylor records of the 3x3 neighbourhood, one 16 B key read+write per site
-        return n * 32 + ne * 9 * tay, n, "32 B/site + 1152 B/element"
-    if kernel == "map_finalize":
-        return n * (16 + 16 + 4), n, "36 B/site"
+    if kernel in ("claim_small", "claim_large"):
+        # the influence map written once (4 B/site), each element's record read once
+        return n * 4 + ne * tay, n, "4 B/site + 128 B/element"
     if kernel in ("spline_rows", "spline_cols"):
         return n * 4 * sr, n, f"{4 * sr} B/site (2 sweeps, read+write)"
     if kernel in ("drift_taylor", "kick_drift"):
         return ne * (24 * 8 + (tay if kernel == "drift_taylor" else 0)), ne, "element state r+w"
     return None
+
+
+def step_bytes_per_update(rc, fp32: bool) -> float:
+    """Algorithmic bytes of one cell update of the whole step: f_ini read and
+    f written once, the element state read and written once per element
+    (304 B over s^2 sites), the map written and read once (8 B), and the
+    remap's 24 B per site amortised over n_s steps."""
+    sr = 4 if fp32 else 8
+    return 2 * sr + 304.0 / (rc.s * rc.s) + 8 + 24.0 / rc.n_s
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# kernels captured with ncu on the 4096^2 workload (the captures summarised
+# under profiles/), with the SHA-256 prefix of the kernel's source file at the
+# time of the capture: a source changed since makes the figure void (null).
+NCU_TRAFFIC = {
+    # kernel: (bytes per launch, source file, sha256 prefix)
+}
+
+
+def ncu_traffic(kernel: str):
+    ent = NCU_TRAFFIC.get(kernel)
+    if not ent:
+        return None
+    nbytes, src, sha = ent
+    import hashlib
+    path = os.path.join(ROOT, "paper_1705_03750_gb300", "csrc", src)
+    try:
+        with open(path, "rb") as fh:
+            h = hashlib.sha256(fh.read()).hexdigest()
+    except OSError:
+        return None
+    return nbytes if h.startswith(sha) else None
 
 
 # ---------------------------------------------------------------------------
@@ -262,8 +293,12 @@ def run_native(args, rank: int, world: int, dist):
         b, units, per = alg
         ach = b / avg_s / 1e9
         roof.update({"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": ach / peaks["hbm_gbs"], "traffic": None, "per_unit": per, "units": units,
-                     "peak_kind": peak_kind})
+                     "frac": ach / peaks["hbm_gbs"], "traffic": ncu_traffic(dom), "per_unit": per,
+                     "units": units, "peak_kind": peak_kind})
+    # the whole step against the same peak (algorithmic bytes per cell update)
+    bpu = step_bytes_per_update(rc, head["fp32"])
+    step_ach = bpu * cells * K / (head["ms"] / 1e3) / 1e9
+    roof["step"] = {"bytes_per_update": bpu, "achieved": step_ach, "frac": step_ach / peaks["hbm_gbs"]}
     line = {
         "metric": METRIC,
         "value": value,

@@ -53,7 +53,9 @@ typedef enum {
   VM_E_NOT_CONVERGED = 4,  /* unexplored-site repair hit its round cap */
   VM_E_PATCH_OVERFLOW = 5, /* an element's influence region exceeded the largest window */
   VM_E_BUDGET = 6,         /* admission refused by a memory budget (batch/serve layer) */
-  VM_E_STATE = 7           /* call out of order (e.g. a step before vm_set_f) */
+  VM_E_STATE = 7,          /* call out of order (e.g. a step before vm_set_f) */
+  VM_E_INTERNAL = 8        /* an index a kernel read from device state failed its bounds check
+                              (the access was skipped; vm_diag.bad_where says which check) */
 } vm_status;
 
 typedef enum { VM_FP64 = 0, VM_FP32_MIXED = 1 } vm_precision;
@@ -91,6 +93,9 @@ typedef struct {
   int32_t tier1_more;        /* elements whose small-window fill tested sites beyond
                                 the region predicted from the linear part of the map */
   int32_t last_tier_elements; /* elements filled in the whole-lattice window */
+  int32_t exact_tests;       /* small-window site tests the FP32 bound could not settle
+                                (run again in FP64) */
+  int32_t bad_where;         /* first failed bounds check since creation (0: none) */
 } vm_diag;
 
 typedef struct vm_solver vm_solver;

@@ -254,6 +254,7 @@ const char* vm_status_string(vm_status st) {
     case VM_E_INVALID_ARG: return "invalid argument";
     case VM_E_OOM: return "workspace too small";
     case VM_E_CUDA: return "CUDA runtime error";
+    case VM_E_INTERNAL: return "internal consistency check failed";
     case VM_E_NOT_CONVERGED: return "unexplored-site repair did not converge";
     case VM_E_PATCH_OVERFLOW: return "influence region larger than the largest flood-fill window";
     case VM_E_BUDGET: return "memory budget exceeded";
@@ -545,6 +546,7 @@ vm_status vm_sync(vm_solver* s) {
   if (err) {
     VM_CUDA_TRY(cudaMemsetAsync(&s->ds->err, 0, sizeof(int32_t), s->stream));
     VM_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (err & vm::ERR_INTERNAL) return VM_E_INTERNAL;
     if (err & vm::ERR_PATCH_OVERFLOW) return VM_E_PATCH_OVERFLOW;
     if (err & vm::ERR_NOT_CONVERGED) return VM_E_NOT_CONVERGED;
     return VM_E_CUDA;
@@ -582,6 +584,8 @@ vm_status vm_diagnostics(vm_solver* s, vm_diag* d) {
   d->overflow_elements = h.overflow_stat;
   d->tier1_more = h.t1_more;
   d->last_tier_elements = s->cfg.map_windows == 0 ? h.overflow3_stat : h.overflow_stat;
+  d->exact_tests = h.n_exact;
+  d->bad_where = h.bad_where;
   return VM_OK;
 }
 

@@ -12,7 +12,17 @@ namespace vm {
 enum : int32_t {
   ERR_NOT_CONVERGED = 1,
   ERR_PATCH_OVERFLOW = 2,  // an element outgrew every window, or the contested-site records ran out
+  ERR_INTERNAL = 4,        // an index read from device state failed its bounds check (the access was skipped)
 };
+
+// Bounds checks on indices that kernels read from device state (lists,
+// records, owner tags): a failed check sets ERR_INTERNAL, records which
+// check (its number) in DevState::bad_where, and skips the access.
+#define VM_BAD(ds, where)                                 \
+  do {                                                    \
+    atomicOr(&(ds)->err, ERR_INTERNAL);                   \
+    atomicCAS(&(ds)->bad_where, 0, (where));              \
+  } while (0)
 
 // Grid, lattice and method constants, passed by value to every kernel.  All
 // derived doubles are computed once on the host in a fixed order (no fused
@@ -43,6 +53,8 @@ struct DevState {
   int32_t overflow3_stat;
   int32_t nrec;          // records of sites claimed by two or more elements
   int32_t t1_more;       // tier-1 elements that needed tests beyond their predicted region
+  int32_t n_exact;       // tests the FP32 bound left to the exact FP64 test (statistics)
+  int32_t bad_where;     // first failed bounds check (0: none); kept until read by vm_sync
   uint32_t epoch;        // epoch of the current influence map (0..kEpochs-1)
   double Mtot;           // total mass of the last reconstruction
   double sum_mass, sum_kin, sum_pot;

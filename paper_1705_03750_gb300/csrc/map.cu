@@ -222,6 +222,7 @@ __global__ void k_map_begin(DevState* ds) {
     ds->noverflow3 = ds->overflow3_stat = 0;
     ds->nrec = 0;
     ds->t1_more = 0;
+    ds->n_exact = 0;
   }
 }
 
@@ -243,6 +244,10 @@ __device__ __noinline__ void contest(const Slots& S, const Grid& g, long long i,
   const double Px = site_x(g, i), Pv = site_v(g, j);
   double xi, ze;
   const int mo = (int)(displaced & SLOT_MASK);
+  if (mo >= g.ne || p >= (size_t)g.nx * g.nv) {
+    VM_BAD(S.ds, 1);
+    return;
+  }
   key_min(key, dkey(dist2_exact(S.tay + (size_t)mo * TY_N, g, Px, Pv, xi, ze)), (unsigned long long)mo);
   key_min(key, dkey(dist2_exact(S.tay + (size_t)m * TY_N, g, Px, Pv, xi, ze)), (unsigned long long)m);
 }
@@ -343,7 +348,7 @@ __device__ __forceinline__ Ctx9 ctx_of(const Grid& g, const Elem9& E, float alo,
 
 __device__ __forceinline__ bool test_site(const Grid& g, const Elem9& E, const Ctx9& c, long long i0, long long j0,
                                           long long i, long long j) {
-  const int r = pass_f32(c, (float)(i - i0), (float)(j - j0));
+  const int r = pass_f32(c, (float)(int)(i - i0), (float)(int)(j - j0));
   if (r >= 0) return r == 1;
   return pass_exact(g, E.T9, E.ex9, site_x(g, i), site_v(g, j));
 }
@@ -487,14 +492,17 @@ __global__ void __launch_bounds__(32 * TE, 6) k_claim_small(Grid g, const double
   const int clo = (int)max(0ll, (long long)(-pad) - c0);
   const int chi = (int)min(64ll, (long long)(g.nv + pad) - c0);
   const unsigned long long valid = (irow >= -pad && irow < g.nx + pad) ? col_mask(0, clo, chi) : 0ull;
-  auto test = [&](long long i, long long j) -> bool {
-    const int r = pass_f32(c, (float)(i - i0), (float)(j - j0));
+  // test of window site (row wr, column wb); offsets from the start in
+  // 32-bit integers (a 64-bit conversion would take the FP64 pipe)
+  auto test = [&](int wr, int wb) -> bool {
+    const int r = pass_f32(c, (float)(wr - TR / 2), (float)(wb - 32));
     if (r >= 0) return r == 1;
-    return pass_exact_g(g, tay, k, l, site_x(g, i), site_v(g, j));
+    atomicAdd(&S.ds->n_exact, 1);
+    return pass_exact_g(g, tay, k, l, site_x(g, r0 + wr), site_v(g, c0 + wb));
   };
   // the start decides whether there is a component at all
   bool ok = false;
-  if (lane == TR / 2) ok = test(i0, j0);
+  if (lane == TR / 2) ok = test(TR / 2, 32);
   ok = __shfl_sync(FULL, ok, TR / 2);
   if (!ok) return;
   unsigned long long comp = 0ull, tested = 0ull, passing = 0ull;
@@ -562,7 +570,7 @@ __global__ void __launch_bounds__(32 * TE, 6) k_claim_small(Grid g, const double
       const int n = min(total - b0, TCAP);
       for (int e = lane; e < n; e += 32) {
         const int code = sh.item[e], r = code >> 6, b = code & 63;
-        if (test(r0 + r, c0 + b)) atomicOr(&sh.passed[r], 1ull << b);
+        if (test(r, b)) atomicOr(&sh.passed[r], 1ull << b);
       }
     }
     __syncwarp();
@@ -627,12 +635,14 @@ __global__ void __launch_bounds__(32 * TE, 6) k_claim_small(Grid g, const double
 // tier 2: larger windows, cooperative block, word-granular tests
 // ---------------------------------------------------------------------------
 
-constexpr int BT = 512;       // threads
-constexpr int BAND_R = 128;   // band window: rows across the band
-constexpr int FAT_R = 640, FAT_W = 10;  // 640 x 640 sites
-constexpr int LIST_CAP = 1024;
-constexpr int AHEAD = 4;      // rows tested ahead of the component per round
-constexpr size_t SMEM_MAX = 227 * 1024;
+constexpr int BT = 256;       // threads
+constexpr int BLOCKS_PER_SM = 3;
+constexpr int BAND_R = 128, BAND_W = 20;  // band window: 128 rows across, up to 1280 sites along
+constexpr int FAT_R = 160, FAT_W = 12;    // 160 x 768 sites
+constexpr int LIST_CAP = 512;
+constexpr int AHEAD = 8;      // rows tested ahead of the component per round
+constexpr size_t SMEM_MAX = 227 * 1024;   // opt-in limit per block
+constexpr size_t SMEM_SM = 228 * 1024;    // shared memory per SM
 
 struct BigHeader {
   Elem9 E;
@@ -652,11 +662,10 @@ __device__ __forceinline__ int mode_for(int sides, int attempt) {
 }
 
 // 64-bit words along a band window for a lattice side n: the whole padded
-// side if it fits in shared memory, else as many as fit.
+// side, at most BAND_W.
 __host__ __device__ __forceinline__ int band_words(long long n, int pad) {
   const long long full = (n + 2 * pad + 63) / 64;
-  const long long fit = (long long)((SMEM_MAX - sizeof(BigHeader)) / (3 * 8 * BAND_R));
-  return (int)(full < fit ? full : fit);
+  return (int)(full < BAND_W ? full : BAND_W);
 }
 
 // Rows and words of a window mode on a lattice (nrow x ncol sites before
@@ -738,7 +747,8 @@ __device__ __forceinline__ unsigned long long dilate(const unsigned long long* c
 }
 
 // Sites worth testing ahead of the component in word q: the word's column
-// within AHEAD rows of it, the whole word if its row neighbours hold some.
+// within AHEAD rows of it, the whole word if a word of its row within two
+// holds some.
 __device__ __forceinline__ unsigned long long ahead(const unsigned long long* comp, const Win& W, int q) {
   const int r = q / W.W, w = q - r * W.W;
   unsigned long long d = dilate(comp, W, q);
@@ -746,7 +756,9 @@ __device__ __forceinline__ unsigned long long ahead(const unsigned long long* co
     if (r - k >= 0) d |= comp[q - k * W.W];
     if (r + k < W.R) d |= comp[q + k * W.W];
   }
-  if ((w > 0 && comp[q - 1]) || (w < W.W - 1 && comp[q + 1])) d = ~0ull;
+  if ((w > 0 && comp[q - 1]) || (w < W.W - 1 && comp[q + 1]) || (w > 1 && comp[q - 2]) ||
+      (w < W.W - 2 && comp[q + 2]))
+    d = ~0ull;
   return d;
 }
 
@@ -759,7 +771,7 @@ __device__ __forceinline__ unsigned long long ahead(const unsigned long long* co
 // the whole padded lattice, its masks in a zeroed global scratch of the
 // block, cleared again (over the touched box) before the next element.
 template <bool kGlobal>
-__global__ void __launch_bounds__(BT) k_claim_big(Grid g, const double* __restrict__ tay,
+__global__ void __launch_bounds__(BT, BLOCKS_PER_SM) k_claim_big(Grid g, const double* __restrict__ tay,
                                                   const float* __restrict__ tayf, Slots Sin, float alo, float ahi,
                                                   const int2* __restrict__ list_in, const int* __restrict__ n_in,
                                                   int* __restrict__ stat, int2* __restrict__ list_out,
@@ -775,7 +787,10 @@ __global__ void __launch_bounds__(BT) k_claim_big(Grid g, const double* __restri
   const int n = *n_in;
   for (int item = blockIdx.x; item < n; item += gridDim.x) {
     const int m = list_in[item].x;
-    if (m < 0 || m >= g.ne) continue;  // (never expected; keeps every index in bounds)
+    if (m < 0 || m >= g.ne) {  // (never expected; keeps every index in bounds)
+      if (tid == 0) VM_BAD(S.ds, 4);
+      continue;
+    }
     const int sides = list_in[item].y >> 4, attempt = list_in[item].y & 15;
     const int mode = kGlobal ? MODE_GLOBAL : mode_for(sides, attempt);
     load_elem9(g, m, tay, tayf, H.E);
@@ -955,8 +970,13 @@ __device__ __forceinline__ unsigned long long exact_key(const Grid& g, const dou
 __global__ void k_resolve(Grid g, Slots Sin) {
   const Slots S = with_epoch(Sin);
   const int n = min(S.ds->nrec, S.rec_cap);
+  const size_t nsites = (size_t)g.nx * g.nv;
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-    const size_t p = (size_t)S.rec_site[r];
+    const size_t p = (size_t)(uint32_t)S.rec_site[r];
+    if (p >= nsites) {
+      VM_BAD(S.ds, 2);
+      continue;
+    }
     const unsigned long long win = S.rec_key[2 * p];
     S.slot0[p] = (S.epoch << 24) | (uint32_t)win;
     S.rec_key[2 * p] = KEY_EMPTY;
@@ -996,6 +1016,11 @@ __global__ void __launch_bounds__(HT) k_holes(Grid g, const double* __restrict__
     const int n = n_s;
     for (int idx = threadIdx.x; idx < n; idx += HT) {
       const int p = la[idx];
+      if (p < 0 || (size_t)p >= (size_t)g.nx * g.nv) {
+        VM_BAD(ds, 3);
+        cho[idx] = -2;  // dropped
+        continue;
+      }
       const int i = p / g.nv, j = p - i * g.nv;
       const double Px = site_x(g, i), Pv = site_v(g, j);
       int best = -1;
@@ -1021,7 +1046,7 @@ __global__ void __launch_bounds__(HT) k_holes(Grid g, const double* __restrict__
       const int ch = cho[idx];
       if (ch >= 0)
         slot0[la[idx]] = (epoch << 24) | (uint32_t)ch;
-      else
+      else if (ch == -1)
         lb[atomicAdd(&next_s, 1)] = la[idx];
     }
     __syncthreads();
@@ -1072,7 +1097,7 @@ void alpha_bounds(double alpha, float& lo, float& hi) {
 // of the kernel, shared by every solver of the process, so it is set to the
 // largest size any grid can ask for rather than to this grid's need.
 bool map_prepare(const Grid& g) {
-  if (big_smem_bytes(g) > SMEM_MAX) return false;
+  if (big_smem_bytes(g) > SMEM_MAX || BLOCKS_PER_SM * (big_smem_bytes(g) + 1024) > SMEM_SM) return false;
   return cudaFuncSetAttribute(k_claim_big<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX) ==
          cudaSuccess;
 }
@@ -1092,8 +1117,8 @@ void launch_map(vm_solver* s) {
   DevState* d = s->ds;
   // Blocks of the large windows: the elements that can escape tier 1 are
   // few on a small lattice, and an idle block still takes a whole SM.
-  const unsigned big1 = (unsigned)std::min<long long>(2 * 152, std::max<long long>(16, s->g.ne / 16));
-  const unsigned big2 = (unsigned)std::min<long long>(152, big1);
+  const unsigned big1 = (unsigned)std::min<long long>(BLOCKS_PER_SM * 152, std::max<long long>(16, s->g.ne / 16));
+  const unsigned big2 = big1;
   const unsigned bigG = (unsigned)std::min<long long>(kGlobalBlocks, big1);
   ps = prof_begin(s, KID_CLAIM_LARGE);
   if (s->cfg.map_windows == 0) {

@@ -303,69 +303,133 @@ struct FPair {
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// Value of f at site (i, j) owned by element m: every case (node choice by
+// the FP64 evaluation when the FP32 bound cannot settle it, stencils that
+// leave the grid).
+__device__ __noinline__ float recon_site32(const Grid& g, const double* __restrict__ tay,
+                                           const float* __restrict__ tayf, const float* __restrict__ fini, int i,
+                                           int j, int m) {
+  const float inv_s = 1.0f / (float)g.s, fs = (float)g.s;
+  float val = 0.f;
+  const float* F = tayf + (size_t)m * TF_N;
+  float px, pv;
+  p_of(F, i, j, inv_s, px, pv);
+  const QF q = qeval(F, px, pv);
+  int Bu, Bw;
+  float bu, bw;
+  anchor(F, Bu, bu, Bw, bw);
+  // index coordinates of Q relative to the anchor
+  const float ru = bu + fs * q.qx, rw = bw + fs * q.qv;
+  const float eu = fs * q.ex + 1e-6f * (1.f + fabsf(ru)), ew = fs * q.ev + 1e-6f * (1.f + fabsf(rw));
+  int in, jn, ic, jc;
+  float x, y;
+  if (!(fabsf(ru) < 1e7f && fabsf(rw) < 1e7f)) {
+    // far outside the grid (or not a number): no node of the stencil exists
+    in = jn = ic = jc = -1000000;
+    x = y = 0.f;
+  } else if (floor_sure(ru + 0.5f, eu) && floor_sure(ru, eu) && floor_sure(rw + 0.5f, ew) && floor_sure(rw, ew)) {
+    const float nu = floorf(ru + 0.5f), nw = floorf(rw + 0.5f);
+    in = Bu + (int)nu;
+    jn = Bw + (int)nw;
+    ic = Bu + (int)floorf(ru);
+    jc = Bw + (int)floorf(rw);
+    x = ru - nu;
+    y = rw - nw;
+  } else {
+    // FP64 evaluation, as the FP64 path takes these decisions
+    const double* t = tay + (size_t)m * TY_N;
+    double dqx, dqv;
+    qofp_exact(t, site_x(g, i), site_v(g, j), dqx, dqv);
+    const double u = dmul(dsub(dadd(t[TY_QX], dqx), g.x_lo), g.inv_dx);
+    const double w = dmul(dsub(dadd(t[TY_QV], dqv), g.v_lo), g.inv_dv);
+    if (!(u > -2.0 && u < (double)g.nx + 1.0 && w > -2.0 && w < (double)g.nv + 1.0)) {
+      in = jn = ic = jc = -1000000;
+      x = y = 0.f;
+    } else {
+      in = (int)floor(dadd(u, 0.5));
+      jn = (int)floor(dadd(w, 0.5));
+      ic = (int)floor(u);
+      jc = (int)floor(w);
+      x = (float)dsub(u, (double)in);
+      y = (float)dsub(w, (double)jn);
+    }
+  }
+  if (in > -2 && in < g.nx + 2 && jn > -2 && jn < g.nv + 2) val = qinterp32(fini, g, in, jn, ic, jc, x, y);
+  return val;
+}
+
+// The common case without branches: the FP32 node choice is certain and the
+// whole stencil is inside the grid.  Otherwise *slow is set (the value is
+// then recon_site32's); the loads stay in bounds either way, so that the
+// loads of several sites can be in flight together.
+__device__ __forceinline__ float recon_fast32(const Grid& g, const float* __restrict__ tayf,
+                                              const float* __restrict__ fini, int i, int j, int m, bool* slow) {
+  const float inv_s = 1.0f / (float)g.s, fs = (float)g.s;
+  const float* F = tayf + (size_t)(m < 0 ? 0 : m) * TF_N;
+  float px, pv;
+  p_of(F, i, j, inv_s, px, pv);
+  const QF q = qeval(F, px, pv);
+  int Bu, Bw;
+  float bu, bw;
+  anchor(F, Bu, bu, Bw, bw);
+  const float ru = bu + fs * q.qx, rw = bw + fs * q.qv;
+  const float eu = fs * q.ex + 1e-6f * (1.f + fabsf(ru)), ew = fs * q.ev + 1e-6f * (1.f + fabsf(rw));
+  const bool finite = fabsf(ru) < 1e6f && fabsf(rw) < 1e6f;
+  const float ruc = finite ? ru : 0.f, rwc = finite ? rw : 0.f;
+  const float nu = floorf(ruc + 0.5f), nw = floorf(rwc + 0.5f);
+  int in = Bu + (int)nu, jn = Bw + (int)nw;
+  int ic = Bu + (int)floorf(ruc), jc = Bw + (int)floorf(rwc);
+  const bool sure = finite && floor_sure(ruc + 0.5f, eu) && floor_sure(ruc, eu) && floor_sure(rwc + 0.5f, ew) &&
+                    floor_sure(rwc, ew);
+  const bool inside = in >= 1 && in <= g.nx - 2 && jn >= 1 && jn <= g.nv - 2;
+  *slow = (m >= 0) && !(sure && inside);
+  if (!(sure && inside)) {  // any in-grid stencil: its value is not used
+    in = jn = 1;
+    ic = jc = 0;
+  }
+  const float v = qinterp32_in(fini, g, in, jn, ic, jc, ruc - nu, rwc - nw);
+  return (m >= 0) ? v : 0.f;
+}
+
 __global__ void __launch_bounds__(256) k_recon32(Grid g, const uint32_t* __restrict__ map, const DevState* ds,
                                                  const double* __restrict__ tay, const float* __restrict__ tayf,
                                                  const float* __restrict__ fini, float* __restrict__ f,
                                                  double* __restrict__ M) {
   __shared__ double sh[32];
   const int i = blockIdx.x;
-  const float inv_s = 1.0f / (float)g.s, fs = (float)g.s;
+  const uint32_t epoch = ds_epoch(ds);
   FPair acc;
-  for (int j = threadIdx.x; j < g.nv; j += blockDim.x) {
-    const size_t p = (size_t)i * g.nv + j;
-    const int m = owner(map, p, ds_epoch(ds), g.ne);
-    float val = 0.f;
-    if (m >= 0) {
-      const float* F = tayf + (size_t)m * TF_N;
-      float px, pv;
-      p_of(F, i, j, inv_s, px, pv);
-      const QF q = qeval(F, px, pv);
-      int Bu, Bw;
-      float bu, bw;
-      anchor(F, Bu, bu, Bw, bw);
-      // index coordinates of Q relative to the anchor
-      const float ru = bu + fs * q.qx, rw = bw + fs * q.qv;
-      const float eu = fs * q.ex + 1e-6f * (1.f + fabsf(ru)), ew = fs * q.ev + 1e-6f * (1.f + fabsf(rw));
-      int in, jn, ic, jc;
-      float x, y;
-      if (!(fabsf(ru) < 1e7f && fabsf(rw) < 1e7f)) {
-        // far outside the grid (or not a number): no node of the stencil exists
-        in = jn = ic = jc = -1000000;
-        x = y = 0.f;
-      } else if (floor_sure(ru + 0.5f, eu) && floor_sure(ru, eu) && floor_sure(rw + 0.5f, ew) && floor_sure(rw, ew)) {
-        const float nu = floorf(ru + 0.5f), nw = floorf(rw + 0.5f);
-        in = Bu + (int)nu;
-        jn = Bw + (int)nw;
-        ic = Bu + (int)floorf(ru);
-        jc = Bw + (int)floorf(rw);
-        x = ru - nu;
-        y = rw - nw;
-      } else {
-        // FP64 evaluation, as the FP64 path takes these decisions
-        const double* t = tay + (size_t)m * TY_N;
-        double dqx, dqv;
-        qofp_exact(t, site_x(g, i), site_v(g, j), dqx, dqv);
-        const double u = dmul(dsub(dadd(t[TY_QX], dqx), g.x_lo), g.inv_dx);
-        const double w = dmul(dsub(dadd(t[TY_QV], dqv), g.v_lo), g.inv_dv);
-        if (!(u > -2.0 && u < (double)g.nx + 1.0 && w > -2.0 && w < (double)g.nv + 1.0)) {
-          in = jn = ic = jc = -1000000;
-          x = y = 0.f;
-        } else {
-          in = (int)floor(dadd(u, 0.5));
-          jn = (int)floor(dadd(w, 0.5));
-          ic = (int)floor(u);
-          jc = (int)floor(w);
-          x = (float)dsub(u, (double)in);
-          y = (float)dsub(w, (double)jn);
-        }
-      }
-      if (in >= 1 && in <= g.nx - 2 && jn >= 1 && jn <= g.nv - 2)
-        val = qinterp32_in(fini, g, in, jn, ic, jc, x, y);
-      else if (in > -2 && in < g.nx + 2 && jn > -2 && jn < g.nv + 2)
-        val = qinterp32(fini, g, in, jn, ic, jc, x, y);
+  // The owners of a chunk of this thread's sites are loaded together first
+  // (one memory latency for the chunk), then the sites are done two at a
+  // time, so that their record and stencil loads overlap.
+  constexpr int CH = 8;
+  const int bd = blockDim.x;
+  for (int jc = threadIdx.x; jc < g.nv; jc += CH * bd) {
+    int own[CH];
+#pragma unroll
+    for (int u = 0; u < CH; u++) {
+      const int j = jc + u * bd;
+      own[u] = (j < g.nv) ? owner(map, (size_t)i * g.nv + j, epoch, g.ne) : -1;
     }
-    f[p] = val;
-    acc.add(val);
+#pragma unroll
+    for (int u = 0; u < CH; u += 2) {
+      const int j0 = jc + u * bd, j1 = j0 + bd;
+      if (j0 >= g.nv) break;
+      const bool has1 = j1 < g.nv;
+      const size_t p0 = (size_t)i * g.nv + j0, p1 = p0 + bd;
+      const int m0 = own[u], m1 = own[u + 1];
+      bool s0, s1;
+      float v0 = recon_fast32(g, tayf, fini, i, j0, m0, &s0);
+      float v1 = recon_fast32(g, tayf, fini, i, has1 ? j1 : j0, m1, &s1);
+      if (s0) v0 = recon_site32(g, tay, tayf, fini, i, j0, m0);
+      if (s1) v1 = recon_site32(g, tay, tayf, fini, i, j1, m1);
+      f[p0] = v0;
+      acc.add(v0);
+      if (has1) {
+        f[p1] = v1;
+        acc.add(v1);
+      }
+    }
   }
   const double rowsum = block_sum(acc.value(), sh);
   if (threadIdx.x == 0) M[i] = dmul(rowsum, g.dxdv);

@@ -22,7 +22,7 @@ VM_DTYPE_F64, VM_DTYPE_F32 = 0, 1
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "workspace too small", 3: "CUDA runtime error",
           4: "unexplored-site repair did not converge", 5: "influence region larger than the largest window",
-          6: "memory budget exceeded", 7: "call out of order"}
+          6: "memory budget exceeded", 7: "call out of order", 8: "internal consistency check failed"}
 
 # Names of every entry point declared in include/vlamet.h.
 EXPORTS = ["vm_config_default", "vm_workspace_bytes", "vm_create", "vm_destroy", "vm_status_string",
@@ -51,7 +51,8 @@ class VmDiag(C.Structure):
     _fields_ = [("mass", C.c_double), ("energy", C.c_double), ("detT_min", C.c_double),
                 ("detT_max", C.c_double), ("step", C.c_int64), ("cycle", C.c_int32),
                 ("holes", C.c_int32), ("hole_rounds", C.c_int32), ("overflow_elements", C.c_int32),
-                ("tier1_more", C.c_int32), ("last_tier_elements", C.c_int32)]
+                ("tier1_more", C.c_int32), ("last_tier_elements", C.c_int32),
+                ("exact_tests", C.c_int32), ("bad_where", C.c_int32)]
 
 
 class VmKernelStat(C.Structure):
