@@ -143,6 +143,7 @@ def step_bytes_per_update(rc, fp32: bool) -> float:
 # time of the capture: a source changed since makes the figure void (null).
 NCU_TRAFFIC = {
     # kernel: (bytes per launch, source file, sha256 prefix)
+    "claim_small": (176_924_416, "map.cu", "8752cb65e9456e93"),
 }
 
 
@@ -505,8 +506,15 @@ def run_serve(args):
         return I.HALOS_4096.with_(name=f"req{i}", nx=nx, nv=nv, seed=10_000 + i)
     base = poisson_requests(args.requests, rate=0.0, seed=args.seed, make_config=make,
                             steps=(args.min_steps, args.max_steps))
-    ics = {r.rid: I.initial_f(r.config) for r in base}
-    ic = lambda rc: ics[int(rc.name[3:])]  # noqa: E731
+    # seeded per request id and grid: the rate runs draw arrival times from
+    # the same stream, so the same id can come with another grid size
+    ics = {}
+
+    def ic(rc):
+        key = (rc.name, rc.nx, rc.nv)
+        if key not in ics:
+            ics[key] = I.initial_f(rc)
+        return ics[key]
     srv = Server(GpuBackend(), budget_bytes=budget, max_active=args.max_active, steps_per_tick=args.tick, ic_fn=ic)
     sat = srv.run(base)
     sat["errors"] = sorted({r.error for r in srv.done if r.error})[:3]

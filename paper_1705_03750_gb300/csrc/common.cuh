@@ -55,6 +55,8 @@ struct DevState {
   int32_t t1_more;       // tier-1 elements that needed tests beyond their predicted region
   int32_t n_exact;       // tests the FP32 bound left to the exact FP64 test (statistics)
   int32_t bad_where;     // first failed bounds check (0: none); kept until read by vm_sync
+  int32_t take[3];       // next item of each large-window launch (blocks fetch work dynamically)
+  int32_t noverflow_back; // tier-1 escapes of elements with all eight neighbours (listed from the end)
   uint32_t epoch;        // epoch of the current influence map (0..kEpochs-1)
   double Mtot;           // total mass of the last reconstruction
   double sum_mass, sum_kin, sum_pot;
@@ -91,7 +93,10 @@ enum { TY_X = 0, TY_V, TY_TI00, TY_TI01, TY_TI10, TY_TI11, TY_GX00, TY_GX01, TY_
 // element's index position u_m = (x_m - x_lo)/dx into integer and fraction.
 enum { TF_T00 = 0, TF_T01, TF_T10, TF_T11, TF_GX00, TF_GX01, TF_GX11, TF_GV00, TF_GV01, TF_GV11,
        TF_K00, TF_K01, TF_K10, TF_K11, TF_C1X, TF_C2X, TF_C1V, TF_C2V, TF_UF, TF_WF, TF_UI, TF_WI,
-       TF_BU, TF_BW, TF_HU, TF_HW, TF_N = 32 };
+       TF_N = 32 };
+// qeval reads words 0-19 of the FP32 record as five float4
+static_assert(TF_T00 == 0 && TF_GX00 == 4 && TF_GV01 == 8 && TF_K10 == 12 && TF_C1V == 16 && TF_WF == 19,
+              "FP32 record layout");
 
 constexpr unsigned long long KEY_EMPTY = ~0ull;
 

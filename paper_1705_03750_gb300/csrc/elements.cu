@@ -95,15 +95,7 @@ __device__ __forceinline__ void taylor_one(const Grid& g, const double* __restri
   // index position of P_m, as the start site of the percolation uses it
   t[TY_U] = dmul(dsub(x, g.x_lo), g.inv_dx);
   t[TY_W] = dmul(dsub(v, g.v_lo), g.inv_dv);
-  float* F = tayf + (size_t)m * TF_N;
-  taylor_f32(g, t, F);
-  // lattice index position of Q_m (a multiple of 1/2): integer part and
-  // half, exactly
-  const int u2 = (g.nx - 1) + 2 * (k - g.Kx - 1) * g.s, w2 = (g.nv - 1) + 2 * (l - g.Kv - 1) * g.s;
-  reinterpret_cast<int*>(F)[TF_BU] = u2 >> 1;
-  reinterpret_cast<int*>(F)[TF_BW] = w2 >> 1;
-  F[TF_HU] = (u2 & 1) ? 0.5f : 0.f;
-  F[TF_HW] = (w2 & 1) ? 0.5f : 0.f;
+  taylor_f32(g, t, tayf + (size_t)m * TF_N);
 }
 
 // Half drift (predictor or corrector of Sec. 2.4): x, T_x. and H_x.. move

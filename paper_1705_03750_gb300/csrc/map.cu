@@ -107,15 +107,18 @@ struct QF {
 
 __device__ __forceinline__ QF qeval(const float* __restrict__ F, float px, float pv) {
   QF r;
-  const float yx = F[TF_T00] * px + F[TF_T01] * pv;
-  const float yv = F[TF_T10] * px + F[TF_T11] * pv;
-  const float sx = px * (F[TF_GX00] * px + F[TF_GX01] * pv) + pv * (F[TF_GX01] * px + F[TF_GX11] * pv);
-  const float sv = px * (F[TF_GV00] * px + F[TF_GV01] * pv) + pv * (F[TF_GV01] * px + F[TF_GV11] * pv);
-  r.qx = yx - 0.5f * (F[TF_K00] * sx + F[TF_K01] * sv);
-  r.qv = yv - 0.5f * (F[TF_K10] * sx + F[TF_K11] * sv);
+  // the record's first 20 words in five 16-byte loads (records are 128-byte aligned)
+  const float4* F4 = reinterpret_cast<const float4*>(F);
+  const float4 f0 = F4[0], f1 = F4[1], f2 = F4[2], f3 = F4[3], f4 = F4[4];
+  const float yx = f0.x * px + f0.y * pv;
+  const float yv = f0.z * px + f0.w * pv;
+  const float sx = px * (f1.x * px + f1.y * pv) + pv * (f1.y * px + f1.z * pv);
+  const float sv = px * (f1.w * px + f2.x * pv) + pv * (f2.x * px + f2.y * pv);
+  r.qx = yx - 0.5f * (f2.z * sx + f2.w * sv);
+  r.qv = yv - 0.5f * (f3.x * sx + f3.y * sv);
   const float P = fmaxf(fabsf(px), fabsf(pv));
-  r.ax = F[TF_C1X] * P + F[TF_C2X] * (P * P);
-  r.av = F[TF_C1V] * P + F[TF_C2V] * (P * P);
+  r.ax = f3.z * P + f3.w * (P * P);
+  r.av = f4.x * P + f4.y * (P * P);
   return r;
 }
 
@@ -142,6 +145,7 @@ __device__ __forceinline__ int pass_f32(const Ctx9& c, float di, float dj) {
   const float ex = kRelQ * m.ax + kAbs * (1.f + m.ax), ev = kRelQ * m.av + kAbs * (1.f + m.av);
   const int ra = range_f(m.qx, ex, c.alo, c.ahi), rb = range_f(m.qv, ev, c.alo, c.ahi);
   if (!ra || !rb) return -1;
+  if (ra == 2 && rb == 2) return 1;  // inside the alpha box on both axes: no neighbour to ask
   const float d2 = m.qx * m.qx + m.qv * m.qv;
   const float A2 = m.ax * m.ax + m.av * m.av;
   const float e2 = kRelD * A2 + kAbs * (1.f + A2);
@@ -223,6 +227,8 @@ __global__ void k_map_begin(DevState* ds) {
     ds->nrec = 0;
     ds->t1_more = 0;
     ds->n_exact = 0;
+    ds->take[0] = ds->take[1] = ds->take[2] = 0;
+    ds->noverflow_back = 0;
   }
 }
 
@@ -444,6 +450,13 @@ __device__ __forceinline__ void list_chunk(unsigned short* item, unsigned long l
 // tests does not change the result: the component is the connected set of
 // passing sites reached from the start, and the loop ends only when every
 // site next to it has been tested.  Claims are made once at the end.
+__device__ __forceinline__ void claim_element(const Grid& g, const double* __restrict__ tay,
+                                              const float* __restrict__ tayf, const Slots& S, float alo, float ahi,
+                                              int2* __restrict__ ovf_list, WarpShared& sh, int lane, int m);
+
+// One element per warp.  (A warp-strided loop that prefetched the next
+// element's records cut the set-up latency but cost more in register spills
+// than it saved.)
 __global__ void __launch_bounds__(32 * TE, 6) k_claim_small(Grid g, const double* __restrict__ tay,
                                                          const float* __restrict__ tayf, Slots Sin, float alo,
                                                          float ahi, int2* __restrict__ ovf_list) {
@@ -452,9 +465,27 @@ __global__ void __launch_bounds__(32 * TE, 6) k_claim_small(Grid g, const double
   const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
   const int m = blockIdx.x * TE + wq;
   if (m >= g.ne) return;
-  WarpShared& sh = shw[wq];
+  claim_element(g, tay, tayf, S, alo, ahi, ovf_list, shw[wq], lane, m);
+}
+
+__device__ __forceinline__ void claim_element(const Grid& g, const double* __restrict__ tay,
+                                              const float* __restrict__ tayf, const Slots& S, float alo, float ahi,
+                                              int2* __restrict__ ovf_list, WarpShared& sh, int lane, int m) {
   const int k = m / g.Lv, l = m - k * g.Lv;
-  // the 3x3 neighbourhood's FP32 records, 16 bytes per lane and load
+  // The 3x3 neighbourhood's FP64 index positions (lanes 0-8) and FP32
+  // records (16 bytes per lane and load): every load issued before any is
+  // used, so the set-up costs one memory round trip.
+  double uq = 0.0, wpos = 0.0;
+  bool exq = false;
+  if (lane < 9) {
+    const int kk = k + lane / 3 - 1, ll = l + lane % 3 - 1;
+    exq = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
+    if (exq) {
+      const double* tq = tay + (size_t)(kk * g.Lv + ll) * TY_N;
+      uq = __ldg(tq + TY_U);
+      wpos = __ldg(tq + TY_W);
+    }
+  }
   for (int idx = lane; idx < 9 * (TF_N / 4); idx += 32) {
     const int q = idx >> 3, c4 = idx & 7;
     const int kk = k + q / 3 - 1, ll = l + q % 3 - 1;
@@ -464,19 +495,15 @@ __global__ void __launch_bounds__(32 * TE, 6) k_claim_small(Grid g, const double
     reinterpret_cast<float4*>(sh.F9[q])[c4] = v;
     if (c4 == 0) sh.ex9[q] = ex;
   }
-  // start site (FP64 index position of P_m)
-  const double* tm = tay + (size_t)m * TY_N;
-  const double us = tm[TY_U], ws = tm[TY_W];
+  // start site (FP64 index position of P_m: lane 4 holds the centre)
+  const double us = __shfl_sync(FULL, uq, 4), ws = __shfl_sync(FULL, wpos, 4);
   if (!(us > -1e9 && us < 1e9 && ws > -1e9 && ws < 1e9)) return;
   const long long i0 = (long long)floor(dadd(us, 0.5)), j0 = (long long)floor(dadd(ws, 0.5));
   const int pad = g.pad;
   if (i0 < -pad || i0 >= g.nx + pad || j0 < -pad || j0 >= g.nv + pad) return;
   if (lane < 9) {
-    const int kk = k + lane / 3 - 1, ll = l + lane % 3 - 1;
-    const bool ex = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
-    const double* tq = tay + (size_t)(kk * g.Lv + ll) * TY_N;
-    sh.offu[lane] = ex ? (float)((double)i0 - tq[TY_U]) : 0.f;
-    sh.offv[lane] = ex ? (float)((double)j0 - tq[TY_W]) : 0.f;
+    sh.offu[lane] = exq ? (float)((double)i0 - uq) : 0.f;
+    sh.offv[lane] = exq ? (float)((double)j0 - wpos) : 0.f;
   }
   __syncwarp();
   Ctx9 c;
@@ -599,8 +626,14 @@ __global__ void __launch_bounds__(32 * TE, 6) k_claim_small(Grid g, const double
                                        ((comp >> 63) && chi == 64 && c0 + 64 < g.nv + pad));
   if (er || ec) {
     if (lane == 0) {
+      // Outer elements (a neighbour missing) claim the long boundary bands,
+      // the longest jobs of the next tier: they are listed from the front and
+      // taken first, the others from the end of the list.
       const int sides = (er ? 1 : 0) | (ec ? 2 : 0);
-      ovf_list[atomicAdd(&S.ds->noverflow, 1)] = make_int2(m, sides << 4);  // attempt 0
+      bool outer = false;
+      for (int q = 0; q < 9; q++) outer |= !sh.ex9[q];
+      const int slot = outer ? atomicAdd(&S.ds->noverflow, 1) : g.ne - 1 - atomicAdd(&S.ds->noverflow_back, 1);
+      ovf_list[slot] = make_int2(m, sides << 4);  // attempt 0
     }
     return;
   }
@@ -646,7 +679,7 @@ constexpr size_t SMEM_SM = 228 * 1024;    // shared memory per SM
 
 struct BigHeader {
   Elem9 E;
-  int nlist, ok;
+  int item, nlist, ok;
   int rmin, rmax, wmin, wmax;  // rows / words holding component bits
   int list[LIST_CAP];          // words to test this round
   unsigned long long lmask[LIST_CAP];  // their untested valid sites
@@ -774,9 +807,10 @@ template <bool kGlobal>
 __global__ void __launch_bounds__(BT, BLOCKS_PER_SM) k_claim_big(Grid g, const double* __restrict__ tay,
                                                   const float* __restrict__ tayf, Slots Sin, float alo, float ahi,
                                                   const int2* __restrict__ list_in, const int* __restrict__ n_in,
+                                                  const int* __restrict__ n_back,
                                                   int* __restrict__ stat, int2* __restrict__ list_out,
-                                                  int* __restrict__ n_out, unsigned long long* __restrict__ gwin,
-                                                  size_t gwin_words) {
+                                                  int* __restrict__ n_out, int* __restrict__ take,
+                                                  unsigned long long* __restrict__ gwin, size_t gwin_words) {
   const Slots S = with_epoch(Sin);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BigHeader& H = *reinterpret_cast<BigHeader*>(smem_raw);
@@ -784,14 +818,23 @@ __global__ void __launch_bounds__(BT, BLOCKS_PER_SM) k_claim_big(Grid g, const d
                                      : reinterpret_cast<unsigned long long*>(smem_raw + sizeof(BigHeader));
   const int tid = threadIdx.x;
   const int pad = g.pad;
-  const int n = *n_in;
-  for (int item = blockIdx.x; item < n; item += gridDim.x) {
-    const int m = list_in[item].x;
+  // n_in items from the front of the list, n_back (if given) from its end
+  const int nf = *n_in, n = nf + (n_back ? *n_back : 0);
+  // items are taken one at a time from a shared counter, so that blocks that
+  // drew short components take more of them
+  for (;;) {
+    if (tid == 0) H.item = atomicAdd(take, 1);
+    __syncthreads();
+    const int item = H.item;
+    if (item >= n) break;
+    const int2 it2 = list_in[item < nf ? item : g.ne - 1 - (item - nf)];
+    const int m = it2.x;
     if (m < 0 || m >= g.ne) {  // (never expected; keeps every index in bounds)
       if (tid == 0) VM_BAD(S.ds, 4);
+      __syncthreads();  // every thread has read H.item before it is taken again
       continue;
     }
-    const int sides = list_in[item].y >> 4, attempt = list_in[item].y & 15;
+    const int sides = it2.y >> 4, attempt = it2.y & 15;
     const int mode = kGlobal ? MODE_GLOBAL : mode_for(sides, attempt);
     load_elem9(g, m, tay, tayf, H.E);
     __syncthreads();
@@ -1110,8 +1153,7 @@ void launch_map(vm_solver* s) {
   k_map_begin<<<1, 32, 0, s->stream>>>(s->ds);
   prof_end(s, ps);
   ps = prof_begin(s, KID_CLAIM_SMALL);
-  k_claim_small<<<(s->g.ne + TE - 1) / TE, 32 * TE, 0, s->stream>>>(s->g, s->tay, s->tayf, S, alo, ahi,
-                                                                    s->overflow_list);
+  k_claim_small<<<(unsigned)((s->g.ne + TE - 1) / TE), 32 * TE, 0, s->stream>>>(s->g, s->tay, s->tayf, S, alo, ahi, s->overflow_list);
   prof_end(s, ps);
   const size_t smem = big_smem_bytes(s->g);
   DevState* d = s->ds;
@@ -1123,18 +1165,20 @@ void launch_map(vm_solver* s) {
   ps = prof_begin(s, KID_CLAIM_LARGE);
   if (s->cfg.map_windows == 0) {
     k_claim_big<false><<<big1, BT, smem, s->stream>>>(s->g, s->tay, s->tayf, S, alo, ahi, s->overflow_list,
-                                                         &d->noverflow, &d->overflow_stat, s->overflow_list2,
-                                                         &d->noverflow2, nullptr, 0);
+                                                         &d->noverflow, &d->noverflow_back, &d->overflow_stat,
+                                                         s->overflow_list2,
+                                                         &d->noverflow2, &d->take[0], nullptr, 0);
     k_claim_big<false><<<big2, BT, smem, s->stream>>>(s->g, s->tay, s->tayf, S, alo, ahi, s->overflow_list2,
-                                                     &d->noverflow2, &d->overflow2_stat, s->overflow_list,
-                                                     &d->noverflow3, nullptr, 0);
+                                                     &d->noverflow2, nullptr, &d->overflow2_stat, s->overflow_list,
+                                                     &d->noverflow3, &d->take[1], nullptr, 0);
   }
   // tier-1 escapes go straight here when the shared-memory windows are off
   int* n_last = s->cfg.map_windows == 0 ? &d->noverflow3 : &d->noverflow;
   int* stat_last = s->cfg.map_windows == 0 ? &d->overflow3_stat : &d->overflow_stat;
   k_claim_big<true><<<bigG, BT, sizeof(BigHeader), s->stream>>>(
-      s->g, s->tay, s->tayf, S, alo, ahi, s->overflow_list, n_last, stat_last, nullptr, nullptr, s->gwin,
-      global_window_words(s->g.nx, s->g.nv, s->g.pad));
+      s->g, s->tay, s->tayf, S, alo, ahi, s->overflow_list, n_last,
+      s->cfg.map_windows == 0 ? nullptr : &d->noverflow_back, stat_last, nullptr, nullptr, &d->take[2],
+      s->gwin, global_window_words(s->g.nx, s->g.nv, s->g.pad));
   prof_end(s, ps);
   ps = prof_begin(s, KID_RESOLVE);
   k_resolve<<<(unsigned)std::min<size_t>(152, (s->n + 1023) / 1024), 256, 0, s->stream>>>(s->g, S);

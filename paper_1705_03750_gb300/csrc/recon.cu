@@ -221,15 +221,18 @@ struct QF {
 
 __device__ __forceinline__ QF qeval(const float* __restrict__ F, float px, float pv) {
   QF r;
-  const float yx = F[TF_T00] * px + F[TF_T01] * pv;
-  const float yv = F[TF_T10] * px + F[TF_T11] * pv;
-  const float sx = px * (F[TF_GX00] * px + F[TF_GX01] * pv) + pv * (F[TF_GX01] * px + F[TF_GX11] * pv);
-  const float sv = px * (F[TF_GV00] * px + F[TF_GV01] * pv) + pv * (F[TF_GV01] * px + F[TF_GV11] * pv);
-  r.qx = yx - 0.5f * (F[TF_K00] * sx + F[TF_K01] * sv);
-  r.qv = yv - 0.5f * (F[TF_K10] * sx + F[TF_K11] * sv);
+  // the record's first 20 words in five 16-byte loads (records are 128-byte aligned)
+  const float4* F4 = reinterpret_cast<const float4*>(F);
+  const float4 f0 = F4[0], f1 = F4[1], f2 = F4[2], f3 = F4[3], f4 = F4[4];
+  const float yx = f0.x * px + f0.y * pv;
+  const float yv = f0.z * px + f0.w * pv;
+  const float sx = px * (f1.x * px + f1.y * pv) + pv * (f1.y * px + f1.z * pv);
+  const float sv = px * (f1.w * px + f2.x * pv) + pv * (f2.x * px + f2.y * pv);
+  r.qx = yx - 0.5f * (f2.z * sx + f2.w * sv);
+  r.qv = yv - 0.5f * (f3.x * sx + f3.y * sv);
   const float P = fmaxf(fabsf(px), fabsf(pv));
-  const float ax = F[TF_C1X] * P + F[TF_C2X] * (P * P);
-  const float av = F[TF_C1V] * P + F[TF_C2V] * (P * P);
+  const float ax = f3.z * P + f3.w * (P * P);
+  const float av = f4.x * P + f4.y * (P * P);
   r.ex = kRelQ * ax + kAbs * (1.f + ax);
   r.ev = kRelQ * av + kAbs * (1.f + av);
   return r;
@@ -243,13 +246,15 @@ __device__ __forceinline__ void p_of(const float* __restrict__ F, int i, int j, 
 }
 
 // The lattice index position of Q_m (a multiple of 1/2): integer part and
-// half, exactly, from the element's FP32 record.
-__device__ __forceinline__ void anchor(const float* __restrict__ F, int& Bu, float& bu, int& Bw, float& bw) {
-  const int* Fi = reinterpret_cast<const int*>(F);
-  Bu = Fi[TF_BU];
-  Bw = Fi[TF_BW];
-  bu = F[TF_HU];
-  bw = F[TF_HW];
+// half flag, exactly (integer arithmetic: no load on the latency chain).
+__device__ __forceinline__ void anchor(const Grid& g, int m, int& Bu, float& bu, int& Bw, float& bw) {
+  const int k = m / g.Lv, l = m - k * g.Lv;
+  const int u2 = (g.nx - 1) + 2 * (k - g.Kx - 1) * g.s;  // 2 * index of Q_m,x
+  const int w2 = (g.nv - 1) + 2 * (l - g.Kv - 1) * g.s;
+  Bu = u2 >> 1;  // floor
+  bu = (u2 & 1) ? 0.5f : 0.f;
+  Bw = w2 >> 1;
+  bw = (w2 & 1) ? 0.5f : 0.f;
 }
 
 // Is floor(x) certain for every value within e of x?
@@ -317,7 +322,7 @@ __device__ __noinline__ float recon_site32(const Grid& g, const double* __restri
   const QF q = qeval(F, px, pv);
   int Bu, Bw;
   float bu, bw;
-  anchor(F, Bu, bu, Bw, bw);
+  anchor(g, m < 0 ? 0 : m, Bu, bu, Bw, bw);
   // index coordinates of Q relative to the anchor
   const float ru = bu + fs * q.qx, rw = bw + fs * q.qv;
   const float eu = fs * q.ex + 1e-6f * (1.f + fabsf(ru)), ew = fs * q.ev + 1e-6f * (1.f + fabsf(rw));
@@ -371,7 +376,7 @@ __device__ __forceinline__ float recon_fast32(const Grid& g, const float* __rest
   const QF q = qeval(F, px, pv);
   int Bu, Bw;
   float bu, bw;
-  anchor(F, Bu, bu, Bw, bw);
+  anchor(g, m < 0 ? 0 : m, Bu, bu, Bw, bw);
   const float ru = bu + fs * q.qx, rw = bw + fs * q.qv;
   const float eu = fs * q.ex + 1e-6f * (1.f + fabsf(ru)), ew = fs * q.ev + 1e-6f * (1.f + fabsf(rw));
   const bool finite = fabsf(ru) < 1e6f && fabsf(rw) < 1e6f;
@@ -399,37 +404,18 @@ __global__ void __launch_bounds__(256) k_recon32(Grid g, const uint32_t* __restr
   const int i = blockIdx.x;
   const uint32_t epoch = ds_epoch(ds);
   FPair acc;
-  // The owners of a chunk of this thread's sites are loaded together first
-  // (one memory latency for the chunk), then the sites are done two at a
-  // time, so that their record and stencil loads overlap.
-  constexpr int CH = 8;
-  const int bd = blockDim.x;
-  for (int jc = threadIdx.x; jc < g.nv; jc += CH * bd) {
-    int own[CH];
-#pragma unroll
-    for (int u = 0; u < CH; u++) {
-      const int j = jc + u * bd;
-      own[u] = (j < g.nv) ? owner(map, (size_t)i * g.nv + j, epoch, g.ne) : -1;
-    }
-#pragma unroll
-    for (int u = 0; u < CH; u += 2) {
-      const int j0 = jc + u * bd, j1 = j0 + bd;
-      if (j0 >= g.nv) break;
-      const bool has1 = j1 < g.nv;
-      const size_t p0 = (size_t)i * g.nv + j0, p1 = p0 + bd;
-      const int m0 = own[u], m1 = own[u + 1];
-      bool s0, s1;
-      float v0 = recon_fast32(g, tayf, fini, i, j0, m0, &s0);
-      float v1 = recon_fast32(g, tayf, fini, i, has1 ? j1 : j0, m1, &s1);
-      if (s0) v0 = recon_site32(g, tay, tayf, fini, i, j0, m0);
-      if (s1) v1 = recon_site32(g, tay, tayf, fini, i, j1, m1);
-      f[p0] = v0;
-      acc.add(v0);
-      if (has1) {
-        f[p1] = v1;
-        acc.add(v1);
-      }
-    }
+  // the owner of the thread's next site is loaded one iteration ahead
+  const size_t row = (size_t)i * g.nv;
+  int m = (threadIdx.x < g.nv) ? owner(map, row + threadIdx.x, epoch, g.ne) : -1;
+  for (int j = threadIdx.x; j < g.nv; j += blockDim.x) {
+    const int jn = j + blockDim.x;
+    const int mn = (jn < g.nv) ? owner(map, row + jn, epoch, g.ne) : -1;
+    bool slow;
+    float v = recon_fast32(g, tayf, fini, i, j, m, &slow);
+    if (slow) v = recon_site32(g, tay, tayf, fini, i, j, m);
+    f[row + j] = v;
+    acc.add(v);
+    m = mn;
   }
   const double rowsum = block_sum(acc.value(), sh);
   if (threadIdx.x == 0) M[i] = dmul(rowsum, g.dxdv);
@@ -506,7 +492,7 @@ __global__ void __launch_bounds__(256) k_remap32(Grid g, const uint32_t* __restr
       const int ra = beta_range_f(q.qx, q.ex, blo, bhi), rb = beta_range_f(q.qv, q.ev, blo, bhi);
       int Bu, Bw;
       float bu, bw;
-      anchor(F, Bu, bu, Bw, bw);
+      anchor(g, m < 0 ? 0 : m, Bu, bu, Bw, bw);
       float ru, rw;
       if (ra && rb) {
         // Q_r - Q_m in element units, blended over the beta set (Sec. 2.3.2)

@@ -78,27 +78,47 @@ __global__ void __launch_bounds__(32 * RW) k_rows(Grid g, const R* __restrict__ 
   (void)myrow;
 }
 
+// One thread per column.  The sweeps are sequential in the row, but the
+// loads are not: they are issued a chunk of CK rows at a time, so that one
+// memory latency covers CK steps of the recurrence.
 template <typename R, typename C>
 __global__ void __launch_bounds__(128) k_cols(Grid g, R* __restrict__ x, const C* __restrict__ th) {
+  constexpr int CK = 16;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= g.nv) return;
   const int nx = g.nx, nv = g.nv;
   const C* cp = th;
   const C* inv = th + nx;
   R dprev = R(0);
-  for (int i = 0; i < nx; i++) {
-    const R sub = (i == 0) ? R(0) : ((i == nx - 1) ? R(2) : R(1));
-    const size_t p = (size_t)i * nv + j;
-    const R d = (R(6) * x[p] - sub * dprev) * (R)inv[i];
-    x[p] = d;
-    dprev = d;
+  for (int i0 = 0; i0 < nx; i0 += CK) {
+    R v[CK];
+#pragma unroll
+    for (int u = 0; u < CK; u++) v[u] = (i0 + u < nx) ? x[(size_t)(i0 + u) * nv + j] : R(0);
+#pragma unroll
+    for (int u = 0; u < CK; u++) {
+      const int i = i0 + u;
+      if (i < nx) {
+        const R sub = (i == 0) ? R(0) : ((i == nx - 1) ? R(2) : R(1));
+        const R d = (R(6) * v[u] - sub * dprev) * (R)inv[i];
+        x[(size_t)i * nv + j] = d;
+        dprev = d;
+      }
+    }
   }
-  R enext = x[(size_t)(nx - 1) * nv + j];
-  for (int i = nx - 2; i >= 0; i--) {
-    const size_t p = (size_t)i * nv + j;
-    const R e = x[p] - (R)cp[i] * enext;
-    x[p] = e;
-    enext = e;
+  R enext = dprev;  // d'_{nx-1} = eta_{nx-1}
+  for (int i1 = nx - 2; i1 >= 0; i1 -= CK) {
+    R v[CK];
+#pragma unroll
+    for (int u = 0; u < CK; u++) v[u] = (i1 - u >= 0) ? x[(size_t)(i1 - u) * nv + j] : R(0);
+#pragma unroll
+    for (int u = 0; u < CK; u++) {
+      const int i = i1 - u;
+      if (i >= 0) {
+        const R e = v[u] - (R)cp[i] * enext;
+        x[(size_t)i * nv + j] = e;
+        enext = e;
+      }
+    }
   }
 }
 

@@ -122,9 +122,15 @@ class Server:
             if self.used + need > self.budget:
                 break
             self.waiting.popleft()
-            f0 = self.ic_fn(req.config) if self.ic_fn else None
-            handle = self.backend.start(req, f0)
             req.admitted = self.now()
+            try:
+                f0 = self.ic_fn(req.config) if self.ic_fn else None
+                handle = self.backend.start(req, f0)
+            except Exception as e:  # noqa: BLE001
+                req.error = f"{type(e).__name__}: {e}"
+                req.finished = self.now()
+                self.done.append(req)
+                continue
             self.used += need
             self.peak_used = max(self.peak_used, self.used)
             self.active.append((req, handle, need))

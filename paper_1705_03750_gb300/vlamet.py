@@ -176,6 +176,9 @@ def force_from_f_static(f, cfg: Config, out: dict, stream=None) -> None:
     assert f.is_cuda and f.is_contiguous() and tuple(f.shape) == (cfg.nx, cfg.nv)
     dtype = {torch.float64: VM_DTYPE_F64, torch.float32: VM_DTYPE_F32}[f.dtype]
     st = stream if stream is not None else torch.cuda.current_stream(f.device)
+    for k, t in out.items():
+        if not (t.is_cuda and t.is_contiguous() and t.dtype == torch.float64 and tuple(t.shape) == (cfg.nx,)):
+            raise ValueError(f"out[{k!r}] must be a contiguous float64 device tensor of shape ({cfg.nx},)")
     ptr = lambda k: C.c_void_p(out[k].data_ptr()) if k in out else None  # noqa: E731
     _check(L.vm_force_from_f_static(C.c_void_p(f.data_ptr()), dtype, cfg.nx, cfg.nv, cfg.x_lo, cfg.x_hi,
                                     cfg.v_lo, cfg.v_hi, cfg.G, cfg.literal_fd, ptr("M"), ptr("a"), ptr("da"),
@@ -230,16 +233,34 @@ class Solver:
         assert x.is_contiguous()
         return C.c_void_p(x.data_ptr()), (1 if x.is_cuda else 0)
 
+    def _arg(self, x, shape, dtype: str):
+        """(pointer, on_device) of an array that a call reads or writes whole.
+        The C ABI takes bare pointers, so the shape, element type, layout and
+        device are checked here: a smaller buffer would be read past its end."""
+        shape = tuple(shape)
+        if isinstance(x, np.ndarray):
+            if x.shape != shape or x.dtype != np.dtype(dtype) or not x.flags.c_contiguous:
+                raise ValueError(f"expected a C-contiguous {dtype} array of shape {shape}, "
+                                 f"got {x.dtype} {x.shape}")
+            return C.c_void_p(x.ctypes.data), 0
+        import torch
+        tdt = {"float64": torch.float64, "float32": torch.float32, "int32": torch.int32}[dtype]
+        if tuple(x.shape) != shape or x.dtype != tdt or not x.is_contiguous():
+            raise ValueError(f"expected a contiguous {dtype} tensor of shape {shape}, got {x.dtype} {tuple(x.shape)}")
+        if x.is_cuda and x.device != self.device:
+            raise ValueError(f"tensor on {x.device}, solver on {self.device}")
+        return C.c_void_p(x.data_ptr()), (1 if x.is_cuda else 0)
+
     def set_f(self, f0) -> None:
         if isinstance(f0, np.ndarray):
             f0 = np.ascontiguousarray(f0, dtype=np.float64)
-        p, dev = self._ptr(f0)
+        p, dev = self._arg(f0, (self.nx, self.nv), "float64")
         _check(self.L.vm_set_f(self.h, p, dev), "vm_set_f")
 
     def set_elements(self, soa12) -> None:
         if isinstance(soa12, np.ndarray):
             soa12 = np.ascontiguousarray(soa12, dtype=np.float64)
-        p, dev = self._ptr(soa12)
+        p, dev = self._arg(soa12, (12, self.ne), "float64")
         _check(self.L.vm_set_elements(self.h, p, dev), "vm_set_elements")
 
     def elements(self) -> np.ndarray:
@@ -266,7 +287,15 @@ class Solver:
         """M, a, a', a'' ([nx] float64 each) of the last reconstruction.  With
         ``out`` (a dict of device tensors) the copy stays on the device."""
         if out is not None:
-            ptrs = [C.c_void_p(out[k].data_ptr()) if k in out else None for k in ("M", "a", "da", "d2a")]
+            ptrs = []
+            for k in ("M", "a", "da", "d2a"):
+                if k in out:
+                    p, dev = self._arg(out[k], (self.nx,), "float64")
+                    if not dev:
+                        raise ValueError("out tensors must be on the device")
+                    ptrs.append(p)
+                else:
+                    ptrs.append(None)
             _check(self.L.vm_density_force(self.h, *ptrs, 1), "vm_density_force")
             return out
         res = {k: np.empty(self.nx) for k in ("M", "a", "da", "d2a")}
@@ -277,7 +306,7 @@ class Solver:
     def _read(self, fn, name, dtype=np.float64, out=None):
         code = VM_DTYPE_F64 if dtype == np.float64 else VM_DTYPE_F32
         if out is not None:
-            p, dev = self._ptr(out)
+            p, dev = self._arg(out, (self.nx, self.nv), "float64" if code == VM_DTYPE_F64 else "float32")
             _check(fn(self.h, p, code, dev), name)
             return out
         res = np.empty((self.nx, self.nv), dtype=dtype)

@@ -79,3 +79,20 @@ def test_product_path_does_not_import_the_oracle():
             txt = open(f).read()
             assert not re.search(r"^\s*(import|from)\s+oracle\b", txt, flags=re.M), f
             assert "vlamet_oracle" not in txt and "oracle/" not in txt, f
+
+
+def test_binding_refuses_arrays_the_call_would_read_past():
+    """The C ABI takes bare pointers: the binding checks shape, dtype and
+    layout first (a smaller buffer would be read past its end)."""
+    import types
+
+    import numpy as np
+
+    from paper_1705_03750_gb300 import vlamet as V
+    fake = types.SimpleNamespace(device=None)
+    ok = np.zeros((8, 6))
+    p, dev = V.Solver._arg(fake, ok, (8, 6), "float64")
+    assert dev == 0 and p.value == ok.ctypes.data
+    for bad in (np.zeros((6, 8)), np.zeros((8, 6), dtype=np.float32), np.zeros((8, 12))[:, ::2]):
+        with pytest.raises(ValueError):
+            V.Solver._arg(fake, bad, (8, 6), "float64")

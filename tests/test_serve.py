@@ -139,3 +139,17 @@ def test_a_solve_that_fails_while_stepping_is_retired():
     rep = srv.run([Request(i, (4, 4), steps=6, arrival=0.0) for i in range(4)])
     assert rep["requests"] == 4 and rep["failed"] == 1
     assert [r.rid for r in srv.done if r.error] == [1] and srv.used == 0
+
+
+def test_a_request_that_cannot_start_is_retired():
+    clock = FakeClock()
+
+    class Refusing(FakeBackend):
+        def start(self, req, f0):
+            if req.rid == 0:
+                raise ValueError("expected an array of shape (4, 4)")
+            return super().start(req, f0)
+
+    srv = Server(Refusing(clock), budget_bytes=10 ** 6, max_active=2, clock=clock)
+    rep = srv.run([Request(i, (4, 4), steps=3, arrival=0.0) for i in range(3)])
+    assert rep["requests"] == 3 and rep["failed"] == 1 and srv.used == 0
