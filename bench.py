@@ -144,6 +144,7 @@ def step_bytes_per_update(rc, fp32: bool) -> float:
 NCU_TRAFFIC = {
     # kernel: (bytes per launch, source file, sha256 prefix)
     "claim_small": (176_924_416, "map.cu", "8752cb65e9456e93"),
+    "reconstruct": (215_340_544, "recon.cu", "6a535ce10230b71d"),
 }
 
 
@@ -518,6 +519,7 @@ def run_serve(args):
     srv = Server(GpuBackend(), budget_bytes=budget, max_active=args.max_active, steps_per_tick=args.tick, ic_fn=ic)
     sat = srv.run(base)
     sat["errors"] = sorted({r.error for r in srv.done if r.error})[:3]
+    print(json.dumps({"partial_saturation": sat}), file=sys.stderr, flush=True)
     sat_rate = sat["requests"] / sat["wall_s"]
     out = {"workload": "serve-halos-256..2048", "requests": args.requests, "budget_gb": args.budget_gb,
            "saturation": {**sat, "requests_per_s": sat_rate}, "rates": []}
@@ -530,6 +532,7 @@ def run_serve(args):
         errs = sorted({r.error for r in srv.done if r.error})
         out["rates"].append({"fraction_of_saturation": frac, "rate_per_s": frac * sat_rate, **rep,
                              "errors": errs[:3]})
+        print(json.dumps({"partial": out["rates"][-1]}), file=sys.stderr, flush=True)
         torch.cuda.synchronize()
     return out
 

@@ -107,18 +107,17 @@ struct QF {
 
 __device__ __forceinline__ QF qeval(const float* __restrict__ F, float px, float pv) {
   QF r;
-  // the record's first 20 words in five 16-byte loads (records are 128-byte aligned)
-  const float4* F4 = reinterpret_cast<const float4*>(F);
-  const float4 f0 = F4[0], f1 = F4[1], f2 = F4[2], f3 = F4[3], f4 = F4[4];
-  const float yx = f0.x * px + f0.y * pv;
-  const float yv = f0.z * px + f0.w * pv;
-  const float sx = px * (f1.x * px + f1.y * pv) + pv * (f1.y * px + f1.z * pv);
-  const float sv = px * (f1.w * px + f2.x * pv) + pv * (f2.x * px + f2.y * pv);
-  r.qx = yx - 0.5f * (f2.z * sx + f2.w * sv);
-  r.qv = yv - 0.5f * (f3.x * sx + f3.y * sv);
+  // (scalar loads from shared memory: in the tier-1 test loop five 16-byte
+  // loads cost more registers than they save issue slots)
+  const float yx = F[TF_T00] * px + F[TF_T01] * pv;
+  const float yv = F[TF_T10] * px + F[TF_T11] * pv;
+  const float sx = px * (F[TF_GX00] * px + F[TF_GX01] * pv) + pv * (F[TF_GX01] * px + F[TF_GX11] * pv);
+  const float sv = px * (F[TF_GV00] * px + F[TF_GV01] * pv) + pv * (F[TF_GV01] * px + F[TF_GV11] * pv);
+  r.qx = yx - 0.5f * (F[TF_K00] * sx + F[TF_K01] * sv);
+  r.qv = yv - 0.5f * (F[TF_K10] * sx + F[TF_K11] * sv);
   const float P = fmaxf(fabsf(px), fabsf(pv));
-  r.ax = f3.z * P + f3.w * (P * P);
-  r.av = f4.x * P + f4.y * (P * P);
+  r.ax = F[TF_C1X] * P + F[TF_C2X] * (P * P);
+  r.av = F[TF_C1V] * P + F[TF_C2V] * (P * P);
   return r;
 }
 
@@ -575,9 +574,34 @@ __device__ __forceinline__ void claim_element(const Grid& g, const double* __res
       return (ihi >= ilo) ? col_mask(0, ilo, ihi + 1) : 0ull;
     };
     const unsigned long long pred = cols(hx, hv) & valid & ~tested;
-    const unsigned long long inner = (ix > 0.f && iv > 0.f) ? cols(ix, iv) : 0ull;
-    fa = pred & inner;
+    unsigned long long inner = (ix > 0.f && iv > 0.f) ? cols(ix, iv) & pred : 0ull;
+    // Inner sites need no test when it is certain that they pass: on them
+    // |T p| <= alpha - 0.02 - sx (the interval above), and q differs from
+    // T p by at most C2 P^2 (second-order terms, P = max |p| over the row's
+    // inner run) plus roundings far below 1e-3 (of T, p, and the interval).
+    // Then |q| < alpha on both axes: no neighbour is investigated, the site
+    // passes (in the FP64 test as in the FP32 one).
+    unsigned long long sure = 0ull;
+    if (inner && fmaxf(fmaxf(fabsf(T00), fabsf(T01)), fmaxf(fabsf(T10), fabsf(T11))) < 50.f) {
+      const int blo = __ffsll((long long)inner) - 1, bhi = 63 - __clzll((long long)inner);
+      const float pvlo = ((float)(blo - 32) + sh.offv[4]) * inv_s, pvhi = ((float)(bhi - 32) + sh.offv[4]) * inv_s;
+      const float Pr = fmaxf(fabsf(px), fmaxf(fabsf(pvlo), fabsf(pvhi)));
+      if (F[TF_C2X] * Pr * Pr + 2e-3f <= 0.02f + sx && F[TF_C2V] * Pr * Pr + 2e-3f <= 0.02f + sv) sure = inner;
+    }
+    tested |= sure;
+    passing |= sure;
+    fa = pred & inner & ~sure;
     fb = pred & ~inner;
+    // the owner slots the claims will exchange: towards L2 now (the first
+    // and last in-grid site of this row's predicted run)
+    const unsigned long long ing = pred & ((irow >= 0 && irow < g.nx) ? col_mask(0, (int)max(0ll, -c0),
+                                                                               (int)min(64ll, (long long)g.nv - c0))
+                                                                      : 0ull);
+    if (ing) {
+      const size_t rowp = (size_t)irow * g.nv + c0;
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(S.slot0 + rowp + (__ffsll((long long)ing) - 1)));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(S.slot0 + rowp + (63 - __clzll((long long)ing))));
+    }
   }
   int rounds = 0;
   for (int it = 0; it < TR * 64; it++) {
@@ -586,8 +610,10 @@ __device__ __forceinline__ void claim_element(const Grid& g, const double* __res
     const int inca = warp_incl(ca, lane), incb = warp_incl(cb, lane);
     const int ta = __shfl_sync(FULL, inca, 31);
     const int total = ta + __shfl_sync(FULL, incb, 31);
-    if (total == 0) break;
-    rounds++;
+    // (the first pass always closes the component: certified sites may
+    // already extend it with nothing left to test)
+    if (total == 0 && it > 0) break;
+    if (total > 0) rounds++;
     sh.passed[lane] = 0ull;
     for (int b0 = 0; b0 < total; b0 += TCAP) {
       __syncwarp();

@@ -6,7 +6,10 @@ enough device memory are free (admission by the solve's exact workspace
 footprint against a budget), keeps every admitted solve's state resident on
 the device, and advances all active solves together: each owns a CUDA
 stream, and each scheduling tick queues a few steps of every active solve, so
-the work of different requests overlaps on the GPU.  A solve that has queued
+the work of different requests overlaps on the GPU.  A solve gets new steps
+only while fewer than two of its earlier chunks are still queued, so that one
+host thread keeps every stream fed instead of blocking on a full launch
+queue.  A solve that has queued
 all its steps records an event; when the event has completed its result (the
 density and force of the last step) is read back, its latency recorded and
 its memory and slot released for the next request.
@@ -55,6 +58,10 @@ class GpuBackend:
     def footprint(self, rc) -> int:
         return self.V.workspace_bytes(self.V.Config.from_run(rc, self.precision)) + 8 * rc.nx * rc.nv
 
+    # steps queued ahead per solve: one host thread feeds every stream, and a
+    # launch into a full queue would block it while the other streams drain
+    MAX_IN_FLIGHT = 2
+
     def start(self, req: Request, f0: np.ndarray):
         torch = self.torch
         stream = torch.cuda.Stream(device=self.device)
@@ -62,14 +69,22 @@ class GpuBackend:
         with torch.cuda.stream(stream):
             f_dev = torch.from_numpy(f0).to(self.device, non_blocking=False)
         solver.set_f(f_dev)
-        return {"solver": solver, "stream": stream, "left": req.steps, "event": None, "f": f_dev}
+        return {"solver": solver, "stream": stream, "left": req.steps, "event": None, "f": f_dev,
+                "inflight": collections.deque()}
+
+    def ready(self, handle) -> bool:
+        q = handle["inflight"]
+        while q and q[0].query():
+            q.popleft()
+        return len(q) < self.MAX_IN_FLIGHT
 
     def advance(self, handle, n: int) -> None:
         handle["solver"].step(n)
         handle["left"] -= n
+        ev = self.torch.cuda.Event()
+        ev.record(handle["stream"])
+        handle["inflight"].append(ev)
         if handle["left"] == 0:
-            ev = self.torch.cuda.Event()
-            ev.record(handle["stream"])
             handle["event"] = ev
 
     def done(self, handle) -> bool:
@@ -139,7 +154,8 @@ class Server:
     def _tick(self) -> None:
         for req, handle, _ in self.active:
             left = handle["left"]
-            if left > 0 and not req.error:
+            ready = getattr(self.backend, "ready", None)
+            if left > 0 and not req.error and (ready is None or ready(handle)):
                 try:
                     self.backend.advance(handle, min(self.steps_per_tick, left))
                 except Exception as e:  # noqa: BLE001

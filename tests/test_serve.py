@@ -153,3 +153,21 @@ def test_a_request_that_cannot_start_is_retired():
     srv = Server(Refusing(clock), budget_bytes=10 ** 6, max_active=2, clock=clock)
     rep = srv.run([Request(i, (4, 4), steps=3, arrival=0.0) for i in range(3)])
     assert rep["requests"] == 3 and rep["failed"] == 1 and srv.used == 0
+
+
+def test_solves_that_are_not_ready_are_skipped_in_a_tick():
+    clock = FakeClock()
+
+    class Busy(FakeBackend):
+        def __init__(self, clock):
+            super().__init__(clock)
+            self.asked = 0
+
+        def ready(self, h):
+            self.asked += 1
+            return self.asked % 2 == 0     # every other query says "still busy"
+
+    be = Busy(clock)
+    srv = Server(be, budget_bytes=10 ** 6, max_active=3, clock=clock)
+    rep = srv.run([Request(i, (4, 4), steps=4, arrival=0.0) for i in range(3)])
+    assert rep["requests"] == 3 and rep["failed"] == 0 and be.asked > 12
