@@ -7,6 +7,8 @@
 
 #include <vector>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace {
@@ -16,7 +18,7 @@ constexpr double kPi = 3.14159265358979323846;
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t fini, eta, f, tmp, map, slot1, rec_key, rec_site, holes_a, holes_b, ovf, gwin, el, tay, tayf, M, a, da, d2a,
+  size_t fini, eta, f, tmp, map, slot1, rec_key, rec_site, holes_a, holes_b, ovf, gwin, seed, el, tay, tayf, M, a, da, d2a,
       thx, thv, thxf, thvf, ds, total;
 };
 
@@ -69,6 +71,7 @@ Layout layout(const vm_config* c) {
   L.ovf = take(2 * ne * 8);
   const long long pad = c->pad ? c->pad : c->elem_stride;
   L.gwin = take(vm::kGlobalBlocks * vm::global_window_words(c->nx, c->nv, pad) * 8);
+  L.seed = take(std::min<size_t>(ne, vm::kSeedRecords) * 96 * 8);
   L.el = take(12 * ne * 8);
   L.tay = take(16 * ne * 8);
   L.tayf = take(32 * ne * 4);
@@ -324,6 +327,8 @@ vm_status vm_create(const vm_config* c, void* d_workspace, size_t bytes, void* s
   s->overflow_list = (int2*)(base + L.ovf);
   s->overflow_list2 = s->overflow_list + ne_total(s);
   s->gwin = (unsigned long long*)(base + L.gwin);
+  s->t1seed = (unsigned long long*)(base + L.seed);
+  s->t1seed_cap = (int32_t)std::min<size_t>(ne_total(s), vm::kSeedRecords);
   s->el = (double*)(base + L.el);
   s->tay = (double*)(base + L.tay);
   s->tayf = (float*)(base + L.tayf);

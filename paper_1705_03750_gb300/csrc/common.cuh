@@ -57,6 +57,7 @@ struct DevState {
   int32_t bad_where;     // first failed bounds check (0: none); kept until read by vm_sync
   int32_t take[3];       // next item of each large-window launch (blocks fetch work dynamically)
   int32_t noverflow_back; // tier-1 escapes of elements with all eight neighbours (listed from the end)
+  int32_t nseed;          // tier-1 mask records written for the next tier
   uint32_t epoch;        // epoch of the current influence map (0..kEpochs-1)
   double Mtot;           // total mass of the last reconstruction
   double sum_mass, sum_kin, sum_pot;
@@ -73,6 +74,7 @@ constexpr uint32_t SLOT_EMPTY = 0xFFFFFFFFu;
 // Whole-lattice flood-fill windows of the last map tier: blocks working at
 // once, and 64-bit words of one window (three masks over the padded lattice).
 constexpr int kGlobalBlocks = 16;
+constexpr int kSeedRecords = 8192;  // tier-1 mask records kept per map (96 words each)
 inline size_t global_window_words(long long nx, long long nv, long long pad) {
   return 3 * (size_t)(nx + 2 * pad) * (size_t)((nv + 2 * pad + 63) / 64);
 }
@@ -133,6 +135,8 @@ struct vm_solver {
   int2* overflow_list;      // (element, window mode) for the second tier
   int2* overflow_list2;     // for the last-resort tier
   unsigned long long* gwin; // bit masks of the whole-lattice windows (kGlobalBlocks of them), kept zeroed
+  unsigned long long* t1seed; // tier-1 masks of escaped elements: t1seed_cap records of 3 x 32 words
+  int32_t t1seed_cap;
   double* el;               // 12 x ne
   double* tay;              // ne x 16
   float* tayf;              // ne x 32 (FP32 record, element units)

@@ -207,6 +207,10 @@ struct Slots {
   const double* tay;
   DevState* ds;
   uint32_t epoch;  // filled in on the device from ds->epoch
+  // tier 1's masks of escaped elements (32 rows x {component, tested,
+  // passing}), handed to tier 2's first window; seed_cap records at most
+  unsigned long long* seed;
+  int seed_cap;
 };
 
 // The map's epoch lives on the device (so that a captured step replays
@@ -228,6 +232,7 @@ __global__ void k_map_begin(DevState* ds) {
     ds->n_exact = 0;
     ds->take[0] = ds->take[1] = ds->take[2] = 0;
     ds->noverflow_back = 0;
+    ds->nseed = 0;
   }
 }
 
@@ -456,7 +461,7 @@ __device__ __forceinline__ void claim_element(const Grid& g, const double* __res
 // One element per warp.  (A warp-strided loop that prefetched the next
 // element's records cut the set-up latency but cost more in register spills
 // than it saved.)
-__global__ void __launch_bounds__(32 * TE, 6) k_claim_small(Grid g, const double* __restrict__ tay,
+__global__ void __launch_bounds__(32 * TE, 8) k_claim_small(Grid g, const double* __restrict__ tay,
                                                          const float* __restrict__ tayf, Slots Sin, float alo,
                                                          float ahi, int2* __restrict__ ovf_list) {
   __shared__ WarpShared shw[TE];
@@ -526,13 +531,10 @@ __device__ __forceinline__ void claim_element(const Grid& g, const double* __res
     atomicAdd(&S.ds->n_exact, 1);
     return pass_exact_g(g, tay, k, l, site_x(g, r0 + wr), site_v(g, c0 + wb));
   };
-  // the start decides whether there is a component at all
-  bool ok = false;
-  if (lane == TR / 2) ok = test(TR / 2, 32);
-  ok = __shfl_sync(FULL, ok, TR / 2);
-  if (!ok) return;
+  // The start site decides whether there is a component at all; it is
+  // tested with the first round (or certified with the inner sites).
   unsigned long long comp = 0ull, tested = 0ull, passing = 0ull;
-  if (lane == TR / 2) comp = tested = passing = 1ull << 32;
+  const unsigned long long seedbit = (lane == TR / 2) ? (1ull << 32) : 0ull;
 
   // predicted region, row by row: |T p|_x <= hx and |T p|_v <= hv for the
   // columns of this lane's row (p in element units).  Its inner part (the
@@ -573,7 +575,7 @@ __device__ __forceinline__ void claim_element(const Grid& g, const double* __res
       const int ilo = max((int)ceilf(blo), 0), ihi = min((int)floorf(bhi), 63);
       return (ihi >= ilo) ? col_mask(0, ilo, ihi + 1) : 0ull;
     };
-    const unsigned long long pred = cols(hx, hv) & valid & ~tested;
+    const unsigned long long pred = (cols(hx, hv) | seedbit) & valid;
     unsigned long long inner = (ix > 0.f && iv > 0.f) ? cols(ix, iv) & pred : 0ull;
     // Inner sites need no test when it is certain that they pass: on them
     // |T p| <= alpha - 0.02 - sx (the interval above), and q differs from
@@ -629,6 +631,10 @@ __device__ __forceinline__ void claim_element(const Grid& g, const double* __res
     __syncwarp();
     tested |= fa | fb;
     passing |= sh.passed[lane];
+    if (it == 0) {
+      if (!__shfl_sync(FULL, (unsigned)((passing >> 32) & 1ull), TR / 2)) return;  // the start fails
+      comp = seedbit;
+    }
     // close the component through every site known to pass
     for (int f = 0; f < TR * 64; f++) {
       const unsigned long long nc = run_fill(vfill(comp, passing, lane), passing);
@@ -651,6 +657,7 @@ __device__ __forceinline__ void claim_element(const Grid& g, const double* __res
   const bool ec = __any_sync(FULL, ((comp & 1ull) && clo == 0 && c0 - 1 >= -pad) ||
                                        ((comp >> 63) && chi == 64 && c0 + 64 < g.nv + pad));
   if (er || ec) {
+    int seed = -1;
     if (lane == 0) {
       // Outer elements (a neighbour missing) claim the long boundary bands,
       // the longest jobs of the next tier: they are listed from the front and
@@ -659,7 +666,18 @@ __device__ __forceinline__ void claim_element(const Grid& g, const double* __res
       bool outer = false;
       for (int q = 0; q < 9; q++) outer |= !sh.ex9[q];
       const int slot = outer ? atomicAdd(&S.ds->noverflow, 1) : g.ne - 1 - atomicAdd(&S.ds->noverflow_back, 1);
-      ovf_list[slot] = make_int2(m, sides << 4);  // attempt 0
+      seed = atomicAdd(&S.ds->nseed, 1);
+      if (seed >= S.seed_cap) seed = -1;
+      // attempt 0; bits 8 and up: the masks' record + 1 (0: none)
+      ovf_list[slot] = make_int2(m, ((seed + 1) << 8) | (sides << 4));
+    }
+    // the window's masks for the next tier (its first window starts from them)
+    seed = __shfl_sync(FULL, seed, 0);
+    if (seed >= 0) {
+      unsigned long long* rec = S.seed + (size_t)seed * (3 * TR);
+      rec[lane] = comp;
+      rec[TR + lane] = tested;
+      rec[2 * TR + lane] = passing;
     }
     return;
   }
@@ -699,7 +717,7 @@ constexpr int BLOCKS_PER_SM = 3;
 constexpr int BAND_R = 128, BAND_W = 20;  // band window: 128 rows across, up to 1280 sites along
 constexpr int FAT_R = 160, FAT_W = 12;    // 160 x 768 sites
 constexpr int LIST_CAP = 512;
-constexpr int AHEAD = 8;      // rows tested ahead of the component per round
+constexpr int AHEAD = 2;      // rows tested ahead of the component per round
 constexpr size_t SMEM_MAX = 227 * 1024;   // opt-in limit per block
 constexpr size_t SMEM_SM = 228 * 1024;    // shared memory per SM
 
@@ -806,8 +824,9 @@ __device__ __forceinline__ unsigned long long dilate(const unsigned long long* c
 }
 
 // Sites worth testing ahead of the component in word q: the word's column
-// within AHEAD rows of it, the whole word if a word of its row within two
-// holds some.
+// within AHEAD rows of it, the whole word if a neighbouring word of its row
+// holds some.  (Deeper speculation, 3 to 12 rows and two words, tested more
+// sites than it saved rounds; no word ahead made the rounds far too many.)
 __device__ __forceinline__ unsigned long long ahead(const unsigned long long* comp, const Win& W, int q) {
   const int r = q / W.W, w = q - r * W.W;
   unsigned long long d = dilate(comp, W, q);
@@ -815,9 +834,7 @@ __device__ __forceinline__ unsigned long long ahead(const unsigned long long* co
     if (r - k >= 0) d |= comp[q - k * W.W];
     if (r + k < W.R) d |= comp[q + k * W.W];
   }
-  if ((w > 0 && comp[q - 1]) || (w < W.W - 1 && comp[q + 1]) || (w > 1 && comp[q - 2]) ||
-      (w < W.W - 2 && comp[q + 2]))
-    d = ~0ull;
+  if ((w > 0 && comp[q - 1]) || (w < W.W - 1 && comp[q + 1])) d = ~0ull;
   return d;
 }
 
@@ -860,7 +877,7 @@ __global__ void __launch_bounds__(BT, BLOCKS_PER_SM) k_claim_big(Grid g, const d
       __syncthreads();  // every thread has read H.item before it is taken again
       continue;
     }
-    const int sides = it2.y >> 4, attempt = it2.y & 15;
+    const int sides = (it2.y >> 4) & 15, attempt = it2.y & 15, seed = (it2.y >> 8) - 1;
     const int mode = kGlobal ? MODE_GLOBAL : mode_for(sides, attempt);
     load_elem9(g, m, tay, tayf, H.E);
     __syncthreads();
@@ -892,6 +909,41 @@ __global__ void __launch_bounds__(BT, BLOCKS_PER_SM) k_claim_big(Grid g, const d
       H.ok = ok;
     }
     __syncthreads();
+    // Tier 1's component, tested and passing masks, when this is the first
+    // window of an element that escaped it (not transposed, in shared memory):
+    // its component is a connected part of this window's, and its tests are
+    // the same tests, so the fill continues from there.
+    if (!kGlobal && seed >= 0 && seed < S.seed_cap && !W.trans && H.ok) {
+      if (tid < TR) {
+        const unsigned long long* rec = S.seed + (size_t)seed * (3 * TR);
+        const unsigned long long mc = rec[tid], mt = rec[TR + tid], mp = rec[2 * TR + tid];
+        const long long r = (i0 - TR / 2 + tid) - W.r0;
+        const long long off = (j0 - 32) - W.c0;  // window bit of tier 1's column 0
+        const long long w0 = (off >= 0) ? off / 64 : -((-off + 63) / 64);
+        const int sh = (int)(off - 64 * w0);
+        if (r >= 0 && r < W.R && (mc | mt | mp)) {
+          for (int k = 0; k < 2; k++) {
+            const long long w = w0 + k;
+            if (w < 0 || w >= W.W) continue;
+            auto part = [&](unsigned long long x) -> unsigned long long {
+              return k == 0 ? (x << sh) : (sh ? (x >> (64 - sh)) : 0ull);
+            };
+            const int q = (int)(r * W.W + w);
+            const unsigned long long vmask = valid_mask(W, (int)r, (int)w);
+            comp[q] |= part(mc) & vmask;
+            eval[q] |= part(mt) & vmask;
+            pass[q] |= part(mp) & vmask;
+            if (part(mc) & vmask) {
+              atomicMin(&H.rmin, (int)r);
+              atomicMax(&H.rmax, (int)r);
+              atomicMin(&H.wmin, (int)w);
+              atomicMax(&H.wmax, (int)w);
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
     bool escaped = false;
     if (H.ok) {
       for (int it = 0; it < NW * 64; it++) {
@@ -1172,7 +1224,7 @@ bool map_prepare(const Grid& g) {
 }
 
 void launch_map(vm_solver* s) {
-  Slots S{s->map, s->slot1, s->rec_key, s->rec_site, s->rec_cap, s->tay, s->ds, 0u};
+  Slots S{s->map, s->slot1, s->rec_key, s->rec_site, s->rec_cap, s->tay, s->ds, 0u, s->t1seed, s->t1seed_cap};
   float alo, ahi;
   alpha_bounds(s->g.alpha, alo, ahi);
   int ps = prof_begin(s, KID_MAP_CLEAR);
