@@ -395,6 +395,7 @@ struct __align__(16) WarpShared {
   int ex9[9];
   float offu[9], offv[9];
   unsigned long long passed[TR];  // passing sites found by one round, per window row
+  unsigned long long unsure[TR];  // sites of the round the FP32 bound could not settle
   unsigned short item[TCAP];      // compacted list (lane << 6 | bit)
 };
 
@@ -525,12 +526,11 @@ __device__ __forceinline__ void claim_element(const Grid& g, const double* __res
   const unsigned long long valid = (irow >= -pad && irow < g.nx + pad) ? col_mask(0, clo, chi) : 0ull;
   // test of window site (row wr, column wb); offsets from the start in
   // 32-bit integers (a 64-bit conversion would take the FP64 pipe)
-  auto test = [&](int wr, int wb) -> bool {
-    const int r = pass_f32(c, (float)(wr - TR / 2), (float)(wb - 32));
-    if (r >= 0) return r == 1;
-    atomicAdd(&S.ds->n_exact, 1);
-    return pass_exact_g(g, tay, k, l, site_x(g, r0 + wr), site_v(g, c0 + wb));
-  };
+  // FP32 test of window site (row wr, column wb): 1 passes, 0 fails, -1 the
+  // bound does not settle it (the exact test runs after the round, outside
+  // the test loop, so that the loop makes no call).  Offsets from the start
+  // in 32-bit integers (a 64-bit conversion would take the FP64 pipe).
+  auto test = [&](int wr, int wb) -> int { return pass_f32(c, (float)(wr - TR / 2), (float)(wb - 32)); };
   // The start site decides whether there is a component at all; it is
   // tested with the first round (or certified with the inner sites).
   unsigned long long comp = 0ull, tested = 0ull, passing = 0ull;
@@ -617,6 +617,7 @@ __device__ __forceinline__ void claim_element(const Grid& g, const double* __res
     if (total == 0 && it > 0) break;
     if (total > 0) rounds++;
     sh.passed[lane] = 0ull;
+    sh.unsure[lane] = 0ull;
     for (int b0 = 0; b0 < total; b0 += TCAP) {
       __syncwarp();
       list_chunk(sh.item, fa, inca - ca, inca, b0, lane);
@@ -625,12 +626,20 @@ __device__ __forceinline__ void claim_element(const Grid& g, const double* __res
       const int n = min(total - b0, TCAP);
       for (int e = lane; e < n; e += 32) {
         const int code = sh.item[e], r = code >> 6, b = code & 63;
-        if (test(r, b)) atomicOr(&sh.passed[r], 1ull << b);
+        const int res = test(r, b);
+        if (res == 1) atomicOr(&sh.passed[r], 1ull << b);
+        if (res < 0) atomicOr(&sh.unsure[r], 1ull << b);
       }
     }
     __syncwarp();
     tested |= fa | fb;
     passing |= sh.passed[lane];
+    // the exact FP64 test of this row's unsettled sites (rare)
+    for (unsigned long long un = sh.unsure[lane]; un; un &= un - 1ull) {
+      const int b = __ffsll((long long)un) - 1;
+      atomicAdd(&S.ds->n_exact, 1);
+      if (pass_exact_g(g, tay, k, l, site_x(g, irow), site_v(g, c0 + b))) passing |= 1ull << b;
+    }
     if (it == 0) {
       if (!__shfl_sync(FULL, (unsigned)((passing >> 32) & 1ull), TR / 2)) return;  // the start fails
       comp = seedbit;

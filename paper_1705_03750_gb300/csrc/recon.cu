@@ -396,7 +396,7 @@ __device__ __forceinline__ float recon_fast32(const Grid& g, const float* __rest
   return (m >= 0) ? v : 0.f;
 }
 
-__global__ void __launch_bounds__(256) k_recon32(Grid g, const uint32_t* __restrict__ map, const DevState* ds,
+__global__ void __launch_bounds__(256, 6) k_recon32(Grid g, const uint32_t* __restrict__ map, const DevState* ds,
                                                  const double* __restrict__ tay, const float* __restrict__ tayf,
                                                  const float* __restrict__ fini, float* __restrict__ f,
                                                  double* __restrict__ M) {

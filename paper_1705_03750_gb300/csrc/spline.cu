@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(128) k_rows_scan(Grid g, const R* __restrict__
 // swept (double buffering), so that memory latency overlaps the recurrence.
 template <typename R, typename C>
 __global__ void __launch_bounds__(32) k_cols(Grid g, R* __restrict__ x, const C* __restrict__ th) {
-  constexpr int CK = 16;
+  constexpr int CK = 32;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= g.nv) return;
   const int nx = g.nx, nv = g.nv;
