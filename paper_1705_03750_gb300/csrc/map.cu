@@ -8,19 +8,22 @@
 //
 //   1. a 32 x 64 window held in registers (one 64-bit row per lane), one
 //      warp per element.  The first round tests the region predicted by the
-//      linear part of the element's map; the component is then closed
-//      through the passing sites by shuffle scans, and further rounds test
-//      only sites next to it left untested (tests compacted into a list so
-//      that all 32 lanes share them);
+//      linear part of the element's map (its inner part, where a bound on
+//      the second-order terms shows that every site passes, needs no test);
+//      the component is then closed through the passing sites by shuffle
+//      scans, and further rounds test only sites next to it left untested
+//      (tests compacted into a list so that all 32 lanes share them);
 //   2. for the elements whose component reached the edge of tier 1, up to
-//      three attempts with larger windows, in an order set by the sides it
-//      escaped from: a band window 128 sites across and as long as shared
-//      memory allows along v (the whole padded lattice at 4096^2), the same
-//      along x, and a 640 x 640 window.  Outer-layer elements whose
-//      neighbours moved away claim long thin bands; to cross them in few
-//      rounds, any 64-site word the component reaches is tested whole and
-//      the component is extended through runs of passing sites inside the
-//      word with one carry-propagating addition.
+//      two attempts with larger windows in shared memory, in an order set by
+//      the sides it escaped from (a band window 128 sites across and up to
+//      1280 along v or along x, or a 160 x 768 window), the first starting
+//      from tier 1's masks of the element; then
+//   3. the whole padded lattice, its masks in global memory.
+//      Outer-layer elements whose neighbours moved away claim long thin
+//      bands; to cross them in few rounds, any 64-site word near the
+//      component is tested whole (two rows ahead, one word ahead) and the
+//      component is extended through runs of passing sites inside a word
+//      with one carry-propagating addition.
 //
 // A window whose component reaches its edge claims nothing: the next, larger
 // window's component contains it.  Claims are made once the component is
@@ -726,16 +729,18 @@ constexpr int BLOCKS_PER_SM = 3;
 constexpr int BAND_R = 128, BAND_W = 20;  // band window: 128 rows across, up to 1280 sites along
 constexpr int FAT_R = 160, FAT_W = 12;    // 160 x 768 sites
 constexpr int LIST_CAP = 512;
+constexpr int UNS_CAP = 128;
 constexpr int AHEAD = 2;      // rows tested ahead of the component per round
 constexpr size_t SMEM_MAX = 227 * 1024;   // opt-in limit per block
 constexpr size_t SMEM_SM = 228 * 1024;    // shared memory per SM
 
 struct BigHeader {
   Elem9 E;
-  int item, nlist, ok;
+  int item, nlist, ok, nuns;
   int rmin, rmax, wmin, wmax;  // rows / words holding component bits
   int list[LIST_CAP];          // words to test this round
   unsigned long long lmask[LIST_CAP];  // their untested valid sites
+  int uns[UNS_CAP];            // sites of the round the FP32 bound left unsettled (word << 6 | bit)
 };
 
 // Window modes of the attempts after tier 1, by the sides its component
@@ -956,7 +961,7 @@ __global__ void __launch_bounds__(BT, BLOCKS_PER_SM) k_claim_big(Grid g, const d
     bool escaped = false;
     if (H.ok) {
       for (int it = 0; it < NW * 64; it++) {
-        if (tid == 0) H.nlist = 0;
+        if (tid == 0) H.nlist = H.nuns = 0;
         const int ra = max(H.rmin - AHEAD, 0), rb = min(H.rmax + AHEAD, W.R - 1);
         const int wa = max(H.wmin - 1, 0), wb = min(H.wmax + 1, W.W - 1);
         const int bw = wb - wa + 1, nbox = (rb - ra + 1) * bw;
@@ -991,7 +996,25 @@ __global__ void __launch_bounds__(BT, BLOCKS_PER_SM) k_claim_big(Grid g, const d
           const int r = q / W.W, w = q - r * W.W;
           long long i, j;
           site_of(W, r, 64 * w + b, i, j);
-          if (test_site(g, H.E, c, i0, j0, i, j)) atomicOr(&pass[q], 1ull << b);
+          const int res = pass_f32(c, (float)(int)(i - i0), (float)(int)(j - j0));
+          if (res == 1) atomicOr(&pass[q], 1ull << b);
+          if (res < 0) {
+            // the exact test after the loop (no call inside it); beyond the
+            // list's room the site is left unevaluated and taken next round
+            const int u = atomicAdd(&H.nuns, 1);
+            if (u < UNS_CAP)
+              H.uns[u] = (q << 6) | b;
+            else
+              atomicAnd(&eval[q], ~(1ull << b));
+          }
+        }
+        __syncthreads();
+        for (int u = tid; u < min(H.nuns, UNS_CAP); u += BT) {
+          const int q = H.uns[u] >> 6, b = H.uns[u] & 63;
+          const int r = q / W.W, w = q - r * W.W;
+          long long i, j;
+          site_of(W, r, 64 * w + b, i, j);
+          if (pass_exact(g, H.E.T9, H.E.ex9, site_x(g, i), site_v(g, j))) atomicOr(&pass[q], 1ull << b);
         }
         __syncthreads();
         // C: close the component through the passing sites (runs inside a
