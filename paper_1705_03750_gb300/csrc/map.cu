@@ -133,8 +133,14 @@ __device__ __forceinline__ int range_f(float q, float e, float alo, float ahi) {
   return 0;
 }
 
+// The map reads words 0-17 of the FP32 records (as five float4).  Their
+// shared-memory copies have a stride of 20 words, so that lanes evaluating
+// different neighbours read the same word from different banks.
+constexpr int TF_M = 20;
+static_assert(TF_C2V < TF_M && TF_M % 4 == 0, "map's FP32 record words");
+
 struct Ctx9 {
-  const float (*F9)[TF_N];
+  const float (*F9)[TF_M];
   const int* ex9;
   const float* offu;  // (i0 - u_m') for the 9 elements, i0 the window's start site
   const float* offv;
@@ -151,20 +157,23 @@ __device__ __forceinline__ int pass_f32(const Ctx9& c, float di, float dj) {
   const float d2 = m.qx * m.qx + m.qv * m.qv;
   const float A2 = m.ax * m.ax + m.av * m.av;
   const float e2 = kRelD * A2 + kAbs * (1.f + A2);
-  const int a0 = (ra == 1) ? -1 : 0, a1 = (ra == 3) ? 1 : 0;
-  const int b0 = (rb == 1) ? -1 : 0, b1 = (rb == 3) ? 1 : 0;
-  for (int a = a0; a <= a1; a++)
-    for (int b = b0; b <= b1; b++) {
-      if (a == 0 && b == 0) continue;
-      const int q = (a + 1) * 3 + (b + 1);
-      if (!c.ex9[q]) continue;
-      const QF n = qeval(c.F9[q], (di + c.offu[q]) * c.inv_s, (dj + c.offv[q]) * c.inv_s);
-      const float d2n = n.qx * n.qx + n.qv * n.qv;
-      const float An = n.ax * n.ax + n.av * n.av;
-      const float en = kRelD * An + kAbs * (1.f + An);
-      if (d2n + en < d2 - e2) return 0;
-      if (!(d2n - en >= d2 + e2)) return -1;
-    }
+  // The neighbours to compare with: (A, 0), (0, B) and (A, B) for the
+  // nonzero ones of A, B (the side of the alpha box q leaves on each axis).
+  // At most three evaluations, in one loop whose trip count is the only
+  // thing that differs between lanes.
+  const int A = ra - 2, B = rb - 2;
+  const int qa = (A + 1) * 3 + 1, qb = 3 + (B + 1), qab = (A + 1) * 3 + (B + 1);
+  const int cnt = (A != 0 && B != 0) ? 3 : 1;
+  for (int t = 0; t < cnt; t++) {
+    const int q = (t == 0) ? (A != 0 ? qa : qb) : (t == 1 ? qb : qab);
+    if (!c.ex9[q]) continue;
+    const QF n = qeval(c.F9[q], (di + c.offu[q]) * c.inv_s, (dj + c.offv[q]) * c.inv_s);
+    const float d2n = n.qx * n.qx + n.qv * n.qv;
+    const float An = n.ax * n.ax + n.av * n.av;
+    const float en = kRelD * An + kAbs * (1.f + An);
+    if (d2n + en < d2 - e2) return 0;
+    if (!(d2n - en >= d2 + e2)) return -1;
+  }
   return 1;
 }
 
@@ -307,7 +316,7 @@ enum : int { MODE_BAND_V = 0, MODE_BAND_X = 1, MODE_FAT = 2, MODE_GLOBAL = 3 };
 // FP32, and the FP32 offsets of their positions from the start site.
 struct Elem9 {
   double T9[9][TY_N];
-  float F9[9][TF_N];
+  float F9[9][TF_M];
   int ex9[9];
   float offu[9], offv[9];
 };
@@ -322,8 +331,8 @@ __device__ __forceinline__ void load_elem9(const Grid& g, int m, const double* _
     E.T9[q][c] = ex ? tay[(size_t)(kk * g.Lv + ll) * TY_N + c] : 0.0;
     if (c == 0) E.ex9[q] = ex;
   }
-  for (int idx = threadIdx.x; idx < 9 * TF_N; idx += blockDim.x) {
-    const int q = idx / TF_N, c = idx - q * TF_N;
+  for (int idx = threadIdx.x; idx < 9 * TF_M; idx += blockDim.x) {
+    const int q = idx / TF_M, c = idx - q * TF_M;
     const int kk = k + q / 3 - 1, ll = l + q % 3 - 1;
     const bool ex = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
     E.F9[q][c] = ex ? tayf[(size_t)(kk * g.Lv + ll) * TF_N + c] : 0.f;
@@ -394,7 +403,7 @@ __device__ __noinline__ bool pass_exact_g(const Grid& g, const double* __restric
 }
 
 struct __align__(16) WarpShared {
-  float F9[9][TF_N];
+  float F9[9][TF_M];
   int ex9[9];
   float offu[9], offv[9];
   unsigned long long passed[TR];  // passing sites found by one round, per window row
@@ -494,8 +503,8 @@ __device__ __forceinline__ void claim_element(const Grid& g, const double* __res
       wpos = __ldg(tq + TY_W);
     }
   }
-  for (int idx = lane; idx < 9 * (TF_N / 4); idx += 32) {
-    const int q = idx >> 3, c4 = idx & 7;
+  for (int idx = lane; idx < 9 * (TF_M / 4); idx += 32) {
+    const int q = idx / (TF_M / 4), c4 = idx - q * (TF_M / 4);
     const int kk = k + q / 3 - 1, ll = l + q % 3 - 1;
     const bool ex = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
     const float4 v = ex ? __ldg(reinterpret_cast<const float4*>(tayf + (size_t)(kk * g.Lv + ll) * TF_N) + c4)
@@ -729,18 +738,16 @@ constexpr int BLOCKS_PER_SM = 3;
 constexpr int BAND_R = 128, BAND_W = 20;  // band window: 128 rows across, up to 1280 sites along
 constexpr int FAT_R = 160, FAT_W = 12;    // 160 x 768 sites
 constexpr int LIST_CAP = 512;
-constexpr int UNS_CAP = 128;
 constexpr int AHEAD = 2;      // rows tested ahead of the component per round
 constexpr size_t SMEM_MAX = 227 * 1024;   // opt-in limit per block
 constexpr size_t SMEM_SM = 228 * 1024;    // shared memory per SM
 
 struct BigHeader {
   Elem9 E;
-  int item, nlist, ok, nuns;
+  int item, nlist, ok;
   int rmin, rmax, wmin, wmax;  // rows / words holding component bits
   int list[LIST_CAP];          // words to test this round
   unsigned long long lmask[LIST_CAP];  // their untested valid sites
-  int uns[UNS_CAP];            // sites of the round the FP32 bound left unsettled (word << 6 | bit)
 };
 
 // Window modes of the attempts after tier 1, by the sides its component
@@ -961,7 +968,7 @@ __global__ void __launch_bounds__(BT, BLOCKS_PER_SM) k_claim_big(Grid g, const d
     bool escaped = false;
     if (H.ok) {
       for (int it = 0; it < NW * 64; it++) {
-        if (tid == 0) H.nlist = H.nuns = 0;
+        if (tid == 0) H.nlist = 0;
         const int ra = max(H.rmin - AHEAD, 0), rb = min(H.rmax + AHEAD, W.R - 1);
         const int wa = max(H.wmin - 1, 0), wb = min(H.wmax + 1, W.W - 1);
         const int bw = wb - wa + 1, nbox = (rb - ra + 1) * bw;
@@ -996,25 +1003,7 @@ __global__ void __launch_bounds__(BT, BLOCKS_PER_SM) k_claim_big(Grid g, const d
           const int r = q / W.W, w = q - r * W.W;
           long long i, j;
           site_of(W, r, 64 * w + b, i, j);
-          const int res = pass_f32(c, (float)(int)(i - i0), (float)(int)(j - j0));
-          if (res == 1) atomicOr(&pass[q], 1ull << b);
-          if (res < 0) {
-            // the exact test after the loop (no call inside it); beyond the
-            // list's room the site is left unevaluated and taken next round
-            const int u = atomicAdd(&H.nuns, 1);
-            if (u < UNS_CAP)
-              H.uns[u] = (q << 6) | b;
-            else
-              atomicAnd(&eval[q], ~(1ull << b));
-          }
-        }
-        __syncthreads();
-        for (int u = tid; u < min(H.nuns, UNS_CAP); u += BT) {
-          const int q = H.uns[u] >> 6, b = H.uns[u] & 63;
-          const int r = q / W.W, w = q - r * W.W;
-          long long i, j;
-          site_of(W, r, 64 * w + b, i, j);
-          if (pass_exact(g, H.E.T9, H.E.ex9, site_x(g, i), site_v(g, j))) atomicOr(&pass[q], 1ull << b);
+          if (test_site(g, H.E, c, i0, j0, i, j)) atomicOr(&pass[q], 1ull << b);
         }
         __syncthreads();
         // C: close the component through the passing sites (runs inside a
