@@ -12,7 +12,8 @@
 //      the second-order terms shows that every site passes, needs no test);
 //      the component is then closed through the passing sites by shuffle
 //      scans, and further rounds test only sites next to it left untested
-//      (tests compacted into a list so that all 32 lanes share them);
+//      (the 32 lanes share a round's tests: lane e of a pass takes the
+//      e-th untested site, found by a search of the rows' counts);
 //   2. for the elements whose component reached the edge of tier 1, up to
 //      two attempts with larger windows in shared memory, in an order set by
 //      the sides it escaped from (a band window 128 sites across and up to
@@ -408,7 +409,7 @@ struct __align__(16) WarpShared {
   float offu[9], offv[9];
   unsigned long long passed[TR];  // passing sites found by one round, per window row
   unsigned long long unsure[TR];  // sites of the round the FP32 bound could not settle
-  unsigned short item[TCAP];      // compacted list (lane << 6 | bit)
+  unsigned short item[TCAP];      // compacted list of the claims (lane << 6 | bit)
 };
 
 // Inclusive sum of v over the lanes of the warp.
@@ -442,6 +443,21 @@ __device__ __forceinline__ unsigned long long vfill(unsigned long long comp, uns
   return gd | gu;
 }
 
+// Position of the n-th set bit (from 0, counted from bit 0) of x; x has
+// more than n set bits.
+__device__ __forceinline__ int nth_bit(unsigned long long x, int n) {
+  int pos = 0;
+  unsigned w = (unsigned)x;
+  int c = __popc(w);
+  if (n >= c) { n -= c; pos = 32; w = (unsigned)(x >> 32); }
+  c = __popc(w & 0xFFFFu); if (n >= c) { n -= c; pos += 16; w >>= 16; }
+  c = __popc(w & 0xFFu); if (n >= c) { n -= c; pos += 8; w >>= 8; }
+  c = __popc(w & 0xFu); if (n >= c) { n -= c; pos += 4; w >>= 4; }
+  c = __popc(w & 0x3u); if (n >= c) { n -= c; pos += 2; w >>= 2; }
+  if (n >= (int)(w & 1u)) pos += 1;
+  return pos;
+}
+
 // Write the positions of the set bits of `bits` (one word per lane) with
 // list index in [b0, b0 + TCAP) to the list; excl / incl: the lane's range.
 __device__ __forceinline__ void list_chunk(unsigned short* item, unsigned long long bits, int excl, int incl, int b0,
@@ -463,7 +479,8 @@ __device__ __forceinline__ void list_chunk(unsigned short* item, unsigned long l
 // and by a bound on the second-order terms); every round then closes the
 // component through all sites known to pass (vertical scan + horizontal
 // runs, to a fixed point) and tests the sites next to it not yet tested.
-// Tests are compacted into a list shared by the 32 lanes.  The order of the
+// The 32 lanes share a round's tests (the e-th test of a pass goes to
+// lane e, whatever row holds it).  The order of the
 // tests does not change the result: the component is the connected set of
 // passing sites reached from the start, and the loop ends only when every
 // site next to it has been tested.  Claims are made once at the end.
@@ -630,14 +647,26 @@ __device__ __forceinline__ void claim_element(const Grid& g, const double* __res
     if (total > 0) rounds++;
     sh.passed[lane] = 0ull;
     sh.unsure[lane] = 0ull;
-    for (int b0 = 0; b0 < total; b0 += TCAP) {
-      __syncwarp();
-      list_chunk(sh.item, fa, inca - ca, inca, b0, lane);
-      list_chunk(sh.item, fb, ta + incb - cb, ta + incb, b0, lane);
-      __syncwarp();
-      const int n = min(total - b0, TCAP);
-      for (int e = lane; e < n; e += 32) {
-        const int code = sh.item[e], r = code >> 6, b = code & 63;
+    __syncwarp();
+    // Test e of the round (fa's sites, then fb's, row by row) is found by
+    // a binary search of the lanes' inclusive counts (both lists' counts
+    // packed in one word) and a select in the row's word.
+    const unsigned incp = (unsigned)inca | ((unsigned)incb << 16);
+    for (int e0 = 0; e0 < total; e0 += 32) {
+      const int e = e0 + lane;
+      const bool inA = e < ta;
+      const int key = inA ? e : e - ta, sh16 = inA ? 0 : 16;
+      int r = 0;
+#pragma unroll
+      for (int st = 16; st; st >>= 1) {
+        const unsigned v = __shfl_sync(FULL, incp, r + st - 1);
+        if ((int)((v >> sh16) & 0xFFFFu) <= key) r += st;
+      }
+      const unsigned vr = __shfl_sync(FULL, incp, r);
+      const unsigned long long wa = __shfl_sync(FULL, fa, r), wb = __shfl_sync(FULL, fb, r);
+      if (e < total) {
+        const unsigned long long w = inA ? wa : wb;
+        const int b = nth_bit(w, key - ((int)((vr >> sh16) & 0xFFFFu) - __popcll(w)));
         const int res = test(r, b);
         if (res == 1) atomicOr(&sh.passed[r], 1ull << b);
         if (res < 0) atomicOr(&sh.unsure[r], 1ull << b);
