@@ -874,9 +874,11 @@ __device__ __forceinline__ unsigned long long dilate(const unsigned long long* c
 }
 
 // Sites worth testing ahead of the component in word q: the word's column
-// within AHEAD rows of it, the whole word if a neighbouring word of its row
-// holds some.  (Deeper speculation, 3 to 12 rows and two words, tested more
-// sites than it saved rounds; no word ahead made the rounds far too many.)
+// within AHEAD rows of it, the whole word if the word or a neighbouring word
+// of its row holds some.  (Deeper speculation, 3 to 12 rows and two words,
+// tested more sites than it saved rounds; growing inside a word one site per
+// round, as the column rule alone does, made a component that starts from one
+// site and runs along the bits take one round per site.)
 __device__ __forceinline__ unsigned long long ahead(const unsigned long long* comp, const Win& W, int q) {
   const int r = q / W.W, w = q - r * W.W;
   unsigned long long d = dilate(comp, W, q);
@@ -884,7 +886,7 @@ __device__ __forceinline__ unsigned long long ahead(const unsigned long long* co
     if (r - k >= 0) d |= comp[q - k * W.W];
     if (r + k < W.R) d |= comp[q + k * W.W];
   }
-  if ((w > 0 && comp[q - 1]) || (w < W.W - 1 && comp[q + 1])) d = ~0ull;
+  if (comp[q] || (w > 0 && comp[q - 1]) || (w < W.W - 1 && comp[q + 1])) d = ~0ull;
   return d;
 }
 
