@@ -777,7 +777,52 @@ struct BigHeader {
   int rmin, rmax, wmin, wmax;  // rows / words holding component bits
   int list[LIST_CAP];          // words to test this round
   unsigned long long lmask[LIST_CAP];  // their untested valid sites
+  int lcnt[LIST_CAP];          // inclusive counts of the listed sites
+  int wtot[BT / 32];           // per-warp totals of a block scan
 };
+
+// Block-wide inclusive sums out[e] = cnt(0) + ... + cnt(e) for e < n (each
+// thread sums a contiguous run of entries); returns the total.  Called by
+// every thread of the block.
+template <class Cnt>
+__device__ __forceinline__ int block_incl(int n, Cnt cnt, int* out, int* wtot) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int per = (n + BT - 1) / BT;
+  const int a = min(tid * per, n), b = min(a + per, n);
+  int sum = 0;
+  for (int e = a; e < b; e++) {
+    sum += cnt(e);
+    out[e] = sum;
+  }
+  const int incl = warp_incl(sum, lane);
+  if (lane == 31) wtot[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    const int v = warp_incl(lane < BT / 32 ? wtot[lane] : 0, lane);
+    __syncwarp();
+    if (lane < BT / 32) wtot[lane] = v;
+  }
+  __syncthreads();
+  const int off = incl - sum + (wid ? wtot[wid - 1] : 0);
+  for (int e = a; e < b; e++) out[e] += off;
+  const int total = wtot[BT / 32 - 1];
+  __syncthreads();
+  return total;
+}
+
+// Entry holding item e of a compacted list (first s with incl[s] > e; e is
+// below incl[n - 1]).
+__device__ __forceinline__ int find_entry(const int* incl, int n, int e) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (incl[mid] > e)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  return lo;
+}
 
 // Window modes of the attempts after tier 1, by the sides its component
 // escaped from (1: rows, 2: columns, 3: both); the last attempt covers the
@@ -1025,11 +1070,14 @@ __global__ void __launch_bounds__(BT, BLOCKS_PER_SM) k_claim_big(Grid g, const d
           }
         }
         if (!__syncthreads_or(open)) break;
-        // B: the listed sites' tests
+        // B: the listed sites' tests, compacted: test e goes to thread
+        // e mod BT whatever word holds it
         const int nl = min(H.nlist, LIST_CAP);
-        for (int e = tid; e < nl * 64; e += BT) {
-          const int s = e >> 6, b = e & 63;
-          if (!((H.lmask[s] >> b) & 1ull)) continue;
+        const int ntest = block_incl(nl, [&](int s) { return __popcll(H.lmask[s]); }, H.lcnt, H.wtot);
+        for (int e = tid; e < ntest; e += BT) {
+          const int s = find_entry(H.lcnt, nl, e);
+          const unsigned long long lm = H.lmask[s];
+          const int b = nth_bit(lm, e - (H.lcnt[s] - __popcll(lm)));
           const int q = H.list[s];
           const int r = q / W.W, w = q - r * W.W;
           long long i, j;
@@ -1087,26 +1135,29 @@ __global__ void __launch_bounds__(BT, BLOCKS_PER_SM) k_claim_big(Grid g, const d
             atomicOr(&S.ds->err, ERR_PATCH_OVERFLOW);
         }
       } else {
-        // claims, a word per thread, several exchanges in flight
+        // claims: the component's sites compacted over the box's words
+        // (their inclusive counts in the eval masks, no longer needed), up
+        // to 8 exchanges in flight per thread
         const int bw = H.wmax - H.wmin + 1, nbox = (H.rmax - H.rmin + 1) * bw;
-        for (int e = tid; e < nbox; e += BT) {
-          const int r = H.rmin + e / bw, w = H.wmin + e % bw;
-          unsigned long long cb = comp[r * W.W + w];
-          while (cb) {
-            size_t pos[8];
+        int* ccnt = reinterpret_cast<int*>(eval);  // nbox <= NW ints fit in NW words
+        auto word_of = [&](int e) { return (H.rmin + e / bw) * W.W + H.wmin + e % bw; };
+        const int nsite = block_incl(nbox, [&](int e) { return __popcll(comp[word_of(e)]); }, ccnt, H.wtot);
+        for (int e0 = 0; e0 < nsite; e0 += 8 * BT) {
+          size_t pos[8];
 #pragma unroll
-            for (int u = 0; u < 8; u++) {
-              pos[u] = ~(size_t)0;
-              if (cb) {
-                const int b = __ffsll((long long)cb) - 1;
-                cb &= cb - 1ull;
-                long long i, j;
-                site_of(W, r, 64 * w + b, i, j);
-                if (i >= 0 && i < g.nx && j >= 0 && j < g.nv) pos[u] = (size_t)i * g.nv + j;
-              }
+          for (int u = 0; u < 8; u++) {
+            const int e = e0 + u * BT + tid;
+            pos[u] = ~(size_t)0;
+            if (e < nsite) {
+              const int x = find_entry(ccnt, nbox, e), q = word_of(x);
+              const unsigned long long cw = comp[q];
+              const int b = nth_bit(cw, e - (ccnt[x] - __popcll(cw)));
+              long long i, j;
+              site_of(W, q / W.W, 64 * (q % W.W) + b, i, j);
+              if (i >= 0 && i < g.nx && j >= 0 && j < g.nv) pos[u] = (size_t)i * g.nv + j;
             }
-            claim_sites(S, g, pos, m);
           }
+          claim_sites(S, g, pos, m);
         }
       }
     }
@@ -1122,6 +1173,9 @@ __global__ void __launch_bounds__(BT, BLOCKS_PER_SM) k_claim_big(Grid g, const d
         eval[q] = 0ull;
         pass[q] = 0ull;
       }
+      // and the claims' counts at the start of the eval masks
+      const int ncl = escaped ? 0 : (H.rmax - H.rmin + 1) * (H.wmax - H.wmin + 1);
+      for (int q = tid; q < (ncl + 1) / 2; q += BT) eval[q] = 0ull;
     }
     __syncthreads();
   }
