@@ -118,7 +118,7 @@ def algorithmic(kernel: str, rc, fp32: bool, ne: int):
         return n * (4 + 2 * sr) + ne * tay, n, f"{4 + 2 * sr} B/site + 128 B/element"
     if kernel == "remap_resample":
         return n * (4 + 2 * sr) + ne * tay, n, f"{4 + 2 * sr} B/site + 128 B/element"
-    if kernel in ("claim_small", "claim_large"):
+    if kernel in ("claim_pair", "claim_small", "claim_large"):
         # the influence map written once (4 B/site), each element's record read once
         return n * 4 + ne * tay, n, "4 B/site + 128 B/element"
     if kernel in ("spline_rows", "spline_cols"):

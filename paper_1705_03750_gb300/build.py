@@ -40,7 +40,8 @@ def _flags(verbose_ptxas: bool) -> list[str]:
 def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
-    deps = [src, os.path.join(CSRC, "common.cuh"), os.path.join(HERE, "..", "include", "vlamet.h")]
+    deps = [src, os.path.join(HERE, "..", "include", "vlamet.h")]
+    deps += [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".cuh")]
     return os.path.getmtime(obj) < max(os.path.getmtime(d) for d in deps if os.path.exists(d))
 
 

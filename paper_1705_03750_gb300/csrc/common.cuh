@@ -58,6 +58,7 @@ struct DevState {
   int32_t take[3];       // next item of each large-window launch (blocks fetch work dynamically)
   int32_t noverflow_back; // tier-1 escapes of elements with all eight neighbours (listed from the end)
   int32_t nseed;          // tier-1 mask records written for the next tier
+  int32_t n_pair_esc;     // tier-0 escapes listed for tier 1
   uint32_t epoch;        // epoch of the current influence map (0..kEpochs-1)
   double Mtot;           // total mass of the last reconstruction
   double sum_mass, sum_kin, sum_pot;
@@ -107,7 +108,7 @@ enum KernelId {
   KID_DRIFT = 0, KID_TAYLOR, KID_KICK_DRIFT, KID_RESET, KID_SCAN_FORCE, KID_DIAG,
   KID_MAP_CLEAR, KID_CLAIM_SMALL, KID_CLAIM_LARGE, KID_FINALIZE, KID_HOLES,
   KID_RESOLVE, KID_READ_MAP,
-  KID_RECON, KID_REMAP, KID_CONVERT, KID_SPLINE_ROWS, KID_SPLINE_COLS, KID_N
+  KID_RECON, KID_REMAP, KID_CONVERT, KID_SPLINE_ROWS, KID_SPLINE_COLS, KID_CLAIM_PAIR, KID_N
 };
 constexpr int PROF_CAP = 1024;
 

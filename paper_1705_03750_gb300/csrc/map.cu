@@ -246,6 +246,7 @@ __global__ void k_map_begin(DevState* ds) {
     ds->take[0] = ds->take[1] = ds->take[2] = 0;
     ds->noverflow_back = 0;
     ds->nseed = 0;
+    ds->n_pair_esc = 0;
   }
 }
 
@@ -488,18 +489,28 @@ __device__ __forceinline__ void claim_element(const Grid& g, const double* __res
                                               const float* __restrict__ tayf, const Slots& S, float alo, float ahi,
                                               int2* __restrict__ ovf_list, WarpShared& sh, int lane, int m);
 
-// One element per warp.  (A warp-strided loop that prefetched the next
-// element's records cut the set-up latency but cost more in register spills
-// than it saved.)
+// One element per warp, the elements whose component escaped tier 0's
+// window (list of n_in entries).  (A warp-strided loop that prefetched the
+// next element's records cut the set-up latency but cost more in register
+// spills than it saved.)
 __global__ void __launch_bounds__(32 * TE, 8) k_claim_small(Grid g, const double* __restrict__ tay,
                                                          const float* __restrict__ tayf, Slots Sin, float alo,
-                                                         float ahi, int2* __restrict__ ovf_list) {
+                                                         float ahi, int2* __restrict__ ovf_list,
+                                                         const int32_t* __restrict__ list_in,
+                                                         const int* __restrict__ n_in) {
   __shared__ WarpShared shw[TE];
   const Slots S = with_epoch(Sin);
   const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
-  const int m = blockIdx.x * TE + wq;
-  if (m >= g.ne) return;
-  claim_element(g, tay, tayf, S, alo, ahi, ovf_list, shw[wq], lane, m);
+  const int n = *n_in;
+  for (int idx = blockIdx.x * TE + wq; idx < n; idx += gridDim.x * TE) {
+    const int m = list_in[idx];
+    if (m < 0 || m >= g.ne) {  // (never expected; keeps every index in bounds)
+      if (lane == 0) VM_BAD(S.ds, 6);
+      continue;
+    }
+    claim_element(g, tay, tayf, S, alo, ahi, ovf_list, shw[wq], lane, m);
+    __syncwarp();
+  }
 }
 
 __device__ __forceinline__ void claim_element(const Grid& g, const double* __restrict__ tay,
@@ -755,6 +766,305 @@ __device__ __forceinline__ void claim_element(const Grid& g, const double* __res
       }
       claim_sites(S, g, pos, m);
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// tier 0: a 16 x 32 window per half warp, two elements per warp
+// ---------------------------------------------------------------------------
+//
+// The same flood fill as tier 1 on a window a quarter of its size: nearly
+// every component of an element of a few sites a side fits in 16 x 32, and
+// the shuffle scans, the fill and the list work of one warp then serve two
+// elements.  Half h = lane / 16 takes element 2w + h; half-lane r owns window
+// row r as one 32-bit mask.  Every shuffle is a 16-wide one over the whole
+// warp, so loops run until both halves are done, a finished half idling.
+// A component that reaches the window's edge goes to tier 1.
+
+constexpr int PR = 16, PC = 32, TP = 4;  // window rows, columns; warps per block
+
+struct __align__(16) HalfShared {
+  float F9[9][TF_M];
+  int ex9[9];
+  float offu[9], offv[9];
+  unsigned passed[PR];
+  unsigned unsure[PR];
+  unsigned short item[PR * PC];  // the component's sites for the claims (row << 5 | column)
+};
+
+// Inclusive sum of v over the 16 lanes of the half.
+__device__ __forceinline__ int half_incl(int v, int hl) {
+#pragma unroll
+  for (int o = 1; o < 16; o <<= 1) {
+    const int t = __shfl_up_sync(FULL, v, o, 16);
+    if (hl >= o) v += t;
+  }
+  return v;
+}
+
+// vfill on 16 rows of 32-bit masks.
+__device__ __forceinline__ unsigned vfill16(unsigned comp, unsigned pass, int hl) {
+  unsigned gd = comp, ad = pass, gu = comp, au = pass;
+#pragma unroll
+  for (int d = 1; d < 16; d <<= 1) {
+    const unsigned g1 = __shfl_up_sync(FULL, gd, d, 16), a1 = __shfl_up_sync(FULL, ad, d, 16);
+    const unsigned g2 = __shfl_down_sync(FULL, gu, d, 16), a2 = __shfl_down_sync(FULL, au, d, 16);
+    if (hl >= d) {
+      gd |= g1 & ad;
+      ad &= a1;
+    }
+    if (hl + d < 16) {
+      gu |= g2 & au;
+      au &= a2;
+    }
+  }
+  return gd | gu;
+}
+
+// run_fill on 32-bit words.
+__device__ __forceinline__ unsigned run_fill32(unsigned S, unsigned P) {
+  S &= P;
+  const unsigned up = (((P + S) ^ P) & P) | S;
+  const unsigned Pr = __brev(P), Sr = __brev(S);
+  const unsigned dn = __brev((((Pr + Sr) ^ Pr) & Pr) | Sr);
+  return up | dn;
+}
+
+__device__ __forceinline__ unsigned col_mask32(int lo, int hi) {
+  const int a = max(lo, 0), b = min(hi, 32);
+  if (b <= a) return 0u;
+  const unsigned up = (b >= 32) ? ~0u : ((1u << b) - 1u);
+  const unsigned dn = (a <= 0) ? 0u : ((1u << a) - 1u);
+  return up & ~dn;
+}
+
+// Position of the n-th set bit (from 0) of a 32-bit x with more than n set bits.
+__device__ __forceinline__ int nth_bit32(unsigned w, int n) {
+  int pos = 0, c = __popc(w & 0xFFFFu);
+  if (n >= c) { n -= c; pos = 16; w >>= 16; }
+  c = __popc(w & 0xFFu); if (n >= c) { n -= c; pos += 8; w >>= 8; }
+  c = __popc(w & 0xFu); if (n >= c) { n -= c; pos += 4; w >>= 4; }
+  c = __popc(w & 0x3u); if (n >= c) { n -= c; pos += 2; w >>= 2; }
+  if (n >= (int)(w & 1u)) pos += 1;
+  return pos;
+}
+
+__global__ void __launch_bounds__(32 * TP, 8) k_claim_pair(Grid g, const double* __restrict__ tay,
+                                                         const float* __restrict__ tayf, Slots Sin, float alo,
+                                                         float ahi, int32_t* __restrict__ esc_list) {
+  __shared__ HalfShared shp[2 * TP];
+  const Slots S = with_epoch(Sin);
+  const int lane = threadIdx.x & 31, h = lane >> 4, hl = lane & 15;
+  const int wq = threadIdx.x >> 5;
+  HalfShared& sh = shp[2 * wq + h];
+  const int m = (blockIdx.x * TP + wq) * 2 + h;
+  if (__all_sync(FULL, m >= g.ne)) return;
+  bool live = m < g.ne;
+  const int k = live ? m / g.Lv : 0, l = live ? m - k * g.Lv : 0;
+  // set-up: the 3x3 neighbourhood's FP64 index positions (half-lanes 0-8)
+  // and FP32 records, every load issued before any is used
+  double uq = 0.0, wpos = 0.0;
+  bool exq = false;
+  if (live && hl < 9) {
+    const int kk = k + hl / 3 - 1, ll = l + hl % 3 - 1;
+    exq = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
+    if (exq) {
+      const double* tq = tay + (size_t)(kk * g.Lv + ll) * TY_N;
+      uq = __ldg(tq + TY_U);
+      wpos = __ldg(tq + TY_W);
+    }
+  }
+  if (live) {
+    for (int idx = hl; idx < 9 * (TF_M / 4); idx += 16) {
+      const int q = idx / (TF_M / 4), c4 = idx - q * (TF_M / 4);
+      const int kk = k + q / 3 - 1, ll = l + q % 3 - 1;
+      const bool ex = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
+      const float4 v = ex ? __ldg(reinterpret_cast<const float4*>(tayf + (size_t)(kk * g.Lv + ll) * TF_N) + c4)
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+      reinterpret_cast<float4*>(sh.F9[q])[c4] = v;
+      if (c4 == 0) sh.ex9[q] = ex;
+    }
+  }
+  const double us = __shfl_sync(FULL, uq, 4, 16), ws = __shfl_sync(FULL, wpos, 4, 16);
+  live = live && us > -1e9 && us < 1e9 && ws > -1e9 && ws < 1e9;
+  const long long i0 = live ? (long long)floor(dadd(us, 0.5)) : 0, j0 = live ? (long long)floor(dadd(ws, 0.5)) : 0;
+  const int pad = g.pad;
+  live = live && !(i0 < -pad || i0 >= g.nx + pad || j0 < -pad || j0 >= g.nv + pad);
+  if (live && hl < 9) {
+    sh.offu[hl] = exq ? (float)((double)i0 - uq) : 0.f;
+    sh.offv[hl] = exq ? (float)((double)j0 - wpos) : 0.f;
+  }
+  __syncwarp();
+  Ctx9 c;
+  c.F9 = sh.F9;
+  c.ex9 = sh.ex9;
+  c.offu = sh.offu;
+  c.offv = sh.offv;
+  c.inv_s = 1.0f / (float)g.s;
+  c.alo = alo;
+  c.ahi = ahi;
+  const long long r0 = i0 - PR / 2, c0 = j0 - PC / 2;
+  const long long irow = r0 + hl;
+  const int clo = (int)max(0ll, (long long)(-pad) - c0);
+  const int chi = (int)min((long long)PC, (long long)(g.nv + pad) - c0);
+  const unsigned valid = (live && irow >= -pad && irow < g.nx + pad) ? col_mask32(clo, chi) : 0u;
+  const unsigned seedbit = (hl == PR / 2) ? (1u << (PC / 2)) : 0u;
+  unsigned comp = 0u, tested = 0u, passing = 0u, fa = 0u, fb = 0u;
+  // predicted region (as in tier 1): the inner part certified or listed
+  // first, the rest after it
+  if (live) {
+    const float* F = sh.F9[4];
+    const float T00 = F[TF_T00], T01 = F[TF_T01], T10 = F[TF_T10], T11 = F[TF_T11];
+    const float inv_s = c.inv_s, sf = (float)g.s;
+    const float det = fabsf(T00 * T11 - T01 * T10);
+    const float ext = (det > 1e-20f) ? fmaxf(fabsf(T11) + fabsf(T01), fabsf(T10) + fabsf(T00)) * __frcp_rn(det) : 0.f;
+    const float P = 0.6f * ext + inv_s;
+    const float sx = F[TF_C2X] * P * P, sv = F[TF_C2V] * P * P;
+    const float hx = 0.52f + 1.1f * fmaxf(fabsf(T00), fabsf(T01)) * inv_s + sx;
+    const float hv = 0.52f + 1.1f * fmaxf(fabsf(T10), fabsf(T11)) * inv_s + sv;
+    const float ix = alo - 0.02f - sx, iv = alo - 0.02f - sv;
+    const float px = ((float)(hl - PR / 2) + sh.offu[4]) * inv_s;
+    const float r01 = (fabsf(T01) > 1e-20f) ? __frcp_rn(T01) : 0.f, r11 = (fabsf(T11) > 1e-20f) ? __frcp_rn(T11) : 0.f;
+    auto cols = [&](float h1, float h2) -> unsigned {
+      float lo = -1e30f, hi = 1e30f;
+      auto cut = [&](float a, float cf, float rcf, float hh) {
+        if (rcf != 0.f) {
+          const float t1 = (-hh - a) * rcf, t2 = (hh - a) * rcf;
+          lo = fmaxf(lo, fminf(t1, t2));
+          hi = fminf(hi, fmaxf(t1, t2));
+        } else if (!(fabsf(a) <= hh)) {
+          lo = 1e30f;
+          hi = -1e30f;
+        }
+      };
+      cut(T00 * px, T01, r01, h1);
+      cut(T10 * px, T11, r11, h2);
+      const float blo = fminf(fmaxf(lo * sf - sh.offv[4] + (float)(PC / 2), -1.f), (float)(PC + 1));
+      const float bhi = fminf(fmaxf(hi * sf - sh.offv[4] + (float)(PC / 2), -1.f), (float)(PC + 1));
+      const int ilo = max((int)ceilf(blo), 0), ihi = min((int)floorf(bhi), PC - 1);
+      return (ihi >= ilo) ? col_mask32(ilo, ihi + 1) : 0u;
+    };
+    const unsigned pred = (cols(hx, hv) | seedbit) & valid;
+    const unsigned inner = (ix > 0.f && iv > 0.f) ? cols(ix, iv) & pred : 0u;
+    // inner sites certified to pass (the bound argument of tier 1)
+    unsigned sure = 0u;
+    if (inner && fmaxf(fmaxf(fabsf(T00), fabsf(T01)), fmaxf(fabsf(T10), fabsf(T11))) < 50.f) {
+      const int blo = __ffs(inner) - 1, bhi = 31 - __clz(inner);
+      const float pvlo = ((float)(blo - PC / 2) + sh.offv[4]) * inv_s;
+      const float pvhi = ((float)(bhi - PC / 2) + sh.offv[4]) * inv_s;
+      const float Pr = fmaxf(fabsf(px), fmaxf(fabsf(pvlo), fabsf(pvhi)));
+      if (F[TF_C2X] * Pr * Pr + 2e-3f <= 0.02f + sx && F[TF_C2V] * Pr * Pr + 2e-3f <= 0.02f + sv) sure = inner;
+    }
+    tested = sure;
+    passing = sure;
+    fa = pred & inner & ~sure;
+    fb = pred & ~inner;
+    const unsigned ing = pred & ((irow >= 0 && irow < g.nx)
+                                     ? col_mask32((int)max(0ll, -c0), (int)min((long long)PC, (long long)g.nv - c0))
+                                     : 0u);
+    if (ing) {
+      const size_t rowp = (size_t)irow * g.nv + c0;
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(S.slot0 + rowp + (__ffs(ing) - 1)));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(S.slot0 + rowp + (31 - __clz(ing))));
+    }
+  }
+  auto test = [&](int wr, int wb) -> int { return pass_f32(c, (float)(wr - PR / 2), (float)(wb - PC / 2)); };
+  int rounds = 0;
+  for (int it = 0; it < PR * PC; it++) {
+    const int ca = __popc(fa), cb = __popc(fb);
+    const int inca = half_incl(ca, hl), incb = half_incl(cb, hl);
+    const int ta = __shfl_sync(FULL, inca, 15, 16);
+    const int total = ta + __shfl_sync(FULL, incb, 15, 16);
+    const bool fin = !live || (total == 0 && it > 0);
+    if (__all_sync(FULL, fin)) break;
+    if (!fin && total > 0) rounds++;
+    sh.passed[hl] = 0u;
+    sh.unsure[hl] = 0u;
+    __syncwarp();
+    const unsigned incp = (unsigned)inca | ((unsigned)incb << 16);
+    const int tmax = max(total, __shfl_xor_sync(FULL, total, 16));
+    for (int e0 = 0; e0 < tmax; e0 += 16) {
+      const int e = e0 + hl;
+      const bool inA = e < ta;
+      const int key = inA ? e : e - ta, sh16 = inA ? 0 : 16;
+      int r = 0;
+#pragma unroll
+      for (int st = 8; st; st >>= 1) {
+        const unsigned v = __shfl_sync(FULL, incp, r + st - 1, 16);
+        if ((int)((v >> sh16) & 0xFFFFu) <= key) r += st;
+      }
+      const unsigned vr = __shfl_sync(FULL, incp, r, 16);
+      const unsigned wa = __shfl_sync(FULL, fa, r, 16), wb = __shfl_sync(FULL, fb, r, 16);
+      if (e < total) {
+        const unsigned w = inA ? wa : wb;
+        const int b = nth_bit32(w, key - ((int)((vr >> sh16) & 0xFFFFu) - __popc(w)));
+        const int res = test(r, b);
+        if (res == 1) atomicOr(&sh.passed[r], 1u << b);
+        if (res < 0) atomicOr(&sh.unsure[r], 1u << b);
+      }
+    }
+    __syncwarp();
+    tested |= fa | fb;
+    passing |= sh.passed[hl];
+    // the exact FP64 test of this row's unsettled sites (rare)
+    for (unsigned un = sh.unsure[hl]; un; un &= un - 1u) {
+      const int b = __ffs(un) - 1;
+      atomicAdd(&S.ds->n_exact, 1);
+      if (pass_exact_g(g, tay, k, l, site_x(g, irow), site_v(g, c0 + b))) passing |= 1u << b;
+    }
+    if (it == 0) {
+      // the start decides whether there is a component at all
+      const bool start = __shfl_sync(FULL, (passing >> (PC / 2)) & 1u, PR / 2, 16) != 0u;
+      live = live && start;
+      comp = live ? seedbit : 0u;
+    }
+    // close the component through every site known to pass
+    for (int f = 0; f < PR * PC; f++) {
+      const unsigned nc = run_fill32(vfill16(comp, passing, hl), passing);
+      const bool grew = nc != comp;
+      comp = nc;
+      if (!__any_sync(FULL, grew)) break;
+    }
+    unsigned up = __shfl_up_sync(FULL, comp, 1, 16), dn = __shfl_down_sync(FULL, comp, 1, 16);
+    if (hl == 0) up = 0u;
+    if (hl == PR - 1) dn = 0u;
+    fa = 0u;
+    fb = live ? ((comp | (comp << 1) | (comp >> 1) | up | dn) & ~comp & valid & ~tested) : 0u;
+  }
+  if (live && rounds > 1 && hl == 0) atomicAdd(&S.ds->t1_more, 1);
+  // Escaped the window?  Then tier 1 takes the element from the start.
+  const unsigned hm = 0xFFFFu << (16 * h);
+  const bool er = (__ballot_sync(FULL, comp != 0u && ((hl == 0 && r0 - 1 >= -pad) ||
+                                                      (hl == PR - 1 && r0 + PR < g.nx + pad))) & hm) != 0u;
+  const bool ec = (__ballot_sync(FULL, ((comp & 1u) && clo == 0 && c0 - 1 >= -pad) ||
+                                           ((comp >> (PC - 1)) && chi == PC && c0 + PC < g.nv + pad)) & hm) != 0u;
+  const bool esc = live && (er || ec);
+  if (esc && hl == 0) esc_list[atomicAdd(&S.ds->n_pair_esc, 1)] = m;
+  const bool claim = live && !esc;
+  // claims: the component's sites listed in row order, four exchanges in
+  // flight per lane
+  const int cnt = claim ? __popc(comp) : 0;
+  const int incl = half_incl(cnt, hl);
+  const int total = __shfl_sync(FULL, incl, 15, 16);
+  if (claim) {
+    int idx = incl - cnt;
+    for (unsigned bits = comp; bits; bits &= bits - 1u) sh.item[idx++] = (unsigned short)((hl << 5) | (__ffs(bits) - 1));
+  }
+  __syncwarp();
+  const int tmax = max(total, __shfl_xor_sync(FULL, total, 16));
+  for (int e = hl; e < tmax; e += 4 * 16) {
+    size_t pos[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int ee = e + 16 * u;
+      pos[u] = ~(size_t)0;
+      if (ee < total) {
+        const int code = sh.item[ee];
+        const long long i = r0 + (code >> 5), j = c0 + (code & 31);
+        if (i >= 0 && i < g.nx && j >= 0 && j < g.nv) pos[u] = (size_t)i * g.nv + j;
+      }
+    }
+    claim_sites(S, g, pos, m);
   }
 }
 
@@ -1336,8 +1646,16 @@ void launch_map(vm_solver* s) {
   int ps = prof_begin(s, KID_MAP_CLEAR);
   k_map_begin<<<1, 32, 0, s->stream>>>(s->ds);
   prof_end(s, ps);
+  // tier 0 (two elements per warp), its escapes to tier 1 through the first
+  // hole list (free until the holes are looked for)
+  ps = prof_begin(s, KID_CLAIM_PAIR);
+  k_claim_pair<<<(unsigned)((s->g.ne + 2 * TP - 1) / (2 * TP)), 32 * TP, 0, s->stream>>>(s->g, s->tay, s->tayf, S,
+                                                                                        alo, ahi, s->holes_a);
+  prof_end(s, ps);
   ps = prof_begin(s, KID_CLAIM_SMALL);
-  k_claim_small<<<(unsigned)((s->g.ne + TE - 1) / TE), 32 * TE, 0, s->stream>>>(s->g, s->tay, s->tayf, S, alo, ahi, s->overflow_list);
+  const unsigned t1 = (unsigned)std::min<long long>(152 * 8, (s->g.ne + TE - 1) / TE);
+  k_claim_small<<<t1, 32 * TE, 0, s->stream>>>(s->g, s->tay, s->tayf, S, alo, ahi, s->overflow_list, s->holes_a,
+                                              &s->ds->n_pair_esc);
   prof_end(s, ps);
   const size_t smem = big_smem_bytes(s->g);
   DevState* d = s->ds;
@@ -1375,7 +1693,7 @@ void launch_map(vm_solver* s) {
   ps = prof_begin(s, KID_HOLES);
   k_holes<<<1, HT, 0, s->stream>>>(s->g, s->tay, s->map, s->holes_a, s->holes_b, s->holes_b + s->n, s->ds);
   prof_end(s, ps);
-  s->launches += s->cfg.map_windows == 0 ? 9 : 7;
+  s->launches += s->cfg.map_windows == 0 ? 10 : 8;
 }
 
 void launch_read_map(vm_solver* s, int32_t* dst) {
