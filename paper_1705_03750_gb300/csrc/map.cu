@@ -1522,10 +1522,22 @@ __global__ void k_resolve(Grid g, Slots Sin) {
   }
 }
 
+// Sites no element claimed, four owner slots per 16-byte load (the slot
+// array is 256-byte aligned); the list's order does not matter (the hole
+// rounds are Jacobi rounds).
 __global__ void k_find_holes(Grid g, const uint32_t* __restrict__ slot0, int32_t* __restrict__ holes, DevState* ds) {
   const uint32_t epoch = *(volatile uint32_t*)&ds->epoch;
-  const size_t n = (size_t)g.nx * g.nv;
-  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
+  const size_t n = (size_t)g.nx * g.nv, n4 = n / 4;
+  const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+  const uint4* s4 = reinterpret_cast<const uint4*>(slot0);
+  for (size_t q = t0; q < n4; q += stride) {
+    const uint4 t = s4[q];
+    const uint32_t e[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+      if ((e[u] >> 24) != epoch) holes[atomicAdd(&ds->nholes, 1)] = (int32_t)(4 * q + u);
+  }
+  for (size_t p = 4 * n4 + t0; p < n; p += stride)
     if ((slot0[p] >> 24) != epoch) holes[atomicAdd(&ds->nholes, 1)] = (int32_t)p;
 }
 
@@ -1685,8 +1697,9 @@ void launch_map(vm_solver* s) {
   ps = prof_begin(s, KID_RESOLVE);
   k_resolve<<<(unsigned)std::min<size_t>(152, (s->n + 1023) / 1024), 256, 0, s->stream>>>(s->g, S);
   prof_end(s, ps);
-  unsigned nb = (unsigned)((s->n + 255) / 256);
+  unsigned nb = (unsigned)((s->n / 4 + 255) / 256);
   if (nb > 152 * 16) nb = 152 * 16;
+  if (nb == 0) nb = 1;
   ps = prof_begin(s, KID_FINALIZE);
   k_find_holes<<<nb, 256, 0, s->stream>>>(s->g, s->map, s->holes_a, s->ds);
   prof_end(s, ps);
