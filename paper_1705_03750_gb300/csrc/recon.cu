@@ -257,6 +257,22 @@ __device__ __forceinline__ void anchor(const Grid& g, int m, int& Bu, float& bu,
   bw = (w2 & 1) ? 0.5f : 0.f;
 }
 
+// The anchor with k = m / Lv from an FP32 reciprocal (m < 2^24 is exact in
+// FP32, the quotient is off by at most one and corrected): a few
+// instructions instead of an integer division per site.
+__device__ __forceinline__ void anchor_r(const Grid& g, int m, float inv_Lv, int& Bu, float& bu, int& Bw, float& bw) {
+  int k = (int)((float)m * inv_Lv);
+  if (k * g.Lv > m) k--;
+  if ((k + 1) * g.Lv <= m) k++;
+  const int l = m - k * g.Lv;
+  const int u2 = (g.nx - 1) + 2 * (k - g.Kx - 1) * g.s;
+  const int w2 = (g.nv - 1) + 2 * (l - g.Kv - 1) * g.s;
+  Bu = u2 >> 1;
+  bu = (u2 & 1) ? 0.5f : 0.f;
+  Bw = w2 >> 1;
+  bw = (w2 & 1) ? 0.5f : 0.f;
+}
+
 // Is floor(x) certain for every value within e of x?
 __device__ __forceinline__ bool floor_sure(float x, float e) {
   const float f = floorf(x);
@@ -368,7 +384,8 @@ __device__ __noinline__ float recon_site32(const Grid& g, const double* __restri
 // then recon_site32's); the loads stay in bounds either way, so that the
 // loads of several sites can be in flight together.
 __device__ __forceinline__ float recon_fast32(const Grid& g, const float* __restrict__ tayf,
-                                              const float* __restrict__ fini, int i, int j, int m, bool* slow) {
+                                              const float* __restrict__ fini, int i, int j, int m, float inv_Lv,
+                                              bool* slow) {
   const float inv_s = 1.0f / (float)g.s, fs = (float)g.s;
   const float* F = tayf + (size_t)(m < 0 ? 0 : m) * TF_N;
   float px, pv;
@@ -376,16 +393,22 @@ __device__ __forceinline__ float recon_fast32(const Grid& g, const float* __rest
   const QF q = qeval(F, px, pv);
   int Bu, Bw;
   float bu, bw;
-  anchor(g, m < 0 ? 0 : m, Bu, bu, Bw, bw);
+  anchor_r(g, m < 0 ? 0 : m, inv_Lv, Bu, bu, Bw, bw);
   const float ru = bu + fs * q.qx, rw = bw + fs * q.qv;
   const float eu = fs * q.ex + 1e-6f * (1.f + fabsf(ru)), ew = fs * q.ev + 1e-6f * (1.f + fabsf(rw));
   const bool finite = fabsf(ru) < 1e6f && fabsf(rw) < 1e6f;
   const float ruc = finite ? ru : 0.f, rwc = finite ? rw : 0.f;
-  const float nu = floorf(ruc + 0.5f), nw = floorf(rwc + 0.5f);
-  int in = Bu + (int)nu, jn = Bw + (int)nw;
-  int ic = Bu + (int)floorf(ruc), jc = Bw + (int)floorf(rwc);
-  const bool sure = finite && floor_sure(ruc + 0.5f, eu) && floor_sure(ruc, eu) && floor_sure(rwc + 0.5f, ew) &&
-                    floor_sure(rwc, ew);
+  // nearest node floor(r + 1/2) and cell floor(r) from one floor of 2r
+  // (exact doubling): both are certain when [2r - 2e, 2r + 2e] holds no
+  // integer (the rounded end points err towards failing the test)
+  const float tu = 2.f * ruc, tw = 2.f * rwc;
+  const float fu = floorf(tu), fw = floorf(tw);
+  const int iu = (int)fu, iw = (int)fw;
+  const float nu = (float)((iu + 1) >> 1), nw = (float)((iw + 1) >> 1);
+  int in = Bu + ((iu + 1) >> 1), jn = Bw + ((iw + 1) >> 1);
+  int ic = Bu + (iu >> 1), jc = Bw + (iw >> 1);
+  const bool sure = finite && (tu - 2.f * eu > fu) && (tu + 2.f * eu < fu + 1.f) && (tw - 2.f * ew > fw) &&
+                    (tw + 2.f * ew < fw + 1.f);
   const bool inside = in >= 1 && in <= g.nx - 2 && jn >= 1 && jn <= g.nv - 2;
   *slow = (m >= 0) && !(sure && inside);
   if (!(sure && inside)) {  // any in-grid stencil: its value is not used
@@ -404,6 +427,7 @@ __global__ void __launch_bounds__(256, 6) k_recon32(Grid g, const uint32_t* __re
   const int i = blockIdx.x;
   const uint32_t epoch = ds_epoch(ds);
   FPair acc;
+  const float inv_Lv = 1.0f / (float)g.Lv;
   // the owner of the thread's next site is loaded one iteration ahead
   const size_t row = (size_t)i * g.nv;
   int m = (threadIdx.x < g.nv) ? owner(map, row + threadIdx.x, epoch, g.ne) : -1;
@@ -411,7 +435,7 @@ __global__ void __launch_bounds__(256, 6) k_recon32(Grid g, const uint32_t* __re
     const int jn = j + blockDim.x;
     const int mn = (jn < g.nv) ? owner(map, row + jn, epoch, g.ne) : -1;
     bool slow;
-    float v = recon_fast32(g, tayf, fini, i, j, m, &slow);
+    float v = recon_fast32(g, tayf, fini, i, j, m, inv_Lv, &slow);
     if (slow) v = recon_site32(g, tay, tayf, fini, i, j, m);
     f[row + j] = v;
     acc.add(v);
