@@ -90,16 +90,17 @@ enum { TY_X = 0, TY_V, TY_TI00, TY_TI01, TY_TI10, TY_TI11, TY_GX00, TY_GX01, TY_
        TY_GV00, TY_GV01, TY_GV11, TY_QX, TY_QV, TY_U, TY_W, TY_N = 16 };
 // FP32 record of the inverse map in element units (32 words = 128 bytes):
 // with p = (P - P_m)/Delta_m and q = (Q - Q_m)/Delta_m,
-//   q_a = sum_b T[a][b] p_b - 1/2 sum_l K[a][l] s_l,  s_l = p^T G_l p,
-// and |each term| of q_a bounded by C1_a |p|_inf + C2_a |p|_inf^2 (the
-// coefficients of the bound are rounded up).  UF/WF and UI/WI split the
-// element's index position u_m = (x_m - x_lo)/dx into integer and fraction.
-enum { TF_T00 = 0, TF_T01, TF_T10, TF_T11, TF_GX00, TF_GX01, TF_GX11, TF_GV00, TF_GV01, TF_GV11,
-       TF_K00, TF_K01, TF_K10, TF_K11, TF_C1X, TF_C2X, TF_C1V, TF_C2V, TF_UF, TF_WF, TF_UI, TF_WI,
-       TF_N = 32 };
-// qeval reads words 0-19 of the FP32 record as five float4
-static_assert(TF_T00 == 0 && TF_GX00 == 4 && TF_GV01 == 8 && TF_K10 == 12 && TF_C1V == 16 && TF_WF == 19,
-              "FP32 record layout");
+//   q_a = sum_b T[a][b] p_b - 1/2 sum_l K[a][l] s_l,  s_l = p^T G_l p
+//       = p_x (T[a][0] + A_a p_x + B_a p_v) + p_v (T[a][1] + C_a p_v),
+// the second-order coefficients A, B, C combined from K and G in FP64; and
+// |each term| of q_a bounded by C1_a |p|_inf + C2_a |p|_inf^2, C2_a from the
+// uncombined terms (the coefficients of the bound are rounded up).  UF/WF
+// and UI/WI split the element's index position u_m = (x_m - x_lo)/dx into
+// integer and fraction.
+enum { TF_T00 = 0, TF_T01, TF_T10, TF_T11, TF_AX, TF_BX, TF_CX, TF_AV, TF_BV, TF_CV,
+       TF_C1X, TF_C2X, TF_C1V, TF_C2V, TF_UF, TF_WF, TF_UI, TF_WI, TF_N = 32 };
+// the reconstruction reads words 0-15 of the FP32 record as four float4
+static_assert(TF_T00 == 0 && TF_AX == 4 && TF_BV == 8 && TF_C1V == 12 && TF_WF == 15, "FP32 record layout");
 
 constexpr unsigned long long KEY_EMPTY = ~0ull;
 

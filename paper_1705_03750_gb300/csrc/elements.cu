@@ -27,23 +27,23 @@ __device__ __forceinline__ void taylor_f32(const Grid& g, const double* t, float
   F[TF_T01] = (float)T01;
   F[TF_T10] = (float)T10;
   F[TF_T11] = (float)T11;
-  double gs[2];
+  double gs[2], G00[2], G01[2], G11[2];
 #pragma unroll
   for (int l = 0; l < 2; l++) {
-    const double g00 = t[TY_GX00 + 3 * l] * dxm * dxm;
-    const double g01 = t[TY_GX01 + 3 * l] * dxm * dvm;
-    const double g11 = t[TY_GX11 + 3 * l] * dvm * dvm;
-    F[TF_GX00 + 3 * l] = (float)g00;
-    F[TF_GX01 + 3 * l] = (float)g01;
-    F[TF_GX11 + 3 * l] = (float)g11;
-    gs[l] = fabs(g00) + 2.0 * fabs(g01) + fabs(g11);
+    G00[l] = t[TY_GX00 + 3 * l] * dxm * dxm;
+    G01[l] = t[TY_GX01 + 3 * l] * dxm * dvm;
+    G11[l] = t[TY_GX11 + 3 * l] * dvm * dvm;
+    gs[l] = fabs(G00[l]) + 2.0 * fabs(G01[l]) + fabs(G11[l]);
   }
   const double K00 = t[TY_TI00] * g.inv_dxm, K01 = t[TY_TI01] * g.inv_dxm;
   const double K10 = t[TY_TI10] * g.inv_dvm, K11 = t[TY_TI11] * g.inv_dvm;
-  F[TF_K00] = (float)K00;
-  F[TF_K01] = (float)K01;
-  F[TF_K10] = (float)K10;
-  F[TF_K11] = (float)K11;
+  // -1/2 (K[a][0] s_x + K[a][1] s_v) = A_a p_x^2 + B_a p_x p_v + C_a p_v^2
+  F[TF_AX] = (float)(-0.5 * (K00 * G00[0] + K01 * G00[1]));
+  F[TF_BX] = (float)(-(K00 * G01[0] + K01 * G01[1]));
+  F[TF_CX] = (float)(-0.5 * (K00 * G11[0] + K01 * G11[1]));
+  F[TF_AV] = (float)(-0.5 * (K10 * G00[0] + K11 * G00[1]));
+  F[TF_BV] = (float)(-(K10 * G01[0] + K11 * G01[1]));
+  F[TF_CV] = (float)(-0.5 * (K10 * G11[0] + K11 * G11[1]));
   const double slack = 1.0 + 1e-6;
   F[TF_C1X] = up32((fabs(T00) + fabs(T01)) * slack);
   F[TF_C2X] = up32(0.5 * (fabs(K00) * gs[0] + fabs(K01) * gs[1]) * slack);

@@ -111,14 +111,12 @@ struct QF {
 
 __device__ __forceinline__ QF qeval(const float* __restrict__ F, float px, float pv) {
   QF r;
-  // (scalar loads from shared memory: in the tier-1 test loop five 16-byte
-  // loads cost more registers than they save issue slots)
-  const float yx = F[TF_T00] * px + F[TF_T01] * pv;
-  const float yv = F[TF_T10] * px + F[TF_T11] * pv;
-  const float sx = px * (F[TF_GX00] * px + F[TF_GX01] * pv) + pv * (F[TF_GX01] * px + F[TF_GX11] * pv);
-  const float sv = px * (F[TF_GV00] * px + F[TF_GV01] * pv) + pv * (F[TF_GV01] * px + F[TF_GV11] * pv);
-  r.qx = yx - 0.5f * (F[TF_K00] * sx + F[TF_K01] * sv);
-  r.qv = yv - 0.5f * (F[TF_K10] * sx + F[TF_K11] * sv);
+  // (scalar loads from shared memory: in the tier-1 test loop 16-byte loads
+  // cost more registers than they save issue slots)
+  const float tx = fmaf(F[TF_AX], px, fmaf(F[TF_BX], pv, F[TF_T00])), ux = fmaf(F[TF_CX], pv, F[TF_T01]);
+  const float tv = fmaf(F[TF_AV], px, fmaf(F[TF_BV], pv, F[TF_T10])), uv = fmaf(F[TF_CV], pv, F[TF_T11]);
+  r.qx = fmaf(px, tx, pv * ux);
+  r.qv = fmaf(px, tv, pv * uv);
   const float P = fmaxf(fabsf(px), fabsf(pv));
   r.ax = F[TF_C1X] * P + F[TF_C2X] * (P * P);
   r.av = F[TF_C1V] * P + F[TF_C2V] * (P * P);
@@ -134,11 +132,11 @@ __device__ __forceinline__ int range_f(float q, float e, float alo, float ahi) {
   return 0;
 }
 
-// The map reads words 0-17 of the FP32 records (as five float4).  Their
-// shared-memory copies have a stride of 20 words, so that lanes evaluating
-// different neighbours read the same word from different banks.
-constexpr int TF_M = 20;
-static_assert(TF_C2V < TF_M && TF_M % 4 == 0, "map's FP32 record words");
+// The map reads words 0-15 of the FP32 records (TF_MW, as four float4).
+// Their shared-memory copies have a stride of 20 words, so that lanes
+// evaluating different neighbours read the same word from different banks.
+constexpr int TF_M = 20, TF_MW = 16;
+static_assert(TF_C2V < TF_MW && TF_MW <= TF_M && TF_M % 4 == 0, "map's FP32 record words");
 
 struct Ctx9 {
   const float (*F9)[TF_M];
@@ -333,8 +331,8 @@ __device__ __forceinline__ void load_elem9(const Grid& g, int m, const double* _
     E.T9[q][c] = ex ? tay[(size_t)(kk * g.Lv + ll) * TY_N + c] : 0.0;
     if (c == 0) E.ex9[q] = ex;
   }
-  for (int idx = threadIdx.x; idx < 9 * TF_M; idx += blockDim.x) {
-    const int q = idx / TF_M, c = idx - q * TF_M;
+  for (int idx = threadIdx.x; idx < 9 * TF_MW; idx += blockDim.x) {
+    const int q = idx / TF_MW, c = idx - q * TF_MW;
     const int kk = k + q / 3 - 1, ll = l + q % 3 - 1;
     const bool ex = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
     E.F9[q][c] = ex ? tayf[(size_t)(kk * g.Lv + ll) * TF_N + c] : 0.f;
@@ -531,8 +529,8 @@ __device__ __forceinline__ void claim_element(const Grid& g, const double* __res
       wpos = __ldg(tq + TY_W);
     }
   }
-  for (int idx = lane; idx < 9 * (TF_M / 4); idx += 32) {
-    const int q = idx / (TF_M / 4), c4 = idx - q * (TF_M / 4);
+  for (int idx = lane; idx < 9 * (TF_MW / 4); idx += 32) {
+    const int q = idx / (TF_MW / 4), c4 = idx - q * (TF_MW / 4);
     const int kk = k + q / 3 - 1, ll = l + q % 3 - 1;
     const bool ex = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
     const float4 v = ex ? __ldg(reinterpret_cast<const float4*>(tayf + (size_t)(kk * g.Lv + ll) * TF_N) + c4)
@@ -851,7 +849,8 @@ __device__ __forceinline__ int nth_bit32(unsigned w, int n) {
 
 __global__ void __launch_bounds__(32 * TP, 8) k_claim_pair(Grid g, const double* __restrict__ tay,
                                                          const float* __restrict__ tayf, Slots Sin, float alo,
-                                                         float ahi, int32_t* __restrict__ esc_list) {
+                                                         float ahi, int32_t* __restrict__ esc_list,
+                                                         int2* __restrict__ ovf_list) {
   __shared__ HalfShared shp[2 * TP];
   const Slots S = with_epoch(Sin);
   const int lane = threadIdx.x & 31, h = lane >> 4, hl = lane & 15;
@@ -875,8 +874,8 @@ __global__ void __launch_bounds__(32 * TP, 8) k_claim_pair(Grid g, const double*
     }
   }
   if (live) {
-    for (int idx = hl; idx < 9 * (TF_M / 4); idx += 16) {
-      const int q = idx / (TF_M / 4), c4 = idx - q * (TF_M / 4);
+    for (int idx = hl; idx < 9 * (TF_MW / 4); idx += 16) {
+      const int q = idx / (TF_MW / 4), c4 = idx - q * (TF_MW / 4);
       const int kk = k + q / 3 - 1, ll = l + q % 3 - 1;
       const bool ex = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
       const float4 v = ex ? __ldg(reinterpret_cast<const float4*>(tayf + (size_t)(kk * g.Lv + ll) * TF_N) + c4)
@@ -1039,7 +1038,36 @@ __global__ void __launch_bounds__(32 * TP, 8) k_claim_pair(Grid g, const double*
   const bool ec = (__ballot_sync(FULL, ((comp & 1u) && clo == 0 && c0 - 1 >= -pad) ||
                                            ((comp >> (PC - 1)) && chi == PC && c0 + PC < g.nv + pad)) & hm) != 0u;
   const bool esc = live && (er || ec);
-  if (esc && hl == 0) esc_list[atomicAdd(&S.ds->n_pair_esc, 1)] = m;
+  // An outer element (a neighbour missing) that escapes claims a boundary
+  // band, which tier 1's window cannot hold either: it goes straight to
+  // tier 2 (listed from the front), with this window's masks as the seed of
+  // tier 2's first window (placed in a 32 x 64 record as tier 1's would
+  // be).  The others start again in tier 1.
+  bool outer = false;
+  for (int q = 0; q < 9; q++) outer |= !sh.ex9[q];
+  int seed = -1;
+  if (esc && outer && hl == 0) {
+    seed = atomicAdd(&S.ds->nseed, 1);
+    if (seed >= S.seed_cap) seed = -1;
+    const int sides = (er ? 1 : 0) | (ec ? 2 : 0);
+    ovf_list[atomicAdd(&S.ds->noverflow, 1)] = make_int2(m, ((seed + 1) << 8) | (sides << 4));
+  }
+  seed = __shfl_sync(FULL, seed, 0, 16);
+  if (esc && outer) {
+    if (seed >= 0) {
+      unsigned long long* rec = S.seed + (size_t)seed * (3 * TR);
+      const int r = TR / 2 - PR / 2 + hl, sh0 = 32 - PC / 2;
+      rec[r] = (unsigned long long)comp << sh0;
+      rec[TR + r] = (unsigned long long)tested << sh0;
+      rec[2 * TR + r] = (unsigned long long)passing << sh0;
+      // the record's other rows
+      rec[hl < 8 ? hl : TR - 16 + hl] = 0ull;
+      rec[TR + (hl < 8 ? hl : TR - 16 + hl)] = 0ull;
+      rec[2 * TR + (hl < 8 ? hl : TR - 16 + hl)] = 0ull;
+    }
+  } else if (esc && hl == 0) {
+    esc_list[atomicAdd(&S.ds->n_pair_esc, 1)] = m;
+  }
   const bool claim = live && !esc;
   // claims: the component's sites listed in row order, four exchanges in
   // flight per lane
@@ -1662,7 +1690,8 @@ void launch_map(vm_solver* s) {
   // hole list (free until the holes are looked for)
   ps = prof_begin(s, KID_CLAIM_PAIR);
   k_claim_pair<<<(unsigned)((s->g.ne + 2 * TP - 1) / (2 * TP)), 32 * TP, 0, s->stream>>>(s->g, s->tay, s->tayf, S,
-                                                                                        alo, ahi, s->holes_a);
+                                                                                        alo, ahi, s->holes_a,
+                                                                                        s->overflow_list);
   prof_end(s, ps);
   ps = prof_begin(s, KID_CLAIM_SMALL);
   const unsigned t1 = (unsigned)std::min<long long>(152 * 8, (s->g.ne + TE - 1) / TE);

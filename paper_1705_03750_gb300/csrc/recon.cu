@@ -221,18 +221,17 @@ struct QF {
 
 __device__ __forceinline__ QF qeval(const float* __restrict__ F, float px, float pv) {
   QF r;
-  // the record's first 20 words in five 16-byte loads (records are 128-byte aligned)
+  // the record's first 16 words in four 16-byte loads (records are 128-byte
+  // aligned): T, A, B, C of both axes, the bound coefficients
   const float4* F4 = reinterpret_cast<const float4*>(F);
-  const float4 f0 = F4[0], f1 = F4[1], f2 = F4[2], f3 = F4[3], f4 = F4[4];
-  const float yx = f0.x * px + f0.y * pv;
-  const float yv = f0.z * px + f0.w * pv;
-  const float sx = px * (f1.x * px + f1.y * pv) + pv * (f1.y * px + f1.z * pv);
-  const float sv = px * (f1.w * px + f2.x * pv) + pv * (f2.x * px + f2.y * pv);
-  r.qx = yx - 0.5f * (f2.z * sx + f2.w * sv);
-  r.qv = yv - 0.5f * (f3.x * sx + f3.y * sv);
+  const float4 f0 = F4[0], f1 = F4[1], f2 = F4[2], f3 = F4[3];
+  const float tx = fmaf(f1.x, px, fmaf(f1.y, pv, f0.x)), ux = fmaf(f1.z, pv, f0.y);
+  const float tv = fmaf(f1.w, px, fmaf(f2.x, pv, f0.z)), uv = fmaf(f2.y, pv, f0.w);
+  r.qx = fmaf(px, tx, pv * ux);
+  r.qv = fmaf(px, tv, pv * uv);
   const float P = fmaxf(fabsf(px), fabsf(pv));
-  const float ax = f3.z * P + f3.w * (P * P);
-  const float av = f4.x * P + f4.y * (P * P);
+  const float ax = f2.z * P + f2.w * (P * P);
+  const float av = f3.x * P + f3.y * (P * P);
   r.ex = kRelQ * ax + kAbs * (1.f + ax);
   r.ev = kRelQ * av + kAbs * (1.f + av);
   return r;
