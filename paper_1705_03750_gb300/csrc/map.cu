@@ -6,8 +6,12 @@
 // smaller d).  Each element is flood-filled inside a window of bit masks
 // (tested / passing / component), sized in tiers:
 //
+//   0. a 16 x 32 window per half warp (one 32-bit row per half-lane), two
+//      elements per warp; nearly every component fits.  Its escapes go to
+//      tier 1, except outer elements (a neighbour missing), which claim
+//      boundary bands and go straight to tier 2 with tier 0's masks;
 //   1. a 32 x 64 window held in registers (one 64-bit row per lane), one
-//      warp per element.  The first round tests the region predicted by the
+//      warp per element.  Both tiers run the same rounds: the first tests the region predicted by the
 //      linear part of the element's map (its inner part, where a bound on
 //      the second-order terms shows that every site passes, needs no test);
 //      the component is then closed through the passing sites by shuffle
@@ -22,7 +26,7 @@
 //   3. the whole padded lattice, its masks in global memory.
 //      Outer-layer elements whose neighbours moved away claim long thin
 //      bands; to cross them in few rounds, any 64-site word near the
-//      component is tested whole (two rows ahead, one word ahead) and the
+//      component is tested whole (three rows ahead, one word ahead) and the
 //      component is extended through runs of passing sites inside a word
 //      with one carry-propagating addition.
 //
@@ -873,15 +877,29 @@ __global__ void __launch_bounds__(32 * TP, 8) k_claim_pair(Grid g, const double*
       wpos = __ldg(tq + TY_W);
     }
   }
-  if (live) {
-    for (int idx = hl; idx < 9 * (TF_MW / 4); idx += 16) {
+  {
+    // the 36 float4 of the nine records over the 16 half-lanes: all loads
+    // issued, then all stores
+    constexpr int NV = (9 * (TF_MW / 4) + 15) / 16;
+    float4 v[NV];
+#pragma unroll
+    for (int u = 0; u < NV; u++) {
+      const int idx = hl + 16 * u;
       const int q = idx / (TF_MW / 4), c4 = idx - q * (TF_MW / 4);
       const int kk = k + q / 3 - 1, ll = l + q % 3 - 1;
-      const bool ex = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
-      const float4 v = ex ? __ldg(reinterpret_cast<const float4*>(tayf + (size_t)(kk * g.Lv + ll) * TF_N) + c4)
-                          : make_float4(0.f, 0.f, 0.f, 0.f);
-      reinterpret_cast<float4*>(sh.F9[q])[c4] = v;
-      if (c4 == 0) sh.ex9[q] = ex;
+      const bool ex = live && idx < 9 * (TF_MW / 4) && kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
+      v[u] = ex ? __ldg(reinterpret_cast<const float4*>(tayf + (size_t)(kk * g.Lv + ll) * TF_N) + c4)
+                : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < NV; u++) {
+      const int idx = hl + 16 * u;
+      const int q = idx / (TF_MW / 4), c4 = idx - q * (TF_MW / 4);
+      const int kk = k + q / 3 - 1, ll = l + q % 3 - 1;
+      if (live && idx < 9 * (TF_MW / 4)) {
+        reinterpret_cast<float4*>(sh.F9[q])[c4] = v[u];
+        if (c4 == 0) sh.ex9[q] = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
+      }
     }
   }
   const double us = __shfl_sync(FULL, uq, 4, 16), ws = __shfl_sync(FULL, wpos, 4, 16);
@@ -1105,7 +1123,7 @@ constexpr int BLOCKS_PER_SM = 3;
 constexpr int BAND_R = 128, BAND_W = 20;  // band window: 128 rows across, up to 1280 sites along
 constexpr int FAT_R = 160, FAT_W = 12;    // 160 x 768 sites
 constexpr int LIST_CAP = 512;
-constexpr int AHEAD = 2;      // rows tested ahead of the component per round
+constexpr int AHEAD = 3;      // rows tested ahead of the component per round
 constexpr size_t SMEM_MAX = 227 * 1024;   // opt-in limit per block
 constexpr size_t SMEM_SM = 228 * 1024;    // shared memory per SM
 
@@ -1258,7 +1276,7 @@ __device__ __forceinline__ unsigned long long dilate(const unsigned long long* c
 
 // Sites worth testing ahead of the component in word q: the word's column
 // within AHEAD rows of it, the whole word if the word or a neighbouring word
-// of its row holds some.  (Deeper speculation, 3 to 12 rows and two words,
+// of its row holds some.  (Deeper speculation, 4 to 12 rows and two words,
 // tested more sites than it saved rounds; growing inside a word one site per
 // round, as the column rule alone does, made a component that starts from one
 // site and runs along the bits take one round per site.)
