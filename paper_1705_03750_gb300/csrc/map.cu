@@ -11,9 +11,10 @@
 //      tier 1, except outer elements (a neighbour missing), which claim
 //      boundary bands and go straight to tier 2 with tier 0's masks;
 //   1. a 32 x 64 window held in registers (one 64-bit row per lane), one
-//      warp per element.  Both tiers run the same rounds: the first tests the region predicted by the
-//      linear part of the element's map (its inner part, where a bound on
-//      the second-order terms shows that every site passes, needs no test);
+//      warp per element.  Both tiers run the same rounds: the first tests
+//      the region predicted by the linear part of the element's map (its
+//      inner part, where a bound on the second-order terms shows that every
+//      site passes, needs no test);
 //      the component is then closed through the passing sites by shuffle
 //      scans, and further rounds test only sites next to it left untested
 //      (the 32 lanes share a round's tests: lane e of a pass takes the
