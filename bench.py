@@ -143,8 +143,8 @@ def step_bytes_per_update(rc, fp32: bool) -> float:
 # time of the capture: a source changed since makes the figure void (null).
 NCU_TRAFFIC = {
     # kernel: (bytes per launch, source file, sha256 prefix)
-    "claim_small": (255_330_304, "map.cu", "92cdb3cef9d30104"),
-    "reconstruct": (215_340_544, "recon.cu", "6a535ce10230b71d"),
+    "claim_pair": (177_773_824, "map.cu", "3ed4716179011d9b"),
+    "reconstruct": (222_159_360, "recon.cu", "64226aaef229a450"),
 }
 
 
