@@ -216,7 +216,7 @@ def run_native(args, rank: int, world: int, dist):
         return max_over_ranks(x, dist, dev)
 
     # An idle GPU ran its first tenth of a second or so measurably slower
-    # (clock and power state): --spin seconds (default half a second) of
+    # (clock and power state): --spin seconds (default two) of
     # untimed steps of a throwaway solve come before any warm-up or timing.
     if args.spin > 0:
         spin = V.Solver(V.Config.from_run(rc, V.VM_FP32_MIXED))
@@ -570,7 +570,7 @@ def main():
     ap.add_argument("--max-active", type=int, default=32)
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--spin", type=float, default=0.5, help="seconds of untimed steps before the warm-up")
+    ap.add_argument("--spin", type=float, default=2.0, help="seconds of untimed steps before the warm-up")
     args = ap.parse_args()
     if args.workload != "halos4096":
         from paper_1705_03750_gb300 import build as B

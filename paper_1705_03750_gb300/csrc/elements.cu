@@ -13,42 +13,42 @@
 namespace vm {
 namespace {
 
-__device__ __forceinline__ float up32(double x) {
-  // float >= x (for bound coefficients, x >= 0)
-  float f = __double2float_ru(x);
-  return f;
-}
-
-// FP32 record of element m (see TF_* in common.cuh) from its FP64 terms.
+// FP32 record of element m (see TF_* in common.cuh) from its FP64 terms,
+// in FP32 arithmetic (FP64 runs at 1/64 of the FP32 rate here): each
+// coefficient carries up to ten roundings, within the budget of the
+// certified decisions' bound constants; the bound coefficients are rounded
+// upwards at every operation, with a slack of 1e-5 over the FP32 values
+// that also covers their distance to the FP64 ones.
 __device__ __forceinline__ void taylor_f32(const Grid& g, const double* t, float* __restrict__ F) {
-  const double dxm = g.dxm, dvm = g.dvm;
-  const double T00 = t[TY_TI00], T01 = t[TY_TI01] * g.r_vx, T10 = t[TY_TI10] * g.r_xv, T11 = t[TY_TI11];
-  F[TF_T00] = (float)T00;
-  F[TF_T01] = (float)T01;
-  F[TF_T10] = (float)T10;
-  F[TF_T11] = (float)T11;
-  double gs[2], G00[2], G01[2], G11[2];
+  const float dxm = (float)g.dxm, dvm = (float)g.dvm;
+  const float ti00 = (float)t[TY_TI00], ti01 = (float)t[TY_TI01], ti10 = (float)t[TY_TI10], ti11 = (float)t[TY_TI11];
+  const float T00 = ti00, T01 = ti01 * (float)g.r_vx, T10 = ti10 * (float)g.r_xv, T11 = ti11;
+  F[TF_T00] = T00;
+  F[TF_T01] = T01;
+  F[TF_T10] = T10;
+  F[TF_T11] = T11;
+  float gs[2], G00[2], G01[2], G11[2];
 #pragma unroll
   for (int l = 0; l < 2; l++) {
-    G00[l] = t[TY_GX00 + 3 * l] * dxm * dxm;
-    G01[l] = t[TY_GX01 + 3 * l] * dxm * dvm;
-    G11[l] = t[TY_GX11 + 3 * l] * dvm * dvm;
-    gs[l] = fabs(G00[l]) + 2.0 * fabs(G01[l]) + fabs(G11[l]);
+    G00[l] = (float)t[TY_GX00 + 3 * l] * (dxm * dxm);
+    G01[l] = (float)t[TY_GX01 + 3 * l] * (dxm * dvm);
+    G11[l] = (float)t[TY_GX11 + 3 * l] * (dvm * dvm);
+    gs[l] = __fadd_ru(__fadd_ru(fabsf(G00[l]), __fmul_ru(2.f, fabsf(G01[l]))), fabsf(G11[l]));
   }
-  const double K00 = t[TY_TI00] * g.inv_dxm, K01 = t[TY_TI01] * g.inv_dxm;
-  const double K10 = t[TY_TI10] * g.inv_dvm, K11 = t[TY_TI11] * g.inv_dvm;
+  const float K00 = ti00 * (float)g.inv_dxm, K01 = ti01 * (float)g.inv_dxm;
+  const float K10 = ti10 * (float)g.inv_dvm, K11 = ti11 * (float)g.inv_dvm;
   // -1/2 (K[a][0] s_x + K[a][1] s_v) = A_a p_x^2 + B_a p_x p_v + C_a p_v^2
-  F[TF_AX] = (float)(-0.5 * (K00 * G00[0] + K01 * G00[1]));
-  F[TF_BX] = (float)(-(K00 * G01[0] + K01 * G01[1]));
-  F[TF_CX] = (float)(-0.5 * (K00 * G11[0] + K01 * G11[1]));
-  F[TF_AV] = (float)(-0.5 * (K10 * G00[0] + K11 * G00[1]));
-  F[TF_BV] = (float)(-(K10 * G01[0] + K11 * G01[1]));
-  F[TF_CV] = (float)(-0.5 * (K10 * G11[0] + K11 * G11[1]));
-  const double slack = 1.0 + 1e-6;
-  F[TF_C1X] = up32((fabs(T00) + fabs(T01)) * slack);
-  F[TF_C2X] = up32(0.5 * (fabs(K00) * gs[0] + fabs(K01) * gs[1]) * slack);
-  F[TF_C1V] = up32((fabs(T10) + fabs(T11)) * slack);
-  F[TF_C2V] = up32(0.5 * (fabs(K10) * gs[0] + fabs(K11) * gs[1]) * slack);
+  F[TF_AX] = -0.5f * (K00 * G00[0] + K01 * G00[1]);
+  F[TF_BX] = -(K00 * G01[0] + K01 * G01[1]);
+  F[TF_CX] = -0.5f * (K00 * G11[0] + K01 * G11[1]);
+  F[TF_AV] = -0.5f * (K10 * G00[0] + K11 * G00[1]);
+  F[TF_BV] = -(K10 * G01[0] + K11 * G01[1]);
+  F[TF_CV] = -0.5f * (K10 * G11[0] + K11 * G11[1]);
+  const float slack = 1.0f + 1e-5f;
+  F[TF_C1X] = __fmul_ru(__fadd_ru(fabsf(T00), fabsf(T01)), slack);
+  F[TF_C2X] = __fmul_ru(__fmul_ru(0.5f, __fadd_ru(__fmul_ru(fabsf(K00), gs[0]), __fmul_ru(fabsf(K01), gs[1]))), slack);
+  F[TF_C1V] = __fmul_ru(__fadd_ru(fabsf(T10), fabsf(T11)), slack);
+  F[TF_C2V] = __fmul_ru(__fmul_ru(0.5f, __fadd_ru(__fmul_ru(fabsf(K10), gs[0]), __fmul_ru(fabsf(K11), gs[1]))), slack);
   const double u = t[TY_U], w = t[TY_W];
   const double ui = floor(u), wi = floor(w);
   const bool ok = (u > -1e9 && u < 1e9 && w > -1e9 && w < 1e9);
