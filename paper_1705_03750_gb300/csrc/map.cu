@@ -103,10 +103,12 @@ __device__ __noinline__ bool pass_exact(const Grid& g, const double (*T9)[TY_N],
 // FP32 test with certified decisions
 // ---------------------------------------------------------------------------
 
-// Bound constants: the FP32 evaluation of q has at most ~15 rounding factors
-// per monomial (inputs rounded to FP32, products and sums), d^2 at most ~31;
-// gamma_31(2^-24) < 1.9e-6.  The constants carry a factor ~2 of margin, and
-// the absolute term covers the last-bit differences between the FP32 inputs'
+// Bound constants: a monomial of the FP32 q passes through at most ~22
+// roundings (its coefficient, computed in FP32 from the FP64 terms, up to
+// ten; the inputs p about four, twice in a square; three fused operations):
+// gamma_22(2^-24) < 1.4e-6 against 2e-6.  d^2 then errs by at most about
+// 2 gamma_22 + 2 ulp relative to the squared bounds: < 2.8e-6 against 4e-6.
+// The absolute term covers the last-bit differences between the FP32 inputs'
 // source values and the FP64 evaluation's own inputs.
 constexpr float kRelQ = 2.0e-6f, kRelD = 4.0e-6f, kAbs = 1.0e-9f;
 
