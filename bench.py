@@ -143,7 +143,7 @@ def step_bytes_per_update(rc, fp32: bool) -> float:
 # time of the capture: a source changed since makes the figure void (null).
 NCU_TRAFFIC = {
     # kernel: (bytes per launch, source file, sha256 prefix)
-    "claim_pair": (177_773_824, "map.cu", "3ed4716179011d9b"),
+    "claim_pair": (177_901_312, "map.cu", "157ed39d738c2067"),
     "reconstruct": (222_159_360, "recon.cu", "64226aaef229a450"),
 }
 

@@ -54,8 +54,9 @@ typedef enum {
   VM_E_PATCH_OVERFLOW = 5, /* an element's influence region exceeded the largest window */
   VM_E_BUDGET = 6,         /* admission refused by a memory budget (batch/serve layer) */
   VM_E_STATE = 7,          /* call out of order (e.g. a step before vm_set_f) */
-  VM_E_INTERNAL = 8        /* an index a kernel read from device state failed its bounds check
+  VM_E_INTERNAL = 8,       /* an index a kernel read from device state failed its bounds check
                               (the access was skipped; vm_diag.bad_where says which check) */
+  VM_E_IO = 9              /* a checkpoint file could not be written or read, or is not one */
 } vm_status;
 
 typedef enum { VM_FP64 = 0, VM_FP32_MIXED = 1 } vm_precision;
@@ -169,6 +170,21 @@ vm_status vm_diagnostics(vm_solver* s, vm_diag* d);
 
 /* Wait for the solver's stream; return and clear any device-side error. */
 vm_status vm_sync(vm_solver* s);
+
+/* Checkpoint of the state the steps carry from one to the next (Sec. 2.4:
+ * the elements' P_m, T, H; Secs. 2.2.2, 2.3.2: f_ini and the spline
+ * coefficients of the last remap; the step count and the position in the
+ * remap cycle), plus the last reconstructed f, to the binary file `path`
+ * (native byte order; a header with the grid, precision and step constants,
+ * then the arrays).  vm_save synchronises the solver's stream first and
+ * returns VM_E_STATE before vm_set_f.  vm_load replaces the state of a
+ * solver created with the same grid, element stride, precision, dt, G,
+ * alpha and beta (VM_E_INVALID_ARG otherwise); the steps that follow are
+ * bit for bit those the saved solver would have taken.  VM_E_IO: the file
+ * cannot be opened, written or read, or is not a checkpoint.  Both calls
+ * synchronise; the path is borrowed for the call. */
+vm_status vm_save(vm_solver* s, const char* path);
+vm_status vm_load(vm_solver* s, const char* path);
 
 /* The CUDA error code behind the last VM_E_CUDA returned to this host thread
  * (cudaSuccess = 0 if none), and its name.  Calls that launch work first

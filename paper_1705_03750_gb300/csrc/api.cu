@@ -2,6 +2,7 @@
 // workspace layout, and the host-side sequencing of the kernels.  The host
 // never touches grid data; it only launches and copies on request.
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -262,6 +263,7 @@ const char* vm_status_string(vm_status st) {
     case VM_E_PATCH_OVERFLOW: return "influence region larger than the largest flood-fill window";
     case VM_E_BUDGET: return "memory budget exceeded";
     case VM_E_STATE: return "call out of order";
+    case VM_E_IO: return "checkpoint file could not be written or read";
   }
   return "unknown status";
 }
@@ -599,3 +601,135 @@ int32_t vm_last_cuda_error(void) { return (int32_t)vm::t_last_cuda; }
 const char* vm_cuda_error_name(int32_t code) { return cudaGetErrorName((cudaError_t)code); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// checkpoints
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr char kCkMagic[8] = {'V', 'L', 'M', 'T', 'C', 'K', 'P', 'T'};
+constexpr uint32_t kCkVersion = 1;
+
+struct CkHeader {
+  char magic[8];
+  uint32_t version;
+  int32_t nx, nv, elem_stride, precision, ne, have_f, cyc;
+  int64_t nstep;
+  uint64_t sreal;
+  double x_lo, x_hi, v_lo, v_hi, dt, G, alpha, beta;
+};
+
+CkHeader ck_header(const vm_solver* s) {
+  CkHeader h;
+  memset(&h, 0, sizeof h);
+  memcpy(h.magic, kCkMagic, sizeof kCkMagic);
+  h.version = kCkVersion;
+  h.nx = s->cfg.nx;
+  h.nv = s->cfg.nv;
+  h.elem_stride = s->cfg.elem_stride;
+  h.precision = s->cfg.precision;
+  h.ne = s->g.ne;
+  h.have_f = s->have_f;
+  h.cyc = s->cyc;
+  h.nstep = s->nstep;
+  h.sreal = s->sreal;
+  h.x_lo = s->cfg.x_lo;
+  h.x_hi = s->cfg.x_hi;
+  h.v_lo = s->cfg.v_lo;
+  h.v_hi = s->cfg.v_hi;
+  h.dt = s->cfg.dt;
+  h.G = s->cfg.G;
+  h.alpha = s->g.alpha;
+  h.beta = s->g.beta;
+  return h;
+}
+
+// The arrays of a checkpoint, in file order.
+struct CkArray {
+  void* dev;
+  size_t bytes;
+};
+
+void ck_arrays(const vm_solver* s, CkArray (&a)[4]) {
+  a[0] = {s->el, 12 * (size_t)s->g.ne * 8};
+  a[1] = {s->fini, s->n * s->sreal};
+  a[2] = {s->eta, s->n * s->sreal};
+  a[3] = {s->f, s->n * s->sreal};
+}
+
+bool same_run(const CkHeader& a, const CkHeader& b) {
+  return a.nx == b.nx && a.nv == b.nv && a.elem_stride == b.elem_stride && a.precision == b.precision &&
+         a.ne == b.ne && a.sreal == b.sreal && a.x_lo == b.x_lo && a.x_hi == b.x_hi && a.v_lo == b.v_lo &&
+         a.v_hi == b.v_hi && a.dt == b.dt && a.G == b.G && a.alpha == b.alpha && a.beta == b.beta;
+}
+
+}  // namespace
+
+vm_status vm_save(vm_solver* s, const char* path) {
+  if (!s || !path) return VM_E_INVALID_ARG;
+  if (!s->have_f) return VM_E_STATE;
+  vm_status st = vm_sync(s);
+  if (st != VM_OK) return st;
+  FILE* fp = fopen(path, "wb");
+  if (!fp) return VM_E_IO;
+  const CkHeader h = ck_header(s);
+  bool ok = fwrite(&h, sizeof h, 1, fp) == 1;
+  CkArray arr[4];
+  ck_arrays(s, arr);
+  std::vector<char> buf;
+  for (int k = 0; k < 4 && ok; k++) {
+    buf.resize(arr[k].bytes);
+    cudaError_t e = cudaMemcpyAsync(buf.data(), arr[k].dev, arr[k].bytes, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+      vm::note_cuda(e);
+      fclose(fp);
+      return VM_E_CUDA;
+    }
+    ok = fwrite(buf.data(), 1, arr[k].bytes, fp) == arr[k].bytes;
+  }
+  ok = (fclose(fp) == 0) && ok;
+  return ok ? VM_OK : VM_E_IO;
+}
+
+vm_status vm_load(vm_solver* s, const char* path) {
+  if (!s || !path) return VM_E_INVALID_ARG;
+  vm_status st = vm_sync(s);
+  if (st != VM_OK) return st;
+  FILE* fp = fopen(path, "rb");
+  if (!fp) return VM_E_IO;
+  CkHeader h;
+  if (fread(&h, sizeof h, 1, fp) != 1 || memcmp(h.magic, kCkMagic, sizeof kCkMagic) != 0 ||
+      h.version != kCkVersion || !h.have_f) {
+    fclose(fp);
+    return VM_E_IO;
+  }
+  if (!same_run(h, ck_header(s))) {
+    fclose(fp);
+    return VM_E_INVALID_ARG;
+  }
+  CkArray arr[4];
+  ck_arrays(s, arr);
+  std::vector<char> buf;
+  for (int k = 0; k < 4; k++) {
+    buf.resize(arr[k].bytes);
+    if (fread(buf.data(), 1, arr[k].bytes, fp) != arr[k].bytes) {
+      fclose(fp);
+      return VM_E_IO;
+    }
+    // (the host buffer is reused for the next array: each copy completes first)
+    cudaError_t e = cudaMemcpyAsync(arr[k].dev, buf.data(), arr[k].bytes, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+      vm::note_cuda(e);
+      fclose(fp);
+      return VM_E_CUDA;
+    }
+  }
+  fclose(fp);
+  s->have_f = 1;
+  s->nstep = h.nstep;
+  s->cyc = h.cyc;
+  return VM_OK;
+}

@@ -22,7 +22,8 @@ VM_DTYPE_F64, VM_DTYPE_F32 = 0, 1
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "workspace too small", 3: "CUDA runtime error",
           4: "unexplored-site repair did not converge", 5: "influence region larger than the largest window",
-          6: "memory budget exceeded", 7: "call out of order", 8: "internal consistency check failed"}
+          6: "memory budget exceeded", 7: "call out of order", 8: "internal consistency check failed",
+          9: "checkpoint file could not be written or read"}
 
 # Names of every entry point declared in include/vlamet.h.
 EXPORTS = ["vm_config_default", "vm_workspace_bytes", "vm_create", "vm_destroy", "vm_status_string",
@@ -31,7 +32,7 @@ EXPORTS = ["vm_config_default", "vm_workspace_bytes", "vm_create", "vm_destroy",
            "vm_read_eta", "vm_read_map", "vm_diagnostics", "vm_sync", "vm_launch_count",
            "vm_profile", "vm_profile_read", "vm_force_from_f_static",
            "vm_batch_create", "vm_batch_step", "vm_batch_launches_per_step", "vm_batch_destroy",
-           "vm_last_cuda_error", "vm_cuda_error_name"]
+           "vm_last_cuda_error", "vm_cuda_error_name", "vm_save", "vm_load"]
 
 VM_STATIC_FORCE_MAX_NX = 16384
 
@@ -109,6 +110,8 @@ def load() -> C.CDLL:
         "vm_batch_destroy": (None, [vp]),
         "vm_last_cuda_error": (i32, []),
         "vm_cuda_error_name": (C.c_char_p, [i32]),
+        "vm_save": (i32, [vp, C.c_char_p]),
+        "vm_load": (i32, [vp, C.c_char_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -282,6 +285,14 @@ class Solver:
 
     def sync(self) -> None:
         _check(self.L.vm_sync(self.h), "vm_sync")
+
+    def save(self, path) -> None:
+        """Checkpoint of the state carried between steps (see vm_save)."""
+        _check(self.L.vm_save(self.h, os.fsencode(path)), "vm_save")
+
+    def load(self, path) -> None:
+        """Replace this solver's state by a checkpoint of the same run (vm_load)."""
+        _check(self.L.vm_load(self.h, os.fsencode(path)), "vm_load")
 
     def density_force(self, out=None) -> dict:
         """M, a, a', a'' ([nx] float64 each) of the last reconstruction.  With
