@@ -323,6 +323,46 @@ struct FPair {
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// The nearest nodes are certain but a containing square (cell) is not: the
+// offset along that axis is within its bound of 0.  The cell enters f only
+// through the cross term, weighted by x y, so the FP32 cell is taken when the
+// largest change the other choice could make, 2 (|x| + e_u)(|y| + e_v) times
+// the largest |cross difference| of the four cells around the node, is at
+// most 1e-7 of the largest |F| of the node's 3x3 block: a proven bound on the
+// effect on f, a tenth of the reconstruction's 1e-6 max|f| tolerance.  (Right
+// after a remap every Q_v lies on a node, and without this rule every site
+// took the FP64 evaluation.)  Returns false, with nothing set, otherwise.
+__device__ __forceinline__ bool cell_free32(const Grid& g, const float* __restrict__ fini, int Bu, float ru,
+                                            float eu, int Bw, float rw, float ew, int& in, int& jn, int& ic,
+                                            int& jc, float& x, float& y) {
+  if (!(floor_sure(ru + 0.5f, eu) && floor_sure(rw + 0.5f, ew))) return false;
+  const float nu = floorf(ru + 0.5f), nw = floorf(rw + 0.5f);
+  const int i0 = Bu + (int)nu, j0 = Bw + (int)nw;
+  float Fb[3][3], fref = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+      Fb[a][b] = F_at32(fini, g, i0 + a - 1, j0 + b - 1);
+      fref = fmaxf(fref, fabsf(Fb[a][b]));
+    }
+  float cm = 0.f;
+#pragma unroll
+  for (int a = 0; a < 2; a++)
+#pragma unroll
+    for (int b = 0; b < 2; b++)
+      cm = fmaxf(cm, fabsf(Fb[a + 1][b + 1] + Fb[a][b] - Fb[a + 1][b] - Fb[a][b + 1]));
+  const float xx = ru - nu, yy = rw - nw;
+  if (!(2.f * (fabsf(xx) + eu) * (fabsf(yy) + ew) * cm <= 1e-7f * fref)) return false;
+  in = i0;
+  jn = j0;
+  ic = Bu + (int)floorf(ru);
+  jc = Bw + (int)floorf(rw);
+  x = xx;
+  y = yy;
+  return true;
+}
+
 // Value of f at site (i, j) owned by element m: every case (node choice by
 // the FP64 evaluation when the FP32 bound cannot settle it, stencils that
 // leave the grid).
@@ -355,6 +395,8 @@ __device__ __noinline__ float recon_site32(const Grid& g, const double* __restri
     jc = Bw + (int)floorf(rw);
     x = ru - nu;
     y = rw - nw;
+  } else if (cell_free32(g, fini, Bu, ru, eu, Bw, rw, ew, in, jn, ic, jc, x, y)) {
+    // nodes certain; the cell taken from the FP32 value (see cell_free32)
   } else {
     // FP64 evaluation, as the FP64 path takes these decisions
     const double* t = tay + (size_t)m * TY_N;
