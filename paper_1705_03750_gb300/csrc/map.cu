@@ -1132,12 +1132,14 @@ constexpr size_t SMEM_SM = 228 * 1024;    // shared memory per SM
 
 struct BigHeader {
   Elem9 E;
-  int item, nlist, ok;
+  int item, nlist, ok, bulk;
   int rmin, rmax, wmin, wmax;  // rows / words holding component bits
   int list[LIST_CAP];          // words to test this round
   unsigned long long lmask[LIST_CAP];  // their untested valid sites
   int lcnt[LIST_CAP];          // inclusive counts of the listed sites
   int wtot[BT / 32];           // per-warp totals of a block scan
+  short plo[FAT_R > BAND_R ? FAT_R : BAND_R];  // per window row: columns of the predicted band
+  short phi[FAT_R > BAND_R ? FAT_R : BAND_R];
 };
 
 // Block-wide inclusive sums out[e] = cnt(0) + ... + cnt(e) for e < n (each
@@ -1400,14 +1402,66 @@ __global__ void __launch_bounds__(BT, BLOCKS_PER_SM) k_claim_big(Grid g, const d
       }
       __syncthreads();
     }
+    // An outer element (a neighbour missing) claims a band that runs to the
+    // padded lattice's edge on its open side.  Its first round also tests,
+    // per window row, the columns where the linear part of its map keeps q
+    // within a margin of the box on every side that has a neighbour (no
+    // bound on a side without one): most of the band in one round instead
+    // of a few rows per round.  Speculative only: the rounds still end only
+    // when every site next to the component has been tested.
+    if (!kGlobal) {
+      bool outer = false;
+      for (int q = 0; q < 9; q++) outer |= !H.E.ex9[q];
+      const float* F = H.E.F9[4];
+      const float T00 = F[TF_T00], T01 = F[TF_T01], T10 = F[TF_T10], T11 = F[TF_T11];
+      const float Tm = fmaxf(fmaxf(fabsf(T00), fabsf(T01)), fmaxf(fabsf(T10), fabsf(T11)));
+      const bool bulk = outer && H.ok && Tm < 1e6f;
+      if (bulk) {
+        const float inv_s = 1.0f / (float)g.s, sf = (float)g.s;
+        const float h = 0.62f + 1.1f * Tm * inv_s;
+        const float xlo = H.E.ex9[1] ? -h : -1e30f, xhi = H.E.ex9[7] ? h : 1e30f;
+        const float vlo = H.E.ex9[3] ? -h : -1e30f, vhi = H.E.ex9[5] ? h : 1e30f;
+        const long long acr0 = W.trans ? j0 : i0, alg0 = W.trans ? i0 : j0;
+        const float offa = W.trans ? H.E.offv[4] : H.E.offu[4];
+        const float C0 = (float)(W.c0 - alg0) + (W.trans ? H.E.offu[4] : H.E.offv[4]);
+        const float cmax = (float)(64 * W.W);
+        for (int r = tid; r < W.R; r += BT) {
+          const float pf = ((float)(W.r0 + r - acr0) + offa) * inv_s;
+          // q_x = ax + bx g, q_v = av + bv g along the row, g = (column + C0) / s
+          const float ax = W.trans ? T01 * pf : T00 * pf, bx = W.trans ? T00 : T01;
+          const float av = W.trans ? T11 * pf : T10 * pf, bv = W.trans ? T10 : T11;
+          float glo = -1e30f, ghi = 1e30f;
+          auto cut = [&](float a, float b, float lo, float hi) {
+            if (fabsf(b) > 1e-20f) {
+              const float t1 = (lo - a) / b, t2 = (hi - a) / b;
+              glo = fmaxf(glo, fminf(t1, t2));
+              ghi = fminf(ghi, fmaxf(t1, t2));
+            } else if (!(a >= lo && a <= hi)) {
+              glo = 1e30f;
+              ghi = -1e30f;
+            }
+          };
+          cut(ax, bx, xlo, xhi);
+          cut(av, bv, vlo, vhi);
+          const float clo = fminf(fmaxf(glo * sf - C0, -1.f), cmax), chi = fmaxf(fminf(ghi * sf - C0, cmax), -1.f);
+          const int lo = max((int)ceilf(clo), 0), hi = min((int)floorf(chi), 64 * W.W - 1);
+          H.plo[r] = (short)(lo <= hi ? lo : 1);
+          H.phi[r] = (short)(lo <= hi ? hi : 0);
+        }
+      }
+      if (tid == 0) H.bulk = bulk;
+    }
     bool escaped = false;
     if (H.ok) {
       for (int it = 0; it < NW * 64; it++) {
         if (tid == 0) H.nlist = 0;
-        const int ra = max(H.rmin - AHEAD, 0), rb = min(H.rmax + AHEAD, W.R - 1);
-        const int wa = max(H.wmin - 1, 0), wb = min(H.wmax + 1, W.W - 1);
-        const int bw = wb - wa + 1, nbox = (rb - ra + 1) * bw;
+        const int ra0 = max(H.rmin - AHEAD, 0), rb0 = min(H.rmax + AHEAD, W.R - 1);
+        const int wa0 = max(H.wmin - 1, 0), wb0 = min(H.wmax + 1, W.W - 1);
         __syncthreads();
+        const bool bulk = !kGlobal && it == 0 && H.bulk;
+        const int ra = bulk ? 0 : ra0, rb = bulk ? W.R - 1 : rb0;
+        const int wa = bulk ? 0 : wa0, wb = bulk ? W.W - 1 : wb0;
+        const int bw = wb - wa + 1, nbox = (rb - ra + 1) * bw;
         // A: is the component open (an untested or passing site next to
         // it)?  List the words with untested sites near it, marking them
         // evaluated now (the list keeps which sites to test).
@@ -1418,7 +1472,8 @@ __global__ void __launch_bounds__(BT, BLOCKS_PER_SM) k_claim_big(Grid g, const d
           const unsigned long long ev = eval[q];
           const unsigned long long near = dilate(comp, W, q) & ~comp[q] & valid;
           if (near & (~ev | pass[q])) open = true;
-          const unsigned long long todo = ahead(comp, W, q) & valid & ~ev;
+          unsigned long long todo = ahead(comp, W, q) & valid & ~ev;
+          if (bulk) todo |= col_mask(w, H.plo[r], H.phi[r] + 1) & valid & ~ev;
           if (todo) {
             const int slot = atomicAdd(&H.nlist, 1);
             if (slot < LIST_CAP) {
