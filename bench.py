@@ -143,8 +143,8 @@ def step_bytes_per_update(rc, fp32: bool) -> float:
 # time of the capture: a source changed since makes the figure void (null).
 NCU_TRAFFIC = {
     # kernel: (bytes per launch, source file, sha256 prefix)
-    "claim_pair": (177_901_312, "map.cu", "157ed39d738c2067"),
-    "reconstruct": (222_159_360, "recon.cu", "64226aaef229a450"),
+    "claim_pair": (177_962_240, "map.cu", "11a635c947a5bdcd"),
+    "reconstruct": (221_293_056, "recon.cu", "5a1b9900593122f6"),
 }
 
 
