@@ -147,9 +147,34 @@ NCU_TRAFFIC = {
     "reconstruct": (221_293_056, "recon.cu", "5a1b9900593122f6"),
 }
 
+# Warp instructions per launch (smsp__inst_executed.sum) from the same
+# captures, for the kernels bound by instruction issue rather than by DRAM:
+# their issue roofline is these instructions over the launch time against
+# one warp instruction per scheduler per clock (4 schedulers x 152 SMs).
+NCU_INSTR = {
+    "claim_pair": (368_574_819, "map.cu", "11a635c947a5bdcd"),
+    "reconstruct": (127_375_042, "recon.cu", "5a1b9900593122f6"),
+}
+SCHEDULERS = 4 * 152
+
+
+def issue_roofline(kernel: str, avg_s: float, sm_mhz):
+    """Issue roofline of a kernel with a captured instruction count, or None."""
+    n = _keyed(NCU_INSTR, kernel)
+    if n is None or not sm_mhz:
+        return None
+    peak = SCHEDULERS * sm_mhz * 1e6
+    ach = n / avg_s
+    return {"warp_instructions": n, "achieved": ach, "peak": peak, "unit": "warp-instr/s",
+            "frac": ach / peak, "clock_mhz": sm_mhz}
+
 
 def ncu_traffic(kernel: str):
-    ent = NCU_TRAFFIC.get(kernel)
+    return _keyed(NCU_TRAFFIC, kernel)
+
+
+def _keyed(table, kernel: str):
+    ent = table.get(kernel)
     if not ent:
         return None
     nbytes, src, sha = ent
@@ -310,6 +335,10 @@ def run_native(args, rank: int, world: int, dist):
         roof.update({"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": ach / peaks["hbm_gbs"], "traffic": ncu_traffic(dom), "per_unit": per,
                      "units": units, "peak_kind": peak_kind})
+    # the limiter the counters show for the map and the reconstruction
+    iss = issue_roofline(dom, avg_s, (head["clocks"] or {}).get("sm_mhz"))
+    if iss is not None:
+        roof["issue"] = iss
     # the whole step against the same peak (algorithmic bytes per cell update)
     bpu = step_bytes_per_update(rc, head["fp32"])
     step_ach = bpu * cells * K / (head["ms"] / 1e3) / 1e9

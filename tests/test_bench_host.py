@@ -18,7 +18,7 @@ def test_step_bytes_per_update_matches_the_per_site_accounting():
 def test_map_algorithmic_bytes_are_one_slot_per_site_and_one_record_per_element():
     rc = I.HALOS_4096
     ne = 515 * 515
-    b, units, _ = bench.algorithmic("claim_small", rc, True, ne)
+    b, units, _ = bench.algorithmic("claim_pair", rc, True, ne)
     assert units == rc.nx * rc.nv and b == 4 * units + 128 * ne
 
 
@@ -31,3 +31,17 @@ def test_ncu_traffic_is_void_once_the_source_changed(monkeypatch):
     assert bench.ncu_traffic("claim_small") == 123
     assert bench.ncu_traffic("reconstruct") is None
     assert bench.ncu_traffic("spline_rows") is None
+
+
+def test_issue_roofline_counts_one_instruction_per_scheduler_per_clock(monkeypatch):
+    src = os.path.join(bench.ROOT, "paper_1705_03750_gb300", "csrc", "map.cu")
+    with open(src, "rb") as fh:
+        sha = hashlib.sha256(fh.read()).hexdigest()
+    monkeypatch.setattr(bench, "NCU_INSTR", {"claim_pair": (1_000_000, "map.cu", sha[:16]),
+                                             "reconstruct": (1_000_000, "map.cu", "0" * 16)})
+    r = bench.issue_roofline("claim_pair", 1e-3, 2000.0)
+    assert r["peak"] == pytest.approx(4 * 152 * 2000e6)
+    assert r["achieved"] == pytest.approx(1e9)
+    assert r["frac"] == pytest.approx(1e9 / (4 * 152 * 2000e6))
+    assert bench.issue_roofline("reconstruct", 1e-3, 2000.0) is None  # source changed
+    assert bench.issue_roofline("claim_pair", 1e-3, None) is None     # no clock sample
