@@ -153,7 +153,13 @@ struct Ctx9 {
   float inv_s, alo, ahi;
 };
 
-// 1: passes, 0: fails, -1: the bound does not settle it (run the exact test).
+// 1: passes, 0: fails; negative: the bound does not settle it (run the exact
+// test).  -1: the alpha ranges themselves are open, or (kOpen false) some
+// comparison is; with kOpen, -2 - mask: the ranges are settled and only the
+// comparisons with the neighbours in `mask` (bit q) are open, every other
+// neighbour being certainly not closer (the windows' tiers, whose rare
+// fallbacks are cheaper than carrying the mask, stop at the first open one).
+template <bool kOpen = false>
 __device__ __forceinline__ int pass_f32(const Ctx9& c, float di, float dj) {
   const QF m = qeval(c.F9[4], (di + c.offu[4]) * c.inv_s, (dj + c.offv[4]) * c.inv_s);
   const float ex = kRelQ * m.ax + kAbs * (1.f + m.ax), ev = kRelQ * m.av + kAbs * (1.f + m.av);
@@ -170,6 +176,7 @@ __device__ __forceinline__ int pass_f32(const Ctx9& c, float di, float dj) {
   const int A = ra - 2, B = rb - 2;
   const int qa = (A + 1) * 3 + 1, qb = 3 + (B + 1), qab = (A + 1) * 3 + (B + 1);
   const int cnt = (A != 0 && B != 0) ? 3 : 1;
+  int open = 0;  // (kOpen) neighbours whose comparison the bound leaves open
   for (int t = 0; t < cnt; t++) {
     const int q = (t == 0) ? (A != 0 ? qa : qb) : (t == 1 ? qb : qab);
     if (!c.ex9[q]) continue;
@@ -178,9 +185,12 @@ __device__ __forceinline__ int pass_f32(const Ctx9& c, float di, float dj) {
     const float An = n.ax * n.ax + n.av * n.av;
     const float en = kRelD * An + kAbs * (1.f + An);
     if (d2n + en < d2 - e2) return 0;
-    if (!(d2n - en >= d2 + e2)) return -1;
+    if (!(d2n - en >= d2 + e2)) {
+      if (!kOpen) return -1;
+      open |= 1 << q;
+    }
   }
-  return 1;
+  return open ? -2 - open : 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -375,11 +385,29 @@ __device__ __forceinline__ Ctx9 ctx_of(const Grid& g, const Elem9& E, float alo,
   return c;
 }
 
+// The exact test restricted to the neighbours whose comparison the FP32
+// bound left open, the alpha ranges being settled: the other neighbours of
+// the ranges are certainly not closer, so the outcome is the full test's.
+__device__ __noinline__ bool pass_exact_open(const Grid& g, const double (*T9)[TY_N], int open, double Px,
+                                             double Pv) {
+  double xi, ze;
+  const double d2 = dist2_exact(T9[4], g, Px, Pv, xi, ze);
+  for (int q = 0; q < 9; q++) {
+    if (!((open >> q) & 1)) continue;
+    double x2, z2;
+    if (dist2_exact(T9[q], g, Px, Pv, x2, z2) < d2) return false;
+  }
+  return true;
+}
+
+// Test of one site in the large windows: their band sites far from the
+// element leave comparisons open far more often than the small windows'.
 __device__ __forceinline__ bool test_site(const Grid& g, const Elem9& E, const Ctx9& c, long long i0, long long j0,
                                           long long i, long long j) {
-  const int r = pass_f32(c, (float)(int)(i - i0), (float)(int)(j - j0));
+  const int r = pass_f32<true>(c, (float)(int)(i - i0), (float)(int)(j - j0));
   if (r >= 0) return r == 1;
-  return pass_exact(g, E.T9, E.ex9, site_x(g, i), site_v(g, j));
+  if (r == -1) return pass_exact(g, E.T9, E.ex9, site_x(g, i), site_v(g, j));
+  return pass_exact_open(g, E.T9, -2 - r, site_x(g, i), site_v(g, j));
 }
 
 // ---------------------------------------------------------------------------
