@@ -266,8 +266,7 @@ def run_native(args, rank: int, world: int, dist):
         launches0 = s.launches
         barrier()
         torch.cuda.synchronize(dev)
-        clocks = ClockSampler(gpu_id, os.path.join(ROOT, "gpurun_out", f"clocks_{name}.csv")
-                              if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+        clocks = ClockSampler(gpu_id, f"{args.clock_log}_{name}.csv" if args.clock_log else None)
         with clocks:
             e0.record(stream)
             s.step(args.steps)
@@ -600,6 +599,7 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--spin", type=float, default=2.0, help="seconds of untimed steps before the warm-up")
+    ap.add_argument("--clock-log", default=None, help="path prefix for the raw clock samples (CSV) of each timed region")
     args = ap.parse_args()
     if args.workload != "halos4096":
         from paper_1705_03750_gb300 import build as B
