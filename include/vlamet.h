@@ -79,6 +79,11 @@ typedef struct {
   int32_t map_windows;        /* 0: every influence-map tier; 1: components that leave the
                                  32 x 64 window go straight to the whole-lattice window
                                  (the last tier), for testing that tier on small grids */
+  double emap_remap;          /* 0: remap every n_s steps only; > 0: also remap after a step
+                                 whose map's E_map (Sec. 2.3.2, element spacings; see
+                                 vm_diag.emap) exceeds this value.  Each step then computes
+                                 E_map and waits for it (vm_step synchronises once per step);
+                                 batches refuse it (VM_E_INVALID_ARG) */
 } vm_config;
 
 typedef struct {
@@ -97,6 +102,15 @@ typedef struct {
   int32_t exact_tests;       /* small-window site tests the FP32 bound could not settle
                                 (run again in FP64) */
   int32_t bad_where;         /* first failed bounds check since creation (0: none) */
+  double entropy;   /* S = -sum f log|f| dx dv of the last f (Sec. 3.2; 0 where f = 0) */
+  double l1;        /* sum |f| dx dv */
+  double l2;        /* sum f^2 dx dv */
+  double emap;      /* E_map of the last influence map (Sec. 2.3.2), in element spacings: the
+                       largest |((a + xi_n) - xi_m, (b + ze_n) - ze_m)| over grid sites P with
+                       owner m and neighbours n = m + (a, b) of the percolation test's alpha
+                       ranges, xi, ze = (Q(P) - Q_elem) / (dx_m, dv_m) from each element's
+                       second-order map; FP64 in the oracle's order (0 before any map) */
+  int64_t emap_remaps; /* remaps that vm_config.emap_remap forced since vm_set_f */
 } vm_diag;
 
 typedef struct vm_solver vm_solver;

@@ -97,6 +97,8 @@ def lib(openmp: bool = True) -> C.CDLL:
             "vo_step_count": (C.c_int64, [C.c_void_p]),
             "vo_cycle_step": (C.c_int32, [C.c_void_p]),
             "vo_diagnostics": (None, [C.c_void_p, _D, _D, _D, _D]),
+            "vo_casimirs": (None, [C.c_void_p, _D, _D, _D]),
+            "vo_emap": (C.c_double, [C.c_void_p]),
             "vo_push_frozen": (None, [C.c_void_p, _D, _D, _D, C.c_double, C.c_double, C.c_int32]),
         }
         for name, (res, args) in sig.items():
@@ -306,7 +308,10 @@ class Oracle:
     def diagnostics(self) -> dict:
         m, e, lo, hi = C.c_double(), C.c_double(), C.c_double(), C.c_double()
         self.L.vo_diagnostics(self.h, C.byref(m), C.byref(e), C.byref(lo), C.byref(hi))
-        return {"mass": m.value, "energy": e.value, "detT_min": lo.value, "detT_max": hi.value}
+        se, l1, l2 = C.c_double(), C.c_double(), C.c_double()
+        self.L.vo_casimirs(self.h, C.byref(se), C.byref(l1), C.byref(l2))
+        return {"mass": m.value, "energy": e.value, "detT_min": lo.value, "detT_max": hi.value,
+                "entropy": se.value, "l1": l1.value, "l2": l2.value, "emap": self.L.vo_emap(self.h)}
 
     def push_frozen(self, a, da, d2a, ext_lo, ext_hi, nsteps):
         a, da, d2a = (np.ascontiguousarray(z, dtype=np.float64) for z in (a, da, d2a))

@@ -983,3 +983,53 @@ void vo_diagnostics(const vo_state* S, double* mass, double* energy, double* dmi
   *dmin = lo;
   *dmax = hi;
 }
+
+/* Sec. 3.2: the Casimir S = -sum f log|f| dx dv (0 where f = 0) and the L1
+ * and L2 norms sum |f| dx dv, sum f^2 dx dv of the last reconstructed f. */
+void vo_casimirs(const vo_state* S, double* entropy, double* l1, double* l2) {
+  const size_t n = (size_t)S->c.nx * S->c.nv;
+  const double dxdv = S->dx * S->dv;
+  double se = 0.0, s1 = 0.0, s2 = 0.0;
+  for (size_t p = 0; p < n; p++) {
+    const double fv = S->f[p];
+    if (fv != 0.0) se = se - fv * log(fabs(fv)) * dxdv;
+    s1 = s1 + fabs(fv) * dxdv;
+    s2 = s2 + fv * fv * dxdv;
+  }
+  *entropy = se;
+  *l1 = s1;
+  *l2 = s2;
+}
+
+/* Sec. 2.3.2: E_map, the largest mismatch, in element spacings, between the
+ * Lagrangian position Q(P) the owner m of a site proposes and the one a
+ * neighbour n investigated by the percolation test proposes:
+ *   ((a + xi_n) - xi_m, (b + ze_n) - ze_m),  (a, b) = n - m,
+ * since Q_n - Q_m = (a dx_m, b dv_m) on the lattice; E_map is the largest
+ * Euclidean norm over the grid's sites, from the last influence map and the
+ * Taylor terms it used. */
+double vo_emap(const vo_state* S) {
+  const int32_t nx = S->c.nx, nv = S->c.nv;
+  double worst = 0.0;
+  for (int32_t i = 0; i < nx; i++)
+    for (int32_t j = 0; j < nv; j++) {
+      const int32_t m = S->map[(size_t)i * nv + j];
+      if (m < 0) continue;
+      const double Px = site_x(S, i), Pv = site_v(S, j);
+      double xi, ze;
+      dist2(S, m, Px, Pv, &xi, &ze);
+      int32_t ab[18];
+      const int32_t nn = vo_alpha_offsets(xi, ze, S->c.alpha, ab);
+      const int32_t k = m / S->Lv, l = m % S->Lv;
+      for (int32_t q = 0; q < nn; q++) {
+        const int32_t kk = k + ab[2 * q], ll = l + ab[2 * q + 1];
+        if (kk < 0 || kk >= S->Lx || ll < 0 || ll >= S->Lv) continue;
+        double xn, zn;
+        dist2(S, kk * S->Lv + ll, Px, Pv, &xn, &zn);
+        const double mx = ((double)ab[2 * q] + xn) - xi, mv = ((double)ab[2 * q + 1] + zn) - ze;
+        const double e2 = mx * mx + mv * mv;
+        if (e2 > worst) worst = e2;
+      }
+    }
+  return sqrt(worst);
+}

@@ -85,6 +85,10 @@ int64_t vo_step_count(const vo_state* S);
 int32_t vo_cycle_step(const vo_state* S);
 void vo_diagnostics(const vo_state* S, double* mass, double* energy, double* detT_min,
                     double* detT_max);
+/* Sec. 3.2: S = -sum f log|f| dx dv, L1 and L2 norms of the last f. */
+void vo_casimirs(const vo_state* S, double* entropy, double* l1, double* l2);
+/* Sec. 2.3.2: E_map of the last influence map, in element spacings. */
+double vo_emap(const vo_state* S);
 /* element push under a frozen grid force (a, a', a'' given on the x nodes) */
 void vo_push_frozen(vo_state* S, const double* a, const double* da, const double* d2a,
                     double ext_lo, double ext_hi, int32_t nsteps);

@@ -30,6 +30,7 @@ bool valid(const vm_config* c) {
   if (c->precision != VM_FP64 && c->precision != VM_FP32_MIXED) return false;
   if (c->pad < 0 || c->max_hole_rounds < 0) return false;
   if (c->map_windows != 0 && c->map_windows != 1) return false;
+  if (!(c->emap_remap >= 0.0) || !isfinite(c->emap_remap)) return false;
   if (!(c->alpha >= 0.0) || !(c->beta >= 0.0)) return false;
   // 32-bit site indices; element indices fit the 24-bit field of the owner slots
   if ((long long)c->nx * (long long)c->nv >= (1ll << 31) / 2) return false;
@@ -161,6 +162,21 @@ cudaError_t step_remap(vm_solver* s) {
 }  // namespace vm
 
 namespace {
+
+// E_map of the current influence map, computed and read back (synchronises).
+vm_status emap_now(vm_solver* s, double* e) {
+  vm::DevState* d = s->ds;
+  VM_CUDA_TRY(cudaMemsetAsync(&d->emap2_bits, 0, sizeof d->emap2_bits, s->stream));
+  vm::launch_emap(s);
+  unsigned long long bits = 0;
+  VM_CUDA_TRY(cudaMemcpyAsync(&bits, &d->emap2_bits, sizeof bits, cudaMemcpyDeviceToHost, s->stream));
+  vm_status st = vm_sync(s);
+  if (st != VM_OK) return st;
+  double e2;
+  memcpy(&e2, &bits, 8);
+  *e = sqrt(e2);
+  return VM_OK;
+}
 
 vm_status remap_internal(vm_solver* s) {
   if (vm::step_remap(s) != cudaSuccess) return VM_E_CUDA;
@@ -447,6 +463,7 @@ vm_status vm_set_f(vm_solver* s, const double* f0, int32_t on_device) {
   vm::launch_reset_elements(s);
   s->have_f = 1;
   s->nstep = 0;
+  s->emap_remaps = 0;
   s->cyc = 0;
   return check_launch(s);
 }
@@ -493,7 +510,18 @@ vm_status vm_step(vm_solver* s, int32_t nsteps) {
     vm::step_transport(s);
     s->nstep++;
     s->cyc++;
-    if (s->cyc >= s->cfg.n_s) {
+    bool remap = s->cyc >= s->cfg.n_s;
+    if (!remap && s->cfg.emap_remap > 0.0) {
+      // E_map of this step's map (Sec. 2.3.2), read back to decide
+      double e = 0.0;
+      vm_status st = emap_now(s, &e);
+      if (st != VM_OK) return st;
+      if (e > s->cfg.emap_remap) {
+        remap = true;
+        s->emap_remaps++;
+      }
+    }
+    if (remap) {
       vm_status st = remap_internal(s);
       if (st != VM_OK) return st;
     }
@@ -571,6 +599,7 @@ vm_status vm_diagnostics(vm_solver* s, vm_diag* d) {
   VM_CUDA_TRY(cudaMemcpyAsync((char*)s->ds + off, (char*)&h + off, sizeof(vm::DevState) - off,
                               cudaMemcpyHostToDevice, s->stream));
   vm::launch_diagnostics(s);
+  vm::launch_emap(s);
   VM_CUDA_TRY(cudaMemcpyAsync(&h, s->ds, sizeof h, cudaMemcpyDeviceToHost, s->stream));
   vm_status st = vm_sync(s);
   if (st != VM_OK) return st;
@@ -593,6 +622,13 @@ vm_status vm_diagnostics(vm_solver* s, vm_diag* d) {
   d->last_tier_elements = s->cfg.map_windows == 0 ? h.overflow3_stat : h.overflow_stat;
   d->exact_tests = h.n_exact;
   d->bad_where = h.bad_where;
+  d->entropy = h.sum_ent;
+  d->l1 = h.sum_l1;
+  d->l2 = h.sum_l2;
+  double e2;
+  memcpy(&e2, &h.emap2_bits, 8);
+  d->emap = sqrt(e2);
+  d->emap_remaps = s->emap_remaps;
   return VM_OK;
 }
 

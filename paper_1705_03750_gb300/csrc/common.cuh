@@ -63,6 +63,8 @@ struct DevState {
   double Mtot;           // total mass of the last reconstruction
   double sum_mass, sum_kin, sum_pot;
   unsigned long long det_min_key, det_max_key;
+  double sum_ent, sum_l1, sum_l2;   // Casimirs of the last f (Sec. 3.2)
+  unsigned long long emap2_bits;     // bits of the largest squared E_map term (>= 0)
 };
 
 // Owner slots of the influence map: (epoch << 24) | element index.  A slot
@@ -154,6 +156,7 @@ struct vm_solver {
   // host-side bookkeeping
   int32_t have_f;
   int64_t nstep;
+  int64_t emap_remaps;      // remaps forced by cfg.emap_remap since vm_set_f
   int32_t cyc;
   int64_t launches;
   // optional per-launch timing: event pairs around each launch
@@ -187,6 +190,8 @@ void launch_scan_force(vm_solver* s);
 void launch_scan_force_raw(const Grid& g, const double* M, double* a, double* da, double* d2a, DevState* ds,
                            cudaStream_t stream);
 void launch_diagnostics(vm_solver* s);
+// E_map of the last influence map (Sec. 2.3.2) into ds->emap2_bits (zeroed by the caller)
+void launch_emap(vm_solver* s);
 // map.cu
 bool map_prepare(const Grid& g);
 void launch_map(vm_solver* s);

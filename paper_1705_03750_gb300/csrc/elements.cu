@@ -265,34 +265,38 @@ __device__ __forceinline__ unsigned long long order_key(double d) {
 template <typename R>
 __global__ void k_diag(Grid g, const R* __restrict__ f, const double* __restrict__ a,
                        const double* __restrict__ el, DevState* ds) {
-  __shared__ double red[2][32];
-  double ms = 0.0, ek = 0.0;
+  __shared__ double red[5][32];
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // mass, kinetic energy, S, L1, L2 (Sec. 3.2)
   const size_t n = (size_t)g.nx * g.nv;
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
     int j = (int)(p % g.nv);
     double v = dadd(g.v_lo, dmul((double)j, g.dv));
     double fv = (double)f[p];
-    ms += fv * g.dxdv;
-    ek += 0.5 * (v * v) * fv * g.dxdv;
+    acc[0] += fv * g.dxdv;
+    acc[1] += 0.5 * (v * v) * fv * g.dxdv;
+    if (fv != 0.0) acc[2] -= fv * log(fabs(fv)) * g.dxdv;
+    acc[3] += fabs(fv) * g.dxdv;
+    acc[4] += fv * fv * g.dxdv;
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    ms += __shfl_down_sync(0xffffffffu, ms, o);
-    ek += __shfl_down_sync(0xffffffffu, ek, o);
-  }
+#pragma unroll
+  for (int c = 0; c < 5; c++)
+    for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], o);
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
-    red[0][wid] = ms;
-    red[1][wid] = ek;
+#pragma unroll
+    for (int c = 0; c < 5; c++) red[c][wid] = acc[c];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double a0 = 0, a1 = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
-      a0 += red[0][w];
-      a1 += red[1][w];
-    }
-    atomicAdd(&ds->sum_mass, a0);
-    atomicAdd(&ds->sum_kin, a1);
+    double t[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++)
+#pragma unroll
+      for (int c = 0; c < 5; c++) t[c] += red[c][w];
+    atomicAdd(&ds->sum_mass, t[0]);
+    atomicAdd(&ds->sum_kin, t[1]);
+    atomicAdd(&ds->sum_ent, t[2]);
+    atomicAdd(&ds->sum_l1, t[3]);
+    atomicAdd(&ds->sum_l2, t[4]);
   }
   // potential energy and det T range (grid-stride, atomics)
   const double a8 = g.A * ds->Mtot;

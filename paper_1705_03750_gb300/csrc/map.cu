@@ -1744,6 +1744,47 @@ __global__ void __launch_bounds__(HT) k_holes(Grid g, const double* __restrict__
   }
 }
 
+// E_map (Sec. 2.3.2) of the current influence map: for every grid site with
+// an owner m, and every existing neighbour n = m + (a, b) in the alpha
+// ranges of the percolation test, the squared mismatch of the Lagrangian
+// positions they propose in element spacings, ((a + xi_n) - xi_m)^2 +
+// ((b + ze_n) - ze_m)^2 (Q_n - Q_m = (a dx_m, b dv_m) on the lattice), FP64
+// in the oracle's order; the largest into ds->emap2_bits (bits of a
+// non-negative double order as the values do).
+__global__ void k_emap(Grid g, const uint32_t* __restrict__ slot0, const double* __restrict__ tay, DevState* ds) {
+  const uint32_t epoch = *(volatile uint32_t*)&ds->epoch;
+  const size_t n = (size_t)g.nx * g.nv;
+  double worst = 0.0;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t t = slot0[p];
+    if ((t >> 24) != epoch) continue;
+    const int m = (int)(t & SLOT_MASK);
+    if (m >= g.ne) continue;
+    const int i = (int)(p / (size_t)g.nv), j = (int)(p - (size_t)i * g.nv);
+    const double Px = site_x(g, i), Pv = site_v(g, j);
+    double xi, ze;
+    dist2_exact(tay + (size_t)m * TY_N, g, Px, Pv, xi, ze);
+    int a0, a1, b0, b1;
+    alpha_range(xi, g.alpha, a0, a1);
+    alpha_range(ze, g.alpha, b0, b1);
+    const int k = m / g.Lv, l = m - k * g.Lv;
+    for (int a = a0; a <= a1; a++)
+      for (int b = b0; b <= b1; b++) {
+        if (a == 0 && b == 0) continue;
+        const int kk = k + a, ll = l + b;
+        if (kk < 0 || kk >= g.Lx || ll < 0 || ll >= g.Lv) continue;
+        double xn, zn;
+        dist2_exact(tay + (size_t)(kk * g.Lv + ll) * TY_N, g, Px, Pv, xn, zn);
+        const double mx = dsub(dadd((double)a, xn), xi), mv = dsub(dadd((double)b, zn), ze);
+        const double e2 = dadd(dmul(mx, mx), dmul(mv, mv));
+        if (e2 > worst) worst = e2;
+      }
+  }
+  for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_down_sync(0xffffffffu, worst, o));
+  if ((threadIdx.x & 31) == 0 && worst > 0.0)
+    atomicMax(&ds->emap2_bits, (unsigned long long)__double_as_longlong(worst));
+}
+
 __global__ void k_read_map(const uint32_t* __restrict__ slot0, const DevState* ds, int32_t* __restrict__ out,
                            size_t n) {
   const uint32_t epoch = *(const volatile uint32_t*)&ds->epoch;
@@ -1752,6 +1793,17 @@ __global__ void k_read_map(const uint32_t* __restrict__ slot0, const DevState* d
     out[p] = ((t >> 24) == epoch) ? (int32_t)(t & SLOT_MASK) : -1;
   }
 }
+
+}  // namespace
+
+void launch_emap(vm_solver* s) {
+  unsigned nb = (unsigned)((s->n + 255) / 256);
+  if (nb > 152 * 16) nb = 152 * 16;
+  k_emap<<<nb, 256, 0, s->stream>>>(s->g, s->map, s->tay, s->ds);
+  s->launches++;
+}
+
+namespace {
 
 size_t big_smem_bytes(const Grid& g) {
   long long nw = 0;

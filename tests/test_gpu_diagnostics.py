@@ -1,0 +1,118 @@
+"""Diagnostics through the C ABI against the FP64 oracle: E_map of an
+influence map (Sec. 2.3.2) and the Casimirs S, L1, L2 (Sec. 3.2); and the
+E_map-triggered remap of vm_config.emap_remap."""
+import numpy as np
+import pytest
+
+import oracle.oracle as O
+from paper_1705_03750_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1705_03750_gb300 import build as B  # noqa: E402
+
+B.build()
+from paper_1705_03750_gb300 import vlamet as V  # noqa: E402
+
+PREC = {"fp64": V.VM_FP64, "fp32": V.VM_FP32_MIXED}
+
+
+def oracle_of(rc, n_s=None):
+    return O.Oracle(rc.nx, rc.nv, rc.x_lo, rc.x_hi, rc.v_lo, rc.v_hi, rc.s, rc.dt,
+                    rc.n_s if n_s is None else n_s, rc.G)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("steps", [0, 40, 150])
+def test_emap_matches_oracle_exactly_on_injected_elements(prec, steps):
+    # the same elements on both sides: the maps are bit-exact and E_map is
+    # the same FP64 expressions in the same order
+    rc = I.SPITZER_128
+    s = V.Solver(V.Config.from_run(rc, PREC[prec]))
+    o = oracle_of(rc)
+    f0 = I.initial_f(rc)
+    s.set_f(f0)
+    o.set_f(f0)
+    if steps:
+        ev = oracle_of(rc, n_s=10 ** 6)
+        ev.set_f(f0)
+        ev.step(steps)
+        el = ev.elements()
+        o.set_elements(el)
+        s.set_elements(np.ascontiguousarray(el.T))
+    s.compute_map()
+    o.compute_map()
+    eg, eo = s.diagnostics()["emap"], o.diagnostics()["emap"]
+    assert eg == eo, (eg, eo)
+    if steps:
+        assert eo > 0.0
+
+
+def test_casimirs_match_oracle_after_a_step():
+    rc = I.SPITZER_128
+    s = V.Solver(V.Config.from_run(rc, V.VM_FP64))
+    o = oracle_of(rc)
+    f0 = I.initial_f(rc)
+    s.set_f(f0)
+    o.set_f(f0)
+    s.step(3)
+    o.step(3)
+    dg, do = s.diagnostics(), o.diagnostics()
+    for k in ("entropy", "l1", "l2"):
+        assert dg[k] == pytest.approx(do[k], rel=1e-11), k
+    # after whole steps the elements agree to rounding only (the force sums
+    # in another order), and so does E_map
+    assert dg["emap"] == pytest.approx(do["emap"], rel=1e-9)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_emap_remap_threshold(prec):
+    # vm_step with emap_remap = thr against the same rule applied by hand:
+    # after each step, read E_map of that step's map (vm_diagnostics) and
+    # call vm_remap when it exceeds thr.  The threshold is the median of a
+    # plain run's values, so that some steps remap and some do not.
+    rc = I.HALOS_4096.with_(nx=128, nv=128, s=4, n_s=1000)
+    f0 = I.initial_f(rc)
+
+    def solver(thr):
+        cfg = V.Config.from_run(rc, PREC[prec])
+        cfg.emap_remap = thr
+        s = V.Solver(cfg)
+        s.set_f(f0)
+        return s
+
+    plain = solver(0.0)
+    seen = []
+    for _ in range(8):
+        plain.step(1)
+        seen.append(plain.diagnostics()["emap"])
+    assert plain.diagnostics()["emap_remaps"] == 0
+    thr = float(np.median(seen))
+    assert thr > 0.0
+    auto, hand = solver(thr), solver(0.0)
+    forced = 0
+    for _ in range(8):
+        auto.step(1)
+        hand.step(1)
+        if hand.diagnostics()["emap"] > thr:
+            hand.remap()
+            forced += 1
+    assert 0 < forced < 8
+    assert auto.diagnostics()["emap_remaps"] == forced
+    assert np.array_equal(auto.read_f(), hand.read_f())
+    assert np.array_equal(auto.elements(), hand.elements())
+
+
+def test_batch_refuses_emap_remap():
+    rc = I.HALOS_4096.with_(nx=64, nv=64, s=4, n_s=4)
+    cfg = V.Config.from_run(rc, V.VM_FP32_MIXED)
+    cfg.emap_remap = 0.5
+    s = V.Solver(cfg)
+    s.set_f(I.initial_f(rc))
+    with pytest.raises(V.VlametError) as e:
+        V.Batch([s], nstreams=1)
+    assert e.value.status == 1

@@ -636,3 +636,62 @@ def test_frozen_potential_backward_map_is_second_order_in_element_spacing():
             Q = np.array([tay[mm, 12] + dq[0], tay[mm, 13] + dq[1]])
             errs.append(np.abs(Q - Minv @ np.array([X[i, j], V[i, j]])).max())
     assert max(errs) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3.2 Casimirs and Sec. 2.3.2 E_map
+# ---------------------------------------------------------------------------
+
+def test_casimirs_of_a_gaussian_match_closed_forms():
+    """S = -int f log f, L1 and L2 of a normalised isotropic Gaussian
+    (variance s2 per axis) are log(2 pi e s2), 1 and 1/(4 pi s2); the grid
+    sums converge to them (midpoint quadrature of a smooth, decayed f)."""
+    s2 = 0.09
+    n = 401
+    o = _oracle(nx=n, nv=n, box=(-3.0, 3.0, -3.0, 3.0))
+    x = np.linspace(-3, 3, n)
+    X, V = np.meshgrid(x, x, indexing="ij")
+    f = np.exp(-(X ** 2 + V ** 2) / (2 * s2)) / (2 * math.pi * s2)
+    o.set_f(f)
+    d = o.diagnostics()
+    assert d["entropy"] == pytest.approx(math.log(2 * math.pi * math.e * s2), rel=1e-6)
+    assert d["l1"] == pytest.approx(1.0, rel=1e-9)
+    assert d["l2"] == pytest.approx(1.0 / (4 * math.pi * s2), rel=1e-6)
+    # |f| and f log|f| for a sign change: S uses |f| inside the log only
+    o.set_f(-f)
+    d2 = o.diagnostics()
+    assert d2["l1"] == pytest.approx(d["l1"]) and d2["l2"] == pytest.approx(d["l2"])
+    assert d2["entropy"] == pytest.approx(-d["entropy"])
+
+
+def test_emap_vanishes_where_the_second_order_maps_are_exact():
+    """E_map compares the positions two neighbouring elements propose for the
+    same site.  Where every element follows the same flow and its
+    second-order map is exact (elements on the lattice at initialisation;
+    free streaming, whose maps are linear) all proposals coincide, and E_map
+    is rounding only; a wrong sign or index in the mismatch
+    ((a + xi_n) - xi_m) would make it of order one.  (A frozen force is no
+    such case: the outer elements, beyond the grid, feel its constant
+    extension, not the interior's law.)"""
+    o = _oracle(nx=129, nv=65, box=(-2.0, 2.0, -2.0, 2.0), s=4, dt=0.02)
+    o.set_f(np.zeros((129, 65)))
+    assert o.diagnostics()["emap"] == 0.0  # no map yet
+    o.compute_map()
+    assert o.diagnostics()["emap"] < 1e-12
+    fr = _oracle(nx=129, nv=65, box=(-2.0, 2.0, -2.0, 2.0), s=4, dt=0.01, G=0.0)
+    fr.set_f(np.zeros((129, 65)))
+    fr.step(30)  # free streaming: exact linear maps; the step's map is the transport map
+    assert fr.diagnostics()["emap"] < 1e-10
+
+
+def test_emap_is_positive_for_a_nonlinear_flow():
+    """An anharmonic frozen force makes the maps curved: neighbouring
+    elements then disagree at third order and E_map is clearly non-zero."""
+    n = 129
+    o = _oracle(nx=n, nv=65, box=(-2.0, 2.0, -2.0, 2.0), s=4, dt=0.02)
+    o.set_f(np.zeros((n, 65)))
+    x = np.linspace(-2, 2, n)
+    k = 2.0
+    o.push_frozen(-np.sin(k * x), -k * np.cos(k * x), k * k * np.sin(k * x), 0.0, 0.0, 30)
+    o.compute_map()
+    assert o.diagnostics()["emap"] > 1e-6
