@@ -143,7 +143,7 @@ def step_bytes_per_update(rc, fp32: bool) -> float:
 # time of the capture: a source changed since makes the figure void (null).
 NCU_TRAFFIC = {
     # kernel: (bytes per launch, source file, sha256 prefix)
-    "claim_pair": (178_178_816, "map.cu", "d00a3f0ed811df29"),
+    "claim_pair": (177_736_448, "map.cu", "9ce38691f9320969"),
     "reconstruct": (221_293_056, "recon.cu", "5a1b9900593122f6"),
 }
 
@@ -152,7 +152,7 @@ NCU_TRAFFIC = {
 # their issue roofline is these instructions over the launch time against
 # one warp instruction per scheduler per clock (4 schedulers x 152 SMs).
 NCU_INSTR = {
-    "claim_pair": (368_574_819, "map.cu", "d00a3f0ed811df29"),
+    "claim_pair": (368_574_819, "map.cu", "9ce38691f9320969"),
     "reconstruct": (127_375_042, "recon.cu", "5a1b9900593122f6"),
 }
 SCHEDULERS = 4 * 152
