@@ -10,7 +10,10 @@ Workloads, shaped after the paper's tests (Sec. 3.2):
     first test, normalised to total mass 1 with G = 1;
   * a sum of warm Gaussian halos, standing in for the paper's random set of
     stationary clouds (whose exact construction is not given in the paper);
-  * a free-streaming (G = 0) run on the Spitzer grid.
+  * a free-streaming (G = 0) run on the Spitzer grid;
+  * the paper's truncated Gaussian initial condition (Sec. 3.2, eqs. monfg,
+    gauini): rho_G exp(-(x^2 + v^2)/(2 sigma_G^2)) inside radius R, cut
+    smoothly beyond it by max[1 + 2 tanh((R - r)/eta_G), 0].
 """
 from __future__ import annotations
 
@@ -118,6 +121,19 @@ def draw_halos(seed: int, n: int = 16, centre: float = 0.5, sx=(0.02, 0.1), sv=(
     return Halos(xc, vc, sxs, svs, m)
 
 
+def gaussian_ic(x, v, rho=4.0, sigma=0.2, R=1.0, eta=0.02):
+    """The paper's Gaussian initial condition (Sec. 3.2): rho exp(-r^2 /
+    (2 sigma^2)) for r = sqrt(x^2 + v^2) <= R, times max[1 + 2 tanh((R - r) /
+    eta), 0] beyond R.  The paper's values rho = 4, sigma = 0.2, R = 1,
+    eta = 0.02 give a total mass close to 1 (a Gaussian cut at 5 sigma)."""
+    x = np.asarray(x, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
+    r = np.sqrt(x * x + v * v)
+    g = rho * np.exp(-0.5 * (x * x + v * v) / (sigma * sigma))
+    cut = np.maximum(1.0 + 2.0 * np.tanh((R - r) / eta), 0.0)
+    return np.where(r <= R, g, g * cut)
+
+
 def initial_f(cfg: RunConfig) -> np.ndarray:
     """f0 sampled on the nodes, [nx, nv] float64, v fastest."""
     X, V = np.meshgrid(cfg.x(), cfg.v(), indexing="ij")
@@ -126,6 +142,8 @@ def initial_f(cfg: RunConfig) -> np.ndarray:
     if cfg.ic == "halos":
         h = draw_halos(cfg.seed, n=cfg.ic_params.get("n", 16))
         return h.on_grid(cfg.x(), cfg.v())
+    if cfg.ic == "gauss":
+        return gaussian_ic(X, V, **cfg.ic_params)
     if cfg.ic == "blob":
         # a single warm Gaussian well inside the box (free-streaming checks)
         p = cfg.ic_params
@@ -141,6 +159,8 @@ def ic_function(cfg: RunConfig):
         return lambda x, v: spitzer(x, v, sigma=sig, G=cfg.G if cfg.G else 1.0)
     if cfg.ic == "halos":
         return draw_halos(cfg.seed, n=cfg.ic_params.get("n", 16))
+    if cfg.ic == "gauss":
+        return lambda x, v: gaussian_ic(x, v, **cfg.ic_params)
     if cfg.ic == "blob":
         p = cfg.ic_params
         return lambda x, v: np.exp(-0.5 * ((x - p.get("x0", 0.0)) / p.get("sx", 0.15)) ** 2
@@ -156,8 +176,11 @@ FREE_128 = SPITZER_128.with_(name="free-streaming-128x128-G0", G=0.0)
 HALOS_4096 = RunConfig("halos16-4096x4096", 4096, 4096, -1.0, 1.0, -1.5, 1.5, 8, 0.002, 25, 1.0, 1000,
                        "halos", {"n": 16}, seed=0)
 HALOS_8192 = HALOS_4096.with_(name="halos16-8192x8192", nx=8192, nv=8192, steps=500)
+# the paper's Gaussian run on a box just wider than the cut radius (Delta = 2.4/127)
+GAUSS_128 = RunConfig("gauss-128x128-G1", 128, 128, -1.2, 1.2, -1.2, 1.2, 4, 0.005, 20, 1.0, 200,
+                      "gauss", {"rho": 4.0, "sigma": 0.2, "R": 1.0, "eta": 0.02})
 
-WORKLOADS = {c.name: c for c in (SPITZER_128, FREE_128, HALOS_4096, HALOS_8192)}
+WORKLOADS = {c.name: c for c in (SPITZER_128, FREE_128, HALOS_4096, HALOS_8192, GAUSS_128)}
 
 
 def batch_member(index: int, base_seed: int = 1000) -> RunConfig:

@@ -695,3 +695,20 @@ def test_emap_is_positive_for_a_nonlinear_flow():
     o.push_frozen(-np.sin(k * x), -k * np.cos(k * x), k * k * np.sin(k * x), 0.0, 0.0, 30)
     o.compute_map()
     assert o.diagnostics()["emap"] > 1e-6
+
+
+def test_gaussian_initial_condition_mass_and_cut():
+    """The paper's Gaussian IC (Sec. 3.2): total mass rho 2 pi sigma^2
+    (1 - exp(-R^2 / 2 sigma^2)) plus a negligible apodised rim, continuous
+    at R, zero beyond R + eta atanh(1/2)."""
+    p = {"rho": 4.0, "sigma": 0.2, "R": 1.0, "eta": 0.02}
+    n = 1201
+    x = np.linspace(-1.2, 1.2, n)
+    X, V = np.meshgrid(x, x, indexing="ij")
+    f = I.gaussian_ic(X, V, **p)
+    dx = x[1] - x[0]
+    exact = p["rho"] * 2 * math.pi * p["sigma"] ** 2 * (1 - math.exp(-p["R"] ** 2 / (2 * p["sigma"] ** 2)))
+    assert f.sum() * dx * dx == pytest.approx(exact, rel=1e-6)
+    r_cut = p["R"] + p["eta"] * math.atanh(0.5)
+    assert I.gaussian_ic(p["R"], 0.0, **p) == pytest.approx(I.gaussian_ic(p["R"] - 1e-12, 0.0, **p), rel=1e-9)
+    assert I.gaussian_ic(r_cut + 1e-9, 0.0, **p) == 0.0 and I.gaussian_ic(r_cut - 1e-3, 0.0, **p) > 0.0
