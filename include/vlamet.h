@@ -84,6 +84,11 @@ typedef struct {
                                  vm_diag.emap) exceeds this value.  Each step then computes
                                  E_map and waits for it (vm_step synchronises once per step);
                                  batches refuse it (VM_E_INVALID_ARG) */
+  double c_dyn;               /* 0: constant dt; > 0: each step takes min(dt, c_dyn /
+                                 sqrt(rho_max)) (Sec. 2.4), rho_max the largest
+                                 rho(x_i) = sum_j f(i, j) dv of the last reconstructed f
+                                 (f0 before the first step); vm_step then synchronises once
+                                 per step; batches refuse it */
 } vm_config;
 
 typedef struct {
@@ -111,6 +116,8 @@ typedef struct {
                        ranges, xi, ze = (Q(P) - Q_elem) / (dx_m, dv_m) from each element's
                        second-order map; FP64 in the oracle's order (0 before any map) */
   int64_t emap_remaps; /* remaps that vm_config.emap_remap forced since vm_set_f */
+  double time;         /* sum of the steps taken since vm_set_f */
+  double last_dt;      /* the last step's time step */
 } vm_diag;
 
 typedef struct vm_solver vm_solver;

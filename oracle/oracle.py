@@ -99,6 +99,9 @@ def lib(openmp: bool = True) -> C.CDLL:
             "vo_diagnostics": (None, [C.c_void_p, _D, _D, _D, _D]),
             "vo_casimirs": (None, [C.c_void_p, _D, _D, _D]),
             "vo_emap": (C.c_double, [C.c_void_p]),
+            "vo_set_cdyn": (None, [C.c_void_p, C.c_double]),
+            "vo_time": (C.c_double, [C.c_void_p]),
+            "vo_last_dt": (C.c_double, [C.c_void_p]),
             "vo_push_frozen": (None, [C.c_void_p, _D, _D, _D, C.c_double, C.c_double, C.c_int32]),
         }
         for name, (res, args) in sig.items():
@@ -312,6 +315,16 @@ class Oracle:
         self.L.vo_casimirs(self.h, C.byref(se), C.byref(l1), C.byref(l2))
         return {"mass": m.value, "energy": e.value, "detT_min": lo.value, "detT_max": hi.value,
                 "entropy": se.value, "l1": l1.value, "l2": l2.value, "emap": self.L.vo_emap(self.h)}
+
+    def set_cdyn(self, c_dyn: float) -> None:
+        """Variable time step min(dt, c_dyn / sqrt(rho_max)) (0: constant)."""
+        self.L.vo_set_cdyn(self.h, float(c_dyn))
+
+    def time(self) -> float:
+        return self.L.vo_time(self.h)
+
+    def last_dt(self) -> float:
+        return self.L.vo_last_dt(self.h)
 
     def push_frozen(self, a, da, d2a, ext_lo, ext_hi, nsteps):
         a, da, d2a = (np.ascontiguousarray(z, dtype=np.float64) for z in (a, da, d2a))

@@ -68,6 +68,9 @@ struct vo_state {
   int64_t nstep;
   int32_t cyc;
   int32_t have_f;
+  double c_dyn;  /* > 0: variable time step (Sec. 2.4), Delta t = min(dt, c_dyn / sqrt(rho_max)) */
+  double time;   /* sum of the steps taken since vo_set_f */
+  double last_dt;
   /* percolation scratch */
   int32_t* stamp;
   int32_t* queue;
@@ -495,8 +498,34 @@ int32_t vo_set_f(vo_state* S, const double* f0) {
   vo_spline_solve_2d(S->c.nx, S->c.nv, S->fini, S->eta);
   reset_elements(S);
   S->nstep = 0;
+  S->time = 0.0;
   S->have_f = 1;
   return VO_OK;
+}
+
+/* Variable time step (Sec. 2.4, eq. of Delta t): each step takes
+ * min(dt, c_dyn / sqrt(rho_max)), rho_max the largest projected density
+ * rho(x_i) = sum_j f(i, j) dv of the last reconstructed f (f0 before the
+ * first step); c_dyn = 0 keeps the constant dt of the configuration. */
+void vo_set_cdyn(vo_state* S, double c_dyn) { S->c_dyn = c_dyn; }
+double vo_time(const vo_state* S) { return S->time; }
+double vo_last_dt(const vo_state* S) { return S->last_dt; }
+
+static double step_dt(vo_state* S, double dt_cap) {
+  if (!(S->c_dyn > 0.0)) return dt_cap;
+  const int32_t nx = S->c.nx, nv = S->c.nv;
+  double rmax = 0.0;
+  for (int32_t i = 0; i < nx; i++) {
+    double r = 0.0;
+    for (int32_t j = 0; j < nv; j++) r = r + S->f[(size_t)i * nv + j];
+    r = r * S->dv;
+    if (r > rmax) rmax = r;
+  }
+  if (rmax > 0.0) {
+    const double lim = S->c_dyn / sqrt(rmax);
+    if (lim < dt_cap) return lim;
+  }
+  return dt_cap;
 }
 
 void vo_get_elements(const vo_state* S, double* out) {
@@ -910,7 +939,10 @@ int32_t vo_remap(vo_state* S) {
  * remap at the end of every n_s-th step of a cycle. */
 int32_t vo_step(vo_state* S, int32_t nsteps) {
   int32_t st = VO_OK;
+  const double dt_cap = S->c.dt;
   for (int32_t it = 0; it < nsteps; it++) {
+    S->c.dt = step_dt(S, dt_cap);
+    S->last_dt = S->c.dt;
     drift_half(S);
     int32_t s1 = vo_compute_map(S, NULL);
     if (s1 != VO_OK) st = s1;
@@ -919,12 +951,14 @@ int32_t vo_step(vo_state* S, int32_t nsteps) {
     kick(S, S->a, S->da, S->d2a, A * S->Mtot, -(A * S->Mtot));
     drift_half(S);
     S->nstep++;
+    S->time = S->time + S->c.dt;
     S->cyc++;
     if (S->cyc >= S->c.n_s) {
       int32_t s2 = vo_remap(S);
       if (s2 != VO_OK) st = s2;
     }
   }
+  S->c.dt = dt_cap;
   return st;
 }
 

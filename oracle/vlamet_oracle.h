@@ -89,6 +89,10 @@ void vo_diagnostics(const vo_state* S, double* mass, double* energy, double* det
 void vo_casimirs(const vo_state* S, double* entropy, double* l1, double* l2);
 /* Sec. 2.3.2: E_map of the last influence map, in element spacings. */
 double vo_emap(const vo_state* S);
+/* Sec. 2.4: variable time step min(dt, c_dyn / sqrt(rho_max)); 0: constant. */
+void vo_set_cdyn(vo_state* S, double c_dyn);
+double vo_time(const vo_state* S);
+double vo_last_dt(const vo_state* S);
 /* element push under a frozen grid force (a, a', a'' given on the x nodes) */
 void vo_push_frozen(vo_state* S, const double* a, const double* da, const double* d2a,
                     double ext_lo, double ext_hi, int32_t nsteps);

@@ -31,6 +31,7 @@ bool valid(const vm_config* c) {
   if (c->pad < 0 || c->max_hole_rounds < 0) return false;
   if (c->map_windows != 0 && c->map_windows != 1) return false;
   if (!(c->emap_remap >= 0.0) || !isfinite(c->emap_remap)) return false;
+  if (!(c->c_dyn >= 0.0) || !isfinite(c->c_dyn)) return false;
   if (!(c->alpha >= 0.0) || !(c->beta >= 0.0)) return false;
   // 32-bit site indices; element indices fit the 24-bit field of the owner slots
   if ((long long)c->nx * (long long)c->nv >= (1ll << 31) / 2) return false;
@@ -162,6 +163,19 @@ cudaError_t step_remap(vm_solver* s) {
 }  // namespace vm
 
 namespace {
+
+// Largest projected density of s->f, computed and read back (synchronises).
+vm_status rho_max_now(vm_solver* s, double* rho) {
+  vm::DevState* d = s->ds;
+  VM_CUDA_TRY(cudaMemsetAsync(&d->rho_max_bits, 0, sizeof d->rho_max_bits, s->stream));
+  vm::launch_rho_max(s);
+  unsigned long long bits = 0;
+  VM_CUDA_TRY(cudaMemcpyAsync(&bits, &d->rho_max_bits, sizeof bits, cudaMemcpyDeviceToHost, s->stream));
+  vm_status st = vm_sync(s);
+  if (st != VM_OK) return st;
+  memcpy(rho, &bits, 8);
+  return VM_OK;
+}
 
 // E_map of the current influence map, computed and read back (synchronises).
 vm_status emap_now(vm_solver* s, double* e) {
@@ -464,6 +478,8 @@ vm_status vm_set_f(vm_solver* s, const double* f0, int32_t on_device) {
   s->have_f = 1;
   s->nstep = 0;
   s->emap_remaps = 0;
+  s->time = 0.0;
+  s->last_dt = 0.0;
   s->cyc = 0;
   return check_launch(s);
 }
@@ -507,8 +523,23 @@ vm_status vm_step(vm_solver* s, int32_t nsteps) {
   vm::clear_foreign_error();
   if (!s->have_f) return VM_E_STATE;
   for (int32_t it = 0; it < nsteps; it++) {
+    if (s->cfg.c_dyn > 0.0) {
+      // Sec. 2.4: this step's dt from the last reconstructed f
+      double rho = 0.0;
+      vm_status st = rho_max_now(s, &rho);
+      if (st != VM_OK) return st;
+      double dt = s->cfg.dt;
+      if (rho > 0.0) {
+        const double lim = s->cfg.c_dyn / sqrt(rho);
+        if (lim < dt) dt = lim;
+      }
+      s->g.dt = dt;
+      s->g.half_dt = 0.5 * dt;
+    }
     vm::step_transport(s);
     s->nstep++;
+    s->time += s->g.dt;
+    s->last_dt = s->g.dt;
     s->cyc++;
     bool remap = s->cyc >= s->cfg.n_s;
     if (!remap && s->cfg.emap_remap > 0.0) {
@@ -629,6 +660,8 @@ vm_status vm_diagnostics(vm_solver* s, vm_diag* d) {
   memcpy(&e2, &h.emap2_bits, 8);
   d->emap = sqrt(e2);
   d->emap_remaps = s->emap_remaps;
+  d->time = s->time;
+  d->last_dt = s->last_dt;
   return VM_OK;
 }
 

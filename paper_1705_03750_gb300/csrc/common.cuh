@@ -65,6 +65,7 @@ struct DevState {
   unsigned long long det_min_key, det_max_key;
   double sum_ent, sum_l1, sum_l2;   // Casimirs of the last f (Sec. 3.2)
   unsigned long long emap2_bits;     // bits of the largest squared E_map term (>= 0)
+  unsigned long long rho_max_bits;   // bits of the largest positive projected density
 };
 
 // Owner slots of the influence map: (epoch << 24) | element index.  A slot
@@ -157,6 +158,8 @@ struct vm_solver {
   int32_t have_f;
   int64_t nstep;
   int64_t emap_remaps;      // remaps forced by cfg.emap_remap since vm_set_f
+  double time;              // sum of the steps since vm_set_f
+  double last_dt;
   int32_t cyc;
   int64_t launches;
   // optional per-launch timing: event pairs around each launch
@@ -192,6 +195,8 @@ void launch_scan_force_raw(const Grid& g, const double* M, double* a, double* da
 void launch_diagnostics(vm_solver* s);
 // E_map of the last influence map (Sec. 2.3.2) into ds->emap2_bits (zeroed by the caller)
 void launch_emap(vm_solver* s);
+// largest projected density sum_j f(i, j) dv of s->f into ds->rho_max_bits (zeroed by the caller)
+void launch_rho_max(vm_solver* s);
 // map.cu
 bool map_prepare(const Grid& g);
 void launch_map(vm_solver* s);

@@ -313,6 +313,26 @@ __global__ void k_diag(Grid g, const R* __restrict__ f, const double* __restrict
   }
 }
 
+// Largest projected density rho(x_i) = (sum_j f(i, j)) dv of f (Sec. 2.4's
+// time-step constraint): a block per x row, the positive maxima into
+// ds->rho_max_bits (bits of a non-negative double order as the values do).
+template <typename R>
+__global__ void __launch_bounds__(256) k_rho_max(Grid g, const R* __restrict__ f, DevState* ds) {
+  __shared__ double sh[8];
+  const int i = blockIdx.x;
+  double acc = 0.0;
+  for (int j = threadIdx.x; j < g.nv; j += blockDim.x) acc += (double)f[(size_t)i * g.nv + j];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += sh[w];
+    const double rho = dmul(t, g.dv);
+    if (rho > 0.0) atomicMax(&ds->rho_max_bits, (unsigned long long)__double_as_longlong(rho));
+  }
+}
+
 inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // Element kernels are FP64-bound (two FP64 lanes per SM per clock): small
@@ -354,6 +374,14 @@ void launch_scan_force_raw(const Grid& g, const double* M, double* a, double* da
                            cudaStream_t stream) {
   k_scan_force<<<1, SCAN_T, 0, stream>>>(g, M, a, ds);
   k_force_diff<<<blocks_for(g.nx, 128), 128, 0, stream>>>(g, a, da, d2a, ds);
+}
+
+void launch_rho_max(vm_solver* s) {
+  if (s->fp32)
+    k_rho_max<float><<<s->g.nx, 256, 0, s->stream>>>(s->g, (const float*)s->f, s->ds);
+  else
+    k_rho_max<double><<<s->g.nx, 256, 0, s->stream>>>(s->g, (const double*)s->f, s->ds);
+  s->launches++;
 }
 
 void launch_diagnostics(vm_solver* s) {

@@ -44,7 +44,7 @@ class VmConfig(C.Structure):
         ("elem_stride", C.c_int32), ("dt", C.c_double), ("n_s", C.c_int32), ("G", C.c_double),
         ("precision", C.c_int32), ("alpha", C.c_double), ("beta", C.c_double),
         ("pad", C.c_int32), ("literal_fd", C.c_int32), ("max_hole_rounds", C.c_int32),
-        ("map_windows", C.c_int32), ("emap_remap", C.c_double),
+        ("map_windows", C.c_int32), ("emap_remap", C.c_double), ("c_dyn", C.c_double),
     ]
 
 
@@ -54,7 +54,8 @@ class VmDiag(C.Structure):
                 ("holes", C.c_int32), ("hole_rounds", C.c_int32), ("overflow_elements", C.c_int32),
                 ("tier1_more", C.c_int32), ("last_tier_elements", C.c_int32),
                 ("exact_tests", C.c_int32), ("bad_where", C.c_int32), ("entropy", C.c_double),
-                ("l1", C.c_double), ("l2", C.c_double), ("emap", C.c_double), ("emap_remaps", C.c_int64)]
+                ("l1", C.c_double), ("l2", C.c_double), ("emap", C.c_double), ("emap_remaps", C.c_int64),
+                ("time", C.c_double), ("last_dt", C.c_double)]
 
 
 class VmKernelStat(C.Structure):
@@ -152,6 +153,7 @@ class Config:
     max_hole_rounds: int = 0
     map_windows: int = 0
     emap_remap: float = 0.0
+    c_dyn: float = 0.0
 
     @classmethod
     def from_run(cls, rc, precision: int = VM_FP64) -> "Config":
@@ -160,7 +162,7 @@ class Config:
     def c(self) -> VmConfig:
         return VmConfig(self.nx, self.nv, self.x_lo, self.x_hi, self.v_lo, self.v_hi, self.s, self.dt,
                         self.n_s, self.G, self.precision, self.alpha, self.beta, self.pad, self.literal_fd,
-                        self.max_hole_rounds, self.map_windows, self.emap_remap)
+                        self.max_hole_rounds, self.map_windows, self.emap_remap, self.c_dyn)
 
 
 def workspace_bytes(cfg: Config) -> int:

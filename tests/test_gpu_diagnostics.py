@@ -139,3 +139,38 @@ def test_gaussian_ic_first_steps_match_oracle(prec):
     dg, do = s.diagnostics(), o.diagnostics()
     assert dg["mass"] == pytest.approx(do["mass"], rel=1e-12 if prec == "fp64" else 1e-6)
     assert dg["entropy"] == pytest.approx(do["entropy"], rel=1e-9 if prec == "fp64" else 1e-5)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_variable_time_step_matches_oracle(prec):
+    # Sec. 2.4: dt = min(dt, C_dyn / sqrt(rho_max)) each step, through a remap
+    rc = I.SPITZER_128
+    cfg = V.Config.from_run(rc, PREC[prec])
+    cfg.c_dyn = 0.005
+    s = V.Solver(cfg)
+    o = oracle_of(rc)
+    f0 = I.initial_f(rc)
+    s.set_f(f0)
+    o.set_f(f0)
+    o.set_cdyn(0.005)
+    s.step(25)
+    o.step(25)
+    d = s.diagnostics()
+    tol_dt = 1e-12 if prec == "fp64" else 1e-6
+    assert d["last_dt"] == pytest.approx(o.last_dt(), rel=tol_dt)
+    assert d["time"] == pytest.approx(o.time(), rel=tol_dt)
+    assert d["last_dt"] < rc.dt  # the density constraint is active
+    fo = o.last_f()
+    err = np.abs(s.read_f() - fo).max() / np.abs(fo).max()
+    assert err <= (1e-9 if prec == "fp64" else 1e-5), err
+
+
+def test_batch_refuses_variable_time_step():
+    rc = I.HALOS_4096.with_(nx=64, nv=64, s=4, n_s=4)
+    cfg = V.Config.from_run(rc, V.VM_FP32_MIXED)
+    cfg.c_dyn = 0.01
+    s = V.Solver(cfg)
+    s.set_f(I.initial_f(rc))
+    with pytest.raises(V.VlametError) as e:
+        V.Batch([s], nstreams=1)
+    assert e.value.status == 1

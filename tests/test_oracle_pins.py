@@ -712,3 +712,29 @@ def test_gaussian_initial_condition_mass_and_cut():
     r_cut = p["R"] + p["eta"] * math.atanh(0.5)
     assert I.gaussian_ic(p["R"], 0.0, **p) == pytest.approx(I.gaussian_ic(p["R"] - 1e-12, 0.0, **p), rel=1e-9)
     assert I.gaussian_ic(r_cut + 1e-9, 0.0, **p) == 0.0 and I.gaussian_ic(r_cut - 1e-3, 0.0, **p) > 0.0
+
+
+def test_variable_time_step_follows_the_density_constraint():
+    """Sec. 2.4: Delta t = min(dt, C_dyn / sqrt(rho_max)).  For the isothermal
+    sheet rho(x) = rho_0 sech^2(x / x_0), rho_0 = 2 pi (M = 1, G = 1, sigma =
+    1/2); the grid has no node at x = 0, so rho_max is rho at x = +-dx/2.  A
+    large C_dyn leaves the constant step."""
+    rc = I.SPITZER_128
+    o = O.Oracle(rc.nx, rc.nv, rc.x_lo, rc.x_hi, rc.v_lo, rc.v_hi, rc.s, rc.dt, rc.n_s, rc.G)
+    o.set_f(I.initial_f(rc))
+    c = 0.005
+    o.set_cdyn(c)
+    o.step(1)
+    x0 = 0.25 / math.pi
+    rho_max = 2 * math.pi / math.cosh(0.5 * rc.dx / x0) ** 2
+    assert o.last_dt() == pytest.approx(c / math.sqrt(rho_max), rel=1e-4)
+    assert o.time() == pytest.approx(o.last_dt(), rel=1e-15)
+    big = O.Oracle(rc.nx, rc.nv, rc.x_lo, rc.x_hi, rc.v_lo, rc.v_hi, rc.s, rc.dt, rc.n_s, rc.G)
+    plain = O.Oracle(rc.nx, rc.nv, rc.x_lo, rc.x_hi, rc.v_lo, rc.v_hi, rc.s, rc.dt, rc.n_s, rc.G)
+    for z in (big, plain):
+        z.set_f(I.initial_f(rc))
+    big.set_cdyn(1e6)
+    big.step(3)
+    plain.step(3)
+    assert big.last_dt() == rc.dt and big.time() == pytest.approx(3 * rc.dt)
+    assert np.array_equal(big.elements(), plain.elements())
