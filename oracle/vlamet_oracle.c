@@ -30,9 +30,11 @@
  *   everywhere (no cut at the box edge); force factor 2*pi*G.
  *
  * Parity status: every function here is pinned by a test against a closed
- * form, an invariant or brute force, except the smooth map Q_r as a whole
- * (its pieces W, ranges and the Taylor map are pinned; the blend itself is
- * checked only through invariants: Q_r = Q when all proposals agree).
+ * form, an invariant or brute force.  The smooth map Q_r and E_map are
+ * pinned on hand-built states of displaced isotropic elements, whose
+ * blended positions and mismatches are simple fractions worked out by hand,
+ * and Q_r's continuity across ownership boundaries is checked under grid
+ * refinement for a curved flow.
  */
 #include "vlamet_oracle.h"
 
@@ -499,6 +501,7 @@ int32_t vo_set_f(vo_state* S, const double* f0) {
   reset_elements(S);
   S->nstep = 0;
   S->time = 0.0;
+  S->last_dt = 0.0;
   S->have_f = 1;
   return VO_OK;
 }
