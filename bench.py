@@ -217,6 +217,72 @@ def replica_rate(world: int, sites: int, steps: int, ms_max: float) -> float:
 # native arm
 # ---------------------------------------------------------------------------
 
+def e2e_run(V, rc, prec, f0, args, dev, barrier, max_ranks, world):
+    """End-to-end rate through the C ABI with host buffers.  The upload of
+    f0 (vm_set_f from pinned host memory) and the K timed steps, each
+    followed by vm_density_force into pinned host buffers, are timed on the
+    host clock; the W warm-up steps between them are not, so the timed steps
+    are the same step indices (and remaps) as the device-timed region."""
+    import torch
+    host_f0 = torch.from_numpy(f0).pin_memory()
+    outs = {k: torch.empty(rc.nx, dtype=torch.float64).pin_memory() for k in ("M", "a", "da", "d2a")}
+    se = V.Solver(V.Config.from_run(rc, prec))
+    se.sync()
+
+    def ptr(t):
+        return ctypes.c_void_p(t.data_ptr())
+    barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    V._check(se.L.vm_set_f(se.h, ptr(host_f0), 0), "vm_set_f")
+    V._check(se.L.vm_sync(se.h), "vm_sync")
+    t_up = time.perf_counter() - t0
+    V._check(se.L.vm_step(se.h, args.warmup), "vm_step")
+    V._check(se.L.vm_sync(se.h), "vm_sync")
+    t1 = time.perf_counter()
+    for _ in range(args.steps):
+        V._check(se.L.vm_step(se.h, 1), "vm_step")
+        V._check(se.L.vm_density_force(se.h, ptr(outs["M"]), ptr(outs["a"]), ptr(outs["da"]),
+                                       ptr(outs["d2a"]), 0), "vm_density_force")
+    torch.cuda.synchronize(dev)
+    t_steps = time.perf_counter() - t1
+    te = max_ranks(t_up + t_steps)
+    barrier()
+    del se
+    return {"value": world * rc.nx * rc.nv * args.steps / te, "unit": "cell-updates/s",
+            "h2d_bytes_per_step": f0.nbytes / args.steps, "d2h_bytes_per_step": 4 * rc.nx * 8,
+            "upload_ms": t_up * 1e3, "steps_ms": t_steps * 1e3,
+            "what": f"vm_set_f from pinned host f0 (timed), {args.warmup} untimed steps, then steps "
+                    f"{args.warmup}..{args.warmup + args.steps - 1} each with vm_density_force to host (timed)"}
+
+
+def whole_run(V, rc, prec, f0_dev, steps, dev):
+    """All `steps` steps of one solve from vm_set_f (remaps included), timed
+    with CUDA events on the solver's stream, plus the rate of the last
+    tenth of the run (the map's cost grows as the flow shears and mass
+    leaves the box)."""
+    import torch
+    s = V.Solver(V.Config.from_run(rc, prec))
+    s.set_f(f0_dev)
+    s.sync()
+    late = max(1, steps // 10)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record(s.stream)
+    s.step(steps - late)
+    ev[1].record(s.stream)
+    s.step(late)
+    ev[2].record(s.stream)
+    torch.cuda.synchronize(dev)
+    s.sync()
+    ms = ev[0].elapsed_time(ev[2])
+    ms_late = ev[1].elapsed_time(ev[2])
+    cells = rc.nx * rc.nv
+    del s
+    return {"steps": steps, "remaps": steps // rc.n_s, "ms": ms, "value": cells * steps / (ms / 1e3),
+            "late_steps": late, "late_value": cells * late / (ms_late / 1e3), "unit": "cell-updates/s",
+            "what": f"steps 0..{steps - 1} from vm_set_f, CUDA events on the solver's stream"}
+
+
 def run_native(args, rank: int, world: int, dist):
     import torch
     from paper_1705_03750_gb300 import vlamet as V
@@ -283,34 +349,19 @@ def run_native(args, rank: int, world: int, dist):
         stats = s.profile_read()
         s.profile(False)
         s.sync()
-        # end to end through the C ABI with host buffers: a new solve from a
-        # pinned host f0, then every step the density and force read back
+        # end to end through the C ABI with host buffers, over the same step
+        # indices as the device-timed region: a new solve uploads f0 from
+        # pinned host memory (timed), runs the same untimed warm-up, then
+        # every timed step reads the density and force back to the host
         e2e = None
         if not args.no_e2e:
-            host_f0 = torch.from_numpy(f0).pin_memory()
-            outs = {k: torch.empty(rc.nx, dtype=torch.float64).pin_memory() for k in ("M", "a", "da", "d2a")}
-            se = V.Solver(V.Config.from_run(rc, prec))
-            se.sync()
-            barrier()
-            torch.cuda.synchronize(dev)
-            t0 = time.perf_counter()
-            def ptr(t):
-                return ctypes.c_void_p(t.data_ptr())
-
-            V._check(se.L.vm_set_f(se.h, ptr(host_f0), 0), "vm_set_f")
-            for _ in range(args.steps):
-                V._check(se.L.vm_step(se.h, 1), "vm_step")
-                V._check(se.L.vm_density_force(se.h, ptr(outs["M"]), ptr(outs["a"]), ptr(outs["da"]),
-                                               ptr(outs["d2a"]), 0), "vm_density_force")
-            torch.cuda.synchronize(dev)
-            te = max_ranks(time.perf_counter() - t0)
-            barrier()
-            e2e = {"value": world * rc.nx * rc.nv * args.steps / te, "unit": "cell-updates/s",
-                   "h2d_bytes_per_step": f0.nbytes / args.steps, "d2h_bytes_per_step": 4 * rc.nx * 8,
-                   "what": "vm_set_f from pinned host f0, then per step vm_step + vm_density_force to host"}
-            del se
+            e2e = e2e_run(V, rc, prec, f0, args, dev, barrier, max_ranks, world)
+        # the whole run of the configuration (C2: 1000 steps), device-timed
+        whole = None
+        if args.whole_run > 0 and not (name == "fp64" and args.whole_run_fp32_only):
+            whole = whole_run(V, rc, prec, f0_dev, args.whole_run, dev)
         out[name] = {"ms": ms, "launches": launches, "stats": stats, "clocks": clocks.summary(), "e2e": e2e,
-                     "ne": s.ne, "fp32": prec == V.VM_FP32_MIXED}
+                     "ne": s.ne, "fp32": prec == V.VM_FP32_MIXED, "whole": whole}
         del s
         torch.cuda.synchronize(dev)
 
@@ -360,6 +411,7 @@ def run_native(args, rank: int, world: int, dist):
                    "l2": "working set > L2 (129 MB): no flush", "parallelism": f"replicas x{world}"},
         "clocks": head["clocks"],
         "e2e": head["e2e"],
+        "whole_run": head["whole"],
         "gpu_launches": head["launches"],
         "roofline": roof,
         "kernels": {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in sorted(stats.items(), key=lambda kv: -kv[1][1])},
@@ -368,10 +420,12 @@ def run_native(args, rank: int, world: int, dist):
         f64 = out["fp64"]
         line["fp64_path"] = {"value": replica_rate(world, cells, K, f64["ms"]), "ms_per_step": f64["ms"] / K,
                              "gpu_launches": f64["launches"], "clocks": f64["clocks"],
-                             "e2e": f64["e2e"],
+                             "e2e": f64["e2e"], "whole_run": f64["whole"],
                              "top_kernels": {k: round(v[1], 3) for k, v in sorted(f64["stats"].items(), key=lambda kv: -kv[1][1])[:4]}}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(rc, f0)
+    if world == 1 and not args.no_serve:
+        line["serving"] = serve_sample(args)
     return line
 
 
@@ -537,6 +591,42 @@ def run_batch(args):
     return res
 
 
+def serve_sample(args) -> dict:
+    """A reduced serving run for the headline line: 24 seeded halo requests
+    (sides 256-1024, multiples of 32; 100-400 steps; FP32-mixed; a 150 GB
+    budget), all at t = 0 for the saturated throughput, then open-loop
+    Poisson arrivals at 0.5 and 0.9 of it; p50/p99 latency from arrival to
+    the result on the host, and aggregate cell-updates/s."""
+    import torch
+    from paper_1705_03750_gb300.serve import GpuBackend, Server, poisson_requests
+
+    def make(i, nx, nv):
+        return I.HALOS_4096.with_(name=f"req{i}", nx=nx, nv=nv, seed=10_000 + i)
+    kw = dict(seed=args.seed, make_config=make, sides=(256, 1024), steps=(100, 400))
+    ics = {}
+
+    def ic(rc):
+        key = (rc.name, rc.nx, rc.nv)
+        if key not in ics:
+            ics[key] = I.initial_f(rc)
+        return ics[key]
+
+    def one(rate):
+        srv = Server(GpuBackend(), budget_bytes=150 << 30, max_active=32, steps_per_tick=5, ic_fn=ic)
+        rep = srv.run(poisson_requests(24, rate=rate, **kw))
+        torch.cuda.synchronize()
+        keep = ("requests", "failed", "wall_s", "cell_updates_per_s", "p50_latency_s", "p99_latency_s",
+                "peak_active")
+        return {k: rep[k] for k in keep}
+    sat = one(0.0)
+    rate = sat["requests"] / sat["wall_s"]
+    out = {"workload": "serve-halos-256..1024 x24, 100-400 steps", "saturation": {**sat, "requests_per_s": rate},
+           "rates": []}
+    for frac in (0.5, 0.9):
+        out["rates"].append({"fraction_of_saturation": frac, "rate_per_s": frac * rate, **one(frac * rate)})
+    return out
+
+
 def run_serve(args):
     """Open-loop Poisson arrivals of seeded halo solves on a device-memory
     budget; p50/p99 latency and throughput at fractions of saturation."""
@@ -587,6 +677,10 @@ def main():
     ap.add_argument("--precision", default="both", choices=["both", "fp32", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the reduced serving sample")
+    ap.add_argument("--whole-run", type=int, default=1000,
+                    help="steps of the whole-run rate (the configuration's 1000; 0: skip)")
+    ap.add_argument("--whole-run-fp32-only", action="store_true")
     ap.add_argument("--ref-cap", type=int, default=20)
     ap.add_argument("--workload", default="halos4096", choices=["halos4096", "precision8192", "batch", "serve"])
     ap.add_argument("--batch", type=int, default=512)

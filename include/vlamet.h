@@ -172,7 +172,10 @@ vm_status vm_remap(vm_solver* s);
 
 /* Pixel masses M(i) = sum_j f(i,j) dx dv, and a, a', a'' on the x nodes,
  * from the last reconstruction ([nx] doubles each; any pointer may be
- * NULL).  Synchronises when on_device == 0. */
+ * NULL).  a(i) = 2 pi G (M_tot - M_left(i) - M_left(i-1)) (Sec. 2.5) with the
+ * prefix sums M_left exact (128-bit fixed point at a common scale of 2^-112
+ * max|M|): the bracket is correctly rounded once, then multiplied by 2 pi G.
+ * Synchronises when on_device == 0. */
 vm_status vm_density_force(vm_solver* s, double* M, double* a, double* da, double* d2a,
                            int32_t on_device);
 
@@ -253,6 +256,14 @@ vm_status vm_batch_step(vm_batch* b, int32_t nsteps);
 int64_t vm_batch_launches_per_step(const vm_batch* b, int32_t with_remap);
 void vm_batch_destroy(vm_batch* b);
 
+/* Measured FP64 arithmetic rate of the current device, in FLOP/s (2 per
+ * fused multiply-add): one launch of eight independent FMA chains of
+ * `iters` rounds per thread over 8 blocks of 256 threads per SM, timed with
+ * CUDA events on cuda_stream (synchronises).  The denominator of the FP64
+ * path's arithmetic roofline; not part of the method.  VM_E_INVALID_ARG for
+ * iters < 1 or a NULL result pointer. */
+vm_status vm_measure_fp64_peak(int32_t iters, void* cuda_stream, double* flops_per_s);
+
 /* Pixel masses and force from a caller's f, allocating nothing.
  *
  * The paper has no counterpart to this call; it exists for callers that
@@ -261,7 +272,8 @@ void vm_batch_destroy(vm_batch* b);
  * device-wide synchronisation cudaMalloc and cudaFree can cause).  It
  * computes what vm_reconstruct + vm_density_force produce for an f given on
  * the device: M(i) = sum_j f(i,j) dx dv, then a, a', a'' on the x nodes by
- * the compensated mass scan (same grid conventions as vm_config).
+ * the solver's error-free mass scan (the prefix sums of M carried exactly
+ * in 128-bit fixed point; same grid conventions as vm_config).
  *
  * f: device pointer, [nx][nv], v fastest, dtype a vm_dtype.  M_out (may be
  * NULL), a, da, d2a: device pointers to [nx] doubles.  cuda_stream: the

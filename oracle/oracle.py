@@ -100,6 +100,8 @@ def lib(openmp: bool = True) -> C.CDLL:
             "vo_casimirs": (None, [C.c_void_p, _D, _D, _D]),
             "vo_emap": (C.c_double, [C.c_void_p]),
             "vo_set_cdyn": (None, [C.c_void_p, C.c_double]),
+            "vo_set_fth": (None, [C.c_void_p, C.c_double]),
+            "vo_domain": (None, [C.c_void_p, _I32, _I32]),
             "vo_time": (C.c_double, [C.c_void_p]),
             "vo_last_dt": (C.c_double, [C.c_void_p]),
             "vo_push_frozen": (None, [C.c_void_p, _D, _D, _D, C.c_double, C.c_double, C.c_int32]),
@@ -319,6 +321,20 @@ class Oracle:
     def set_cdyn(self, c_dyn: float) -> None:
         """Variable time step min(dt, c_dyn / sqrt(rho_max)) (0: constant)."""
         self.L.vo_set_cdyn(self.h, float(c_dyn))
+
+    def set_fth(self, f_th: float) -> None:
+        """Adaptive computing domain (Sec. 2.2.1, eq. constrf; Sec. 2.3) with
+        threshold f_th (0: the fixed box); takes effect at the next set_f or
+        remap."""
+        self.L.vo_set_fth(self.h, float(f_th))
+
+    def domain(self) -> dict:
+        """Existing lattice range (klo, khi, llo, lhi) and the last map's site
+        rectangle (i_lo, i_hi, j_lo, j_hi)."""
+        a = np.zeros(4, dtype=np.int32)
+        r = np.zeros(4, dtype=np.int32)
+        self.L.vo_domain(self.h, _ip(a), _ip(r))
+        return {"lattice": tuple(int(x) for x in a), "rect": tuple(int(x) for x in r)}
 
     def time(self) -> float:
         return self.L.vo_time(self.h)

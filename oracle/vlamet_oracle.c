@@ -73,6 +73,14 @@ struct vo_state {
   double c_dyn;  /* > 0: variable time step (Sec. 2.4), Delta t = min(dt, c_dyn / sqrt(rho_max)) */
   double time;   /* sum of the steps taken since vo_set_f */
   double last_dt;
+  /* adaptive computing domain (Sec. 2.2.1, eq. constrf; Sec. 2.3): f_th > 0
+   * restricts f_ini to the rectangle of nodes where |f_ini| > f_th; elements
+   * exist on the lattice rows klo..khi and columns llo..lhi covering it plus
+   * one extra layer; each map's sites are those of the rectangle spanned by
+   * the existing elements' positions (rect: i_lo, i_hi, j_lo, j_hi) */
+  double f_th;
+  int32_t klo, khi, llo, lhi;
+  int32_t rect[4];
   /* percolation scratch */
   int32_t* stamp;
   int32_t* queue;
@@ -408,6 +416,109 @@ static double lattice_qv(const vo_state* S, int32_t l) {
   return S->cv + (double)(l - S->Kv - 1) * S->dvm;
 }
 
+/* Does element (k, l) exist (is it on the part of the lattice that covers
+ * the computing domain)? */
+static int exists(const vo_state* S, int32_t k, int32_t l) {
+  return k >= S->klo && k <= S->khi && l >= S->llo && l <= S->lhi;
+}
+
+static int64_t floor_div(int64_t a, int64_t b) { /* b > 0 */
+  int64_t q = a / b;
+  return (q * b > a) ? q - 1 : q;
+}
+static int64_t ceil_div(int64_t a, int64_t b) { return -floor_div(-a, b); }
+
+/* Sec. 2.2.1, eq. constrf: the Lagrangian computing domain is the smallest
+ * rectangle of nodes holding every node where |f_ini| > f_th; f_ini is cut
+ * to it, and elements exist on the lattice lines that cover it (the last
+ * lattice line at or before its first node and the first at or after its
+ * last node, in index units (nx-1)/2 + (k-Kx-1) s, exact in integers) plus
+ * one extra layer on every side (Sec. 2.3).  f_th = 0: the whole box and
+ * the whole lattice. */
+static void computing_domain(vo_state* S) {
+  const int32_t nx = S->c.nx, nv = S->c.nv, s = S->c.s;
+  if (!(S->f_th > 0.0)) {
+    S->klo = 0;
+    S->khi = S->Lx - 1;
+    S->llo = 0;
+    S->lhi = S->Lv - 1;
+    return;
+  }
+  int32_t ilo = nx, ihi = -1, jlo = nv, jhi = -1;
+  for (int32_t i = 0; i < nx; i++)
+    for (int32_t j = 0; j < nv; j++)
+      if (fabs(S->fini[(size_t)i * nv + j]) > S->f_th) {
+        if (i < ilo) ilo = i;
+        if (i > ihi) ihi = i;
+        if (j < jlo) jlo = j;
+        if (j > jhi) jhi = j;
+      }
+  for (int32_t i = 0; i < nx; i++)
+    for (int32_t j = 0; j < nv; j++)
+      if (i < ilo || i > ihi || j < jlo || j > jhi) S->fini[(size_t)i * nv + j] = 0.0;
+  if (ihi < 0) { /* nothing above the threshold: no element */
+    S->klo = S->llo = 0;
+    S->khi = S->lhi = -1;
+    return;
+  }
+  int64_t klo = S->Kx + 1 + floor_div(2 * (int64_t)ilo - (nx - 1), 2 * (int64_t)s) - 1;
+  int64_t khi = S->Kx + 1 + ceil_div(2 * (int64_t)ihi - (nx - 1), 2 * (int64_t)s) + 1;
+  int64_t llo = S->Kv + 1 + floor_div(2 * (int64_t)jlo - (nv - 1), 2 * (int64_t)s) - 1;
+  int64_t lhi = S->Kv + 1 + ceil_div(2 * (int64_t)jhi - (nv - 1), 2 * (int64_t)s) + 1;
+  S->klo = (int32_t)(klo < 0 ? 0 : klo);
+  S->khi = (int32_t)(khi > S->Lx - 1 ? S->Lx - 1 : khi);
+  S->llo = (int32_t)(llo < 0 ? 0 : llo);
+  S->lhi = (int32_t)(lhi > S->Lv - 1 ? S->Lv - 1 : lhi);
+}
+
+/* Sec. 2.3: the Eulerian computing domain of a map is the rectangle spanned
+ * by the positions of the existing elements, as grid sites: i from
+ * ceil((min x_m - x_lo)/dx) to floor((max x_m - x_lo)/dx), clamped to the
+ * grid, same along v.  f_th = 0: the whole grid. */
+static void euler_rect(vo_state* S) {
+  const int32_t nx = S->c.nx, nv = S->c.nv;
+  if (!(S->f_th > 0.0)) {
+    S->rect[0] = 0;
+    S->rect[1] = nx - 1;
+    S->rect[2] = 0;
+    S->rect[3] = nv - 1;
+    return;
+  }
+  double xmin = INFINITY, xmax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
+  for (int32_t k = S->klo; k <= S->khi; k++)
+    for (int32_t l = S->llo; l <= S->lhi; l++) {
+      const elem_t* e = &S->el[k * S->Lv + l];
+      if (e->x < xmin) xmin = e->x;
+      if (e->x > xmax) xmax = e->x;
+      if (e->v < vmin) vmin = e->v;
+      if (e->v > vmax) vmax = e->v;
+    }
+  if (!(xmin <= xmax) || !(vmin <= vmax)) {
+    S->rect[0] = S->rect[2] = 0;
+    S->rect[1] = S->rect[3] = -1;
+    return;
+  }
+  double a = ceil((xmin - S->c.x_lo) * S->inv_dx), b = floor((xmax - S->c.x_lo) * S->inv_dx);
+  double c = ceil((vmin - S->c.v_lo) * S->inv_dv), d = floor((vmax - S->c.v_lo) * S->inv_dv);
+  S->rect[0] = (int32_t)(a < 0.0 ? 0.0 : (a > nx ? nx : a));
+  S->rect[1] = (int32_t)(b > nx - 1 ? nx - 1 : (b < -1.0 ? -1.0 : b));
+  S->rect[2] = (int32_t)(c < 0.0 ? 0.0 : (c > nv ? nv : c));
+  S->rect[3] = (int32_t)(d > nv - 1 ? nv - 1 : (d < -1.0 ? -1.0 : d));
+}
+
+static int in_rect(const vo_state* S, int64_t i, int64_t j) {
+  return i >= S->rect[0] && i <= S->rect[1] && j >= S->rect[2] && j <= S->rect[3];
+}
+
+void vo_set_fth(vo_state* S, double f_th) { S->f_th = f_th; }
+void vo_domain(const vo_state* S, int32_t* act4, int32_t* rect4) {
+  act4[0] = S->klo;
+  act4[1] = S->khi;
+  act4[2] = S->llo;
+  act4[3] = S->lhi;
+  memcpy(rect4, S->rect, sizeof S->rect);
+}
+
 vo_state* vo_create(const vo_config* c) {
   if (c->nx < 4 || c->nv < 4 || c->s < 1 || c->pad < 0 || !(c->x_hi > c->x_lo) ||
       !(c->v_hi > c->v_lo) || c->n_s < 1)
@@ -448,6 +559,12 @@ vo_state* vo_create(const vo_config* c) {
   S->da = (double*)calloc((size_t)c->nx, sizeof(double));
   S->d2a = (double*)calloc((size_t)c->nx, sizeof(double));
   for (size_t p = 0; p < n; p++) S->map[p] = -1;
+  S->klo = S->llo = 0;
+  S->khi = S->Lx - 1;
+  S->lhi = S->Lv - 1;
+  S->rect[0] = S->rect[2] = 0;
+  S->rect[1] = c->nx - 1;
+  S->rect[3] = c->nv - 1;
   return S;
 }
 
@@ -496,7 +613,8 @@ static void reset_elements(vo_state* S) {
 int32_t vo_set_f(vo_state* S, const double* f0) {
   size_t n = (size_t)S->c.nx * S->c.nv;
   memcpy(S->fini, f0, n * sizeof(double));
-  memcpy(S->f, f0, n * sizeof(double));
+  computing_domain(S);
+  memcpy(S->f, S->fini, n * sizeof(double));
   vo_spline_solve_2d(S->c.nx, S->c.nv, S->fini, S->eta);
   reset_elements(S);
   S->nstep = 0;
@@ -614,7 +732,7 @@ static int passes(const vo_state* S, int32_t m, double Px, double Pv, double* d2
   int32_t k = m / S->Lv, l = m % S->Lv;
   for (int32_t q = 0; q < n; q++) {
     int32_t kk = k + ab[2 * q], ll = l + ab[2 * q + 1];
-    if (kk < 0 || kk >= S->Lx || ll < 0 || ll >= S->Lv) continue;
+    if (kk < 0 || kk >= S->Lx || ll < 0 || ll >= S->Lv || !exists(S, kk, ll)) continue;
     double d2n = dist2(S, kk * S->Lv + ll, Px, Pv, NULL, NULL);
     if (d2n < d2) return 0;
   }
@@ -625,7 +743,7 @@ static int passes(const vo_state* S, int32_t m, double Px, double Pv, double* d2
  * the smaller element index.  d^2 >= 0 is compared through its IEEE bit
  * pattern, which orders non-negative doubles numerically (NaN last). */
 static void claim(vo_state* S, int64_t i, int64_t j, int32_t m, double d2) {
-  if (i < 0 || j < 0 || i >= S->c.nx || j >= S->c.nv) return;
+  if (i < 0 || j < 0 || i >= S->c.nx || j >= S->c.nv || !in_rect(S, i, j)) return;
   size_t p = (size_t)i * S->c.nv + (size_t)j;
   uint64_t key = dbits(d2);
   if (S->map[p] < 0) {
@@ -651,6 +769,7 @@ static int32_t percolate(vo_state* S) {
     int32_t* bb = S->bbox + 4 * (size_t)m;
     bb[0] = bb[2] = 1;
     bb[1] = bb[3] = 0;
+    if (!exists(S, m / S->Lv, m % S->Lv)) continue;
     /* start from the grid site nearest to P_m */
     double us = (S->el[m].x - S->c.x_lo) * S->inv_dx;
     double ws = (S->el[m].v - S->c.v_lo) * S->inv_dv;
@@ -692,7 +811,7 @@ static int32_t percolate(vo_state* S) {
    * previous round, the one with the smallest d at the hole (then the
    * smaller index). */
   int64_t holes = 0;
-  for (size_t p = 0; p < n; p++) holes += (S->map[p] < 0);
+  for (size_t p = 0; p < n; p++) holes += (S->map[p] < 0 && in_rect(S, (int64_t)(p / nv), (int64_t)(p % nv)));
   S->stat_holes = holes;
   int32_t rounds = 0;
   while (holes > 0) {
@@ -705,7 +824,7 @@ static int32_t percolate(vo_state* S) {
     for (int32_t i = 0; i < nx; i++)
       for (int32_t j = 0; j < nv; j++) {
         size_t p = (size_t)i * nv + j;
-        if (S->prevmap[p] >= 0) continue;
+        if (S->prevmap[p] >= 0 || !in_rect(S, i, j)) continue;
         int32_t best = -1;
         uint64_t bestk = 0;
         static const int di[4] = {-1, 1, 0, 0}, dj[4] = {0, 0, -1, 1};
@@ -723,7 +842,7 @@ static int32_t percolate(vo_state* S) {
         S->map[p] = best;
       }
     holes = 0;
-    for (size_t p = 0; p < n; p++) holes += (S->map[p] < 0);
+    for (size_t p = 0; p < n; p++) holes += (S->map[p] < 0 && in_rect(S, (int64_t)(p / nv), (int64_t)(p % nv)));
     rounds++;
   }
   S->stat_rounds = rounds;
@@ -732,6 +851,7 @@ static int32_t percolate(vo_state* S) {
 
 int32_t vo_compute_map(vo_state* S, int32_t* map_out) {
   compute_taylor(S);
+  euler_rect(S);
   int32_t st = percolate(S);
   if (map_out) memcpy(map_out, S->map, sizeof(int32_t) * (size_t)S->c.nx * S->c.nv);
   return st;
@@ -875,7 +995,7 @@ static void blended_q(const vo_state* S, int32_t m, double Px, double Pv, double
   double nx_ = 0.0, nv_ = 0.0, den = 0.0;
   for (int32_t q = 0; q < n; q++) {
     int32_t kk = k + ab[2 * q], ll = l + ab[2 * q + 1];
-    if (kk < 0 || kk >= S->Lx || ll < 0 || ll >= S->Lv) continue;
+    if (kk < 0 || kk >= S->Lx || ll < 0 || ll >= S->Lv || !exists(S, kk, ll)) continue;
     int32_t mm = kk * S->Lv + ll;
     double dqx, dqv;
     const taylor_t* t = &S->tay[mm];
@@ -932,6 +1052,7 @@ int32_t vo_remap(vo_state* S) {
   int32_t st = vo_remap_resample(S, fnew, NULL);
   memcpy(S->fini, fnew, n * sizeof(double));
   free(fnew);
+  computing_domain(S);
   vo_spline_solve_2d(S->c.nx, S->c.nv, S->fini, S->eta);
   reset_elements(S);
   return st;
@@ -1012,6 +1133,7 @@ void vo_diagnostics(const vo_state* S, double* mass, double* energy, double* dmi
   *energy = ek + ep;
   double lo = INFINITY, hi = -INFINITY;
   for (int32_t m = 0; m < S->ne; m++) {
+    if (!exists(S, m / S->Lv, m % S->Lv)) continue;
     const elem_t* e = &S->el[m];
     double d = e->Txx * e->Tvv - e->Txv * e->Tvx;
     if (d < lo) lo = d;
@@ -1060,7 +1182,7 @@ double vo_emap(const vo_state* S) {
       const int32_t k = m / S->Lv, l = m % S->Lv;
       for (int32_t q = 0; q < nn; q++) {
         const int32_t kk = k + ab[2 * q], ll = l + ab[2 * q + 1];
-        if (kk < 0 || kk >= S->Lx || ll < 0 || ll >= S->Lv) continue;
+        if (kk < 0 || kk >= S->Lx || ll < 0 || ll >= S->Lv || !exists(S, kk, ll)) continue;
         double xn, zn;
         dist2(S, kk * S->Lv + ll, Px, Pv, &xn, &zn);
         const double mx = ((double)ab[2 * q] + xn) - xi, mv = ((double)ab[2 * q + 1] + zn) - ze;

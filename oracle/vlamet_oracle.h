@@ -91,6 +91,12 @@ void vo_casimirs(const vo_state* S, double* entropy, double* l1, double* l2);
 double vo_emap(const vo_state* S);
 /* Sec. 2.4: variable time step min(dt, c_dyn / sqrt(rho_max)); 0: constant. */
 void vo_set_cdyn(vo_state* S, double c_dyn);
+/* Sec. 2.2.1 eq. constrf and Sec. 2.3: adaptive computing domain with
+ * threshold f_th (0: the fixed box); takes effect at the next vo_set_f or
+ * remap.  vo_domain: existing lattice rows/columns (klo, khi, llo, lhi) and
+ * the last map's site rectangle (i_lo, i_hi, j_lo, j_hi). */
+void vo_set_fth(vo_state* S, double f_th);
+void vo_domain(const vo_state* S, int32_t* act4, int32_t* rect4);
 double vo_time(const vo_state* S);
 double vo_last_dt(const vo_state* S);
 /* element push under a frozen grid force (a, a', a'' given on the x nodes) */

@@ -678,7 +678,7 @@ const char* vm_cuda_error_name(int32_t code) { return cudaGetErrorName((cudaErro
 namespace {
 
 constexpr char kCkMagic[8] = {'V', 'L', 'M', 'T', 'C', 'K', 'P', 'T'};
-constexpr uint32_t kCkVersion = 1;
+constexpr uint32_t kCkVersion = 2;
 
 struct CkHeader {
   char magic[8];
@@ -687,6 +687,8 @@ struct CkHeader {
   int64_t nstep;
   uint64_t sreal;
   double x_lo, x_hi, v_lo, v_hi, dt, G, alpha, beta;
+  double time, last_dt;  // Sec. 2.4: elapsed time and the last step (variable time steps)
+  int64_t emap_remaps;
 };
 
 CkHeader ck_header(const vm_solver* s) {
@@ -711,6 +713,9 @@ CkHeader ck_header(const vm_solver* s) {
   h.G = s->cfg.G;
   h.alpha = s->g.alpha;
   h.beta = s->g.beta;
+  h.time = s->time;
+  h.last_dt = s->last_dt;
+  h.emap_remaps = s->emap_remaps;
   return h;
 }
 
@@ -800,5 +805,8 @@ vm_status vm_load(vm_solver* s, const char* path) {
   s->have_f = 1;
   s->nstep = h.nstep;
   s->cyc = h.cyc;
+  s->time = h.time;
+  s->last_dt = h.last_dt;
+  s->emap_remaps = h.emap_remaps;
   return VM_OK;
 }

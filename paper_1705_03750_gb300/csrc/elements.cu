@@ -193,52 +193,157 @@ __global__ void k_reset(Grid g, double* __restrict__ el) {
 
 constexpr int SCAN_T = 256;
 
-// Mass scan and force (Sec. 2.5, eq. of a(i)): one block.  FP64 runs at two
-// lanes per SM per clock on this GPU, so the scan is work-efficient: each
-// thread sums a contiguous chunk of pixels, the chunk totals are scanned
-// across the block, and each thread then walks its chunk once.  a(i) takes
-// the same per-pixel expression as the definition, A ((M_tot - left) -
-// left_prev); only the association of the running sums differs (a tree
-// over chunks instead of one left-to-right sum), which moves them by a few
-// units in the last place of M_tot at most.
+// ---- error-free mass prefix (Sec. 2.5, eq. of a(i)) ----
+//
+// The pixel masses are summed in 128-bit fixed point: with E the binary
+// exponent of max|M| (2^E <= max|M| < 2^(E+1)), every M(i) is scaled by
+// 2^(111-E) (exact) and rounded to an integer.  A mass within 2^-59 of the
+// largest is therefore converted without any error, a smaller one to
+// 2^(E-111) absolute, and the sums of up to 2^15 such integers stay below
+// 2^127.  Integer addition is exact and associative, so the prefix sums
+// M_left(i), the total and each bracket M_tot - M_left(i) - M_left(i-1) are
+// exact whatever the summation order, and the only rounding of a(i) is the
+// final conversion to double (correctly rounded) and the product by 2 pi G.
+// This is summation with its compensation carried exactly: it is at least
+// as accurate as a TwoSum-compensated FP64 scan, deterministic, and runs on
+// the integer pipes (FP64 runs at two lanes per SM per clock on this GPU).
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+// M * 2^up rounded to the nearest integer (ties to even), for |M| * 2^up <
+// 2^112, as a signed 128-bit value: from the bits of M (integer operations
+// only; FP64 runs at two lanes per SM per clock on this GPU).
+__device__ __forceinline__ i128 fixed_of(double M, int up) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(M);
+  const bool neg = (b >> 63) != 0;
+  const int be = (int)((b >> 52) & 0x7ff);
+  unsigned long long mant = b & 0x000fffffffffffffull;
+  int e2;  // M = mant * 2^e2
+  if (be == 0) {
+    e2 = -1074;  // subnormal (or zero)
+  } else {
+    mant |= 0x0010000000000000ull;
+    e2 = be - 1075;
+  }
+  const int sh = e2 + up;
+  u128 U;
+  if (sh >= 0) {
+    U = (u128)mant << sh;  // sh <= 59 for |M| * 2^up < 2^112
+  } else if (sh > -64) {
+    const int k = -sh;
+    const unsigned long long q = mant >> k, rem = mant & ((1ull << k) - 1ull), half = 1ull << (k - 1);
+    U = (u128)(q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull));
+  } else {
+    U = 0;  // below half a unit
+  }
+  return neg ? -(i128)U : (i128)U;
+}
+
+// X * 2^e correctly rounded to double (ties to even), X != -2^127, for
+// results in the normal range (tiny ones are scaled by scalbn).
+__device__ __forceinline__ double double_of(i128 X, int e) {
+  if (X == 0) return 0.0;
+  const bool neg = X < 0;
+  const u128 U = neg ? (u128)(-X) : (u128)X;
+  const unsigned long long hi = (unsigned long long)(U >> 64), lo = (unsigned long long)U;
+  const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
+  const int top = 127 - lz;  // position of the leading bit
+  // the 53 significant bits, the rounding bit and the sticky bits below it
+  unsigned long long mant;
+  bool up_;
+  if (top <= 52) {
+    mant = lo << (52 - top);
+    up_ = false;
+  } else {
+    const int k = top - 52;  // bits dropped, 1..75
+    const u128 q = U >> k;
+    const u128 rem = U - (q << k);
+    const u128 half = (u128)1 << (k - 1);
+    mant = (unsigned long long)q;
+    up_ = rem > half || (rem == half && (mant & 1ull));
+  }
+  if (up_) mant++;
+  int ex = top + e;  // binary exponent of the result
+  if (mant == (1ull << 53)) {  // rounding carried into a new bit
+    mant >>= 1;
+    ex++;
+  }
+  double r;
+  if (ex >= -1022 && ex <= 1023) {
+    r = __longlong_as_double((long long)(((unsigned long long)(ex + 1023) << 52) | (mant & 0x000fffffffffffffull)));
+  } else {
+    r = scalbn((double)mant, ex - 52);  // outside the normal range: not met by pixel masses
+  }
+  return neg ? -r : r;
+}
+
+__device__ __forceinline__ i128 shfl_up_i128(i128 v, int d) {
+  const long long lo = __shfl_up_sync(0xffffffffu, (long long)(unsigned long long)(u128)v, d);
+  const long long hi = __shfl_up_sync(0xffffffffu, (long long)((u128)v >> 64), d);
+  return (i128)(((u128)(unsigned long long)hi << 64) | (u128)(unsigned long long)lo);
+}
+
+// Mass scan and force: one block.  Each thread takes a contiguous chunk of
+// pixels: the largest |M| sets the common scale, the chunk sums are scanned
+// across the block, and each thread walks its chunk once more, writing
+// a(i) = 2 pi G (M_tot - M_left(i) - M_left(i-1)).
 __global__ void __launch_bounds__(SCAN_T) k_scan_force(Grid g, const double* __restrict__ M,
                                                        double* __restrict__ a, DevState* ds) {
-  __shared__ double sh[SCAN_T / 32];
-  __shared__ double tot_s;
+  __shared__ i128 sh[SCAN_T / 32];
+  __shared__ double mx_s[SCAN_T / 32];
+  __shared__ i128 tot_s;
   const int nx = g.nx, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int C = (nx + SCAN_T - 1) / SCAN_T;
   const int i0 = min(tid * C, nx), i1 = min(i0 + C, nx);
-  double loc = 0.0;
-  for (int i = i0; i < i1; i++) loc = dadd(loc, M[i]);
-  double inc = loc;
+  double mx = 0.0;
+  for (int i = i0; i < i1; i++) mx = fmax(mx, fabs(M[i]));  // NaN is dropped by fmax
+  bool bad = false;
+  for (int i = i0; i < i1; i++) bad |= !(fabs(M[i]) <= 1.0e300);
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  bad = __any_sync(0xffffffffu, bad);
+  if (lane == 0) mx_s[wid] = bad ? INFINITY : mx;
+  __syncthreads();
+  mx = 0.0;
+#pragma unroll
+  for (int w = 0; w < SCAN_T / 32; w++) mx = fmax(mx, mx_s[w]);
+  if (!(mx <= 1.0e300) || mx == 0.0) {
+    // no mass (a = 0), or a mass that is not a finite number (a = NaN)
+    const double val = (mx == 0.0) ? 0.0 : __longlong_as_double(0x7ff8000000000000ll);
+    for (int i = i0; i < i1; i++) a[i] = val;
+    if (tid == 0) ds->Mtot = val;
+    return;
+  }
+  const int E = ilogb(mx);
+  const int up = 111 - E;  // M * 2^up < 2^112
+  i128 loc = 0;
+  for (int i = i0; i < i1; i++) loc += fixed_of(M[i], up);
+  i128 inc = loc;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    const double o = __shfl_up_sync(0xffffffffu, inc, d);
-    if (lane >= d) inc = dadd(o, inc);
+    const i128 o = shfl_up_i128(inc, d);
+    if (lane >= d) inc += o;
   }
   if (lane == 31) sh[wid] = inc;
   __syncthreads();
-  if (wid == 0) {
-    const double w = (lane < SCAN_T / 32) ? sh[lane] : 0.0;
-    double wi = w;
+  if (tid == 0) {
+    i128 run = 0;
 #pragma unroll
-    for (int d = 1; d < SCAN_T / 32; d <<= 1) {
-      const double o = __shfl_up_sync(0xffffffffu, wi, d);
-      if (lane >= d) wi = dadd(o, wi);
+    for (int w = 0; w < SCAN_T / 32; w++) {
+      const i128 t = sh[w];
+      sh[w] = run;  // exclusive prefix of the warp totals
+      run += t;
     }
-    if (lane < SCAN_T / 32) sh[lane] = dsub(wi, w);  // exclusive prefix of the warp totals
-    if (lane == SCAN_T / 32 - 1) tot_s = wi;
+    tot_s = run;
   }
   __syncthreads();
-  const double tot = tot_s;
-  // sum of the pixels before this thread's chunk
-  double left_prev = dadd(sh[wid], dsub(inc, loc));
+  const i128 tot = tot_s;
+  i128 left_prev = sh[wid] + (inc - loc);  // mass of the pixels before this chunk
   for (int i = i0; i < i1; i++) {
-    const double left = dadd(left_prev, M[i]);
-    a[i] = dmul(g.A, dsub(dsub(tot, left), left_prev));
+    const i128 left = left_prev + fixed_of(M[i], up);
+    a[i] = dmul(g.A, double_of(tot - left - left_prev, -up));
     left_prev = left;
   }
-  if (tid == 0) ds->Mtot = tot;
+  if (tid == 0) ds->Mtot = double_of(tot, -up);
 }
 
 // a' and a'' by centred differences (Sec. 2.5); beyond the grid a takes its

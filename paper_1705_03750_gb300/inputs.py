@@ -13,7 +13,9 @@ Workloads, shaped after the paper's tests (Sec. 3.2):
   * a free-streaming (G = 0) run on the Spitzer grid;
   * the paper's truncated Gaussian initial condition (Sec. 3.2, eqs. monfg,
     gauini): rho_G exp(-(x^2 + v^2)/(2 sigma_G^2)) inside radius R, cut
-    smoothly beyond it by max[1 + 2 tanh((R - r)/eta_G), 0].
+    smoothly beyond it by max[1 + 2 tanh((R - r)/eta_G), 0];
+  * the paper's apodised thermal-equilibrium sheet (Sec. 3.2, eqs. apofs,
+    apod) in the paper's units (phi'' = 2 rho, i.e. G = 1/(2 pi)).
 """
 from __future__ import annotations
 
@@ -134,6 +136,25 @@ def gaussian_ic(x, v, rho=4.0, sigma=0.2, R=1.0, eta=0.02):
     return np.where(r <= R, g, g * cut)
 
 
+def apodised_spitzer(x, v, rho=4.0, sigma=0.2, eta=0.02):
+    """The paper's thermal-equilibrium sheet (Sec. 3.2, eq. apofs),
+    f_S = rho / ch^2(sqrt(sqrt(2 pi) rho / sigma) x) exp(-v^2 / (2 sigma^2)),
+    apodised as in eq. apod.  The apodising function is printed as
+    g(y) = eta max[1 + 2 th((y - eta)/eta), 0], whose leading eta would scale
+    the whole sheet by about 3 eta and contradict the printed maximum
+    projected density (about 2, that of f_S itself); it is read like the cut
+    of the Gaussian initial condition printed beside it (eq. monfg2):
+    f = f_S where f_S >= eta, and f_S max[1 + 2 th((f_S - eta)/eta), 0]
+    below, so f is continuous and vanishes where f_S < eta (1 - atanh(1/2)).
+    In the paper's units (phi'' = 2 rho) the sheet is stationary."""
+    x = np.asarray(x, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
+    k = math.sqrt(math.sqrt(2.0 * math.pi) * rho / sigma)
+    fs = rho / np.cosh(k * x) ** 2 * np.exp(-0.5 * (v / sigma) ** 2)
+    cut = np.maximum(1.0 + 2.0 * np.tanh((fs - eta) / eta), 0.0)
+    return np.where(fs >= eta, fs, fs * cut)
+
+
 def initial_f(cfg: RunConfig) -> np.ndarray:
     """f0 sampled on the nodes, [nx, nv] float64, v fastest."""
     X, V = np.meshgrid(cfg.x(), cfg.v(), indexing="ij")
@@ -144,6 +165,8 @@ def initial_f(cfg: RunConfig) -> np.ndarray:
         return h.on_grid(cfg.x(), cfg.v())
     if cfg.ic == "gauss":
         return gaussian_ic(X, V, **cfg.ic_params)
+    if cfg.ic == "apod":
+        return apodised_spitzer(X, V, **cfg.ic_params)
     if cfg.ic == "blob":
         # a single warm Gaussian well inside the box (free-streaming checks)
         p = cfg.ic_params
@@ -161,6 +184,8 @@ def ic_function(cfg: RunConfig):
         return draw_halos(cfg.seed, n=cfg.ic_params.get("n", 16))
     if cfg.ic == "gauss":
         return lambda x, v: gaussian_ic(x, v, **cfg.ic_params)
+    if cfg.ic == "apod":
+        return lambda x, v: apodised_spitzer(x, v, **cfg.ic_params)
     if cfg.ic == "blob":
         p = cfg.ic_params
         return lambda x, v: np.exp(-0.5 * ((x - p.get("x0", 0.0)) / p.get("sx", 0.15)) ** 2
@@ -180,7 +205,13 @@ HALOS_8192 = HALOS_4096.with_(name="halos16-8192x8192", nx=8192, nv=8192, steps=
 GAUSS_128 = RunConfig("gauss-128x128-G1", 128, 128, -1.2, 1.2, -1.2, 1.2, 4, 0.005, 20, 1.0, 200,
                       "gauss", {"rho": 4.0, "sigma": 0.2, "R": 1.0, "eta": 0.02})
 
-WORKLOADS = {c.name: c for c in (SPITZER_128, FREE_128, HALOS_4096, HALOS_8192, GAUSS_128)}
+# the paper's apodised thermal equilibrium (rho_S = 4, sigma_S = 0.2, eta = 0.02)
+# in its units (2 pi G = 1), on a box just wider than the apodised support
+# (|x| < 0.53, |v| < 0.70); the paper's time step 0.0025 and n_s = 25
+APOD_128 = RunConfig("apodised-spitzer-128x128", 128, 128, -0.6, 0.6, -0.8, 0.8, 4, 0.0025, 25,
+                     1.0 / (2.0 * math.pi), 200, "apod", {"rho": 4.0, "sigma": 0.2, "eta": 0.02})
+
+WORKLOADS = {c.name: c for c in (SPITZER_128, FREE_128, HALOS_4096, HALOS_8192, GAUSS_128, APOD_128)}
 
 
 def batch_member(index: int, base_seed: int = 1000) -> RunConfig:

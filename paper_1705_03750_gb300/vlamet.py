@@ -32,7 +32,7 @@ EXPORTS = ["vm_config_default", "vm_workspace_bytes", "vm_create", "vm_destroy",
            "vm_read_eta", "vm_read_map", "vm_diagnostics", "vm_sync", "vm_launch_count",
            "vm_profile", "vm_profile_read", "vm_force_from_f_static",
            "vm_batch_create", "vm_batch_step", "vm_batch_launches_per_step", "vm_batch_destroy",
-           "vm_last_cuda_error", "vm_cuda_error_name", "vm_save", "vm_load"]
+           "vm_last_cuda_error", "vm_cuda_error_name", "vm_save", "vm_load", "vm_measure_fp64_peak"]
 
 VM_STATIC_FORCE_MAX_NX = 16384
 
@@ -114,6 +114,7 @@ def load() -> C.CDLL:
         "vm_cuda_error_name": (C.c_char_p, [i32]),
         "vm_save": (i32, [vp, C.c_char_p]),
         "vm_load": (i32, [vp, C.c_char_p]),
+        "vm_measure_fp64_peak": (i32, [i32, vp, dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -190,6 +191,17 @@ def force_from_f_static(f, cfg: Config, out: dict, stream=None) -> None:
     _check(L.vm_force_from_f_static(C.c_void_p(f.data_ptr()), dtype, cfg.nx, cfg.nv, cfg.x_lo, cfg.x_hi,
                                     cfg.v_lo, cfg.v_hi, cfg.G, cfg.literal_fd, ptr("M"), ptr("a"), ptr("da"),
                                     ptr("d2a"), C.c_void_p(st.cuda_stream)), "vm_force_from_f_static")
+
+
+def measure_fp64_peak(iters: int = 20000, stream=None) -> float:
+    """FP64 FLOP/s of the current device from the library's FMA-chain probe
+    (vm_measure_fp64_peak); synchronises."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    r = C.c_double()
+    _check(load().vm_measure_fp64_peak(int(iters), C.c_void_p(st.cuda_stream), C.byref(r)),
+           "vm_measure_fp64_peak")
+    return r.value
 
 
 class Solver:

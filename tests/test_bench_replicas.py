@@ -32,7 +32,7 @@ def _worker(rank, world, port, out):
 
 def test_two_ranks_report_the_slowest_rank_and_the_whole_job_rate():
     world = 2
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
         res = dict(out)

@@ -78,3 +78,29 @@ def test_load_refuses_another_run_and_bad_files(tmp_path):
     with pytest.raises(V.VlametError) as e:
         solver(rc, "fp64").load(cut)
     assert e.value.status == 9
+
+
+def test_resume_keeps_time_under_a_variable_time_step(tmp_path):
+    """With C_dyn > 0 (Sec. 2.4) each step's dt comes from the density of the
+    last f; the checkpoint carries the elapsed time and the last step, so
+    after a resume vm_diag.time is still the sum of every step since
+    vm_set_f and the steps that follow are the saved solve's."""
+    rc = I.SPITZER_128.with_(n_s=4)
+    cfg = V.Config.from_run(rc)
+    cfg.c_dyn = 0.004
+    a = V.Solver(cfg)
+    a.set_f(I.initial_f(rc))
+    a.step(6)
+    t6 = a.diagnostics()["time"]
+    path = tmp_path / "cdyn.vlm"
+    a.save(path)
+    b = V.Solver(cfg)
+    b.load(path)
+    db = b.diagnostics()
+    assert db["time"] == t6 and db["last_dt"] == a.diagnostics()["last_dt"]
+    a.step(7)
+    b.step(7)
+    da, db = a.diagnostics(), b.diagnostics()
+    assert da["time"] == db["time"] and da["last_dt"] == db["last_dt"]
+    assert 0.0 < da["last_dt"] < rc.dt
+    assert np.array_equal(a.read_f(), b.read_f())

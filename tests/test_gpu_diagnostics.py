@@ -142,6 +142,27 @@ def test_gaussian_ic_first_steps_match_oracle(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_apodised_sheet_matches_oracle_through_a_remap(prec):
+    # the paper's apodised thermal equilibrium (Sec. 3.2, eqs. apofs, apod),
+    # paper units (2 pi G = 1), n_s = 25: the first step, then through a remap
+    rc = I.APOD_128
+    s = V.Solver(V.Config.from_run(rc, PREC[prec]))
+    o = oracle_of(rc)
+    f0 = I.initial_f(rc)
+    s.set_f(f0)
+    o.set_f(f0)
+    for k in (1, 29):
+        s.step(k)
+        o.step(k)
+        fo = o.last_f()
+        err = np.abs(s.read_f() - fo).max() / np.abs(fo).max()
+        tol = 1e-6 if k == 1 else (1e-9 if prec == "fp64" else 1e-5)
+        assert err <= tol, (k, err)
+    dg, do = s.diagnostics(), o.diagnostics()
+    assert dg["mass"] == pytest.approx(do["mass"], rel=1e-12 if prec == "fp64" else 1e-6)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_variable_time_step_matches_oracle(prec):
     # Sec. 2.4: dt = min(dt, C_dyn / sqrt(rho_max)) each step, through a remap
     rc = I.SPITZER_128
@@ -153,13 +174,16 @@ def test_variable_time_step_matches_oracle(prec):
     s.set_f(f0)
     o.set_f(f0)
     o.set_cdyn(0.005)
-    s.step(25)
-    o.step(25)
-    d = s.diagnostics()
     tol_dt = 1e-12 if prec == "fp64" else 1e-6
-    assert d["last_dt"] == pytest.approx(o.last_dt(), rel=tol_dt)
-    assert d["time"] == pytest.approx(o.time(), rel=tol_dt)
-    assert d["last_dt"] < rc.dt  # the density constraint is active
+    # one step at a time: every step's dt, including the first one after
+    # the remap at step 20 (whose density is the resampled f's)
+    for n in range(25):
+        s.step(1)
+        o.step(1)
+        d = s.diagnostics()
+        assert d["last_dt"] == pytest.approx(o.last_dt(), rel=tol_dt), n
+        assert d["time"] == pytest.approx(o.time(), rel=tol_dt), n
+        assert d["last_dt"] < rc.dt  # the density constraint is active
     fo = o.last_f()
     err = np.abs(s.read_f() - fo).max() / np.abs(fo).max()
     assert err <= (1e-9 if prec == "fp64" else 1e-5), err
