@@ -89,6 +89,16 @@ typedef struct {
                                  rho(x_i) = sum_j f(i, j) dv of the last reconstructed f
                                  (f0 before the first step); vm_step then synchronises once
                                  per step; batches refuse it */
+  double f_th;                /* 0: fixed box (every element, every site); > 0: adaptive
+                                 computing domain (Sec. 2.2.1, eq. constrf; Sec. 2.3).  At
+                                 vm_set_f and at every remap f_ini is cut to the smallest
+                                 node rectangle holding every |f_ini| > f_th, and elements
+                                 exist only on the lattice lines covering it plus one extra
+                                 layer on every side; each map then claims and repairs only
+                                 the sites of the rectangle spanned by the existing
+                                 elements' positions (f = 0 elsewhere).  The remap reads
+                                 the rectangle back (vm_step synchronises once per remap);
+                                 batches refuse it */
 } vm_config;
 
 typedef struct {
@@ -118,6 +128,9 @@ typedef struct {
   int64_t emap_remaps; /* remaps that vm_config.emap_remap forced since vm_set_f */
   double time;         /* sum of the steps taken since vm_set_f */
   double last_dt;      /* the last step's time step */
+  int32_t lattice_range[4]; /* existing elements: lattice rows k_lo..k_hi, columns l_lo..l_hi */
+  int32_t site_rect[4];     /* the last map's sites: rows i_lo..i_hi, columns j_lo..j_hi
+                               (the whole grid with vm_config.f_th = 0) */
 } vm_diag;
 
 typedef struct vm_solver vm_solver;

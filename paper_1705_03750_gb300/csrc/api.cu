@@ -20,7 +20,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
   size_t fini, eta, f, tmp, map, slot1, rec_key, rec_site, holes_a, holes_b, ovf, gwin, seed, el, tay, tayf, M, a, da, d2a,
-      thx, thv, thxf, thvf, ds, total;
+      thx, thv, thxf, thvf, rect, ds, total;
 };
 
 bool valid(const vm_config* c) {
@@ -33,6 +33,7 @@ bool valid(const vm_config* c) {
   if (!(c->emap_remap >= 0.0) || !isfinite(c->emap_remap)) return false;
   if (!(c->c_dyn >= 0.0) || !isfinite(c->c_dyn)) return false;
   if (!(c->alpha >= 0.0) || !(c->beta >= 0.0)) return false;
+  if (!(c->f_th >= 0.0) || !isfinite(c->f_th)) return false;
   // 32-bit site indices; element indices fit the 24-bit field of the owner slots
   if ((long long)c->nx * (long long)c->nv >= (1ll << 31) / 2) return false;
   const long long s = c->elem_stride;
@@ -86,6 +87,7 @@ Layout layout(const vm_config* c) {
   L.thv = take(2 * c->nv * 8);
   L.thxf = take(2 * c->nx * 4);
   L.thvf = take(2 * c->nv * 4);
+  L.rect = take(4 * vm::kRectBlocks * 8);
   L.ds = take(sizeof(vm::DevState));
   L.total = o;
   return L;
@@ -135,6 +137,47 @@ void note_cuda(cudaError_t e) { t_last_cuda = e; }
 // context persists and makes our own launches fail.
 void clear_foreign_error() { (void)cudaGetLastError(); }
 
+namespace {
+long long floor_div(long long a, long long b) {  // b > 0
+  const long long q = a / b;
+  return (q * b > a) ? q - 1 : q;
+}
+}  // namespace
+
+// Adaptive computing domain (Sec. 2.2.1, eq. constrf; Sec. 2.3), after f_ini
+// changed (vm_set_f, remap): the node rectangle of |f_ini| > f_th, read back
+// (synchronises), f_ini cut to it, and the lattice lines that exist: the
+// last line at or before its first node and the first at or after its last
+// node (integer arithmetic on the lines' index positions (n-1)/2 + (k-K-1)s),
+// plus one extra layer on every side.
+cudaError_t domain_update(vm_solver* s) {
+  Grid& g = s->g;
+  if (!g.fth_on) return cudaSuccess;
+  int32_t box[4] = {g.nx, -1, g.nv, -1};
+  cudaError_t e = cudaMemcpyAsync(s->ds->fbox, box, sizeof box, cudaMemcpyHostToDevice, s->stream);
+  if (e != cudaSuccess) return e;
+  launch_fth_box(s);
+  e = cudaMemcpyAsync(box, s->ds->fbox, sizeof box, cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return e;
+  if (box[1] < 0) {  // nothing above the threshold: no element exists
+    g.klo = g.llo = 0;
+    g.khi = g.lhi = -1;
+  } else {
+    const long long s2 = 2ll * g.s;
+    const long long klo = g.Kx + 1 + floor_div(2ll * box[0] - (g.nx - 1), s2) - 1;
+    const long long khi = g.Kx + 1 - floor_div(-(2ll * box[1] - (g.nx - 1)), s2) + 1;
+    const long long llo = g.Kv + 1 + floor_div(2ll * box[2] - (g.nv - 1), s2) - 1;
+    const long long lhi = g.Kv + 1 - floor_div(-(2ll * box[3] - (g.nv - 1)), s2) + 1;
+    g.klo = (int32_t)std::max(0ll, klo);
+    g.khi = (int32_t)std::min<long long>(g.Lx - 1, khi);
+    g.llo = (int32_t)std::max(0ll, llo);
+    g.lhi = (int32_t)std::min<long long>(g.Lv - 1, lhi);
+  }
+  launch_fth_cut(s);
+  return cudaGetLastError();
+}
+
 // One transport step t -> t + dt (Sec. 2.4): predictor drift + Taylor terms
 // at t + dt/2, map, f(t + dt/2) and M(i), force, kick + corrector.  Only
 // enqueues work (safe inside a stream capture); host counters untouched.
@@ -153,7 +196,9 @@ cudaError_t step_remap(vm_solver* s) {
   launch_remap_resample(s, s->tmp);
   // the resampled f becomes f_ini (a copy, not a pointer swap, so that a
   // captured step keeps its buffers)
-  const cudaError_t e = cudaMemcpyAsync(s->fini, s->tmp, s->n * s->sreal, cudaMemcpyDeviceToDevice, s->stream);
+  cudaError_t e = cudaMemcpyAsync(s->fini, s->tmp, s->n * s->sreal, cudaMemcpyDeviceToDevice, s->stream);
+  if (e != cudaSuccess) return e;
+  e = domain_update(s);
   if (e != cudaSuccess) return e;
   launch_spline_solve(s, s->fini, s->eta);
   launch_reset_elements(s);
@@ -343,6 +388,11 @@ vm_status vm_create(const vm_config* c, void* d_workspace, size_t bytes, void* s
   g.A = 2.0 * kPi * c->G;
   g.literal_fd = c->literal_fd;
   g.max_hole_rounds = s->cfg.max_hole_rounds;
+  g.fth_on = c->f_th > 0.0 ? 1 : 0;
+  g.klo = 0;
+  g.khi = g.Lx - 1;
+  g.llo = 0;
+  g.lhi = g.Lv - 1;
   char* base = (char*)d_workspace;
   s->fini = base + L.fini;
   s->eta = base + L.eta;
@@ -372,6 +422,7 @@ vm_status vm_create(const vm_config* c, void* d_workspace, size_t bytes, void* s
   s->thomas_v = (double*)(base + L.thv);
   s->thomas_xf = (float*)(base + L.thxf);
   s->thomas_vf = (float*)(base + L.thvf);
+  s->rect_part = (double*)(base + L.rect);
   s->ds = (vm::DevState*)(base + L.ds);
   if (!vm::map_prepare(g)) {
     free(s);
@@ -472,6 +523,7 @@ vm_status vm_set_f(vm_solver* s, const double* f0, int32_t on_device) {
     }
     vm::launch_store_real(s, src, s->fini, s->n);
   }
+  VM_CUDA_TRY(vm::domain_update(s));
   VM_CUDA_TRY(cudaMemcpyAsync(s->f, s->fini, s->n * s->sreal, cudaMemcpyDeviceToDevice, s->stream));
   vm::launch_spline_solve(s, s->fini, s->eta);
   vm::launch_reset_elements(s);
@@ -624,11 +676,10 @@ vm_status vm_diagnostics(vm_solver* s, vm_diag* d) {
   if (!s || !d) return VM_E_INVALID_ARG;
   // zero the accumulators: sum_mass, sum_kin, sum_pot, and the det keys
   vm::DevState h{};
-  const size_t off = offsetof(vm::DevState, sum_mass);
+  const size_t off = offsetof(vm::DevState, sum_mass), end = offsetof(vm::DevState, rect);
   h.det_min_key = ~0ull;
   h.det_max_key = 0ull;
-  VM_CUDA_TRY(cudaMemcpyAsync((char*)s->ds + off, (char*)&h + off, sizeof(vm::DevState) - off,
-                              cudaMemcpyHostToDevice, s->stream));
+  VM_CUDA_TRY(cudaMemcpyAsync((char*)s->ds + off, (char*)&h + off, end - off, cudaMemcpyHostToDevice, s->stream));
   vm::launch_diagnostics(s);
   vm::launch_emap(s);
   VM_CUDA_TRY(cudaMemcpyAsync(&h, s->ds, sizeof h, cudaMemcpyDeviceToHost, s->stream));
@@ -662,6 +713,11 @@ vm_status vm_diagnostics(vm_solver* s, vm_diag* d) {
   d->emap_remaps = s->emap_remaps;
   d->time = s->time;
   d->last_dt = s->last_dt;
+  d->lattice_range[0] = s->g.klo;
+  d->lattice_range[1] = s->g.khi;
+  d->lattice_range[2] = s->g.llo;
+  d->lattice_range[3] = s->g.lhi;
+  for (int q = 0; q < 4; q++) d->site_rect[q] = s->g.fth_on ? h.rect[q] : (q == 1 ? s->g.nx - 1 : (q == 3 ? s->g.nv - 1 : 0));
   return VM_OK;
 }
 
@@ -678,7 +734,7 @@ const char* vm_cuda_error_name(int32_t code) { return cudaGetErrorName((cudaErro
 namespace {
 
 constexpr char kCkMagic[8] = {'V', 'L', 'M', 'T', 'C', 'K', 'P', 'T'};
-constexpr uint32_t kCkVersion = 2;
+constexpr uint32_t kCkVersion = 3;
 
 struct CkHeader {
   char magic[8];
@@ -689,6 +745,8 @@ struct CkHeader {
   double x_lo, x_hi, v_lo, v_hi, dt, G, alpha, beta;
   double time, last_dt;  // Sec. 2.4: elapsed time and the last step (variable time steps)
   int64_t emap_remaps;
+  double f_th;            // adaptive computing domain: threshold and existing lattice range
+  int32_t lattice[4];
 };
 
 CkHeader ck_header(const vm_solver* s) {
@@ -716,6 +774,11 @@ CkHeader ck_header(const vm_solver* s) {
   h.time = s->time;
   h.last_dt = s->last_dt;
   h.emap_remaps = s->emap_remaps;
+  h.f_th = s->cfg.f_th;
+  h.lattice[0] = s->g.klo;
+  h.lattice[1] = s->g.khi;
+  h.lattice[2] = s->g.llo;
+  h.lattice[3] = s->g.lhi;
   return h;
 }
 
@@ -735,7 +798,8 @@ void ck_arrays(const vm_solver* s, CkArray (&a)[4]) {
 bool same_run(const CkHeader& a, const CkHeader& b) {
   return a.nx == b.nx && a.nv == b.nv && a.elem_stride == b.elem_stride && a.precision == b.precision &&
          a.ne == b.ne && a.sreal == b.sreal && a.x_lo == b.x_lo && a.x_hi == b.x_hi && a.v_lo == b.v_lo &&
-         a.v_hi == b.v_hi && a.dt == b.dt && a.G == b.G && a.alpha == b.alpha && a.beta == b.beta;
+         a.v_hi == b.v_hi && a.dt == b.dt && a.G == b.G && a.alpha == b.alpha && a.beta == b.beta &&
+         a.f_th == b.f_th;
 }
 
 }  // namespace
@@ -808,5 +872,9 @@ vm_status vm_load(vm_solver* s, const char* path) {
   s->time = h.time;
   s->last_dt = h.last_dt;
   s->emap_remaps = h.emap_remaps;
+  s->g.klo = h.lattice[0];
+  s->g.khi = h.lattice[1];
+  s->g.llo = h.lattice[2];
+  s->g.lhi = h.lattice[3];
   return VM_OK;
 }

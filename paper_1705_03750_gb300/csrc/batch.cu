@@ -91,7 +91,8 @@ extern "C" vm_status vm_batch_create(vm_solver* const* solvers, int32_t n, int32
     if (!s) return VM_E_INVALID_ARG;
     if (!s->have_f || s->prof) return VM_E_STATE;
     if (s->cfg.n_s != n_s || s->cyc != cyc) return VM_E_STATE;  // one remap phase per batch
-    if (s->cfg.emap_remap > 0.0 || s->cfg.c_dyn > 0.0) return VM_E_INVALID_ARG;  // host decisions per step: not capturable
+    // host decisions per step or per remap: not capturable
+    if (s->cfg.emap_remap > 0.0 || s->cfg.c_dyn > 0.0 || s->cfg.f_th > 0.0) return VM_E_INVALID_ARG;
     for (int32_t j = 0; j < i; j++)
       if (solvers[j] == s) return VM_E_INVALID_ARG;
   }

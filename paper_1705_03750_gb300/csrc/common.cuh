@@ -36,6 +36,12 @@ struct Grid {
   double r_vx, r_xv;      // dv_m/dx_m and dx_m/dv_m
   int32_t literal_fd;
   int32_t max_hole_rounds;
+  // adaptive computing domain (Sec. 2.2.1, eq. constrf; Sec. 2.3): fth_on
+  // restricts each map to the site rectangle DevState::rect spanned by the
+  // existing elements; elements exist on lattice rows klo..khi and columns
+  // llo..lhi (the whole lattice when fth_on is 0)
+  int32_t fth_on;
+  int32_t klo, khi, llo, lhi;
 };
 
 // Small device-resident control block.
@@ -66,6 +72,13 @@ struct DevState {
   double sum_ent, sum_l1, sum_l2;   // Casimirs of the last f (Sec. 3.2)
   unsigned long long emap2_bits;     // bits of the largest squared E_map term (>= 0)
   unsigned long long rho_max_bits;   // bits of the largest positive projected density
+  // adaptive computing domain: the current map's site rectangle (i_lo, i_hi,
+  // j_lo, j_hi; empty when lo > hi), the node rectangle of |f_ini| > f_th
+  // (same order, atomics), and the completion counter of the rectangle's
+  // block reduction
+  int32_t rect[4];
+  int32_t fbox[4];
+  uint32_t rect_done;
 };
 
 // Owner slots of the influence map: (epoch << 24) | element index.  A slot
@@ -83,6 +96,12 @@ inline size_t global_window_words(long long nx, long long nv, long long pad) {
   return 3 * (size_t)(nx + 2 * pad) * (size_t)((nv + 2 * pad + 63) / 64);
 }
 constexpr uint32_t SLOT_MASK = 0x00FFFFFFu;
+// Element field of an owner slot marking a site outside the computing
+// domain of the current map (never an element: the lattice has fewer than
+// 2^24 - 1 elements).
+constexpr uint32_t SLOT_OUTSIDE = SLOT_MASK;
+// Blocks of the domain-rectangle reduction (partials kept in the workspace).
+constexpr int kRectBlocks = 256;
 constexpr int kEpochs = 255;  // epochs 0..254; 255 never current
 
 // Element state: 12 doubles per element, structure of arrays.
@@ -153,6 +172,7 @@ struct vm_solver {
   double* thomas_v;         // 2 x nv
   float* thomas_xf;
   float* thomas_vf;
+  double* rect_part;        // kRectBlocks x 4 partial minima/maxima of the element positions
   vm::DevState* ds;
   // host-side bookkeeping
   int32_t have_f;
@@ -208,6 +228,22 @@ void launch_convert(vm_solver* s, const void* src, void* dst, int32_t dst_dtype,
 void launch_store_real(vm_solver* s, const double* src, void* dst, size_t count);
 // spline.cu
 void launch_spline_solve(vm_solver* s, const void* src, void* dst);
+
+// adaptive computing domain (api.cu launches, elements.cu kernels)
+// node rectangle of |f_ini| > f_th into ds->fbox (reset first)
+void launch_fth_box(vm_solver* s);
+// f_ini <- 0 outside the node rectangle of ds->fbox
+void launch_fth_cut(vm_solver* s);
+// the map's site rectangle from the existing elements' positions into ds->rect
+void launch_domain_rect(vm_solver* s);
+// map.cu: owner slots outside ds->rect tagged SLOT_OUTSIDE
+void launch_clear_outside(vm_solver* s);
+
+// Does element (kk, ll) exist (inside the lattice and the part of it that
+// covers the computing domain)?
+__device__ __forceinline__ bool elem_exists(const Grid& g, int kk, int ll) {
+  return kk >= g.klo && kk <= g.khi && ll >= g.llo && ll <= g.lhi;
+}
 
 // ---- exact-order FP64 arithmetic (never contracted into FMA) ----
 __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }

@@ -6,6 +6,7 @@
 // operation in a fixed order with non-contracting intrinsics, so that given
 // the same force arrays the element trajectories are reproducible to the
 // last bit by any FP64 restatement that uses the same order.
+#include <algorithm>
 #include <climits>
 
 #include "common.cuh"
@@ -411,6 +412,8 @@ __global__ void k_diag(Grid g, const R* __restrict__ f, const double* __restrict
   if (ep != 0.0) atomicAdd(&ds->sum_pot, ep);
   for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < g.ne; m += gridDim.x * blockDim.x) {
     const int ne = g.ne;
+    const int km = m / g.Lv;
+    if (!elem_exists(g, km, m - km * g.Lv)) continue;
     double d = el[EL_TXX * ne + m] * el[EL_TVV * ne + m] - el[EL_TXV * ne + m] * el[EL_TVX * ne + m];
     unsigned long long k = order_key(d);
     atomicMin(&ds->det_min_key, k);
@@ -436,6 +439,126 @@ __global__ void __launch_bounds__(256) k_rho_max(Grid g, const R* __restrict__ f
     const double rho = dmul(t, g.dv);
     if (rho > 0.0) atomicMax(&ds->rho_max_bits, (unsigned long long)__double_as_longlong(rho));
   }
+}
+
+// ---- adaptive computing domain (Sec. 2.2.1, eq. constrf; Sec. 2.3) ----
+
+// Node rectangle of |f_ini| > f_th: a block per row, the row's smallest and
+// largest such column, then atomics into ds->fbox (reset by the caller to
+// nx, -1, nv, -1).
+template <typename R>
+__global__ void __launch_bounds__(256) k_fth_box(Grid g, const R* __restrict__ f, double f_th, DevState* ds) {
+  __shared__ int lo_s, hi_s;
+  const int i = blockIdx.x;
+  if (threadIdx.x == 0) {
+    lo_s = g.nv;
+    hi_s = -1;
+  }
+  __syncthreads();
+  int lo = g.nv, hi = -1;
+  for (int j = threadIdx.x; j < g.nv; j += blockDim.x)
+    if (fabs((double)f[(size_t)i * g.nv + j]) > f_th) {
+      lo = min(lo, j);
+      hi = max(hi, j);
+    }
+  if (hi >= 0) {
+    atomicMin(&lo_s, lo);
+    atomicMax(&hi_s, hi);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && hi_s >= 0) {
+    atomicMin(&ds->fbox[0], i);
+    atomicMax(&ds->fbox[1], i);
+    atomicMin(&ds->fbox[2], lo_s);
+    atomicMax(&ds->fbox[3], hi_s);
+  }
+}
+
+// f_ini <- 0 outside the node rectangle ds->fbox.
+template <typename R>
+__global__ void k_fth_cut(Grid g, R* __restrict__ f, const DevState* ds) {
+  const int i0 = ds->fbox[0], i1 = ds->fbox[1], j0 = ds->fbox[2], j1 = ds->fbox[3];
+  for (int i = blockIdx.x; i < g.nx; i += gridDim.x) {
+    R* row = f + (size_t)i * g.nv;
+    const bool all = i < i0 || i > i1;
+    for (int j = threadIdx.x; j < g.nv; j += blockDim.x)
+      if (all || j < j0 || j > j1) row[j] = R(0);
+  }
+}
+
+__device__ __forceinline__ unsigned long long okey(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double okey_inv(unsigned long long k) {
+  const unsigned long long b = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+  return __longlong_as_double((long long)b);
+}
+
+// Site rectangle of a map: the extent of the existing elements' positions
+// (Sec. 2.3), i from ceil((min x_m - x_lo)/dx) to floor((max x_m - x_lo)/dx)
+// clamped to the grid, same along v, in the oracle's operation order.  Each
+// block reduces its elements into rect_part; the last block to finish
+// reduces the partials into ds->rect and re-arms the counter.
+__global__ void __launch_bounds__(256) k_domain_rect(Grid g, const double* __restrict__ el,
+                                                     unsigned long long* __restrict__ part, DevState* ds) {
+  __shared__ unsigned long long red[4][8];
+  __shared__ bool last;
+  const int nk = g.khi - g.klo + 1, nl = g.lhi - g.llo + 1;
+  const long long nact = (nk > 0 && nl > 0) ? (long long)nk * nl : 0;
+  // keys ordered as the values; max of ~key = min of key
+  unsigned long long kmin_x = 0, kmax_x = 0, kmin_v = 0, kmax_v = 0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nact; q += (long long)gridDim.x * blockDim.x) {
+    const int k = g.klo + (int)(q / nl), l = g.llo + (int)(q % nl);
+    const int m = k * g.Lv + l;
+    const unsigned long long kx = okey(el[EL_X * g.ne + m]), kv = okey(el[EL_V * g.ne + m]);
+    kmin_x = max(kmin_x, ~kx);
+    kmax_x = max(kmax_x, kx);
+    kmin_v = max(kmin_v, ~kv);
+    kmax_v = max(kmax_v, kv);
+  }
+  unsigned long long v4[4] = {kmin_x, kmax_x, kmin_v, kmax_v};
+#pragma unroll
+  for (int c = 0; c < 4; c++)
+    for (int o = 16; o > 0; o >>= 1) v4[c] = max(v4[c], __shfl_down_sync(0xffffffffu, v4[c], o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int c = 0; c < 4; c++) red[c][wid] = v4[c];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < 4; c++) {
+      unsigned long long t = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) t = max(t, red[c][w]);
+      part[4 * blockIdx.x + c] = t;
+    }
+    __threadfence();
+    last = (atomicAdd(&ds->rect_done, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  unsigned long long t[4] = {0, 0, 0, 0};
+  for (unsigned b = 0; b < gridDim.x; b++)
+    for (int c = 0; c < 4; c++) t[c] = max(t[c], __ldcg(&part[4 * b + c]));
+  ds->rect_done = 0;
+  if (nact == 0 || t[1] == 0) {
+    ds->rect[0] = ds->rect[2] = 0;
+    ds->rect[1] = ds->rect[3] = -1;
+    return;
+  }
+  const double xmin = okey_inv(~t[0]), xmax = okey_inv(t[1]), vmin = okey_inv(~t[2]), vmax = okey_inv(t[3]);
+  if (!(xmin <= xmax) || !(vmin <= vmax)) {
+    ds->rect[0] = ds->rect[2] = 0;
+    ds->rect[1] = ds->rect[3] = -1;
+    return;
+  }
+  const double a = ceil(dmul(dsub(xmin, g.x_lo), g.inv_dx)), b = floor(dmul(dsub(xmax, g.x_lo), g.inv_dx));
+  const double c = ceil(dmul(dsub(vmin, g.v_lo), g.inv_dv)), d = floor(dmul(dsub(vmax, g.v_lo), g.inv_dv));
+  ds->rect[0] = (int)(a < 0.0 ? 0.0 : (a > g.nx ? (double)g.nx : a));
+  ds->rect[1] = (int)(b > g.nx - 1 ? (double)(g.nx - 1) : (b < -1.0 ? -1.0 : b));
+  ds->rect[2] = (int)(c < 0.0 ? 0.0 : (c > g.nv ? (double)g.nv : c));
+  ds->rect[3] = (int)(d > g.nv - 1 ? (double)(g.nv - 1) : (d < -1.0 ? -1.0 : d));
 }
 
 inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -479,6 +602,31 @@ void launch_scan_force_raw(const Grid& g, const double* M, double* a, double* da
                            cudaStream_t stream) {
   k_scan_force<<<1, SCAN_T, 0, stream>>>(g, M, a, ds);
   k_force_diff<<<blocks_for(g.nx, 128), 128, 0, stream>>>(g, a, da, d2a, ds);
+}
+
+void launch_fth_box(vm_solver* s) {
+  if (s->fp32)
+    k_fth_box<float><<<s->g.nx, 256, 0, s->stream>>>(s->g, (const float*)s->fini, s->cfg.f_th, s->ds);
+  else
+    k_fth_box<double><<<s->g.nx, 256, 0, s->stream>>>(s->g, (const double*)s->fini, s->cfg.f_th, s->ds);
+  s->launches++;
+}
+
+void launch_fth_cut(vm_solver* s) {
+  const unsigned nb = (unsigned)std::min(s->g.nx, 152 * 8);
+  if (s->fp32)
+    k_fth_cut<float><<<nb, 256, 0, s->stream>>>(s->g, (float*)s->fini, s->ds);
+  else
+    k_fth_cut<double><<<nb, 256, 0, s->stream>>>(s->g, (double*)s->fini, s->ds);
+  s->launches++;
+}
+
+void launch_domain_rect(vm_solver* s) {
+  const long long nact = (long long)std::max(0, s->g.khi - s->g.klo + 1) * std::max(0, s->g.lhi - s->g.llo + 1);
+  const unsigned nb = (unsigned)std::max(1ll, std::min<long long>(kRectBlocks, (nact + 255) / 256));
+  k_domain_rect<<<nb, 256, 0, s->stream>>>(s->g, s->el, reinterpret_cast<unsigned long long*>(s->rect_part),
+                                          s->ds);
+  s->launches++;
 }
 
 void launch_rho_max(vm_solver* s) {

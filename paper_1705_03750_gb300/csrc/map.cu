@@ -344,14 +344,14 @@ __device__ __forceinline__ void load_elem9(const Grid& g, int m, const double* _
   for (int idx = threadIdx.x; idx < 9 * TY_N; idx += blockDim.x) {
     const int q = idx / TY_N, c = idx - q * TY_N;
     const int kk = k + q / 3 - 1, ll = l + q % 3 - 1;
-    const bool ex = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
+    const bool ex = elem_exists(g, kk, ll);
     E.T9[q][c] = ex ? tay[(size_t)(kk * g.Lv + ll) * TY_N + c] : 0.0;
     if (c == 0) E.ex9[q] = ex;
   }
   for (int idx = threadIdx.x; idx < 9 * TF_MW; idx += blockDim.x) {
     const int q = idx / TF_MW, c = idx - q * TF_MW;
     const int kk = k + q / 3 - 1, ll = l + q % 3 - 1;
-    const bool ex = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
+    const bool ex = elem_exists(g, kk, ll);
     E.F9[q][c] = ex ? tayf[(size_t)(kk * g.Lv + ll) * TF_N + c] : 0.f;
   }
 }
@@ -430,7 +430,7 @@ __device__ __noinline__ bool pass_exact_g(const Grid& g, const double* __restric
     for (int b = b0; b <= b1; b++) {
       if (a == 0 && b == 0) continue;
       const int kk = k + a, ll = l + b;
-      if (kk < 0 || kk >= g.Lx || ll < 0 || ll >= g.Lv) continue;
+      if (!elem_exists(g, kk, ll)) continue;
       double x2, z2;
       if (dist2_exact(tay + (size_t)(kk * g.Lv + ll) * TY_N, g, Px, Pv, x2, z2) < d2) return false;
     }
@@ -557,7 +557,7 @@ __device__ __forceinline__ void claim_element(const Grid& g, const double* __res
   bool exq = false;
   if (lane < 9) {
     const int kk = k + lane / 3 - 1, ll = l + lane % 3 - 1;
-    exq = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
+    exq = elem_exists(g, kk, ll);
     if (exq) {
       const double* tq = tay + (size_t)(kk * g.Lv + ll) * TY_N;
       uq = __ldg(tq + TY_U);
@@ -567,7 +567,7 @@ __device__ __forceinline__ void claim_element(const Grid& g, const double* __res
   for (int idx = lane; idx < 9 * (TF_MW / 4); idx += 32) {
     const int q = idx / (TF_MW / 4), c4 = idx - q * (TF_MW / 4);
     const int kk = k + q / 3 - 1, ll = l + q % 3 - 1;
-    const bool ex = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
+    const bool ex = elem_exists(g, kk, ll);
     const float4 v = ex ? __ldg(reinterpret_cast<const float4*>(tayf + (size_t)(kk * g.Lv + ll) * TF_N) + c4)
                         : make_float4(0.f, 0.f, 0.f, 0.f);
     reinterpret_cast<float4*>(sh.F9[q])[c4] = v;
@@ -895,13 +895,14 @@ __global__ void __launch_bounds__(32 * TP, 8) k_claim_pair(Grid g, const double*
   if (__all_sync(FULL, m >= g.ne)) return;
   bool live = m < g.ne;
   const int k = live ? m / g.Lv : 0, l = live ? m - k * g.Lv : 0;
+  live = live && elem_exists(g, k, l);  // elements off the computing domain claim nothing
   // set-up: the 3x3 neighbourhood's FP64 index positions (half-lanes 0-8)
   // and FP32 records, every load issued before any is used
   double uq = 0.0, wpos = 0.0;
   bool exq = false;
   if (live && hl < 9) {
     const int kk = k + hl / 3 - 1, ll = l + hl % 3 - 1;
-    exq = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
+    exq = elem_exists(g, kk, ll);
     if (exq) {
       const double* tq = tay + (size_t)(kk * g.Lv + ll) * TY_N;
       uq = __ldg(tq + TY_U);
@@ -918,7 +919,7 @@ __global__ void __launch_bounds__(32 * TP, 8) k_claim_pair(Grid g, const double*
       const int idx = hl + 16 * u;
       const int q = idx / (TF_MW / 4), c4 = idx - q * (TF_MW / 4);
       const int kk = k + q / 3 - 1, ll = l + q % 3 - 1;
-      const bool ex = live && idx < 9 * (TF_MW / 4) && kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
+      const bool ex = live && idx < 9 * (TF_MW / 4) && elem_exists(g, kk, ll);
       v[u] = ex ? __ldg(reinterpret_cast<const float4*>(tayf + (size_t)(kk * g.Lv + ll) * TF_N) + c4)
                 : make_float4(0.f, 0.f, 0.f, 0.f);
     }
@@ -929,7 +930,7 @@ __global__ void __launch_bounds__(32 * TP, 8) k_claim_pair(Grid g, const double*
       const int kk = k + q / 3 - 1, ll = l + q % 3 - 1;
       if (live && idx < 9 * (TF_MW / 4)) {
         reinterpret_cast<float4*>(sh.F9[q])[c4] = v[u];
-        if (c4 == 0) sh.ex9[q] = kk >= 0 && kk < g.Lx && ll >= 0 && ll < g.Lv;
+        if (c4 == 0) sh.ex9[q] = elem_exists(g, kk, ll);
       }
     }
   }
@@ -1772,7 +1773,7 @@ __global__ void k_emap(Grid g, const uint32_t* __restrict__ slot0, const double*
       for (int b = b0; b <= b1; b++) {
         if (a == 0 && b == 0) continue;
         const int kk = k + a, ll = l + b;
-        if (kk < 0 || kk >= g.Lx || ll < 0 || ll >= g.Lv) continue;
+        if (!elem_exists(g, kk, ll)) continue;
         double xn, zn;
         dist2_exact(tay + (size_t)(kk * g.Lv + ll) * TY_N, g, Px, Pv, xn, zn);
         const double mx = dsub(dadd((double)a, xn), xi), mv = dsub(dadd((double)b, zn), ze);
@@ -1786,15 +1787,39 @@ __global__ void k_emap(Grid g, const uint32_t* __restrict__ slot0, const double*
 }
 
 __global__ void k_read_map(const uint32_t* __restrict__ slot0, const DevState* ds, int32_t* __restrict__ out,
-                           size_t n) {
+                           size_t n, int ne) {
   const uint32_t epoch = *(const volatile uint32_t*)&ds->epoch;
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
     const uint32_t t = slot0[p];
-    out[p] = ((t >> 24) == epoch) ? (int32_t)(t & SLOT_MASK) : -1;
+    out[p] = ((t >> 24) == epoch && (int)(t & SLOT_MASK) < ne) ? (int32_t)(t & SLOT_MASK) : -1;
+  }
+}
+
+// Adaptive computing domain: sites outside the map's rectangle ds->rect get
+// the current epoch with no element (SLOT_OUTSIDE), so that they are
+// neither holes to repair nor candidates of a repair, and read as unowned.
+__global__ void k_clear_outside(Grid g, uint32_t* __restrict__ slot0, const DevState* ds) {
+  const uint32_t epoch = *(const volatile uint32_t*)&ds->epoch;
+  const int i0 = ds->rect[0], i1 = ds->rect[1], j0 = ds->rect[2], j1 = ds->rect[3];
+  const uint32_t tag = (epoch << 24) | SLOT_OUTSIDE;
+  for (int i = blockIdx.x; i < g.nx; i += gridDim.x) {
+    uint32_t* row = slot0 + (size_t)i * g.nv;
+    if (i < i0 || i > i1 || j0 > j1) {
+      for (int j = threadIdx.x; j < g.nv; j += blockDim.x) row[j] = tag;
+    } else {
+      for (int j = threadIdx.x; j < j0; j += blockDim.x) row[j] = tag;
+      for (int j = j1 + 1 + threadIdx.x; j < g.nv; j += blockDim.x) row[j] = tag;
+    }
   }
 }
 
 }  // namespace
+
+void launch_clear_outside(vm_solver* s) {
+  const unsigned nb = (unsigned)std::min(s->g.nx, 152 * 8);
+  k_clear_outside<<<nb, 256, 0, s->stream>>>(s->g, s->map, s->ds);
+  s->launches++;
+}
 
 void launch_emap(vm_solver* s) {
   unsigned nb = (unsigned)((s->n + 255) / 256);
@@ -1840,6 +1865,7 @@ void launch_map(vm_solver* s) {
   float alo, ahi;
   alpha_bounds(s->g.alpha, alo, ahi);
   int ps = prof_begin(s, KID_MAP_CLEAR);
+  if (s->g.fth_on) launch_domain_rect(s);
   k_map_begin<<<1, 32, 0, s->stream>>>(s->ds);
   prof_end(s, ps);
   // tier 0 (two elements per warp), its escapes to tier 1 through the first
@@ -1881,6 +1907,7 @@ void launch_map(vm_solver* s) {
   prof_end(s, ps);
   ps = prof_begin(s, KID_RESOLVE);
   k_resolve<<<(unsigned)std::min<size_t>(152, (s->n + 1023) / 1024), 256, 0, s->stream>>>(s->g, S);
+  if (s->g.fth_on) launch_clear_outside(s);
   prof_end(s, ps);
   unsigned nb = (unsigned)((s->n / 4 + 255) / 256);
   if (nb > 152 * 16) nb = 152 * 16;
@@ -1898,7 +1925,7 @@ void launch_read_map(vm_solver* s, int32_t* dst) {
   unsigned nb = (unsigned)((s->n + 255) / 256);
   if (nb > 152 * 16) nb = 152 * 16;
   const int ps = prof_begin(s, KID_READ_MAP);
-  k_read_map<<<nb, 256, 0, s->stream>>>(s->map, s->ds, dst, s->n);
+  k_read_map<<<nb, 256, 0, s->stream>>>(s->map, s->ds, dst, s->n, s->g.ne);
   prof_end(s, ps);
   s->launches++;
 }

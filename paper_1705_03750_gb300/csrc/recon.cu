@@ -63,6 +63,34 @@ __device__ __forceinline__ int owner(const uint32_t* __restrict__ map, size_t p,
   return ((t >> 24) == epoch && m < ne) ? m : -1;
 }
 
+// The columns [j0, j1] of row i inside the map's computing domain (the whole
+// row unless the adaptive domain is on; empty when j0 > j1).
+__device__ __forceinline__ void row_span(const Grid& g, const DevState* ds, int i, int& j0, int& j1) {
+  j0 = 0;
+  j1 = g.nv - 1;
+  if (g.fth_on) {
+    const int i0 = ds->rect[0], i1 = ds->rect[1];
+    if (i < i0 || i > i1) {
+      j0 = g.nv;
+      j1 = -1;
+    } else {
+      j0 = max(ds->rect[2], 0);
+      j1 = min(ds->rect[3], g.nv - 1);
+    }
+  }
+}
+
+// Zeros of row `row` outside [j0, j1].
+template <typename R>
+__device__ __forceinline__ void zero_outside(const Grid& g, R* __restrict__ row, int j0, int j1) {
+  if (j0 > j1) {
+    for (int j = threadIdx.x; j < g.nv; j += blockDim.x) row[j] = R(0);
+    return;
+  }
+  for (int j = threadIdx.x; j < j0; j += blockDim.x) row[j] = R(0);
+  for (int j = j1 + 1 + threadIdx.x; j < g.nv; j += blockDim.x) row[j] = R(0);
+}
+
 __global__ void __launch_bounds__(256) k_recon64(Grid g, const uint32_t* __restrict__ map, const DevState* ds,
                                                  const double* __restrict__ tay, const double* __restrict__ fini,
                                                  double* __restrict__ f, double* __restrict__ M) {
@@ -70,8 +98,11 @@ __global__ void __launch_bounds__(256) k_recon64(Grid g, const uint32_t* __restr
   __shared__ double sh[32];
   const int i = blockIdx.x;
   const double Px = site_x(g, i);
+  int js, je;
+  row_span(g, ds, i, js, je);
+  zero_outside(g, f + (size_t)i * g.nv, js, je);
   double acc = 0.0;
-  for (int j = threadIdx.x; j < g.nv; j += blockDim.x) {
+  for (int j = js + threadIdx.x; j <= je; j += blockDim.x) {
     const size_t p = (size_t)i * g.nv + j;
     const int m = owner(map, p, ds_epoch(ds), g.ne);
     double val = 0.0;
@@ -118,7 +149,7 @@ __device__ __forceinline__ void blended_q(const Grid& g, const double* __restric
     for (int b = b0; b <= b1; b++) {
       if (full && a != 0 && b != 0) continue;
       const int kk = k + a, ll = l + b;
-      if (kk < 0 || kk >= g.Lx || ll < 0 || ll >= g.Lv) continue;
+      if (!elem_exists(g, kk, ll)) continue;
       const double* t = tay + (size_t)(kk * g.Lv + ll) * TY_N;
       double dqx, dqv;
       qofp_exact(t, Px, Pv, dqx, dqv);
@@ -193,7 +224,10 @@ __global__ void __launch_bounds__(256) k_remap64(Grid g, const uint32_t* __restr
   using R = double;
   const int i = blockIdx.x;
   const double Px = site_x(g, i);
-  for (int j = threadIdx.x; j < g.nv; j += blockDim.x) {
+  int js, je;
+  row_span(g, ds, i, js, je);
+  zero_outside(g, out + (size_t)i * g.nv, js, je);
+  for (int j = js + threadIdx.x; j <= je; j += blockDim.x) {
     const size_t p = (size_t)i * g.nv + j;
     const int m = owner(map, p, ds_epoch(ds), g.ne);
     double val = 0.0;
@@ -469,12 +503,15 @@ __global__ void __launch_bounds__(256, 6) k_recon32(Grid g, const uint32_t* __re
   const uint32_t epoch = ds_epoch(ds);
   FPair acc;
   const float inv_Lv = 1.0f / (float)g.Lv;
-  // the owner of the thread's next site is loaded one iteration ahead
   const size_t row = (size_t)i * g.nv;
-  int m = (threadIdx.x < g.nv) ? owner(map, row + threadIdx.x, epoch, g.ne) : -1;
-  for (int j = threadIdx.x; j < g.nv; j += blockDim.x) {
+  int js, je;
+  row_span(g, ds, i, js, je);
+  zero_outside(g, f + row, js, je);
+  // the owner of the thread's next site is loaded one iteration ahead
+  int m = (js + (int)threadIdx.x <= je) ? owner(map, row + js + threadIdx.x, epoch, g.ne) : -1;
+  for (int j = js + threadIdx.x; j <= je; j += blockDim.x) {
     const int jn = j + blockDim.x;
-    const int mn = (jn < g.nv) ? owner(map, row + jn, epoch, g.ne) : -1;
+    const int mn = (jn <= je) ? owner(map, row + jn, epoch, g.ne) : -1;
     bool slow;
     float v = recon_fast32(g, tayf, fini, i, j, m, inv_Lv, &slow);
     if (slow) v = recon_site32(g, tay, tayf, fini, i, j, m);
@@ -545,7 +582,10 @@ __global__ void __launch_bounds__(256) k_remap32(Grid g, const uint32_t* __restr
                                                  float bhi) {
   const int i = blockIdx.x;
   const float inv_s = 1.0f / (float)g.s, fs = (float)g.s;
-  for (int j = threadIdx.x; j < g.nv; j += blockDim.x) {
+  int js, je;
+  row_span(g, ds, i, js, je);
+  zero_outside(g, out + (size_t)i * g.nv, js, je);
+  for (int j = js + threadIdx.x; j <= je; j += blockDim.x) {
     const size_t p = (size_t)i * g.nv + j;
     const int m = owner(map, p, ds_epoch(ds), g.ne);
     float val = 0.f;
@@ -570,7 +610,7 @@ __global__ void __launch_bounds__(256) k_remap32(Grid g, const uint32_t* __restr
           for (int b = b0; b <= b1; b++) {
             if (full && a != 0 && b != 0) continue;
             const int kk = k + a, ll = l + b;
-            if (kk < 0 || kk >= g.Lx || ll < 0 || ll >= g.Lv) continue;
+            if (!elem_exists(g, kk, ll)) continue;
             const float* Fn = tayf + (size_t)(kk * g.Lv + ll) * TF_N;
             float pxn, pvn;
             p_of(Fn, i, j, inv_s, pxn, pvn);

@@ -45,6 +45,7 @@ class VmConfig(C.Structure):
         ("precision", C.c_int32), ("alpha", C.c_double), ("beta", C.c_double),
         ("pad", C.c_int32), ("literal_fd", C.c_int32), ("max_hole_rounds", C.c_int32),
         ("map_windows", C.c_int32), ("emap_remap", C.c_double), ("c_dyn", C.c_double),
+        ("f_th", C.c_double),
     ]
 
 
@@ -55,7 +56,8 @@ class VmDiag(C.Structure):
                 ("tier1_more", C.c_int32), ("last_tier_elements", C.c_int32),
                 ("exact_tests", C.c_int32), ("bad_where", C.c_int32), ("entropy", C.c_double),
                 ("l1", C.c_double), ("l2", C.c_double), ("emap", C.c_double), ("emap_remaps", C.c_int64),
-                ("time", C.c_double), ("last_dt", C.c_double)]
+                ("time", C.c_double), ("last_dt", C.c_double),
+                ("lattice_range", C.c_int32 * 4), ("site_rect", C.c_int32 * 4)]
 
 
 class VmKernelStat(C.Structure):
@@ -155,6 +157,7 @@ class Config:
     map_windows: int = 0
     emap_remap: float = 0.0
     c_dyn: float = 0.0
+    f_th: float = 0.0
 
     @classmethod
     def from_run(cls, rc, precision: int = VM_FP64) -> "Config":
@@ -163,7 +166,7 @@ class Config:
     def c(self) -> VmConfig:
         return VmConfig(self.nx, self.nv, self.x_lo, self.x_hi, self.v_lo, self.v_hi, self.s, self.dt,
                         self.n_s, self.G, self.precision, self.alpha, self.beta, self.pad, self.literal_fd,
-                        self.max_hole_rounds, self.map_windows, self.emap_remap, self.c_dyn)
+                        self.max_hole_rounds, self.map_windows, self.emap_remap, self.c_dyn, self.f_th)
 
 
 def workspace_bytes(cfg: Config) -> int:
@@ -357,7 +360,10 @@ class Solver:
     def diagnostics(self) -> dict:
         d = VmDiag()
         _check(self.L.vm_diagnostics(self.h, C.byref(d)), "vm_diagnostics")
-        return {k: getattr(d, k) for k, _ in VmDiag._fields_}
+        out = {k: getattr(d, k) for k, _ in VmDiag._fields_}
+        for k in ("lattice_range", "site_rect"):
+            out[k] = tuple(int(x) for x in out[k])
+        return out
 
     def profile(self, enable: bool = True) -> None:
         """Start (or stop) per-kernel event timing; resets the totals."""
