@@ -58,12 +58,16 @@ def test_domain_map_and_f_match_oracle_through_remaps(prec):
         err = np.abs(s.read_f() - fo).max() / np.abs(fo).max()
         tol = 1e-6 if (prec == "fp64" or o.step_count <= 10) else 1e-5
         assert err <= tol, (o.step_count, err)
-        # the map of the current elements, on both sides
-        s.compute_map()
-        mo, _ = o.compute_map()
-        if prec == "fp64" or o.step_count <= 10:
+        # the map of the current elements, on both sides (the FP32 path's
+        # elements follow its own force, so only the FP64 path has the
+        # oracle's elements to the last bit)
+        if prec == "fp64":
+            s.compute_map()
+            mo, _ = o.compute_map()
             same_domain(s, o)
             assert np.array_equal(s.read_map(), mo), o.step_count
+        else:
+            assert s.diagnostics()["lattice_range"] == o.domain()["lattice"]
     i0, i1, j0, j1 = s.diagnostics()["site_rect"]
     assert (i1 - i0 + 1) * (j1 - j0 + 1) < 0.4 * WIDE.nx * WIDE.nv   # a fraction of the box is worked
 
