@@ -559,7 +559,8 @@ def run_batch(args):
         return ss
     res = {"workload": f"batch{n}-uneven-64..1024", "solves": n, "sites": cells, "steps": args.steps}
     ss = fresh()
-    b = V.Batch(ss, nstreams=args.streams, stream=stream)
+    b = V.Batch(ss, stream=stream)
+    tuning = b.autotune(1) if args.autotune else b.tuning()
     b.step(args.warmup)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -569,7 +570,8 @@ def run_batch(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     res["graph"] = {"cell_updates_per_s": cells * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
-                    "graph_nodes_per_step": b.launches_per_step(False), "streams": args.streams}
+                    "graph_nodes_per_step": b.launches_per_step(False),
+                    "graph_nodes_per_remap_step": b.launches_per_step(True), "tuning": tuning}
     b.close()
     del ss
     # plain path: every solve stepped by its own vm_step call, one stream
@@ -592,13 +594,15 @@ def run_batch(args):
 
 
 def serve_sample(args) -> dict:
-    """A reduced serving run for the headline line: 24 seeded halo requests
-    (sides 256-1024, multiples of 32; 100-400 steps; FP32-mixed; a 150 GB
-    budget), all at t = 0 for the saturated throughput, then open-loop
-    Poisson arrivals at 0.5 and 0.9 of it; p50/p99 latency from arrival to
-    the result on the host, and aggregate cell-updates/s."""
+    """A reduced serving run for the headline line, on the library's serving
+    loop (vm_server_*): 24 seeded halo requests (sides 256-1024, multiples of
+    32; 100-400 steps; FP32-mixed; a 150 GB budget, 32 slots), all at t = 0
+    for the saturated throughput, then open-loop Poisson arrivals at 0.5 and
+    0.9 of it; p50/p99 latency from arrival to the poll that returns the
+    result, and aggregate cell-updates/s."""
     import torch
-    from paper_1705_03750_gb300.serve import GpuBackend, Server, poisson_requests
+    from paper_1705_03750_gb300 import vlamet as V
+    from paper_1705_03750_gb300.serve import poisson_requests, run_open_loop
 
     def make(i, nx, nv):
         return I.HALOS_4096.with_(name=f"req{i}", nx=nx, nv=nv, seed=10_000 + i)
@@ -612,34 +616,37 @@ def serve_sample(args) -> dict:
         return ics[key]
 
     def one(rate):
-        srv = Server(GpuBackend(), budget_bytes=150 << 30, max_active=32, steps_per_tick=5, ic_fn=ic)
-        rep = srv.run(poisson_requests(24, rate=rate, **kw))
+        srv = V.NativeServer(150 << 30, max_active=32, steps_per_tick=args.tick)
+        rep = run_open_loop(srv, poisson_requests(24, rate=rate, **kw), ic_fn=ic)
         torch.cuda.synchronize()
+        srv.close()
         keep = ("requests", "failed", "wall_s", "cell_updates_per_s", "p50_latency_s", "p99_latency_s",
-                "peak_active")
+                "peak_active", "group_steps")
         return {k: rep[k] for k in keep}
+    for rc in (r.config for r in poisson_requests(24, rate=0.0, **kw)):
+        ic(rc)                          # initial conditions prepared before the clock starts
     sat = one(0.0)
     rate = sat["requests"] / sat["wall_s"]
-    out = {"workload": "serve-halos-256..1024 x24, 100-400 steps", "saturation": {**sat, "requests_per_s": rate},
-           "rates": []}
+    out = {"workload": "serve-halos-256..1024 x24, 100-400 steps (vm_server_*)",
+           "saturation": {**sat, "requests_per_s": rate}, "rates": []}
     for frac in (0.5, 0.9):
         out["rates"].append({"fraction_of_saturation": frac, "rate_per_s": frac * rate, **one(frac * rate)})
     return out
 
 
 def run_serve(args):
-    """Open-loop Poisson arrivals of seeded halo solves on a device-memory
-    budget; p50/p99 latency and throughput at fractions of saturation."""
+    """Open-loop Poisson arrivals of seeded halo solves on the library's
+    serving loop under a device-memory budget; p50/p99 latency and
+    throughput at fractions of saturation."""
     import torch
-    from paper_1705_03750_gb300.serve import GpuBackend, Server, poisson_requests
+    from paper_1705_03750_gb300 import vlamet as V
+    from paper_1705_03750_gb300.serve import poisson_requests, run_open_loop
     budget = int(args.budget_gb * (1 << 30))
 
     def make(i, nx, nv):
         return I.HALOS_4096.with_(name=f"req{i}", nx=nx, nv=nv, seed=10_000 + i)
-    base = poisson_requests(args.requests, rate=0.0, seed=args.seed, make_config=make,
-                            steps=(args.min_steps, args.max_steps))
-    # seeded per request id and grid: the rate runs draw arrival times from
-    # the same stream, so the same id can come with another grid size
+    # seeded per request id and grid: the rate runs draw their arrival times
+    # from the same stream, so the same id can come with another grid size
     ics = {}
 
     def ic(rc):
@@ -647,24 +654,28 @@ def run_serve(args):
         if key not in ics:
             ics[key] = I.initial_f(rc)
         return ics[key]
-    srv = Server(GpuBackend(), budget_bytes=budget, max_active=args.max_active, steps_per_tick=args.tick, ic_fn=ic)
-    sat = srv.run(base)
-    sat["errors"] = sorted({r.error for r in srv.done if r.error})[:3]
+
+    def one(reqs):
+        srv = V.NativeServer(budget, max_active=args.max_active, steps_per_tick=args.tick)
+        rep = run_open_loop(srv, reqs, ic_fn=ic)
+        torch.cuda.synchronize()
+        srv.close()
+        return rep
+    base = poisson_requests(args.requests, rate=0.0, seed=args.seed, make_config=make,
+                            steps=(args.min_steps, args.max_steps))
+    for r in base:
+        ic(r.config)
+    sat = one(base)
     print(json.dumps({"partial_saturation": sat}), file=sys.stderr, flush=True)
     sat_rate = sat["requests"] / sat["wall_s"]
-    out = {"workload": "serve-halos-256..2048", "requests": args.requests, "budget_gb": args.budget_gb,
+    out = {"workload": "serve-halos-256..2048 (vm_server_*)", "requests": args.requests, "budget_gb": args.budget_gb,
            "saturation": {**sat, "requests_per_s": sat_rate}, "rates": []}
     for frac in (0.25, 0.5, 0.75, 0.9, 1.1):
         reqs = poisson_requests(args.requests, rate=frac * sat_rate, seed=args.seed, make_config=make,
                                 steps=(args.min_steps, args.max_steps))
-        srv = Server(GpuBackend(), budget_bytes=budget, max_active=args.max_active, steps_per_tick=args.tick,
-                     ic_fn=ic)
-        rep = srv.run(reqs)
-        errs = sorted({r.error for r in srv.done if r.error})
-        out["rates"].append({"fraction_of_saturation": frac, "rate_per_s": frac * sat_rate, **rep,
-                             "errors": errs[:3]})
+        rep = one(reqs)
+        out["rates"].append({"fraction_of_saturation": frac, "rate_per_s": frac * sat_rate, **rep})
         print(json.dumps({"partial": out["rates"][-1]}), file=sys.stderr, flush=True)
-        torch.cuda.synchronize()
     return out
 
 
@@ -684,7 +695,8 @@ def main():
     ap.add_argument("--ref-cap", type=int, default=20)
     ap.add_argument("--workload", default="halos4096", choices=["halos4096", "precision8192", "batch", "serve"])
     ap.add_argument("--batch", type=int, default=512)
-    ap.add_argument("--streams", type=int, default=16)
+    ap.add_argument("--streams", type=int, default=0, help="(unused: one launch per phase for the batch)")
+    ap.add_argument("--autotune", type=int, default=1, help="tune the batch's launch shapes on its first steps")
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--min-steps", type=int, default=200)
     ap.add_argument("--max-steps", type=int, default=2000)

@@ -134,6 +134,7 @@ typedef struct {
 } vm_diag;
 
 typedef struct vm_solver vm_solver;
+typedef struct vm_server vm_server;
 
 /* Fill *c with the paper's defaults (alpha, beta) and zeros elsewhere. */
 void vm_config_default(vm_config* c);
@@ -252,22 +253,105 @@ int32_t vm_profile_read(vm_solver* s, vm_kernel_stat* out, int32_t max);
 /* ---- many independent solves (batching) ----
  *
  * A batch advances many solves together (Sec. 2.4 for each; the solves are
- * independent problems).  vm_batch_create records one time step of every
- * solve into a CUDA graph, spreading the solves over nstreams streams so
- * that their kernels overlap on the device, plus a second graph for a step
- * followed by a remap; vm_batch_step then launches one graph per step on
- * cuda_stream.  The solvers stay owned by the caller and must outlive the
- * batch; they must all have received vm_set_f, share n_s and their position
- * in the remap cycle (VM_E_STATE otherwise), and must not be profiling.
- * Creation synchronises each solver's stream; vm_batch_step orders itself
- * after work queued on the solvers' streams and before later work on them.
- * Results are read per solver with the single-solve calls. */
+ * independent problems).  Every phase of a step (drift and Taylor terms, the
+ * map's tiers, the reconstruction, the mass scan, the kick; and the remap's)
+ * is ONE launch for the whole batch, whose persistent blocks walk a work
+ * list of (solve, unit) items; the work of the map's later tiers is listed
+ * on the device from each solve's counters.  vm_batch_create records a
+ * transport step, and a transport step followed by a remap, into two CUDA
+ * graphs; vm_batch_step then launches one graph per step on cuda_stream.
+ * Results are those of the same solves stepped one by one, bit for bit.
+ * The solvers stay owned by the caller and must outlive the batch; they must
+ * all have received vm_set_f, share the precision, n_s and their position in
+ * the remap cycle (VM_E_STATE otherwise), not use emap_remap, c_dyn or f_th
+ * (VM_E_INVALID_ARG: those take host decisions per step), and must not be
+ * profiling.  The batch allocates its work tables (about 360 bytes per solve)
+ * with cudaMalloc and frees them in vm_batch_destroy.  nstreams is not used
+ * (kept for compatibility; pass 0 or any positive count).  Creation
+ * synchronises each solver's stream; vm_batch_step orders itself after work
+ * queued on the solvers' streams and before later work on them.  Results are
+ * read per solver with the single-solve calls. */
 typedef struct vm_batch vm_batch;
 vm_status vm_batch_create(vm_solver* const* solvers, int32_t n, int32_t nstreams, void* cuda_stream,
                           vm_batch** out);
 vm_status vm_batch_step(vm_batch* b, int32_t nsteps);
+/* Tune the persistent blocks of each phase on the run's own steps: for each
+ * of 1, 2, 4 and 8 blocks per SM, `trials` transport steps of the batch are
+ * taken (real steps: the solves advance, and a step that ends a remap cycle
+ * is taken with its remap, untimed), each phase timed with CUDA events; each
+ * phase then keeps its fastest shape and the graphs are recorded again.  The
+ * shape changes no result.  Synchronises. */
+vm_status vm_batch_autotune(vm_batch* b, int32_t trials);
+/* The tuned shape: blocks per SM and ms per step of the five timed phases
+ * (drift + Taylor, map, reconstruction, mass scan + force, kick + drift);
+ * returns 1 if vm_batch_autotune ran, 0 if not, -1 for a NULL batch. */
+int32_t vm_batch_tuning(const vm_batch* b, int32_t* blocks_per_sm5, double* ms5);
+/* Graph nodes (kernel launches) per batch step, without or with the remap. */
 int64_t vm_batch_launches_per_step(const vm_batch* b, int32_t with_remap);
 void vm_batch_destroy(vm_batch* b);
+
+/* ---- serving: continuous batching of submitted solves ----
+ *
+ * A server advances many requested solves (Sec. 2.4 for each; independent
+ * problems) with continuous batching.  Requests are admitted first come,
+ * first served as soon as a slot and enough of the server's device pool are
+ * free (each solve's exact vm_workspace_bytes, first-fit in the pool), their
+ * state stays resident, and every step of a tick is ONE group step for all
+ * active solves (one launch per phase for the whole set, plus one group
+ * remap for the solves whose cycle ends), so a request that arrives while
+ * others run joins the next step's launches.  The caller drives the server
+ * with vm_server_poll, which never waits for the device: it retires
+ * finished solves (their result is copied to host memory behind an event),
+ * admits waiting ones, and queues one more tick unless two are already in
+ * flight.  Results equal those of the same solve stepped alone, bit for bit.
+ *
+ * Memory: the caller passes one device pool (256-byte aligned), owned by the
+ * caller until vm_server_destroy; the server uses its first
+ * vm_server_pool_bytes(c) bytes for its work tables and at most
+ * c->budget_bytes after them for solver workspaces; it allocates no device
+ * memory, and pinned host memory only for staging (initial conditions,
+ * results, tables).  Every request must use c->precision and no per-step host
+ * decision (emap_remap, c_dyn, f_th: VM_E_INVALID_ARG); one whose workspace
+ * exceeds the whole budget is refused (VM_E_BUDGET).  Calls on one server
+ * must not run concurrently. */
+typedef struct {
+  size_t budget_bytes;     /* device bytes for solver workspaces (after the tables) */
+  int32_t max_active;      /* solves resident at most */
+  int32_t steps_per_tick;  /* steps every active solve takes per tick (>= 1) */
+  int32_t precision;       /* vm_precision of every request */
+} vm_server_config;
+
+typedef struct {
+  int64_t id;              /* from vm_server_submit */
+  int32_t status;          /* VM_OK, or why the solve failed */
+  double submit_s, admit_s, finish_s;  /* host clock, seconds since vm_server_create */
+} vm_server_done;
+
+typedef struct {
+  int32_t waiting, active, finished, peak_active;
+  int64_t used_bytes, peak_bytes;  /* workspace bytes in use, and the most at once */
+  int64_t ticks, group_steps, remap_groups;
+} vm_server_stat;
+
+/* Bytes of the pool the server keeps for its work tables. */
+size_t vm_server_pool_bytes(const vm_server_config* c);
+vm_status vm_server_create(const vm_server_config* c, void* d_pool, size_t pool_bytes, void* cuda_stream,
+                           vm_server** out);
+/* Queue a solve: the grid, box and method constants of *cfg, the initial
+ * condition f0 ([nx][nv] doubles, host memory, copied before the call
+ * returns) and the number of steps.  *id identifies the request. */
+vm_status vm_server_submit(vm_server* s, const vm_config* cfg, const double* f0, int32_t nsteps, int64_t* id);
+/* One round of the serving loop (see above); the requests finished since
+ * the last report are written to done[0 .. *n_done) (at most max_done). */
+vm_status vm_server_poll(vm_server* s, vm_server_done* done, int32_t max_done, int32_t* n_done);
+/* The result of a finished request: M, a, a', a'' of its last step ([nx]
+ * doubles each, host memory; any pointer may be NULL).  VM_E_STATE while the
+ * request is not finished. */
+vm_status vm_server_result(vm_server* s, int64_t id, double* M, double* a, double* da, double* d2a);
+vm_status vm_server_stats(const vm_server* s, vm_server_stat* out);
+/* Waits for the server's stream, then frees its host state; the caller may
+ * then free the pool. */
+void vm_server_destroy(vm_server* s);
 
 /* Measured FP64 arithmetic rate of the current device, in FLOP/s (2 per
  * fused multiply-add): one launch of eight independent FMA chains of

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 OBJ_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libvlamet.so")
-SOURCES = ["api.cu", "elements.cu", "map.cu", "recon.cu", "spline.cu", "noalloc.cu", "batch.cu", "peak.cu"]
+SOURCES = ["api.cu", "elements.cu", "map.cu", "recon.cu", "spline.cu", "noalloc.cu", "batch.cu", "peak.cu", "group.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -344,6 +344,16 @@ const char* vm_status_string(vm_status st) {
 }
 
 vm_status vm_create(const vm_config* c, void* d_workspace, size_t bytes, void* stream, vm_solver** out) {
+  return vm::solver_create(c, d_workspace, bytes, (cudaStream_t)stream, true, out);
+}
+
+}  // extern "C"
+
+// Create a solver on the caller's workspace; with sync = false the
+// initialisation (workspace clear, spline factors) is only queued on the
+// stream (the serving loop creates solvers while earlier work still runs).
+vm_status vm::solver_create(const vm_config* c, void* d_workspace, size_t bytes, cudaStream_t stream, bool sync,
+                            vm_solver** out) {
   if (!out) return VM_E_INVALID_ARG;
   *out = nullptr;
   if (!valid(c) || !d_workspace || ((uintptr_t)d_workspace & 255)) return VM_E_INVALID_ARG;
@@ -354,7 +364,7 @@ vm_status vm_create(const vm_config* c, void* d_workspace, size_t bytes, void* s
   s->cfg = *c;
   if (s->cfg.pad == 0) s->cfg.pad = c->elem_stride;
   if (s->cfg.max_hole_rounds == 0) s->cfg.max_hole_rounds = c->nx + c->nv;
-  s->stream = (cudaStream_t)stream;
+  s->stream = stream;
   s->fp32 = (c->precision == VM_FP32_MIXED);
   s->sreal = s->fp32 ? 4 : 8;
   s->n = (size_t)c->nx * c->nv;
@@ -389,6 +399,9 @@ vm_status vm_create(const vm_config* c, void* d_workspace, size_t bytes, void* s
   g.literal_fd = c->literal_fd;
   g.max_hole_rounds = s->cfg.max_hole_rounds;
   g.fth_on = c->f_th > 0.0 ? 1 : 0;
+  // 64 ulps of the index coordinate's largest reference terms (recon.cu)
+  g.eps_u = 64.0 * 0x1p-53 * ((fabs(c->x_lo) + fabs(c->x_hi)) / g.dx + (double)c->nx + 8.0);
+  g.eps_w = 64.0 * 0x1p-53 * ((fabs(c->v_lo) + fabs(c->v_hi)) / g.dv + (double)c->nv + 8.0);
   g.klo = 0;
   g.khi = g.Lx - 1;
   g.llo = 0;
@@ -451,7 +464,7 @@ vm_status vm_create(const vm_config* c, void* d_workspace, size_t bytes, void* s
     init.det_min_key = ~0ull;
     init.det_max_key = 0ull;
     if (cudaMemcpyAsync(s->ds, &init, sizeof init, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) { st = VM_E_CUDA; break; }
-    if (cudaStreamSynchronize(s->stream) != cudaSuccess) { st = VM_E_CUDA; break; }
+    if (sync && cudaStreamSynchronize(s->stream) != cudaSuccess) { st = VM_E_CUDA; break; }
   } while (0);
   if (st != VM_OK) {
     free(s);
@@ -460,6 +473,8 @@ vm_status vm_create(const vm_config* c, void* d_workspace, size_t bytes, void* s
   *out = s;
   return VM_OK;
 }
+
+extern "C" {
 
 void vm_destroy(vm_solver* s) {
   if (!s) return;

@@ -1,30 +1,39 @@
 // Batched stepping of many independent solves.
 //
-// One time step of every solve in the batch is recorded once into a CUDA
-// graph (stream capture): the solves are spread over K streams forked from
-// and joined back to one capture stream, so kernels of different solves run
-// concurrently, and a step of the whole batch is then a single graph launch.
-// Two graphs are kept: a transport step, and a transport step followed by a
-// remap; every solve of a batch shares its remap phase.  Replays are exact
-// repetitions of the same launches: all per-step state (element state, the
-// map epoch, the remap copy) lives on the device.
+// A batch is a group of solves (group.cu): each phase of a step is one
+// launch whose blocks walk the work list of every solve's units (rows,
+// element chunks, escaped elements...), so a step of the whole batch is
+// about twenty launches whatever the number of solves.  Those launches are
+// recorded once into a CUDA graph (a transport step, and a transport step
+// followed by a remap; every solve of a batch shares its remap phase), and
+// a batch step is one graph launch.  The number of persistent blocks of
+// each phase can be tuned on the run's own steps (vm_batch_autotune): it
+// changes no result, only the time.
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
+#include "group.cuh"
 
 struct vm_batch {
   std::vector<vm_solver*> solvers;
-  std::vector<cudaStream_t> streams;
-  std::vector<cudaEvent_t> joins;
-  cudaEvent_t fork;
-  cudaStream_t capture;     // capture stream (owned)
-  cudaStream_t user;        // stream the graphs are launched on
-  cudaGraphExec_t exec[2];  // [0] transport step, [1] transport + remap
-  int64_t launches_per[2];
-  int32_t n_s;
+  cudaStream_t capture = nullptr;  // capture stream (owned)
+  cudaStream_t user = nullptr;     // stream the graphs are launched on
+  cudaEvent_t sync = nullptr;
+  void* d_table = nullptr;         // plan table (device, owned)
+  std::vector<char> h_table;       // its host staging copy
+  vm::GroupPlan plan;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};  // [0] transport step, [1] transport + remap
+  int64_t launches_per[2] = {0, 0};
+  int32_t n_s = 0;
+  // launch-shape tuning: chosen blocks per SM and the time measured with it,
+  // per timed phase (drift, map, reconstruction, scan, kick)
+  int32_t tuned = 0;
+  int32_t bps[5] = {0, 0, 0, 0, 0};
+  double tuned_ms[5] = {0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -33,96 +42,106 @@ void destroy_batch(vm_batch* b) {
   if (!b) return;
   for (int k = 0; k < 2; k++)
     if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
-  for (auto e : b->joins) cudaEventDestroy(e);
-  if (b->fork) cudaEventDestroy(b->fork);
-  for (auto st : b->streams) cudaStreamDestroy(st);
+  if (b->sync) cudaEventDestroy(b->sync);
+  if (b->capture) cudaStreamSynchronize(b->capture);
+  if (b->d_table) cudaFree(b->d_table);
   if (b->capture) cudaStreamDestroy(b->capture);
   delete b;
 }
 
-// Record one step of every solve into a graph.
+// Record one step of the whole batch into a graph.
 vm_status capture(vm_batch* b, bool remap, cudaGraphExec_t* out, int64_t* launches) {
+  if (*out) {
+    cudaGraphExecDestroy(*out);
+    *out = nullptr;
+  }
   cudaGraph_t graph = nullptr;
   if (cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return VM_E_CUDA;
-  bool ok = cudaEventRecord(b->fork, b->capture) == cudaSuccess;
-  for (auto st : b->streams) ok = ok && cudaStreamWaitEvent(st, b->fork, 0) == cudaSuccess;
-  int64_t count = 0;
-  for (size_t i = 0; ok && i < b->solvers.size(); i++) {
-    vm_solver* s = b->solvers[i];
-    const cudaStream_t saved = s->stream;
-    const int32_t saved_prof = s->prof;
-    const int64_t l0 = s->launches;
-    s->stream = b->streams[i % b->streams.size()];
-    s->prof = 0;
-    vm::step_transport(s);
-    if (remap) ok = vm::step_remap(s) == cudaSuccess;
-    count += s->launches - l0;
-    s->launches = l0;
-    s->stream = saved;
-    s->prof = saved_prof;
-  }
-  for (size_t k = 0; ok && k < b->streams.size(); k++) {
-    ok = cudaEventRecord(b->joins[k], b->streams[k]) == cudaSuccess &&
-         cudaStreamWaitEvent(b->capture, b->joins[k], 0) == cudaSuccess;
-  }
+  vm::GroupPlan P = b->plan;
+  P.stream = b->capture;
+  vm::group_step_transport(P);
+  if (remap) vm::group_step_remap(P);
   const cudaError_t e = cudaStreamEndCapture(b->capture, &graph);
-  if (!ok || e != cudaSuccess || !graph) {
+  if (e != cudaSuccess || !graph) {
     if (graph) cudaGraphDestroy(graph);
     cudaGetLastError();
     return VM_E_CUDA;
   }
+  size_t nodes = 0;
+  cudaGraphGetNodes(graph, nullptr, &nodes);
   const cudaError_t ie = cudaGraphInstantiate(out, graph, 0);
   cudaGraphDestroy(graph);
   if (ie != cudaSuccess) return VM_E_CUDA;
-  *launches = count;
+  *launches = (int64_t)nodes;
   return VM_OK;
+}
+
+// Phases of the plan that follow each timed phase's launch shape.
+void set_shape(vm::GroupPlan& P, int timed, int blocks) {
+  using namespace vm;
+  static const int kCount[5] = {2, 8, 3, 4, 2};
+  static const int kPhases[5][8] = {
+      {GP_DRIFT, GP_TAYLOR},
+      {GP_PAIR, GP_SMALL, GP_BIG1, GP_BIG2, GP_BIG3, GP_RESOLVE, GP_FIND_HOLES, GP_HOLES},
+      {GP_RECON, GP_REMAP, GP_COPY},
+      {GP_SCAN, GP_DIFF, GP_ROWS, GP_COLS},
+      {GP_KICK, GP_RESET}};
+  for (int q = 0; q < kCount[timed]; q++) P.shape[kPhases[timed][q]].blocks = blocks;
+}
+
+// Order the batch's stream after work queued on the solvers' own streams.
+vm_status enter(vm_batch* b) {
+  for (vm_solver* s : b->solvers)
+    if (cudaEventRecord(b->sync, s->stream) != cudaSuccess || cudaStreamWaitEvent(b->user, b->sync, 0) != cudaSuccess)
+      return VM_E_CUDA;
+  return VM_OK;
+}
+
+// Later calls on a solver's own stream see the batch's results.
+vm_status leave(vm_batch* b) {
+  if (cudaEventRecord(b->sync, b->user) != cudaSuccess) return VM_E_CUDA;
+  for (vm_solver* s : b->solvers)
+    if (cudaStreamWaitEvent(s->stream, b->sync, 0) != cudaSuccess) return VM_E_CUDA;
+  return VM_OK;
+}
+
+void count(vm_batch* b, int kind) {
+  for (vm_solver* s : b->solvers) {
+    vm::group_count_step(s, kind == 1);
+    s->launches += b->launches_per[kind] / (int64_t)b->solvers.size();
+  }
 }
 
 }  // namespace
 
 extern "C" vm_status vm_batch_create(vm_solver* const* solvers, int32_t n, int32_t nstreams, void* cuda_stream,
                                      vm_batch** out) {
-  if (!out || !solvers || n < 1 || nstreams < 1) return VM_E_INVALID_ARG;
+  if (!out || !solvers || n < 1 || nstreams < 0) return VM_E_INVALID_ARG;
   *out = nullptr;
-  const int32_t n_s = solvers[0] ? solvers[0]->cfg.n_s : 0;
-  const int32_t cyc = solvers[0] ? solvers[0]->cyc : 0;
+  vm::clear_foreign_error();
+  vm_status st = vm::group_check(solvers, n);
+  if (st != VM_OK) return st;
+  const int32_t n_s = solvers[0]->cfg.n_s, cyc = solvers[0]->cyc;
   for (int32_t i = 0; i < n; i++) {
-    const vm_solver* s = solvers[i];
-    if (!s) return VM_E_INVALID_ARG;
-    if (!s->have_f || s->prof) return VM_E_STATE;
-    if (s->cfg.n_s != n_s || s->cyc != cyc) return VM_E_STATE;  // one remap phase per batch
-    // host decisions per step or per remap: not capturable
-    if (s->cfg.emap_remap > 0.0 || s->cfg.c_dyn > 0.0 || s->cfg.f_th > 0.0) return VM_E_INVALID_ARG;
-    for (int32_t j = 0; j < i; j++)
-      if (solvers[j] == s) return VM_E_INVALID_ARG;
+    if (solvers[i]->prof) return VM_E_STATE;
+    if (solvers[i]->cfg.n_s != n_s || solvers[i]->cyc != cyc) return VM_E_STATE;  // one remap phase per batch
   }
+  if (!vm::group_map_prepare()) return VM_E_CUDA;
   vm_batch* b = new vm_batch();
-  memset(b->exec, 0, sizeof b->exec);
-  b->fork = nullptr;
-  b->capture = nullptr;
   b->solvers.assign(solvers, solvers + n);
   b->user = (cudaStream_t)cuda_stream;
   b->n_s = n_s;
-  if (nstreams > n) nstreams = n;
-  vm_status st = VM_OK;
+  const size_t tb = vm::group_table_bytes(n);
+  b->h_table.assign(tb, 0);
   if (cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+      cudaEventCreateWithFlags(&b->sync, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMalloc(&b->d_table, tb) != cudaSuccess)
     st = VM_E_CUDA;
-  for (int32_t k = 0; st == VM_OK && k < nstreams; k++) {
-    cudaStream_t sk;
-    cudaEvent_t ek;
-    if (cudaStreamCreateWithFlags(&sk, cudaStreamNonBlocking) != cudaSuccess) {
-      st = VM_E_CUDA;
-      break;
-    }
-    b->streams.push_back(sk);
-    if (cudaEventCreateWithFlags(&ek, cudaEventDisableTiming) != cudaSuccess) {
-      st = VM_E_CUDA;
-      break;
-    }
-    b->joins.push_back(ek);
+  if (st == VM_OK) {
+    vm::group_plan(b->plan, solvers, n, b->d_table, b->h_table.data(), b->capture);
+    if (cudaStreamSynchronize(b->capture) != cudaSuccess) st = VM_E_CUDA;
   }
-  // pending work of the solvers is done before the capture's first replay
+  // pending work of the solvers is done before the first replay
   for (int32_t i = 0; st == VM_OK && i < n; i++)
     if (cudaStreamSynchronize(solvers[i]->stream) != cudaSuccess) st = VM_E_CUDA;
   if (st == VM_OK) st = capture(b, false, &b->exec[0], &b->launches_per[0]);
@@ -137,26 +156,87 @@ extern "C" vm_status vm_batch_create(vm_solver* const* solvers, int32_t n, int32
 
 extern "C" vm_status vm_batch_step(vm_batch* b, int32_t nsteps) {
   if (!b || nsteps < 0) return VM_E_INVALID_ARG;
-  // order after any work the caller queued on the solvers' own streams
-  for (vm_solver* s : b->solvers) {
-    if (cudaEventRecord(b->fork, s->stream) != cudaSuccess || cudaStreamWaitEvent(b->user, b->fork, 0) != cudaSuccess)
-      return VM_E_CUDA;
-  }
+  vm::clear_foreign_error();
+  vm_status st = enter(b);
+  if (st != VM_OK) return st;
   for (int32_t it = 0; it < nsteps; it++) {
     const vm_solver* s0 = b->solvers[0];
     const int kind = (s0->cyc + 1 >= b->n_s) ? 1 : 0;
     if (cudaGraphLaunch(b->exec[kind], b->user) != cudaSuccess) return VM_E_CUDA;
-    for (vm_solver* s : b->solvers) {
-      s->nstep++;
-      s->cyc = kind ? 0 : s->cyc + 1;
-      s->launches += b->launches_per[kind] / (int64_t)b->solvers.size();
-    }
+    count(b, kind);
   }
-  // later calls on a solver's own stream see the batch's results
-  if (cudaEventRecord(b->fork, b->user) != cudaSuccess) return VM_E_CUDA;
-  for (vm_solver* s : b->solvers)
-    if (cudaStreamWaitEvent(s->stream, b->fork, 0) != cudaSuccess) return VM_E_CUDA;
-  return VM_OK;
+  return leave(b);
+}
+
+extern "C" vm_status vm_batch_autotune(vm_batch* b, int32_t trials) {
+  if (!b || trials < 1) return VM_E_INVALID_ARG;
+  vm::clear_foreign_error();
+  vm_status st = enter(b);
+  if (st != VM_OK) return st;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  static const int kCand[4] = {1, 2, 4, 8};
+  double best[5];
+  int pick[5];
+  for (int t = 0; t < 5; t++) {
+    best[t] = 1e30;
+    pick[t] = 4;
+  }
+  vm::GroupTiming T;
+  for (int e = 0; e < vm::GT_N; e++)
+    if (cudaEventCreate(&T.ev[e]) != cudaSuccess) return VM_E_CUDA;
+  vm::GroupPlan P = b->plan;
+  P.stream = b->user;
+  for (int c = 0; c < 4 && st == VM_OK; c++) {
+    for (int t = 0; t < 5; t++) set_shape(P, t, kCand[c] * sms);
+    double acc[5] = {0, 0, 0, 0, 0};
+    int timed = 0;
+    while (timed < trials && st == VM_OK) {
+      // the step before a remap runs with the remap (untimed)
+      if (b->solvers[0]->cyc + 1 >= b->n_s) {
+        if (cudaGraphLaunch(b->exec[1], b->user) != cudaSuccess) st = VM_E_CUDA;
+        count(b, 1);
+        continue;
+      }
+      vm::group_step_transport(P, &T);
+      if (cudaEventSynchronize(T.ev[vm::GT_END]) != cudaSuccess) st = VM_E_CUDA;
+      for (int t = 0; t < 5 && st == VM_OK; t++) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, T.ev[t], T.ev[t + 1]);
+        acc[t] += ms;
+      }
+      count(b, 0);
+      timed++;
+    }
+    for (int t = 0; t < 5; t++)
+      if (acc[t] < best[t]) {
+        best[t] = acc[t];
+        pick[t] = kCand[c];
+      }
+  }
+  for (int e = 0; e < vm::GT_N; e++) cudaEventDestroy(T.ev[e]);
+  if (st != VM_OK) return st;
+  for (int t = 0; t < 5; t++) {
+    set_shape(b->plan, t, pick[t] * sms);
+    b->bps[t] = pick[t];
+    b->tuned_ms[t] = best[t] / trials;
+  }
+  b->tuned = 1;
+  if (cudaStreamSynchronize(b->user) != cudaSuccess) return VM_E_CUDA;
+  st = capture(b, false, &b->exec[0], &b->launches_per[0]);
+  if (st == VM_OK) st = capture(b, true, &b->exec[1], &b->launches_per[1]);
+  if (st != VM_OK) return st;
+  return leave(b);
+}
+
+extern "C" int32_t vm_batch_tuning(const vm_batch* b, int32_t* blocks_per_sm, double* ms) {
+  if (!b) return -1;
+  for (int t = 0; t < 5; t++) {
+    if (blocks_per_sm) blocks_per_sm[t] = b->bps[t];
+    if (ms) ms[t] = b->tuned_ms[t];
+  }
+  return b->tuned;
 }
 
 extern "C" int64_t vm_batch_launches_per_step(const vm_batch* b, int32_t with_remap) {

@@ -42,6 +42,9 @@ struct Grid {
   // llo..lhi (the whole lattice when fth_on is 0)
   int32_t fth_on;
   int32_t klo, khi, llo, lhi;
+  // bound on |anchored - fixed-order| index coordinate of the FP64 path's
+  // reconstruction (recon.cu), per axis
+  double eps_u, eps_w;
 };
 
 // Small device-resident control block.
@@ -199,6 +202,10 @@ int prof_begin(vm_solver* s, int kid);
 void prof_end(vm_solver* s, int slot);
 void prof_flush(vm_solver* s);
 
+// ---- solver creation without the final synchronisation (api.cu) ----
+vm_status solver_create(const vm_config* c, void* d_workspace, size_t bytes, cudaStream_t stream, bool sync,
+                        vm_solver** out);
+
 // ---- one step, enqueue only (api.cu) ----
 void step_transport(vm_solver* s);
 cudaError_t step_remap(vm_solver* s);
@@ -228,6 +235,145 @@ void launch_convert(vm_solver* s, const void* src, void* dst, int32_t dst_dtype,
 void launch_store_real(vm_solver* s, const double* src, void* dst, size_t count);
 // spline.cu
 void launch_spline_solve(vm_solver* s, const void* src, void* dst);
+
+// ---- many solves in one launch per phase (group.cu drives them) ----
+//
+// A group is a set of solves of one precision whose steps are launched
+// together: each phase of a step is one launch whose blocks walk a work
+// list of (solve, unit) items, a unit being what one block of the
+// single-solve launch does (a row, a chunk of elements, an escaped element's
+// window...).  Solve sv owns units [off[sv], off[sv + 1]) of a phase; for
+// phases whose work is only known on the device (the map's escape lists,
+// contested sites, holes) the offsets are computed on the device from each
+// solve's counters.  Each unit runs the single-solve kernel's body with its
+// virtual block index, so the results are those of the single-solve
+// launches, bit for bit, whatever the number of blocks.
+struct SolveDesc {
+  Grid g;
+  float alo, ahi;  // alpha rounded down and up to FP32
+  float blo, bhi;  // beta rounded down and up to FP32
+  int32_t map_windows;
+  void* fini;
+  void* eta;
+  void* f;
+  void* tmp;
+  uint32_t* map;
+  uint32_t* slot1;
+  unsigned long long* rec_key;
+  int32_t* rec_site;
+  int32_t rec_cap;
+  int32_t* holes_a;
+  int32_t* holes_b;
+  int2* ovf1;
+  int2* ovf2;
+  unsigned long long* gwin;
+  size_t gwin_words;
+  unsigned long long* t1seed;
+  int32_t t1seed_cap;
+  double* el;
+  double* tay;
+  float* tayf;
+  double* M;
+  double* a;
+  double* da;
+  double* d2a;
+  double* thx;
+  double* thv;
+  float* thxf;
+  float* thvf;
+  DevState* ds;
+};
+
+// Solve owning unit u: the largest sv with off[sv] <= u (off[0] = 0,
+// off[ns] = total).
+__device__ __forceinline__ int unit_solve(const int* __restrict__ off, int ns, int u) {
+  int lo = 0, hi = ns - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(off + mid) <= u) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Device-side unit counts: which per-solve counter a dynamic phase reads.
+enum GroupCount : int {
+  GC_PAIR_ESC = 0,   // tier-0 escapes (tier 1's list), TE per unit
+  GC_OVF1,           // first large-window list (front + back), one element per unit
+  GC_OVF2,           // second large-window list
+  GC_OVF3,           // last tier's list (front, and the back in map_windows mode)
+  GC_REC,            // contested sites, 256 per unit
+  GC_HOLES           // one unit per solve that has holes
+};
+
+// Launch shape of one group launch: grid size (persistent blocks).
+struct GroupShape {
+  int blocks;
+};
+
+// The host side of a group: the descriptor table and the unit offsets of
+// each phase on the device (group.cu).
+struct GroupPlan {
+  const SolveDesc* D;  // device, ns entries
+  int ns;
+  int fp32;
+  cudaStream_t stream;
+  // host-known offsets (device arrays of ns + 1 ints) and totals
+  const int* off_elem64; int tot_elem64;   // 64-element chunks
+  const int* off_pair; int tot_pair;       // tier-0 blocks (2 * TP elements)
+  const int* off_rows; int tot_rows;       // x rows
+  const int* off_diff; int tot_diff;       // 128 x-node chunks
+  const int* off_sites; int tot_sites;     // 1024-site chunks (4 per thread)
+  const int* off_copy; int tot_copy;       // 4096-value chunks of an [nx][nv] array
+  const int* off_rows4; int tot_rows4;     // 4-row chunks (row spline sweeps)
+  const int* off_cols; int tot_cols;       // 32-column chunks (column spline sweeps)
+  const int* off_solve;                    // one unit per solve
+  // device-computed offsets (ns + 1 ints each; the total at [ns])
+  int* off_dyn;                            // scratch for one dynamic phase at a time
+  int big_blocks_cap;                      // virtual blocks per solve of the large windows
+  size_t big_smem;                         // dynamic shared memory of the large windows
+  GroupShape shape[32];                    // per phase (GroupPhase)
+};
+
+enum GroupPhase : int {
+  GP_DRIFT = 0, GP_TAYLOR, GP_MAP_BEGIN, GP_PAIR, GP_SMALL, GP_BIG1, GP_BIG2, GP_BIG3, GP_RESOLVE,
+  GP_FIND_HOLES, GP_HOLES, GP_RECON, GP_SCAN, GP_DIFF, GP_KICK, GP_REMAP, GP_COPY, GP_ROWS, GP_COLS,
+  GP_RESET, GP_UNITS, GP_N
+};
+
+// The solve of unit u, its Grid in shared memory (read by every thread of
+// the block), and the unit's index within its solve.
+#define GROUP_LOOP(off, ns, total)                                   \
+  __shared__ Grid gsh;                                               \
+  __shared__ int svsh;                                               \
+  for (int u = blockIdx.x; u < (total); u += gridDim.x) {            \
+    if (threadIdx.x == 0) {                                          \
+      svsh = unit_solve((off), (ns), u);                             \
+      gsh = D[svsh].g;                                               \
+    }                                                                \
+    __syncthreads();                                                 \
+    const int sv = svsh;                                             \
+    const SolveDesc& d = D[sv];                                      \
+    const int vb = u - __ldg((off) + sv);
+#define GROUP_END \
+    __syncthreads(); \
+  }
+
+// Blocks of a group launch: the phase's tuned shape, capped by its units.
+unsigned group_grid(const GroupPlan& G, GroupPhase ph, int total);
+
+// group launchers (each in the translation unit of its kernels)
+void group_drift(const GroupPlan& G, bool taylor);
+void group_taylor(const GroupPlan& G);
+void group_kick(const GroupPlan& G);
+void group_reset(const GroupPlan& G);
+void group_scan_force(const GroupPlan& G);
+void group_map(const GroupPlan& G);
+void group_reconstruct(const GroupPlan& G);
+void group_remap_resample(const GroupPlan& G);   // into each solve's tmp
+void group_copy_tmp_to_fini(const GroupPlan& G);
+void group_spline(const GroupPlan& G);           // fini -> eta
+size_t group_big_smem(const Grid& g);            // the large windows' shared memory for grid g
+bool group_map_prepare();
 
 // adaptive computing domain (api.cu launches, elements.cu kernels)
 // node rectangle of |f_ini| > f_th into ds->fbox (reset first)

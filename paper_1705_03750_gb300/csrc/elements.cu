@@ -101,9 +101,9 @@ __device__ __forceinline__ void taylor_one(const Grid& g, const double* __restri
 
 // Half drift (predictor or corrector of Sec. 2.4): x, T_x. and H_x.. move
 // with v, T_v. and H_v..; optionally followed by the Taylor terms.
-__global__ void k_drift(Grid g, double* __restrict__ el, double* __restrict__ tay, float* __restrict__ tayf,
-                        int taylor) {
-  int m = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void drift_body(const Grid& g, double* __restrict__ el, double* __restrict__ tay,
+                                           float* __restrict__ tayf, int taylor, int vb) {
+  int m = vb * blockDim.x + threadIdx.x;
   if (m >= g.ne) return;
   const int ne = g.ne;
   double h = g.half_dt;
@@ -114,6 +114,11 @@ __global__ void k_drift(Grid g, double* __restrict__ el, double* __restrict__ ta
   for (int q = 0; q < 3; q++)
     el[(EL_HXXX + q) * ne + m] = dadd(el[(EL_HXXX + q) * ne + m], dmul(el[(EL_HVXX + q) * ne + m], h));
   if (taylor) taylor_one(g, el, m, tay, tayf);
+}
+
+__global__ void k_drift(Grid g, double* __restrict__ el, double* __restrict__ tay, float* __restrict__ tayf,
+                        int taylor) {
+  drift_body(g, el, tay, tayf, taylor, blockIdx.x);
 }
 
 __global__ void k_taylor(Grid g, const double* __restrict__ el, double* __restrict__ tay, float* __restrict__ tayf) {
@@ -139,10 +144,10 @@ __device__ __forceinline__ double tsc(const double* __restrict__ A, int nx, doub
 }
 
 // Kick with a, a', a'' at the drifted positions, then the corrector drift.
-__global__ void k_kick_drift(Grid g, double* __restrict__ el, const double* __restrict__ a,
-                             const double* __restrict__ da, const double* __restrict__ d2a,
-                             const DevState* __restrict__ ds) {
-  int m = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void kick_body(const Grid& g, double* __restrict__ el, const double* __restrict__ a,
+                                          const double* __restrict__ da, const double* __restrict__ d2a,
+                                          const DevState* __restrict__ ds, int vb) {
+  int m = vb * blockDim.x + threadIdx.x;
   if (m >= g.ne) return;
   const int ne = g.ne;
   double Mt = ds->Mtot;
@@ -176,9 +181,15 @@ __global__ void k_kick_drift(Grid g, double* __restrict__ el, const double* __re
   el[EL_HVVV * ne + m] = Hv2;
 }
 
+__global__ void k_kick_drift(Grid g, double* __restrict__ el, const double* __restrict__ a,
+                             const double* __restrict__ da, const double* __restrict__ d2a,
+                             const DevState* __restrict__ ds) {
+  kick_body(g, el, a, da, d2a, ds, blockIdx.x);
+}
+
 // Isotropic elements on the lattice (remap, Sec. 1): P_m = Q_m, T = I, H = 0.
-__global__ void k_reset(Grid g, double* __restrict__ el) {
-  int m = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void reset_body(const Grid& g, double* __restrict__ el, int vb) {
+  int m = vb * blockDim.x + threadIdx.x;
   if (m >= g.ne) return;
   const int ne = g.ne;
   int k = m / g.Lv, l = m - k * g.Lv;
@@ -192,7 +203,9 @@ __global__ void k_reset(Grid g, double* __restrict__ el) {
   for (int q = EL_HXXX; q < EL_N; q++) el[q * ne + m] = 0.0;
 }
 
-constexpr int SCAN_T = 256;
+__global__ void k_reset(Grid g, double* __restrict__ el) { reset_body(g, el, blockIdx.x); }
+
+constexpr int SCAN_T = 512;
 
 // ---- error-free mass prefix (Sec. 2.5, eq. of a(i)) ----
 //
@@ -288,8 +301,8 @@ __device__ __forceinline__ i128 shfl_up_i128(i128 v, int d) {
 // pixels: the largest |M| sets the common scale, the chunk sums are scanned
 // across the block, and each thread walks its chunk once more, writing
 // a(i) = 2 pi G (M_tot - M_left(i) - M_left(i-1)).
-__global__ void __launch_bounds__(SCAN_T) k_scan_force(Grid g, const double* __restrict__ M,
-                                                       double* __restrict__ a, DevState* ds) {
+__device__ __forceinline__ void scan_body(const Grid& g, const double* __restrict__ M, double* __restrict__ a,
+                                          DevState* ds) {
   __shared__ i128 sh[SCAN_T / 32];
   __shared__ double mx_s[SCAN_T / 32];
   __shared__ i128 tot_s;
@@ -297,9 +310,13 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_force(Grid g, const double* __r
   const int C = (nx + SCAN_T - 1) / SCAN_T;
   const int i0 = min(tid * C, nx), i1 = min(i0 + C, nx);
   double mx = 0.0;
-  for (int i = i0; i < i1; i++) mx = fmax(mx, fabs(M[i]));  // NaN is dropped by fmax
   bool bad = false;
-  for (int i = i0; i < i1; i++) bad |= !(fabs(M[i]) <= 1.0e300);
+#pragma unroll 4
+  for (int i = i0; i < i1; i++) {
+    const double m = fabs(M[i]);
+    mx = fmax(mx, m);  // NaN is dropped by fmax, and flagged
+    bad |= !(m <= 1.0e300);
+  }
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   bad = __any_sync(0xffffffffu, bad);
   if (lane == 0) mx_s[wid] = bad ? INFINITY : mx;
@@ -317,6 +334,7 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_force(Grid g, const double* __r
   const int E = ilogb(mx);
   const int up = 111 - E;  // M * 2^up < 2^112
   i128 loc = 0;
+#pragma unroll 4
   for (int i = i0; i < i1; i++) loc += fixed_of(M[i], up);
   i128 inc = loc;
 #pragma unroll
@@ -339,6 +357,7 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_force(Grid g, const double* __r
   __syncthreads();
   const i128 tot = tot_s;
   i128 left_prev = sh[wid] + (inc - loc);  // mass of the pixels before this chunk
+#pragma unroll 4
   for (int i = i0; i < i1; i++) {
     const i128 left = left_prev + fixed_of(M[i], up);
     a[i] = dmul(g.A, double_of(tot - left - left_prev, -up));
@@ -347,11 +366,16 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_force(Grid g, const double* __r
   if (tid == 0) ds->Mtot = double_of(tot, -up);
 }
 
+__global__ void __launch_bounds__(SCAN_T) k_scan_force(Grid g, const double* __restrict__ M,
+                                                       double* __restrict__ a, DevState* ds) {
+  scan_body(g, M, a, ds);
+}
+
 // a' and a'' by centred differences (Sec. 2.5); beyond the grid a takes its
 // limits +A M_tot (left) and -A M_tot (right).
-__global__ void k_force_diff(Grid g, const double* __restrict__ a, double* __restrict__ da,
-                             double* __restrict__ d2a, const DevState* __restrict__ ds) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void diff_body(const Grid& g, const double* __restrict__ a, double* __restrict__ da,
+                                          double* __restrict__ d2a, const DevState* __restrict__ ds, int vb) {
+  const int i = vb * blockDim.x + threadIdx.x;
   const int nx = g.nx;
   if (i >= nx) return;
   const double Mt = ds->Mtot;
@@ -361,6 +385,53 @@ __global__ void k_force_diff(Grid g, const double* __restrict__ a, double* __res
   const double ap = (i < nx - 1) ? a[i + 1] : -dmul(g.A, Mt);
   da[i] = dsub(ap, am) / twodx;
   d2a[i] = dsub(dadd(ap, am), dmul(2.0, a[i])) / dx2;
+}
+
+__global__ void k_force_diff(Grid g, const double* __restrict__ a, double* __restrict__ da,
+                             double* __restrict__ d2a, const DevState* __restrict__ ds) {
+  diff_body(g, a, da, d2a, ds, blockIdx.x);
+}
+
+// ---- group launches: every solve of a group in one launch per phase ----
+
+__global__ void k_drift_group(const SolveDesc* __restrict__ D, const int* __restrict__ off, int ns, int total,
+                              int taylor) {
+  GROUP_LOOP(off, ns, total)
+  drift_body(gsh, d.el, d.tay, d.tayf, taylor, vb);
+  GROUP_END
+}
+
+__global__ void k_taylor_group(const SolveDesc* __restrict__ D, const int* __restrict__ off, int ns, int total) {
+  GROUP_LOOP(off, ns, total)
+  const int m = vb * blockDim.x + threadIdx.x;
+  if (m < gsh.ne) taylor_one(gsh, d.el, m, d.tay, d.tayf);
+  GROUP_END
+}
+
+__global__ void k_kick_group(const SolveDesc* __restrict__ D, const int* __restrict__ off, int ns, int total) {
+  GROUP_LOOP(off, ns, total)
+  kick_body(gsh, d.el, d.a, d.da, d.d2a, d.ds, vb);
+  GROUP_END
+}
+
+__global__ void k_reset_group(const SolveDesc* __restrict__ D, const int* __restrict__ off, int ns, int total) {
+  GROUP_LOOP(off, ns, total)
+  reset_body(gsh, d.el, vb);
+  GROUP_END
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_group(const SolveDesc* __restrict__ D,
+                                                       const int* __restrict__ off, int ns, int total) {
+  GROUP_LOOP(off, ns, total)
+  (void)vb;
+  scan_body(gsh, d.M, d.a, d.ds);
+  GROUP_END
+}
+
+__global__ void k_diff_group(const SolveDesc* __restrict__ D, const int* __restrict__ off, int ns, int total) {
+  GROUP_LOOP(off, ns, total)
+  diff_body(gsh, d.a, d.da, d.d2a, d.ds, vb);
+  GROUP_END
 }
 
 __device__ __forceinline__ unsigned long long order_key(double d) {
@@ -587,6 +658,37 @@ void launch_kick_drift(vm_solver* s) {
 void launch_reset_elements(vm_solver* s) {
   { const int ps_ = prof_begin(s, KID_RESET); k_reset<<<blocks_for(s->g.ne, ET), ET, 0, s->stream>>>(s->g, s->el); prof_end(s, ps_); }
   s->launches++;
+}
+
+unsigned group_grid(const GroupPlan& G, GroupPhase ph, int total) {
+  const int b = G.shape[ph].blocks > 0 ? G.shape[ph].blocks : 152 * 4;
+  return (unsigned)std::max(1, std::min(b, total));
+}
+
+void group_drift(const GroupPlan& G, bool taylor) {
+  if (G.tot_elem64 == 0) return;
+  k_drift_group<<<group_grid(G, GP_DRIFT, G.tot_elem64), ET, 0, G.stream>>>(G.D, G.off_elem64, G.ns, G.tot_elem64,
+                                                                           taylor ? 1 : 0);
+}
+
+void group_taylor(const GroupPlan& G) {
+  if (G.tot_elem64 == 0) return;
+  k_taylor_group<<<group_grid(G, GP_TAYLOR, G.tot_elem64), ET, 0, G.stream>>>(G.D, G.off_elem64, G.ns, G.tot_elem64);
+}
+
+void group_kick(const GroupPlan& G) {
+  if (G.tot_elem64 == 0) return;
+  k_kick_group<<<group_grid(G, GP_KICK, G.tot_elem64), ET, 0, G.stream>>>(G.D, G.off_elem64, G.ns, G.tot_elem64);
+}
+
+void group_reset(const GroupPlan& G) {
+  if (G.tot_elem64 == 0) return;
+  k_reset_group<<<group_grid(G, GP_RESET, G.tot_elem64), ET, 0, G.stream>>>(G.D, G.off_elem64, G.ns, G.tot_elem64);
+}
+
+void group_scan_force(const GroupPlan& G) {
+  k_scan_group<<<group_grid(G, GP_SCAN, G.ns), SCAN_T, 0, G.stream>>>(G.D, G.off_solve, G.ns, G.ns);
+  k_diff_group<<<group_grid(G, GP_DIFF, G.tot_diff), 128, 0, G.stream>>>(G.D, G.off_diff, G.ns, G.tot_diff);
 }
 
 void launch_scan_force(vm_solver* s) {

@@ -249,8 +249,8 @@ __device__ __forceinline__ Slots with_epoch(Slots S) {
 }
 
 // Start of a map: next epoch, counters cleared.
-__global__ void k_map_begin(DevState* ds) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
+__device__ __forceinline__ void map_begin_body(DevState* ds) {
+  {
     ds->epoch = (ds->epoch + 1) % kEpochs;
     ds->nholes = ds->holes_found = ds->hole_rounds = 0;
     ds->noverflow = ds->overflow_stat = ds->noverflow2 = ds->overflow2_stat = 0;
@@ -263,6 +263,10 @@ __global__ void k_map_begin(DevState* ds) {
     ds->nseed = 0;
     ds->n_pair_esc = 0;
   }
+}
+
+__global__ void k_map_begin(DevState* ds) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) map_begin_body(ds);
 }
 
 __device__ __noinline__ void contest(const Slots& S, const Grid& g, long long i, long long j, size_t p, int m,
@@ -526,16 +530,16 @@ __device__ __forceinline__ void claim_element(const Grid& g, const double* __res
 // window (list of n_in entries).  (A warp-strided loop that prefetched the
 // next element's records cut the set-up latency but cost more in register
 // spills than it saved.)
-__global__ void __launch_bounds__(32 * TE, 8) k_claim_small(Grid g, const double* __restrict__ tay,
+__device__ __forceinline__ void claim_small_body(const Grid& g, const double* __restrict__ tay,
                                                          const float* __restrict__ tayf, Slots Sin, float alo,
                                                          float ahi, int2* __restrict__ ovf_list,
                                                          const int32_t* __restrict__ list_in,
-                                                         const int* __restrict__ n_in) {
+                                                         const int* __restrict__ n_in, int vb, int vg) {
   __shared__ WarpShared shw[TE];
   const Slots S = with_epoch(Sin);
   const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
   const int n = *n_in;
-  for (int idx = blockIdx.x * TE + wq; idx < n; idx += gridDim.x * TE) {
+  for (int idx = vb * TE + wq; idx < n; idx += vg * TE) {
     const int m = list_in[idx];
     if (m < 0 || m >= g.ne) {  // (never expected; keeps every index in bounds)
       if (lane == 0) VM_BAD(S.ds, 6);
@@ -544,6 +548,14 @@ __global__ void __launch_bounds__(32 * TE, 8) k_claim_small(Grid g, const double
     claim_element(g, tay, tayf, S, alo, ahi, ovf_list, shw[wq], lane, m);
     __syncwarp();
   }
+}
+
+__global__ void __launch_bounds__(32 * TE, 8) k_claim_small(Grid g, const double* __restrict__ tay,
+                                                         const float* __restrict__ tayf, Slots Sin, float alo,
+                                                         float ahi, int2* __restrict__ ovf_list,
+                                                         const int32_t* __restrict__ list_in,
+                                                         const int* __restrict__ n_in) {
+  claim_small_body(g, tay, tayf, Sin, alo, ahi, ovf_list, list_in, n_in, blockIdx.x, gridDim.x);
 }
 
 __device__ __forceinline__ void claim_element(const Grid& g, const double* __restrict__ tay,
@@ -882,16 +894,16 @@ __device__ __forceinline__ int nth_bit32(unsigned w, int n) {
   return pos;
 }
 
-__global__ void __launch_bounds__(32 * TP, 8) k_claim_pair(Grid g, const double* __restrict__ tay,
+__device__ __forceinline__ void claim_pair_body(const Grid& g, const double* __restrict__ tay,
                                                          const float* __restrict__ tayf, Slots Sin, float alo,
                                                          float ahi, int32_t* __restrict__ esc_list,
-                                                         int2* __restrict__ ovf_list) {
+                                                         int2* __restrict__ ovf_list, int vb) {
   __shared__ HalfShared shp[2 * TP];
   const Slots S = with_epoch(Sin);
   const int lane = threadIdx.x & 31, h = lane >> 4, hl = lane & 15;
   const int wq = threadIdx.x >> 5;
   HalfShared& sh = shp[2 * wq + h];
-  const int m = (blockIdx.x * TP + wq) * 2 + h;
+  const int m = (vb * TP + wq) * 2 + h;
   if (__all_sync(FULL, m >= g.ne)) return;
   bool live = m < g.ne;
   const int k = live ? m / g.Lv : 0, l = live ? m - k * g.Lv : 0;
@@ -1146,6 +1158,13 @@ __global__ void __launch_bounds__(32 * TP, 8) k_claim_pair(Grid g, const double*
   }
 }
 
+__global__ void __launch_bounds__(32 * TP, 8) k_claim_pair(Grid g, const double* __restrict__ tay,
+                                                         const float* __restrict__ tayf, Slots Sin, float alo,
+                                                         float ahi, int32_t* __restrict__ esc_list,
+                                                         int2* __restrict__ ovf_list) {
+  claim_pair_body(g, tay, tayf, Sin, alo, ahi, esc_list, ovf_list, blockIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // tier 2: larger windows, cooperative block, word-granular tests
 // ---------------------------------------------------------------------------
@@ -1334,17 +1353,17 @@ __device__ __forceinline__ unsigned long long ahead(const unsigned long long* co
 // the whole padded lattice, its masks in a zeroed global scratch of the
 // block, cleared again (over the touched box) before the next element.
 template <bool kGlobal>
-__global__ void __launch_bounds__(BT, BLOCKS_PER_SM) k_claim_big(Grid g, const double* __restrict__ tay,
+__device__ __forceinline__ void claim_big_body(const Grid& g, const double* __restrict__ tay,
                                                   const float* __restrict__ tayf, Slots Sin, float alo, float ahi,
                                                   const int2* __restrict__ list_in, const int* __restrict__ n_in,
                                                   const int* __restrict__ n_back,
                                                   int* __restrict__ stat, int2* __restrict__ list_out,
                                                   int* __restrict__ n_out, int* __restrict__ take,
-                                                  unsigned long long* __restrict__ gwin, size_t gwin_words) {
+                                                  unsigned long long* __restrict__ gwin, size_t gwin_words, int vb) {
   const Slots S = with_epoch(Sin);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BigHeader& H = *reinterpret_cast<BigHeader*>(smem_raw);
-  unsigned long long* bits = kGlobal ? gwin + (size_t)blockIdx.x * gwin_words
+  unsigned long long* bits = kGlobal ? gwin + (size_t)vb * gwin_words
                                      : reinterpret_cast<unsigned long long*>(smem_raw + sizeof(BigHeader));
   const int tid = threadIdx.x;
   const int pad = g.pad;
@@ -1622,7 +1641,19 @@ __global__ void __launch_bounds__(BT, BLOCKS_PER_SM) k_claim_big(Grid g, const d
     }
     __syncthreads();
   }
-  if (blockIdx.x == 0 && tid == 0) *stat = n;
+  if (vb == 0 && tid == 0) *stat = n;
+}
+
+template <bool kGlobal>
+__global__ void __launch_bounds__(BT, BLOCKS_PER_SM) k_claim_big(Grid g, const double* __restrict__ tay,
+                                                  const float* __restrict__ tayf, Slots Sin, float alo, float ahi,
+                                                  const int2* __restrict__ list_in, const int* __restrict__ n_in,
+                                                  const int* __restrict__ n_back,
+                                                  int* __restrict__ stat, int2* __restrict__ list_out,
+                                                  int* __restrict__ n_out, int* __restrict__ take,
+                                                  unsigned long long* __restrict__ gwin, size_t gwin_words) {
+  claim_big_body<kGlobal>(g, tay, tayf, Sin, alo, ahi, list_in, n_in, n_back, stat, list_out, n_out, take, gwin,
+                          gwin_words, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1637,11 +1668,11 @@ __device__ __forceinline__ unsigned long long exact_key(const Grid& g, const dou
 
 // Contested sites: the record's minimum is the owner; the record and the
 // flag are emptied for the next map.
-__global__ void k_resolve(Grid g, Slots Sin) {
+__device__ __forceinline__ void resolve_body(const Grid& g, const Slots& Sin, int vb, int vg) {
   const Slots S = with_epoch(Sin);
   const int n = min(S.ds->nrec, S.rec_cap);
   const size_t nsites = (size_t)g.nx * g.nv;
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+  for (int r = vb * blockDim.x + threadIdx.x; r < n; r += vg * blockDim.x) {
     const size_t p = (size_t)(uint32_t)S.rec_site[r];
     if (p >= nsites) {
       VM_BAD(S.ds, 2);
@@ -1655,13 +1686,16 @@ __global__ void k_resolve(Grid g, Slots Sin) {
   }
 }
 
+__global__ void k_resolve(Grid g, Slots Sin) { resolve_body(g, Sin, blockIdx.x, gridDim.x); }
+
 // Sites no element claimed, four owner slots per 16-byte load (the slot
 // array is 256-byte aligned); the list's order does not matter (the hole
 // rounds are Jacobi rounds).
-__global__ void k_find_holes(Grid g, const uint32_t* __restrict__ slot0, int32_t* __restrict__ holes, DevState* ds) {
+__device__ __forceinline__ void find_holes_body(const Grid& g, const uint32_t* __restrict__ slot0,
+                                                int32_t* __restrict__ holes, DevState* ds, int vb, int vg) {
   const uint32_t epoch = *(volatile uint32_t*)&ds->epoch;
   const size_t n = (size_t)g.nx * g.nv, n4 = n / 4;
-  const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+  const size_t t0 = vb * (size_t)blockDim.x + threadIdx.x, stride = (size_t)vg * blockDim.x;
   const uint4* s4 = reinterpret_cast<const uint4*>(slot0);
   for (size_t q = t0; q < n4; q += stride) {
     const uint4 t = s4[q];
@@ -1674,14 +1708,18 @@ __global__ void k_find_holes(Grid g, const uint32_t* __restrict__ slot0, int32_t
     if ((slot0[p] >> 24) != epoch) holes[atomicAdd(&ds->nholes, 1)] = (int32_t)p;
 }
 
+__global__ void k_find_holes(Grid g, const uint32_t* __restrict__ slot0, int32_t* __restrict__ holes, DevState* ds) {
+  find_holes_body(g, slot0, holes, ds, blockIdx.x, gridDim.x);
+}
+
 constexpr int HT = 1024;
 
 // Unexplored sites (Sec. 2.3.1, end): Jacobi rounds; in each round every
 // hole takes, among the elements its in-grid 4-neighbours held at the end of
 // the previous round, the one with the smallest d at the hole, then the
 // smaller index.
-__global__ void __launch_bounds__(HT) k_holes(Grid g, const double* __restrict__ tay, uint32_t* __restrict__ slot0,
-                                              int32_t* la, int32_t* lb, int32_t* cho, DevState* ds) {
+__device__ __forceinline__ void holes_body(const Grid& g, const double* __restrict__ tay, uint32_t* __restrict__ slot0,
+                                           int32_t* la, int32_t* lb, int32_t* cho, DevState* ds) {
   const uint32_t epoch = *(volatile uint32_t*)&ds->epoch;
   __shared__ int n_s, next_s;
   if (threadIdx.x == 0) {
@@ -1743,6 +1781,11 @@ __global__ void __launch_bounds__(HT) k_holes(Grid g, const double* __restrict__
     ds->hole_rounds = rounds;
     ds->nholes = 0;
   }
+}
+
+__global__ void __launch_bounds__(HT) k_holes(Grid g, const double* __restrict__ tay, uint32_t* __restrict__ slot0,
+                                              int32_t* la, int32_t* lb, int32_t* cho, DevState* ds) {
+  holes_body(g, tay, slot0, la, lb, cho, ds);
 }
 
 // E_map (Sec. 2.3.2) of the current influence map: for every grid site with
@@ -1811,6 +1854,158 @@ __global__ void k_clear_outside(Grid g, uint32_t* __restrict__ slot0, const DevS
       for (int j = j1 + 1 + threadIdx.x; j < g.nv; j += blockDim.x) row[j] = tag;
     }
   }
+}
+
+// ---- group launches: the influence maps of every solve of a group ----
+
+__device__ __forceinline__ Slots slots_of(const SolveDesc& d) {
+  Slots S;
+  S.slot0 = d.map;
+  S.slot1 = d.slot1;
+  S.rec_key = d.rec_key;
+  S.rec_site = d.rec_site;
+  S.rec_cap = d.rec_cap;
+  S.tay = d.tay;
+  S.ds = d.ds;
+  S.epoch = 0u;
+  S.seed = d.t1seed;
+  S.seed_cap = d.t1seed_cap;
+  return S;
+}
+
+__global__ void k_map_begin_group(const SolveDesc* __restrict__ D, int ns) {
+  for (int sv = blockIdx.x * blockDim.x + threadIdx.x; sv < ns; sv += gridDim.x * blockDim.x) map_begin_body(D[sv].ds);
+}
+
+// Units of a dynamic phase, per solve, from the solve's counters (read after
+// the previous phase): an exclusive prefix into off[0..ns], one block.
+__global__ void __launch_bounds__(1024) k_units(const SolveDesc* __restrict__ D, int ns, int kind, int cap,
+                                              int* __restrict__ off) {
+  __shared__ int wsum[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int base = 0; base < ns; base += blockDim.x) {
+    const int sv = base + threadIdx.x;
+    int u = 0;
+    if (sv < ns) {
+      const DevState* ds = D[sv].ds;
+      const bool lastonly = D[sv].map_windows != 0;
+      int n = 0;
+      switch (kind) {
+        case GC_PAIR_ESC: n = (ds->n_pair_esc + TE - 1) / TE; break;
+        case GC_OVF1: n = lastonly ? 0 : ds->noverflow + ds->noverflow_back; break;
+        case GC_OVF2: n = lastonly ? 0 : ds->noverflow2; break;
+        case GC_OVF3: n = lastonly ? ds->noverflow + ds->noverflow_back : ds->noverflow3; break;
+        case GC_REC: n = (min(ds->nrec, D[sv].rec_cap) + 255) / 256; break;
+        default: n = ds->nholes > 0 ? 1 : 0; break;
+      }
+      u = min(max(n, 0), cap);
+    }
+    int inc = u;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    if (lane == 31) wsum[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+      const int w = (lane < (int)(blockDim.x >> 5)) ? wsum[lane] : 0;
+      int wi = w;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += t;
+      }
+      wsum[lane] = wi - w;
+    }
+    __syncthreads();
+    if (sv < ns) off[sv] = carry + wsum[wid] + inc - u;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry += wsum[wid] + inc;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) off[ns] = carry;
+}
+
+// The loop of a dynamic phase: units [off[sv], off[sv + 1]) of solve sv,
+// the unit count of the solve being the virtual grid.
+#define GROUP_DYN_LOOP(off, ns)                                      \
+  __shared__ Grid gsh;                                               \
+  __shared__ int svsh;                                               \
+  const int total_ = __ldcg((off) + (ns));                           \
+  for (int u = blockIdx.x; u < total_; u += gridDim.x) {             \
+    if (threadIdx.x == 0) {                                          \
+      int lo = 0, hi = (ns) - 1;                                     \
+      while (lo < hi) {                                              \
+        const int mid = (lo + hi + 1) >> 1;                          \
+        if (__ldcg((off) + mid) <= u) lo = mid; else hi = mid - 1;   \
+      }                                                              \
+      svsh = lo;                                                     \
+      gsh = D[lo].g;                                                 \
+    }                                                                \
+    __syncthreads();                                                 \
+    const int sv = svsh;                                             \
+    const SolveDesc& d = D[sv];                                      \
+    const int o0 = __ldcg((off) + sv);                               \
+    const int vb = u - o0, vg = __ldcg((off) + sv + 1) - o0;         \
+    (void)vg;
+
+__global__ void __launch_bounds__(32 * TP, 8) k_claim_pair_group(const SolveDesc* __restrict__ D,
+                                                               const int* __restrict__ off, int ns, int total) {
+  GROUP_LOOP(off, ns, total)
+  claim_pair_body(gsh, d.tay, d.tayf, slots_of(d), d.alo, d.ahi, d.holes_a, d.ovf1, vb);
+  GROUP_END
+}
+
+__global__ void __launch_bounds__(32 * TE, 8) k_claim_small_group(const SolveDesc* __restrict__ D,
+                                                                const int* __restrict__ off, int ns) {
+  GROUP_DYN_LOOP(off, ns)
+  claim_small_body(gsh, d.tay, d.tayf, slots_of(d), d.alo, d.ahi, d.ovf1, d.holes_a, &d.ds->n_pair_esc, vb, vg);
+  GROUP_END
+}
+
+// attempt 0: the first large windows; 1: the second; 2: the whole lattice
+template <int kAttempt>
+__global__ void __launch_bounds__(BT, BLOCKS_PER_SM) k_claim_big_group(const SolveDesc* __restrict__ D,
+                                                                      const int* __restrict__ off, int ns) {
+  GROUP_DYN_LOOP(off, ns)
+  DevState* ds = d.ds;
+  const Slots S = slots_of(d);
+  if (kAttempt == 0)
+    claim_big_body<false>(gsh, d.tay, d.tayf, S, d.alo, d.ahi, d.ovf1, &ds->noverflow, &ds->noverflow_back,
+                          &ds->overflow_stat, d.ovf2, &ds->noverflow2, &ds->take[0], nullptr, 0, vb);
+  else if (kAttempt == 1)
+    claim_big_body<false>(gsh, d.tay, d.tayf, S, d.alo, d.ahi, d.ovf2, &ds->noverflow2, nullptr,
+                          &ds->overflow2_stat, d.ovf1, &ds->noverflow3, &ds->take[1], nullptr, 0, vb);
+  else if (d.map_windows == 0)
+    claim_big_body<true>(gsh, d.tay, d.tayf, S, d.alo, d.ahi, d.ovf1, &ds->noverflow3, nullptr, &ds->overflow3_stat,
+                         nullptr, nullptr, &ds->take[2], d.gwin, d.gwin_words, vb);
+  else
+    claim_big_body<true>(gsh, d.tay, d.tayf, S, d.alo, d.ahi, d.ovf1, &ds->noverflow, &ds->noverflow_back,
+                         &ds->overflow_stat, nullptr, nullptr, &ds->take[2], d.gwin, d.gwin_words, vb);
+  GROUP_END
+}
+
+__global__ void k_resolve_group(const SolveDesc* __restrict__ D, const int* __restrict__ off, int ns) {
+  GROUP_DYN_LOOP(off, ns)
+  resolve_body(gsh, slots_of(d), vb, vg);
+  GROUP_END
+}
+
+__global__ void k_find_holes_group(const SolveDesc* __restrict__ D, const int* __restrict__ off, int ns, int total) {
+  GROUP_LOOP(off, ns, total)
+  const int vg = __ldg(off + sv + 1) - __ldg(off + sv);
+  find_holes_body(gsh, d.map, d.holes_a, d.ds, vb, vg);
+  GROUP_END
+}
+
+__global__ void __launch_bounds__(HT) k_holes_group(const SolveDesc* __restrict__ D, const int* __restrict__ off,
+                                                  int ns) {
+  GROUP_DYN_LOOP(off, ns)
+  (void)vb;
+  holes_body(gsh, d.tay, d.map, d.holes_a, d.holes_b, d.holes_b + (size_t)gsh.nx * gsh.nv, d.ds);
+  GROUP_END
 }
 
 }  // namespace
@@ -1928,6 +2123,42 @@ void launch_read_map(vm_solver* s, int32_t* dst) {
   k_read_map<<<nb, 256, 0, s->stream>>>(s->map, s->ds, dst, s->n, s->g.ne);
   prof_end(s, ps);
   s->launches++;
+}
+
+// The maps of every solve of a group: the single-solve sequence of launches,
+// each over the group's work list (dynamic phases from each solve's counters).
+size_t group_big_smem(const Grid& g) { return big_smem_bytes(g); }
+
+void group_map(const GroupPlan& G) {
+  cudaStream_t st = G.stream;
+  const int ns = G.ns;
+  const int persist = 152 * 8;
+  k_map_begin_group<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(G.D, ns);
+  if (G.tot_pair > 0)
+    k_claim_pair_group<<<group_grid(G, GP_PAIR, G.tot_pair), 32 * TP, 0, st>>>(G.D, G.off_pair, ns, G.tot_pair);
+  k_units<<<1, 1024, 0, st>>>(G.D, ns, GC_PAIR_ESC, persist, G.off_dyn);
+  k_claim_small_group<<<group_grid(G, GP_SMALL, persist), 32 * TE, 0, st>>>(G.D, G.off_dyn, ns);
+  const int capb = G.big_blocks_cap > 0 ? G.big_blocks_cap : BLOCKS_PER_SM * 152;
+  k_units<<<1, 1024, 0, st>>>(G.D, ns, GC_OVF1, capb, G.off_dyn);
+  k_claim_big_group<0><<<group_grid(G, GP_BIG1, BLOCKS_PER_SM * 152), BT, G.big_smem, st>>>(G.D, G.off_dyn, ns);
+  k_units<<<1, 1024, 0, st>>>(G.D, ns, GC_OVF2, capb, G.off_dyn);
+  k_claim_big_group<1><<<group_grid(G, GP_BIG2, BLOCKS_PER_SM * 152), BT, G.big_smem, st>>>(G.D, G.off_dyn, ns);
+  k_units<<<1, 1024, 0, st>>>(G.D, ns, GC_OVF3, kGlobalBlocks, G.off_dyn);
+  k_claim_big_group<2><<<group_grid(G, GP_BIG3, BLOCKS_PER_SM * 152), BT, sizeof(BigHeader), st>>>(G.D, G.off_dyn, ns);
+  k_units<<<1, 1024, 0, st>>>(G.D, ns, GC_REC, 152, G.off_dyn);
+  k_resolve_group<<<group_grid(G, GP_RESOLVE, 152 * 4), 256, 0, st>>>(G.D, G.off_dyn, ns);
+  if (G.tot_sites > 0)
+    k_find_holes_group<<<group_grid(G, GP_FIND_HOLES, G.tot_sites), 256, 0, st>>>(G.D, G.off_sites, ns, G.tot_sites);
+  k_units<<<1, 1024, 0, st>>>(G.D, ns, GC_HOLES, 1, G.off_dyn);
+  k_holes_group<<<group_grid(G, GP_HOLES, 152), HT, 0, st>>>(G.D, G.off_dyn, ns);
+}
+
+// Opt the group's large-window kernels in to shared memory (as map_prepare does).
+bool group_map_prepare() {
+  return cudaFuncSetAttribute(k_claim_big_group<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX) ==
+             cudaSuccess &&
+         cudaFuncSetAttribute(k_claim_big_group<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX) ==
+             cudaSuccess;
 }
 
 }  // namespace vm

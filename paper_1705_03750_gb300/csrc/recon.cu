@@ -91,12 +91,67 @@ __device__ __forceinline__ void zero_outside(const Grid& g, R* __restrict__ row,
   for (int j = j1 + 1 + threadIdx.x; j < g.nv; j += blockDim.x) row[j] = R(0);
 }
 
-__global__ void __launch_bounds__(256) k_recon64(Grid g, const uint32_t* __restrict__ map, const DevState* ds,
+// FP64 path, fused interpolation.  Q - Q_m is evaluated in the fixed order
+// (so it is the reference order's to the bit), but the index coordinate is
+// anchored on the exact lattice position of Q_m ((n-1)/2 + (k-K-1)s, an
+// integer or a half) with one fused operation, instead of (Q_m + dq - x_lo)
+// / dx in three roundings.  The two differ by at most the roundings of the
+// reference's constants and operations, bounded per grid by Grid::eps_u,
+// eps_w (computed on the host: 64 ulps of (|x_lo| + |x_hi|)/dx + n + 8).
+// The nearest node and the containing cell are taken from the anchored value
+// when it lies farther than that bound from every decision boundary,
+// otherwise the caller evaluates the site in the fixed order; the six-point
+// value uses fused operations (rounding changes only).
+__device__ __forceinline__ bool decide64(double u, double eps, long long& in, long long& ic, double& dq) {
+  const double fl = floor(u);
+  const double r = u - fl;  // exact
+  if (!(r > eps && r < 1.0 - eps && fabs(r - 0.5) > eps)) return false;
+  ic = (long long)fl;
+  in = (r >= 0.5) ? ic + 1 : ic;
+  dq = u - (double)in;  // exact
+  return true;
+}
+
+__device__ __forceinline__ double qinterp64_fused(const double* __restrict__ F, const Grid& g, long long in,
+                                                  long long jn, long long ic, long long jc, double x, double y) {
+  const double hx = 0.5 * x, hy = 0.5 * y;
+  double f = F_at(F, g, in, jn) * fma(-y, y, fma(-x, x, 1.0));
+  f = fma(F_at(F, g, in + 1, jn), fma(hx, x, hx), f);
+  f = fma(F_at(F, g, in - 1, jn), fma(hx, x, -hx), f);
+  f = fma(F_at(F, g, in, jn + 1), fma(hy, y, hy), f);
+  f = fma(F_at(F, g, in, jn - 1), fma(hy, y, -hy), f);
+  const double cross = (F_at(F, g, ic + 1, jc + 1) + F_at(F, g, ic, jc)) - (F_at(F, g, ic + 1, jc) + F_at(F, g, ic, jc + 1));
+  return fma(cross, x * y, f);
+}
+
+// f at site (i, j) owned by element m with offsets dq (fixed order); false
+// when a decision is not certain.
+__device__ __forceinline__ bool recon_site64_fused(const Grid& g, int m, double dqx, double dqv,
+                                                   const double* __restrict__ fini, double& val) {
+  const double eu = g.eps_u, ew = g.eps_w;
+  const int k = m / g.Lv, l = m - k * g.Lv;
+  const double ua = 0.5 * (double)((g.nx - 1) + 2 * (k - g.Kx - 1) * g.s);
+  const double wa = 0.5 * (double)((g.nv - 1) + 2 * (l - g.Kv - 1) * g.s);
+  const double u = fma(dqx, g.inv_dx, ua), w = fma(dqv, g.inv_dv, wa);
+  if (!(u > -2.0 + eu && u < (double)g.nx + 1.0 - eu && w > -2.0 + ew && w < (double)g.nv + 1.0 - ew)) {
+    // outside the interpolation's reach, or too close to its edge to tell
+    if (u > -2.0 - eu && u < (double)g.nx + 1.0 + eu && w > -2.0 - ew && w < (double)g.nv + 1.0 + ew) return false;
+    val = 0.0;
+    return true;
+  }
+  long long in, ic, jn, jc;
+  double x, y;
+  if (!decide64(u, eu, in, ic, x) || !decide64(w, ew, jn, jc, y)) return false;
+  val = qinterp64_fused(fini, g, in, jn, ic, jc, x, y);
+  return true;
+}
+
+__device__ __forceinline__ void k_recon64_body(const Grid& g, const uint32_t* __restrict__ map, const DevState* ds,
                                                  const double* __restrict__ tay, const double* __restrict__ fini,
-                                                 double* __restrict__ f, double* __restrict__ M) {
+                                                 double* __restrict__ f, double* __restrict__ M, int vb) {
   using R = double;
   __shared__ double sh[32];
-  const int i = blockIdx.x;
+  const int i = vb;
   const double Px = site_x(g, i);
   int js, je;
   row_span(g, ds, i, js, je);
@@ -110,9 +165,12 @@ __global__ void __launch_bounds__(256) k_recon64(Grid g, const uint32_t* __restr
       const double* t = tay + (size_t)m * TY_N;
       double dqx, dqv;
       qofp_exact(t, Px, site_v(g, j), dqx, dqv);
-      const double u = dmul(dsub(dadd(t[TY_QX], dqx), g.x_lo), g.inv_dx);
-      const double w = dmul(dsub(dadd(t[TY_QV], dqv), g.v_lo), g.inv_dv);
-      val = qinterp(fini, g, u, w);
+      if (!recon_site64_fused(g, m, dqx, dqv, fini, val)) {
+        // a decision the anchored value cannot settle: the fixed order
+        const double u = dmul(dsub(dadd(t[TY_QX], dqx), g.x_lo), g.inv_dx);
+        const double w = dmul(dsub(dadd(t[TY_QV], dqv), g.v_lo), g.inv_dv);
+        val = qinterp(fini, g, u, w);
+      }
     }
     const R out = (R)val;
     f[p] = out;
@@ -120,6 +178,12 @@ __global__ void __launch_bounds__(256) k_recon64(Grid g, const uint32_t* __restr
   }
   const double rowsum = block_sum(acc, sh);
   if (threadIdx.x == 0) M[i] = dmul(rowsum, g.dxdv);
+}
+
+__global__ void __launch_bounds__(256) k_recon64(Grid g, const uint32_t* __restrict__ map, const DevState* ds,
+                                                 const double* __restrict__ tay, const double* __restrict__ fini,
+                                                 double* __restrict__ f, double* __restrict__ M) {
+  k_recon64_body(g, map, ds, tay, fini, f, M, blockIdx.x);
 }
 
 // Monaghan M4 kernel, unnormalised (Sec. 2.3.2).
@@ -218,11 +282,11 @@ __device__ __forceinline__ double spline_eval(const R* __restrict__ eta, const G
   return (double)sum;
 }
 
-__global__ void __launch_bounds__(256) k_remap64(Grid g, const uint32_t* __restrict__ map, const DevState* ds,
+__device__ __forceinline__ void k_remap64_body(const Grid& g, const uint32_t* __restrict__ map, const DevState* ds,
                                                  const double* __restrict__ tay, const double* __restrict__ eta,
-                                                 double* __restrict__ out) {
+                                                 double* __restrict__ out, int vb) {
   using R = double;
-  const int i = blockIdx.x;
+  const int i = vb;
   const double Px = site_x(g, i);
   int js, je;
   row_span(g, ds, i, js, je);
@@ -240,6 +304,12 @@ __global__ void __launch_bounds__(256) k_remap64(Grid g, const uint32_t* __restr
     }
     out[p] = (R)val;
   }
+}
+
+__global__ void __launch_bounds__(256) k_remap64(Grid g, const uint32_t* __restrict__ map, const DevState* ds,
+                                                 const double* __restrict__ tay, const double* __restrict__ eta,
+                                                 double* __restrict__ out) {
+  k_remap64_body(g, map, ds, tay, eta, out, blockIdx.x);
 }
 
 
@@ -494,12 +564,12 @@ __device__ __forceinline__ float recon_fast32(const Grid& g, const float* __rest
   return (m >= 0) ? v : 0.f;
 }
 
-__global__ void __launch_bounds__(256, 6) k_recon32(Grid g, const uint32_t* __restrict__ map, const DevState* ds,
+__device__ __forceinline__ void k_recon32_body(const Grid& g, const uint32_t* __restrict__ map, const DevState* ds,
                                                  const double* __restrict__ tay, const float* __restrict__ tayf,
                                                  const float* __restrict__ fini, float* __restrict__ f,
-                                                 double* __restrict__ M) {
+                                                 double* __restrict__ M, int vb) {
   __shared__ double sh[32];
-  const int i = blockIdx.x;
+  const int i = vb;
   const uint32_t epoch = ds_epoch(ds);
   FPair acc;
   const float inv_Lv = 1.0f / (float)g.Lv;
@@ -521,6 +591,13 @@ __global__ void __launch_bounds__(256, 6) k_recon32(Grid g, const uint32_t* __re
   }
   const double rowsum = block_sum(acc.value(), sh);
   if (threadIdx.x == 0) M[i] = dmul(rowsum, g.dxdv);
+}
+
+__global__ void __launch_bounds__(256, 6) k_recon32(Grid g, const uint32_t* __restrict__ map, const DevState* ds,
+                                                 const double* __restrict__ tay, const float* __restrict__ tayf,
+                                                 const float* __restrict__ fini, float* __restrict__ f,
+                                                 double* __restrict__ M) {
+  k_recon32_body(g, map, ds, tay, tayf, fini, f, M, blockIdx.x);
 }
 
 __device__ __forceinline__ float W4f(float x) {
@@ -576,11 +653,11 @@ __device__ __forceinline__ float spline32(const float* __restrict__ eta, const G
   return sum;
 }
 
-__global__ void __launch_bounds__(256) k_remap32(Grid g, const uint32_t* __restrict__ map, const DevState* ds,
+__device__ __forceinline__ void k_remap32_body(const Grid& g, const uint32_t* __restrict__ map, const DevState* ds,
                                                  const double* __restrict__ tay, const float* __restrict__ tayf,
                                                  const float* __restrict__ eta, float* __restrict__ out, float blo,
-                                                 float bhi) {
-  const int i = blockIdx.x;
+                                                 float bhi, int vb) {
+  const int i = vb;
   const float inv_s = 1.0f / (float)g.s, fs = (float)g.s;
   int js, je;
   row_span(g, ds, i, js, je);
@@ -644,6 +721,56 @@ __global__ void __launch_bounds__(256) k_remap32(Grid g, const uint32_t* __restr
   }
 }
 
+__global__ void __launch_bounds__(256) k_remap32(Grid g, const uint32_t* __restrict__ map, const DevState* ds,
+                                                 const double* __restrict__ tay, const float* __restrict__ tayf,
+                                                 const float* __restrict__ eta, float* __restrict__ out, float blo,
+                                                 float bhi) {
+  k_remap32_body(g, map, ds, tay, tayf, eta, out, blo, bhi, blockIdx.x);
+}
+
+// ---- group launches ----
+
+__global__ void __launch_bounds__(256, 6) k_recon_group32(const SolveDesc* __restrict__ D, const int* __restrict__ off,
+                                                        int ns, int total) {
+  GROUP_LOOP(off, ns, total)
+  k_recon32_body(gsh, d.map, d.ds, d.tay, d.tayf, (const float*)d.fini, (float*)d.f, d.M, vb);
+  GROUP_END
+}
+
+__global__ void __launch_bounds__(256) k_recon_group64(const SolveDesc* __restrict__ D, const int* __restrict__ off,
+                                                     int ns, int total) {
+  GROUP_LOOP(off, ns, total)
+  k_recon64_body(gsh, d.map, d.ds, d.tay, (const double*)d.fini, (double*)d.f, d.M, vb);
+  GROUP_END
+}
+
+__global__ void __launch_bounds__(256) k_remap_group32(const SolveDesc* __restrict__ D, const int* __restrict__ off,
+                                                     int ns, int total) {
+  GROUP_LOOP(off, ns, total)
+  k_remap32_body(gsh, d.map, d.ds, d.tay, d.tayf, (const float*)d.eta, (float*)d.tmp, d.blo, d.bhi, vb);
+  GROUP_END
+}
+
+__global__ void __launch_bounds__(256) k_remap_group64(const SolveDesc* __restrict__ D, const int* __restrict__ off,
+                                                     int ns, int total) {
+  GROUP_LOOP(off, ns, total)
+  k_remap64_body(gsh, d.map, d.ds, d.tay, (const double*)d.eta, (double*)d.tmp, vb);
+  GROUP_END
+}
+
+// f_ini <- tmp (the resampled f of a remap), 4096 values per unit.
+template <typename R>
+__global__ void __launch_bounds__(256) k_copy_group(const SolveDesc* __restrict__ D, const int* __restrict__ off,
+                                                  int ns, int total) {
+  GROUP_LOOP(off, ns, total)
+  const size_t n = (size_t)gsh.nx * gsh.nv;
+  const size_t p0 = (size_t)vb * 4096;
+  const R* src = (const R*)d.tmp;
+  R* dst = (R*)d.fini;
+  for (size_t p = p0 + threadIdx.x; p < p0 + 4096 && p < n; p += blockDim.x) dst[p] = src[p];
+  GROUP_END
+}
+
 template <typename S, typename D>
 __global__ void k_convert(const S* __restrict__ src, D* __restrict__ dst, size_t n) {
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
@@ -656,6 +783,34 @@ inline unsigned grid_for(size_t n) {
 }
 
 }  // namespace
+
+// The reconstruction's block size: the single-solve rule (it sets the row
+// sums' association, so it is not a tuning parameter).
+inline int recon_threads(int nv) { return nv >= 256 ? 256 : ((nv + 31) / 32) * 32; }
+
+void group_reconstruct(const GroupPlan& G) {
+  // every solve of a group has the same block size (the group is built so)
+  const int nt = 256;
+  if (G.fp32)
+    k_recon_group32<<<group_grid(G, GP_RECON, G.tot_rows), nt, 0, G.stream>>>(G.D, G.off_rows, G.ns, G.tot_rows);
+  else
+    k_recon_group64<<<group_grid(G, GP_RECON, G.tot_rows), nt, 0, G.stream>>>(G.D, G.off_rows, G.ns, G.tot_rows);
+}
+
+void group_remap_resample(const GroupPlan& G) {
+  const int nt = 256;
+  if (G.fp32)
+    k_remap_group32<<<group_grid(G, GP_REMAP, G.tot_rows), nt, 0, G.stream>>>(G.D, G.off_rows, G.ns, G.tot_rows);
+  else
+    k_remap_group64<<<group_grid(G, GP_REMAP, G.tot_rows), nt, 0, G.stream>>>(G.D, G.off_rows, G.ns, G.tot_rows);
+}
+
+void group_copy_tmp_to_fini(const GroupPlan& G) {
+  if (G.fp32)
+    k_copy_group<float><<<group_grid(G, GP_COPY, G.tot_copy), 256, 0, G.stream>>>(G.D, G.off_copy, G.ns, G.tot_copy);
+  else
+    k_copy_group<double><<<group_grid(G, GP_COPY, G.tot_copy), 256, 0, G.stream>>>(G.D, G.off_copy, G.ns, G.tot_copy);
+}
 
 void launch_reconstruct(vm_solver* s) {
   const int nt = s->g.nv >= 256 ? 256 : ((s->g.nv + 31) / 32) * 32;

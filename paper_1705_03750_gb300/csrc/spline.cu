@@ -86,10 +86,10 @@ __global__ void __launch_bounds__(32 * RW) k_rows(Grid g, const R* __restrict__ 
 // group then continues from the previous group's last value.  Loads and
 // stores are coalesced (32 consecutive entries per warp instruction).
 template <typename R, typename C>
-__global__ void __launch_bounds__(128) k_rows_scan(Grid g, const R* __restrict__ src, R* __restrict__ dst,
-                                                   const C* __restrict__ th) {
+__device__ __forceinline__ void rows_scan_body(const Grid& g, const R* __restrict__ src, R* __restrict__ dst,
+                                               const C* __restrict__ th, int vb) {
   const int lane = threadIdx.x & 31;
-  const int row = blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int row = vb * 4 + (threadIdx.x >> 5);
   if (row >= g.nx) return;
   const int nv = g.nv;
   const C* cp = th;
@@ -149,9 +149,15 @@ __global__ void __launch_bounds__(128) k_rows_scan(Grid g, const R* __restrict__
 // the loads are not: the next CK rows are loaded while the current CK are
 // swept (double buffering), so that memory latency overlaps the recurrence.
 template <typename R, typename C>
-__global__ void __launch_bounds__(32) k_cols(Grid g, R* __restrict__ x, const C* __restrict__ th) {
+__global__ void __launch_bounds__(128) k_rows_scan(Grid g, const R* __restrict__ src, R* __restrict__ dst,
+                                                   const C* __restrict__ th) {
+  rows_scan_body(g, src, dst, th, blockIdx.x);
+}
+
+template <typename R, typename C>
+__device__ __forceinline__ void cols_body(const Grid& g, R* __restrict__ x, const C* __restrict__ th, int vb) {
   constexpr int CK = 32;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = vb * blockDim.x + threadIdx.x;
   if (j >= g.nv) return;
   const int nx = g.nx, nv = g.nv;
   const C* cp = th;
@@ -204,6 +210,34 @@ __global__ void __launch_bounds__(32) k_cols(Grid g, R* __restrict__ x, const C*
   }
 }
 
+template <typename R, typename C>
+__global__ void __launch_bounds__(32) k_cols(Grid g, R* __restrict__ x, const C* __restrict__ th) {
+  cols_body(g, x, th, blockIdx.x);
+}
+
+// ---- group launches: f_ini -> eta of every solve ----
+template <typename R>
+__global__ void __launch_bounds__(128) k_rows_group(const SolveDesc* __restrict__ D, const int* __restrict__ off,
+                                                  int ns, int total) {
+  GROUP_LOOP(off, ns, total)
+  if constexpr (sizeof(R) == 4)
+    rows_scan_body<float, float>(gsh, (const float*)d.fini, (float*)d.eta, d.thvf, vb);
+  else
+    rows_scan_body<double, double>(gsh, (const double*)d.fini, (double*)d.eta, d.thv, vb);
+  GROUP_END
+}
+
+template <typename R>
+__global__ void __launch_bounds__(32) k_cols_group(const SolveDesc* __restrict__ D, const int* __restrict__ off,
+                                                 int ns, int total) {
+  GROUP_LOOP(off, ns, total)
+  if constexpr (sizeof(R) == 4)
+    cols_body<float, float>(gsh, (float*)d.eta, d.thxf, vb);
+  else
+    cols_body<double, double>(gsh, (double*)d.eta, d.thx, vb);
+  GROUP_END
+}
+
 }  // namespace
 
 void launch_spline_solve(vm_solver* s, const void* src, void* dst) {
@@ -224,6 +258,17 @@ void launch_spline_solve(vm_solver* s, const void* src, void* dst) {
     k_cols<double, double><<<cb, 32, 0, s->stream>>>(s->g, (double*)dst, s->thomas_x);
   prof_end(s, ps);
   s->launches += 2;
+}
+
+void group_spline(const GroupPlan& G) {
+  if (G.fp32) {
+    k_rows_group<float><<<group_grid(G, GP_ROWS, G.tot_rows4), 128, 0, G.stream>>>(G.D, G.off_rows4, G.ns, G.tot_rows4);
+    k_cols_group<float><<<group_grid(G, GP_COLS, G.tot_cols), 32, 0, G.stream>>>(G.D, G.off_cols, G.ns, G.tot_cols);
+  } else {
+    k_rows_group<double><<<group_grid(G, GP_ROWS, G.tot_rows4), 128, 0, G.stream>>>(G.D, G.off_rows4, G.ns,
+                                                                                  G.tot_rows4);
+    k_cols_group<double><<<group_grid(G, GP_COLS, G.tot_cols), 32, 0, G.stream>>>(G.D, G.off_cols, G.ns, G.tot_cols);
+  }
 }
 
 }  // namespace vm

@@ -32,6 +32,9 @@ EXPORTS = ["vm_config_default", "vm_workspace_bytes", "vm_create", "vm_destroy",
            "vm_read_eta", "vm_read_map", "vm_diagnostics", "vm_sync", "vm_launch_count",
            "vm_profile", "vm_profile_read", "vm_force_from_f_static",
            "vm_batch_create", "vm_batch_step", "vm_batch_launches_per_step", "vm_batch_destroy",
+           "vm_batch_autotune", "vm_batch_tuning",
+           "vm_server_pool_bytes", "vm_server_create", "vm_server_submit", "vm_server_poll", "vm_server_result",
+           "vm_server_stats", "vm_server_destroy",
            "vm_last_cuda_error", "vm_cuda_error_name", "vm_save", "vm_load", "vm_measure_fp64_peak"]
 
 VM_STATIC_FORCE_MAX_NX = 16384
@@ -58,6 +61,22 @@ class VmDiag(C.Structure):
                 ("l1", C.c_double), ("l2", C.c_double), ("emap", C.c_double), ("emap_remaps", C.c_int64),
                 ("time", C.c_double), ("last_dt", C.c_double),
                 ("lattice_range", C.c_int32 * 4), ("site_rect", C.c_int32 * 4)]
+
+
+class VmServerConfig(C.Structure):
+    _fields_ = [("budget_bytes", C.c_size_t), ("max_active", C.c_int32), ("steps_per_tick", C.c_int32),
+                ("precision", C.c_int32)]
+
+
+class VmServerDone(C.Structure):
+    _fields_ = [("id", C.c_int64), ("status", C.c_int32), ("submit_s", C.c_double), ("admit_s", C.c_double),
+                ("finish_s", C.c_double)]
+
+
+class VmServerStat(C.Structure):
+    _fields_ = [("waiting", C.c_int32), ("active", C.c_int32), ("finished", C.c_int32), ("peak_active", C.c_int32),
+                ("used_bytes", C.c_int64), ("peak_bytes", C.c_int64), ("ticks", C.c_int64),
+                ("group_steps", C.c_int64), ("remap_groups", C.c_int64)]
 
 
 class VmKernelStat(C.Structure):
@@ -112,6 +131,15 @@ def load() -> C.CDLL:
         "vm_batch_step": (i32, [vp, i32]),
         "vm_batch_launches_per_step": (i64, [vp, i32]),
         "vm_batch_destroy": (None, [vp]),
+        "vm_batch_autotune": (i32, [vp, i32]),
+        "vm_server_pool_bytes": (C.c_size_t, [C.POINTER(VmServerConfig)]),
+        "vm_server_create": (i32, [C.POINTER(VmServerConfig), vp, C.c_size_t, vp, C.POINTER(vp)]),
+        "vm_server_submit": (i32, [vp, C.POINTER(VmConfig), vp, i32, C.POINTER(i64)]),
+        "vm_server_poll": (i32, [vp, C.POINTER(VmServerDone), i32, C.POINTER(i32)]),
+        "vm_server_result": (i32, [vp, i64, vp, vp, vp, vp]),
+        "vm_server_stats": (i32, [vp, C.POINTER(VmServerStat)]),
+        "vm_server_destroy": (None, [vp]),
+        "vm_batch_tuning": (i32, [vp, C.POINTER(i32), dp]),
         "vm_last_cuda_error": (i32, []),
         "vm_cuda_error_name": (C.c_char_p, [i32]),
         "vm_save": (i32, [vp, C.c_char_p]),
@@ -383,11 +411,12 @@ class Solver:
 
 
 class Batch:
-    """Many independent solves advanced together, one CUDA graph launch per
-    step (the solves' kernels spread over ``nstreams`` streams inside the
-    graph).  All solvers must have had set_f and share their remap phase."""
+    """Many independent solves advanced together: every phase of a step is
+    one launch for the whole batch, the step one CUDA graph launch.  All
+    solvers must have had set_f, share their precision and remap phase.
+    ``nstreams`` is not used (kept for compatibility)."""
 
-    def __init__(self, solvers, nstreams: int = 16, stream=None):
+    def __init__(self, solvers, nstreams: int = 0, stream=None):
         import torch
         self.L = load()
         self.solvers = list(solvers)
@@ -405,9 +434,91 @@ class Batch:
     def launches_per_step(self, with_remap: bool = False) -> int:
         return int(self.L.vm_batch_launches_per_step(self.h, int(with_remap)))
 
+    def autotune(self, trials: int = 1) -> dict:
+        """Tune the persistent blocks of each phase on real steps (4 x trials
+        transport steps are taken); returns the chosen shape."""
+        _check(self.L.vm_batch_autotune(self.h, int(trials)), "vm_batch_autotune")
+        return self.tuning()
+
+    def tuning(self) -> dict:
+        bps = (C.c_int32 * 5)()
+        ms = (C.c_double * 5)()
+        tuned = self.L.vm_batch_tuning(self.h, bps, ms)
+        names = ("drift_taylor", "map", "reconstruct", "scan_force", "kick_drift")
+        return {"tuned": bool(tuned), "blocks_per_sm": dict(zip(names, list(bps))),
+                "ms_per_step": dict(zip(names, list(ms)))}
+
     def close(self):
         if getattr(self, "h", None):
             self.L.vm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class NativeServer:
+    """The library's serving loop (vm_server_*): continuous batching of
+    submitted solves on one device pool.  ``budget_bytes`` of the pool hold
+    the solves' workspaces; ``poll()`` drives it without waiting for the
+    device and returns the requests finished since the last call."""
+
+    def __init__(self, budget_bytes: int, max_active: int = 32, steps_per_tick: int = 5,
+                 precision: int = VM_FP32_MIXED, stream=None, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("NativeServer needs a CUDA device")
+        self.L = load()
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        self.precision = precision
+        self._c = VmServerConfig(int(budget_bytes), int(max_active), int(steps_per_tick), int(precision))
+        reserve = int(self.L.vm_server_pool_bytes(C.byref(self._c)))
+        nbytes = reserve + int(budget_bytes)
+        self._pool = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = (self._pool.data_ptr() + 255) // 256 * 256
+        h = C.c_void_p()
+        _check(self.L.vm_server_create(C.byref(self._c), C.c_void_p(base), nbytes, C.c_void_p(self.stream.cuda_stream),
+                                       C.byref(h)), "vm_server_create")
+        self.h = h
+        self.nx = {}
+        self._done = (VmServerDone * 256)()
+
+    def submit(self, rc, f0: np.ndarray, steps: int) -> int:
+        cfg = Config.from_run(rc, self.precision).c()
+        f0 = np.ascontiguousarray(f0, dtype=np.float64)
+        if f0.shape != (rc.nx, rc.nv):
+            raise ValueError(f"f0 must have shape ({rc.nx}, {rc.nv})")
+        rid = C.c_int64()
+        _check(self.L.vm_server_submit(self.h, C.byref(cfg), C.c_void_p(f0.ctypes.data), int(steps), C.byref(rid)),
+               "vm_server_submit")
+        self.nx[rid.value] = rc.nx
+        return rid.value
+
+    def poll(self) -> list:
+        n = C.c_int32()
+        _check(self.L.vm_server_poll(self.h, self._done, len(self._done), C.byref(n)), "vm_server_poll")
+        return [{"id": d.id, "status": d.status, "submit_s": d.submit_s, "admit_s": d.admit_s,
+                 "finish_s": d.finish_s} for d in self._done[:n.value]]
+
+    def result(self, rid: int) -> dict:
+        nx = self.nx[rid]
+        out = {k: np.empty(nx) for k in ("M", "a", "da", "d2a")}
+        _check(self.L.vm_server_result(self.h, int(rid), *[C.c_void_p(out[k].ctypes.data) for k in ("M", "a", "da", "d2a")]),
+               "vm_server_result")
+        return out
+
+    def stats(self) -> dict:
+        st = VmServerStat()
+        _check(self.L.vm_server_stats(self.h, C.byref(st)), "vm_server_stats")
+        return {k: getattr(st, k) for k, _ in VmServerStat._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.vm_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -1,10 +1,14 @@
 """Batched and served solves give what the same solves give alone.
 
 Every kernel of a solve is deterministic (claims are resolved by exact keys,
-reductions run in a fixed order), so a solve advanced inside a batch graph,
-or among other requests on the server, must match the same solve advanced on
-its own bit for bit.
+reductions run in a fixed order), and a group launch runs, for each solve,
+exactly the blocks of that solve's own launches, so a solve advanced inside
+a batch graph, or among other requests on the library's serving loop, must
+match the same solve advanced on its own bit for bit, whatever the launch
+shapes the tuner picks.
 """
+import time
+
 import numpy as np
 import pytest
 
@@ -20,13 +24,24 @@ from paper_1705_03750_gb300 import build as B  # noqa: E402
 
 B.build()
 from paper_1705_03750_gb300 import vlamet as V  # noqa: E402
-from paper_1705_03750_gb300.serve import GpuBackend, Request, Server  # noqa: E402
+from paper_1705_03750_gb300.serve import Request, run_open_loop  # noqa: E402
 
 
 def _solver(rc, prec):
     s = V.Solver(V.Config.from_run(rc, prec), stream=torch.cuda.Stream())
     s.set_f(I.initial_f(rc))
     return s
+
+
+def _same(s1, s2):
+    s1.sync()
+    s2.sync()
+    np.testing.assert_array_equal(s1.read_f(), s2.read_f())
+    np.testing.assert_array_equal(s1.read_fini(), s2.read_fini())
+    np.testing.assert_array_equal(s1.elements(), s2.elements())
+    d1, d2 = s1.density_force(), s2.density_force()
+    for k in d1:
+        np.testing.assert_array_equal(d1[k], d2[k])
 
 
 @pytest.mark.parametrize("prec", [V.VM_FP32_MIXED, V.VM_FP64])
@@ -36,41 +51,82 @@ def test_batch_graph_matches_individual_solves(prec):
     for s in alone:
         s.step(23)                      # two remaps included
     batched = [_solver(rc, prec) for rc in cfgs]
-    b = V.Batch(batched, nstreams=4)
+    b = V.Batch(batched)
     b.step(20)
     b.step(3)
-    assert b.launches_per_step(False) > 0 and b.launches_per_step(True) > b.launches_per_step(False)
+    # about twenty launches per step for the whole batch
+    assert 0 < b.launches_per_step(False) < 40 and b.launches_per_step(True) > b.launches_per_step(False)
     for s1, s2 in zip(alone, batched):
-        s1.sync()
-        s2.sync()
-        np.testing.assert_array_equal(s1.read_f(), s2.read_f())
-        np.testing.assert_array_equal(s1.read_fini(), s2.read_fini())
-        np.testing.assert_array_equal(s1.elements(), s2.elements())
-        d1, d2 = s1.density_force(), s2.density_force()
-        for k in d1:
-            np.testing.assert_array_equal(d1[k], d2[k])
+        _same(s1, s2)
+        assert s2.diagnostics()["step"] == 23
     b.close()
 
 
-def test_batch_refuses_solves_out_of_phase():
+def test_batch_autotune_changes_no_result():
+    cfgs = [I.batch_member(i).with_(n_s=6) for i in range(10, 18)]
+    prec = V.VM_FP32_MIXED
+    alone = [_solver(rc, prec) for rc in cfgs]
+    for s in alone:
+        s.step(20)
+    batched = [_solver(rc, prec) for rc in cfgs]
+    b = V.Batch(batched)
+    t = b.autotune(1)                   # 4 shapes x 1 timed step (and a remap step when one comes)
+    assert t["tuned"] and set(t["blocks_per_sm"].values()) <= {1, 2, 4, 8}
+    done = batched[0].diagnostics()["step"]
+    assert done >= 4
+    b.step(20 - done)
+    for s1, s2 in zip(alone, batched):
+        _same(s1, s2)
+    b.close()
+
+
+def test_batch_refuses_solves_out_of_phase_or_precision():
     a = _solver(I.batch_member(0).with_(n_s=10), V.VM_FP32_MIXED)
     c = _solver(I.batch_member(1).with_(n_s=10), V.VM_FP32_MIXED)
     a.step(1)
     with pytest.raises(V.VlametError) as e:
         V.Batch([a, c])
     assert e.value.status == 7
+    d = _solver(I.batch_member(2).with_(n_s=10), V.VM_FP64)
+    with pytest.raises(V.VlametError) as e:
+        V.Batch([c, d])
+    assert e.value.status == 1
 
 
-def test_served_result_is_the_same_alone_and_in_the_mix():
-    mk = lambda i, nx, nv, steps: Request(i, I.HALOS_4096.with_(nx=nx, nv=nv, seed=100 + i), steps, 0.0)  # noqa: E731
-    target = lambda: mk(0, 384, 320, 30)  # noqa: E731
-    srv = Server(GpuBackend(), budget_bytes=8 << 30, max_active=8, ic_fn=I.initial_f)
-    srv.run([target()])
-    alone = srv.done[0].result
-    mix = [target()] + [mk(i, 256 + 64 * i, 512 - 32 * i, 10 + 7 * i) for i in range(1, 6)]
-    srv2 = Server(GpuBackend(), budget_bytes=8 << 30, max_active=4, ic_fn=I.initial_f)
-    rep = srv2.run(mix)
-    assert rep["requests"] == 6 and srv2.peak_active >= 2
-    in_mix = next(r for r in srv2.done if r.rid == 0).result
-    for k in alone:
-        np.testing.assert_array_equal(alone[k], in_mix[k])
+def _served(reqs, budget=8 << 30, max_active=8, tick=3):
+    srv = V.NativeServer(budget, max_active=max_active, steps_per_tick=tick)
+    rep = run_open_loop(srv, reqs, ic_fn=I.initial_f, keep_results=True)
+    return srv, rep
+
+
+def test_served_result_is_the_same_alone_in_the_mix_and_stepped_directly():
+    mk = lambda i, nx, nv, steps, t: Request(i, I.HALOS_4096.with_(nx=nx, nv=nv, s=8, n_s=7, seed=100 + i),  # noqa: E731
+                                              steps, t)
+    target = lambda: mk(0, 384, 320, 30, 0.0)  # noqa: E731
+    _, rep = _served([target()])
+    assert rep["requests"] == 1 and rep["failed"] == 0
+    # the same solve stepped by vm_step on its own
+    rc = target().config
+    s = V.Solver(V.Config.from_run(rc, V.VM_FP32_MIXED))
+    s.set_f(I.initial_f(rc))
+    s.step(30)
+    direct = s.density_force()
+    mix = [target()] + [mk(i, 256 + 64 * i, 512 - 32 * i, 10 + 7 * i, 0.002 * i) for i in range(1, 6)]
+    srv, rep2 = _served(mix, max_active=4)
+    assert rep2["requests"] == 6 and rep2["failed"] == 0 and rep2["peak_active"] >= 2
+    res = next(r for r in mix if r.rid == 0).result
+    for k in direct:
+        np.testing.assert_array_equal(direct[k], res[k])
+    st = srv.stats()
+    assert st["group_steps"] < sum(r.steps for r in mix)   # steps of different requests shared launches
+    assert st["used_bytes"] == 0 and st["active"] == 0
+
+
+def test_server_budget_bounds_the_resident_set_and_refuses_what_never_fits():
+    rc = I.HALOS_4096.with_(nx=256, nv=256, s=8, n_s=5)
+    need = V.workspace_bytes(V.Config.from_run(rc, V.VM_FP32_MIXED))
+    reqs = [Request(i, rc.with_(seed=i), 12, 0.0) for i in range(4)]
+    big = Request(9, rc.with_(nx=2048, nv=2048), 3, 0.0)
+    srv, rep = _served(reqs + [big], budget=int(1.5 * need))
+    assert rep["requests"] == 5 and rep["failed"] == 1 and "status 6" in big.error
+    assert rep["peak_active"] == 1 and srv.stats()["peak_bytes"] <= 1.5 * need

@@ -304,10 +304,19 @@ def test_halos_4096_first_step_full_grid(prec):
     assert (s.read_map() == mo).all()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("windows", [0, 1])
-def test_halos_4096_remap_after_a_cycle_full_grid(windows):
+def test_halos_4096_evolved_state_transport_and_remap_full_grid(prec, windows):
+    """The state the timed steps run on: 24 steps of the 4096^2 halo workload
+    on the GPU (sheared elements, long boundary bands in the large map
+    windows, certified FP32 decisions on the FP32-mixed path).  Its elements
+    and its f_ini (widened from the stored precision) are injected into the
+    oracle; then, on the full grid: one transport reconstruction (map bit for
+    bit, f and M to the per-step bar), the remap (resampled f_ini and the
+    spline coefficients of the row and column sweeps), and the first
+    transport step after it (the step whose every Q_v lies on a node)."""
     rc = I.HALOS_4096
-    cfg = V.Config.from_run(rc.with_(n_s=10 ** 6))
+    cfg = V.Config.from_run(rc.with_(n_s=10 ** 6), PREC[prec])
     cfg.map_windows = windows
     s = V.Solver(cfg)
     f0 = I.initial_f(rc)
@@ -315,16 +324,29 @@ def test_halos_4096_remap_after_a_cycle_full_grid(windows):
     s.step(rc.n_s - 1)
     s.sync()
     el = s.elements()
-    o = O.Oracle(rc.nx, rc.nv, rc.x_lo, rc.x_hi, rc.v_lo, rc.v_hi, rc.s, rc.dt, rc.n_s, rc.G)
-    o.set_f(f0)
+    o = O.Oracle(rc.nx, rc.nv, rc.x_lo, rc.x_hi, rc.v_lo, rc.v_hi, rc.s, rc.dt, 10 ** 6, rc.G)
+    o.set_f(s.read_fini())
     o.set_elements(np.ascontiguousarray(el.T))
-    s.compute_map()
+    # transport reconstruction at the evolved elements
+    s.reconstruct()
+    fo = o.reconstruct()
     mo, _ = o.compute_map()
     assert (s.read_map() == mo).all()
-    fo, _ = o.remap_resample()
+    assert_f_close(s.read_f(), fo)
+    dg, do = s.density_force(), o.density_force()
+    tol = 1e-12 * do["Mtot"] if prec == "fp64" else F_TOL * rc.nv * np.abs(fo).max() * rc.dx * rc.dv
+    np.testing.assert_allclose(dg["M"], do["M"], rtol=0, atol=tol)
+    # the remap: Q_r blend, spline of f_ini, the new f_ini and its coefficients
     s.remap()
+    o.remap()
     s.sync()
-    assert_f_close(s.read_fini(), fo)
+    assert_f_close(s.read_fini(), o.fini())
+    eo = o.eta()
+    assert np.abs(s.read_eta() - eo).max() <= (1e-12 if prec == "fp64" else 1e-6) * np.abs(eo).max()
+    # the first step after the remap, from each side's own state
+    s.step(1)
+    o.step(1)
+    assert_f_close(s.read_f(), o.last_f())
 
 
 # ---------------------------------------------------------------------------

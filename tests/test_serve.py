@@ -1,9 +1,11 @@
-"""Scheduling of the serving layer with a fake device backend (no GPU)."""
+"""The open-loop serving driver (submission at arrival times, latency from
+arrival to the poll that returns the result, percentiles, refused and
+failed requests) against a fake of the library's serving loop (no GPU)."""
 import math
 
 import pytest
 
-from paper_1705_03750_gb300.serve import Request, Server, poisson_requests
+from paper_1705_03750_gb300.serve import Request, poisson_requests, run_open_loop
 
 
 class FakeClock:
@@ -11,93 +13,80 @@ class FakeClock:
         self.t = 0.0
 
     def __call__(self):
+        self.t += 1e-4          # every look at the clock takes a little time
         return self.t
 
 
-class FakeBackend:
-    """Each request's footprint is nx*nv bytes; a step of a request takes one
-    tick; the clock advances 1 per tick."""
+class FakeServer:
+    """Each request finishes `steps` polls after its submission; submissions
+    with nx > limit are refused; request ids listed in `fail` finish with a
+    non-zero status."""
 
-    def __init__(self, clock):
-        self.clock = clock
-        self.log = []
+    def __init__(self, clock, limit=10 ** 9, fail=()):
+        self.clock, self.limit, self.fail = clock, limit, set(fail)
+        self.live = {}
+        self.submitted = []
+        self.next = 100
+        self.peak = 0
 
-    def footprint(self, cfg):
-        return cfg[0] * cfg[1]
+    def submit(self, cfg, f0, steps):
+        if cfg[0] > self.limit:
+            raise RuntimeError("vm_server_submit: memory budget exceeded (status 6)")
+        rid = self.next
+        self.next += 1
+        self.live[rid] = [steps, cfg]
+        self.submitted.append((rid, self.clock.t))
+        self.peak = max(self.peak, len(self.live))
+        return rid
 
-    def start(self, req, f0):
-        self.log.append(("start", req.rid, self.clock.t))
-        return {"left": req.steps, "rid": req.rid}
+    def poll(self):
+        out = []
+        for rid in list(self.live):
+            self.live[rid][0] -= 1
+            if self.live[rid][0] <= 0:
+                del self.live[rid]
+                out.append({"id": rid, "status": 5 if rid in self.fail else 0})
+        return out
 
-    def advance(self, h, n):
-        h["left"] -= n
-        self.clock.t += 0.001
+    def result(self, rid):
+        return {"rid": rid}
 
-    def done(self, h):
-        return h["left"] == 0
-
-    def result(self, h):
-        return {"rid": h["rid"]}
-
-    def release(self, h):
-        self.log.append(("end", h["rid"], self.clock.t))
+    def stats(self):
+        return {"peak_active": self.peak}
 
 
-def test_budget_and_slots_bound_the_active_set():
+def test_arrivals_are_submitted_at_their_time_and_latency_counts_from_arrival():
     clock = FakeClock()
-    be = FakeBackend(clock)
-    srv = Server(be, budget_bytes=100, max_active=3, clock=clock)
-    reqs = [Request(i, (5, 10), steps=3 + i, arrival=0.0) for i in range(8)]   # 50 B each
-    rep = srv.run(reqs)
-    assert rep["requests"] == 8
-    assert srv.peak_used <= 100 and srv.peak_active <= 2       # the budget binds before the slots
-    assert all(r.result["rid"] == r.rid for r in srv.done)
-    # first come, first served
-    starts = [rid for kind, rid, _ in be.log if kind == "start"]
-    assert starts == sorted(starts)
+    srv = FakeServer(clock)
+    reqs = [Request(0, (4, 4), steps=5, arrival=0.0), Request(1, (4, 4), steps=5, arrival=0.01)]
+    rep = run_open_loop(srv, reqs, ic_fn=lambda c: None, clock=clock)
+    assert rep["requests"] == 2 and rep["failed"] == 0
+    t_sub = dict(srv.submitted)
+    assert t_sub[101] - t_sub[100] >= 0.01 - 2e-4      # the second waited for its arrival
+    r0, r1 = sorted(reqs, key=lambda r: r.rid)
+    assert 0 < r0.latency < 0.01 and 0 < r1.latency < 0.01
+    assert r1.latency == pytest.approx(r1.finished - 0.01)
 
 
-def test_arrivals_wait_for_their_time_and_latency_counts_from_arrival():
+def test_report_percentiles_and_throughput():
     clock = FakeClock()
-    be = FakeBackend(clock)
-
-    class TickingBackend(FakeBackend):
-        pass
-
-    srv = Server(be, budget_bytes=10 ** 6, max_active=8, clock=clock)
-    reqs = [Request(0, (4, 4), steps=5, arrival=0.0), Request(1, (4, 4), steps=5, arrival=0.003)]
-
-    # advance the clock while idle so that the second arrival comes due
-    orig = srv._admit
-
-    def admit():
-        if not srv.active and srv.waiting:
-            clock.t += 0.001
-        orig()
-    srv._admit = admit
-    srv.run(reqs)
-    r0, r1 = sorted(srv.done, key=lambda r: r.rid)
-    assert r1.admitted >= 0.003 - 1e-12
-    assert r0.latency > 0 and r1.latency > 0
-    assert r1.latency == pytest.approx(r1.finished - 0.003)
-
-
-def test_request_larger_than_the_budget_is_refused():
-    clock = FakeClock()
-    srv = Server(FakeBackend(clock), budget_bytes=10, clock=clock)
-    with pytest.raises(ValueError):
-        srv.submit(Request(0, (10, 10), steps=1, arrival=0.0))
-
-
-def test_report_percentiles():
-    clock = FakeClock()
-    be = FakeBackend(clock)
-    srv = Server(be, budget_bytes=10 ** 9, max_active=100, clock=clock)
     reqs = [Request(i, (8, 8), steps=1 + (i % 10), arrival=0.0) for i in range(100)]
-    rep = srv.run(reqs)
-    lat = sorted(r.latency for r in srv.done)
+    rep = run_open_loop(FakeServer(clock), reqs, ic_fn=lambda c: None, clock=clock)
+    lat = sorted(r.latency for r in reqs)
     assert rep["p50_latency_s"] == lat[49] and rep["p99_latency_s"] == lat[98]
-    assert rep["cell_updates_per_s"] > 0
+    assert rep["cell_updates_per_s"] == pytest.approx(sum(64 * r.steps for r in reqs) / rep["wall_s"])
+    assert rep["peak_active"] == 100
+
+
+def test_refused_and_failed_requests_are_reported_and_the_rest_complete():
+    clock = FakeClock()
+    srv = FakeServer(clock, limit=16, fail={102})
+    reqs = [Request(i, (32 if i == 1 else 8, 8), steps=2 + i, arrival=0.0) for i in range(5)]
+    rep = run_open_loop(srv, reqs, ic_fn=lambda c: None, clock=clock, keep_results=True)
+    assert rep["requests"] == 5 and rep["failed"] == 2
+    bad = sorted((r for r in reqs if r.error), key=lambda r: r.rid)
+    assert "status 6" in bad[0].error and bad[1].error == "status 5"
+    assert all(r.result for r in reqs if not r.error)
 
 
 def test_poisson_requests_are_seeded():
@@ -107,67 +96,3 @@ def test_poisson_requests_are_seeded():
     assert all(256 <= nx <= 2048 and nx % 32 == 0 for nx, _ in (r.config for r in a))
     arr = [r.arrival for r in a]
     assert arr == sorted(arr) and not math.isnan(arr[-1])
-
-
-def test_a_failed_solve_is_reported_and_the_rest_complete():
-    clock = FakeClock()
-
-    class Failing(FakeBackend):
-        def result(self, h):
-            if h["rid"] == 2:
-                raise RuntimeError("device status 5")
-            return super().result(h)
-
-    srv = Server(Failing(clock), budget_bytes=10 ** 6, max_active=4, clock=clock)
-    rep = srv.run([Request(i, (4, 4), steps=2 + i, arrival=0.0) for i in range(5)])
-    assert rep["requests"] == 5 and rep["failed"] == 1
-    bad = [r for r in srv.done if r.error]
-    assert [r.rid for r in bad] == [2] and "status 5" in bad[0].error and bad[0].result == {}
-    assert srv.used == 0
-
-
-def test_a_solve_that_fails_while_stepping_is_retired():
-    clock = FakeClock()
-
-    class Failing(FakeBackend):
-        def advance(self, h, n):
-            if h["rid"] == 1 and h["left"] < 4:
-                raise RuntimeError("vm_step: CUDA runtime error")
-            super().advance(h, n)
-
-    srv = Server(Failing(clock), budget_bytes=10 ** 6, max_active=2, clock=clock)
-    rep = srv.run([Request(i, (4, 4), steps=6, arrival=0.0) for i in range(4)])
-    assert rep["requests"] == 4 and rep["failed"] == 1
-    assert [r.rid for r in srv.done if r.error] == [1] and srv.used == 0
-
-
-def test_a_request_that_cannot_start_is_retired():
-    clock = FakeClock()
-
-    class Refusing(FakeBackend):
-        def start(self, req, f0):
-            if req.rid == 0:
-                raise ValueError("expected an array of shape (4, 4)")
-            return super().start(req, f0)
-
-    srv = Server(Refusing(clock), budget_bytes=10 ** 6, max_active=2, clock=clock)
-    rep = srv.run([Request(i, (4, 4), steps=3, arrival=0.0) for i in range(3)])
-    assert rep["requests"] == 3 and rep["failed"] == 1 and srv.used == 0
-
-
-def test_solves_that_are_not_ready_are_skipped_in_a_tick():
-    clock = FakeClock()
-
-    class Busy(FakeBackend):
-        def __init__(self, clock):
-            super().__init__(clock)
-            self.asked = 0
-
-        def ready(self, h):
-            self.asked += 1
-            return self.asked % 2 == 0     # every other query says "still busy"
-
-    be = Busy(clock)
-    srv = Server(be, budget_bytes=10 ** 6, max_active=3, clock=clock)
-    rep = srv.run([Request(i, (4, 4), steps=4, arrival=0.0) for i in range(3)])
-    assert rep["requests"] == 3 and rep["failed"] == 0 and be.asked > 12
