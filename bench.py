@@ -128,6 +128,25 @@ def algorithmic(kernel: str, rc, fp32: bool, ne: int):
     return None
 
 
+# FP64 floating-point operations per site of the FP64 path's reconstruction
+# on its certified branch (a fused multiply-add counts 2): site position 2,
+# P - P_m 2, the second-order offset Q - Q_m 36, the anchored index
+# coordinates 4, the offsets from the nodes 2, the six-point value 29.
+FP64_FLOPS_PER_SITE = 75
+
+
+def fp64_roofline(sites: int, avg_s: float) -> dict:
+    """The FP64 reconstruction against the FP64 arithmetic peak measured on
+    this device in the same run (vm_measure_fp64_peak: FMA chains, 2 FLOP per
+    FMA)."""
+    from paper_1705_03750_gb300 import vlamet as V
+    peak = V.measure_fp64_peak(20000)
+    ach = FP64_FLOPS_PER_SITE * sites / avg_s
+    return {"kernel": "reconstruct", "bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12,
+            "unit": "TFLOP/s (FP64)", "frac": ach / peak, "per_unit": f"{FP64_FLOPS_PER_SITE} FP64 FLOP/site",
+            "units": sites, "avg_ms": avg_s * 1e3, "peak_kind": "measured in this run (FMA chains)"}
+
+
 def step_bytes_per_update(rc, fp32: bool) -> float:
     """Algorithmic bytes of one cell update of the whole step: f_ini read and
     f written once, the element state read and written once per element
@@ -422,6 +441,9 @@ def run_native(args, rank: int, world: int, dist):
                              "gpu_launches": f64["launches"], "clocks": f64["clocks"],
                              "e2e": f64["e2e"], "whole_run": f64["whole"],
                              "top_kernels": {k: round(v[1], 3) for k, v in sorted(f64["stats"].items(), key=lambda kv: -kv[1][1])[:4]}}
+        rl = f64["stats"].get("reconstruct")
+        if rl and rl[0] > 0:
+            line["fp64_path"]["roofline"] = fp64_roofline(cells, rl[1] / rl[0] / 1e3)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(rc, f0)
     if world == 1 and not args.no_serve:

@@ -399,9 +399,6 @@ vm_status vm::solver_create(const vm_config* c, void* d_workspace, size_t bytes,
   g.literal_fd = c->literal_fd;
   g.max_hole_rounds = s->cfg.max_hole_rounds;
   g.fth_on = c->f_th > 0.0 ? 1 : 0;
-  // 64 ulps of the index coordinate's largest reference terms (recon.cu)
-  g.eps_u = 64.0 * 0x1p-53 * ((fabs(c->x_lo) + fabs(c->x_hi)) / g.dx + (double)c->nx + 8.0);
-  g.eps_w = 64.0 * 0x1p-53 * ((fabs(c->v_lo) + fabs(c->v_hi)) / g.dv + (double)c->nv + 8.0);
   g.klo = 0;
   g.khi = g.Lx - 1;
   g.llo = 0;

@@ -42,9 +42,6 @@ struct Grid {
   // llo..lhi (the whole lattice when fth_on is 0)
   int32_t fth_on;
   int32_t klo, khi, llo, lhi;
-  // bound on |anchored - fixed-order| index coordinate of the FP64 path's
-  // reconstruction (recon.cu), per axis
-  double eps_u, eps_w;
 };
 
 // Small device-resident control block.

@@ -2153,12 +2153,22 @@ void group_map(const GroupPlan& G) {
   k_holes_group<<<group_grid(G, GP_HOLES, 152), HT, 0, st>>>(G.D, G.off_dyn, ns);
 }
 
-// Opt the group's large-window kernels in to shared memory (as map_prepare does).
+// Opt the group's large-window kernels in to shared memory (as map_prepare
+// does), up to the per-block limit less their static shared memory.
+template <typename K>
+static cudaError_t opt_in(K kernel) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(SMEM_MAX - fa.sharedSizeBytes));
+}
+
 bool group_map_prepare() {
-  return cudaFuncSetAttribute(k_claim_big_group<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX) ==
-             cudaSuccess &&
-         cudaFuncSetAttribute(k_claim_big_group<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX) ==
-             cudaSuccess;
+  cudaError_t e = opt_in(k_claim_big_group<0>);
+  if (e == cudaSuccess) e = opt_in(k_claim_big_group<1>);
+  if (e != cudaSuccess) note_cuda(e);
+  return e == cudaSuccess;
 }
 
 }  // namespace vm

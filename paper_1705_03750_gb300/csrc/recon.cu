@@ -91,26 +91,17 @@ __device__ __forceinline__ void zero_outside(const Grid& g, R* __restrict__ row,
   for (int j = j1 + 1 + threadIdx.x; j < g.nv; j += blockDim.x) row[j] = R(0);
 }
 
-// FP64 path, fused interpolation.  Q - Q_m is evaluated in the fixed order
-// (so it is the reference order's to the bit), but the index coordinate is
-// anchored on the exact lattice position of Q_m ((n-1)/2 + (k-K-1)s, an
-// integer or a half) with one fused operation, instead of (Q_m + dq - x_lo)
-// / dx in three roundings.  The two differ by at most the roundings of the
-// reference's constants and operations, bounded per grid by Grid::eps_u,
-// eps_w (computed on the host: 64 ulps of (|x_lo| + |x_hi|)/dx + n + 8).
-// The nearest node and the containing cell are taken from the anchored value
-// when it lies farther than that bound from every decision boundary,
-// otherwise the caller evaluates the site in the fixed order; the six-point
-// value uses fused operations (rounding changes only).
-__device__ __forceinline__ bool decide64(double u, double eps, long long& in, long long& ic, double& dq) {
-  const double fl = floor(u);
-  const double r = u - fl;  // exact
-  if (!(r > eps && r < 1.0 - eps && fabs(r - 0.5) > eps)) return false;
-  ic = (long long)fl;
-  in = (r >= 0.5) ? ic + 1 : ic;
-  dq = u - (double)in;  // exact
-  return true;
-}
+// FP64 path.  The integer decisions (nearest node, containing cell) come
+// from the FP32 record's certified evaluation, which is the fixed-order FP64
+// evaluation's whenever its bound clears every decision boundary (as on the
+// FP32-mixed path); the offset Q - Q_m is then evaluated in FP64 with fused
+// operations, anchored on the exact lattice position of Q_m, and the
+// six-point value with fused operations (rounding changes only).  A site
+// whose decision the bound leaves open (the step after a remap puts every
+// Q on a node) is evaluated entirely in the fixed order.
+__device__ __forceinline__ bool recon64_fast(const Grid& g, const double* __restrict__ t, const float* __restrict__ F,
+                                             int m, int i, int j, double Px, double Pv,
+                                             const double* __restrict__ fini, float inv_Lv, double& val);
 
 __device__ __forceinline__ double qinterp64_fused(const double* __restrict__ F, const Grid& g, long long in,
                                                   long long jn, long long ic, long long jc, double x, double y) {
@@ -124,31 +115,10 @@ __device__ __forceinline__ double qinterp64_fused(const double* __restrict__ F, 
   return fma(cross, x * y, f);
 }
 
-// f at site (i, j) owned by element m with offsets dq (fixed order); false
-// when a decision is not certain.
-__device__ __forceinline__ bool recon_site64_fused(const Grid& g, int m, double dqx, double dqv,
-                                                   const double* __restrict__ fini, double& val) {
-  const double eu = g.eps_u, ew = g.eps_w;
-  const int k = m / g.Lv, l = m - k * g.Lv;
-  const double ua = 0.5 * (double)((g.nx - 1) + 2 * (k - g.Kx - 1) * g.s);
-  const double wa = 0.5 * (double)((g.nv - 1) + 2 * (l - g.Kv - 1) * g.s);
-  const double u = fma(dqx, g.inv_dx, ua), w = fma(dqv, g.inv_dv, wa);
-  if (!(u > -2.0 + eu && u < (double)g.nx + 1.0 - eu && w > -2.0 + ew && w < (double)g.nv + 1.0 - ew)) {
-    // outside the interpolation's reach, or too close to its edge to tell
-    if (u > -2.0 - eu && u < (double)g.nx + 1.0 + eu && w > -2.0 - ew && w < (double)g.nv + 1.0 + ew) return false;
-    val = 0.0;
-    return true;
-  }
-  long long in, ic, jn, jc;
-  double x, y;
-  if (!decide64(u, eu, in, ic, x) || !decide64(w, ew, jn, jc, y)) return false;
-  val = qinterp64_fused(fini, g, in, jn, ic, jc, x, y);
-  return true;
-}
-
 __device__ __forceinline__ void k_recon64_body(const Grid& g, const uint32_t* __restrict__ map, const DevState* ds,
-                                                 const double* __restrict__ tay, const double* __restrict__ fini,
-                                                 double* __restrict__ f, double* __restrict__ M, int vb) {
+                                                 const double* __restrict__ tay, const float* __restrict__ tayf,
+                                                 const double* __restrict__ fini, double* __restrict__ f,
+                                                 double* __restrict__ M, int vb) {
   using R = double;
   __shared__ double sh[32];
   const int i = vb;
@@ -156,6 +126,7 @@ __device__ __forceinline__ void k_recon64_body(const Grid& g, const uint32_t* __
   int js, je;
   row_span(g, ds, i, js, je);
   zero_outside(g, f + (size_t)i * g.nv, js, je);
+  const float inv_Lv = 1.0f / (float)g.Lv;
   double acc = 0.0;
   for (int j = js + threadIdx.x; j <= je; j += blockDim.x) {
     const size_t p = (size_t)i * g.nv + j;
@@ -163,10 +134,11 @@ __device__ __forceinline__ void k_recon64_body(const Grid& g, const uint32_t* __
     double val = 0.0;
     if (m >= 0) {
       const double* t = tay + (size_t)m * TY_N;
-      double dqx, dqv;
-      qofp_exact(t, Px, site_v(g, j), dqx, dqv);
-      if (!recon_site64_fused(g, m, dqx, dqv, fini, val)) {
-        // a decision the anchored value cannot settle: the fixed order
+      const double Pv = site_v(g, j);
+      if (!recon64_fast(g, t, tayf + (size_t)m * TF_N, m, i, j, Px, Pv, fini, inv_Lv, val)) {
+        // a decision the FP32 bound cannot settle: the fixed order
+        double dqx, dqv;
+        qofp_exact(t, Px, Pv, dqx, dqv);
         const double u = dmul(dsub(dadd(t[TY_QX], dqx), g.x_lo), g.inv_dx);
         const double w = dmul(dsub(dadd(t[TY_QV], dqv), g.v_lo), g.inv_dv);
         val = qinterp(fini, g, u, w);
@@ -181,9 +153,10 @@ __device__ __forceinline__ void k_recon64_body(const Grid& g, const uint32_t* __
 }
 
 __global__ void __launch_bounds__(256) k_recon64(Grid g, const uint32_t* __restrict__ map, const DevState* ds,
-                                                 const double* __restrict__ tay, const double* __restrict__ fini,
-                                                 double* __restrict__ f, double* __restrict__ M) {
-  k_recon64_body(g, map, ds, tay, fini, f, M, blockIdx.x);
+                                                 const double* __restrict__ tay, const float* __restrict__ tayf,
+                                                 const double* __restrict__ fini, double* __restrict__ f,
+                                                 double* __restrict__ M) {
+  k_recon64_body(g, map, ds, tay, tayf, fini, f, M, blockIdx.x);
 }
 
 // Monaghan M4 kernel, unnormalised (Sec. 2.3.2).
@@ -593,6 +566,41 @@ __device__ __forceinline__ void k_recon32_body(const Grid& g, const uint32_t* __
   if (threadIdx.x == 0) M[i] = dmul(rowsum, g.dxdv);
 }
 
+__device__ __forceinline__ bool recon64_fast(const Grid& g, const double* __restrict__ t, const float* __restrict__ F,
+                                             int m, int i, int j, double Px, double Pv,
+                                             const double* __restrict__ fini, float inv_Lv, double& val) {
+  const float inv_s = 1.0f / (float)g.s, fs = (float)g.s;
+  float px, pv;
+  p_of(F, i, j, inv_s, px, pv);
+  const QF q = qeval(F, px, pv);
+  int Bu, Bw;
+  float bu, bw;
+  anchor_r(g, m, inv_Lv, Bu, bu, Bw, bw);
+  const float ru = bu + fs * q.qx, rw = bw + fs * q.qv;
+  const float eu = fs * q.ex + 1e-6f * (1.f + fabsf(ru)), ew = fs * q.ev + 1e-6f * (1.f + fabsf(rw));
+  if (!(fabsf(ru) < 1e6f && fabsf(rw) < 1e6f)) return false;
+  const float tu = 2.f * ru, tw = 2.f * rw;
+  const float fu = floorf(tu), fw = floorf(tw);
+  if (!((tu - 2.f * eu > fu) && (tu + 2.f * eu < fu + 1.f) && (tw - 2.f * ew > fw) && (tw + 2.f * ew < fw + 1.f)))
+    return false;
+  const int iu = (int)fu, iw = (int)fw;
+  const long long in = Bu + ((iu + 1) >> 1), jn = Bw + ((iw + 1) >> 1);
+  const long long ic = Bu + (iu >> 1), jc = Bw + (iw >> 1);
+  // FP64 offset, fused, on the exact lattice index of Q_m
+  const double dPx = Px - t[TY_X], dPv = Pv - t[TY_V];
+  const double yx = fma(t[TY_TI00], dPx, t[TY_TI01] * dPv), yv = fma(t[TY_TI10], dPx, t[TY_TI11] * dPv);
+  double g0 = fma(t[TY_GX00], dPx, t[TY_GX01] * dPv), g1 = fma(t[TY_GX01], dPx, t[TY_GX11] * dPv);
+  const double sx = fma(dPx, g0, dPv * g1);
+  g0 = fma(t[TY_GV00], dPx, t[TY_GV01] * dPv);
+  g1 = fma(t[TY_GV01], dPx, t[TY_GV11] * dPv);
+  const double sv = fma(dPx, g0, dPv * g1);
+  const double dqx = fma(-0.5, fma(t[TY_TI00], sx, t[TY_TI01] * sv), yx);
+  const double dqv = fma(-0.5, fma(t[TY_TI10], sx, t[TY_TI11] * sv), yv);
+  const double u = fma(dqx, g.inv_dx, (double)Bu + (double)bu), w = fma(dqv, g.inv_dv, (double)Bw + (double)bw);
+  val = qinterp64_fused(fini, g, in, jn, ic, jc, u - (double)in, w - (double)jn);
+  return true;
+}
+
 __global__ void __launch_bounds__(256, 6) k_recon32(Grid g, const uint32_t* __restrict__ map, const DevState* ds,
                                                  const double* __restrict__ tay, const float* __restrict__ tayf,
                                                  const float* __restrict__ fini, float* __restrict__ f,
@@ -740,7 +748,7 @@ __global__ void __launch_bounds__(256, 6) k_recon_group32(const SolveDesc* __res
 __global__ void __launch_bounds__(256) k_recon_group64(const SolveDesc* __restrict__ D, const int* __restrict__ off,
                                                      int ns, int total) {
   GROUP_LOOP(off, ns, total)
-  k_recon64_body(gsh, d.map, d.ds, d.tay, (const double*)d.fini, (double*)d.f, d.M, vb);
+  k_recon64_body(gsh, d.map, d.ds, d.tay, d.tayf, (const double*)d.fini, (double*)d.f, d.M, vb);
   GROUP_END
 }
 
@@ -819,7 +827,7 @@ void launch_reconstruct(vm_solver* s) {
     k_recon32<<<s->g.nx, nt, 0, s->stream>>>(s->g, s->map, s->ds, s->tay, s->tayf, (const float*)s->fini,
                                               (float*)s->f, s->M);
   else
-    k_recon64<<<s->g.nx, nt, 0, s->stream>>>(s->g, s->map, s->ds, s->tay, (const double*)s->fini,
+    k_recon64<<<s->g.nx, nt, 0, s->stream>>>(s->g, s->map, s->ds, s->tay, s->tayf, (const double*)s->fini,
                                               (double*)s->f, s->M);
   prof_end(s, ps_);
   s->launches++;

@@ -340,9 +340,18 @@ def test_halos_4096_evolved_state_transport_and_remap_full_grid(prec, windows):
     s.remap()
     o.remap()
     s.sync()
-    assert_f_close(s.read_fini(), o.fini())
+    fio = o.fini()
+    assert_f_close(s.read_fini(), fio)
+    # the spline system (rows (1, 4, 1)/6, diagonally dominant) has an
+    # inverse of infinity-norm at most 1/(4/6 - 2/6) = 3 per axis, so an
+    # error e of f_ini moves eta by at most 9 |e| (here e <= 1e-6 max f_ini),
+    # plus the sweeps' own rounding (FP32: a few units of 6e-8 of max |eta|)
     eo = o.eta()
-    assert np.abs(s.read_eta() - eo).max() <= (1e-12 if prec == "fp64" else 1e-6) * np.abs(eo).max()
+    if prec == "fp64":
+        tol = 1e-12 * np.abs(eo).max()
+    else:
+        tol = 9 * F_TOL * np.abs(fio).max() + 1e-6 * np.abs(eo).max()
+    assert np.abs(s.read_eta() - eo).max() <= tol
     # the first step after the remap, from each side's own state
     s.step(1)
     o.step(1)
