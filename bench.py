@@ -275,6 +275,37 @@ def e2e_run(V, rc, prec, f0, args, dev, barrier, max_ranks, world):
                     f"{args.warmup}..{args.warmup + args.steps - 1} each with vm_density_force to host (timed)"}
 
 
+def recon_tiles_ab(V, rc, f0_dev, args, row_stats) -> dict:
+    """The FP32-mixed step with the reconstruction in tiles staged by bulk
+    copies (recon_mode 1) over the same steps, beside the one-block-per-row
+    kernel of the headline: step time and the reconstruction's launch time
+    (events around each launch, second pass as for the headline)."""
+    import torch
+    cfg = V.Config.from_run(rc, V.VM_FP32_MIXED)
+    cfg.recon_mode = 1
+    s = V.Solver(cfg)
+    s.set_f(f0_dev)
+    s.step(args.warmup)
+    s.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s.stream)
+    s.step(args.steps)
+    e1.record(s.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    s.profile(True)
+    s.step(args.steps)
+    st = s.profile_read()
+    s.profile(False)
+    s.sync()
+    del s
+    rec = st.get("reconstruct", (1, float("nan")))
+    row = row_stats.get("reconstruct", (1, float("nan")))
+    return {"ms_per_step": ms / args.steps, "value": rc.nx * rc.nv * args.steps / (ms / 1e3),
+            "reconstruct_ms": rec[1] / rec[0], "row_kernel_reconstruct_ms": row[1] / row[0],
+            "what": "FP32-mixed step with recon_mode 1 (tiles, f_ini patch by cp.async.bulk), same steps"}
+
+
 def whole_run(V, rc, prec, f0_dev, steps, dev):
     """All `steps` steps of one solve from vm_set_f (remaps included), timed
     with CUDA events on the solver's stream, plus the rate of the last
@@ -444,6 +475,8 @@ def run_native(args, rank: int, world: int, dist):
         rl = f64["stats"].get("reconstruct")
         if rl and rl[0] > 0:
             line["fp64_path"]["roofline"] = fp64_roofline(cells, rl[1] / rl[0] / 1e3)
+    if world == 1 and not args.no_ab:
+        line["recon_tiles"] = recon_tiles_ab(V, rc, f0_dev, args, stats)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(rc, f0)
     if world == 1 and not args.no_serve:
@@ -711,6 +744,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the reduced serving sample")
+    ap.add_argument("--no-ab", action="store_true", help="skip the staged-tile reconstruction comparison")
     ap.add_argument("--whole-run", type=int, default=1000,
                     help="steps of the whole-run rate (the configuration's 1000; 0: skip)")
     ap.add_argument("--whole-run-fp32-only", action="store_true")

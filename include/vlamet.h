@@ -99,6 +99,11 @@ typedef struct {
                                  elements' positions (f = 0 elsewhere).  The remap reads
                                  the rectangle back (vm_step synchronises once per remap);
                                  batches refuse it */
+  int32_t recon_mode;         /* FP32-mixed path's transport reconstruction: 0 one block per x
+                                 row, f_ini gathered through the caches; 1 tiles of 4 x rows by
+                                 256 v columns whose f_ini patch is staged in shared memory by
+                                 bulk copies (cp.async.bulk, the TMA engine).  Results agree to
+                                 rounding (the pixel masses are summed in another order) */
 } vm_config;
 
 typedef struct {

@@ -20,7 +20,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
   size_t fini, eta, f, tmp, map, slot1, rec_key, rec_site, holes_a, holes_b, ovf, gwin, seed, el, tay, tayf, M, a, da, d2a,
-      thx, thv, thxf, thvf, rect, ds, total;
+      thx, thv, thxf, thvf, rect, mpart, dpart, ds, total;
 };
 
 bool valid(const vm_config* c) {
@@ -34,6 +34,7 @@ bool valid(const vm_config* c) {
   if (!(c->c_dyn >= 0.0) || !isfinite(c->c_dyn)) return false;
   if (!(c->alpha >= 0.0) || !(c->beta >= 0.0)) return false;
   if (!(c->f_th >= 0.0) || !isfinite(c->f_th)) return false;
+  if (c->recon_mode != 0 && c->recon_mode != 1) return false;
   // 32-bit site indices; element indices fit the 24-bit field of the owner slots
   if ((long long)c->nx * (long long)c->nv >= (1ll << 31) / 2) return false;
   const long long s = c->elem_stride;
@@ -88,6 +89,8 @@ Layout layout(const vm_config* c) {
   L.thxf = take(2 * c->nx * 4);
   L.thvf = take(2 * c->nv * 4);
   L.rect = take(4 * vm::kRectBlocks * 8);
+  L.mpart = take((size_t)c->nx * (size_t)((c->nv + 255) / 256) * 8);
+  L.dpart = take(6 * vm::kRectBlocks * 8);
   L.ds = take(sizeof(vm::DevState));
   L.total = o;
   return L;
@@ -399,6 +402,7 @@ vm_status vm::solver_create(const vm_config* c, void* d_workspace, size_t bytes,
   g.literal_fd = c->literal_fd;
   g.max_hole_rounds = s->cfg.max_hole_rounds;
   g.fth_on = c->f_th > 0.0 ? 1 : 0;
+  g.recon_tiles = (c->precision == VM_FP32_MIXED && c->recon_mode == 1) ? 1 : 0;
   g.klo = 0;
   g.khi = g.Lx - 1;
   g.llo = 0;
@@ -433,8 +437,10 @@ vm_status vm::solver_create(const vm_config* c, void* d_workspace, size_t bytes,
   s->thomas_xf = (float*)(base + L.thxf);
   s->thomas_vf = (float*)(base + L.thvf);
   s->rect_part = (double*)(base + L.rect);
+  s->Mpart = (double*)(base + L.mpart);
+  s->diag_part = (double*)(base + L.dpart);
   s->ds = (vm::DevState*)(base + L.ds);
-  if (!vm::map_prepare(g)) {
+  if (!vm::map_prepare(g) || !vm::recon_prepare()) {
     free(s);
     return VM_E_INVALID_ARG;
   }

@@ -42,6 +42,7 @@ struct Grid {
   // llo..lhi (the whole lattice when fth_on is 0)
   int32_t fth_on;
   int32_t klo, khi, llo, lhi;
+  int32_t recon_tiles;  // FP32-mixed path: 1 = reconstruction in tiles staged by bulk copies
 };
 
 // Small device-resident control block.
@@ -119,10 +120,13 @@ enum { TY_X = 0, TY_V, TY_TI00, TY_TI01, TY_TI10, TY_TI11, TY_GX00, TY_GX01, TY_
 // uncombined terms (the coefficients of the bound are rounded up).  UF/WF
 // and UI/WI split the element's index position u_m = (x_m - x_lo)/dx into
 // integer and fraction.
+// Words 20-23 repeat u_m and w_m in FP64 (a 16-byte aligned pair), so that
+// the map's first tiers read one 128-byte line per neighbour.
 enum { TF_T00 = 0, TF_T01, TF_T10, TF_T11, TF_AX, TF_BX, TF_CX, TF_AV, TF_BV, TF_CV,
-       TF_C1X, TF_C2X, TF_C1V, TF_C2V, TF_UF, TF_WF, TF_UI, TF_WI, TF_N = 32 };
+       TF_C1X, TF_C2X, TF_C1V, TF_C2V, TF_UF, TF_WF, TF_UI, TF_WI, TF_UD = 20, TF_N = 32 };
 // the reconstruction reads words 0-15 of the FP32 record as four float4
 static_assert(TF_T00 == 0 && TF_AX == 4 && TF_BV == 8 && TF_C1V == 12 && TF_WF == 15, "FP32 record layout");
+static_assert(TF_UD % 4 == 0 && TF_UD >= TF_WI + 1 && TF_UD + 4 <= TF_N, "FP64 index positions in the FP32 record");
 
 constexpr unsigned long long KEY_EMPTY = ~0ull;
 
@@ -173,6 +177,8 @@ struct vm_solver {
   float* thomas_xf;
   float* thomas_vf;
   double* rect_part;        // kRectBlocks x 4 partial minima/maxima of the element positions
+  double* Mpart;            // nx x ceil(nv / 256) row sums of the reconstruction's tiles
+  double* diag_part;        // kRectBlocks x 6 partial sums of the diagnostics
   vm::DevState* ds;
   // host-side bookkeeping
   int32_t have_f;
@@ -227,6 +233,8 @@ void launch_map(vm_solver* s);
 void launch_read_map(vm_solver* s, int32_t* dst);
 // recon.cu
 void launch_reconstruct(vm_solver* s);
+int recon_tiles_of(const Grid& g);
+bool recon_prepare();
 void launch_remap_resample(vm_solver* s, void* out);
 void launch_convert(vm_solver* s, const void* src, void* dst, int32_t dst_dtype, size_t count);
 void launch_store_real(vm_solver* s, const double* src, void* dst, size_t count);
@@ -278,6 +286,7 @@ struct SolveDesc {
   double* thv;
   float* thxf;
   float* thvf;
+  double* Mpart;  // tile row sums of the staged reconstruction
   DevState* ds;
 };
 
@@ -324,6 +333,8 @@ struct GroupPlan {
   const int* off_rows4; int tot_rows4;     // 4-row chunks (row spline sweeps)
   const int* off_cols; int tot_cols;       // 32-column chunks (column spline sweeps)
   const int* off_solve;                    // one unit per solve
+  const int* off_tiles; int tot_tiles;     // reconstruction tiles (4 x rows by 256 v columns)
+  int recon_tiles;                         // the group's reconstruction kernel (all solves alike)
   // device-computed offsets (ns + 1 ints each; the total at [ns])
   int* off_dyn;                            // scratch for one dynamic phase at a time
   int big_blocks_cap;                      // virtual blocks per solve of the large windows

@@ -57,6 +57,7 @@ __device__ __forceinline__ void taylor_f32(const Grid& g, const double* t, float
   F[TF_WF] = ok ? (float)(w - wi) : 0.f;
   reinterpret_cast<int*>(F)[TF_UI] = ok ? (int)ui : INT_MIN / 2;
   reinterpret_cast<int*>(F)[TF_WI] = ok ? (int)wi : INT_MIN / 2;
+  reinterpret_cast<double2*>(F + TF_UD)[0] = make_double2(u, w);
 }
 
 __device__ __forceinline__ void taylor_one(const Grid& g, const double* __restrict__ el, int m,
@@ -439,9 +440,13 @@ __device__ __forceinline__ unsigned long long order_key(double d) {
   return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
 
+// Diagnostics of the last f (Sec. 3.2): each block's sums into part[6 x
+// blockIdx] (mass, kinetic energy, S, L1, L2, the potential term), added in
+// block order by k_diag_sum, so that the totals do not depend on the order
+// in which blocks finish; the det T range by atomic min/max (order-free).
 template <typename R>
 __global__ void k_diag(Grid g, const R* __restrict__ f, const double* __restrict__ a,
-                       const double* __restrict__ el, DevState* ds) {
+                       const double* __restrict__ el, DevState* ds, double* __restrict__ part) {
   __shared__ double red[5][32];
   double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // mass, kinetic energy, S, L1, L2 (Sec. 3.2)
   const size_t n = (size_t)g.nx * g.nv;
@@ -464,23 +469,25 @@ __global__ void k_diag(Grid g, const R* __restrict__ f, const double* __restrict
     for (int c = 0; c < 5; c++) red[c][wid] = acc[c];
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double t[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int w = 0; w < (int)(blockDim.x >> 5); w++)
-#pragma unroll
-      for (int c = 0; c < 5; c++) t[c] += red[c][w];
-    atomicAdd(&ds->sum_mass, t[0]);
-    atomicAdd(&ds->sum_kin, t[1]);
-    atomicAdd(&ds->sum_ent, t[2]);
-    atomicAdd(&ds->sum_l1, t[3]);
-    atomicAdd(&ds->sum_l2, t[4]);
-  }
-  // potential energy and det T range (grid-stride, atomics)
+  // potential energy term, reduced like the others
   const double a8 = g.A * ds->Mtot;
   double ep = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.nx; i += gridDim.x * blockDim.x)
     ep += (a[i] * a[i] - a8 * a8) * g.dx;
-  if (ep != 0.0) atomicAdd(&ds->sum_pot, ep);
+  for (int o = 16; o > 0; o >>= 1) ep += __shfl_down_sync(0xffffffffu, ep, o);
+  __shared__ double red_p[32];
+  if (lane == 0) red_p[wid] = ep;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+#pragma unroll
+      for (int c = 0; c < 5; c++) t[c] += red[c][w];
+      t[5] += red_p[w];
+    }
+#pragma unroll
+    for (int c = 0; c < 6; c++) part[6 * blockIdx.x + c] = t[c];
+  }
   for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < g.ne; m += gridDim.x * blockDim.x) {
     const int ne = g.ne;
     const int km = m / g.Lv;
@@ -490,6 +497,19 @@ __global__ void k_diag(Grid g, const R* __restrict__ f, const double* __restrict
     atomicMin(&ds->det_min_key, k);
     atomicMax(&ds->det_max_key, k);
   }
+}
+
+__global__ void k_diag_sum(const double* __restrict__ part, int nb, DevState* ds) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double t[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int b = 0; b < nb; b++)
+    for (int c = 0; c < 6; c++) t[c] += part[6 * b + c];
+  ds->sum_mass = t[0];
+  ds->sum_kin = t[1];
+  ds->sum_ent = t[2];
+  ds->sum_l1 = t[3];
+  ds->sum_l2 = t[4];
+  ds->sum_pot = t[5];
 }
 
 // Largest projected density rho(x_i) = (sum_j f(i, j)) dv of f (Sec. 2.4's
@@ -741,14 +761,16 @@ void launch_rho_max(vm_solver* s) {
 
 void launch_diagnostics(vm_solver* s) {
   unsigned nb = blocks_for((long long)s->n, 256);
-  if (nb > 2048) nb = 2048;
+  if (nb > (unsigned)kRectBlocks) nb = kRectBlocks;  // 6 partial sums per block in diag_part
+  double* part = s->diag_part;
   const int ps_ = prof_begin(s, KID_DIAG);
   if (s->fp32)
-    k_diag<float><<<nb, 256, 0, s->stream>>>(s->g, (const float*)s->f, s->a, s->el, s->ds);
+    k_diag<float><<<nb, 256, 0, s->stream>>>(s->g, (const float*)s->f, s->a, s->el, s->ds, part);
   else
-    k_diag<double><<<nb, 256, 0, s->stream>>>(s->g, (const double*)s->f, s->a, s->el, s->ds);
+    k_diag<double><<<nb, 256, 0, s->stream>>>(s->g, (const double*)s->f, s->a, s->el, s->ds, part);
+  k_diag_sum<<<1, 32, 0, s->stream>>>(part, (int)nb, s->ds);
   prof_end(s, ps_);
-  s->launches++;
+  s->launches += 2;
 }
 
 }  // namespace vm

@@ -60,12 +60,13 @@ SolveDesc desc_of(const vm_solver* s) {
   d.thv = s->thomas_v;
   d.thxf = s->thomas_xf;
   d.thvf = s->thomas_vf;
+  d.Mpart = s->Mpart;
   d.ds = s->ds;
   return d;
 }
 
 // Per-phase unit counts of one solve, in the order of the offset arrays.
-enum { U_ELEM64 = 0, U_PAIR, U_ROWS, U_DIFF, U_SITES, U_COPY, U_ROWS4, U_COLS, U_SOLVE, U_N };
+enum { U_ELEM64 = 0, U_PAIR, U_ROWS, U_DIFF, U_SITES, U_COPY, U_ROWS4, U_COLS, U_SOLVE, U_TILES, U_N };
 
 void units_of(const vm_solver* s, int (&u)[U_N]) {
   const long long n = (long long)s->g.nx * s->g.nv;
@@ -78,6 +79,7 @@ void units_of(const vm_solver* s, int (&u)[U_N]) {
   u[U_ROWS4] = cdiv(s->g.nx, 4);
   u[U_COLS] = cdiv(s->g.nv, 32);
   u[U_SOLVE] = 1;
+  u[U_TILES] = recon_tiles_of(s->g);
 }
 
 }  // namespace
@@ -93,6 +95,7 @@ vm_status group_check(vm_solver* const* solvers, int n) {
     if (!s) return VM_E_INVALID_ARG;
     if (!s->have_f) return VM_E_STATE;
     if (s->fp32 != solvers[0]->fp32) return VM_E_INVALID_ARG;
+    if (s->g.recon_tiles != solvers[0]->g.recon_tiles) return VM_E_INVALID_ARG;
     // host decisions per step or per remap: not part of a group step
     if (s->cfg.emap_remap > 0.0 || s->cfg.c_dyn > 0.0 || s->cfg.f_th > 0.0) return VM_E_INVALID_ARG;
     for (int j = 0; j < i; j++)
@@ -147,6 +150,9 @@ void group_plan(GroupPlan& P, vm_solver* const* solvers, int n, void* d_table, v
   P.off_cols = doff + U_COLS * (n + 1);
   P.tot_cols = tot[U_COLS];
   P.off_solve = doff + U_SOLVE * (n + 1);
+  P.off_tiles = doff + U_TILES * (n + 1);
+  P.tot_tiles = tot[U_TILES];
+  P.recon_tiles = solvers[0]->g.recon_tiles;
   P.off_dyn = (int*)(db + dbytes) + U_N * (n + 1);
   P.big_smem = big;
   P.big_blocks_cap = 0;

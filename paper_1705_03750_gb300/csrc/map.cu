@@ -571,9 +571,9 @@ __device__ __forceinline__ void claim_element(const Grid& g, const double* __res
     const int kk = k + lane / 3 - 1, ll = l + lane % 3 - 1;
     exq = elem_exists(g, kk, ll);
     if (exq) {
-      const double* tq = tay + (size_t)(kk * g.Lv + ll) * TY_N;
-      uq = __ldg(tq + TY_U);
-      wpos = __ldg(tq + TY_W);
+      const double2 uw = __ldg(reinterpret_cast<const double2*>(tayf + (size_t)(kk * g.Lv + ll) * TF_N + TF_UD));
+      uq = uw.x;
+      wpos = uw.y;
     }
   }
   for (int idx = lane; idx < 9 * (TF_MW / 4); idx += 32) {
@@ -916,9 +916,9 @@ __device__ __forceinline__ void claim_pair_body(const Grid& g, const double* __r
     const int kk = k + hl / 3 - 1, ll = l + hl % 3 - 1;
     exq = elem_exists(g, kk, ll);
     if (exq) {
-      const double* tq = tay + (size_t)(kk * g.Lv + ll) * TY_N;
-      uq = __ldg(tq + TY_U);
-      wpos = __ldg(tq + TY_W);
+      const double2 uw = __ldg(reinterpret_cast<const double2*>(tayf + (size_t)(kk * g.Lv + ll) * TF_N + TF_UD));
+      uq = uw.x;
+      wpos = uw.y;
     }
   }
   {

@@ -13,6 +13,7 @@
 // (nearest node, containing square, beta ranges) are taken from the FP32
 // value only when it clears a rigorous bound on its distance to the FP64
 // value, and otherwise from the FP64 evaluation, so they are the FP64 path's.
+#include <climits>
 #include <math.h>
 
 #include "common.cuh"
@@ -608,6 +609,259 @@ __global__ void __launch_bounds__(256, 6) k_recon32(Grid g, const uint32_t* __re
   k_recon32_body(g, map, ds, tay, tayf, fini, f, M, blockIdx.x);
 }
 
+// ---------------------------------------------------------------------------
+// FP32-mixed reconstruction in tiles staged by bulk copies
+// ---------------------------------------------------------------------------
+//
+// A block takes a tile of RT_R x rows by RT_C v columns (one column per
+// thread).  Phase 1 takes every site's certified node and cell decisions
+// (as recon_fast32, without touching f_ini) and the bounding rectangle of
+// the six-point stencils of the tile; if that patch of f_ini fits the
+// shared-memory budget (and rows are 16-byte aligned, nv % 4 == 0), one
+// thread issues a bulk copy (cp.async.bulk, the TMA engine) of each of its
+// rows inside the grid, completing on one mbarrier, while the others zero
+// the parts outside the grid (F = 0 there).  Phase 2 interpolates from
+// shared memory, writes f (a warp writes 128 contiguous bytes) and the
+// tile's row sums.  Sites the bound leaves open take recon_site32 (global
+// memory); a patch too large for the budget falls back to global gathers
+// for the tile.  The pixel masses are the tiles' row sums added in order
+// (k_row_mass).
+constexpr int RT_R = 4, RT_C = 256, RT_PR = 32, RT_PC = 288;
+
+struct __align__(16) TileShared {
+  float patch[RT_PR * RT_PC];
+  float2 xy[RT_R * RT_C];
+  int2 node[RT_R * RT_C];  // (in, jn) of a certain site; (m, -) of a site for recon_site32
+  unsigned char kind[RT_R * RT_C];  // 0: f = 0; 1: certain (bit 2: ic = in - 1, bit 3: jc = jn - 1); 2: slow
+  double rsum[RT_R][RT_C / 32];
+  unsigned long long bar;
+  int bounds[4];
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_inval(unsigned long long* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// The certified decisions of site (i, j) owned by m (recon_fast32's test):
+// 1 with the nodes and offsets when they are certain and finite, else 2.
+__device__ __forceinline__ int decide32(const Grid& g, const float* __restrict__ tayf, int i, int j, int m,
+                                        float inv_Lv, int& in, int& jn, int& dic, int& djc, float& x, float& y) {
+  const float inv_s = 1.0f / (float)g.s, fs = (float)g.s;
+  const float* F = tayf + (size_t)m * TF_N;
+  float px, pv;
+  p_of(F, i, j, inv_s, px, pv);
+  const QF q = qeval(F, px, pv);
+  int Bu, Bw;
+  float bu, bw;
+  anchor_r(g, m, inv_Lv, Bu, bu, Bw, bw);
+  const float ru = bu + fs * q.qx, rw = bw + fs * q.qv;
+  const float eu = fs * q.ex + 1e-6f * (1.f + fabsf(ru)), ew = fs * q.ev + 1e-6f * (1.f + fabsf(rw));
+  if (!(fabsf(ru) < 1e6f && fabsf(rw) < 1e6f)) return 2;
+  const float tu = 2.f * ru, tw = 2.f * rw;
+  const float fu = floorf(tu), fw = floorf(tw);
+  if (!((tu - 2.f * eu > fu) && (tu + 2.f * eu < fu + 1.f) && (tw - 2.f * ew > fw) && (tw + 2.f * ew < fw + 1.f)))
+    return 2;
+  const int iu = (int)fu, iw = (int)fw;
+  const int nu = (iu + 1) >> 1, nw = (iw + 1) >> 1;
+  in = Bu + nu;
+  jn = Bw + nw;
+  dic = (iu >> 1) - nu;  // 0 or -1
+  djc = (iw >> 1) - nw;
+  x = ru - (float)nu;
+  y = rw - (float)nw;
+  return 1;
+}
+
+// The six-point value (the arithmetic of qinterp32_in) from node values.
+__device__ __forceinline__ float six_point(float c, float cxp, float cxm, float cyp, float cym, float d00, float d10,
+                                           float d01, float d11, float x, float y) {
+  float f = c * (1.0f - x * x - y * y);
+  f += 0.5f * x * (cxp * (1.0f + x) + cxm * (x - 1.0f));
+  f += 0.5f * y * (cyp * (1.0f + y) + cym * (y - 1.0f));
+  f += (d11 + d00 - d10 - d01) * x * y;
+  return f;
+}
+
+__device__ __forceinline__ void recon32_tile_body(const Grid& g, const uint32_t* __restrict__ map, const DevState* ds,
+                                                  const double* __restrict__ tay, const float* __restrict__ tayf,
+                                                  const float* __restrict__ fini, float* __restrict__ f,
+                                                  double* __restrict__ Mpart, DevState* dse, int vb) {
+  extern __shared__ __align__(16) unsigned char tile_raw[];
+  TileShared& S = *reinterpret_cast<TileShared*>(tile_raw);
+  const int ntj = (g.nv + RT_C - 1) / RT_C;
+  const int ti = vb / ntj, tj = vb - ti * ntj;
+  const int i0 = ti * RT_R, j = tj * RT_C + (int)threadIdx.x;
+  const int tid = threadIdx.x;
+  const uint32_t epoch = ds_epoch(ds);
+  const float inv_Lv = 1.0f / (float)g.Lv;
+  if (tid < 4) S.bounds[tid] = (tid & 1) ? INT_MIN : INT_MAX;
+  __syncthreads();
+  // phase 1: decisions
+  int lo_i = INT_MAX, hi_i = INT_MIN, lo_j = INT_MAX, hi_j = INT_MIN;
+#pragma unroll
+  for (int r = 0; r < RT_R; r++) {
+    const int i = i0 + r, q = r * RT_C + tid;
+    unsigned char kd = 0;
+    if (i < g.nx && j < g.nv) {
+      int js, je;
+      row_span(g, ds, i, js, je);
+      const int m = (j >= js && j <= je) ? owner(map, (size_t)i * g.nv + j, epoch, g.ne) : -1;
+      if (m >= 0) {
+        int in, jn, dic, djc;
+        float x, y;
+        if (decide32(g, tayf, i, j, m, inv_Lv, in, jn, dic, djc, x, y) == 1) {
+          kd = (unsigned char)(1 | (dic ? 4 : 0) | (djc ? 8 : 0));
+          S.node[q] = make_int2(in, jn);
+          S.xy[q] = make_float2(x, y);
+          lo_i = min(lo_i, in - 1);
+          hi_i = max(hi_i, in + 1);
+          lo_j = min(lo_j, jn - 1);
+          hi_j = max(hi_j, jn + 1);
+        } else {
+          kd = 2;
+          S.node[q] = make_int2(m, 0);
+        }
+      }
+    }
+    S.kind[q] = kd;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo_i = min(lo_i, __shfl_xor_sync(0xffffffffu, lo_i, o));
+    hi_i = max(hi_i, __shfl_xor_sync(0xffffffffu, hi_i, o));
+    lo_j = min(lo_j, __shfl_xor_sync(0xffffffffu, lo_j, o));
+    hi_j = max(hi_j, __shfl_xor_sync(0xffffffffu, hi_j, o));
+  }
+  if ((tid & 31) == 0 && lo_i <= hi_i) {
+    atomicMin(&S.bounds[0], lo_i);
+    atomicMax(&S.bounds[1], hi_i);
+    atomicMin(&S.bounds[2], lo_j);
+    atomicMax(&S.bounds[3], hi_j);
+  }
+  __syncthreads();
+  const int pi0 = S.bounds[0], pi1 = S.bounds[1];
+  const int pj0 = (S.bounds[2] >> 2) << 2, pj1 = ((S.bounds[3] + 4) >> 2) << 2;  // [pj0, pj1), multiples of 4
+  const bool fits = (g.nv % 4 == 0) && pi0 <= pi1 && (pi1 - pi0 + 1) <= RT_PR && (pj1 - pj0) <= RT_PC;
+  if (fits) {
+    const int nrows = pi1 - pi0 + 1, ncols = pj1 - pj0;
+    // zeros where the patch leaves the grid
+    for (int idx = tid; idx < nrows * ncols; idx += blockDim.x) {
+      const int rr = idx / ncols, cc = idx - rr * ncols;
+      const int ii = pi0 + rr, jj = pj0 + cc;
+      if (ii < 0 || ii >= g.nx || jj < 0 || jj >= g.nv) S.patch[rr * RT_PC + cc] = 0.f;
+    }
+    const int c0 = max(pj0, 0), c1 = min(pj1, g.nv);
+    const int r0 = max(pi0, 0), r1 = min(pi1, g.nx - 1);
+    const unsigned row_bytes = (c1 > c0) ? (unsigned)(c1 - c0) * 4u : 0u;
+    const unsigned total = (r1 >= r0) ? row_bytes * (unsigned)(r1 - r0 + 1) : 0u;
+    if (tid == 0) mbar_init(&S.bar, 1);
+    __syncthreads();
+    if (tid == 0) {
+      if (total > 0) {
+        mbar_expect_tx(&S.bar, total);
+        for (int ii = r0; ii <= r1; ii++)
+          bulk_g2s(&S.patch[(ii - pi0) * RT_PC + (c0 - pj0)], fini + (size_t)ii * g.nv + c0, row_bytes, &S.bar);
+      } else {
+        mbar_arrive(&S.bar);
+      }
+    }
+    // every copy completes unless a byte count were wrong: the wait is
+    // bounded all the same, and a wait that runs out is reported
+    bool ok = false;
+    for (int it = 0; it < (1 << 22) && !ok; it++) ok = mbar_try_wait(&S.bar, 0);
+    if (!ok) VM_BAD(dse, 41);
+    __syncthreads();
+    if (tid == 0) mbar_inval(&S.bar);
+  }
+  // phase 2: values, f, row sums
+  double rs[RT_R];
+#pragma unroll
+  for (int r = 0; r < RT_R; r++) {
+    const int i = i0 + r, q = r * RT_C + tid;
+    const unsigned char kd = S.kind[q];
+    float v = 0.f;
+    if (kd & 1) {
+      const int2 nd = S.node[q];
+      const float2 xy = S.xy[q];
+      const int in = nd.x, jn = nd.y, ic = in + ((kd & 4) ? -1 : 0), jc = jn + ((kd & 8) ? -1 : 0);
+      if (fits) {
+        const float* P = S.patch;
+        auto at = [&](int a, int b) { return P[(a - pi0) * RT_PC + (b - pj0)]; };
+        v = six_point(at(in, jn), at(in + 1, jn), at(in - 1, jn), at(in, jn + 1), at(in, jn - 1), at(ic, jc),
+                      at(ic + 1, jc), at(ic, jc + 1), at(ic + 1, jc + 1), xy.x, xy.y);
+      } else {
+        v = six_point(F_at32(fini, g, in, jn), F_at32(fini, g, in + 1, jn), F_at32(fini, g, in - 1, jn),
+                      F_at32(fini, g, in, jn + 1), F_at32(fini, g, in, jn - 1), F_at32(fini, g, ic, jc),
+                      F_at32(fini, g, ic + 1, jc), F_at32(fini, g, ic, jc + 1), F_at32(fini, g, ic + 1, jc + 1),
+                      xy.x, xy.y);
+      }
+    } else if (kd == 2) {
+      v = recon_site32(g, tay, tayf, fini, i, j, S.node[q].x);
+    }
+    if (i < g.nx && j < g.nv) f[(size_t)i * g.nv + j] = v;
+    double w = (double)v;
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+    rs[r] = w;
+  }
+  if ((tid & 31) == 0)
+#pragma unroll
+    for (int r = 0; r < RT_R; r++) S.rsum[r][tid >> 5] = rs[r];
+  __syncthreads();
+  if (tid < RT_R && i0 + tid < g.nx) {
+    double t = 0.0;
+    for (int w = 0; w < RT_C / 32; w++) t += S.rsum[tid][w];
+    Mpart[(size_t)(i0 + tid) * ntj + tj] = t;
+  }
+}
+
+__global__ void __launch_bounds__(RT_C) k_recon32_tiles(Grid g, const uint32_t* __restrict__ map, DevState* ds,
+                                                        const double* __restrict__ tay, const float* __restrict__ tayf,
+                                                        const float* __restrict__ fini, float* __restrict__ f,
+                                                        double* __restrict__ Mpart) {
+  recon32_tile_body(g, map, ds, tay, tayf, fini, f, Mpart, ds, blockIdx.x);
+}
+
+// M(i) = (sum of the row's tile sums, in tile order) dx dv.
+__device__ __forceinline__ void row_mass_body(const Grid& g, const double* __restrict__ Mpart, double* __restrict__ M,
+                                              int vb) {
+  const int i = vb * blockDim.x + threadIdx.x;
+  if (i >= g.nx) return;
+  const int ntj = (g.nv + RT_C - 1) / RT_C;
+  double t = 0.0;
+  for (int k = 0; k < ntj; k++) t += Mpart[(size_t)i * ntj + k];
+  M[i] = dmul(t, g.dxdv);
+}
+
+__global__ void k_row_mass(Grid g, const double* __restrict__ Mpart, double* __restrict__ M) {
+  row_mass_body(g, Mpart, M, blockIdx.x);
+}
+
 __device__ __forceinline__ float W4f(float x) {
   if (x <= 1.f) return 1.f - 1.5f * x * x + 0.75f * x * x * x;
   if (x <= 2.f) {
@@ -766,6 +1020,19 @@ __global__ void __launch_bounds__(256) k_remap_group64(const SolveDesc* __restri
   GROUP_END
 }
 
+__global__ void __launch_bounds__(RT_C) k_recon_tiles_group(const SolveDesc* __restrict__ D,
+                                                            const int* __restrict__ off, int ns, int total) {
+  GROUP_LOOP(off, ns, total)
+  recon32_tile_body(gsh, d.map, d.ds, d.tay, d.tayf, (const float*)d.fini, (float*)d.f, d.Mpart, d.ds, vb);
+  GROUP_END
+}
+
+__global__ void k_row_mass_group(const SolveDesc* __restrict__ D, const int* __restrict__ off, int ns, int total) {
+  GROUP_LOOP(off, ns, total)
+  row_mass_body(gsh, d.Mpart, d.M, vb);
+  GROUP_END
+}
+
 // f_ini <- tmp (the resampled f of a remap), 4096 values per unit.
 template <typename R>
 __global__ void __launch_bounds__(256) k_copy_group(const SolveDesc* __restrict__ D, const int* __restrict__ off,
@@ -799,7 +1066,11 @@ inline int recon_threads(int nv) { return nv >= 256 ? 256 : ((nv + 31) / 32) * 3
 void group_reconstruct(const GroupPlan& G) {
   // every solve of a group has the same block size (the group is built so)
   const int nt = 256;
-  if (G.fp32)
+  if (G.fp32 && G.recon_tiles) {
+    k_recon_tiles_group<<<group_grid(G, GP_RECON, G.tot_tiles), RT_C, sizeof(TileShared), G.stream>>>(
+        G.D, G.off_tiles, G.ns, G.tot_tiles);
+    k_row_mass_group<<<group_grid(G, GP_DIFF, G.tot_diff), 128, 0, G.stream>>>(G.D, G.off_diff, G.ns, G.tot_diff);
+  } else if (G.fp32)
     k_recon_group32<<<group_grid(G, GP_RECON, G.tot_rows), nt, 0, G.stream>>>(G.D, G.off_rows, G.ns, G.tot_rows);
   else
     k_recon_group64<<<group_grid(G, GP_RECON, G.tot_rows), nt, 0, G.stream>>>(G.D, G.off_rows, G.ns, G.tot_rows);
@@ -820,10 +1091,34 @@ void group_copy_tmp_to_fini(const GroupPlan& G) {
     k_copy_group<double><<<group_grid(G, GP_COPY, G.tot_copy), 256, 0, G.stream>>>(G.D, G.off_copy, G.ns, G.tot_copy);
 }
 
+int recon_tiles_of(const Grid& g) { return (g.nx + RT_R - 1) / RT_R * ((g.nv + RT_C - 1) / RT_C); }
+size_t recon_tile_smem() { return sizeof(TileShared); }
+
+bool recon_prepare() {
+  static bool done = false;
+  if (done) return true;
+  cudaError_t e = cudaFuncSetAttribute(k_recon32_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(TileShared));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_recon_tiles_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(TileShared));
+  if (e != cudaSuccess) {
+    note_cuda(e);
+    return false;
+  }
+  done = true;
+  return true;
+}
+
 void launch_reconstruct(vm_solver* s) {
   const int nt = s->g.nv >= 256 ? 256 : ((s->g.nv + 31) / 32) * 32;
   const int ps_ = prof_begin(s, KID_RECON);
-  if (s->fp32)
+  if (s->fp32 && s->g.recon_tiles) {
+    k_recon32_tiles<<<recon_tiles_of(s->g), RT_C, sizeof(TileShared), s->stream>>>(
+        s->g, s->map, s->ds, s->tay, s->tayf, (const float*)s->fini, (float*)s->f, s->Mpart);
+    k_row_mass<<<(s->g.nx + 127) / 128, 128, 0, s->stream>>>(s->g, s->Mpart, s->M);
+    s->launches++;
+  } else if (s->fp32)
     k_recon32<<<s->g.nx, nt, 0, s->stream>>>(s->g, s->map, s->ds, s->tay, s->tayf, (const float*)s->fini,
                                               (float*)s->f, s->M);
   else

@@ -48,7 +48,7 @@ class VmConfig(C.Structure):
         ("precision", C.c_int32), ("alpha", C.c_double), ("beta", C.c_double),
         ("pad", C.c_int32), ("literal_fd", C.c_int32), ("max_hole_rounds", C.c_int32),
         ("map_windows", C.c_int32), ("emap_remap", C.c_double), ("c_dyn", C.c_double),
-        ("f_th", C.c_double),
+        ("f_th", C.c_double), ("recon_mode", C.c_int32),
     ]
 
 
@@ -186,6 +186,7 @@ class Config:
     emap_remap: float = 0.0
     c_dyn: float = 0.0
     f_th: float = 0.0
+    recon_mode: int = 0
 
     @classmethod
     def from_run(cls, rc, precision: int = VM_FP64) -> "Config":
@@ -194,7 +195,8 @@ class Config:
     def c(self) -> VmConfig:
         return VmConfig(self.nx, self.nv, self.x_lo, self.x_hi, self.v_lo, self.v_hi, self.s, self.dt,
                         self.n_s, self.G, self.precision, self.alpha, self.beta, self.pad, self.literal_fd,
-                        self.max_hole_rounds, self.map_windows, self.emap_remap, self.c_dyn, self.f_th)
+                        self.max_hole_rounds, self.map_windows, self.emap_remap, self.c_dyn, self.f_th,
+                        self.recon_mode)
 
 
 def workspace_bytes(cfg: Config) -> int:

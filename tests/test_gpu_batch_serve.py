@@ -44,9 +44,19 @@ def _same(s1, s2):
         np.testing.assert_array_equal(d1[k], d2[k])
 
 
-@pytest.mark.parametrize("prec", [V.VM_FP32_MIXED, V.VM_FP64])
-def test_batch_graph_matches_individual_solves(prec):
+def _solver_mode(rc, prec, mode):
+    cfg = V.Config.from_run(rc, prec)
+    cfg.recon_mode = mode
+    s = V.Solver(cfg, stream=torch.cuda.Stream())
+    s.set_f(I.initial_f(rc))
+    return s
+
+
+@pytest.mark.parametrize("prec,mode", [(V.VM_FP32_MIXED, 0), (V.VM_FP64, 0), (V.VM_FP32_MIXED, 1)],
+                         ids=["fp32", "fp64", "fp32-tiles"])
+def test_batch_graph_matches_individual_solves(prec, mode):
     cfgs = [I.batch_member(i).with_(n_s=10) for i in range(6)]
+    _solver = lambda rc, prec: _solver_mode(rc, prec, mode)  # noqa: E731
     alone = [_solver(rc, prec) for rc in cfgs]
     for s in alone:
         s.step(23)                      # two remaps included

@@ -198,3 +198,19 @@ def test_batch_refuses_variable_time_step():
     with pytest.raises(V.VlametError) as e:
         V.Batch([s], nstreams=1)
     assert e.value.status == 1
+
+
+def test_diagnostics_are_deterministic():
+    """Each block's sums are added in block order: two identical solves, and
+    two calls on one solve, report the same bits."""
+    rc = I.HALOS_4096.with_(nx=1024, nv=768, s=8, n_s=6)
+    sols = []
+    for _ in range(2):
+        s = V.Solver(V.Config.from_run(rc, V.VM_FP32_MIXED))
+        s.set_f(I.initial_f(rc))
+        s.step(8)
+        sols.append(s)
+    keys = ("mass", "energy", "entropy", "l1", "l2", "detT_min", "detT_max", "emap")
+    d0, d1, d2 = sols[0].diagnostics(), sols[1].diagnostics(), sols[0].diagnostics()
+    for k in keys:
+        assert d0[k] == d1[k] == d2[k], k

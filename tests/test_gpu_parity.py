@@ -381,3 +381,43 @@ def test_halos_8192_map_after_a_cycle_full_grid():
     mg = s.read_map()
     assert (mg == mo).all(), f"{(mg != mo).sum()} sites differ"
     assert d["overflow_elements"] > 0
+
+
+# ---------------------------------------------------------------------------
+# the FP32-mixed reconstruction in tiles staged by bulk copies (recon_mode 1)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape", [(4096, 4096), (130, 254), (97, 301), (64, 64)], ids=lambda s: f"{s[0]}x{s[1]}")
+def test_staged_tiles_match_oracle_and_the_row_kernel(shape):
+    """Tiles of 4 x rows by 256 v columns, their f_ini patch staged in shared
+    memory by bulk copies where it fits (nv % 4 == 0), global gathers where
+    not (nv = 301, odd rows): one reconstruction of an evolved state against
+    the oracle (f to the per-step bar, map bit for bit) and against the
+    one-block-per-row kernel (f to rounding)."""
+    nx, nv = shape
+    rc = I.HALOS_4096.with_(nx=nx, nv=nv, s=8 if nx >= 1024 else 4)
+    steps = 24 if nx >= 1024 else 18
+    base = V.Config.from_run(rc.with_(n_s=10 ** 6), V.VM_FP32_MIXED)
+    tiles = V.Config.from_run(rc.with_(n_s=10 ** 6), V.VM_FP32_MIXED)
+    tiles.recon_mode = 1
+    a, b = V.Solver(base), V.Solver(tiles)
+    f0 = I.initial_f(rc)
+    for s in (a, b):
+        s.set_f(f0)
+    b.step(steps)
+    b.sync()
+    el = b.elements()
+    a.set_elements(np.ascontiguousarray(el))
+    o = O.Oracle(rc.nx, rc.nv, rc.x_lo, rc.x_hi, rc.v_lo, rc.v_hi, rc.s, rc.dt, 10 ** 6, rc.G)
+    o.set_f(b.read_fini())
+    o.set_elements(np.ascontiguousarray(el.T))
+    b.reconstruct()
+    a.reconstruct()
+    fo = o.reconstruct()
+    assert (b.read_map() == o.compute_map()[0]).all()
+    fb = b.read_f()
+    assert_f_close(fb, fo)
+    assert np.abs(fb - a.read_f()).max() <= 1e-6 * np.abs(fo).max()
+    db, do = b.density_force(), o.density_force()
+    np.testing.assert_allclose(db["M"], do["M"], rtol=0, atol=F_TOL * rc.nv * np.abs(fo).max() * rc.dx * rc.dv)
+    assert b.diagnostics()["bad_where"] == 0
