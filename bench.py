@@ -648,6 +648,54 @@ def run_batch(args):
     return res
 
 
+def run_batch_classes(args):
+    """Group launches against the same solves stepped one by one (one stream),
+    for uniform batches of halo solves: 16 of 1024^2, 64 of 256^2, 256 of
+    64^2 (elements every 8 sites above 128, else 4), 20 steps each."""
+    import torch
+    from paper_1705_03750_gb300 import vlamet as V
+    out = {"workload": "uniform halo batches", "steps": args.steps, "classes": {}}
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for side, n in ((1024, 16), (256, 64), (64, 256)):
+        cfgs = [I.HALOS_4096.with_(nx=side, nv=side, s=8 if side > 128 else 4, seed=i) for i in range(n)]
+        f0s = [torch.from_numpy(I.initial_f(rc)).cuda() for rc in cfgs]
+
+        def fresh():
+            ss = [V.Solver(V.Config.from_run(rc, V.VM_FP32_MIXED), stream=stream) for rc in cfgs]
+            for s_, f in zip(ss, f0s):
+                s_.set_f(f)
+            return ss
+
+        def timed(fn):
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
+        ss = fresh()
+        b = V.Batch(ss, stream=stream)
+        b.step(args.warmup)
+        g = timed(lambda: b.step(args.steps))
+        b.close()
+        ss = fresh()
+        for s_ in ss:
+            s_.step(args.warmup)
+
+        def plain():
+            for _ in range(args.steps):
+                for s_ in ss:
+                    s_.step(1)
+        p = timed(plain)
+        sites = side * side * n * args.steps
+        out["classes"][f"{n}x{side}^2"] = {"group_cell_updates_per_s": sites / (g / 1e3),
+                                          "one_by_one_cell_updates_per_s": sites / (p / 1e3),
+                                          "group_ms_per_step": g / args.steps, "one_by_one_ms_per_step": p / args.steps}
+        del ss
+    return out
+
+
 def serve_sample(args) -> dict:
     """A reduced serving run for the headline line, on the library's serving
     loop (vm_server_*): 24 seeded halo requests (sides 256-1024, multiples of
@@ -749,7 +797,8 @@ def main():
                     help="steps of the whole-run rate (the configuration's 1000; 0: skip)")
     ap.add_argument("--whole-run-fp32-only", action="store_true")
     ap.add_argument("--ref-cap", type=int, default=20)
-    ap.add_argument("--workload", default="halos4096", choices=["halos4096", "precision8192", "batch", "serve"])
+    ap.add_argument("--workload", default="halos4096",
+                    choices=["halos4096", "precision8192", "batch", "batch-classes", "serve"])
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--streams", type=int, default=0, help="(unused: one launch per phase for the batch)")
     ap.add_argument("--autotune", type=int, default=1, help="tune the batch's launch shapes on its first steps")
@@ -766,7 +815,8 @@ def main():
     if args.workload != "halos4096":
         from paper_1705_03750_gb300 import build as B
         B.build()
-        fn = {"precision8192": run_precision, "batch": run_batch, "serve": run_serve}[args.workload]
+        fn = {"precision8192": run_precision, "batch": run_batch, "batch-classes": run_batch_classes,
+              "serve": run_serve}[args.workload]
         print(json.dumps(fn(args)))
         return
     if args.warmup < 3:
