@@ -361,7 +361,13 @@ enum GroupPhase : int {
     __syncthreads();                                                 \
     const int sv = svsh;                                             \
     const SolveDesc& d = D[sv];                                      \
-    const int vb = u - __ldg((off) + sv);
+    const int vb = u - __ldg((off) + sv);                            \
+    if (vb >= __ldg((off) + sv + 1) - __ldg((off) + sv)) {           \
+      /* (a table and its totals out of step: never expected) */     \
+      if (threadIdx.x == 0) VM_BAD(d.ds, 50);                        \
+      __syncthreads();                                               \
+      continue;                                                      \
+    }
 #define GROUP_END \
     __syncthreads(); \
   }

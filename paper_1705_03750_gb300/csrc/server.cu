@@ -15,6 +15,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <deque>
 #include <map>
@@ -26,7 +27,8 @@
 namespace {
 
 constexpr int kInFlight = 2;     // ticks queued ahead of the device
-constexpr int kTableSlots = 16;  // plan tables in the ring
+constexpr int kTableSlots = 16;  // plan tables in the pool
+constexpr int kPlanSlots = 2;    // of them for the transport plan (alternating); the rest a ring for remaps
 
 double now_s(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -99,11 +101,15 @@ struct vm_server {
   size_t pool_bytes = 0;
   cudaStream_t stream = nullptr;
   PoolAlloc alloc;
-  // plan tables: a ring of device slots, each with its pinned staging copy
+  // plan tables: device slots, each with its pinned staging copy and an event
+  // after its last use; slots 0-1 hold the transport plan of the stepping
+  // set (alternating, so that a rebuild never overwrites the table queued
+  // steps still read), slots 2.. a ring for the remap subsets
   size_t table_bytes = 0;
   char* h_tables = nullptr;
   cudaEvent_t table_ev[kTableSlots];
-  int table_next = 0;
+  int table_next = kPlanSlots;
+  int plan_slot = 0;
   cudaEvent_t tick_ev[kInFlight];
   int tick_next = 0, ticks_queued = 0;
   // the plan of the current stepping set (rebuilt when the set changes)
@@ -140,16 +146,22 @@ void pinned_put(vm_server* S, double* p, size_t cap) {
   if (p) S->pinned_free.emplace_back(cap, p);
 }
 
-// The next plan-table slot (its last use has completed) and its addresses.
-int table_slot(vm_server* S) {
-  const int k = S->table_next;
-  S->table_next = (k + 1) % kTableSlots;
+// A plan-table slot whose last use has completed: the other transport slot,
+// or the next slot of the remap ring.
+int table_slot(vm_server* S, bool transport) {
+  int k;
+  if (transport) {
+    k = S->plan_slot = (S->plan_slot + 1) % kPlanSlots;
+  } else {
+    k = S->table_next;
+    S->table_next = (k + 1 - kPlanSlots) % (kTableSlots - kPlanSlots) + kPlanSlots;
+  }
   cudaEventSynchronize(S->table_ev[k]);
   return k;
 }
 
-void plan_into_slot(vm_server* S, vm::GroupPlan& P, const std::vector<vm_solver*>& set) {
-  const int k = table_slot(S);
+void plan_into_slot(vm_server* S, vm::GroupPlan& P, const std::vector<vm_solver*>& set, bool transport) {
+  const int k = table_slot(S, transport);
   vm::group_plan(P, set.data(), (int)set.size(), S->pool + (size_t)k * S->table_bytes,
                  S->h_tables + (size_t)k * S->table_bytes, S->stream);
   cudaEventRecord(S->table_ev[k], S->stream);  // re-recorded after the plan's last use
@@ -169,6 +181,14 @@ int retire(vm_server* S) {
     if (r->left == 0 && r->done_ev && cudaEventQuery(r->done_ev) == cudaSuccess) {
       const size_t nx = (size_t)r->cfg.nx;
       r->result.assign(r->pinned, r->pinned + 4 * nx);
+      int32_t err = 0;
+      memcpy(&err, r->pinned + 4 * nx, sizeof err);
+      if (err & vm::ERR_INTERNAL)
+        r->status = VM_E_INTERNAL;
+      else if (err & vm::ERR_PATCH_OVERFLOW)
+        r->status = VM_E_PATCH_OVERFLOW;
+      else if (err & vm::ERR_NOT_CONVERGED)
+        r->status = VM_E_NOT_CONVERGED;
       r->t_finish = now_s(S->t0);
       r->finished = true;
       pinned_put(S, r->pinned, r->pinned_cap);
@@ -237,7 +257,7 @@ vm_status tick(vm_server* S) {
       }
     if (set.empty()) break;
     if (!S->plan_valid || set != S->plan_set) {
-      plan_into_slot(S, S->plan, set);
+      plan_into_slot(S, S->plan, set, true);
       S->plan_set = set;
       S->plan_valid = true;
     }
@@ -255,7 +275,7 @@ vm_status tick(vm_server* S) {
     }
     if (!remap.empty()) {
       vm::GroupPlan R;
-      plan_into_slot(S, R, remap);
+      plan_into_slot(S, R, remap, false);
       vm::group_step_remap(R);
       mark_slot_used(S, R);
       S->remap_groups++;
@@ -270,6 +290,8 @@ vm_status tick(vm_server* S) {
       cudaMemcpyAsync(h + r->cfg.nx, r->s->a, b, cudaMemcpyDeviceToHost, S->stream);
       cudaMemcpyAsync(h + 2 * r->cfg.nx, r->s->da, b, cudaMemcpyDeviceToHost, S->stream);
       cudaMemcpyAsync(h + 3 * r->cfg.nx, r->s->d2a, b, cudaMemcpyDeviceToHost, S->stream);
+      // and the solve's device error word (a map that did not converge, a failed bounds check)
+      cudaMemcpyAsync(h + 4 * r->cfg.nx, &r->s->ds->err, sizeof(int32_t), cudaMemcpyDeviceToHost, S->stream);
       cudaEventRecord(r->done_ev, S->stream);
     }
   }
@@ -339,7 +361,8 @@ vm_status vm_server_submit(vm_server* S, const vm_config* cfg, const double* f0,
   r->steps = r->left = nsteps;
   r->ws_bytes = need;
   const size_t n = (size_t)cfg->nx * cfg->nv;
-  r->pinned = pinned_get(S, n, &r->pinned_cap);
+  // f0 at submission; at completion M, a, a', a'' and the error word
+  r->pinned = pinned_get(S, std::max(n, 4 * (size_t)cfg->nx + 1), &r->pinned_cap);
   if (!r->pinned) {
     delete r;
     return VM_E_OOM;

@@ -140,3 +140,24 @@ def test_server_budget_bounds_the_resident_set_and_refuses_what_never_fits():
     srv, rep = _served(reqs + [big], budget=int(1.5 * need))
     assert rep["requests"] == 5 and rep["failed"] == 1 and "status 6" in big.error
     assert rep["peak_active"] == 1 and srv.stats()["peak_bytes"] <= 1.5 * need
+
+
+def test_served_results_stay_exact_through_many_remap_subsets():
+    """Requests admitted at different times remap in different steps: every
+    step builds a plan for its remap subset (more than the server's ring of
+    plan tables holds over the run) while the transport plan of the active
+    set stays in use.  Each result must equal its solve stepped alone, and
+    every served solve must report success."""
+    mk = lambda i: Request(i, I.HALOS_4096.with_(nx=192 + 32 * (i % 3), nv=160 + 32 * (i % 4), s=4,  # noqa: E731
+                                                 n_s=2 + (i % 3), seed=300 + i), 24 + 3 * i, 0.004 * i)
+    reqs = [mk(i) for i in range(8)]
+    srv, rep = _served(reqs, max_active=8, tick=2)
+    assert rep["requests"] == 8 and rep["failed"] == 0
+    assert srv.stats()["remap_groups"] > 20
+    for r in reqs:
+        s = V.Solver(V.Config.from_run(r.config, V.VM_FP32_MIXED))
+        s.set_f(I.initial_f(r.config))
+        s.step(r.steps)
+        direct = s.density_force()
+        for k in direct:
+            np.testing.assert_array_equal(direct[k], r.result[k], err_msg=f"request {r.rid} {k}")
