@@ -719,15 +719,16 @@ def serve_sample(args) -> dict:
         return ics[key]
 
     def one(rate):
+        reqs = poisson_requests(24, rate=rate, **kw)
+        for r in reqs:
+            ic(r.config)                # initial conditions prepared before the clock starts
         srv = V.NativeServer(150 << 30, max_active=32, steps_per_tick=args.tick)
-        rep = run_open_loop(srv, poisson_requests(24, rate=rate, **kw), ic_fn=ic)
+        rep = run_open_loop(srv, reqs, ic_fn=ic)
         torch.cuda.synchronize()
         srv.close()
         keep = ("requests", "failed", "wall_s", "cell_updates_per_s", "p50_latency_s", "p99_latency_s",
                 "peak_active", "group_steps")
         return {k: rep[k] for k in keep}
-    for rc in (r.config for r in poisson_requests(24, rate=0.0, **kw)):
-        ic(rc)                          # initial conditions prepared before the clock starts
     sat = one(0.0)
     rate = sat["requests"] / sat["wall_s"]
     out = {"workload": "serve-halos-256..1024 x24, 100-400 steps (vm_server_*)",
@@ -759,6 +760,8 @@ def run_serve(args):
         return ics[key]
 
     def one(reqs):
+        for r in reqs:
+            ic(r.config)                # initial conditions prepared before the clock starts
         srv = V.NativeServer(budget, max_active=args.max_active, steps_per_tick=args.tick)
         rep = run_open_loop(srv, reqs, ic_fn=ic)
         torch.cuda.synchronize()
@@ -766,8 +769,6 @@ def run_serve(args):
         return rep
     base = poisson_requests(args.requests, rate=0.0, seed=args.seed, make_config=make,
                             steps=(args.min_steps, args.max_steps))
-    for r in base:
-        ic(r.config)
     sat = one(base)
     print(json.dumps({"partial_saturation": sat}), file=sys.stderr, flush=True)
     sat_rate = sat["requests"] / sat["wall_s"]
