@@ -522,6 +522,7 @@ class NativeServer:
         if getattr(self, "h", None):
             self.L.vm_server_destroy(self.h)
             self.h = None
+        self._pool = None           # the device pool goes back with the handle
 
     def __del__(self):
         try:
