@@ -82,8 +82,11 @@ typedef struct {
   double emap_remap;          /* 0: remap every n_s steps only; > 0: also remap after a step
                                  whose map's E_map (Sec. 2.3.2, element spacings; see
                                  vm_diag.emap) exceeds this value.  Each step then computes
-                                 E_map and waits for it (vm_step synchronises once per step);
-                                 batches refuse it (VM_E_INVALID_ARG) */
+                                 E_map, and the decision is taken on the device: the remap's
+                                 launches are queued after every step and return at once
+                                 unless the decision kernel opens them, so vm_step does not
+                                 wait (with f_th > 0 the host decides and vm_step synchronises
+                                 once per step).  Batches and servers accept it */
   double c_dyn;               /* 0: constant dt; > 0: each step takes min(dt, c_dyn /
                                  sqrt(rho_max)) (Sec. 2.4), rho_max the largest
                                  rho(x_i) = sum_j f(i, j) dv of the last reconstructed f
@@ -268,9 +271,12 @@ int32_t vm_profile_read(vm_solver* s, vm_kernel_stat* out, int32_t max);
  * Results are those of the same solves stepped one by one, bit for bit.
  * The solvers stay owned by the caller and must outlive the batch; they must
  * all have received vm_set_f, share the precision, n_s and their position in
- * the remap cycle (VM_E_STATE otherwise), not use emap_remap, c_dyn or f_th
+ * the remap cycle (VM_E_STATE otherwise; solves with emap_remap > 0 keep
+ * their own cycles on the device and are exempt), not use c_dyn or f_th
  * (VM_E_INVALID_ARG: those take host decisions per step), and must not be
- * profiling.  The batch allocates its work tables (about 360 bytes per solve)
+ * profiling.  Every step of a batch with emap_remap solves ends with their
+ * E_map, each one's decision and their remap launches, which skip the solves
+ * that do not remap this step.  The batch allocates its work tables (about 360 bytes per solve)
  * with cudaMalloc and frees them in vm_batch_destroy.  nstreams is not used
  * (kept for compatibility; pass 0 or any positive count).  Creation
  * synchronises each solver's stream; vm_batch_step orders itself after work
@@ -316,7 +322,8 @@ void vm_batch_destroy(vm_batch* b);
  * c->budget_bytes after them for solver workspaces; it allocates no device
  * memory, and pinned host memory only for staging (initial conditions,
  * results, tables).  Every request must use c->precision and no per-step host
- * decision (emap_remap, c_dyn, f_th: VM_E_INVALID_ARG); one whose workspace
+ * decision (c_dyn, f_th: VM_E_INVALID_ARG; emap_remap is decided on the
+ * device, its remaps behind each solve's own decision); one whose workspace
  * exceeds the whole budget is refused (VM_E_BUDGET).  Calls on one server
  * must not run concurrently. */
 typedef struct {

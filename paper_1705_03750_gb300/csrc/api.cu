@@ -208,6 +208,50 @@ cudaError_t step_remap(vm_solver* s) {
   return cudaSuccess;
 }
 
+// The remap after a step, behind the device's decision (Sec. 2.3.2): E_map
+// and the decision kernel, then the remap's launches with the Grid's gate
+// set, each of which returns at once unless the decision opened it.
+// Enqueue only; host counters untouched.
+void step_remap_gated(vm_solver* s) {
+  launch_remap_gate(s);
+  s->g.gate = &s->ds->gate;
+  launch_taylor(s);
+  launch_map(s);
+  launch_remap_resample(s, s->tmp);
+  launch_copy_gated(s);
+  launch_spline_solve(s, s->fini, s->eta);
+  launch_reset_elements(s);
+  s->g.gate = nullptr;
+}
+
+// Device copies of the remap cycle, from the host's (cycle, forced remaps);
+// the gate shut.  Not inside a stream capture (a pageable source).
+cudaError_t cycle_to_device(vm_solver* s) {
+  struct {
+    long long emap_remaps;
+    int32_t cyc, gate;
+  } c{(long long)s->emap_remaps, s->cyc, 0};
+  static_assert(offsetof(DevState, cyc) == offsetof(DevState, emap_remaps) + 8 &&
+                    offsetof(DevState, gate) == offsetof(DevState, cyc) + 4 && sizeof c == 16,
+                "cycle fields of DevState");
+  return cudaMemcpyAsync(&s->ds->emap_remaps, &c, sizeof c, cudaMemcpyHostToDevice, s->stream);
+}
+
+// Host copies of a device-kept cycle (synchronises).
+cudaError_t cycle_to_host(vm_solver* s) {
+  if (!device_cycle(s)) return cudaSuccess;
+  int32_t cyc = 0;
+  long long er = 0;
+  cudaError_t e = cudaMemcpyAsync(&cyc, &s->ds->cyc, sizeof cyc, cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&er, &s->ds->emap_remaps, sizeof er, cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e == cudaSuccess) {
+    s->cyc = cyc;
+    s->emap_remaps = er;
+  }
+  return e;
+}
+
 }  // namespace vm
 
 namespace {
@@ -243,6 +287,7 @@ vm_status emap_now(vm_solver* s, double* e) {
 vm_status remap_internal(vm_solver* s) {
   if (vm::step_remap(s) != cudaSuccess) return VM_E_CUDA;
   s->cyc = 0;
+  if (vm::device_cycle(s)) VM_CUDA_TRY(cudaMemsetAsync(&s->ds->cyc, 0, 2 * sizeof(int32_t), s->stream));
   return check_launch(s);
 }
 
@@ -551,6 +596,7 @@ vm_status vm_set_f(vm_solver* s, const double* f0, int32_t on_device) {
   s->time = 0.0;
   s->last_dt = 0.0;
   s->cyc = 0;
+  VM_CUDA_TRY(vm::cycle_to_device(s));
   return check_launch(s);
 }
 
@@ -610,6 +656,11 @@ vm_status vm_step(vm_solver* s, int32_t nsteps) {
     s->nstep++;
     s->time += s->g.dt;
     s->last_dt = s->g.dt;
+    if (vm::device_cycle(s)) {
+      // E_map and the cycle decide on the device; no round trip
+      vm::step_remap_gated(s);
+      continue;
+    }
     s->cyc++;
     bool remap = s->cyc >= s->cfg.n_s;
     if (!remap && s->cfg.emap_remap > 0.0) {
@@ -714,7 +765,7 @@ vm_status vm_diagnostics(vm_solver* s, vm_diag* d) {
   d->detT_min = decode(h.det_min_key);
   d->detT_max = decode(h.det_max_key);
   d->step = s->nstep;
-  d->cycle = s->cyc;
+  d->cycle = vm::device_cycle(s) ? h.cyc : s->cyc;
   d->holes = h.holes_found;
   d->hole_rounds = h.hole_rounds;
   d->overflow_elements = h.overflow_stat;
@@ -728,7 +779,7 @@ vm_status vm_diagnostics(vm_solver* s, vm_diag* d) {
   double e2;
   memcpy(&e2, &h.emap2_bits, 8);
   d->emap = sqrt(e2);
-  d->emap_remaps = s->emap_remaps;
+  d->emap_remaps = vm::device_cycle(s) ? (int64_t)h.emap_remaps : s->emap_remaps;
   d->time = s->time;
   d->last_dt = s->last_dt;
   d->lattice_range[0] = s->g.klo;
@@ -827,6 +878,7 @@ vm_status vm_save(vm_solver* s, const char* path) {
   if (!s->have_f) return VM_E_STATE;
   vm_status st = vm_sync(s);
   if (st != VM_OK) return st;
+  VM_CUDA_TRY(vm::cycle_to_host(s));
   FILE* fp = fopen(path, "wb");
   if (!fp) return VM_E_IO;
   const CkHeader h = ck_header(s);
@@ -894,5 +946,6 @@ vm_status vm_load(vm_solver* s, const char* path) {
   s->g.khi = h.lattice[1];
   s->g.llo = h.lattice[2];
   s->g.lhi = h.lattice[3];
+  VM_CUDA_TRY(vm::cycle_to_device(s));
   return VM_OK;
 }

@@ -5,8 +5,11 @@
 // element chunks, escaped elements...), so a step of the whole batch is
 // about twenty launches whatever the number of solves.  Those launches are
 // recorded once into a CUDA graph (a transport step, and a transport step
-// followed by a remap; every solve of a batch shares its remap phase), and
-// a batch step is one graph launch.  The number of persistent blocks of
+// followed by a remap; every solve whose cycle the host keeps shares one
+// remap phase), and a batch step is one graph launch.  Solves that remap on
+// the E_map criterion keep their cycle on the device: every step of the
+// graph ends with their E_map, each one's decision and their remap
+// launches, which skip the solves that do not remap this step.  The number of persistent blocks of
 // each phase can be tuned on the run's own steps (vm_batch_autotune): it
 // changes no result, only the time.
 #include <stdlib.h>
@@ -20,12 +23,15 @@
 
 struct vm_batch {
   std::vector<vm_solver*> solvers;
+  std::vector<vm_solver*> hosts;   // cycle kept on the host (one shared remap phase)
+  std::vector<vm_solver*> gated;   // cycle kept on the device (device_cycle)
   cudaStream_t capture = nullptr;  // capture stream (owned)
   cudaStream_t user = nullptr;     // stream the graphs are launched on
   cudaEvent_t sync = nullptr;
-  void* d_table = nullptr;         // plan table (device, owned)
-  std::vector<char> h_table;       // its host staging copy
-  vm::GroupPlan plan;
+  void* d_table = nullptr;         // plan tables (device, owned): all, hosts, gated
+  std::vector<char> h_table;       // their host staging copy
+  vm::GroupPlan plan;              // every solve (transport); carries the launch shapes
+  vm::GroupPlan plan_h, plan_g;    // remaps of the host-cycle / device-cycle solves
   cudaGraphExec_t exec[2] = {nullptr, nullptr};  // [0] transport step, [1] transport + remap
   int64_t launches_per[2] = {0, 0};
   int32_t n_s = 0;
@@ -49,6 +55,28 @@ void destroy_batch(vm_batch* b) {
   delete b;
 }
 
+// The three plans on `stream`, with the launch shapes of b->plan.
+void plans_on(const vm_batch* b, cudaStream_t stream, vm::GroupPlan& P, vm::GroupPlan& Ph, vm::GroupPlan& Pg) {
+  P = b->plan;
+  Ph = b->plan_h;
+  Pg = b->plan_g;
+  P.stream = Ph.stream = Pg.stream = stream;
+  memcpy(Ph.shape, P.shape, sizeof P.shape);
+  memcpy(Pg.shape, P.shape, sizeof P.shape);
+}
+
+// Enqueue one step: transport of every solve, the gated remaps, and (remap)
+// the host-cycle solves' remap.
+void enqueue_step(const vm_batch* b, const vm::GroupPlan& P, const vm::GroupPlan& Ph, const vm::GroupPlan& Pg,
+                  bool remap, const vm::GroupTiming* T = nullptr) {
+  vm::group_step_transport(P, T);
+  if (!b->gated.empty()) vm::group_step_gated(Pg);
+  if (remap && !b->hosts.empty()) vm::group_step_remap(Ph);
+}
+
+// Whether the next step ends the host-cycle solves' remap cycle.
+bool host_remap_next(const vm_batch* b) { return !b->hosts.empty() && b->hosts[0]->cyc + 1 >= b->n_s; }
+
 // Record one step of the whole batch into a graph.
 vm_status capture(vm_batch* b, bool remap, cudaGraphExec_t* out, int64_t* launches) {
   if (*out) {
@@ -57,10 +85,9 @@ vm_status capture(vm_batch* b, bool remap, cudaGraphExec_t* out, int64_t* launch
   }
   cudaGraph_t graph = nullptr;
   if (cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return VM_E_CUDA;
-  vm::GroupPlan P = b->plan;
-  P.stream = b->capture;
-  vm::group_step_transport(P);
-  if (remap) vm::group_step_remap(P);
+  vm::GroupPlan P, Ph, Pg;
+  plans_on(b, b->capture, P, Ph, Pg);
+  enqueue_step(b, P, Ph, Pg, remap);
   const cudaError_t e = cudaStreamEndCapture(b->capture, &graph);
   if (e != cudaSuccess || !graph) {
     if (graph) cudaGraphDestroy(graph);
@@ -121,24 +148,36 @@ extern "C" vm_status vm_batch_create(vm_solver* const* solvers, int32_t n, int32
   vm::clear_foreign_error();
   vm_status st = vm::group_check(solvers, n);
   if (st != VM_OK) return st;
-  const int32_t n_s = solvers[0]->cfg.n_s, cyc = solvers[0]->cyc;
+  std::vector<vm_solver*> hosts, gated;
   for (int32_t i = 0; i < n; i++) {
     if (solvers[i]->prof) return VM_E_STATE;
-    if (solvers[i]->cfg.n_s != n_s || solvers[i]->cyc != cyc) return VM_E_STATE;  // one remap phase per batch
+    (vm::device_cycle(solvers[i]) ? gated : hosts).push_back(solvers[i]);
   }
+  const int32_t n_s = hosts.empty() ? 0 : hosts[0]->cfg.n_s, cyc = hosts.empty() ? 0 : hosts[0]->cyc;
+  for (vm_solver* s : hosts)
+    if (s->cfg.n_s != n_s || s->cyc != cyc) return VM_E_STATE;  // one remap phase for the host-cycle solves
   if (!vm::group_map_prepare()) return VM_E_CUDA;
   vm_batch* b = new vm_batch();
   b->solvers.assign(solvers, solvers + n);
+  b->hosts = hosts;
+  b->gated = gated;
   b->user = (cudaStream_t)cuda_stream;
   b->n_s = n_s;
-  const size_t tb = vm::group_table_bytes(n);
-  b->h_table.assign(tb, 0);
+  auto seg = [](int k) { return (vm::group_table_bytes(k) + 255) / 256 * 256; };
+  const size_t t0 = seg(n), t1 = seg((int)hosts.size()), t2 = seg((int)gated.size());
+  b->h_table.assign(t0 + t1 + t2, 0);
   if (cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->sync, cudaEventDisableTiming) != cudaSuccess ||
-      cudaMalloc(&b->d_table, tb) != cudaSuccess)
+      cudaMalloc(&b->d_table, t0 + t1 + t2) != cudaSuccess)
     st = VM_E_CUDA;
   if (st == VM_OK) {
-    vm::group_plan(b->plan, solvers, n, b->d_table, b->h_table.data(), b->capture);
+    char* d = (char*)b->d_table;
+    char* h = b->h_table.data();
+    vm::group_plan(b->plan, solvers, n, d, h, b->capture);
+    if (!hosts.empty())
+      vm::group_plan(b->plan_h, hosts.data(), (int)hosts.size(), d + t0, h + t0, b->capture);
+    if (!gated.empty())
+      vm::group_plan(b->plan_g, gated.data(), (int)gated.size(), d + t0 + t1, h + t0 + t1, b->capture, true);
     if (cudaStreamSynchronize(b->capture) != cudaSuccess) st = VM_E_CUDA;
   }
   // pending work of the solvers is done before the first replay
@@ -160,8 +199,7 @@ extern "C" vm_status vm_batch_step(vm_batch* b, int32_t nsteps) {
   vm_status st = enter(b);
   if (st != VM_OK) return st;
   for (int32_t it = 0; it < nsteps; it++) {
-    const vm_solver* s0 = b->solvers[0];
-    const int kind = (s0->cyc + 1 >= b->n_s) ? 1 : 0;
+    const int kind = host_remap_next(b) ? 1 : 0;
     if (cudaGraphLaunch(b->exec[kind], b->user) != cudaSuccess) return VM_E_CUDA;
     count(b, kind);
   }
@@ -186,20 +224,22 @@ extern "C" vm_status vm_batch_autotune(vm_batch* b, int32_t trials) {
   vm::GroupTiming T;
   for (int e = 0; e < vm::GT_N; e++)
     if (cudaEventCreate(&T.ev[e]) != cudaSuccess) return VM_E_CUDA;
-  vm::GroupPlan P = b->plan;
-  P.stream = b->user;
+  vm::GroupPlan P, Ph, Pg;
+  plans_on(b, b->user, P, Ph, Pg);
   for (int c = 0; c < 4 && st == VM_OK; c++) {
     for (int t = 0; t < 5; t++) set_shape(P, t, kCand[c] * sms);
+    memcpy(Pg.shape, P.shape, sizeof P.shape);
     double acc[5] = {0, 0, 0, 0, 0};
     int timed = 0;
     while (timed < trials && st == VM_OK) {
-      // the step before a remap runs with the remap (untimed)
-      if (b->solvers[0]->cyc + 1 >= b->n_s) {
+      // the step before a host-cycle remap runs with the remap (untimed)
+      if (host_remap_next(b)) {
         if (cudaGraphLaunch(b->exec[1], b->user) != cudaSuccess) st = VM_E_CUDA;
         count(b, 1);
         continue;
       }
-      vm::group_step_transport(P, &T);
+      // the transport phases timed; the gated remaps follow untimed
+      enqueue_step(b, P, Ph, Pg, false, &T);
       if (cudaEventSynchronize(T.ev[vm::GT_END]) != cudaSuccess) st = VM_E_CUDA;
       for (int t = 0; t < 5 && st == VM_OK; t++) {
         float ms = 0.f;

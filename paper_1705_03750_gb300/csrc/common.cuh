@@ -43,7 +43,14 @@ struct Grid {
   int32_t fth_on;
   int32_t klo, khi, llo, lhi;
   int32_t recon_tiles;  // FP32-mixed path: 1 = reconstruction in tiles staged by bulk copies
+  // Remap decided on the device (Sec. 2.3.2): when set, every kernel of a
+  // remap enqueued with this Grid returns at once while *gate is 0
+  const int32_t* gate;
 };
+
+// True when the remap this Grid was enqueued for is not to run (read by
+// every thread of a kernel before any barrier, so all return together).
+__device__ __forceinline__ bool gate_shut(const Grid& g) { return g.gate != nullptr && __ldcg(g.gate) == 0; }
 
 // Small device-resident control block.
 struct DevState {
@@ -80,6 +87,12 @@ struct DevState {
   int32_t rect[4];
   int32_t fbox[4];
   uint32_t rect_done;
+  // Remap cycle kept on the device when the remap is decided there (E_map
+  // criterion, Sec. 2.3.2): the remaps E_map forced since vm_set_f, steps
+  // since the last remap, and the decision of the last step (1: remap now)
+  long long emap_remaps;
+  int32_t cyc;
+  int32_t gate;
 };
 
 // Owner slots of the influence map: (epoch << 24) | element index.  A slot
@@ -199,6 +212,16 @@ struct vm_solver {
 };
 
 namespace vm {
+// A solve whose remap cycle lives on the device (DevState cyc, gate,
+// emap_remaps): the E_map criterion decided without a host round trip.  The
+// adaptive domain reads its rectangle back at each remap, so with f_th > 0
+// the host keeps the decision.
+inline bool device_cycle(const vm_solver* s) { return s->cfg.emap_remap > 0.0 && s->cfg.f_th == 0.0; }
+cudaError_t cycle_to_device(vm_solver* s);  // host (cyc, emap_remaps) -> device, gate shut
+cudaError_t cycle_to_host(vm_solver* s);    // device -> host when device_cycle (synchronises)
+}  // namespace vm
+
+namespace vm {
 
 // ---- per-launch timing (no-ops unless vm_profile enabled it) ----
 int prof_begin(vm_solver* s, int kid);
@@ -225,6 +248,10 @@ void launch_scan_force_raw(const Grid& g, const double* M, double* a, double* da
 void launch_diagnostics(vm_solver* s);
 // E_map of the last influence map (Sec. 2.3.2) into ds->emap2_bits (zeroed by the caller)
 void launch_emap(vm_solver* s);
+// E_map of the step's map and the remap decision on the device (DevState
+// cyc, gate, emap_remaps); the gated remap's tmp -> f_ini copy
+void launch_remap_gate(vm_solver* s);
+void launch_copy_gated(vm_solver* s);
 // largest projected density sum_j f(i, j) dv of s->f into ds->rho_max_bits (zeroed by the caller)
 void launch_rho_max(vm_solver* s);
 // map.cu
@@ -288,6 +315,8 @@ struct SolveDesc {
   float* thvf;
   double* Mpart;  // tile row sums of the staged reconstruction
   DevState* ds;
+  int32_t n_s;      // steps per remap cycle
+  double emap_thr;  // E_map remap threshold (0: the cycle alone decides)
 };
 
 // Solve owning unit u: the largest sv with off[sv] <= u (off[0] = 0,
@@ -345,20 +374,35 @@ struct GroupPlan {
 enum GroupPhase : int {
   GP_DRIFT = 0, GP_TAYLOR, GP_MAP_BEGIN, GP_PAIR, GP_SMALL, GP_BIG1, GP_BIG2, GP_BIG3, GP_RESOLVE,
   GP_FIND_HOLES, GP_HOLES, GP_RECON, GP_SCAN, GP_DIFF, GP_KICK, GP_REMAP, GP_COPY, GP_ROWS, GP_COLS,
-  GP_RESET, GP_UNITS, GP_N
+  GP_RESET, GP_UNITS, GP_EMAP, GP_N
 };
 
 // The solve of unit u, its Grid in shared memory (read by every thread of
-// the block), and the unit's index within its solve.
-#define GROUP_LOOP(off, ns, total)                                   \
+// the block), and the unit's index within its solve.  GROUP_LOOP also skips
+// the solves whose gated remap is not to run (gate_shut): a block that meets
+// one moves on to its first unit past that solve.  GROUP_LOOP_ALL visits
+// every unit (the phases that take the decision).
+#define GROUP_LOOP_GATED_(off, ns, total, gated)                     \
   __shared__ Grid gsh;                                               \
-  __shared__ int svsh;                                               \
+  __shared__ int svsh, skipsh;                                       \
   for (int u = blockIdx.x; u < (total); u += gridDim.x) {            \
     if (threadIdx.x == 0) {                                          \
-      svsh = unit_solve((off), (ns), u);                             \
-      gsh = D[svsh].g;                                               \
+      const int sv_ = unit_solve((off), (ns), u);                    \
+      svsh = sv_;                                                    \
+      skipsh = -1;                                                   \
+      if ((gated) && gate_shut(D[sv_].g)) {                          \
+        const int nx_ = __ldg((off) + sv_ + 1), G_ = (int)gridDim.x; \
+        skipsh = nx_ + ((int)blockIdx.x - nx_ % G_ + G_) % G_;       \
+      } else {                                                       \
+        gsh = D[sv_].g;                                              \
+      }                                                              \
     }                                                                \
     __syncthreads();                                                 \
+    if (skipsh >= 0) {                                               \
+      u = skipsh - (int)gridDim.x;                                   \
+      __syncthreads();                                               \
+      continue;                                                      \
+    }                                                                \
     const int sv = svsh;                                             \
     const SolveDesc& d = D[sv];                                      \
     const int vb = u - __ldg((off) + sv);                            \
@@ -368,6 +412,8 @@ enum GroupPhase : int {
       __syncthreads();                                               \
       continue;                                                      \
     }
+#define GROUP_LOOP(off, ns, total) GROUP_LOOP_GATED_(off, ns, total, true)
+#define GROUP_LOOP_ALL(off, ns, total) GROUP_LOOP_GATED_(off, ns, total, false)
 #define GROUP_END \
     __syncthreads(); \
   }
@@ -385,6 +431,7 @@ void group_map(const GroupPlan& G);
 void group_reconstruct(const GroupPlan& G);
 void group_remap_resample(const GroupPlan& G);   // into each solve's tmp
 void group_copy_tmp_to_fini(const GroupPlan& G);
+void group_remap_gate(const GroupPlan& G);        // E_map + decision of each solve (gated plans)
 void group_spline(const GroupPlan& G);           // fini -> eta
 size_t group_big_smem(const Grid& g);            // the large windows' shared memory for grid g
 bool group_map_prepare();

@@ -123,6 +123,7 @@ __global__ void k_drift(Grid g, double* __restrict__ el, double* __restrict__ ta
 }
 
 __global__ void k_taylor(Grid g, const double* __restrict__ el, double* __restrict__ tay, float* __restrict__ tayf) {
+  if (gate_shut(g)) return;
   int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m < g.ne) taylor_one(g, el, m, tay, tayf);
 }
@@ -204,7 +205,10 @@ __device__ __forceinline__ void reset_body(const Grid& g, double* __restrict__ e
   for (int q = EL_HXXX; q < EL_N; q++) el[q * ne + m] = 0.0;
 }
 
-__global__ void k_reset(Grid g, double* __restrict__ el) { reset_body(g, el, blockIdx.x); }
+__global__ void k_reset(Grid g, double* __restrict__ el) {
+  if (gate_shut(g)) return;
+  reset_body(g, el, blockIdx.x);
+}
 
 constexpr int SCAN_T = 512;
 

@@ -22,10 +22,11 @@ namespace {
 
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
-SolveDesc desc_of(const vm_solver* s) {
+SolveDesc desc_of(const vm_solver* s, bool gated) {
   SolveDesc d;
   memset(&d, 0, sizeof d);
   d.g = s->g;
+  d.g.gate = gated ? &s->ds->gate : nullptr;
   const float fa = (float)s->g.alpha, fb = (float)s->g.beta;
   d.alo = ((double)fa <= s->g.alpha) ? fa : nextafterf(fa, -INFINITY);
   d.ahi = ((double)fa >= s->g.alpha) ? fa : nextafterf(fa, INFINITY);
@@ -62,6 +63,8 @@ SolveDesc desc_of(const vm_solver* s) {
   d.thvf = s->thomas_vf;
   d.Mpart = s->Mpart;
   d.ds = s->ds;
+  d.n_s = s->cfg.n_s;
+  d.emap_thr = s->cfg.emap_remap;
   return d;
 }
 
@@ -96,8 +99,9 @@ vm_status group_check(vm_solver* const* solvers, int n) {
     if (!s->have_f) return VM_E_STATE;
     if (s->fp32 != solvers[0]->fp32) return VM_E_INVALID_ARG;
     if (s->g.recon_tiles != solvers[0]->g.recon_tiles) return VM_E_INVALID_ARG;
-    // host decisions per step or per remap: not part of a group step
-    if (s->cfg.emap_remap > 0.0 || s->cfg.c_dyn > 0.0 || s->cfg.f_th > 0.0) return VM_E_INVALID_ARG;
+    // host decisions per step or per remap: not part of a group step (the
+    // E_map criterion is decided on the device, see device_cycle)
+    if (s->cfg.c_dyn > 0.0 || s->cfg.f_th > 0.0) return VM_E_INVALID_ARG;
     for (int j = 0; j < i; j++)
       if (solvers[j] == s) return VM_E_INVALID_ARG;
   }
@@ -107,8 +111,10 @@ vm_status group_check(vm_solver* const* solvers, int n) {
 // Fill the plan of solvers[0..n) into the device table at d_table (at least
 // group_table_bytes(n) bytes, 256-byte aligned), staging through the host
 // buffer `host` (the same size, kept alive until the copy completes: the
-// copy is asynchronous on `stream`).
-void group_plan(GroupPlan& P, vm_solver* const* solvers, int n, void* d_table, void* host, cudaStream_t stream) {
+// copy is asynchronous on `stream`).  gated: the plan of the remaps each
+// solve's device decision may skip (its Grids carry the solves' gates).
+void group_plan(GroupPlan& P, vm_solver* const* solvers, int n, void* d_table, void* host, cudaStream_t stream,
+                bool gated) {
   memset(&P, 0, sizeof P);
   char* hb = (char*)host;
   char* db = (char*)d_table;
@@ -118,7 +124,7 @@ void group_plan(GroupPlan& P, vm_solver* const* solvers, int n, void* d_table, v
   int tot[U_N] = {0};
   size_t big = 0;
   for (int i = 0; i < n; i++) {
-    hd[i] = desc_of(solvers[i]);
+    hd[i] = desc_of(solvers[i], gated);
     int u[U_N];
     units_of(solvers[i], u);
     for (int k = 0; k < U_N; k++) {
@@ -187,12 +193,20 @@ void group_step_remap(const GroupPlan& P) {
   group_reset(P);
 }
 
-// Host counters of a solve after a group step (as vm_step keeps them).
+// The remaps of a gated plan after a transport step: E_map and each solve's
+// decision, then the remap launches, which skip the solves left shut.
+void group_step_gated(const GroupPlan& P) {
+  group_remap_gate(P);
+  group_step_remap(P);
+}
+
+// Host counters of a solve after a group step (as vm_step keeps them; the
+// cycle of a device_cycle solve is counted on the device).
 void group_count_step(vm_solver* s, bool remapped) {
   s->nstep++;
   s->time += s->g.dt;
   s->last_dt = s->g.dt;
-  s->cyc = remapped ? 0 : s->cyc + 1;
+  if (!device_cycle(s)) s->cyc = remapped ? 0 : s->cyc + 1;
 }
 
 }  // namespace vm

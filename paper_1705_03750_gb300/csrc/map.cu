@@ -262,11 +262,12 @@ __device__ __forceinline__ void map_begin_body(DevState* ds) {
     ds->noverflow_back = 0;
     ds->nseed = 0;
     ds->n_pair_esc = 0;
+    ds->emap2_bits = 0ull;  // E_map describes the current map only
   }
 }
 
-__global__ void k_map_begin(DevState* ds) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) map_begin_body(ds);
+__global__ void k_map_begin(DevState* ds, const int32_t* gate) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && !(gate != nullptr && __ldcg(gate) == 0)) map_begin_body(ds);
 }
 
 __device__ __noinline__ void contest(const Slots& S, const Grid& g, long long i, long long j, size_t p, int m,
@@ -555,6 +556,7 @@ __global__ void __launch_bounds__(32 * TE, 8) k_claim_small(Grid g, const double
                                                          float ahi, int2* __restrict__ ovf_list,
                                                          const int32_t* __restrict__ list_in,
                                                          const int* __restrict__ n_in) {
+  if (gate_shut(g)) return;
   claim_small_body(g, tay, tayf, Sin, alo, ahi, ovf_list, list_in, n_in, blockIdx.x, gridDim.x);
 }
 
@@ -1162,6 +1164,7 @@ __global__ void __launch_bounds__(32 * TP, 8) k_claim_pair(Grid g, const double*
                                                          const float* __restrict__ tayf, Slots Sin, float alo,
                                                          float ahi, int32_t* __restrict__ esc_list,
                                                          int2* __restrict__ ovf_list) {
+  if (gate_shut(g)) return;
   claim_pair_body(g, tay, tayf, Sin, alo, ahi, esc_list, ovf_list, blockIdx.x);
 }
 
@@ -1652,6 +1655,7 @@ __global__ void __launch_bounds__(BT, BLOCKS_PER_SM) k_claim_big(Grid g, const d
                                                   int* __restrict__ stat, int2* __restrict__ list_out,
                                                   int* __restrict__ n_out, int* __restrict__ take,
                                                   unsigned long long* __restrict__ gwin, size_t gwin_words) {
+  if (gate_shut(g)) return;
   claim_big_body<kGlobal>(g, tay, tayf, Sin, alo, ahi, list_in, n_in, n_back, stat, list_out, n_out, take, gwin,
                           gwin_words, blockIdx.x);
 }
@@ -1686,7 +1690,10 @@ __device__ __forceinline__ void resolve_body(const Grid& g, const Slots& Sin, in
   }
 }
 
-__global__ void k_resolve(Grid g, Slots Sin) { resolve_body(g, Sin, blockIdx.x, gridDim.x); }
+__global__ void k_resolve(Grid g, Slots Sin) {
+  if (gate_shut(g)) return;
+  resolve_body(g, Sin, blockIdx.x, gridDim.x);
+}
 
 // Sites no element claimed, four owner slots per 16-byte load (the slot
 // array is 256-byte aligned); the list's order does not matter (the hole
@@ -1709,6 +1716,7 @@ __device__ __forceinline__ void find_holes_body(const Grid& g, const uint32_t* _
 }
 
 __global__ void k_find_holes(Grid g, const uint32_t* __restrict__ slot0, int32_t* __restrict__ holes, DevState* ds) {
+  if (gate_shut(g)) return;
   find_holes_body(g, slot0, holes, ds, blockIdx.x, gridDim.x);
 }
 
@@ -1785,6 +1793,7 @@ __device__ __forceinline__ void holes_body(const Grid& g, const double* __restri
 
 __global__ void __launch_bounds__(HT) k_holes(Grid g, const double* __restrict__ tay, uint32_t* __restrict__ slot0,
                                               int32_t* la, int32_t* lb, int32_t* cho, DevState* ds) {
+  if (gate_shut(g)) return;
   holes_body(g, tay, slot0, la, lb, cho, ds);
 }
 
@@ -1795,11 +1804,12 @@ __global__ void __launch_bounds__(HT) k_holes(Grid g, const double* __restrict__
 // ((b + ze_n) - ze_m)^2 (Q_n - Q_m = (a dx_m, b dv_m) on the lattice), FP64
 // in the oracle's order; the largest into ds->emap2_bits (bits of a
 // non-negative double order as the values do).
-__global__ void k_emap(Grid g, const uint32_t* __restrict__ slot0, const double* __restrict__ tay, DevState* ds) {
+__device__ __forceinline__ void emap_body(const Grid& g, const uint32_t* __restrict__ slot0,
+                                          const double* __restrict__ tay, DevState* ds, int vb, int vg) {
   const uint32_t epoch = *(volatile uint32_t*)&ds->epoch;
   const size_t n = (size_t)g.nx * g.nv;
   double worst = 0.0;
-  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
+  for (size_t p = (size_t)vb * blockDim.x + threadIdx.x; p < n; p += (size_t)vg * blockDim.x) {
     const uint32_t t = slot0[p];
     if ((t >> 24) != epoch) continue;
     const int m = (int)(t & SLOT_MASK);
@@ -1827,6 +1837,32 @@ __global__ void k_emap(Grid g, const uint32_t* __restrict__ slot0, const double*
   for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_down_sync(0xffffffffu, worst, o));
   if ((threadIdx.x & 31) == 0 && worst > 0.0)
     atomicMax(&ds->emap2_bits, (unsigned long long)__double_as_longlong(worst));
+}
+
+__global__ void k_emap(Grid g, const uint32_t* __restrict__ slot0, const double* __restrict__ tay, DevState* ds) {
+  emap_body(g, slot0, tay, ds, blockIdx.x, gridDim.x);
+}
+
+// The remap decision of one solve after a step (Sec. 2.3.2), on the device:
+// the cycle advances, and the remap runs at once when n_s steps are complete
+// or, for thr > 0, when the step's E_map exceeds thr (counted).  The same
+// rule, in the same order, as the host's decision.
+__device__ __forceinline__ void remap_decide(DevState* ds, int n_s, double thr) {
+  const int cyc = ds->cyc + 1;
+  bool remap = cyc >= n_s;
+  if (!remap && thr > 0.0) {
+    const double e = sqrt(__longlong_as_double((long long)ds->emap2_bits));
+    if (e > thr) {
+      remap = true;
+      ds->emap_remaps++;
+    }
+  }
+  ds->cyc = remap ? 0 : cyc;
+  ds->gate = remap ? 1 : 0;
+}
+
+__global__ void k_remap_gate(DevState* ds, int n_s, double thr) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) remap_decide(ds, n_s, thr);
 }
 
 __global__ void k_read_map(const uint32_t* __restrict__ slot0, const DevState* ds, int32_t* __restrict__ out,
@@ -1874,7 +1910,8 @@ __device__ __forceinline__ Slots slots_of(const SolveDesc& d) {
 }
 
 __global__ void k_map_begin_group(const SolveDesc* __restrict__ D, int ns) {
-  for (int sv = blockIdx.x * blockDim.x + threadIdx.x; sv < ns; sv += gridDim.x * blockDim.x) map_begin_body(D[sv].ds);
+  for (int sv = blockIdx.x * blockDim.x + threadIdx.x; sv < ns; sv += gridDim.x * blockDim.x)
+    if (!gate_shut(D[sv].g)) map_begin_body(D[sv].ds);
 }
 
 // Units of a dynamic phase, per solve, from the solve's counters (read after
@@ -1901,7 +1938,7 @@ __global__ void __launch_bounds__(1024) k_units(const SolveDesc* __restrict__ D,
         case GC_REC: n = (min(ds->nrec, D[sv].rec_cap) + 255) / 256; break;
         default: n = ds->nholes > 0 ? 1 : 0; break;
       }
-      u = min(max(n, 0), cap);
+      u = gate_shut(D[sv].g) ? 0 : min(max(n, 0), cap);
     }
     int inc = u;
     for (int o = 1; o < 32; o <<= 1) {
@@ -2000,6 +2037,18 @@ __global__ void k_find_holes_group(const SolveDesc* __restrict__ D, const int* _
   GROUP_END
 }
 
+__global__ void k_emap_group(const SolveDesc* __restrict__ D, const int* __restrict__ off, int ns, int total) {
+  GROUP_LOOP_ALL(off, ns, total)
+  const int vg = __ldg(off + sv + 1) - __ldg(off + sv);
+  emap_body(gsh, d.map, d.tay, d.ds, vb, vg);
+  GROUP_END
+}
+
+__global__ void k_remap_gate_group(const SolveDesc* __restrict__ D, int ns) {
+  for (int sv = blockIdx.x * blockDim.x + threadIdx.x; sv < ns; sv += gridDim.x * blockDim.x)
+    remap_decide(D[sv].ds, D[sv].n_s, D[sv].emap_thr);
+}
+
 __global__ void __launch_bounds__(HT) k_holes_group(const SolveDesc* __restrict__ D, const int* __restrict__ off,
                                                   int ns) {
   GROUP_DYN_LOOP(off, ns)
@@ -2021,6 +2070,18 @@ void launch_emap(vm_solver* s) {
   if (nb > 152 * 16) nb = 152 * 16;
   k_emap<<<nb, 256, 0, s->stream>>>(s->g, s->map, s->tay, s->ds);
   s->launches++;
+}
+
+void launch_remap_gate(vm_solver* s) {
+  launch_emap(s);
+  k_remap_gate<<<1, 32, 0, s->stream>>>(s->ds, s->cfg.n_s, s->cfg.emap_remap);
+  s->launches++;
+}
+
+void group_remap_gate(const GroupPlan& G) {
+  if (G.tot_sites > 0)
+    k_emap_group<<<group_grid(G, GP_EMAP, G.tot_sites), 256, 0, G.stream>>>(G.D, G.off_sites, G.ns, G.tot_sites);
+  k_remap_gate_group<<<(unsigned)((G.ns + 255) / 256), 256, 0, G.stream>>>(G.D, G.ns);
 }
 
 namespace {
@@ -2061,7 +2122,7 @@ void launch_map(vm_solver* s) {
   alpha_bounds(s->g.alpha, alo, ahi);
   int ps = prof_begin(s, KID_MAP_CLEAR);
   if (s->g.fth_on) launch_domain_rect(s);
-  k_map_begin<<<1, 32, 0, s->stream>>>(s->ds);
+  k_map_begin<<<1, 32, 0, s->stream>>>(s->ds, s->g.gate);
   prof_end(s, ps);
   // tier 0 (two elements per warp), its escapes to tier 1 through the first
   // hole list (free until the holes are looked for)

@@ -283,6 +283,7 @@ __device__ __forceinline__ void k_remap64_body(const Grid& g, const uint32_t* __
 __global__ void __launch_bounds__(256) k_remap64(Grid g, const uint32_t* __restrict__ map, const DevState* ds,
                                                  const double* __restrict__ tay, const double* __restrict__ eta,
                                                  double* __restrict__ out) {
+  if (gate_shut(g)) return;
   k_remap64_body(g, map, ds, tay, eta, out, blockIdx.x);
 }
 
@@ -987,6 +988,7 @@ __global__ void __launch_bounds__(256) k_remap32(Grid g, const uint32_t* __restr
                                                  const double* __restrict__ tay, const float* __restrict__ tayf,
                                                  const float* __restrict__ eta, float* __restrict__ out, float blo,
                                                  float bhi) {
+  if (gate_shut(g)) return;
   k_remap32_body(g, map, ds, tay, tayf, eta, out, blo, bhi, blockIdx.x);
 }
 
@@ -1046,6 +1048,16 @@ __global__ void __launch_bounds__(256) k_copy_group(const SolveDesc* __restrict_
   GROUP_END
 }
 
+// tmp -> f_ini of one solve inside a gated remap (the copy a remap decided
+// on the device may skip; element by element, any site count).
+template <typename R>
+__global__ void __launch_bounds__(256) k_copy_gated(Grid g, const R* __restrict__ src, R* __restrict__ dst) {
+  if (gate_shut(g)) return;
+  const size_t n = (size_t)g.nx * g.nv;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
+    dst[p] = src[p];
+}
+
 template <typename S, typename D>
 __global__ void k_convert(const S* __restrict__ src, D* __restrict__ dst, size_t n) {
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
@@ -1082,6 +1094,15 @@ void group_remap_resample(const GroupPlan& G) {
     k_remap_group32<<<group_grid(G, GP_REMAP, G.tot_rows), nt, 0, G.stream>>>(G.D, G.off_rows, G.ns, G.tot_rows);
   else
     k_remap_group64<<<group_grid(G, GP_REMAP, G.tot_rows), nt, 0, G.stream>>>(G.D, G.off_rows, G.ns, G.tot_rows);
+}
+
+void launch_copy_gated(vm_solver* s) {
+  const unsigned nb = grid_for(s->n);
+  if (s->fp32)
+    k_copy_gated<float><<<nb, 256, 0, s->stream>>>(s->g, (const float*)s->tmp, (float*)s->fini);
+  else
+    k_copy_gated<double><<<nb, 256, 0, s->stream>>>(s->g, (const double*)s->tmp, (double*)s->fini);
+  s->launches++;
 }
 
 void group_copy_tmp_to_fini(const GroupPlan& G) {

@@ -6,7 +6,9 @@
 // first-fit with coalescing), keeps every admitted solve's state resident,
 // and advances ALL active solves together: every step of a tick is one group
 // step (group.cu: one launch per phase for the whole active set, the remaps
-// of the solves whose cycle ends in one more group), so requests that arrive
+// of the solves whose cycle ends in one more group, and the solves that remap
+// on the E_map criterion behind their own device decisions in a third), so
+// requests that arrive
 // while others run join the next step's launches.  A solve that has taken
 // all its steps has its pixel masses and force copied to pinned host memory
 // behind an event; the poll that finds the event complete hands the result
@@ -28,7 +30,9 @@ namespace {
 
 constexpr int kInFlight = 2;     // ticks queued ahead of the device
 constexpr int kTableSlots = 16;  // plan tables in the pool
-constexpr int kPlanSlots = 2;    // of them for the transport plan (alternating); the rest a ring for remaps
+// of them, two (alternating) for the transport plan, two for the gated plan,
+// and the rest a ring for the host-cycle remaps
+constexpr int kPlanSlots = 4;
 
 double now_s(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -103,17 +107,20 @@ struct vm_server {
   PoolAlloc alloc;
   // plan tables: device slots, each with its pinned staging copy and an event
   // after its last use; slots 0-1 hold the transport plan of the stepping
-  // set (alternating, so that a rebuild never overwrites the table queued
-  // steps still read), slots 2.. a ring for the remap subsets
+  // set and 2-3 the gated plan of its device-cycle solves (each pair
+  // alternating, so that a rebuild never overwrites a table queued steps
+  // still read), slots 4.. a ring for the host-cycle remap subsets
   size_t table_bytes = 0;
   char* h_tables = nullptr;
   cudaEvent_t table_ev[kTableSlots];
   int table_next = kPlanSlots;
-  int plan_slot = 0;
+  int plan_slot = 0, gated_slot = 0;
   cudaEvent_t tick_ev[kInFlight];
   int tick_next = 0, ticks_queued = 0;
-  // the plan of the current stepping set (rebuilt when the set changes)
-  vm::GroupPlan plan;
+  // the plans of the current stepping set (rebuilt when the set changes):
+  // transport of all, gated remaps of the device-cycle solves (if any)
+  vm::GroupPlan plan, plan_g;
+  bool have_gated = false;
   std::vector<vm_solver*> plan_set;
   bool plan_valid = false;
   std::deque<Req*> waiting;
@@ -146,12 +153,16 @@ void pinned_put(vm_server* S, double* p, size_t cap) {
   if (p) S->pinned_free.emplace_back(cap, p);
 }
 
-// A plan-table slot whose last use has completed: the other transport slot,
-// or the next slot of the remap ring.
-int table_slot(vm_server* S, bool transport) {
+enum PlanKind { PK_TRANSPORT, PK_GATED, PK_REMAP };
+
+// A plan-table slot whose last use has completed: the other slot of the
+// transport or gated pair, or the next slot of the remap ring.
+int table_slot(vm_server* S, PlanKind kind) {
   int k;
-  if (transport) {
-    k = S->plan_slot = (S->plan_slot + 1) % kPlanSlots;
+  if (kind == PK_TRANSPORT) {
+    k = S->plan_slot = (S->plan_slot + 1) % 2;
+  } else if (kind == PK_GATED) {
+    k = 2 + (S->gated_slot = (S->gated_slot + 1) % 2);
   } else {
     k = S->table_next;
     S->table_next = (k + 1 - kPlanSlots) % (kTableSlots - kPlanSlots) + kPlanSlots;
@@ -160,10 +171,10 @@ int table_slot(vm_server* S, bool transport) {
   return k;
 }
 
-void plan_into_slot(vm_server* S, vm::GroupPlan& P, const std::vector<vm_solver*>& set, bool transport) {
-  const int k = table_slot(S, transport);
+void plan_into_slot(vm_server* S, vm::GroupPlan& P, const std::vector<vm_solver*>& set, PlanKind kind) {
+  const int k = table_slot(S, kind);
   vm::group_plan(P, set.data(), (int)set.size(), S->pool + (size_t)k * S->table_bytes,
-                 S->h_tables + (size_t)k * S->table_bytes, S->stream);
+                 S->h_tables + (size_t)k * S->table_bytes, S->stream, kind == PK_GATED);
   cudaEventRecord(S->table_ev[k], S->stream);  // re-recorded after the plan's last use
   P.big_blocks_cap = 0;
 }
@@ -257,12 +268,21 @@ vm_status tick(vm_server* S) {
       }
     if (set.empty()) break;
     if (!S->plan_valid || set != S->plan_set) {
-      plan_into_slot(S, S->plan, set, true);
+      plan_into_slot(S, S->plan, set, PK_TRANSPORT);
+      std::vector<vm_solver*> gated;
+      for (vm_solver* s : set)
+        if (vm::device_cycle(s)) gated.push_back(s);
+      S->have_gated = !gated.empty();
+      if (S->have_gated) plan_into_slot(S, S->plan_g, gated, PK_GATED);
       S->plan_set = set;
       S->plan_valid = true;
     }
     vm::group_step_transport(S->plan);
     mark_slot_used(S, S->plan);
+    if (S->have_gated) {
+      vm::group_step_gated(S->plan_g);
+      mark_slot_used(S, S->plan_g);
+    }
     S->group_steps++;
     std::vector<vm_solver*> remap;
     for (Req* r : reqs) {
@@ -270,12 +290,13 @@ vm_status tick(vm_server* S) {
       s->nstep++;
       s->time += s->g.dt;
       s->last_dt = s->g.dt;
+      if (vm::device_cycle(s)) continue;  // its cycle and remaps are on the device
       s->cyc++;
       if (s->cyc >= s->cfg.n_s) remap.push_back(s);
     }
     if (!remap.empty()) {
       vm::GroupPlan R;
-      plan_into_slot(S, R, remap, false);
+      plan_into_slot(S, R, remap, PK_REMAP);
       vm::group_step_remap(R);
       mark_slot_used(S, R);
       S->remap_groups++;
@@ -351,7 +372,7 @@ vm_status vm_server_create(const vm_server_config* c, void* d_pool, size_t pool_
 vm_status vm_server_submit(vm_server* S, const vm_config* cfg, const double* f0, int32_t nsteps, int64_t* id) {
   if (!S || !cfg || !f0 || !id || nsteps < 1) return VM_E_INVALID_ARG;
   if (cfg->precision != S->c.precision) return VM_E_INVALID_ARG;
-  if (cfg->emap_remap > 0.0 || cfg->c_dyn > 0.0 || cfg->f_th > 0.0) return VM_E_INVALID_ARG;
+  if (cfg->c_dyn > 0.0 || cfg->f_th > 0.0) return VM_E_INVALID_ARG;
   const size_t need = vm_workspace_bytes(cfg);
   if (need == 0) return VM_E_INVALID_ARG;
   if (((need + 255) & ~size_t(255)) > S->alloc.size - vm_server_pool_bytes(&S->c)) return VM_E_BUDGET;

@@ -151,6 +151,7 @@ __device__ __forceinline__ void rows_scan_body(const Grid& g, const R* __restric
 template <typename R, typename C>
 __global__ void __launch_bounds__(128) k_rows_scan(Grid g, const R* __restrict__ src, R* __restrict__ dst,
                                                    const C* __restrict__ th) {
+  if (gate_shut(g)) return;
   rows_scan_body(g, src, dst, th, blockIdx.x);
 }
 
@@ -212,6 +213,7 @@ __device__ __forceinline__ void cols_body(const Grid& g, R* __restrict__ x, cons
 
 template <typename R, typename C>
 __global__ void __launch_bounds__(32) k_cols(Grid g, R* __restrict__ x, const C* __restrict__ th) {
+  if (gate_shut(g)) return;
   cols_body(g, x, th, blockIdx.x);
 }
 

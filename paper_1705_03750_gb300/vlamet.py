@@ -466,10 +466,12 @@ class NativeServer:
     """The library's serving loop (vm_server_*): continuous batching of
     submitted solves on one device pool.  ``budget_bytes`` of the pool hold
     the solves' workspaces; ``poll()`` drives it without waiting for the
-    device and returns the requests finished since the last call."""
+    device and returns the requests finished since the last call.
+    ``emap_remap`` (> 0) is every request's E_map remap threshold unless
+    submit() gives its own."""
 
     def __init__(self, budget_bytes: int, max_active: int = 32, steps_per_tick: int = 5,
-                 precision: int = VM_FP32_MIXED, stream=None, device=None):
+                 precision: int = VM_FP32_MIXED, stream=None, device=None, emap_remap: float = 0.0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("NativeServer needs a CUDA device")
@@ -477,6 +479,7 @@ class NativeServer:
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
         self.precision = precision
+        self.emap_remap = float(emap_remap)
         self._c = VmServerConfig(int(budget_bytes), int(max_active), int(steps_per_tick), int(precision))
         reserve = int(self.L.vm_server_pool_bytes(C.byref(self._c)))
         nbytes = reserve + int(budget_bytes)
@@ -489,8 +492,10 @@ class NativeServer:
         self.nx = {}
         self._done = (VmServerDone * 256)()
 
-    def submit(self, rc, f0: np.ndarray, steps: int) -> int:
-        cfg = Config.from_run(rc, self.precision).c()
+    def submit(self, rc, f0: np.ndarray, steps: int, emap_remap: float | None = None) -> int:
+        c = Config.from_run(rc, self.precision)
+        c.emap_remap = self.emap_remap if emap_remap is None else float(emap_remap)
+        cfg = c.c()
         f0 = np.ascontiguousarray(f0, dtype=np.float64)
         if f0.shape != (rc.nx, rc.nv):
             raise ValueError(f"f0 must have shape ({rc.nx}, {rc.nv})")

@@ -103,8 +103,51 @@ def test_batch_refuses_solves_out_of_phase_or_precision():
     assert e.value.status == 1
 
 
-def _served(reqs, budget=8 << 30, max_active=8, tick=3):
-    srv = V.NativeServer(budget, max_active=max_active, steps_per_tick=tick)
+def _emap_solver(rc, prec, thr):
+    cfg = V.Config.from_run(rc, prec)
+    cfg.emap_remap = thr
+    s = V.Solver(cfg, stream=torch.cuda.Stream())
+    s.set_f(I.initial_f(rc))
+    return s
+
+
+def _median_emap(rc, prec, steps=8):
+    s = _solver(rc, prec)
+    seen = []
+    for _ in range(steps):
+        s.step(1)
+        seen.append(s.diagnostics()["emap"])
+    return float(np.median(seen))
+
+
+@pytest.mark.parametrize("prec", [V.VM_FP32_MIXED, V.VM_FP64], ids=["fp32", "fp64"])
+def test_batch_with_emap_remap_solves_matches_individual_solves(prec):
+    # host-cycle solves (one shared remap phase) and E_map solves, which keep
+    # their cycles on the device and join at other positions in them
+    host = [I.batch_member(i).with_(n_s=10) for i in range(3)]
+    emap = [I.batch_member(i).with_(n_s=6) for i in range(3, 7)]
+    thr = [_median_emap(rc, prec) for rc in emap]
+    pre = [0, 2, 5, 1]                  # steps each E_map solve takes before joining
+    alone = [_solver(rc, prec) for rc in host] + [_emap_solver(rc, prec, t) for rc, t in zip(emap, thr)]
+    for k, s in enumerate(alone):
+        s.step(24 + (pre[k - 3] if k >= 3 else 0))
+    batched = [_solver(rc, prec) for rc in host] + [_emap_solver(rc, prec, t) for rc, t in zip(emap, thr)]
+    for k, p in enumerate(pre):
+        batched[3 + k].step(p)
+    b = V.Batch(batched)
+    b.step(24)
+    forced = 0
+    for s1, s2 in zip(alone, batched):
+        _same(s1, s2)
+        d1, d2 = s1.diagnostics(), s2.diagnostics()
+        assert (d1["cycle"], d1["emap_remaps"], d1["step"]) == (d2["cycle"], d2["emap_remaps"], d2["step"])
+        forced += d2["emap_remaps"]
+    assert forced > 0                   # some E_map remaps happened inside the batch
+    b.close()
+
+
+def _served(reqs, budget=8 << 30, max_active=8, tick=3, emap_remap=0.0):
+    srv = V.NativeServer(budget, max_active=max_active, steps_per_tick=tick, emap_remap=emap_remap)
     rep = run_open_loop(srv, reqs, ic_fn=I.initial_f, keep_results=True)
     return srv, rep
 
@@ -130,6 +173,30 @@ def test_served_result_is_the_same_alone_in_the_mix_and_stepped_directly():
     st = srv.stats()
     assert st["group_steps"] < sum(r.steps for r in mix)   # steps of different requests shared launches
     assert st["used_bytes"] == 0 and st["active"] == 0
+
+
+def test_served_emap_remap_request_matches_vm_step():
+    # requests that remap on E_map keep their cycles on the device inside
+    # the serving loop's group steps
+    mk = lambda i, nx, nv, steps, t: Request(i, I.HALOS_4096.with_(nx=nx, nv=nv, s=8, n_s=7, seed=300 + i),  # noqa: E731
+                                              steps, t)
+    mix = [mk(i, 256 + 32 * i, 448 - 32 * i, 20 + 5 * i, 0.003 * i) for i in range(5)]
+    thr = _median_emap(mix[0].config, V.VM_FP32_MIXED)
+    srv, rep = _served(mix, max_active=3, emap_remap=thr)
+    assert rep["requests"] == 5 and rep["failed"] == 0
+    forced = 0
+    for r in mix:
+        cfg = V.Config.from_run(r.config, V.VM_FP32_MIXED)
+        cfg.emap_remap = thr
+        s = V.Solver(cfg)
+        s.set_f(I.initial_f(r.config))
+        s.step(r.steps)
+        direct = s.density_force()
+        forced += s.diagnostics()["emap_remaps"]
+        for k in direct:
+            np.testing.assert_array_equal(direct[k], r.result[k])
+    assert forced > 0
+    srv.close()
 
 
 def test_server_budget_bounds_the_resident_set_and_refuses_what_never_fits():

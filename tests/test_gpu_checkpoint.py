@@ -49,6 +49,36 @@ def test_resume_is_bit_exact_across_a_remap(tmp_path, prec):
     assert np.array_equal(a.read_map(), b.read_map())
 
 
+def test_resume_keeps_a_device_kept_cycle(tmp_path):
+    # emap_remap > 0: the cycle and the forced-remap count live on the
+    # device; a checkpoint carries them, and the resumed solve decides its
+    # remaps (cycle end or E_map) as the saved one does
+    rc = I.HALOS_4096.with_(nx=128, nv=128, s=4, n_s=5)
+    f0 = I.initial_f(rc)
+
+    def mk():
+        cfg = V.Config.from_run(rc, PREC["fp32"])
+        cfg.emap_remap = 1e-3           # small: some steps remap on E_map
+        return V.Solver(cfg)
+
+    a = mk()
+    a.set_f(f0)
+    a.step(7)
+    path = tmp_path / "state.vlm"
+    a.save(path)
+    da = a.diagnostics()
+    a.step(9)
+    b = mk()
+    b.load(path)
+    db = b.diagnostics()
+    assert (db["cycle"], db["emap_remaps"], db["step"]) == (da["cycle"], da["emap_remaps"], da["step"])
+    b.step(9)
+    assert a.diagnostics()["emap_remaps"] == b.diagnostics()["emap_remaps"]
+    assert a.diagnostics()["cycle"] == b.diagnostics()["cycle"]
+    assert np.array_equal(a.elements(), b.elements())
+    assert np.array_equal(a.read_f(), b.read_f())
+
+
 def test_load_refuses_another_run_and_bad_files(tmp_path):
     rc = I.HALOS_4096.with_(nx=128, nv=128, s=4, n_s=4)
     a = solver(rc, "fp64")

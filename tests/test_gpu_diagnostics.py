@@ -107,15 +107,55 @@ def test_emap_remap_threshold(prec):
     assert np.array_equal(auto.elements(), hand.elements())
 
 
-def test_batch_refuses_emap_remap():
-    rc = I.HALOS_4096.with_(nx=64, nv=64, s=4, n_s=4)
-    cfg = V.Config.from_run(rc, V.VM_FP32_MIXED)
-    cfg.emap_remap = 0.5
-    s = V.Solver(cfg)
-    s.set_f(I.initial_f(rc))
-    with pytest.raises(V.VlametError) as e:
-        V.Batch([s], nstreams=1)
-    assert e.value.status == 1
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_emap_remap_with_a_short_cycle(prec):
+    # the device's decision interleaves cycle-end remaps (every n_s = 3 steps)
+    # and E_map remaps (which restart the cycle) as the host rule does: after
+    # each step the cycle advances; a complete cycle remaps; otherwise E_map
+    # above thr remaps (counted)
+    rc = I.HALOS_4096.with_(nx=128, nv=128, s=4, n_s=3)
+    f0 = I.initial_f(rc)
+
+    def solver(thr, n_s):
+        cfg = V.Config.from_run(rc, PREC[prec])
+        cfg.emap_remap = thr
+        cfg.n_s = n_s
+        s = V.Solver(cfg)
+        s.set_f(f0)
+        return s
+
+    plain = solver(0.0, 1000)
+    seen = []
+    for _ in range(10):
+        plain.step(1)
+        seen.append(plain.diagnostics()["emap"])
+    # a low threshold (below the second step's value: E_map decides; the
+    # first step's value can be exactly 0) and the median (the cycle decides
+    # more often); both strictly positive, so that the criterion is on
+    forced_all = cycled_all = 0
+    low = max(float(np.sqrt(seen[0] * seen[1])), 0.5 * seen[1])
+    for thr in (low, float(np.median(seen))):
+        assert thr > 0.0
+        auto, hand = solver(thr, 3), solver(0.0, 1000)
+        cyc = forced = 0
+        for _ in range(14):
+            auto.step(1)
+            hand.step(1)
+            cyc += 1
+            if cyc >= 3:
+                hand.remap()
+                cyc = 0
+                cycled_all += 1
+            elif hand.diagnostics()["emap"] > thr:
+                hand.remap()
+                cyc = 0
+                forced += 1
+            d = auto.diagnostics()
+            assert d["cycle"] == cyc and d["emap_remaps"] == forced
+        forced_all += forced
+        assert np.array_equal(auto.read_f(), hand.read_f())
+        assert np.array_equal(auto.elements(), hand.elements())
+    assert forced_all > 0 and cycled_all > 0
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
