@@ -699,9 +699,10 @@ def run_batch_classes(args):
 def serve_sample(args) -> dict:
     """A reduced serving run for the headline line, on the library's serving
     loop (vm_server_*): 24 seeded halo requests (sides 256-1024, multiples of
-    32; 100-400 steps; FP32-mixed; a 150 GB budget, 32 slots), all at t = 0
-    for the saturated throughput, then open-loop Poisson arrivals at 0.5 and
-    0.9 of it; p50/p99 latency from arrival to the poll that returns the
+    32; 100-400 steps; FP32-mixed; a 150 GB budget, 32 slots; every request
+    also remaps when its map's E_map exceeds --emap element spacings), all at
+    t = 0 for the saturated throughput, then open-loop Poisson arrivals at 0.5
+    and 0.9 of it; p50/p99 latency from arrival to the poll that returns the
     result, and aggregate cell-updates/s."""
     import torch
     from paper_1705_03750_gb300 import vlamet as V
@@ -722,7 +723,7 @@ def serve_sample(args) -> dict:
         reqs = poisson_requests(24, rate=rate, **kw)
         for r in reqs:
             ic(r.config)                # initial conditions prepared before the clock starts
-        srv = V.NativeServer(150 << 30, max_active=32, steps_per_tick=args.tick)
+        srv = V.NativeServer(150 << 30, max_active=32, steps_per_tick=args.tick, emap_remap=args.emap)
         rep = run_open_loop(srv, reqs, ic_fn=ic)
         torch.cuda.synchronize()
         srv.close()
@@ -731,7 +732,7 @@ def serve_sample(args) -> dict:
         return {k: rep[k] for k in keep}
     sat = one(0.0)
     rate = sat["requests"] / sat["wall_s"]
-    out = {"workload": "serve-halos-256..1024 x24, 100-400 steps (vm_server_*)",
+    out = {"workload": "serve-halos-256..1024 x24, 100-400 steps (vm_server_*)", "emap_remap": args.emap,
            "saturation": {**sat, "requests_per_s": rate}, "rates": []}
     for frac in (0.5, 0.9):
         out["rates"].append({"fraction_of_saturation": frac, "rate_per_s": frac * rate, **one(frac * rate)})
@@ -762,7 +763,7 @@ def run_serve(args):
     def one(reqs):
         for r in reqs:
             ic(r.config)                # initial conditions prepared before the clock starts
-        srv = V.NativeServer(budget, max_active=args.max_active, steps_per_tick=args.tick)
+        srv = V.NativeServer(budget, max_active=args.max_active, steps_per_tick=args.tick, emap_remap=args.emap)
         rep = run_open_loop(srv, reqs, ic_fn=ic)
         torch.cuda.synchronize()
         srv.close()
@@ -773,6 +774,7 @@ def run_serve(args):
     print(json.dumps({"partial_saturation": sat}), file=sys.stderr, flush=True)
     sat_rate = sat["requests"] / sat["wall_s"]
     out = {"workload": "serve-halos-256..2048 (vm_server_*)", "requests": args.requests, "budget_gb": args.budget_gb,
+           "emap_remap": args.emap,
            "saturation": {**sat, "requests_per_s": sat_rate}, "rates": []}
     for frac in (0.25, 0.5, 0.75, 0.9, 1.1):
         reqs = poisson_requests(args.requests, rate=frac * sat_rate, seed=args.seed, make_config=make,
@@ -810,6 +812,9 @@ def main():
     ap.add_argument("--max-active", type=int, default=32)
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--emap", type=float, default=0.5,
+                    help="serving runs: each request also remaps when its map's E_map exceeds this many "
+                         "element spacings (0: every n_s steps only)")
     ap.add_argument("--spin", type=float, default=2.0, help="seconds of untimed steps before the warm-up")
     ap.add_argument("--clock-log", default=None, help="path prefix for the raw clock samples (CSV) of each timed region")
     args = ap.parse_args()

@@ -319,7 +319,7 @@ vm_status read_real(vm_solver* s, const void* src, void* out, int32_t dtype, int
 const char* const kKernelNames[vm::KID_N] = {
     "drift_taylor", "taylor", "kick_drift", "reset_elements", "scan_force", "diagnostics",
     "map_begin", "claim_small", "claim_large", "find_holes", "holes", "resolve", "read_map",
-    "reconstruct", "remap_resample", "convert", "spline_rows", "spline_cols", "claim_pair"};
+    "reconstruct", "remap_resample", "convert", "spline_rows", "spline_cols", "claim_pair", "emap_gate"};
 
 }  // namespace
 

@@ -93,6 +93,7 @@ struct DevState {
   long long emap_remaps;
   int32_t cyc;
   int32_t gate;
+  int32_t emap_hit;  // the current map's E_map exceeds the threshold (set by the test, cleared at map start)
 };
 
 // Owner slots of the influence map: (epoch << 24) | element index.  A slot
@@ -148,7 +149,7 @@ enum KernelId {
   KID_DRIFT = 0, KID_TAYLOR, KID_KICK_DRIFT, KID_RESET, KID_SCAN_FORCE, KID_DIAG,
   KID_MAP_CLEAR, KID_CLAIM_SMALL, KID_CLAIM_LARGE, KID_FINALIZE, KID_HOLES,
   KID_RESOLVE, KID_READ_MAP,
-  KID_RECON, KID_REMAP, KID_CONVERT, KID_SPLINE_ROWS, KID_SPLINE_COLS, KID_CLAIM_PAIR, KID_N
+  KID_RECON, KID_REMAP, KID_CONVERT, KID_SPLINE_ROWS, KID_SPLINE_COLS, KID_CLAIM_PAIR, KID_EMAP, KID_N
 };
 constexpr int PROF_CAP = 1024;
 

@@ -263,6 +263,7 @@ __device__ __forceinline__ void map_begin_body(DevState* ds) {
     ds->nseed = 0;
     ds->n_pair_esc = 0;
     ds->emap2_bits = 0ull;  // E_map describes the current map only
+    ds->emap_hit = 0;
   }
 }
 
@@ -1843,19 +1844,135 @@ __global__ void k_emap(Grid g, const uint32_t* __restrict__ slot0, const double*
   emap_body(g, slot0, tay, ds, blockIdx.x, gridDim.x);
 }
 
+// Whether the current map's E_map exceeds thr, without computing it: the
+// same terms as emap_body, each settled from the FP32 records where their
+// error bounds leave a margin (the bounds of the percolation's FP32 test on
+// q, plus the roundings of the two FP32 differences), and from the exact
+// FP64 terms at the sites where they do not (an alpha range that the bound
+// leaves open, or a term within the margin of thr).  The outcome equals
+// sqrt(max exact term) > thr.  Sets ds->emap_hit; blocks stop once it is set.
+// Nothing to do when the step completes the remap cycle (the cycle decides).
+constexpr float kRelE = 4.0e-6f;     // margin on thr^2 (FP32 squares and sums; thr^2 to FP32)
+constexpr float kRndE = 2.4e-7f;     // two FP32 roundings of a difference of O(1) terms, doubled
+
+// q of the FP32 record F at grid site (i, j) and its bounds (|q - xi| <= e);
+// p from the record's integer and fraction split of the index position
+// (FP32 and integer arithmetic only, as the reconstruction forms it).
+__device__ __forceinline__ QF q_at_site(const float* __restrict__ F, int i, int j, float inv_s, float& ex,
+                                        float& ev) {
+  float f[TF_MW];  // words 0-15: the map's part of the record, 128-byte aligned
+#pragma unroll
+  for (int c = 0; c < TF_MW / 4; c++) {
+    const float4 w = __ldg(reinterpret_cast<const float4*>(F) + c);
+    f[4 * c] = w.x;
+    f[4 * c + 1] = w.y;
+    f[4 * c + 2] = w.z;
+    f[4 * c + 3] = w.w;
+  }
+  static_assert(TF_UF < TF_MW && TF_WF < TF_MW && TF_UI % 2 == 0 && TF_WI == TF_UI + 1, "index split words");
+  const int2 ui = __ldg(reinterpret_cast<const int2*>(F + TF_UI));  // UI, WI (8-byte aligned)
+  const float px = ((float)(i - ui.x) - f[TF_UF]) * inv_s;
+  const float pv = ((float)(j - ui.y) - f[TF_WF]) * inv_s;
+  const QF r = qeval(f, px, pv);
+  ex = kRelQ * r.ax + kAbs * (1.f + r.ax);
+  ev = kRelQ * r.av + kAbs * (1.f + r.av);
+  return r;
+}
+
+// The exact terms of one site (as emap_body): true when one of them exceeds thr.
+__device__ __noinline__ bool emap_site_exceeds(const Grid& g, const double* __restrict__ tay, int m, long long i,
+                                               long long j, double thr) {
+  const double Px = site_x(g, i), Pv = site_v(g, j);
+  double xi, ze;
+  dist2_exact(tay + (size_t)m * TY_N, g, Px, Pv, xi, ze);
+  int a0, a1, b0, b1;
+  alpha_range(xi, g.alpha, a0, a1);
+  alpha_range(ze, g.alpha, b0, b1);
+  const int k = m / g.Lv, l = m - k * g.Lv;
+  for (int a = a0; a <= a1; a++)
+    for (int b = b0; b <= b1; b++) {
+      if (a == 0 && b == 0) continue;
+      const int kk = k + a, ll = l + b;
+      if (!elem_exists(g, kk, ll)) continue;
+      double xn, zn;
+      dist2_exact(tay + (size_t)(kk * g.Lv + ll) * TY_N, g, Px, Pv, xn, zn);
+      const double mx = dsub(dadd((double)a, xn), xi), mv = dsub(dadd((double)b, zn), ze);
+      if (sqrt(dadd(dmul(mx, mx), dmul(mv, mv))) > thr) return true;
+    }
+  return false;
+}
+
+__device__ __forceinline__ void emap_test_body(const Grid& g, const uint32_t* __restrict__ slot0,
+                                               const double* __restrict__ tay, const float* __restrict__ tayf,
+                                               DevState* ds, double thr, int n_s, float alo, float ahi, int vb,
+                                               int vg) {
+  if (__ldcg(&ds->cyc) + 1 >= n_s) return;
+  const uint32_t epoch = *(volatile uint32_t*)&ds->epoch;
+  const float T2 = (float)(thr * thr);
+  const float t_hi = T2 * (1.f + kRelE), t_lo = T2 * (1.f - kRelE);
+  const float inv_s = 1.0f / (float)g.s;
+  // rows by virtual block, sites of a row by thread (coalesced owner reads)
+  for (int i = vb; i < g.nx; i += vg) {
+    if (*(volatile int32_t*)&ds->emap_hit) return;
+    const uint32_t* row = slot0 + (size_t)i * g.nv;
+    for (int j = threadIdx.x; j < g.nv; j += blockDim.x) {
+      const uint32_t t = row[j];
+      if ((t >> 24) != epoch) continue;
+      const int m = (int)(t & SLOT_MASK);
+      if (m >= g.ne) continue;
+      float exm, evm;
+      const QF qm = q_at_site(tayf + (size_t)m * TF_N, i, j, inv_s, exm, evm);
+      const int ra = range_f(qm.qx, exm, alo, ahi), rb = range_f(qm.qv, evm, alo, ahi);
+      bool hit = false, open = (ra == 0 || rb == 0);
+      if (!open && !(ra == 2 && rb == 2)) {
+        // the terms of the settled alpha ranges: (A, 0), (0, B), (A, B) for
+        // the nonzero ones of A, B
+        const int A = ra - 2, B = rb - 2;
+        const int k = m / g.Lv, l = m - k * g.Lv;
+        for (int q = 0; q < 3 && !hit; q++) {
+          const int a = (q == 1) ? 0 : A, b = (q == 0) ? 0 : B;
+          if (a == 0 && b == 0) continue;
+          if (q == 2 && (A == 0 || B == 0)) continue;
+          const int kk = k + a, ll = l + b;
+          if (!elem_exists(g, kk, ll)) continue;
+          float exn, evn;
+          const QF qn = q_at_site(tayf + (size_t)(kk * g.Lv + ll) * TF_N, i, j, inv_s, exn, evn);
+          const float mx = ((float)a + qn.qx) - qm.qx, mv = ((float)b + qn.qv) - qm.qv;
+          const float amx = fabsf(mx), amv = fabsf(mv);
+          const float ux = exn + exm + kRndE * (1.f + fabsf(qn.qx) + amx);
+          const float uv = evn + evm + kRndE * (1.f + fabsf(qn.qv) + amv);
+          const float lx = fmaxf(amx - ux, 0.f), lv = fmaxf(amv - uv, 0.f);
+          const float hx = amx + ux, hv = amv + uv;
+          if (lx * lx + lv * lv > t_hi)
+            hit = true;
+          else if (!(hx * hx + hv * hv < t_lo))
+            open = true;
+        }
+      }
+      if (!hit && open) hit = emap_site_exceeds(g, tay, m, i, j, thr);
+      if (hit) {
+        atomicOr(&ds->emap_hit, 1);
+        return;
+      }
+    }
+  }
+}
+
+__global__ void k_emap_test(Grid g, const uint32_t* __restrict__ slot0, const double* __restrict__ tay,
+                            const float* __restrict__ tayf, DevState* ds, double thr, int n_s, float alo, float ahi) {
+  emap_test_body(g, slot0, tay, tayf, ds, thr, n_s, alo, ahi, blockIdx.x, gridDim.x);
+}
+
 // The remap decision of one solve after a step (Sec. 2.3.2), on the device:
 // the cycle advances, and the remap runs at once when n_s steps are complete
-// or, for thr > 0, when the step's E_map exceeds thr (counted).  The same
-// rule, in the same order, as the host's decision.
+// or, for thr > 0, when the step's E_map exceeds thr (emap_hit, counted).
+// The same rule, in the same order, as the host's decision.
 __device__ __forceinline__ void remap_decide(DevState* ds, int n_s, double thr) {
   const int cyc = ds->cyc + 1;
   bool remap = cyc >= n_s;
-  if (!remap && thr > 0.0) {
-    const double e = sqrt(__longlong_as_double((long long)ds->emap2_bits));
-    if (e > thr) {
-      remap = true;
-      ds->emap_remaps++;
-    }
+  if (!remap && thr > 0.0 && ds->emap_hit) {
+    remap = true;
+    ds->emap_remaps++;
   }
   ds->cyc = remap ? 0 : cyc;
   ds->gate = remap ? 1 : 0;
@@ -2037,10 +2154,11 @@ __global__ void k_find_holes_group(const SolveDesc* __restrict__ D, const int* _
   GROUP_END
 }
 
-__global__ void k_emap_group(const SolveDesc* __restrict__ D, const int* __restrict__ off, int ns, int total) {
+__global__ void k_emap_test_group(const SolveDesc* __restrict__ D, const int* __restrict__ off, int ns,
+                                  int total) {
   GROUP_LOOP_ALL(off, ns, total)
   const int vg = __ldg(off + sv + 1) - __ldg(off + sv);
-  emap_body(gsh, d.map, d.tay, d.ds, vb, vg);
+  emap_test_body(gsh, d.map, d.tay, d.tayf, d.ds, d.emap_thr, d.n_s, d.alo, d.ahi, vb, vg);
   GROUP_END
 }
 
@@ -2072,15 +2190,27 @@ void launch_emap(vm_solver* s) {
   s->launches++;
 }
 
+namespace {
+void alpha_bounds(double alpha, float& lo, float& hi);
+}  // namespace
+
 void launch_remap_gate(vm_solver* s) {
-  launch_emap(s);
+  const int ps = prof_begin(s, KID_EMAP);
+  float alo, ahi;
+  alpha_bounds(s->g.alpha, alo, ahi);
+  unsigned nb = (unsigned)((s->n + 255) / 256);
+  if (nb > 152 * 8) nb = 152 * 8;
+  k_emap_test<<<nb, 256, 0, s->stream>>>(s->g, s->map, s->tay, s->tayf, s->ds, s->cfg.emap_remap, s->cfg.n_s, alo,
+                                         ahi);
   k_remap_gate<<<1, 32, 0, s->stream>>>(s->ds, s->cfg.n_s, s->cfg.emap_remap);
+  prof_end(s, ps);
   s->launches++;
 }
 
 void group_remap_gate(const GroupPlan& G) {
   if (G.tot_sites > 0)
-    k_emap_group<<<group_grid(G, GP_EMAP, G.tot_sites), 256, 0, G.stream>>>(G.D, G.off_sites, G.ns, G.tot_sites);
+    k_emap_test_group<<<group_grid(G, GP_EMAP, G.tot_sites), 256, 0, G.stream>>>(G.D, G.off_sites, G.ns,
+                                                                                  G.tot_sites);
   k_remap_gate_group<<<(unsigned)((G.ns + 255) / 256), 256, 0, G.stream>>>(G.D, G.ns);
 }
 
