@@ -279,7 +279,8 @@ def recon_tiles_ab(V, rc, f0_dev, args, row_stats) -> dict:
     """The FP32-mixed step with the reconstruction in tiles staged by bulk
     copies (recon_mode 1) over the same steps, beside the one-block-per-row
     kernel of the headline: step time and the reconstruction's launch time
-    (events around each launch, second pass as for the headline)."""
+    (events around each launch, on a second solve over the same step
+    indices, as for the headline)."""
     import torch
     cfg = V.Config.from_run(rc, V.VM_FP32_MIXED)
     cfg.recon_mode = 1
@@ -293,6 +294,10 @@ def recon_tiles_ab(V, rc, f0_dev, args, row_stats) -> dict:
     e1.record(s.stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    del s
+    s = V.Solver(cfg)
+    s.set_f(f0_dev)
+    s.step(args.warmup)
     s.profile(True)
     s.step(args.steps)
     st = s.profile_read()
@@ -392,8 +397,13 @@ def run_native(args, rank: int, world: int, dist):
         s.sync()
         ms = max_ranks(e0.elapsed_time(e1))
         launches = s.launches - launches0
-        # per-kernel device time over the same number of steps (events on the
-        # solver's stream around each launch)
+        # per-kernel device time over the same step indices (a new solve from
+        # f0, the same untimed warm-up; events on the solver's stream around
+        # each launch)
+        del s
+        s = V.Solver(V.Config.from_run(rc, prec))
+        s.set_f(f0_dev)
+        s.step(args.warmup)
         s.profile(True)
         s.step(args.steps)
         stats = s.profile_read()
