@@ -162,8 +162,8 @@ def step_bytes_per_update(rc, fp32: bool) -> float:
 # time of the capture: a source changed since makes the figure void (null).
 NCU_TRAFFIC = {
     # kernel: (bytes per launch, source file, sha256 prefix)
-    "claim_pair": (137_610_240, "map.cu", "5a668f4d2ccd1ba7"),
-    "reconstruct": (220_137_472, "recon.cu", "48266d708019da0c"),
+    "claim_pair": (137_233_408, "map.cu", "269f958b85f47eba"),
+    "reconstruct": (219_803_904, "recon.cu", "69a045f1457ded49"),
 }
 
 # Warp instructions per launch (smsp__inst_executed.sum) from the same
@@ -171,8 +171,8 @@ NCU_TRAFFIC = {
 # their issue roofline is these instructions over the launch time against
 # one warp instruction per scheduler per clock (4 schedulers x 152 SMs).
 NCU_INSTR = {
-    "claim_pair": (375_841_157, "map.cu", "5a668f4d2ccd1ba7"),
-    "reconstruct": (126_116_341, "recon.cu", "48266d708019da0c"),
+    "claim_pair": (377_299_942, "map.cu", "269f958b85f47eba"),
+    "reconstruct": (126_116_341, "recon.cu", "69a045f1457ded49"),
 }
 SCHEDULERS = 4 * 152
 
