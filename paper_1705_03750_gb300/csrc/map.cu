@@ -408,12 +408,18 @@ __device__ __noinline__ bool pass_exact_open(const Grid& g, const double (*T9)[T
 
 // Test of one site in the large windows: their band sites far from the
 // element leave comparisons open far more often than the small windows'.
+// The exact test of site (i, j) after the FP32 test left it open with
+// result r (-1: every neighbour of the ranges; -2 - mask: those in mask).
+__device__ __forceinline__ bool exact_open(const Grid& g, const Elem9& E, int r, long long i, long long j) {
+  if (r == -1) return pass_exact(g, E.T9, E.ex9, site_x(g, i), site_v(g, j));
+  return pass_exact_open(g, E.T9, -2 - r, site_x(g, i), site_v(g, j));
+}
+
 __device__ __forceinline__ bool test_site(const Grid& g, const Elem9& E, const Ctx9& c, long long i0, long long j0,
                                           long long i, long long j) {
   const int r = pass_f32<true>(c, (float)(int)(i - i0), (float)(int)(j - j0));
   if (r >= 0) return r == 1;
-  if (r == -1) return pass_exact(g, E.T9, E.ex9, site_x(g, i), site_v(g, j));
-  return pass_exact_open(g, E.T9, -2 - r, site_x(g, i), site_v(g, j));
+  return exact_open(g, E, r, i, j);
 }
 
 // ---------------------------------------------------------------------------
@@ -768,13 +774,14 @@ __device__ __forceinline__ void claim_element(const Grid& g, const double* __res
   if (er || ec) {
     int seed = -1;
     if (lane == 0) {
-      // Outer elements (a neighbour missing) claim the long boundary bands,
-      // the longest jobs of the next tier: they are listed from the front and
-      // taken first, the others from the end of the list.
+      // Outer elements (a neighbour missing) that left along v claim the
+      // long boundary bands, the longest jobs of the next tier: they are
+      // listed from the front and taken first, the others from the end.
       const int sides = (er ? 1 : 0) | (ec ? 2 : 0);
       bool outer = false;
       for (int q = 0; q < 9; q++) outer |= !sh.ex9[q];
-      const int slot = outer ? atomicAdd(&S.ds->noverflow, 1) : g.ne - 1 - atomicAdd(&S.ds->noverflow_back, 1);
+      const int slot = (outer && sides == 2) ? atomicAdd(&S.ds->noverflow, 1)
+                                             : g.ne - 1 - atomicAdd(&S.ds->noverflow_back, 1);
       seed = atomicAdd(&S.ds->nseed, 1);
       if (seed >= S.seed_cap) seed = -1;
       // attempt 0; bits 8 and up: the masks' record + 1 (0: none)
@@ -1105,7 +1112,7 @@ __device__ __forceinline__ void claim_pair_body(const Grid& g, const double* __r
   const bool esc = live && (er || ec);
   // An outer element (a neighbour missing) that escapes claims a boundary
   // band, which tier 1's window cannot hold either: it goes straight to
-  // tier 2 (listed from the front), with this window's masks as the seed of
+  // tier 2 (the v bands listed from the front), with this window's masks as the seed of
   // tier 2's first window (placed in a 32 x 64 record as tier 1's would
   // be).  The others start again in tier 1.
   bool outer = false;
@@ -1115,7 +1122,10 @@ __device__ __forceinline__ void claim_pair_body(const Grid& g, const double* __r
     seed = atomicAdd(&S.ds->nseed, 1);
     if (seed >= S.seed_cap) seed = -1;
     const int sides = (er ? 1 : 0) | (ec ? 2 : 0);
-    ovf_list[atomicAdd(&S.ds->noverflow, 1)] = make_int2(m, ((seed + 1) << 8) | (sides << 4));
+    // the v bands (the longest jobs) from the front, taken first; the others
+    // from the end
+    const int slot = (sides == 2) ? atomicAdd(&S.ds->noverflow, 1) : g.ne - 1 - atomicAdd(&S.ds->noverflow_back, 1);
+    ovf_list[slot] = make_int2(m, ((seed + 1) << 8) | (sides << 4));
   }
   seed = __shfl_sync(FULL, seed, 0, 16);
   if (esc && outer) {
@@ -1178,6 +1188,7 @@ constexpr int BLOCKS_PER_SM = 3;
 constexpr int BAND_R = 128, BAND_W = 20;  // band window: 128 rows across, up to 1280 sites along
 constexpr int FAT_R = 160, FAT_W = 12;    // 160 x 768 sites
 constexpr int LIST_CAP = 512;
+constexpr int UNS_CAP = 512;  // sites per round whose FP32 test is left open, tested exactly together
 constexpr int AHEAD = 3;      // rows tested ahead of the component per round
 constexpr size_t SMEM_MAX = 227 * 1024;   // opt-in limit per block
 constexpr size_t SMEM_SM = 228 * 1024;    // shared memory per SM
@@ -1192,6 +1203,9 @@ struct BigHeader {
   int wtot[BT / 32];           // per-warp totals of a block scan
   short plo[FAT_R > BAND_R ? FAT_R : BAND_R];  // per window row: columns of the predicted band
   short phi[FAT_R > BAND_R ? FAT_R : BAND_R];
+  int nuns;                    // this round's sites left open by the FP32 test
+  int uns_site[UNS_CAP];       // their window bit (word * 64 + bit)
+  int uns_res[UNS_CAP];        // and the FP32 test's open result (-1, or -2 - neighbour mask)
 };
 
 // Block-wide inclusive sums out[e] = cnt(0) + ... + cnt(e) for e < n (each
@@ -1221,6 +1235,25 @@ __device__ __forceinline__ int block_incl(int n, Cnt cnt, int* out, int* wtot) {
   const int total = wtot[BT / 32 - 1];
   __syncthreads();
   return total;
+}
+
+// Entry holding item e, at or after entry s0 (which holds an earlier item):
+// a few steps forward, doubling, then a binary search of the last stretch.
+__device__ __forceinline__ int find_entry_from(const int* incl, int s0, int n, int e) {
+  int lo = s0, step = 1;
+  while (lo + step < n && incl[lo + step - 1] <= e) {
+    lo += step;
+    step <<= 1;
+  }
+  int hi = min(lo + step, n) - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (incl[mid] > e)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  return lo;
 }
 
 // Entry holding item e of a compacted list (first s with incl[s] > e; e is
@@ -1506,7 +1539,10 @@ __device__ __forceinline__ void claim_big_body(const Grid& g, const double* __re
     bool escaped = false;
     if (H.ok) {
       for (int it = 0; it < NW * 64; it++) {
-        if (tid == 0) H.nlist = 0;
+        if (tid == 0) {
+          H.nlist = 0;
+          H.nuns = 0;
+        }
         const int ra0 = max(H.rmin - AHEAD, 0), rb0 = min(H.rmax + AHEAD, W.R - 1);
         const int wa0 = max(H.wmin - 1, 0), wb0 = min(H.wmax + 1, W.W - 1);
         __syncthreads();
@@ -1540,15 +1576,37 @@ __device__ __forceinline__ void claim_big_body(const Grid& g, const double* __re
         // e mod BT whatever word holds it
         const int nl = min(H.nlist, LIST_CAP);
         const int ntest = block_incl(nl, [&](int s) { return __popcll(H.lmask[s]); }, H.lcnt, H.wtot);
+        int s = 0;  // a thread's entries only move forward: search on from the last one
         for (int e = tid; e < ntest; e += BT) {
-          const int s = find_entry(H.lcnt, nl, e);
+          s = find_entry_from(H.lcnt, s, nl, e);
           const unsigned long long lm = H.lmask[s];
           const int b = nth_bit(lm, e - (H.lcnt[s] - __popcll(lm)));
           const int q = H.list[s];
           const int r = q / W.W, w = q - r * W.W;
           long long i, j;
           site_of(W, r, 64 * w + b, i, j);
-          if (test_site(g, H.E, c, i0, j0, i, j)) atomicOr(&pass[q], 1ull << b);
+          const int res = pass_f32<true>(c, (float)(int)(i - i0), (float)(int)(j - j0));
+          if (res == 1) {
+            atomicOr(&pass[q], 1ull << b);
+          } else if (res < 0) {
+            // left open: tested exactly below with the others, every lane busy
+            // (an FP64 instruction takes the SM's FP64 unit for a whole warp)
+            const int u = atomicAdd(&H.nuns, 1);
+            if (u < UNS_CAP) {
+              H.uns_site[u] = q * 64 + b;
+              H.uns_res[u] = res;
+            } else if (exact_open(g, H.E, res, i, j)) {
+              atomicOr(&pass[q], 1ull << b);
+            }
+          }
+        }
+        __syncthreads();
+        for (int u = tid; u < min(H.nuns, UNS_CAP); u += BT) {
+          const int q = H.uns_site[u] >> 6, b = H.uns_site[u] & 63;
+          const int r = q / W.W, w = q - r * W.W;
+          long long i, j;
+          site_of(W, r, 64 * w + b, i, j);
+          if (exact_open(g, H.E, H.uns_res[u], i, j)) atomicOr(&pass[q], 1ull << b);
         }
         __syncthreads();
         // C: close the component through the passing sites (runs inside a
@@ -1608,6 +1666,7 @@ __device__ __forceinline__ void claim_big_body(const Grid& g, const double* __re
         int* ccnt = reinterpret_cast<int*>(eval);  // nbox <= NW ints fit in NW words
         auto word_of = [&](int e) { return (H.rmin + e / bw) * W.W + H.wmin + e % bw; };
         const int nsite = block_incl(nbox, [&](int e) { return __popcll(comp[word_of(e)]); }, ccnt, H.wtot);
+        int xs = 0;  // (entries only move forward, as for the tests)
         for (int e0 = 0; e0 < nsite; e0 += 8 * BT) {
           size_t pos[8];
 #pragma unroll
@@ -1615,7 +1674,7 @@ __device__ __forceinline__ void claim_big_body(const Grid& g, const double* __re
             const int e = e0 + u * BT + tid;
             pos[u] = ~(size_t)0;
             if (e < nsite) {
-              const int x = find_entry(ccnt, nbox, e), q = word_of(x);
+              const int x = xs = find_entry_from(ccnt, xs, nbox, e), q = word_of(x);
               const unsigned long long cw = comp[q];
               const int b = nth_bit(cw, e - (ccnt[x] - __popcll(cw)));
               long long i, j;
