@@ -56,6 +56,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <climits>
 
 #include "common.cuh"
 
@@ -918,17 +919,23 @@ __device__ __forceinline__ void claim_pair_body(const Grid& g, const double* __r
   bool live = m < g.ne;
   const int k = live ? m / g.Lv : 0, l = live ? m - k * g.Lv : 0;
   live = live && elem_exists(g, k, l);  // elements off the computing domain claim nothing
-  // set-up: the 3x3 neighbourhood's FP64 index positions (half-lanes 0-8)
-  // and FP32 records, every load issued before any is used
-  double uq = 0.0, wpos = 0.0;
+  // set-up: the 3x3 neighbourhood's index positions as integer part and
+  // FP32 fraction (half-lanes 0-8; integer INT_MIN/2 where not finite) and
+  // FP32 records, every load issued before any is used
+  int uiq = 0, wiq = 0;
+  float ufq = 0.f, wfq = 0.f;
   bool exq = false;
   if (live && hl < 9) {
     const int kk = k + hl / 3 - 1, ll = l + hl % 3 - 1;
     exq = elem_exists(g, kk, ll);
     if (exq) {
-      const double2 uw = __ldg(reinterpret_cast<const double2*>(tayf + (size_t)(kk * g.Lv + ll) * TF_N + TF_UD));
-      uq = uw.x;
-      wpos = uw.y;
+      const float* R = tayf + (size_t)(kk * g.Lv + ll) * TF_N;
+      const int2 iw = __ldg(reinterpret_cast<const int2*>(R + TF_UI));
+      const float2 fw = __ldg(reinterpret_cast<const float2*>(R + TF_UF));
+      uiq = iw.x;
+      wiq = iw.y;
+      ufq = fw.x;
+      wfq = fw.y;
     }
   }
   {
@@ -956,14 +963,30 @@ __device__ __forceinline__ void claim_pair_body(const Grid& g, const double* __r
       }
     }
   }
-  const double us = __shfl_sync(FULL, uq, 4, 16), ws = __shfl_sync(FULL, wpos, 4, 16);
-  live = live && us > -1e9 && us < 1e9 && ws > -1e9 && ws < 1e9;
-  const long long i0 = live ? (long long)floor(dadd(us, 0.5)) : 0, j0 = live ? (long long)floor(dadd(ws, 0.5)) : 0;
+  // the start site floor(u + 1/2) (u = ui + uf exactly in FP64): ui + 1
+  // when the fraction is at least 1/2, settled by its FP32 rounding unless
+  // that is 1/2 itself (then the FP64 index position decides); the offsets
+  // i0 - u of the nine positions in FP32 from the integer difference and
+  // the fraction (the same rounding as the FP64 difference rounded to FP32,
+  // within the FP32 tests' bound)
+  const int uis = __shfl_sync(FULL, uiq, 4, 16), wis = __shfl_sync(FULL, wiq, 4, 16);
+  const float ufs = __shfl_sync(FULL, ufq, 4, 16), wfs = __shfl_sync(FULL, wfq, 4, 16);
+  live = live && uis != INT_MIN / 2 && wis != INT_MIN / 2;  // (index position not finite: no element)
+  long long i0 = 0, j0 = 0;
+  if (live) {
+    i0 = (long long)uis + (ufs > 0.5f ? 1 : 0);
+    j0 = (long long)wis + (wfs > 0.5f ? 1 : 0);
+    if (ufs == 0.5f || wfs == 0.5f) {
+      const double2 uw = __ldg(reinterpret_cast<const double2*>(tayf + (size_t)m * TF_N + TF_UD));
+      if (ufs == 0.5f) i0 = (long long)floor(dadd(uw.x, 0.5));
+      if (wfs == 0.5f) j0 = (long long)floor(dadd(uw.y, 0.5));
+    }
+  }
   const int pad = g.pad;
   live = live && !(i0 < -pad || i0 >= g.nx + pad || j0 < -pad || j0 >= g.nv + pad);
   if (live && hl < 9) {
-    sh.offu[hl] = exq ? (float)((double)i0 - uq) : 0.f;
-    sh.offv[hl] = exq ? (float)((double)j0 - wpos) : 0.f;
+    sh.offu[hl] = exq ? (float)((int)i0 - uiq) - ufq : 0.f;
+    sh.offv[hl] = exq ? (float)((int)j0 - wiq) - wfq : 0.f;
   }
   __syncwarp();
   Ctx9 c;
