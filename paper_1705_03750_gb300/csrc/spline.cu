@@ -8,8 +8,9 @@
 // Row systems are contiguous in memory: a warp owns 32 rows and walks them
 // in 32 x 32 tiles staged in shared memory, so global loads and stores stay
 // coalesced while each lane runs the sequential sweep of its own row.  Column
-// systems are strided by nv: one thread per column, so a warp's loads at a
-// given step are 32 consecutive values.
+// systems are strided by nv: a lane per column, so a warp's loads at a given
+// step are 32 consecutive values, and warps split the rows into chunks
+// joined by their carries.
 #include "common.cuh"
 
 namespace vm {
@@ -144,10 +145,6 @@ __device__ __forceinline__ void rows_scan_body(const Grid& g, const R* __restric
   }
 }
 
-// Column systems, one thread per column (a warp: 32 consecutive columns, so
-// every load and store is coalesced).  The sweeps are sequential in the row,
-// the loads are not: the next CK rows are loaded while the current CK are
-// swept (double buffering), so that memory latency overlaps the recurrence.
 template <typename R, typename C>
 __global__ void __launch_bounds__(128) k_rows_scan(Grid g, const R* __restrict__ src, R* __restrict__ dst,
                                                    const C* __restrict__ th) {
@@ -155,64 +152,105 @@ __global__ void __launch_bounds__(128) k_rows_scan(Grid g, const R* __restrict__
   rows_scan_body(g, src, dst, th, blockIdx.x);
 }
 
+// Column systems: a block per 32 consecutive columns (lane = column, so
+// every load and store is coalesced) and CW warps, warp w owning a chunk of
+// consecutive rows.  Both sweeps are affine recurrences in the row,
+//   forward  d_i = (6 f_i - sub_i d_{i-1}) / den_i = a_i d_{i-1} + (6 f_i / den_i),  a_i = -sub_i / den_i,
+//   backward e_i = d_i - c'_i e_{i+1},
+// so each warp first runs its chunk from a zero carry, keeping the chunk's
+// composition (the product of its factors A, and its last value B); warp 0
+// then chains the chunks' carries in order (CW steps per column); and each
+// warp adds to every row the product of the chunk's factors up to that row
+// times the carry that enters the chunk.  The whole column takes about
+// 3 nx / CW dependent steps instead of 2 nx.
+constexpr int CW = 32;  // warps per column block
+
 template <typename R, typename C>
 __device__ __forceinline__ void cols_body(const Grid& g, R* __restrict__ x, const C* __restrict__ th, int vb) {
-  constexpr int CK = 32;
-  const int j = vb * blockDim.x + threadIdx.x;
-  if (j >= g.nv) return;
+  __shared__ R cB[CW][32];  // per chunk and column: the chunk's last value from a zero carry
+  __shared__ R cC[CW][32];  // ... then the carry entering the chunk
+  __shared__ C cA[CW];      // per chunk: the product of its factors (the same for every column)
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int nx = g.nx, nv = g.nv;
+  const int j = vb * 32 + lane;
+  const bool col = j < nv;
   const C* cp = th;
   const C* inv = th + nx;
-  R cur[CK], nxt[CK];
-  // forward
-#pragma unroll
-  for (int u = 0; u < CK; u++) cur[u] = (u < nx) ? x[(size_t)u * nv + j] : R(0);
-  R dprev = R(0);
-  for (int i0 = 0; i0 < nx; i0 += CK) {
-#pragma unroll
-    for (int u = 0; u < CK; u++) {
-      const int i = i0 + CK + u;
-      nxt[u] = (i < nx) ? x[(size_t)i * nv + j] : R(0);
+  const int L = (nx + CW - 1) / CW;
+  const int i0 = min(w * L, nx), i1 = min(i0 + L, nx);  // this warp's rows [i0, i1)
+  R* xc = x + (col ? j : 0);
+  // forward, each chunk from a zero carry
+  {
+    R d = R(0);
+    C A = C(1);
+#pragma unroll 8
+    for (int i = i0; i < i1; i++) {
+      const C sub = (i == 0) ? C(0) : ((i == nx - 1) ? C(2) : C(1));
+      const R f = col ? xc[(size_t)i * nv] : R(0);
+      d = (R(6) * f - (R)sub * d) * (R)inv[i];
+      A *= -sub * inv[i];
+      if (col) xc[(size_t)i * nv] = d;
     }
-#pragma unroll
-    for (int u = 0; u < CK; u++) {
-      const int i = i0 + u;
-      if (i < nx) {
-        const R sub = (i == 0) ? R(0) : ((i == nx - 1) ? R(2) : R(1));
-        const R d = (R(6) * cur[u] - sub * dprev) * (R)inv[i];
-        x[(size_t)i * nv + j] = d;
-        dprev = d;
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < CK; u++) cur[u] = nxt[u];
+    cB[w][lane] = d;
+    if (lane == 0) cA[w] = A;
   }
-  // backward: eta_{nx-1} = d'_{nx-1}, then eta_i = d'_i - c'_i eta_{i+1}
-  R enext = dprev;
-#pragma unroll
-  for (int u = 0; u < CK; u++) cur[u] = (nx - 2 - u >= 0) ? x[(size_t)(nx - 2 - u) * nv + j] : R(0);
-  for (int i1 = nx - 2; i1 >= 0; i1 -= CK) {
-#pragma unroll
-    for (int u = 0; u < CK; u++) {
-      const int i = i1 - CK - u;
-      nxt[u] = (i >= 0) ? x[(size_t)i * nv + j] : R(0);
+  __syncthreads();
+  if (w == 0) {
+    R c = R(0);
+    for (int q = 0; q < CW; q++) {
+      cC[q][lane] = c;
+      c = (R)cA[q] * c + cB[q][lane];
     }
-#pragma unroll
-    for (int u = 0; u < CK; u++) {
-      const int i = i1 - u;
-      if (i >= 0) {
-        const R e = cur[u] - (R)cp[i] * enext;
-        x[(size_t)i * nv + j] = e;
-        enext = e;
-      }
+  }
+  __syncthreads();
+  // forward completed (d_i += P_i carry), then the backward sweep of the
+  // chunk from a zero carry: e_i = d_i - c'_i e_{i+1}, e at i1 taken as 0
+  {
+    const R cin = cC[w][lane];
+    C P = C(1);
+#pragma unroll 8
+    for (int i = i0; i < i1; i++) {
+      const C sub = (i == 0) ? C(0) : ((i == nx - 1) ? C(2) : C(1));
+      P *= -sub * inv[i];
+      if (col) xc[(size_t)i * nv] += (R)P * cin;
     }
-#pragma unroll
-    for (int u = 0; u < CK; u++) cur[u] = nxt[u];
+    R e = R(0);
+    C Q = C(1);
+#pragma unroll 8
+    for (int i = i1 - 1; i >= i0; i--) {
+      const C c = (i == nx - 1) ? C(0) : cp[i];
+      const R d = col ? xc[(size_t)i * nv] : R(0);
+      e = d - (R)c * e;
+      Q *= -c;
+      if (col) xc[(size_t)i * nv] = e;
+    }
+    __syncthreads();  // every warp has read its cC entry
+    cB[w][lane] = e;
+    if (lane == 0) cA[w] = Q;
+  }
+  __syncthreads();
+  if (w == 0) {
+    R c = R(0);
+    for (int q = CW - 1; q >= 0; q--) {
+      cC[q][lane] = c;
+      c = (R)cA[q] * c + cB[q][lane];
+    }
+  }
+  __syncthreads();
+  {
+    const R cin = cC[w][lane];
+    C Q = C(1);
+#pragma unroll 8
+    for (int i = i1 - 1; i >= i0; i--) {
+      const C c = (i == nx - 1) ? C(0) : cp[i];
+      Q *= -c;
+      if (col) xc[(size_t)i * nv] += (R)Q * cin;
+    }
   }
 }
 
 template <typename R, typename C>
-__global__ void __launch_bounds__(32) k_cols(Grid g, R* __restrict__ x, const C* __restrict__ th) {
+__global__ void __launch_bounds__(32 * CW) k_cols(Grid g, R* __restrict__ x, const C* __restrict__ th) {
   if (gate_shut(g)) return;
   cols_body(g, x, th, blockIdx.x);
 }
@@ -230,8 +268,8 @@ __global__ void __launch_bounds__(128) k_rows_group(const SolveDesc* __restrict_
 }
 
 template <typename R>
-__global__ void __launch_bounds__(32) k_cols_group(const SolveDesc* __restrict__ D, const int* __restrict__ off,
-                                                 int ns, int total) {
+__global__ void __launch_bounds__(32 * CW) k_cols_group(const SolveDesc* __restrict__ D, const int* __restrict__ off,
+                                                      int ns, int total) {
   GROUP_LOOP(off, ns, total)
   if constexpr (sizeof(R) == 4)
     cols_body<float, float>(gsh, (float*)d.eta, d.thxf, vb);
@@ -255,9 +293,9 @@ void launch_spline_solve(vm_solver* s, const void* src, void* dst) {
   prof_end(s, ps);
   ps = prof_begin(s, KID_SPLINE_COLS);
   if (s->fp32)
-    k_cols<float, float><<<cb, 32, 0, s->stream>>>(s->g, (float*)dst, s->thomas_xf);
+    k_cols<float, float><<<cb, 32 * CW, 0, s->stream>>>(s->g, (float*)dst, s->thomas_xf);
   else
-    k_cols<double, double><<<cb, 32, 0, s->stream>>>(s->g, (double*)dst, s->thomas_x);
+    k_cols<double, double><<<cb, 32 * CW, 0, s->stream>>>(s->g, (double*)dst, s->thomas_x);
   prof_end(s, ps);
   s->launches += 2;
 }
@@ -265,11 +303,13 @@ void launch_spline_solve(vm_solver* s, const void* src, void* dst) {
 void group_spline(const GroupPlan& G) {
   if (G.fp32) {
     k_rows_group<float><<<group_grid(G, GP_ROWS, G.tot_rows4), 128, 0, G.stream>>>(G.D, G.off_rows4, G.ns, G.tot_rows4);
-    k_cols_group<float><<<group_grid(G, GP_COLS, G.tot_cols), 32, 0, G.stream>>>(G.D, G.off_cols, G.ns, G.tot_cols);
+    k_cols_group<float><<<group_grid(G, GP_COLS, G.tot_cols), 32 * CW, 0, G.stream>>>(G.D, G.off_cols, G.ns,
+                                                                                    G.tot_cols);
   } else {
     k_rows_group<double><<<group_grid(G, GP_ROWS, G.tot_rows4), 128, 0, G.stream>>>(G.D, G.off_rows4, G.ns,
                                                                                   G.tot_rows4);
-    k_cols_group<double><<<group_grid(G, GP_COLS, G.tot_cols), 32, 0, G.stream>>>(G.D, G.off_cols, G.ns, G.tot_cols);
+    k_cols_group<double><<<group_grid(G, GP_COLS, G.tot_cols), 32 * CW, 0, G.stream>>>(G.D, G.off_cols, G.ns,
+                                                                                     G.tot_cols);
   }
 }
 
