@@ -162,7 +162,7 @@ def step_bytes_per_update(rc, fp32: bool) -> float:
 # time of the capture: a source changed since makes the figure void (null).
 NCU_TRAFFIC = {
     # kernel: (bytes per launch, source file, sha256 prefix)
-    "claim_pair": (137_233_408, "map.cu", "269f958b85f47eba"),
+    "claim_pair": (137_008_128, "map.cu", "6003cf0f8e281f04"),
     "reconstruct": (219_803_904, "recon.cu", "69a045f1457ded49"),
 }
 
@@ -171,7 +171,7 @@ NCU_TRAFFIC = {
 # their issue roofline is these instructions over the launch time against
 # one warp instruction per scheduler per clock (4 schedulers x 152 SMs).
 NCU_INSTR = {
-    "claim_pair": (377_299_942, "map.cu", "269f958b85f47eba"),
+    "claim_pair": (373_507_280, "map.cu", "6003cf0f8e281f04"),
     "reconstruct": (126_116_341, "recon.cu", "69a045f1457ded49"),
 }
 SCHEDULERS = 4 * 152
