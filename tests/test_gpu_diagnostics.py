@@ -112,6 +112,43 @@ def test_emap_remap_threshold(prec, pick):
     assert np.array_equal(auto.elements(), hand.elements())
 
 
+def test_emap_remap_decisions_at_full_size():
+    # the device's certified E_map test against the host rule on the 4096^2
+    # halo workload: 30 steps, the threshold the median of a plain run's
+    # values (some steps remap, some do not); decisions, f and elements equal
+    rc = I.HALOS_4096
+    f0 = I.initial_f(rc)
+
+    def solver(thr):
+        cfg = V.Config.from_run(rc, V.VM_FP32_MIXED)
+        cfg.emap_remap = thr
+        cfg.n_s = 1000
+        s = V.Solver(cfg)
+        s.set_f(f0)
+        return s
+
+    plain = solver(0.0)
+    seen = []
+    for _ in range(12):
+        plain.step(1)
+        seen.append(plain.diagnostics()["emap"])
+    plain.close()
+    thr = float(np.median(seen))
+    assert thr > 0.0
+    auto, hand = solver(thr), solver(0.0)
+    forced = 0
+    for _ in range(30):
+        auto.step(1)
+        hand.step(1)
+        if hand.diagnostics()["emap"] > thr:
+            hand.remap()
+            forced += 1
+        assert auto.diagnostics()["emap_remaps"] == forced
+    assert 0 < forced < 30
+    assert np.array_equal(auto.elements(), hand.elements())
+    assert np.array_equal(auto.read_f(), hand.read_f())
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_emap_remap_with_a_short_cycle(prec):
     # the device's decision interleaves cycle-end remaps (every n_s = 3 steps)
