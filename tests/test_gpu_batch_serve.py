@@ -199,6 +199,58 @@ def test_served_emap_remap_request_matches_vm_step():
     srv.close()
 
 
+def test_server_mixes_emap_and_fixed_cycle_requests():
+    # requests with and without the E_map criterion in one serving loop: the
+    # gated remaps of the first and the host-cycle remap subsets of the
+    # second share the steps; each result equals its solve stepped alone
+    mk = lambda i, nx, nv, steps, t: Request(i, I.HALOS_4096.with_(nx=nx, nv=nv, s=8, n_s=5, seed=500 + i),  # noqa: E731
+                                              steps, t)
+    mix = [mk(i, 224 + 32 * i, 416 - 32 * i, 18 + 4 * i, 0.002 * i) for i in range(6)]
+    thr = _median_emap(mix[0].config, V.VM_FP32_MIXED)
+    use = {r.rid: (thr if r.rid % 2 == 0 else 0.0) for r in mix}
+    srv = V.NativeServer(8 << 30, max_active=4, steps_per_tick=3)
+    orig = srv.submit
+    srv.submit = lambda rc, f0, steps: orig(rc, f0, steps, emap_remap=use[int(rc.name[3:])])  # noqa: E731
+    for r in mix:
+        r.config = r.config.with_(name=f"req{r.rid}")
+    rep = run_open_loop(srv, mix, ic_fn=I.initial_f, keep_results=True)
+    assert rep["requests"] == 6 and rep["failed"] == 0
+    forced = 0
+    for r in mix:
+        cfg = V.Config.from_run(r.config, V.VM_FP32_MIXED)
+        cfg.emap_remap = use[r.rid]
+        s = V.Solver(cfg)
+        s.set_f(I.initial_f(r.config))
+        s.step(r.steps)
+        forced += s.diagnostics()["emap_remaps"]
+        direct = s.density_force()
+        for k in direct:
+            np.testing.assert_array_equal(direct[k], r.result[k])
+    assert forced > 0
+    srv.close()
+
+
+def test_batch_autotune_with_emap_solves_changes_no_result():
+    # the tuner's real steps include the gated remaps of the E_map solves
+    host = [I.batch_member(i).with_(n_s=6) for i in range(20, 23)]
+    emap = [I.batch_member(i).with_(n_s=6) for i in range(23, 26)]
+    prec = V.VM_FP32_MIXED
+    thr = [_median_emap(rc, prec) for rc in emap]
+    alone = [_solver(rc, prec) for rc in host] + [_emap_solver(rc, prec, t) for rc, t in zip(emap, thr)]
+    for s in alone:
+        s.step(16)
+    batched = [_solver(rc, prec) for rc in host] + [_emap_solver(rc, prec, t) for rc, t in zip(emap, thr)]
+    b = V.Batch(batched)
+    t = b.autotune(1)
+    assert t["tuned"]
+    done = batched[0].diagnostics()["step"]
+    b.step(16 - done)
+    for s1, s2 in zip(alone, batched):
+        _same(s1, s2)
+        assert s1.diagnostics()["emap_remaps"] == s2.diagnostics()["emap_remaps"]
+    b.close()
+
+
 def test_server_budget_bounds_the_resident_set_and_refuses_what_never_fits():
     rc = I.HALOS_4096.with_(nx=256, nv=256, s=8, n_s=5)
     need = V.workspace_bytes(V.Config.from_run(rc, V.VM_FP32_MIXED))
