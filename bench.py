@@ -54,38 +54,77 @@ def _peaks():
 # ---------------------------------------------------------------------------
 
 class ClockSampler:
+    """nvidia-smi clock and throttle samples every 20 ms, read by a thread
+    that stamps each line with the host clock: started before the warm-up
+    (its start-up takes longer than a short timed region), the summary keeps
+    the samples that arrived while the timed region ran (mark_begin to
+    mark_end, plus one interval of reporting slack)."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 20
 
     def __init__(self, gpu_id: str, path: str | None = None):
         self.gpu_id, self.path, self.proc = gpu_id, path, None
+        self.lines, self.t_begin, self.t_end, self.thread = [], None, None, None
 
-    def __enter__(self):
+    def start(self):
+        import threading
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
-                 "-i", self.gpu_id], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms",
+                 str(self.INTERVAL_MS), "-i", self.gpu_id], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
         except Exception:
             self.proc = None
+            return self
+
+        def read():
+            for line in self.proc.stdout:
+                self.lines.append((time.perf_counter(), line))
+        self.thread = threading.Thread(target=read, daemon=True)
+        self.thread.start()
+        return self
+
+    def mark_begin(self):
+        self.t_begin = time.perf_counter()
+
+    def mark_end(self):
+        self.t_end = time.perf_counter()
+
+    def stop(self):
+        if self.proc is not None:
+            time.sleep(2 * self.INTERVAL_MS / 1e3)  # the samples of the region's last interval
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            if self.thread is not None:
+                self.thread.join(timeout=5)
+        if self.path:
+            with open(self.path, "a") as fh:
+                fh.write("".join(f"{t:.4f},{ln}" for t, ln in self.lines))
+
+    def __enter__(self):
+        self.start()
+        self.mark_begin()
         return self
 
     def __exit__(self, *exc):
-        self.out = ""
-        if self.proc is not None:
-            self.proc.terminate()
-            try:
-                self.out, _ = self.proc.communicate(timeout=5)
-            except Exception:
-                self.proc.kill()
-        if self.path:
-            with open(self.path, "a") as fh:
-                fh.write(self.out)
+        self.mark_end()
+        self.stop()
 
     def summary(self) -> dict:
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in (self.out or "").splitlines():
+        lo = self.t_begin if self.t_begin is not None else float("-inf")
+        hi = (self.t_end if self.t_end is not None else float("inf")) + self.INTERVAL_MS / 1e3
+        inside = [ln for t, ln in self.lines if lo <= t <= hi]
+        if not inside:  # a region shorter than the sampler's first interval: the next sample
+            after = [ln for t, ln in self.lines if t >= lo]
+            inside = after[:1]
+        for line in inside:
             p = [x.strip() for x in line.split(",")]
             if len(p) < 9:
                 continue
@@ -378,6 +417,8 @@ def run_native(args, rank: int, world: int, dist):
     for name, prec in (("fp32", V.VM_FP32_MIXED), ("fp64", V.VM_FP64)):
         if args.precision not in ("both", name):
             continue
+        # clock samples during the timed region (the sampler starts first)
+        clocks = ClockSampler(gpu_id, f"{args.clock_log}_{name}.csv" if args.clock_log else None).start()
         s = V.Solver(V.Config.from_run(rc, prec))
         s.set_f(f0_dev)
         s.step(args.warmup)
@@ -387,12 +428,13 @@ def run_native(args, rank: int, world: int, dist):
         launches0 = s.launches
         barrier()
         torch.cuda.synchronize(dev)
-        clocks = ClockSampler(gpu_id, f"{args.clock_log}_{name}.csv" if args.clock_log else None)
-        with clocks:
-            e0.record(stream)
-            s.step(args.steps)
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
+        clocks.mark_begin()
+        e0.record(stream)
+        s.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        clocks.mark_end()
+        clocks.stop()
         barrier()
         s.sync()
         ms = max_ranks(e0.elapsed_time(e1))
