@@ -1787,8 +1787,9 @@ __device__ __forceinline__ void find_holes_body(const Grid& g, const uint32_t* _
   const size_t n = (size_t)g.nx * g.nv, n4 = n / 4;
   const size_t t0 = vb * (size_t)blockDim.x + threadIdx.x, stride = (size_t)vg * blockDim.x;
   const uint4* s4 = reinterpret_cast<const uint4*>(slot0);
+#pragma unroll 4
   for (size_t q = t0; q < n4; q += stride) {
-    const uint4 t = s4[q];
+    const uint4 t = __ldcs(s4 + q);  // read once: streamed past the caches
     const uint32_t e[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
     for (int u = 0; u < 4; u++)
