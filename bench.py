@@ -201,7 +201,7 @@ def step_bytes_per_update(rc, fp32: bool) -> float:
 # time of the capture: a source changed since makes the figure void (null).
 NCU_TRAFFIC = {
     # kernel: (bytes per launch, source file, sha256 prefix)
-    "claim_pair": (137_008_128, "map.cu", "6003cf0f8e281f04"),
+    "claim_pair": (137_759_488, "map.cu", "7ef7750fd3fe8b25"),
     "reconstruct": (219_803_904, "recon.cu", "69a045f1457ded49"),
 }
 
@@ -210,7 +210,7 @@ NCU_TRAFFIC = {
 # their issue roofline is these instructions over the launch time against
 # one warp instruction per scheduler per clock (4 schedulers x 152 SMs).
 NCU_INSTR = {
-    "claim_pair": (373_507_280, "map.cu", "6003cf0f8e281f04"),
+    "claim_pair": (373_507_280, "map.cu", "7ef7750fd3fe8b25"),
     "reconstruct": (126_116_341, "recon.cu", "69a045f1457ded49"),
 }
 SCHEDULERS = 4 * 152
