@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "vlamet_oracle.c")
+_SRC4 = os.path.join(_HERE, "vlamet4d_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _lock = threading.Lock()
 _libs: dict[bool, C.CDLL] = {}
@@ -30,11 +31,12 @@ def build(openmp: bool = True, force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     out = os.path.join(_BUILD, "libvlamet_oracle_omp.so" if openmp else "libvlamet_oracle.so")
     if (not force and os.path.exists(out)
-            and os.path.getmtime(out) >= max(os.path.getmtime(_SRC),
-                                             os.path.getmtime(os.path.join(_HERE, "vlamet_oracle.h")))):
+            and os.path.getmtime(out) >= max(os.path.getmtime(_SRC), os.path.getmtime(_SRC4),
+                                             os.path.getmtime(os.path.join(_HERE, "vlamet_oracle.h")),
+                                             os.path.getmtime(os.path.join(_HERE, "vlamet4d_oracle.h")))):
         return out
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-Wall", "-Wno-unknown-pragmas", _SRC, "-o", out + ".tmp", "-lm"]
+           "-Wall", "-Wno-unknown-pragmas", _SRC, _SRC4, "-o", out + ".tmp", "-lm"]
     if openmp:
         cmd.insert(1, "-fopenmp")
     subprocess.run(cmd, check=True)
