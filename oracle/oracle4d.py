@@ -59,6 +59,7 @@ def lib(openmp: bool = False) -> C.CDLL:
             "vo4_set_elements": (None, [C.c_void_p, _D]),
             "vo4_get_taylor": (None, [C.c_void_p, _D]),
             "vo4_compute_map": (C.c_int32, [C.c_void_p, _I32]),
+            "vo4_get_map": (None, [C.c_void_p, _I32]),
             "vo4_map_stats": (None, [C.c_void_p, _I64, _I64, _I32]),
             "vo4_reconstruct": (C.c_int32, [C.c_void_p, _D]),
             "vo4_density_force": (None, [C.c_void_p, _D, _D, _D]),
@@ -205,6 +206,11 @@ class Oracle4D:
         out = np.empty(self.n, dtype=np.int32)
         st = self.L.vo4_compute_map(self.h, _ip(out))
         return out, st
+
+    def last_map(self) -> np.ndarray:
+        out = np.empty(self.n, dtype=np.int32)
+        self.L.vo4_get_map(self.h, _ip(out))
+        return out
 
     def map_stats(self) -> dict:
         a, b, c = C.c_int64(), C.c_int64(), C.c_int32()

@@ -717,6 +717,10 @@ int32_t vo4_compute_map(vo4_state* S, int32_t* map_out) {
   return st;
 }
 
+void vo4_get_map(const vo4_state* S, int32_t* out) {
+  memcpy(out, S->map, sizeof(int32_t) * (size_t)S->nsite);
+}
+
 void vo4_map_stats(const vo4_state* S, int64_t* multi, int64_t* holes, int32_t* rounds) {
   *multi = S->stat_multi;
   *holes = S->stat_holes;

@@ -74,6 +74,8 @@ void vo4_get_elements(const vo4_state* S, double* out60xne);
 void vo4_set_elements(vo4_state* S, const double* in60xne);
 void vo4_get_taylor(vo4_state* S, double* out64xne);
 int32_t vo4_compute_map(vo4_state* S, int32_t* map_out);
+/* the last map (of vo4_compute_map, vo4_reconstruct, a step or a remap) */
+void vo4_get_map(const vo4_state* S, int32_t* out);
 void vo4_map_stats(const vo4_state* S, int64_t* claimed_multi, int64_t* holes, int32_t* rounds);
 int32_t vo4_reconstruct(vo4_state* S, double* f_out);
 /* pixel masses of the last reconstruction and the field at the grid nodes */

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 OBJ_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libvlamet.so")
-SOURCES = ["api.cu", "elements.cu", "map.cu", "recon.cu", "spline.cu", "noalloc.cu", "batch.cu", "peak.cu", "group.cu", "server.cu"]
+SOURCES = ["api.cu", "elements.cu", "map.cu", "recon.cu", "spline.cu", "noalloc.cu", "batch.cu", "peak.cu", "group.cu", "server.cu", "phase4d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -40,7 +40,7 @@ def _flags(verbose_ptxas: bool) -> list[str]:
 def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
-    deps = [src, os.path.join(HERE, "..", "include", "vlamet.h")]
+    deps = [src, os.path.join(HERE, "..", "include", "vlamet.h"), os.path.join(HERE, "..", "include", "vlamet4d.h")]
     deps += [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".cuh")]
     return os.path.getmtime(obj) < max(os.path.getmtime(d) for d in deps if os.path.exists(d))
 

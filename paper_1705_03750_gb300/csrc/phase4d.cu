@@ -1,0 +1,1468 @@
+// 4D phase-space (x, y, vx, vy) form of the metric semi-Lagrangian step, FP64.
+//
+// The paper implements 2D phase space and gives the 4D generalisation piece by
+// piece: 60-number elements and the inverse map of eq. QofP (Sec. 2.1), the
+// 15-point quadratic hypersurface (Sec. 2.2.1), percolation with per-axis
+// ranges (Sec. 2.3), and Poisson's equation in the space dimensions on a fixed
+// grid (Sec. 2.5).  Kernels of one step, on the caller's stream:
+//
+//   k4_drift        half drift of every element (one thread per element)
+//   k4_taylor       T^-1 = adj(T)/det T and G_l = [T^-1]^T H_l T^-1
+//   k4_percolate    one block per element: breadth-first flood fill of its
+//                   component in a shared-memory bit window around its start
+//                   site, frontier waves in shared memory, claims by a 128-bit
+//                   compare-and-swap minimum of (d^2 bits, element index);
+//                   k4_percolate_big fills the elements that left their window
+//                   again over the whole padded lattice (global-memory bits)
+//   k4_map_finish   owner of every site from its key; hole list
+//   k4_holes        Jacobi rounds of the unexplored-site repair (one block)
+//   k4_recon        one block per (x, y) pixel: f at its vx-vy plane by the
+//                   15-point interpolation of f_ini at Q(P); pixel mass by a
+//                   block reduction (the v-integration fused in)
+//   k4_accel        direct sum of the 2D Green function over the pixel masses
+//                   for the nodes of the grid and a halo, sources split over
+//                   blocks; k4_accel_sum adds the partial sums in order
+//   k4_kick_drift   2D TSC of the field, its gradient and Hessian (centred
+//                   differences) at the element; kick; second half drift
+//   remap           k4_resample (Q_r blend of the beta set, 4^4-term cubic
+//                   B-spline of eta), k4_spline_axis x 4 (batched tridiagonal
+//                   solves along vy, vx, y, x), k4_reset
+//
+// Every integer decision (start sites, alpha and beta ranges, the d^2
+// comparisons, nearest nodes, spline cells) is taken on FP64 values computed
+// in one fixed order without fused multiply-add (the __d*_rn intrinsics), the
+// order of the FP64 restatement of the method; the map is therefore exactly
+// the one that restatement gives for the same elements.  The reconstruction
+// and the resample use the same order, the spline solve divides by the same
+// pivots, so f and f_ini agree to the last bit with it as well; the pixel
+// masses are block sums (a different order) and the field is summed over
+// blocks, so element trajectories agree to rounding.
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "../../include/vlamet4d.h"
+
+namespace {
+
+constexpr int NE4 = 60;  // doubles per element
+constexpr int NT4 = 64;  // doubles per Taylor record
+constexpr int FCAP = 4096;  // frontier capacity of the flood fill (sites per wave)
+constexpr int ERR_NC = 1, ERR_OVF = 2, ERR_INT = 4;
+constexpr unsigned long long KEY_EMPTY = ~0ull;
+
+struct G4 {
+  int32_t n[4];
+  long long nsite;
+  long long st[4];  // strides of f
+  double lo[4], d[4], inv_d[4], dm[4], inv_dm[4], ctr[4];
+  int32_t s, pad, K[4], L[4], ne;
+  double alpha, beta, half_dt, dt, twoG, dV;
+  int32_t E, We0, We1;  // field cache: nodes [-E, n0-1+E] x [-E, n1-1+E]
+  int32_t R, W;         // flood window: side W = 2R+1 sites around the start site
+  int32_t max_rounds;
+};
+
+struct Dev4 {
+  int32_t err;
+  int32_t nholes;
+  int32_t bad_where;
+  int32_t novf;  // elements whose component left the shared-memory window (this map)
+};
+
+// whole-lattice flood fill of the elements that left their window: per slot,
+// a bit per site of the padded lattice and two frontier buffers
+constexpr int BIG_SLOTS = 8;
+constexpr int BIG_FCAP = 1 << 18;
+
+__device__ __forceinline__ double M_(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double A_(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double S_(double a, double b) { return __dsub_rn(a, b); }
+
+__device__ __forceinline__ void bad(Dev4* ds, int where) {
+  atomicOr(&ds->err, ERR_INT);
+  atomicCAS(&ds->bad_where, 0, where);
+}
+
+// symmetric index of (b, c) in the order 00,01,02,03,11,12,13,22,23,33
+__host__ __device__ __forceinline__ int sym4(int b, int c) {
+  if (b > c) {
+    int t = b;
+    b = c;
+    c = t;
+  }
+  return 4 * b - (b * (b - 1)) / 2 + (c - b);
+}
+
+__device__ __forceinline__ long long nearest_i(double u) { return (long long)floor(A_(u, 0.5)); }
+
+// ---------------------------------------------------------------------------
+// Sec. 2.1: inverse map
+// ---------------------------------------------------------------------------
+
+// dQ = y - T^-1 s / 2, y = T^-1 dP, s_l = dP^T G_l dP
+__device__ __forceinline__ void qofp4(const double* __restrict__ t, const double* P, double* dQ) {
+  double dP[4], s[4];
+  for (int a = 0; a < 4; a++) dP[a] = S_(P[a], t[a]);
+  const double* Ti = t + 4;
+#pragma unroll
+  for (int l = 0; l < 4; l++) {
+    const double* G = t + 20 + 10 * l;
+    double g[4];
+#pragma unroll
+    for (int b = 0; b < 4; b++)
+      g[b] = A_(A_(A_(M_(G[sym4(b, 0)], dP[0]), M_(G[sym4(b, 1)], dP[1])), M_(G[sym4(b, 2)], dP[2])),
+                M_(G[sym4(b, 3)], dP[3]));
+    s[l] = A_(A_(A_(M_(dP[0], g[0]), M_(dP[1], g[1])), M_(dP[2], g[2])), M_(dP[3], g[3]));
+  }
+#pragma unroll
+  for (int a = 0; a < 4; a++) {
+    double y = A_(A_(A_(M_(Ti[4 * a], dP[0]), M_(Ti[4 * a + 1], dP[1])), M_(Ti[4 * a + 2], dP[2])),
+                  M_(Ti[4 * a + 3], dP[3]));
+    double c = A_(A_(A_(M_(Ti[4 * a], s[0]), M_(Ti[4 * a + 1], s[1])), M_(Ti[4 * a + 2], s[2])),
+                  M_(Ti[4 * a + 3], s[3]));
+    dQ[a] = S_(y, M_(0.5, c));
+  }
+}
+
+// squared Lagrangian distance in element spacings (Sec. 2.3.1, eq. distdef)
+__device__ __forceinline__ double dist2_4(const G4& g, const double* __restrict__ t, const double* P,
+                                          double* x) {
+  double dQ[4], xl[4];
+  qofp4(t, P, dQ);
+  for (int a = 0; a < 4; a++) xl[a] = M_(dQ[a], g.inv_dm[a]);
+  if (x)
+    for (int a = 0; a < 4; a++) x[a] = xl[a];
+  return A_(A_(A_(M_(xl[0], xl[0]), M_(xl[1], xl[1])), M_(xl[2], xl[2])), M_(xl[3], xl[3]));
+}
+
+__device__ __forceinline__ void elem_coords(const G4& g, int m, int* k) {
+  for (int a = 3; a >= 0; a--) {
+    k[a] = m % g.L[a];
+    m /= g.L[a];
+  }
+}
+
+__device__ __forceinline__ double site_coord(const G4& g, int a, long long i) {
+  return A_(g.lo[a], M_((double)i, g.d[a]));
+}
+
+// ---------------------------------------------------------------------------
+// elements
+// ---------------------------------------------------------------------------
+
+__global__ void k4_reset(G4 g, double* __restrict__ el) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= g.ne) return;
+  int k[4];
+  elem_coords(g, m, k);
+  double* e = el + (size_t)NE4 * m;
+  for (int q = 0; q < NE4; q++) e[q] = 0.0;
+  for (int a = 0; a < 4; a++) {
+    e[a] = A_(g.ctr[a], M_((double)(k[a] - g.K[a] - 1), g.dm[a]));
+    e[4 + 5 * a] = 1.0;
+  }
+}
+
+// half drift: x_a += v_a h, rows a = 0, 1 of T and H take rows a + 2 times h
+__device__ __forceinline__ void drift_one(double* e, double h) {
+  for (int a = 0; a < 2; a++) {
+    e[a] = A_(e[a], M_(e[a + 2], h));
+    for (int b = 0; b < 4; b++) e[4 + 4 * a + b] = A_(e[4 + 4 * a + b], M_(e[4 + 4 * (a + 2) + b], h));
+    for (int q = 0; q < 10; q++) e[20 + 10 * a + q] = A_(e[20 + 10 * a + q], M_(e[20 + 10 * (a + 2) + q], h));
+  }
+}
+
+__global__ void k4_drift(G4 g, double* __restrict__ el) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= g.ne) return;
+  drift_one(el + (size_t)NE4 * m, g.half_dt);
+}
+
+// T^-1 by the adjugate from the 2x2 minors of rows 0-1 (s) and rows 2-3 (c)
+__device__ void inverse4(const double* A, double* B) {
+  const double a00 = A[0], a01 = A[1], a02 = A[2], a03 = A[3];
+  const double a10 = A[4], a11 = A[5], a12 = A[6], a13 = A[7];
+  const double a20 = A[8], a21 = A[9], a22 = A[10], a23 = A[11];
+  const double a30 = A[12], a31 = A[13], a32 = A[14], a33 = A[15];
+  const double s0 = S_(M_(a00, a11), M_(a10, a01)), s1 = S_(M_(a00, a12), M_(a10, a02));
+  const double s2 = S_(M_(a00, a13), M_(a10, a03)), s3 = S_(M_(a01, a12), M_(a11, a02));
+  const double s4 = S_(M_(a01, a13), M_(a11, a03)), s5 = S_(M_(a02, a13), M_(a12, a03));
+  const double c5 = S_(M_(a22, a33), M_(a32, a23)), c4 = S_(M_(a21, a33), M_(a31, a23));
+  const double c3 = S_(M_(a21, a32), M_(a31, a22)), c2 = S_(M_(a20, a33), M_(a30, a23));
+  const double c1 = S_(M_(a20, a32), M_(a30, a22)), c0 = S_(M_(a20, a31), M_(a30, a21));
+  const double det =
+      A_(S_(A_(A_(S_(M_(s0, c5), M_(s1, c4)), M_(s2, c3)), M_(s3, c2)), M_(s4, c1)), M_(s5, c0));
+  const double id = __ddiv_rn(1.0, det);
+  B[0] = M_(A_(S_(M_(a11, c5), M_(a12, c4)), M_(a13, c3)), id);
+  B[1] = M_(S_(S_(M_(a02, c4), M_(a01, c5)), M_(a03, c3)), id);
+  B[2] = M_(A_(S_(M_(a31, s5), M_(a32, s4)), M_(a33, s3)), id);
+  B[3] = M_(S_(S_(M_(a22, s4), M_(a21, s5)), M_(a23, s3)), id);
+  B[4] = M_(S_(S_(M_(a12, c2), M_(a10, c5)), M_(a13, c1)), id);
+  B[5] = M_(A_(S_(M_(a00, c5), M_(a02, c2)), M_(a03, c1)), id);
+  B[6] = M_(S_(S_(M_(a32, s2), M_(a30, s5)), M_(a33, s1)), id);
+  B[7] = M_(A_(S_(M_(a20, s5), M_(a22, s2)), M_(a23, s1)), id);
+  B[8] = M_(A_(S_(M_(a10, c4), M_(a11, c2)), M_(a13, c0)), id);
+  B[9] = M_(S_(S_(M_(a01, c2), M_(a00, c4)), M_(a03, c0)), id);
+  B[10] = M_(A_(S_(M_(a30, s4), M_(a31, s2)), M_(a33, s0)), id);
+  B[11] = M_(S_(S_(M_(a21, s2), M_(a20, s4)), M_(a23, s0)), id);
+  B[12] = M_(S_(S_(M_(a11, c1), M_(a10, c3)), M_(a12, c0)), id);
+  B[13] = M_(A_(S_(M_(a00, c3), M_(a01, c1)), M_(a02, c0)), id);
+  B[14] = M_(S_(S_(M_(a31, s1), M_(a30, s3)), M_(a32, s0)), id);
+  B[15] = M_(A_(S_(M_(a20, s3), M_(a21, s1)), M_(a22, s0)), id);
+}
+
+__global__ void __launch_bounds__(128) k4_taylor(G4 g, const double* __restrict__ el, double* __restrict__ tay) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= g.ne) return;
+  const double* e = el + (size_t)NE4 * m;
+  double* t = tay + (size_t)NT4 * m;
+  double Ti[16];
+  inverse4(e + 4, Ti);
+  for (int a = 0; a < 4; a++) t[a] = e[a];
+  for (int q = 0; q < 16; q++) t[4 + q] = Ti[q];
+  for (int l = 0; l < 4; l++) {
+    const double* h = e + 20 + 10 * l;
+    double Am[4][4];
+    for (int b = 0; b < 4; b++)
+      for (int c = 0; c < 4; c++)
+        Am[b][c] = A_(A_(A_(M_(h[sym4(b, 0)], Ti[c]), M_(h[sym4(b, 1)], Ti[4 + c])), M_(h[sym4(b, 2)], Ti[8 + c])),
+                      M_(h[sym4(b, 3)], Ti[12 + c]));
+    for (int b = 0; b < 4; b++)
+      for (int c = b; c < 4; c++)
+        t[20 + 10 * l + sym4(b, c)] =
+            A_(A_(A_(M_(Ti[b], Am[0][c]), M_(Ti[4 + b], Am[1][c])), M_(Ti[8 + b], Am[2][c])), M_(Ti[12 + b], Am[3][c]));
+  }
+  int k[4];
+  elem_coords(g, m, k);
+  for (int a = 0; a < 4; a++) t[60 + a] = A_(g.ctr[a], M_((double)(k[a] - g.K[a] - 1), g.dm[a]));
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 2.3.1: percolation
+// ---------------------------------------------------------------------------
+
+// 128-bit compare-and-swap on global memory (sm_90 and later)
+__device__ __forceinline__ ulonglong2 cas128_4(ulonglong2* addr, ulonglong2 cmp, ulonglong2 val) {
+  ulonglong2 old;
+  asm volatile(
+      "{\n\t"
+      ".reg .b128 c, v, r;\n\t"
+      "mov.b128 c, {%2, %3};\n\t"
+      "mov.b128 v, {%4, %5};\n\t"
+      "atom.global.cas.b128 r, [%6], c, v;\n\t"
+      "mov.b128 {%0, %1}, r;\n\t"
+      "}"
+      : "=l"(old.x), "=l"(old.y)
+      : "l"(cmp.x), "l"(cmp.y), "l"(val.x), "l"(val.y), "l"(addr)
+      : "memory");
+  return old;
+}
+
+// key.y = bits of d^2 (non-negative doubles order as integers), key.x = element:
+// the smaller (d^2, index) wins the site
+__device__ __forceinline__ void claim4(ulonglong2* key, unsigned long long dbits, unsigned long long idx) {
+  ulonglong2 cur = __ldcg(key);
+  const ulonglong2 val = make_ulonglong2(idx, dbits);
+  while (dbits < cur.y || (dbits == cur.y && idx < cur.x)) {
+    const ulonglong2 prev = cas128_4(key, cur, val);
+    if (prev.x == cur.x && prev.y == cur.y) break;
+    cur = prev;
+  }
+}
+
+// The percolation test (Sec. 2.3.1): the site passes for m unless an element
+// of the alpha ranges (per axis: below -alpha {-1,0}, below alpha {0}, else
+// {0,1}) proposes a strictly smaller distance.
+__device__ bool passes4(const G4& g, const int* k, const double* tself, const double* __restrict__ tay,
+                        const double* P, double* d2o) {
+  double x[4];
+  const double d2 = dist2_4(g, tself, P, x);
+  *d2o = d2;
+  int lo[4], hi[4];
+  for (int a = 0; a < 4; a++) {
+    if (x[a] < -g.alpha) {
+      lo[a] = -1;
+      hi[a] = 0;
+    } else if (x[a] < g.alpha) {
+      lo[a] = 0;
+      hi[a] = 0;
+    } else {
+      lo[a] = 0;
+      hi[a] = 1;
+    }
+  }
+  for (int o0 = lo[0]; o0 <= hi[0]; o0++)
+    for (int o1 = lo[1]; o1 <= hi[1]; o1++)
+      for (int o2 = lo[2]; o2 <= hi[2]; o2++)
+        for (int o3 = lo[3]; o3 <= hi[3]; o3++) {
+          if ((o0 | o1 | o2 | o3) == 0) continue;
+          const int k0 = k[0] + o0, k1 = k[1] + o1, k2 = k[2] + o2, k3 = k[3] + o3;
+          if (k0 < 0 || k0 >= g.L[0] || k1 < 0 || k1 >= g.L[1] || k2 < 0 || k2 >= g.L[2] || k3 < 0 ||
+              k3 >= g.L[3])
+            continue;
+          const int mm = ((k0 * g.L[1] + k1) * g.L[2] + k2) * g.L[3] + k3;
+          if (dist2_4(g, tay + (size_t)NT4 * mm, P, nullptr) < d2) return false;
+        }
+  return true;
+}
+
+// One block per element: its 4-connected component of passing sites from the
+// site nearest to its position, within the padded lattice [-pad, n-1+pad]^4,
+// explored wave by wave inside a window of side W around the start site.  An
+// element whose component would leave the window, or whose wave outgrows the
+// frontier buffer, is listed for k4_percolate_big.
+__global__ void __launch_bounds__(256) k4_percolate(G4 g, const double* __restrict__ el,
+                                                    const double* __restrict__ tay, ulonglong2* __restrict__ key,
+                                                    int32_t* __restrict__ ovf_list, Dev4* ds) {
+  extern __shared__ uint32_t sm4[];
+  const int W = g.W;
+  const int nwin = W * W * W * W;
+  const int nwords = (nwin + 31) >> 5;
+  uint32_t* stamp = sm4;
+  int32_t* front0 = (int32_t*)(sm4 + ((nwords + 3) & ~3));
+  int32_t* front1 = front0 + FCAP;
+  __shared__ double tself[NT4];
+  __shared__ int org[4], kk[4];
+  __shared__ int go, ncur, nnext, ovf;
+  const int m = blockIdx.x;
+  const int tid = threadIdx.x;
+  if (tid < NT4) tself[tid] = tay[(size_t)NT4 * m + tid];
+  for (int w = tid; w < nwords; w += blockDim.x) stamp[w] = 0u;
+  if (tid == 0) {
+    const double* e = el + (size_t)NE4 * m;
+    int ok = 1;
+    for (int a = 0; a < 4; a++) {
+      const double u = M_(S_(e[a], g.lo[a]), g.inv_d[a]);
+      if (!(u > -1e9 && u < 1e9)) {
+        ok = 0;
+        break;
+      }
+      const long long g0 = nearest_i(u);
+      if (g0 < -g.pad || g0 >= g.n[a] + g.pad) ok = 0;
+      org[a] = (int)g0 - g.R;
+    }
+    int kc[4];
+    elem_coords(g, m, kc);
+    for (int a = 0; a < 4; a++) kk[a] = kc[a];
+    go = ok;
+    ncur = 0;
+    ovf = 0;
+  }
+  __syncthreads();
+  if (!go) return;
+  if (tid == 0) {
+    const int c = g.R;
+    const int lw = ((c * W + c) * W + c) * W + c;
+    stamp[lw >> 5] |= 1u << (lw & 31);
+    double P[4], d2;
+    long long gs[4];
+    for (int a = 0; a < 4; a++) {
+      gs[a] = org[a] + c;
+      P[a] = site_coord(g, a, gs[a]);
+    }
+    if (passes4(g, kk, tself, tay, P, &d2)) {
+      bool in = true;
+      long long p = 0;
+      for (int a = 0; a < 4; a++) {
+        in = in && gs[a] >= 0 && gs[a] < g.n[a];
+        p += gs[a] * g.st[a];
+      }
+      if (in) claim4(key + p, (unsigned long long)__double_as_longlong(d2), (unsigned long long)m);
+      front0[0] = lw;
+      ncur = 1;
+    }
+  }
+  __syncthreads();
+  int cur = 0;
+  int kl[4];
+  for (int a = 0; a < 4; a++) kl[a] = kk[a];
+  while (ncur > 0) {
+    if (tid == 0) nnext = 0;
+    __syncthreads();
+    const int32_t* fc = cur ? front1 : front0;
+    int32_t* fn = cur ? front0 : front1;
+    const int ntask = ncur * 8;
+    for (int t = tid; t < ntask; t += blockDim.x) {
+      const int e = t >> 3, dir = t & 7, ax = dir >> 1, sg = (dir & 1) ? 1 : -1;
+      int lw = fc[e];
+      int l[4];
+      for (int a = 3; a >= 0; a--) {
+        l[a] = lw % W;
+        lw /= W;
+      }
+      l[ax] += sg;
+      const long long ga = (long long)org[ax] + l[ax];
+      if (ga < -g.pad || ga >= g.n[ax] + g.pad) continue;
+      if (l[ax] < 0 || l[ax] >= W) {
+        ovf = 1;
+        continue;
+      }
+      const int nw = ((l[0] * W + l[1]) * W + l[2]) * W + l[3];
+      const uint32_t bit = 1u << (nw & 31);
+      if (atomicOr(&stamp[nw >> 5], bit) & bit) continue;
+      double P[4], d2;
+      long long gs[4];
+      for (int a = 0; a < 4; a++) {
+        gs[a] = (long long)org[a] + l[a];
+        P[a] = site_coord(g, a, gs[a]);
+      }
+      if (!passes4(g, kl, tself, tay, P, &d2)) continue;
+      bool in = true;
+      long long p = 0;
+      for (int a = 0; a < 4; a++) {
+        in = in && gs[a] >= 0 && gs[a] < g.n[a];
+        p += gs[a] * g.st[a];
+      }
+      if (in) claim4(key + p, (unsigned long long)__double_as_longlong(d2), (unsigned long long)m);
+      const int idx = atomicAdd(&nnext, 1);
+      if (idx < FCAP)
+        fn[idx] = nw;
+      else
+        ovf = 1;
+    }
+    __syncthreads();
+    if (tid == 0) ncur = ovf ? 0 : min(nnext, FCAP);
+    cur ^= 1;
+    __syncthreads();
+  }
+  // the component reached the window's edge (or a wave its buffer): the
+  // element is filled again over the whole padded lattice (its claims so far
+  // are a subset of the full component's, with the same keys)
+  if (tid == 0 && ovf) ovf_list[atomicAdd(&ds->novf, 1)] = m;
+}
+
+// Whole-lattice flood fill of the listed elements: the same breadth-first
+// search over the padded lattice [-pad, n-1+pad]^4, with its visited bits and
+// frontiers in global memory (one slot per block).
+__global__ void __launch_bounds__(256) k4_percolate_big(G4 g, const double* __restrict__ el,
+                                                        const double* __restrict__ tay, ulonglong2* __restrict__ key,
+                                                        const int32_t* __restrict__ ovf_list, uint32_t* __restrict__ big,
+                                                        Dev4* ds) {
+  __shared__ double tself[NT4];
+  __shared__ int kk[4];
+  __shared__ int go, ncur, nnext, bad_wave;
+  const int nlist = ds->novf;
+  long long pw[4], npad = 1;
+  for (int a = 0; a < 4; a++) {
+    pw[a] = g.n[a] + 2 * g.pad;
+    npad *= pw[a];
+  }
+  const long long nwords = (npad + 31) >> 5;
+  const size_t slot_words = (size_t)((nwords + 63) & ~63ll) + 2 * (size_t)BIG_FCAP;
+  uint32_t* stamp = big + (size_t)blockIdx.x * slot_words;
+  int32_t* front0 = (int32_t*)(stamp + ((nwords + 63) & ~63ll));
+  int32_t* front1 = front0 + BIG_FCAP;
+  const int tid = threadIdx.x;
+  for (int it = blockIdx.x; it < nlist; it += gridDim.x) {
+    const int m = ovf_list[it];
+    __syncthreads();
+    if (tid < NT4) tself[tid] = tay[(size_t)NT4 * m + tid];
+    for (long long w = tid; w < nwords; w += blockDim.x) stamp[w] = 0u;
+    if (tid == 0) {
+      const double* e = el + (size_t)NE4 * m;
+      long long p0 = 0;
+      bool ok = true;
+      for (int a = 0; a < 4; a++) {
+        const double u = M_(S_(e[a], g.lo[a]), g.inv_d[a]);
+        const long long g0 = nearest_i(u);
+        ok = ok && (g0 >= -g.pad && g0 < g.n[a] + g.pad);
+        p0 = p0 * pw[a] + (g0 + g.pad);
+      }
+      int kc[4];
+      elem_coords(g, m, kc);
+      for (int a = 0; a < 4; a++) kk[a] = kc[a];
+      go = ok;
+      ncur = 0;
+      bad_wave = 0;
+      if (ok) front0[0] = (int32_t)p0;
+    }
+    __syncthreads();
+    __threadfence_block();
+    if (!go) continue;
+    if (tid == 0) {
+      // the start site passed in the window pass (the element overflowed from it)
+      const long long p0 = front0[0];
+      atomicOr(&stamp[p0 >> 5], 1u << (p0 & 31));
+      ncur = 1;
+    }
+    __syncthreads();
+    int kl[4];
+    for (int a = 0; a < 4; a++) kl[a] = kk[a];
+    int cur = 0;
+    while (ncur > 0) {
+      if (tid == 0) nnext = 0;
+      __syncthreads();
+      const int32_t* fc = cur ? front1 : front0;
+      int32_t* fn = cur ? front0 : front1;
+      const long long ntask = (long long)ncur * 8;
+      for (long long t = tid; t < ntask; t += blockDim.x) {
+        const long long e = t >> 3;
+        const int dir = (int)(t & 7), ax = dir >> 1, sg = (dir & 1) ? 1 : -1;
+        long long r = fc[e], gl[4];
+        for (int a = 3; a >= 0; a--) {
+          gl[a] = r % pw[a];
+          r /= pw[a];
+        }
+        gl[ax] += sg;
+        if (gl[ax] < 0 || gl[ax] >= pw[ax]) continue;
+        const long long np = ((gl[0] * pw[1] + gl[1]) * pw[2] + gl[2]) * pw[3] + gl[3];
+        const uint32_t bit = 1u << (np & 31);
+        if (atomicOr(&stamp[np >> 5], bit) & bit) continue;
+        double P[4], d2;
+        long long gs[4];
+        for (int a = 0; a < 4; a++) {
+          gs[a] = gl[a] - g.pad;
+          P[a] = site_coord(g, a, gs[a]);
+        }
+        if (!passes4(g, kl, tself, tay, P, &d2)) continue;
+        bool in = true;
+        long long p = 0;
+        for (int a = 0; a < 4; a++) {
+          in = in && gs[a] >= 0 && gs[a] < g.n[a];
+          p += gs[a] * g.st[a];
+        }
+        if (in) claim4(key + p, (unsigned long long)__double_as_longlong(d2), (unsigned long long)m);
+        const int idx = atomicAdd(&nnext, 1);
+        if (idx < BIG_FCAP)
+          fn[idx] = (int32_t)np;
+        else
+          bad_wave = 1;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        if (bad_wave) atomicOr(&ds->err, ERR_OVF);
+        ncur = bad_wave ? 0 : min(nnext, BIG_FCAP);
+      }
+      cur ^= 1;
+      __syncthreads();
+    }
+  }
+}
+
+// owner of every site from its key (the key is emptied for the next map);
+// sites nobody claimed go to the hole list
+__global__ void k4_map_finish(G4 g, ulonglong2* __restrict__ key, int32_t* __restrict__ map,
+                              int32_t* __restrict__ holes, Dev4* ds) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.nsite) return;
+  const ulonglong2 k = key[p];
+  int owner = -1;
+  if (k.y != KEY_EMPTY) {
+    if (k.x < (unsigned long long)g.ne)
+      owner = (int)k.x;
+    else
+      bad(ds, 41);
+  }
+  map[p] = owner;
+  key[p] = make_ulonglong2(KEY_EMPTY, KEY_EMPTY);
+  if (owner < 0) {
+    const int i = atomicAdd(&ds->nholes, 1);
+    holes[i] = (int32_t)p;
+  }
+}
+
+// Unexplored sites (Sec. 2.3.1): in each round every hole takes, among the
+// owners of its in-grid face neighbours at the end of the previous round, the
+// one with the smallest (d^2 at the hole, index).  One block; rounds are
+// separated by block barriers.
+__global__ void __launch_bounds__(1024) k4_holes(G4 g, const double* __restrict__ tay, int32_t* __restrict__ map,
+                                                 const int32_t* __restrict__ holes, int32_t* __restrict__ cand,
+                                                 Dev4* ds) {
+  __shared__ int remaining;
+  const int nh = ds->nholes;
+  if (nh == 0) return;
+  int rounds = 0;
+  while (true) {
+    if (threadIdx.x == 0) remaining = 0;
+    for (int i = threadIdx.x; i < nh; i += blockDim.x) {
+      const long long p = holes[i];
+      const int cur = map[p];
+      if (cur >= 0) {
+        cand[i] = cur;
+        continue;
+      }
+      long long gc[4], r = p;
+      for (int a = 3; a >= 0; a--) {
+        gc[a] = r % g.n[a];
+        r /= g.n[a];
+      }
+      double P[4];
+      for (int a = 0; a < 4; a++) P[a] = site_coord(g, a, gc[a]);
+      int best = -1;
+      unsigned long long bestk = 0;
+      for (int a = 0; a < 4; a++)
+        for (int sgn = -1; sgn <= 1; sgn += 2) {
+          const long long ga = gc[a] + sgn;
+          if (ga < 0 || ga >= g.n[a]) continue;
+          const int c = map[p + sgn * g.st[a]];
+          if (c < 0) continue;
+          if (c >= g.ne) {
+            bad(ds, 42);
+            continue;
+          }
+          const unsigned long long kd =
+              (unsigned long long)__double_as_longlong(dist2_4(g, tay + (size_t)NT4 * c, P, nullptr));
+          if (best < 0 || kd < bestk || (kd == bestk && c < best)) {
+            best = c;
+            bestk = kd;
+          }
+        }
+      cand[i] = best;
+    }
+    __syncthreads();
+    int left = 0;
+    for (int i = threadIdx.x; i < nh; i += blockDim.x) {
+      map[holes[i]] = cand[i];
+      left += cand[i] < 0;
+    }
+    if (left) atomicAdd(&remaining, left);
+    __syncthreads();
+    rounds++;
+    const int rem = remaining;
+    __syncthreads();
+    if (rem == 0) break;
+    if (rounds >= g.max_rounds) {
+      if (threadIdx.x == 0) atomicOr(&ds->err, ERR_NC);
+      break;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 2.2.1: 15-point quadratic interpolation; transport reconstruction
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double F4at(const G4& g, const double* __restrict__ F, const long long* c) {
+  for (int a = 0; a < 4; a++)
+    if (c[a] < 0 || c[a] >= g.n[a]) return 0.0;
+  return __ldg(F + c[0] * g.st[0] + c[1] * g.st[1] + c[2] * g.st[2] + c[3]);
+}
+
+// nearest node, its 9-point cross, and per pair of axes the corner of the
+// square that holds the projection of u (from the integer parts)
+__device__ double qinterp4(const G4& g, const double* __restrict__ F, const double* u) {
+  for (int a = 0; a < 4; a++)
+    if (!(u[a] > -2.0 && u[a] < (double)g.n[a] + 1.0)) return 0.0;
+  long long gn[4], gc[4];
+  double dq[4];
+  for (int a = 0; a < 4; a++) {
+    gn[a] = nearest_i(u[a]);
+    gc[a] = (long long)floor(u[a]);
+    dq[a] = S_(u[a], (double)gn[a]);
+  }
+  const double w0 = S_(S_(S_(S_(1.0, M_(dq[0], dq[0])), M_(dq[1], dq[1])), M_(dq[2], dq[2])), M_(dq[3], dq[3]));
+  double f = M_(F4at(g, F, gn), w0);
+  for (int a = 0; a < 4; a++) {
+    long long c[4] = {gn[0], gn[1], gn[2], gn[3]};
+    c[a] = gn[a] + 1;
+    f = A_(f, M_(M_(M_(0.5, F4at(g, F, c)), dq[a]), A_(1.0, dq[a])));
+    c[a] = gn[a] - 1;
+    f = A_(f, M_(M_(M_(0.5, F4at(g, F, c)), dq[a]), S_(dq[a], 1.0)));
+  }
+  for (int a = 0; a < 4; a++)
+    for (int b = a + 1; b < 4; b++) {
+      long long c00[4] = {gn[0], gn[1], gn[2], gn[3]};
+      c00[a] = gc[a];
+      c00[b] = gc[b];
+      long long c11[4] = {c00[0], c00[1], c00[2], c00[3]}, c10[4] = {c00[0], c00[1], c00[2], c00[3]},
+                c01[4] = {c00[0], c00[1], c00[2], c00[3]};
+      c11[a] += 1;
+      c11[b] += 1;
+      c10[a] += 1;
+      c01[b] += 1;
+      const double cross = S_(S_(A_(F4at(g, F, c11), F4at(g, F, c00)), F4at(g, F, c10)), F4at(g, F, c01));
+      f = A_(f, M_(M_(cross, dq[a]), dq[b]));
+    }
+  return f;
+}
+
+// One block per (x, y) pixel: f(P) = f_ini(Q(P)) at every (vx, vy) site of
+// the pixel through the owner's inverse map, and the pixel mass
+// M = (sum f) dx dy dvx dvy.
+__global__ void __launch_bounds__(256) k4_recon(G4 g, const double* __restrict__ tay, const int32_t* __restrict__ map,
+                                                const double* __restrict__ fini, double* __restrict__ f,
+                                                double* __restrict__ Mpix, Dev4* ds) {
+  __shared__ double red[32];
+  const int pix = blockIdx.x;
+  const long long i0 = pix / g.n[1], i1 = pix % g.n[1];
+  const int nvel = g.n[2] * g.n[3];
+  const long long base = (long long)pix * nvel;
+  double sum = 0.0;
+  for (int q = threadIdx.x; q < nvel; q += blockDim.x) {
+    const long long p = base + q;
+    const int m = map[p];
+    double fv = 0.0;
+    if (m >= 0 && m < g.ne) {
+      const double* t = tay + (size_t)NT4 * m;
+      double P[4], dQ[4], u[4];
+      P[0] = site_coord(g, 0, i0);
+      P[1] = site_coord(g, 1, i1);
+      P[2] = site_coord(g, 2, q / g.n[3]);
+      P[3] = site_coord(g, 3, q % g.n[3]);
+      qofp4(t, P, dQ);
+      for (int a = 0; a < 4; a++) u[a] = M_(S_(A_(__ldg(t + 60 + a), dQ[a]), g.lo[a]), g.inv_d[a]);
+      fv = qinterp4(g, fini, u);
+    } else if (m >= g.ne) {
+      bad(ds, 43);
+    }
+    f[p] = fv;
+    sum += fv;
+  }
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) Mpix[pix] = v * g.dV;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 2.5: Poisson in 2D space
+// ---------------------------------------------------------------------------
+
+// partial direct sums g_part[chunk][node] = sum over the chunk's pixels p !=
+// node of M_p (r - r_p)/|r - r_p|^2, for the nodes of the cache block
+constexpr int ACC_CHUNK = 1024;
+
+__global__ void __launch_bounds__(256) k4_accel(G4 g, const double* __restrict__ Mpix, double2* __restrict__ part) {
+  __shared__ double ms[ACC_CHUNK];
+  const int nsrc = g.n[0] * g.n[1];
+  const int c0 = blockIdx.y * ACC_CHUNK;
+  const int cn = min(ACC_CHUNK, nsrc - c0);
+  for (int q = threadIdx.x; q < cn; q += blockDim.x) ms[q] = Mpix[c0 + q];
+  __syncthreads();
+  const int nodes = g.We0 * g.We1;
+  const int node = blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= nodes) return;
+  const long long i = node / g.We1 - g.E, j = node % g.We1 - g.E;
+  double gx = 0.0, gy = 0.0;
+  for (int q = 0; q < cn; q++) {
+    const int src = c0 + q;
+    const long long p0 = src / g.n[1], p1 = src % g.n[1];
+    if (p0 == i && p1 == j) continue;
+    const double rx = (double)(i - p0) * g.d[0];
+    const double ry = (double)(j - p1) * g.d[1];
+    const double c = ms[q] / (rx * rx + ry * ry);
+    gx += c * rx;
+    gy += c * ry;
+  }
+  part[(size_t)blockIdx.y * nodes + node] = make_double2(gx, gy);
+}
+
+__global__ void k4_accel_sum(G4 g, const double2* __restrict__ part, int nchunk, double2* __restrict__ gext) {
+  const int nodes = g.We0 * g.We1;
+  const int node = blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= nodes) return;
+  double gx = 0.0, gy = 0.0;
+  for (int c = 0; c < nchunk; c++) {
+    const double2 v = part[(size_t)c * nodes + node];
+    gx += v.x;
+    gy += v.y;
+  }
+  gext[node] = make_double2(-g.twoG * gx, -g.twoG * gy);
+}
+
+// acceleration at any node: the cache block, else the direct sum
+__device__ double2 accel_node(const G4& g, const double* __restrict__ Mpix, const double2* __restrict__ gext,
+                              long long i, long long j) {
+  if (i >= -g.E && i < g.n[0] + g.E && j >= -g.E && j < g.n[1] + g.E)
+    return gext[(i + g.E) * g.We1 + (j + g.E)];
+  double gx = 0.0, gy = 0.0;
+  for (long long p0 = 0; p0 < g.n[0]; p0++)
+    for (long long p1 = 0; p1 < g.n[1]; p1++) {
+      const double rx = (double)(i - p0) * g.d[0];
+      const double ry = (double)(j - p1) * g.d[1];
+      const double c = Mpix[p0 * g.n[1] + p1] / (rx * rx + ry * ry);
+      gx += c * rx;
+      gy += c * ry;
+    }
+  return make_double2(-g.twoG * gx, -g.twoG * gy);
+}
+
+// field record (g, J, K) at a node from the accelerations of its 3x3 block
+__device__ __forceinline__ void field_block(const G4& g, const double2 b[3][3], double* o) {
+  o[0] = b[1][1].x;
+  o[1] = b[1][1].y;
+  const double dx = g.d[0], dy = g.d[1];
+  for (int a = 0; a < 2; a++) {
+    const double v21 = a ? b[2][1].y : b[2][1].x, v01 = a ? b[0][1].y : b[0][1].x;
+    const double v12 = a ? b[1][2].y : b[1][2].x, v10 = a ? b[1][0].y : b[1][0].x;
+    const double v11 = a ? b[1][1].y : b[1][1].x;
+    const double v22 = a ? b[2][2].y : b[2][2].x, v20 = a ? b[2][0].y : b[2][0].x;
+    const double v02 = a ? b[0][2].y : b[0][2].x, v00 = a ? b[0][0].y : b[0][0].x;
+    o[2 + 2 * a] = (v21 - v01) / (2.0 * dx);
+    o[3 + 2 * a] = (v12 - v10) / (2.0 * dy);
+    o[6 + 3 * a] = ((v21 + v01) - 2.0 * v11) / (dx * dx);
+    o[7 + 3 * a] = (((v22 - v20) - v02) + v00) / ((4.0 * dx) * dy);
+    o[8 + 3 * a] = ((v12 + v10) - 2.0 * v11) / (dy * dy);
+  }
+}
+
+__global__ void k4_node_fields(G4 g, const double* __restrict__ Mpix, const double2* __restrict__ gext,
+                               double* __restrict__ out) {
+  const int node = blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g.n[0] * g.n[1]) return;
+  const long long i = node / g.n[1], j = node % g.n[1];
+  double2 b[3][3];
+  for (int p = 0; p < 3; p++)
+    for (int q = 0; q < 3; q++) b[p][q] = accel_node(g, Mpix, gext, i + p - 1, j + q - 1);
+  field_block(g, b, out + 12 * (size_t)node);
+}
+
+// Kick (Sec. 2.4) with the field interpolated at the drifted element by the
+// 2D TSC weights: dv_a = g_a dt, dT_{2+a,.} = J_a. T_{0:2,.} dt,
+// dH_{2+a,bc} = (J_a. H_{0:2,bc} + K_a,.. T_.b T_.c) dt; then the second half
+// drift.
+__global__ void __launch_bounds__(128) k4_kick_drift(G4 g, const double* __restrict__ Mpix,
+                                                     const double2* __restrict__ gext, double* __restrict__ el) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= g.ne) return;
+  double* e = el + (size_t)NE4 * m;
+  const double ux = (e[0] - g.lo[0]) * g.inv_d[0];
+  const double uy = (e[1] - g.lo[1]) * g.inv_d[1];
+  if (ux > -1e9 && ux < 1e9 && uy > -1e9 && uy < 1e9) {
+    const long long i = (long long)floor(ux + 0.5), j = (long long)floor(uy + 0.5);
+    double wx[3], wy[3];
+    {
+      const double w = ux - (double)i;
+      wx[0] = 0.5 * ((0.5 - w) * (0.5 - w));
+      wx[1] = 0.75 - w * w;
+      wx[2] = 0.5 * ((0.5 + w) * (0.5 + w));
+      const double v = uy - (double)j;
+      wy[0] = 0.5 * ((0.5 - v) * (0.5 - v));
+      wy[1] = 0.75 - v * v;
+      wy[2] = 0.5 * ((0.5 + v) * (0.5 + v));
+    }
+    double F[12];
+    for (int c = 0; c < 12; c++) F[c] = 0.0;
+    for (int p = 0; p < 3; p++) {
+      double row[12];
+      for (int c = 0; c < 12; c++) row[c] = 0.0;
+      for (int q = 0; q < 3; q++) {
+        double2 b[3][3];
+        for (int pp = 0; pp < 3; pp++)
+          for (int qq = 0; qq < 3; qq++) b[pp][qq] = accel_node(g, Mpix, gext, i + p + pp - 2, j + q + qq - 2);
+        double nf[12];
+        field_block(g, b, nf);
+        for (int c = 0; c < 12; c++) row[c] += wy[q] * nf[c];
+      }
+      for (int c = 0; c < 12; c++) F[c] += wx[p] * row[c];
+    }
+    double Tx[2][4], Hx[2][10];
+    for (int b = 0; b < 2; b++) {
+      for (int q = 0; q < 4; q++) Tx[b][q] = e[4 + 4 * b + q];
+      for (int q = 0; q < 10; q++) Hx[b][q] = e[20 + 10 * b + q];
+    }
+    const double dt = g.dt;
+    for (int a = 0; a < 2; a++) {
+      const double Ja0 = F[2 + 2 * a], Ja1 = F[3 + 2 * a];
+      const double Kxx = F[6 + 3 * a], Kxy = F[7 + 3 * a], Kyy = F[8 + 3 * a];
+      e[2 + a] += F[a] * dt;
+      for (int q = 0; q < 4; q++) e[4 + 4 * (2 + a) + q] += (Ja0 * Tx[0][q] + Ja1 * Tx[1][q]) * dt;
+      for (int b = 0; b < 4; b++)
+        for (int c = b; c < 4; c++) {
+          const int q = sym4(b, c);
+          const double t1 = Ja0 * Hx[0][q] + Ja1 * Hx[1][q];
+          const double t2 = (((Kxx * Tx[0][b]) * Tx[0][c] + (Kxy * Tx[0][b]) * Tx[1][c]) + (Kxy * Tx[1][b]) * Tx[0][c]) +
+                            (Kyy * Tx[1][b]) * Tx[1][c];
+          e[20 + 10 * (2 + a) + q] += (t1 + t2) * dt;
+        }
+    }
+  }
+  drift_one(e, g.half_dt);
+}
+
+// ---------------------------------------------------------------------------
+// Secs. 2.2.2 and 2.3.2: remap
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double bspline3_4(double t) {
+  t = fabs(t);
+  if (t < 1.0) return A_(S_(2.0 / 3.0, M_(t, t)), M_(0.5, M_(M_(t, t), t)));
+  if (t < 2.0) {
+    const double r = S_(2.0, t);
+    return __ddiv_rn(M_(M_(r, r), r), 6.0);
+  }
+  return 0.0;
+}
+
+__device__ __forceinline__ double W4(double x) {
+  if (x <= 1.0) return A_(S_(1.0, M_(1.5, M_(x, x))), M_(0.75, M_(M_(x, x), x)));
+  if (x <= 2.0) {
+    const double r = S_(2.0, x);
+    return M_(0.25, M_(M_(r, r), r));
+  }
+  return 0.0;
+}
+
+__device__ __forceinline__ long long ghost4(long long k, int n) {
+  if (k >= 0 && k < n) return k;
+  if (k == -1) return 1;
+  if (k == n) return n - 2;
+  return -1;
+}
+
+// sum over the 4^4 coefficients around u of eta_k prod_a B(u_a - k_a)
+__device__ double spline_eval4(const G4& g, const double* __restrict__ eta, const double* u) {
+  for (int a = 0; a < 4; a++)
+    if (!(u[a] > -3.0 && u[a] < (double)(g.n[a] + 2))) return 0.0;
+  double B[4][4];
+  long long gk[4][4];
+  for (int a = 0; a < 4; a++) {
+    const long long k0 = (long long)floor(u[a]) - 1;
+    for (int q = 0; q < 4; q++) {
+      B[a][q] = bspline3_4(S_(u[a], (double)(k0 + q)));
+      gk[a][q] = ghost4(k0 + q, g.n[a]);
+    }
+  }
+  double sum = 0.0;
+  for (int q0 = 0; q0 < 4; q0++) {
+    if (gk[0][q0] < 0) continue;
+    for (int q1 = 0; q1 < 4; q1++) {
+      if (gk[1][q1] < 0) continue;
+      for (int q2 = 0; q2 < 4; q2++) {
+        if (gk[2][q2] < 0) continue;
+        const long long b012 = gk[0][q0] * g.st[0] + gk[1][q1] * g.st[1] + gk[2][q2] * g.st[2];
+        for (int q3 = 0; q3 < 4; q3++) {
+          if (gk[3][q3] < 0) continue;
+          const double v = __ldg(eta + b012 + gk[3][q3]);
+          sum = A_(sum, M_(M_(M_(M_(v, B[0][q0]), B[1][q1]), B[2][q2]), B[3][q3]));
+        }
+      }
+    }
+  }
+  return sum;
+}
+
+// f_new(P) = spline[f_ini](Q_r(P)), Q_r = sum W(2 d_m') Q(P, m') / sum W(2 d_m')
+// over the beta set of the owner (per axis below -beta {-1,0}, below beta
+// {-1,0,1}, else {0,1}; an offset with two or more non-zero components is
+// dropped when one of them lies on a {-1,0,1} axis)
+__global__ void __launch_bounds__(128) k4_resample(G4 g, const double* __restrict__ tay, const int32_t* __restrict__ map,
+                                                  const double* __restrict__ eta, double* __restrict__ fnew, Dev4* ds) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.nsite) return;
+  const int m = map[p];
+  double val = 0.0;
+  if (m >= 0 && m < g.ne) {
+    long long gc[4], r = p;
+    for (int a = 3; a >= 0; a--) {
+      gc[a] = r % g.n[a];
+      r /= g.n[a];
+    }
+    double P[4], x[4];
+    for (int a = 0; a < 4; a++) P[a] = site_coord(g, a, gc[a]);
+    const double* tm = tay + (size_t)NT4 * m;
+    dist2_4(g, tm, P, x);
+    int lo[4], hi[4], full[4];
+    for (int a = 0; a < 4; a++) {
+      lo[a] = (x[a] < -g.beta) ? -1 : ((x[a] < g.beta) ? -1 : 0);
+      hi[a] = (x[a] < -g.beta) ? 0 : 1;
+      full[a] = (lo[a] == -1 && hi[a] == 1);
+    }
+    int k[4];
+    elem_coords(g, m, k);
+    double num[4] = {0.0, 0.0, 0.0, 0.0}, den = 0.0;
+    for (int o0 = lo[0]; o0 <= hi[0]; o0++)
+      for (int o1 = lo[1]; o1 <= hi[1]; o1++)
+        for (int o2 = lo[2]; o2 <= hi[2]; o2++)
+          for (int o3 = lo[3]; o3 <= hi[3]; o3++) {
+            const int o[4] = {o0, o1, o2, o3};
+            int nz = 0, onfull = 0;
+            for (int a = 0; a < 4; a++)
+              if (o[a] != 0) {
+                nz++;
+                onfull |= full[a];
+              }
+            if (nz >= 2 && onfull) continue;
+            int kk[4], ok = 1;
+            for (int a = 0; a < 4; a++) {
+              kk[a] = k[a] + o[a];
+              ok &= (kk[a] >= 0 && kk[a] < g.L[a]);
+            }
+            if (!ok) continue;
+            const int mm = ((kk[0] * g.L[1] + kk[1]) * g.L[2] + kk[2]) * g.L[3] + kk[3];
+            const double* t = tay + (size_t)NT4 * mm;
+            double dQ[4], xl[4];
+            qofp4(t, P, dQ);
+            for (int a = 0; a < 4; a++) xl[a] = M_(dQ[a], g.inv_dm[a]);
+            const double dd =
+                __dsqrt_rn(A_(A_(A_(M_(xl[0], xl[0]), M_(xl[1], xl[1])), M_(xl[2], xl[2])), M_(xl[3], xl[3])));
+            const double w = W4(M_(2.0, dd));
+            for (int a = 0; a < 4; a++) num[a] = A_(num[a], M_(w, A_(__ldg(t + 60 + a), dQ[a])));
+            den = A_(den, w);
+          }
+    double Qr[4];
+    if (den > 0.0) {
+      for (int a = 0; a < 4; a++) Qr[a] = __ddiv_rn(num[a], den);
+    } else {
+      double dQ[4];
+      qofp4(tm, P, dQ);
+      for (int a = 0; a < 4; a++) Qr[a] = A_(__ldg(tm + 60 + a), dQ[a]);
+    }
+    double u[4];
+    for (int a = 0; a < 4; a++) u[a] = M_(S_(Qr[a], g.lo[a]), g.inv_d[a]);
+    val = spline_eval4(g, eta, u);
+  } else if (m >= g.ne) {
+    bad(ds, 44);
+  }
+  fnew[p] = val;
+}
+
+// Batched tridiagonal solves of the zero-slope cubic spline along one axis
+// (Sec. 2.2.2), in place on eta, one thread per line.  tab holds, per node i
+// of the axis, the sub-diagonal, the pivot and the eliminated super-diagonal
+// of the Thomas algorithm (pivots computed once on the host).
+__global__ void k4_spline_axis(G4 g, int ax, const double* __restrict__ tab, double* __restrict__ eta) {
+  const long long nl = g.nsite / g.n[ax];
+  const long long line = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (line >= nl) return;
+  const long long st = g.st[ax];
+  const long long base = (line / st) * (st * g.n[ax]) + (line % st);
+  const int n = g.n[ax];
+  const double* sub = tab;
+  const double* den = tab + n;
+  const double* cp = tab + 2 * n;
+  double dp = 0.0;
+  for (int i = 0; i < n; i++) {
+    const double rhs = M_(6.0, eta[base + i * st]);
+    dp = __ddiv_rn(S_(rhs, M_(__ldg(sub + i), dp)), __ldg(den + i));
+    eta[base + i * st] = dp;
+  }
+  double nxt = eta[base + (long long)(n - 1) * st];
+  for (int i = n - 2; i >= 0; i--) {
+    nxt = S_(eta[base + i * st], M_(__ldg(cp + i), nxt));
+    eta[base + i * st] = nxt;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+struct vm_4d_solver {
+  G4 g;
+  cudaStream_t stream;
+  char* ws;
+  double *fini, *eta, *f, *el, *tay, *Mpix, *fld, *tab;
+  ulonglong2* key;
+  int32_t *map, *holes, *cand, *ovf_list;
+  uint32_t* big;
+  double2 *gext, *part;
+  Dev4* ds;
+  int nchunk;
+  size_t smem;
+  int64_t launches;
+  int have_f;
+  int cyc;
+  int n_s;
+};
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+size_t up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
+
+bool fill_grid(const vm_4d_config* c, G4* g) {
+  if (!c) return false;
+  memset(g, 0, sizeof *g);
+  const int s = c->elem_stride;
+  if (s < 1 || s > 8 || c->n_s < 1 || !(c->dt > 0.0) || c->pad < 0) return false;
+  long long ns = 1;
+  for (int a = 0; a < 4; a++) {
+    if (c->n[a] < 4 || c->n[a] > 4096 || !(c->hi[a] > c->lo[a])) return false;
+    ns *= c->n[a];
+  }
+  if (ns > (1ll << 31) - 1) return false;
+  g->nsite = ns;
+  g->s = s;
+  g->pad = c->pad > 0 ? c->pad : s;
+  long long ne = 1;
+  for (int a = 0; a < 4; a++) {
+    g->n[a] = c->n[a];
+    g->lo[a] = c->lo[a];
+    g->d[a] = (c->hi[a] - c->lo[a]) / (double)(c->n[a] - 1);
+    g->dm[a] = (double)s * g->d[a];
+    g->inv_d[a] = 1.0 / g->d[a];
+    g->inv_dm[a] = 1.0 / g->dm[a];
+    g->ctr[a] = 0.5 * (c->lo[a] + c->hi[a]);
+    g->K[a] = (c->n[a] - 1 + 2 * s - 1) / (2 * s);
+    g->L[a] = 2 * g->K[a] + 3;
+    ne *= g->L[a];
+  }
+  if (ne > (1ll << 30)) return false;
+  long long npad = 1;
+  for (int a = 0; a < 4; a++) npad *= c->n[a] + 2 * g->pad;
+  if (npad > (1ll << 31) - 1) return false;
+  g->ne = (int32_t)ne;
+  g->st[3] = 1;
+  for (int a = 2; a >= 0; a--) g->st[a] = g->st[a + 1] * c->n[a + 1];
+  g->alpha = c->alpha > 0.0 ? c->alpha : sqrt(3.0) / 4.0;
+  g->beta = c->beta > 0.0 ? c->beta : 0.5 * (1.0 - sqrt(3.0) / 2.0);
+  g->dt = c->dt;
+  g->half_dt = 0.5 * c->dt;
+  g->twoG = 2.0 * c->G;
+  g->dV = ((g->d[0] * g->d[1]) * g->d[2]) * g->d[3];
+  g->E = g->pad + 2 * s + 4;
+  g->We0 = c->n[0] + 2 * g->E;
+  g->We1 = c->n[1] + 2 * g->E;
+  g->R = std::min(2 * s, 12);
+  g->W = 2 * g->R + 1;
+  g->max_rounds = c->max_hole_rounds > 0 ? c->max_hole_rounds : (c->n[0] + c->n[1] + c->n[2] + c->n[3]);
+  return true;
+}
+
+int nchunks(const G4& g) {
+  const int nsrc = g.n[0] * g.n[1];
+  return (nsrc + ACC_CHUNK - 1) / ACC_CHUNK;
+}
+
+struct Layout {
+  size_t fini, eta, f, key, map, holes, cand, el, tay, Mpix, fld, gext, part, tab, ovf, big, ds, total;
+};
+
+Layout layout(const G4& g) {
+  Layout L;
+  size_t o = 0;
+  const size_t ns = (size_t)g.nsite;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = up(o + bytes);
+    return at;
+  };
+  L.fini = take(8 * ns);
+  L.eta = take(8 * ns);
+  L.f = take(8 * ns);
+  L.key = take(16 * ns);
+  L.map = take(4 * ns);
+  L.holes = take(4 * ns);
+  L.cand = take(4 * ns);
+  L.el = take(8 * (size_t)NE4 * g.ne);
+  L.tay = take(8 * (size_t)NT4 * g.ne);
+  L.Mpix = take(8 * (size_t)g.n[0] * g.n[1]);
+  L.fld = take(8 * 12 * (size_t)g.n[0] * g.n[1]);
+  L.gext = take(16 * (size_t)g.We0 * g.We1);
+  L.part = take(16 * (size_t)g.We0 * g.We1 * nchunks(g));
+  int nmax = 0;
+  for (int a = 0; a < 4; a++) nmax = std::max(nmax, g.n[a]);
+  L.tab = take(8 * 3 * 4 * (size_t)nmax);
+  L.ovf = take(4 * (size_t)g.ne);
+  long long npad = 1;
+  for (int a = 0; a < 4; a++) npad *= g.n[a] + 2 * g.pad;
+  const size_t nwords = (size_t)((npad + 31) >> 5);
+  L.big = take(4 * (size_t)BIG_SLOTS * (((nwords + 63) & ~(size_t)63) + 2 * (size_t)BIG_FCAP));
+  L.ds = take(sizeof(Dev4));
+  L.total = o;
+  return L;
+}
+
+// pivots of the Thomas algorithm of the zero-slope spline along an axis of
+// n nodes: rows (multiplied by 6) 4 e0 + 2 e1; e_{i-1} + 4 e_i + e_{i+1};
+// 2 e_{n-2} + 4 e_{n-1}
+void spline_table(int n, double* sub, double* den, double* cp) {
+  for (int i = 0; i < n; i++) {
+    const double sb = (i == 0) ? 0.0 : ((i == n - 1) ? 2.0 : 1.0);
+    const double sp = (i == n - 1) ? 0.0 : ((i == 0) ? 2.0 : 1.0);
+    const double dia = 4.0;
+    sub[i] = sb;
+    if (i == 0) {
+      den[i] = dia;
+      cp[i] = sp / dia;
+    } else {
+      const double d = dia - sb * cp[i - 1];
+      den[i] = d;
+      cp[i] = sp / d;
+    }
+  }
+}
+
+inline unsigned blocks(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+vm_status cuda_ok(cudaError_t e) { return e == cudaSuccess ? VM_OK : VM_E_CUDA; }
+
+vm_status launched(vm_4d_solver* s) {
+  s->launches++;
+  return cuda_ok(cudaGetLastError());
+}
+
+vm_status run_map(vm_4d_solver* s) {
+  const G4& g = s->g;
+  k4_taylor<<<blocks(g.ne, 128), 128, 0, s->stream>>>(g, s->el, s->tay);
+  if (launched(s)) return VM_E_CUDA;
+  if (cudaMemsetAsync(&s->ds->nholes, 0, sizeof(int32_t), s->stream) != cudaSuccess ||
+      cudaMemsetAsync(&s->ds->novf, 0, sizeof(int32_t), s->stream) != cudaSuccess)
+    return VM_E_CUDA;
+  k4_percolate<<<g.ne, 256, s->smem, s->stream>>>(g, s->el, s->tay, s->key, s->ovf_list, s->ds);
+  if (launched(s)) return VM_E_CUDA;
+  // returns at once when no element left its window
+  k4_percolate_big<<<BIG_SLOTS, 256, 0, s->stream>>>(g, s->el, s->tay, s->key, s->ovf_list, s->big, s->ds);
+  if (launched(s)) return VM_E_CUDA;
+  k4_map_finish<<<blocks(g.nsite, 256), 256, 0, s->stream>>>(g, s->key, s->map, s->holes, s->ds);
+  if (launched(s)) return VM_E_CUDA;
+  k4_holes<<<1, 1024, 0, s->stream>>>(g, s->tay, s->map, s->holes, s->cand, s->ds);
+  return launched(s);
+}
+
+vm_status run_recon(vm_4d_solver* s) {
+  const G4& g = s->g;
+  k4_recon<<<g.n[0] * g.n[1], 256, 0, s->stream>>>(g, s->tay, s->map, s->fini, s->f, s->Mpix, s->ds);
+  if (launched(s)) return VM_E_CUDA;
+  const int nodes = g.We0 * g.We1;
+  k4_accel<<<dim3(blocks(nodes, 256), s->nchunk), 256, 0, s->stream>>>(g, s->Mpix, s->part);
+  if (launched(s)) return VM_E_CUDA;
+  k4_accel_sum<<<blocks(nodes, 256), 256, 0, s->stream>>>(g, s->part, s->nchunk, s->gext);
+  return launched(s);
+}
+
+vm_status run_spline(vm_4d_solver* s) {
+  const G4& g = s->g;
+  int nmax = 0;
+  for (int a = 0; a < 4; a++) nmax = std::max(nmax, g.n[a]);
+  for (int a = 3; a >= 0; a--) {
+    k4_spline_axis<<<blocks(g.nsite / g.n[a], 128), 128, 0, s->stream>>>(g, a, s->tab + 3 * (size_t)nmax * a, s->eta);
+    if (launched(s)) return VM_E_CUDA;
+  }
+  return VM_OK;
+}
+
+vm_status run_reset(vm_4d_solver* s) {
+  k4_reset<<<blocks(s->g.ne, 128), 128, 0, s->stream>>>(s->g, s->el);
+  s->cyc = 0;
+  return launched(s);
+}
+
+vm_status run_remap(vm_4d_solver* s) {
+  const G4& g = s->g;
+  vm_status st = run_map(s);
+  if (st) return st;
+  // f_ini <- spline(f_ini)(Q_r): the resample reads eta only
+  k4_resample<<<blocks(g.nsite, 128), 128, 0, s->stream>>>(g, s->tay, s->map, s->eta, s->fini, s->ds);
+  if (launched(s)) return VM_E_CUDA;
+  if (cudaMemcpyAsync(s->eta, s->fini, 8 * (size_t)g.nsite, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess)
+    return VM_E_CUDA;
+  st = run_spline(s);
+  if (st) return st;
+  return run_reset(s);
+}
+
+vm_status copy_out(vm_4d_solver* s, void* dst, const void* src, size_t bytes, int on_device) {
+  if (!dst) return VM_E_INVALID_ARG;
+  if (cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream) !=
+      cudaSuccess)
+    return VM_E_CUDA;
+  return vm_4d_sync(s);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t vm_4d_workspace_bytes(const vm_4d_config* c) {
+  G4 g;
+  if (!fill_grid(c, &g)) return 0;
+  return layout(g).total;
+}
+
+vm_status vm_4d_create(const vm_4d_config* c, void* d_ws, size_t bytes, void* stream, vm_4d_solver** out) {
+  if (!out) return VM_E_INVALID_ARG;
+  *out = nullptr;
+  G4 g;
+  if (!fill_grid(c, &g)) return VM_E_INVALID_ARG;
+  if (!d_ws || ((uintptr_t)d_ws & (ALIGN - 1))) return VM_E_INVALID_ARG;
+  const Layout L = layout(g);
+  if (bytes < L.total) return VM_E_OOM;
+  vm_4d_solver* s = new (std::nothrow) vm_4d_solver();
+  if (!s) return VM_E_OOM;
+  s->g = g;
+  s->n_s = c->n_s;
+  s->stream = (cudaStream_t)stream;
+  s->ws = (char*)d_ws;
+  s->fini = (double*)(s->ws + L.fini);
+  s->eta = (double*)(s->ws + L.eta);
+  s->f = (double*)(s->ws + L.f);
+  s->key = (ulonglong2*)(s->ws + L.key);
+  s->map = (int32_t*)(s->ws + L.map);
+  s->holes = (int32_t*)(s->ws + L.holes);
+  s->cand = (int32_t*)(s->ws + L.cand);
+  s->el = (double*)(s->ws + L.el);
+  s->tay = (double*)(s->ws + L.tay);
+  s->Mpix = (double*)(s->ws + L.Mpix);
+  s->fld = (double*)(s->ws + L.fld);
+  s->gext = (double2*)(s->ws + L.gext);
+  s->part = (double2*)(s->ws + L.part);
+  s->tab = (double*)(s->ws + L.tab);
+  s->ovf_list = (int32_t*)(s->ws + L.ovf);
+  s->big = (uint32_t*)(s->ws + L.big);
+  s->ds = (Dev4*)(s->ws + L.ds);
+  s->nchunk = nchunks(g);
+  const int nwin = g.W * g.W * g.W * g.W;
+  const int nwords = (nwin + 31) / 32;
+  s->smem = 4 * (size_t)((nwords + 3) & ~3) + 2 * 4 * (size_t)FCAP;
+  if (cudaFuncSetAttribute(k4_percolate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem) != cudaSuccess) {
+    delete s;
+    return VM_E_CUDA;
+  }
+  int nmax = 0;
+  for (int a = 0; a < 4; a++) nmax = std::max(nmax, g.n[a]);
+  std::vector<double> tab(3 * 4 * (size_t)nmax, 0.0);
+  for (int a = 0; a < 4; a++) {
+    double* t = tab.data() + 3 * (size_t)nmax * a;
+    spline_table(g.n[a], t, t + g.n[a], t + 2 * g.n[a]);
+  }
+  vm_status st = VM_OK;
+  if (cudaMemcpyAsync(s->tab, tab.data(), 8 * tab.size(), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+      cudaMemsetAsync(s->key, 0xff, 16 * (size_t)g.nsite, s->stream) != cudaSuccess ||
+      cudaMemsetAsync(s->map, 0xff, 4 * (size_t)g.nsite, s->stream) != cudaSuccess ||
+      cudaMemsetAsync(s->ds, 0, sizeof(Dev4), s->stream) != cudaSuccess ||
+      cudaMemsetAsync(s->Mpix, 0, 8 * (size_t)g.n[0] * g.n[1], s->stream) != cudaSuccess ||
+      cudaStreamSynchronize(s->stream) != cudaSuccess)
+    st = VM_E_CUDA;
+  if (st == VM_OK) st = run_reset(s);
+  if (st != VM_OK) {
+    delete s;
+    return st;
+  }
+  *out = s;
+  return VM_OK;
+}
+
+void vm_4d_destroy(vm_4d_solver* s) {
+  if (!s) return;
+  cudaStreamSynchronize(s->stream);
+  delete s;
+}
+
+vm_status vm_4d_set_f(vm_4d_solver* s, const double* f, int on_device) {
+  if (!s || !f) return VM_E_INVALID_ARG;
+  const size_t b = 8 * (size_t)s->g.nsite;
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (cudaMemcpyAsync(s->fini, f, b, k, s->stream) != cudaSuccess ||
+      cudaMemcpyAsync(s->f, s->fini, b, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess ||
+      cudaMemcpyAsync(s->eta, s->fini, b, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess)
+    return VM_E_CUDA;
+  vm_status st = run_spline(s);
+  if (st) return st;
+  st = run_reset(s);
+  if (st) return st;
+  s->have_f = 1;
+  if (!on_device) return cuda_ok(cudaStreamSynchronize(s->stream));  // the host buffer may be reused
+  return VM_OK;
+}
+
+vm_status vm_4d_step(vm_4d_solver* s, int32_t nsteps) {
+  if (!s || nsteps < 0) return VM_E_INVALID_ARG;
+  if (!s->have_f) return VM_E_STATE;
+  const G4& g = s->g;
+  for (int32_t it = 0; it < nsteps; it++) {
+    k4_drift<<<blocks(g.ne, 128), 128, 0, s->stream>>>(g, s->el);
+    if (launched(s)) return VM_E_CUDA;
+    vm_status st = run_map(s);
+    if (st) return st;
+    st = run_recon(s);
+    if (st) return st;
+    k4_kick_drift<<<blocks(g.ne, 128), 128, 0, s->stream>>>(g, s->Mpix, s->gext, s->el);
+    if (launched(s)) return VM_E_CUDA;
+    if (++s->cyc >= s->n_s) {
+      st = run_remap(s);
+      if (st) return st;
+    }
+  }
+  return VM_OK;
+}
+
+vm_status vm_4d_reconstruct(vm_4d_solver* s) {
+  if (!s) return VM_E_INVALID_ARG;
+  if (!s->have_f) return VM_E_STATE;
+  vm_status st = run_map(s);
+  if (st) return st;
+  return run_recon(s);
+}
+
+vm_status vm_4d_remap(vm_4d_solver* s) {
+  if (!s) return VM_E_INVALID_ARG;
+  if (!s->have_f) return VM_E_STATE;
+  return run_remap(s);
+}
+
+vm_status vm_4d_read_f(vm_4d_solver* s, double* out, int on_device) {
+  if (!s) return VM_E_INVALID_ARG;
+  return copy_out(s, out, s->f, 8 * (size_t)s->g.nsite, on_device);
+}
+
+vm_status vm_4d_read_fini(vm_4d_solver* s, double* out, int on_device) {
+  if (!s) return VM_E_INVALID_ARG;
+  return copy_out(s, out, s->fini, 8 * (size_t)s->g.nsite, on_device);
+}
+
+vm_status vm_4d_read_eta(vm_4d_solver* s, double* out, int on_device) {
+  if (!s) return VM_E_INVALID_ARG;
+  return copy_out(s, out, s->eta, 8 * (size_t)s->g.nsite, on_device);
+}
+
+vm_status vm_4d_read_map(vm_4d_solver* s, int32_t* out, int on_device) {
+  if (!s) return VM_E_INVALID_ARG;
+  return copy_out(s, out, s->map, 4 * (size_t)s->g.nsite, on_device);
+}
+
+vm_status vm_4d_density_force(vm_4d_solver* s, double* M, double* field, int on_device) {
+  if (!s) return VM_E_INVALID_ARG;
+  const G4& g = s->g;
+  const size_t npix = (size_t)g.n[0] * g.n[1];
+  vm_status st = VM_OK;
+  if (M) st = copy_out(s, M, s->Mpix, 8 * npix, on_device);
+  if (st) return st;
+  if (field) {
+    k4_node_fields<<<blocks((long long)npix, 128), 128, 0, s->stream>>>(g, s->Mpix, s->gext, s->fld);
+    if (launched(s)) return VM_E_CUDA;
+    st = copy_out(s, field, s->fld, 8 * 12 * npix, on_device);
+  }
+  return st;
+}
+
+vm_status vm_4d_get_elements(vm_4d_solver* s, double* out, int on_device) {
+  if (!s) return VM_E_INVALID_ARG;
+  return copy_out(s, out, s->el, 8 * (size_t)NE4 * s->g.ne, on_device);
+}
+
+vm_status vm_4d_set_elements(vm_4d_solver* s, const double* in, int on_device) {
+  if (!s || !in) return VM_E_INVALID_ARG;
+  if (cudaMemcpyAsync(s->el, in, 8 * (size_t)NE4 * s->g.ne,
+                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+    return VM_E_CUDA;
+  return cuda_ok(cudaStreamSynchronize(s->stream));
+}
+
+int32_t vm_4d_num_elements(const vm_4d_solver* s, int32_t* L4) {
+  if (!s) return 0;
+  if (L4)
+    for (int a = 0; a < 4; a++) L4[a] = s->g.L[a];
+  return s->g.ne;
+}
+
+int64_t vm_4d_launches(const vm_4d_solver* s) { return s ? s->launches : 0; }
+
+vm_status vm_4d_sync(vm_4d_solver* s) {
+  if (!s) return VM_E_INVALID_ARG;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return VM_E_CUDA;
+  Dev4 h;
+  if (cudaMemcpy(&h, s->ds, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess) return VM_E_CUDA;
+  if (h.err == 0) return VM_OK;
+  const int32_t zero = 0;
+  if (cudaMemcpy(&s->ds->err, &zero, sizeof zero, cudaMemcpyHostToDevice) != cudaSuccess) return VM_E_CUDA;
+  if (h.err & ERR_INT) return VM_E_INTERNAL;
+  if (h.err & ERR_OVF) return VM_E_PATCH_OVERFLOW;
+  return VM_E_NOT_CONVERGED;
+}
+
+}  // extern "C"

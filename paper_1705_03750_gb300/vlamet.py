@@ -35,7 +35,12 @@ EXPORTS = ["vm_config_default", "vm_workspace_bytes", "vm_create", "vm_destroy",
            "vm_batch_autotune", "vm_batch_tuning",
            "vm_server_pool_bytes", "vm_server_create", "vm_server_submit", "vm_server_poll", "vm_server_result",
            "vm_server_stats", "vm_server_destroy",
-           "vm_last_cuda_error", "vm_cuda_error_name", "vm_save", "vm_load", "vm_measure_fp64_peak"]
+           "vm_last_cuda_error", "vm_cuda_error_name", "vm_save", "vm_load", "vm_measure_fp64_peak",
+           # include/vlamet4d.h
+           "vm_4d_workspace_bytes", "vm_4d_create", "vm_4d_destroy", "vm_4d_set_f", "vm_4d_step",
+           "vm_4d_reconstruct", "vm_4d_remap", "vm_4d_read_f", "vm_4d_read_fini", "vm_4d_read_eta",
+           "vm_4d_read_map", "vm_4d_density_force", "vm_4d_get_elements", "vm_4d_set_elements",
+           "vm_4d_num_elements", "vm_4d_launches", "vm_4d_sync"]
 
 VM_STATIC_FORCE_MAX_NX = 16384
 
@@ -145,6 +150,23 @@ def load() -> C.CDLL:
         "vm_save": (i32, [vp, C.c_char_p]),
         "vm_load": (i32, [vp, C.c_char_p]),
         "vm_measure_fp64_peak": (i32, [i32, vp, dp]),
+        "vm_4d_workspace_bytes": (C.c_size_t, [vp]),
+        "vm_4d_create": (i32, [vp, vp, C.c_size_t, vp, C.POINTER(vp)]),
+        "vm_4d_destroy": (None, [vp]),
+        "vm_4d_set_f": (i32, [vp, vp, i32]),
+        "vm_4d_step": (i32, [vp, i32]),
+        "vm_4d_reconstruct": (i32, [vp]),
+        "vm_4d_remap": (i32, [vp]),
+        "vm_4d_read_f": (i32, [vp, vp, i32]),
+        "vm_4d_read_fini": (i32, [vp, vp, i32]),
+        "vm_4d_read_eta": (i32, [vp, vp, i32]),
+        "vm_4d_read_map": (i32, [vp, vp, i32]),
+        "vm_4d_density_force": (i32, [vp, vp, vp, i32]),
+        "vm_4d_get_elements": (i32, [vp, vp, i32]),
+        "vm_4d_set_elements": (i32, [vp, vp, i32]),
+        "vm_4d_num_elements": (i32, [vp, C.POINTER(i32)]),
+        "vm_4d_launches": (i64, [vp]),
+        "vm_4d_sync": (i32, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
