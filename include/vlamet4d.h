@@ -111,6 +111,12 @@ vm_status vm_4d_set_elements(vm_4d_solver* s, const double* in, int on_device);
 int32_t vm_4d_num_elements(const vm_4d_solver* s, int32_t* L4);
 int64_t vm_4d_launches(const vm_4d_solver* s);
 
+/* Statistics of the last influence map (synchronises): out3[0] elements whose
+ * component outgrew the shared-memory flood window of side 2*min(2s, 12)+1
+ * and were filled again over the whole padded lattice, out3[1] unexplored
+ * sites left by the percolation, out3[2] repair rounds (Sec. 2.3.1). */
+vm_status vm_4d_map_stats(vm_4d_solver* s, int32_t* out3);
+
 /* Wait for the solver's stream and report (and clear) its error word:
  * VM_E_NOT_CONVERGED (hole repair hit its cap), VM_E_PATCH_OVERFLOW (one
  * breadth-first wave of an element's whole-lattice flood fill held more than

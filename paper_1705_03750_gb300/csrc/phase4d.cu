@@ -74,6 +74,7 @@ struct Dev4 {
   int32_t nholes;
   int32_t bad_where;
   int32_t novf;  // elements whose component left the shared-memory window (this map)
+  int32_t rounds;  // hole-repair rounds of the last map
 };
 
 // whole-lattice flood fill of the elements that left their window: per slot,
@@ -577,6 +578,7 @@ __global__ void __launch_bounds__(1024) k4_holes(G4 g, const double* __restrict_
                                                  Dev4* ds) {
   __shared__ int remaining;
   const int nh = ds->nholes;
+  if (threadIdx.x == 0) ds->rounds = 0;
   if (nh == 0) return;
   int rounds = 0;
   while (true) {
@@ -626,6 +628,7 @@ __global__ void __launch_bounds__(1024) k4_holes(G4 g, const double* __restrict_
     __syncthreads();
     rounds++;
     const int rem = remaining;
+    if (threadIdx.x == 0) ds->rounds = rounds;
     __syncthreads();
     if (rem == 0) break;
     if (rounds >= g.max_rounds) {
@@ -1451,6 +1454,17 @@ int32_t vm_4d_num_elements(const vm_4d_solver* s, int32_t* L4) {
 }
 
 int64_t vm_4d_launches(const vm_4d_solver* s) { return s ? s->launches : 0; }
+
+vm_status vm_4d_map_stats(vm_4d_solver* s, int32_t* out3) {
+  if (!s || !out3) return VM_E_INVALID_ARG;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return VM_E_CUDA;
+  Dev4 h;
+  if (cudaMemcpy(&h, s->ds, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess) return VM_E_CUDA;
+  out3[0] = h.novf;
+  out3[1] = h.nholes;
+  out3[2] = h.rounds;
+  return VM_OK;
+}
 
 vm_status vm_4d_sync(vm_4d_solver* s) {
   if (!s) return VM_E_INVALID_ARG;

@@ -105,6 +105,11 @@ class Solver4D:
     def remap(self) -> None:
         V._check(self.L.vm_4d_remap(self.h), "vm_4d_remap")
 
+    def map_stats(self) -> dict:
+        out = (C.c_int32 * 3)()
+        V._check(self.L.vm_4d_map_stats(self.h, out), "vm_4d_map_stats")
+        return {"window_overflows": int(out[0]), "holes": int(out[1]), "rounds": int(out[2])}
+
     def sync(self) -> None:
         V._check(self.L.vm_4d_sync(self.h), "vm_4d_sync")
 

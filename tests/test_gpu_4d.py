@@ -25,7 +25,7 @@ def _pair(rc):
     return s, o, f0
 
 
-def _distort(o, rc, seed=7, amp=0.15, hamp=0.3, disp=0.2):
+def _distort(o, rc, seed=7, amp=0.1, hamp=0.05, disp=0.2):
     el = o.elements()
     rng = np.random.default_rng(seed)
     dm = np.array(rc.d) * rc.s
@@ -69,6 +69,22 @@ def test_map_and_reconstruction_on_a_distorted_state(name):
     assert (np.abs(dg["field"] - do["field"]).max(axis=(0, 1)) <= 1e-10 * scale).all()
 
 
+def test_components_larger_than_the_window_are_filled_over_the_whole_lattice():
+    # a strong second-order term stretches components far beyond the
+    # shared-memory window; those elements take the whole-lattice pass
+    rc = I4.HALOS4D_16.with_(n=(9, 8, 10, 9), s=3)
+    s, o, f0 = _pair(rc)
+    el = _distort(o, rc, amp=0.15, hamp=0.3, disp=0.2)
+    o.set_elements(el)
+    s.set_elements(el)
+    fo = o.reconstruct()
+    s.reconstruct()
+    s.sync()
+    assert s.map_stats()["window_overflows"] > 0
+    assert (s.read_map() == o.last_map()).all()
+    assert np.abs(s.read_f() - fo).max() <= 1e-12 * np.abs(fo).max()
+
+
 @pytest.mark.parametrize("distort", [False, True])
 def test_holes_are_repaired_like_the_oracle(distort):
     # a one-site connectivity margin keeps the outer elements from
@@ -88,6 +104,8 @@ def test_holes_are_repaired_like_the_oracle(distort):
     assert o.map_stats()["holes"] > 0
     s.reconstruct()
     s.sync()
+    st = s.map_stats()
+    assert st["holes"] == o.map_stats()["holes"] and st["rounds"] == o.map_stats()["rounds"]
     assert (s.read_map() == o.last_map()).all()
     assert np.abs(s.read_f() - fo).max() <= 1e-12 * np.abs(fo).max()
 
