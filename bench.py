@@ -533,6 +533,8 @@ def run_native(args, rank: int, world: int, dist):
         line["cpu_baseline"] = cpu_baseline(rc, f0)
     if world == 1 and not args.no_serve:
         line["serving"] = serve_sample(args)
+    if world == 1 and not args.no_4d:
+        line["phase4d"] = phase4d_run(args, dev, peaks)
     return line
 
 
@@ -595,6 +597,137 @@ def run_reference(args, rank: int):
 # ---------------------------------------------------------------------------
 # other workloads (their own JSON lines; not the headline)
 # ---------------------------------------------------------------------------
+
+# FP64 operations per unit of work of the 4D kernels, counted from the code:
+# one inverse-map evaluation Q(P) is 208 (dP 4, s_l 4 x 35, y 28, T^-1 s 28,
+# dQ 8); a distance d^2 adds 11; the 15-point interpolation with its
+# coordinates adds 97 per reconstructed site
+FLOP4_D2 = 219
+FLOP4_SITE = 305
+
+
+def phase4d_run(args, dev, peaks, fp64_peak=None) -> dict:
+    """The 4D phase-space path (2D space) on its 64^4 halo workload: K steps
+    device-timed after the warm-up (remaps at their cadence inside), a
+    profiled pass over the same step indices for the kernel shares and the
+    roofline of the dominant kernel, an end-to-end pass through the C ABI
+    with host buffers, and the FP64 oracle on a bounded sample."""
+    import torch
+    from paper_1705_03750_gb300 import inputs4d as I4
+    from paper_1705_03750_gb300 import vlamet as V
+    from paper_1705_03750_gb300 import vlamet4d as V4
+    rc = I4.HALOS4D_64
+    K, W = args.steps4d, max(3, args.warmup4d)
+    f0 = I4.initial_f4(rc)
+    f0_dev = torch.from_numpy(f0).to(dev)
+    sites = rc.sites
+    s = V4.Solver4D(V4.config(rc))
+    s.set_f(f0_dev)
+    s.step(W)
+    s.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = s.launches
+    torch.cuda.synchronize(dev)
+    e0.record(s.stream)
+    s.step(K)
+    e1.record(s.stream)
+    torch.cuda.synchronize(dev)
+    s.sync()
+    ms = e0.elapsed_time(e1)
+    launches = s.launches - l0
+    del s
+    # profiled pass over the same step indices
+    s = V4.Solver4D(V4.config(rc))
+    s.set_f(f0_dev)
+    s.step(W)
+    s.sync()
+    ev0 = s.map_stats()["d2_evals"]
+    s.profile(True)
+    s.step(K)
+    stats = s.profile_read()
+    s.profile(False)
+    ev1 = s.map_stats()["d2_evals"]
+    s.sync()
+    del s
+    if fp64_peak is None:
+        fp64_peak = V.measure_fp64_peak()
+    total = sum(v[1] for v in stats.values())
+    dom = max(stats, key=lambda k: stats[k][1])
+    nl, tms = stats[dom]
+    roof = {"kernel": dom, "launches_per_step": nl / K, "avg_ms": tms / nl, "share_of_step": tms / total}
+    if dom in ("percolate", "reconstruct"):
+        if dom == "percolate":
+            flop = FLOP4_D2 * (ev1 - ev0) / nl
+            per, units = f"{FLOP4_D2} FP64 FLOP per distance evaluation", (ev1 - ev0) / nl
+        else:
+            flop = FLOP4_SITE * sites
+            per, units = f"{FLOP4_SITE} FP64 FLOP per site", sites
+        ach = flop / (tms / nl / 1e3) / 1e12
+        roof.update({"bound": "alu", "achieved": ach, "peak": fp64_peak / 1e12, "unit": "TFLOP/s (FP64)",
+                     "frac": ach / (fp64_peak / 1e12), "per_unit": per, "units": units,
+                     "peak_kind": "measured in this run (FP64 FMA chains)"})
+    # end to end through the C ABI with host buffers over the same step
+    # indices: upload of f0 from pinned host memory, then every timed step
+    # reads the pixel masses back to the host
+    f0_pin = torch.from_numpy(f0).pin_memory()
+    M_host = torch.empty((rc.n[0], rc.n[1]), dtype=torch.float64).pin_memory()
+    s = V4.Solver4D(V4.config(rc))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    s.set_f(f0_pin.numpy())
+    up = time.perf_counter() - t0
+    s.step(W)
+    s.sync()
+    t1 = time.perf_counter()
+    Mh = M_host.numpy()
+    for _ in range(K):
+        s.step(1)
+        V._check(s.L.vm_4d_density_force(s.h, ctypes.c_void_p(Mh.ctypes.data), None, 0), "vm_4d_density_force")
+    t2 = time.perf_counter()
+    e2e = {"value": sites * K / (up + (t2 - t1)), "unit": "cell-updates/s",
+           "h2d_bytes_per_step": f0.nbytes / K, "d2h_bytes_per_step": 8 * rc.n[0] * rc.n[1],
+           "what": f"vm_4d_set_f from pinned host f0 (timed), {W} untimed steps, then {K} steps each with "
+                   "vm_4d_density_force to host (timed)"}
+    del s
+    out = {"workload": rc.name, "sites": sites, "elem_stride": rc.s, "elements": None, "dt": rc.dt, "n_s": rc.n_s,
+           "G": rc.G, "steps": K, "warmup": W, "remaps_in_timed_steps": (W + K) // rc.n_s - W // rc.n_s,
+           "value": sites * K / (ms / 1e3), "unit": "cell-updates/s", "ms_per_step": ms / K, "dtype": "f64",
+           "gpu_launches": launches, "e2e": e2e, "roofline": roof,
+           "kernels": {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in sorted(stats.items(), key=lambda kv: -kv[1][1])}}
+    L4 = 1
+    for a in range(4):
+        L4 *= 2 * ((rc.n[a] - 1 + 2 * rc.s - 1) // (2 * rc.s)) + 3
+    out["elements"] = L4
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_4d(rc, f0)
+    return out
+
+
+def cpu_baseline_4d(rc, f0) -> dict:
+    """The FP64 4D oracle (serial) on a bounded sample of the same workload:
+    one transport reconstruction (map, f, pixel masses, field) of the 64^4
+    state at t = 0; rate = sites / that time."""
+    import oracle.oracle4d as Q4
+    o = Q4.Oracle4D.from_run(rc)
+    o.set_f(f0)
+    t0 = time.perf_counter()
+    o.reconstruct()
+    dt = time.perf_counter() - t0
+    return {"value": rc.sites / dt, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{rc.name}: one transport reconstruction (map, f, pixel masses, field) timed ({dt:.1f} s)"}
+
+
+def run_phase4d(args):
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    peaks, _ = _peaks()
+    line = phase4d_run(args, dev, peaks)
+    line.update({"metric": "cell-updates/s of the 4D phase-space (2D space) path", "n_gpus": 1,
+                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                 "data": "synthetic (seeded 4-halo 4D initial condition)",
+                 "config": {"workload": line["workload"], "l2": "working set > L2 (129 MB): no flush"}})
+    return line
 
 def run_precision(args):
     """8192^2 halos: FP32-mixed vs FP64 GPU paths over many steps (f
@@ -853,7 +986,7 @@ def main():
     ap.add_argument("--whole-run-fp32-only", action="store_true")
     ap.add_argument("--ref-cap", type=int, default=20)
     ap.add_argument("--workload", default="halos4096",
-                    choices=["halos4096", "precision8192", "batch", "batch-classes", "serve"])
+                    choices=["halos4096", "precision8192", "batch", "batch-classes", "serve", "phase4d"])
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--streams", type=int, default=0, help="(unused: one launch per phase for the batch)")
     ap.add_argument("--autotune", type=int, default=1, help="tune the batch's launch shapes on its first steps")
@@ -867,6 +1000,9 @@ def main():
     ap.add_argument("--emap", type=float, default=0.5,
                     help="serving runs: each request also remaps when its map's E_map exceeds this many "
                          "element spacings (0: every n_s steps only)")
+    ap.add_argument("--no-4d", action="store_true", help="skip the 4D phase-space sample")
+    ap.add_argument("--steps4d", type=int, default=20, help="timed steps of the 4D phase-space sample")
+    ap.add_argument("--warmup4d", type=int, default=3)
     ap.add_argument("--spin", type=float, default=2.0, help="seconds of untimed steps before the warm-up")
     ap.add_argument("--clock-log", default=None, help="path prefix for the raw clock samples (CSV) of each timed region")
     args = ap.parse_args()
@@ -874,7 +1010,7 @@ def main():
         from paper_1705_03750_gb300 import build as B
         B.build()
         fn = {"precision8192": run_precision, "batch": run_batch, "batch-classes": run_batch_classes,
-              "serve": run_serve}[args.workload]
+              "serve": run_serve, "phase4d": run_phase4d}[args.workload]
         print(json.dumps(fn(args)))
         return
     if args.warmup < 3:

@@ -114,8 +114,18 @@ int64_t vm_4d_launches(const vm_4d_solver* s);
 /* Statistics of the last influence map (synchronises): out3[0] elements whose
  * component outgrew the shared-memory flood window of side 2*min(2s, 12)+1
  * and were filled again over the whole padded lattice, out3[1] unexplored
- * sites left by the percolation, out3[2] repair rounds (Sec. 2.3.1). */
-vm_status vm_4d_map_stats(vm_4d_solver* s, int32_t* out3);
+ * sites left by the percolation, out3[2] repair rounds (Sec. 2.3.1);
+ * *d2_evals (may be NULL): distance evaluations d^2 = |Q(P) - Q_m|^2 of the
+ * percolation tests since creation, 219 FP64 operations each. */
+vm_status vm_4d_map_stats(vm_4d_solver* s, int32_t* out3, int64_t* d2_evals);
+
+/* Per-kernel timing: while on, CUDA events on the solver's stream bracket
+ * every launch; vm_4d_profile_read (synchronises) writes, per kernel id
+ * 0..n-1 (names from vm_4d_kernel_name), the launches and milliseconds since
+ * the last read, and returns the number of kernel ids. */
+vm_status vm_4d_profile(vm_4d_solver* s, int on);
+int32_t vm_4d_profile_read(vm_4d_solver* s, int64_t* launches, double* ms, int32_t nmax);
+const char* vm_4d_kernel_name(int32_t id);
 
 /* Wait for the solver's stream and report (and clear) its error word:
  * VM_E_NOT_CONVERGED (hole repair hit its cap), VM_E_PATCH_OVERFLOW (one

@@ -75,6 +75,7 @@ struct Dev4 {
   int32_t bad_where;
   int32_t novf;  // elements whose component left the shared-memory window (this map)
   int32_t rounds;  // hole-repair rounds of the last map
+  unsigned long long d2_evals;  // distance evaluations of the percolation kernels (cumulative)
 };
 
 // whole-lattice flood fill of the elements that left their window: per slot,
@@ -282,10 +283,11 @@ __device__ __forceinline__ void claim4(ulonglong2* key, unsigned long long dbits
 // of the alpha ranges (per axis: below -alpha {-1,0}, below alpha {0}, else
 // {0,1}) proposes a strictly smaller distance.
 __device__ bool passes4(const G4& g, const int* k, const double* tself, const double* __restrict__ tay,
-                        const double* P, double* d2o) {
+                        const double* P, double* d2o, unsigned& nev) {
   double x[4];
   const double d2 = dist2_4(g, tself, P, x);
   *d2o = d2;
+  nev++;
   int lo[4], hi[4];
   for (int a = 0; a < 4; a++) {
     if (x[a] < -g.alpha) {
@@ -309,6 +311,7 @@ __device__ bool passes4(const G4& g, const int* k, const double* tself, const do
               k3 >= g.L[3])
             continue;
           const int mm = ((k0 * g.L[1] + k1) * g.L[2] + k2) * g.L[3] + k3;
+          nev++;
           if (dist2_4(g, tay + (size_t)NT4 * mm, P, nullptr) < d2) return false;
         }
   return true;
@@ -334,6 +337,7 @@ __global__ void __launch_bounds__(256) k4_percolate(G4 g, const double* __restri
   __shared__ int go, ncur, nnext, ovf;
   const int m = blockIdx.x;
   const int tid = threadIdx.x;
+  unsigned nev = 0;
   if (tid < NT4) tself[tid] = tay[(size_t)NT4 * m + tid];
   for (int w = tid; w < nwords; w += blockDim.x) stamp[w] = 0u;
   if (tid == 0) {
@@ -368,7 +372,7 @@ __global__ void __launch_bounds__(256) k4_percolate(G4 g, const double* __restri
       gs[a] = org[a] + c;
       P[a] = site_coord(g, a, gs[a]);
     }
-    if (passes4(g, kk, tself, tay, P, &d2)) {
+    if (passes4(g, kk, tself, tay, P, &d2, nev)) {
       bool in = true;
       long long p = 0;
       for (int a = 0; a < 4; a++) {
@@ -414,7 +418,7 @@ __global__ void __launch_bounds__(256) k4_percolate(G4 g, const double* __restri
         gs[a] = (long long)org[a] + l[a];
         P[a] = site_coord(g, a, gs[a]);
       }
-      if (!passes4(g, kl, tself, tay, P, &d2)) continue;
+      if (!passes4(g, kl, tself, tay, P, &d2, nev)) continue;
       bool in = true;
       long long p = 0;
       for (int a = 0; a < 4; a++) {
@@ -437,6 +441,8 @@ __global__ void __launch_bounds__(256) k4_percolate(G4 g, const double* __restri
   // element is filled again over the whole padded lattice (its claims so far
   // are a subset of the full component's, with the same keys)
   if (tid == 0 && ovf) ovf_list[atomicAdd(&ds->novf, 1)] = m;
+  for (int o = 16; o > 0; o >>= 1) nev += __shfl_down_sync(0xffffffffu, nev, o);
+  if ((tid & 31) == 0 && nev) atomicAdd(&ds->d2_evals, (unsigned long long)nev);
 }
 
 // Whole-lattice flood fill of the listed elements: the same breadth-first
@@ -461,6 +467,7 @@ __global__ void __launch_bounds__(256) k4_percolate_big(G4 g, const double* __re
   int32_t* front0 = (int32_t*)(stamp + ((nwords + 63) & ~63ll));
   int32_t* front1 = front0 + BIG_FCAP;
   const int tid = threadIdx.x;
+  unsigned nev = 0;
   for (int it = blockIdx.x; it < nlist; it += gridDim.x) {
     const int m = ovf_list[it];
     __syncthreads();
@@ -522,7 +529,7 @@ __global__ void __launch_bounds__(256) k4_percolate_big(G4 g, const double* __re
           gs[a] = gl[a] - g.pad;
           P[a] = site_coord(g, a, gs[a]);
         }
-        if (!passes4(g, kl, tself, tay, P, &d2)) continue;
+        if (!passes4(g, kl, tself, tay, P, &d2, nev)) continue;
         bool in = true;
         long long p = 0;
         for (int a = 0; a < 4; a++) {
@@ -545,6 +552,8 @@ __global__ void __launch_bounds__(256) k4_percolate_big(G4 g, const double* __re
       __syncthreads();
     }
   }
+  for (int o = 16; o > 0; o >>= 1) nev += __shfl_down_sync(0xffffffffu, nev, o);
+  if ((tid & 31) == 0 && nev) atomicAdd(&ds->d2_evals, (unsigned long long)nev);
 }
 
 // owner of every site from its key (the key is emptied for the next map);
@@ -1054,8 +1063,22 @@ __global__ void k4_spline_axis(G4 g, int ax, const double* __restrict__ tab, dou
 // host side
 // ---------------------------------------------------------------------------
 
+namespace {
+enum K4Id { K_DRIFT, K_TAYLOR, K_PERC, K_PERC_BIG, K_FINISH, K_HOLES, K_RECON, K_ACCEL, K_ACCEL_SUM, K_KICK,
+            K_RESAMPLE, K_SPLINE, K_RESET, K_FIELDS, K_COUNT };
+const char* const k4_names[K_COUNT] = {"drift", "taylor", "percolate", "percolate_big", "map_finish", "holes",
+                                       "reconstruct", "accel", "accel_sum", "kick_drift", "resample", "spline_axis",
+                                       "reset", "node_fields"};
+struct ProfRec {
+  int id;
+  cudaEvent_t a, b;
+};
+}  // namespace
+
 struct vm_4d_solver {
   G4 g;
+  bool profiling;
+  std::vector<ProfRec> prof;
   cudaStream_t stream;
   char* ws;
   double *fini, *eta, *f, *el, *tay, *Mpix, *fld, *tab;
@@ -1199,33 +1222,51 @@ vm_status launched(vm_4d_solver* s) {
   return cuda_ok(cudaGetLastError());
 }
 
+// per-launch events on the solver's stream while profiling is on
+void prof_begin(vm_4d_solver* s, cudaEvent_t* a) {
+  *a = nullptr;
+  if (!s->profiling) return;
+  if (cudaEventCreate(a) == cudaSuccess) cudaEventRecord(*a, s->stream);
+}
+void prof_end(vm_4d_solver* s, int id, cudaEvent_t a) {
+  if (!s->profiling || !a) return;
+  cudaEvent_t b;
+  if (cudaEventCreate(&b) != cudaSuccess) return;
+  cudaEventRecord(b, s->stream);
+  s->prof.push_back({id, a, b});
+}
+
+#define K4_LAUNCH(s, id, ...)          \
+  do {                                 \
+    cudaEvent_t ev_;                   \
+    prof_begin((s), &ev_);             \
+    __VA_ARGS__;                       \
+    prof_end((s), (id), ev_);          \
+    if (launched(s)) return VM_E_CUDA; \
+  } while (0)
+
 vm_status run_map(vm_4d_solver* s) {
   const G4& g = s->g;
-  k4_taylor<<<blocks(g.ne, 128), 128, 0, s->stream>>>(g, s->el, s->tay);
-  if (launched(s)) return VM_E_CUDA;
+  K4_LAUNCH(s, K_TAYLOR, k4_taylor<<<blocks(g.ne, 128), 128, 0, s->stream>>>(g, s->el, s->tay));
   if (cudaMemsetAsync(&s->ds->nholes, 0, sizeof(int32_t), s->stream) != cudaSuccess ||
       cudaMemsetAsync(&s->ds->novf, 0, sizeof(int32_t), s->stream) != cudaSuccess)
     return VM_E_CUDA;
-  k4_percolate<<<g.ne, 256, s->smem, s->stream>>>(g, s->el, s->tay, s->key, s->ovf_list, s->ds);
-  if (launched(s)) return VM_E_CUDA;
+  K4_LAUNCH(s, K_PERC, k4_percolate<<<g.ne, 256, s->smem, s->stream>>>(g, s->el, s->tay, s->key, s->ovf_list, s->ds));
   // returns at once when no element left its window
-  k4_percolate_big<<<BIG_SLOTS, 256, 0, s->stream>>>(g, s->el, s->tay, s->key, s->ovf_list, s->big, s->ds);
-  if (launched(s)) return VM_E_CUDA;
-  k4_map_finish<<<blocks(g.nsite, 256), 256, 0, s->stream>>>(g, s->key, s->map, s->holes, s->ds);
-  if (launched(s)) return VM_E_CUDA;
-  k4_holes<<<1, 1024, 0, s->stream>>>(g, s->tay, s->map, s->holes, s->cand, s->ds);
-  return launched(s);
+  K4_LAUNCH(s, K_PERC_BIG,
+            k4_percolate_big<<<BIG_SLOTS, 256, 0, s->stream>>>(g, s->el, s->tay, s->key, s->ovf_list, s->big, s->ds));
+  K4_LAUNCH(s, K_FINISH, k4_map_finish<<<blocks(g.nsite, 256), 256, 0, s->stream>>>(g, s->key, s->map, s->holes, s->ds));
+  K4_LAUNCH(s, K_HOLES, k4_holes<<<1, 1024, 0, s->stream>>>(g, s->tay, s->map, s->holes, s->cand, s->ds));
+  return VM_OK;
 }
 
 vm_status run_recon(vm_4d_solver* s) {
   const G4& g = s->g;
-  k4_recon<<<g.n[0] * g.n[1], 256, 0, s->stream>>>(g, s->tay, s->map, s->fini, s->f, s->Mpix, s->ds);
-  if (launched(s)) return VM_E_CUDA;
+  K4_LAUNCH(s, K_RECON, k4_recon<<<g.n[0] * g.n[1], 256, 0, s->stream>>>(g, s->tay, s->map, s->fini, s->f, s->Mpix, s->ds));
   const int nodes = g.We0 * g.We1;
-  k4_accel<<<dim3(blocks(nodes, 256), s->nchunk), 256, 0, s->stream>>>(g, s->Mpix, s->part);
-  if (launched(s)) return VM_E_CUDA;
-  k4_accel_sum<<<blocks(nodes, 256), 256, 0, s->stream>>>(g, s->part, s->nchunk, s->gext);
-  return launched(s);
+  K4_LAUNCH(s, K_ACCEL, k4_accel<<<dim3(blocks(nodes, 256), s->nchunk), 256, 0, s->stream>>>(g, s->Mpix, s->part));
+  K4_LAUNCH(s, K_ACCEL_SUM, k4_accel_sum<<<blocks(nodes, 256), 256, 0, s->stream>>>(g, s->part, s->nchunk, s->gext));
+  return VM_OK;
 }
 
 vm_status run_spline(vm_4d_solver* s) {
@@ -1233,16 +1274,16 @@ vm_status run_spline(vm_4d_solver* s) {
   int nmax = 0;
   for (int a = 0; a < 4; a++) nmax = std::max(nmax, g.n[a]);
   for (int a = 3; a >= 0; a--) {
-    k4_spline_axis<<<blocks(g.nsite / g.n[a], 128), 128, 0, s->stream>>>(g, a, s->tab + 3 * (size_t)nmax * a, s->eta);
-    if (launched(s)) return VM_E_CUDA;
+    K4_LAUNCH(s, K_SPLINE,
+              k4_spline_axis<<<blocks(g.nsite / g.n[a], 128), 128, 0, s->stream>>>(g, a, s->tab + 3 * (size_t)nmax * a, s->eta));
   }
   return VM_OK;
 }
 
 vm_status run_reset(vm_4d_solver* s) {
-  k4_reset<<<blocks(s->g.ne, 128), 128, 0, s->stream>>>(s->g, s->el);
   s->cyc = 0;
-  return launched(s);
+  K4_LAUNCH(s, K_RESET, k4_reset<<<blocks(s->g.ne, 128), 128, 0, s->stream>>>(s->g, s->el));
+  return VM_OK;
 }
 
 vm_status run_remap(vm_4d_solver* s) {
@@ -1250,8 +1291,7 @@ vm_status run_remap(vm_4d_solver* s) {
   vm_status st = run_map(s);
   if (st) return st;
   // f_ini <- spline(f_ini)(Q_r): the resample reads eta only
-  k4_resample<<<blocks(g.nsite, 128), 128, 0, s->stream>>>(g, s->tay, s->map, s->eta, s->fini, s->ds);
-  if (launched(s)) return VM_E_CUDA;
+  K4_LAUNCH(s, K_RESAMPLE, k4_resample<<<blocks(g.nsite, 128), 128, 0, s->stream>>>(g, s->tay, s->map, s->eta, s->fini, s->ds));
   if (cudaMemcpyAsync(s->eta, s->fini, 8 * (size_t)g.nsite, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess)
     return VM_E_CUDA;
   st = run_spline(s);
@@ -1343,6 +1383,10 @@ vm_status vm_4d_create(const vm_4d_config* c, void* d_ws, size_t bytes, void* st
 void vm_4d_destroy(vm_4d_solver* s) {
   if (!s) return;
   cudaStreamSynchronize(s->stream);
+  for (const ProfRec& r : s->prof) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
   delete s;
 }
 
@@ -1368,14 +1412,12 @@ vm_status vm_4d_step(vm_4d_solver* s, int32_t nsteps) {
   if (!s->have_f) return VM_E_STATE;
   const G4& g = s->g;
   for (int32_t it = 0; it < nsteps; it++) {
-    k4_drift<<<blocks(g.ne, 128), 128, 0, s->stream>>>(g, s->el);
-    if (launched(s)) return VM_E_CUDA;
+    K4_LAUNCH(s, K_DRIFT, k4_drift<<<blocks(g.ne, 128), 128, 0, s->stream>>>(g, s->el));
     vm_status st = run_map(s);
     if (st) return st;
     st = run_recon(s);
     if (st) return st;
-    k4_kick_drift<<<blocks(g.ne, 128), 128, 0, s->stream>>>(g, s->Mpix, s->gext, s->el);
-    if (launched(s)) return VM_E_CUDA;
+    K4_LAUNCH(s, K_KICK, k4_kick_drift<<<blocks(g.ne, 128), 128, 0, s->stream>>>(g, s->Mpix, s->gext, s->el));
     if (++s->cyc >= s->n_s) {
       st = run_remap(s);
       if (st) return st;
@@ -1426,8 +1468,7 @@ vm_status vm_4d_density_force(vm_4d_solver* s, double* M, double* field, int on_
   if (M) st = copy_out(s, M, s->Mpix, 8 * npix, on_device);
   if (st) return st;
   if (field) {
-    k4_node_fields<<<blocks((long long)npix, 128), 128, 0, s->stream>>>(g, s->Mpix, s->gext, s->fld);
-    if (launched(s)) return VM_E_CUDA;
+    K4_LAUNCH(s, K_FIELDS, k4_node_fields<<<blocks((long long)npix, 128), 128, 0, s->stream>>>(g, s->Mpix, s->gext, s->fld));
     st = copy_out(s, field, s->fld, 8 * 12 * npix, on_device);
   }
   return st;
@@ -1455,7 +1496,7 @@ int32_t vm_4d_num_elements(const vm_4d_solver* s, int32_t* L4) {
 
 int64_t vm_4d_launches(const vm_4d_solver* s) { return s ? s->launches : 0; }
 
-vm_status vm_4d_map_stats(vm_4d_solver* s, int32_t* out3) {
+vm_status vm_4d_map_stats(vm_4d_solver* s, int32_t* out3, int64_t* d2_evals) {
   if (!s || !out3) return VM_E_INVALID_ARG;
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return VM_E_CUDA;
   Dev4 h;
@@ -1463,8 +1504,39 @@ vm_status vm_4d_map_stats(vm_4d_solver* s, int32_t* out3) {
   out3[0] = h.novf;
   out3[1] = h.nholes;
   out3[2] = h.rounds;
+  if (d2_evals) *d2_evals = (int64_t)h.d2_evals;
   return VM_OK;
 }
+
+vm_status vm_4d_profile(vm_4d_solver* s, int on) {
+  if (!s) return VM_E_INVALID_ARG;
+  s->profiling = on != 0;
+  return VM_OK;
+}
+
+int32_t vm_4d_profile_read(vm_4d_solver* s, int64_t* launches, double* ms, int32_t nmax) {
+  if (!s) return 0;
+  cudaStreamSynchronize(s->stream);
+  const int n = std::min<int>(K_COUNT, nmax);
+  for (int i = 0; i < n; i++) {
+    if (launches) launches[i] = 0;
+    if (ms) ms[i] = 0.0;
+  }
+  for (const ProfRec& r : s->prof) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, r.a, r.b);
+    if (r.id < n) {
+      if (launches) launches[r.id]++;
+      if (ms) ms[r.id] += t;
+    }
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  s->prof.clear();
+  return K_COUNT;
+}
+
+const char* vm_4d_kernel_name(int32_t id) { return (id >= 0 && id < K_COUNT) ? k4_names[id] : nullptr; }
 
 vm_status vm_4d_sync(vm_4d_solver* s) {
   if (!s) return VM_E_INVALID_ARG;

@@ -40,7 +40,8 @@ EXPORTS = ["vm_config_default", "vm_workspace_bytes", "vm_create", "vm_destroy",
            "vm_4d_workspace_bytes", "vm_4d_create", "vm_4d_destroy", "vm_4d_set_f", "vm_4d_step",
            "vm_4d_reconstruct", "vm_4d_remap", "vm_4d_read_f", "vm_4d_read_fini", "vm_4d_read_eta",
            "vm_4d_read_map", "vm_4d_density_force", "vm_4d_get_elements", "vm_4d_set_elements",
-           "vm_4d_num_elements", "vm_4d_launches", "vm_4d_map_stats", "vm_4d_sync"]
+           "vm_4d_num_elements", "vm_4d_launches", "vm_4d_map_stats", "vm_4d_sync",
+           "vm_4d_profile", "vm_4d_profile_read", "vm_4d_kernel_name"]
 
 VM_STATIC_FORCE_MAX_NX = 16384
 
@@ -166,7 +167,10 @@ def load() -> C.CDLL:
         "vm_4d_set_elements": (i32, [vp, vp, i32]),
         "vm_4d_num_elements": (i32, [vp, C.POINTER(i32)]),
         "vm_4d_launches": (i64, [vp]),
-        "vm_4d_map_stats": (i32, [vp, C.POINTER(i32)]),
+        "vm_4d_map_stats": (i32, [vp, C.POINTER(i32), C.POINTER(i64)]),
+        "vm_4d_profile": (i32, [vp, i32]),
+        "vm_4d_profile_read": (i32, [vp, C.POINTER(i64), dp, i32]),
+        "vm_4d_kernel_name": (C.c_char_p, [i32]),
         "vm_4d_sync": (i32, [vp]),
     }
     for name, (res, args) in sig.items():

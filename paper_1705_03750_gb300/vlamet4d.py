@@ -107,8 +107,25 @@ class Solver4D:
 
     def map_stats(self) -> dict:
         out = (C.c_int32 * 3)()
-        V._check(self.L.vm_4d_map_stats(self.h, out), "vm_4d_map_stats")
-        return {"window_overflows": int(out[0]), "holes": int(out[1]), "rounds": int(out[2])}
+        ev = C.c_int64()
+        V._check(self.L.vm_4d_map_stats(self.h, out, C.byref(ev)), "vm_4d_map_stats")
+        return {"window_overflows": int(out[0]), "holes": int(out[1]), "rounds": int(out[2]),
+                "d2_evals": int(ev.value)}
+
+    def profile(self, on: bool) -> None:
+        V._check(self.L.vm_4d_profile(self.h, int(bool(on))), "vm_4d_profile")
+
+    def profile_read(self) -> dict:
+        """{kernel name: (launches, ms)} since the last read (synchronises)."""
+        n = 32
+        la = (C.c_int64 * n)()
+        ms = (C.c_double * n)()
+        k = int(self.L.vm_4d_profile_read(self.h, la, ms, n))
+        out = {}
+        for i in range(min(k, n)):
+            if la[i]:
+                out[self.L.vm_4d_kernel_name(i).decode()] = (int(la[i]), float(ms[i]))
+        return out
 
     def sync(self) -> None:
         V._check(self.L.vm_4d_sync(self.h), "vm_4d_sync")
