@@ -53,7 +53,9 @@ namespace {
 
 constexpr int NE4 = 60;  // doubles per element
 constexpr int NT4 = 64;  // doubles per Taylor record
-constexpr int FCAP = 4096;  // frontier capacity of the flood fill (sites per wave)
+constexpr int FCAP = 1024;  // frontier capacity of the flood fill (sites per wave)
+constexpr int PERC_THREADS = 64;  // one block of two warps per element
+static_assert(PERC_THREADS >= NT4, "a block loads its element's Taylor record one value per thread");
 constexpr int ERR_NC = 1, ERR_OVF = 2, ERR_INT = 4;
 constexpr unsigned long long KEY_EMPTY = ~0ull;
 
@@ -322,7 +324,7 @@ __device__ bool passes4(const G4& g, const int* k, const double* tself, const do
 // explored wave by wave inside a window of side W around the start site.  An
 // element whose component would leave the window, or whose wave outgrows the
 // frontier buffer, is listed for k4_percolate_big.
-__global__ void __launch_bounds__(256) k4_percolate(G4 g, const double* __restrict__ el,
+__global__ void __launch_bounds__(PERC_THREADS) k4_percolate(G4 g, const double* __restrict__ el,
                                                     const double* __restrict__ tay, ulonglong2* __restrict__ key,
                                                     int32_t* __restrict__ ovf_list, Dev4* ds) {
   extern __shared__ uint32_t sm4[];
@@ -1251,7 +1253,7 @@ vm_status run_map(vm_4d_solver* s) {
   if (cudaMemsetAsync(&s->ds->nholes, 0, sizeof(int32_t), s->stream) != cudaSuccess ||
       cudaMemsetAsync(&s->ds->novf, 0, sizeof(int32_t), s->stream) != cudaSuccess)
     return VM_E_CUDA;
-  K4_LAUNCH(s, K_PERC, k4_percolate<<<g.ne, 256, s->smem, s->stream>>>(g, s->el, s->tay, s->key, s->ovf_list, s->ds));
+  K4_LAUNCH(s, K_PERC, k4_percolate<<<g.ne, PERC_THREADS, s->smem, s->stream>>>(g, s->el, s->tay, s->key, s->ovf_list, s->ds));
   // returns at once when no element left its window
   K4_LAUNCH(s, K_PERC_BIG,
             k4_percolate_big<<<BIG_SLOTS, 256, 0, s->stream>>>(g, s->el, s->tay, s->key, s->ovf_list, s->big, s->ds));
