@@ -321,9 +321,23 @@ __device__ bool passes4(const G4& g, const int* k, const double* tself, const do
 
 // One block per element: its 4-connected component of passing sites from the
 // site nearest to its position, within the padded lattice [-pad, n-1+pad]^4,
-// explored wave by wave inside a window of side W around the start site.  An
-// element whose component would leave the window, or whose wave outgrows the
-// frontier buffer, is listed for k4_percolate_big.
+// explored wave by wave inside a window of side W around the start site.
+// Each wave runs in three packed phases, so that the FP64 unit (a few
+// operations per clock per SM on this part) works on full warps rather than
+// on the scattered lanes of a diverged search:
+//   1. expansion: the 8 neighbours of every frontier site are stamped in the
+//      window's visited bits; newly reached sites form the test list;
+//   2. own distances: one lane per listed site computes its d^2 for the
+//      element and the alpha ranges, and appends the (site, neighbour
+//      element) pairs those ranges name to the pair list;
+//   3. pair distances: one lane per pair; a strictly smaller d^2 fails the
+//      site.
+// Passing sites are claimed and form the next frontier.  An element whose
+// component would leave the window, or whose lists outgrow their buffers, is
+// listed for k4_percolate_big.
+constexpr int TCAP = 1024;  // sites tested per wave
+constexpr int PCAP = 2048;  // (site, neighbour) pairs per wave
+
 __global__ void __launch_bounds__(PERC_THREADS) k4_percolate(G4 g, const double* __restrict__ el,
                                                     const double* __restrict__ tay, ulonglong2* __restrict__ key,
                                                     int32_t* __restrict__ ovf_list, Dev4* ds) {
@@ -332,11 +346,14 @@ __global__ void __launch_bounds__(PERC_THREADS) k4_percolate(G4 g, const double*
   const int nwin = W * W * W * W;
   const int nwords = (nwin + 31) >> 5;
   uint32_t* stamp = sm4;
-  int32_t* front0 = (int32_t*)(sm4 + ((nwords + 3) & ~3));
-  int32_t* front1 = front0 + FCAP;
+  int32_t* front = (int32_t*)(sm4 + ((nwords + 3) & ~3));  // FCAP
+  int32_t* tlist = front + FCAP;                             // TCAP
+  int32_t* pairs = tlist + TCAP;                             // PCAP
+  double* d2s = (double*)(pairs + PCAP);                     // TCAP (8-byte aligned: FCAP+TCAP+PCAP even)
   __shared__ double tself[NT4];
   __shared__ int org[4], kk[4];
-  __shared__ int go, ncur, nnext, ovf;
+  __shared__ int go, ncur, ntest, npairs, ovf;
+  __shared__ unsigned char fail[TCAP];
   const int m = blockIdx.x;
   const int tid = threadIdx.x;
   unsigned nev = 0;
@@ -359,87 +376,148 @@ __global__ void __launch_bounds__(PERC_THREADS) k4_percolate(G4 g, const double*
     elem_coords(g, m, kc);
     for (int a = 0; a < 4; a++) kk[a] = kc[a];
     go = ok;
-    ncur = 0;
     ovf = 0;
+    // the start site is the first wave's only site to test
+    const int c = g.R;
+    const int lw = ((c * W + c) * W + c) * W + c;
+    tlist[0] = lw;
+    ntest = 1;
+    ncur = 0;
   }
   __syncthreads();
   if (!go) return;
   if (tid == 0) {
-    const int c = g.R;
-    const int lw = ((c * W + c) * W + c) * W + c;
+    const int lw = tlist[0];
     stamp[lw >> 5] |= 1u << (lw & 31);
-    double P[4], d2;
-    long long gs[4];
-    for (int a = 0; a < 4; a++) {
-      gs[a] = org[a] + c;
-      P[a] = site_coord(g, a, gs[a]);
-    }
-    if (passes4(g, kk, tself, tay, P, &d2, nev)) {
-      bool in = true;
-      long long p = 0;
-      for (int a = 0; a < 4; a++) {
-        in = in && gs[a] >= 0 && gs[a] < g.n[a];
-        p += gs[a] * g.st[a];
-      }
-      if (in) claim4(key + p, (unsigned long long)__double_as_longlong(d2), (unsigned long long)m);
-      front0[0] = lw;
-      ncur = 1;
-    }
   }
-  __syncthreads();
-  int cur = 0;
   int kl[4];
   for (int a = 0; a < 4; a++) kl[a] = kk[a];
-  while (ncur > 0) {
-    if (tid == 0) nnext = 0;
+  bool first = true;
+  while (true) {
+    // 1. expansion of the frontier (the first wave tests the start site only)
+    if (!first) {
+      if (tid == 0) ntest = 0;
+      __syncthreads();
+      const int ntask = ncur * 8;
+      for (int t = tid; t < ntask; t += blockDim.x) {
+        const int e = t >> 3, dir = t & 7, ax = dir >> 1, sg = (dir & 1) ? 1 : -1;
+        int lw = front[e];
+        int l[4];
+        for (int a = 3; a >= 0; a--) {
+          l[a] = lw % W;
+          lw /= W;
+        }
+        l[ax] += sg;
+        const long long ga = (long long)org[ax] + l[ax];
+        if (ga < -g.pad || ga >= g.n[ax] + g.pad) continue;
+        if (l[ax] < 0 || l[ax] >= W) {
+          ovf = 1;
+          continue;
+        }
+        const int nw = ((l[0] * W + l[1]) * W + l[2]) * W + l[3];
+        const uint32_t bit = 1u << (nw & 31);
+        if (atomicOr(&stamp[nw >> 5], bit) & bit) continue;
+        const int idx = atomicAdd(&ntest, 1);
+        if (idx < TCAP)
+          tlist[idx] = nw;
+        else
+          ovf = 1;
+      }
+    }
+    first = false;
+    if (tid == 0) npairs = 0;
     __syncthreads();
-    const int32_t* fc = cur ? front1 : front0;
-    int32_t* fn = cur ? front0 : front1;
-    const int ntask = ncur * 8;
-    for (int t = tid; t < ntask; t += blockDim.x) {
-      const int e = t >> 3, dir = t & 7, ax = dir >> 1, sg = (dir & 1) ? 1 : -1;
-      int lw = fc[e];
-      int l[4];
+    const int nt = ovf ? 0 : min(ntest, TCAP);
+    if (nt == 0) break;
+    // 2. own distances and the pair list
+    for (int i = tid; i < nt; i += blockDim.x) {
+      int lw = tlist[i], l[4];
       for (int a = 3; a >= 0; a--) {
         l[a] = lw % W;
         lw /= W;
       }
-      l[ax] += sg;
-      const long long ga = (long long)org[ax] + l[ax];
-      if (ga < -g.pad || ga >= g.n[ax] + g.pad) continue;
-      if (l[ax] < 0 || l[ax] >= W) {
-        ovf = 1;
-        continue;
-      }
-      const int nw = ((l[0] * W + l[1]) * W + l[2]) * W + l[3];
-      const uint32_t bit = 1u << (nw & 31);
-      if (atomicOr(&stamp[nw >> 5], bit) & bit) continue;
-      double P[4], d2;
-      long long gs[4];
+      double P[4], x[4];
+      for (int a = 0; a < 4; a++) P[a] = site_coord(g, a, (long long)org[a] + l[a]);
+      d2s[i] = dist2_4(g, tself, P, x);
+      nev++;
+      fail[i] = 0;
+      int lo[4], hi[4];
       for (int a = 0; a < 4; a++) {
-        gs[a] = (long long)org[a] + l[a];
-        P[a] = site_coord(g, a, gs[a]);
+        lo[a] = (x[a] < -g.alpha) ? -1 : 0;
+        hi[a] = (x[a] < -g.alpha) ? 0 : ((x[a] < g.alpha) ? 0 : 1);
       }
-      if (!passes4(g, kl, tself, tay, P, &d2, nev)) continue;
+      int cnt = 0, codes[15];
+      for (int o0 = lo[0]; o0 <= hi[0]; o0++)
+        for (int o1 = lo[1]; o1 <= hi[1]; o1++)
+          for (int o2 = lo[2]; o2 <= hi[2]; o2++)
+            for (int o3 = lo[3]; o3 <= hi[3]; o3++) {
+              if ((o0 | o1 | o2 | o3) == 0) continue;
+              const int k0 = kl[0] + o0, k1 = kl[1] + o1, k2 = kl[2] + o2, k3 = kl[3] + o3;
+              if (k0 < 0 || k0 >= g.L[0] || k1 < 0 || k1 >= g.L[1] || k2 < 0 || k2 >= g.L[2] || k3 < 0 ||
+                  k3 >= g.L[3])
+                continue;
+              codes[cnt++] = (((o0 + 1) * 3 + (o1 + 1)) * 3 + (o2 + 1)) * 3 + (o3 + 1);
+            }
+      if (cnt) {
+        const int at = atomicAdd(&npairs, cnt);
+        if (at + cnt <= PCAP) {
+          for (int q = 0; q < cnt; q++) pairs[at + q] = (i << 7) | codes[q];
+        } else {
+          ovf = 1;
+        }
+      }
+    }
+    __syncthreads();
+    if (ovf) break;
+    // 3. the neighbours' distances at the listed sites
+    const int np = npairs;
+    for (int j = tid; j < np; j += blockDim.x) {
+      const int pr = pairs[j];
+      const int i = pr >> 7;
+      int code = pr & 127, o[4];
+      for (int a = 3; a >= 0; a--) {
+        o[a] = code % 3 - 1;
+        code /= 3;
+      }
+      const int mm = (((kl[0] + o[0]) * g.L[1] + (kl[1] + o[1])) * g.L[2] + (kl[2] + o[2])) * g.L[3] + (kl[3] + o[3]);
+      int lw = tlist[i], l[4];
+      for (int a = 3; a >= 0; a--) {
+        l[a] = lw % W;
+        lw /= W;
+      }
+      double P[4];
+      for (int a = 0; a < 4; a++) P[a] = site_coord(g, a, (long long)org[a] + l[a]);
+      nev++;
+      if (dist2_4(g, tay + (size_t)NT4 * mm, P, nullptr) < d2s[i]) fail[i] = 1;
+    }
+    if (tid == 0) ncur = 0;
+    __syncthreads();
+    // claims and the next frontier
+    for (int i = tid; i < nt; i += blockDim.x) {
+      if (fail[i]) continue;
+      int lw = tlist[i], l[4];
+      for (int a = 3; a >= 0; a--) {
+        l[a] = lw % W;
+        lw /= W;
+      }
       bool in = true;
       long long p = 0;
       for (int a = 0; a < 4; a++) {
-        in = in && gs[a] >= 0 && gs[a] < g.n[a];
-        p += gs[a] * g.st[a];
+        const long long gs = (long long)org[a] + l[a];
+        in = in && gs >= 0 && gs < g.n[a];
+        p += gs * g.st[a];
       }
-      if (in) claim4(key + p, (unsigned long long)__double_as_longlong(d2), (unsigned long long)m);
-      const int idx = atomicAdd(&nnext, 1);
+      if (in) claim4(key + p, (unsigned long long)__double_as_longlong(d2s[i]), (unsigned long long)m);
+      const int idx = atomicAdd(&ncur, 1);
       if (idx < FCAP)
-        fn[idx] = nw;
+        front[idx] = tlist[i];
       else
         ovf = 1;
     }
     __syncthreads();
-    if (tid == 0) ncur = ovf ? 0 : min(nnext, FCAP);
-    cur ^= 1;
-    __syncthreads();
+    if (ovf || ncur == 0) break;
   }
-  // the component reached the window's edge (or a wave its buffer): the
+  // the component reached the window's edge (or a list its buffer): the
   // element is filled again over the whole padded lattice (its claims so far
   // are a subset of the full component's, with the same keys)
   if (tid == 0 && ovf) ovf_list[atomicAdd(&ds->novf, 1)] = m;
@@ -1353,7 +1431,7 @@ vm_status vm_4d_create(const vm_4d_config* c, void* d_ws, size_t bytes, void* st
   s->nchunk = nchunks(g);
   const int nwin = g.W * g.W * g.W * g.W;
   const int nwords = (nwin + 31) / 32;
-  s->smem = 4 * (size_t)((nwords + 3) & ~3) + 2 * 4 * (size_t)FCAP;
+  s->smem = 4 * (size_t)((nwords + 3) & ~3) + 4 * (size_t)(FCAP + TCAP + PCAP) + 8 * (size_t)TCAP;
   if (cudaFuncSetAttribute(k4_percolate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem) != cudaSuccess) {
     delete s;
     return VM_E_CUDA;
