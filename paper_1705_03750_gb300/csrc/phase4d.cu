@@ -222,7 +222,17 @@ __device__ void inverse4(const double* A, double* B) {
   B[15] = M_(A_(S_(M_(a20, s3), M_(a21, s1)), M_(a22, s0)), id);
 }
 
-__global__ void __launch_bounds__(128) k4_taylor(G4 g, const double* __restrict__ el, double* __restrict__ tay) {
+// FP32 record of an element's inverse map in element units, for the certified
+// percolation tests: with p_b = (P_b - P_m,b)/dm_b,
+//   xi_a = (Q_a - Q_m,a)/dm_a = sum_b A_ab p_b + sum_{b<=c} B_a,bc p_b p_c,
+// A_ab = T^-1_ab dm_b/dm_a, B_a,bc = -(1/2)(2 - [b=c]) sum_l T^-1_al G_l,bc dm_b dm_c/dm_a
+// (the same polynomial the FP64 evaluation computes in another order), and
+// K_a = (1/2) sum_l |T^-1_al| max_bc |G_l,bc| dm_b dm_c / dm_a (bounds the
+// absolute terms of that FP64 evaluation).  Layout: A[16], B[40], K[4], pad.
+constexpr int NF4 = 64;
+
+__global__ void __launch_bounds__(128) k4_taylor(G4 g, const double* __restrict__ el, double* __restrict__ tay,
+                                                 float* __restrict__ tay32) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= g.ne) return;
   const double* e = el + (size_t)NE4 * m;
@@ -246,6 +256,74 @@ __global__ void __launch_bounds__(128) k4_taylor(G4 g, const double* __restrict_
   int k[4];
   elem_coords(g, m, k);
   for (int a = 0; a < 4; a++) t[60 + a] = A_(g.ctr[a], M_((double)(k[a] - g.K[a] - 1), g.dm[a]));
+  float* r = tay32 + (size_t)NF4 * m;
+  for (int a = 0; a < 4; a++) {
+    for (int b = 0; b < 4; b++) r[4 * a + b] = (float)(Ti[4 * a + b] * g.dm[b] * g.inv_dm[a]);
+    double kmax = 0.0;
+    for (int l = 0; l < 4; l++) {
+      double gm = 0.0;
+      for (int b = 0; b < 4; b++)
+        for (int c = b; c < 4; c++) gm = fmax(gm, fabs(t[20 + 10 * l + sym4(b, c)]) * g.dm[b] * g.dm[c]);
+      kmax += fabs(Ti[4 * a + l]) * gm;
+    }
+    r[56 + a] = (float)(0.5 * kmax * g.inv_dm[a] * 1.0000001);
+    for (int b = 0; b < 4; b++)
+      for (int c = b; c < 4; c++) {
+        double v = 0.0;
+        for (int l = 0; l < 4; l++) v += Ti[4 * a + l] * t[20 + 10 * l + sym4(b, c)];
+        r[16 + 10 * a + sym4(b, c)] = (float)(-0.5 * (b == c ? 1.0 : 2.0) * v * g.dm[b] * g.dm[c] * g.inv_dm[a]);
+      }
+  }
+  for (int q = 60; q < NF4; q++) r[q] = 0.f;
+}
+
+// FP32 offsets xi of an element at a site with rigorous bounds e_a >=
+// |xi_a - x_a|, x_a the FP64 evaluation's (dQ_a / dm_a in the exact order).
+// Roundings: p (3), products p_b p_c (3 more), coefficients (1), the FMA
+// chain of 14 terms (14): below 23 u = 1.4e-6 of the sum of absolute terms;
+// the FP64 evaluation's own error (under 1e-14 of its absolute terms,
+// bounded by K (sum |p|)^2 and the linear part) and the conversion of the
+// FP64 inputs add the second and third terms.
+constexpr float kRel4 = 2.0e-6f, kAbs4 = 1.0e-9f;
+
+__device__ __forceinline__ void eval32_4(const G4& g, const float* __restrict__ R, const double* __restrict__ t,
+                                         const double* P, float* xi, float* e) {
+  float p[4], ap[4];
+  for (int b = 0; b < 4; b++) {
+    p[b] = (float)S_(P[b], t[b]) * (float)g.inv_dm[b];
+    ap[b] = fabsf(p[b]);
+  }
+  float pp[10], app[10];
+  for (int b = 0; b < 4; b++)
+    for (int c = b; c < 4; c++) {
+      pp[sym4(b, c)] = p[b] * p[c];
+      app[sym4(b, c)] = ap[b] * ap[c];
+    }
+  const float S = (ap[0] + ap[1]) + (ap[2] + ap[3]);
+  for (int a = 0; a < 4; a++) {
+    float v = 0.f, E = 0.f;
+    for (int b = 0; b < 4; b++) {
+      v = fmaf(R[4 * a + b], p[b], v);
+      E = fmaf(fabsf(R[4 * a + b]), ap[b], E);
+    }
+    for (int q = 0; q < 10; q++) {
+      v = fmaf(R[16 + 10 * a + q], pp[q], v);
+      E = fmaf(fabsf(R[16 + 10 * a + q]), app[q], E);
+    }
+    xi[a] = v;
+    e[a] = kRel4 * E + kAbs4 * (1.f + E) + 1e-13f * R[56 + a] * (S * S) * 16.f;
+  }
+}
+
+// d^2 in FP32 and a bound on its distance to the FP64 value
+__device__ __forceinline__ float d2_32(const float* xi, const float* e, float* bd) {
+  float d2 = 0.f, b = 0.f;
+  for (int a = 0; a < 4; a++) {
+    d2 = fmaf(xi[a], xi[a], d2);
+    b = fmaf(e[a], 2.f * fabsf(xi[a]) + e[a], b);
+  }
+  *bd = b + 6e-7f * d2 + 1e-30f;
+  return d2;
 }
 
 // ---------------------------------------------------------------------------
@@ -322,24 +400,38 @@ __device__ bool passes4(const G4& g, const int* k, const double* tself, const do
 // One block per element: its 4-connected component of passing sites from the
 // site nearest to its position, within the padded lattice [-pad, n-1+pad]^4,
 // explored wave by wave inside a window of side W around the start site.
-// Each wave runs in three packed phases, so that the FP64 unit (a few
-// operations per clock per SM on this part) works on full warps rather than
-// on the scattered lanes of a diverged search:
+// Each wave runs in packed phases, so that the FP64 unit (a few operations
+// per clock per SM on this part) sees as little work as possible and that on
+// full warps:
 //   1. expansion: the 8 neighbours of every frontier site are stamped in the
 //      window's visited bits; newly reached sites form the test list;
-//   2. own distances: one lane per listed site computes its d^2 for the
-//      element and the alpha ranges, and appends the (site, neighbour
-//      element) pairs those ranges name to the pair list;
-//   3. pair distances: one lane per pair; a strictly smaller d^2 fails the
-//      site.
-// Passing sites are claimed and form the next frontier.  An element whose
-// component would leave the window, or whose lists outgrow their buffers, is
-// listed for k4_percolate_big.
+//   2. own offsets: one lane per listed site evaluates the element's inverse
+//      map in FP32 with a bound on its distance to the FP64 value
+//      (eval32_4); the alpha ranges are decided where the bound settles them
+//      (else the site is left to the exact test), and the (site, neighbour)
+//      pairs they name are listed;
+//   3. pair distances: one lane per pair, FP32 with bounds: a neighbour
+//      certainly closer fails the site, one whose comparison the bound
+//      leaves open sends the site to the exact test;
+//   4. exact work: the sites left open run the FP64 test in the oracle's
+//      order; every passing site's claim key takes its FP64 d^2.
+// The outcome is the all-FP64 percolation's.  Passing sites are claimed and
+// form the next frontier.  An element whose component would leave the window,
+// or whose lists outgrow their buffers, is listed for k4_percolate_big.
 constexpr int TCAP = 1024;  // sites tested per wave
 constexpr int PCAP = 2048;  // (site, neighbour) pairs per wave
+enum : int { ST_PASS = 0, ST_OPEN = 1, ST_FAIL = 2 };
+
+__device__ __forceinline__ void decode_w(int lw, int W, int* l) {
+  for (int a = 3; a >= 0; a--) {
+    l[a] = lw % W;
+    lw /= W;
+  }
+}
 
 __global__ void __launch_bounds__(PERC_THREADS) k4_percolate(G4 g, const double* __restrict__ el,
-                                                    const double* __restrict__ tay, ulonglong2* __restrict__ key,
+                                                    const double* __restrict__ tay,
+                                                    const float* __restrict__ tay32, ulonglong2* __restrict__ key,
                                                     int32_t* __restrict__ ovf_list, Dev4* ds) {
   extern __shared__ uint32_t sm4[];
   const int W = g.W;
@@ -349,16 +441,20 @@ __global__ void __launch_bounds__(PERC_THREADS) k4_percolate(G4 g, const double*
   int32_t* front = (int32_t*)(sm4 + ((nwords + 3) & ~3));  // FCAP
   int32_t* tlist = front + FCAP;                             // TCAP
   int32_t* pairs = tlist + TCAP;                             // PCAP
-  double* d2s = (double*)(pairs + PCAP);                     // TCAP (8-byte aligned: FCAP+TCAP+PCAP even)
+  int32_t* status = pairs + PCAP;                            // TCAP
+  float* d2f = (float*)(status + TCAP);                      // TCAP
+  float* bdf = d2f + TCAP;                                   // TCAP
   __shared__ double tself[NT4];
+  __shared__ float rself[NF4];
   __shared__ int org[4], kk[4];
   __shared__ int go, ncur, ntest, npairs, ovf;
-  __shared__ unsigned char fail[TCAP];
   const int m = blockIdx.x;
   const int tid = threadIdx.x;
   unsigned nev = 0;
   if (tid < NT4) tself[tid] = tay[(size_t)NT4 * m + tid];
+  if (tid < NF4) rself[tid] = tay32[(size_t)NF4 * m + tid];
   for (int w = tid; w < nwords; w += blockDim.x) stamp[w] = 0u;
+  const float af = (float)g.alpha, aerr = 1e-7f * (1.f + af);
   if (tid == 0) {
     const double* e = el + (size_t)NE4 * m;
     int ok = 1;
@@ -401,12 +497,8 @@ __global__ void __launch_bounds__(PERC_THREADS) k4_percolate(G4 g, const double*
       const int ntask = ncur * 8;
       for (int t = tid; t < ntask; t += blockDim.x) {
         const int e = t >> 3, dir = t & 7, ax = dir >> 1, sg = (dir & 1) ? 1 : -1;
-        int lw = front[e];
         int l[4];
-        for (int a = 3; a >= 0; a--) {
-          l[a] = lw % W;
-          lw /= W;
-        }
+        decode_w(front[e], W, l);
         l[ax] += sg;
         const long long ga = (long long)org[ax] + l[ax];
         if (ga < -g.pad || ga >= g.n[ax] + g.pad) continue;
@@ -429,23 +521,39 @@ __global__ void __launch_bounds__(PERC_THREADS) k4_percolate(G4 g, const double*
     __syncthreads();
     const int nt = ovf ? 0 : min(ntest, TCAP);
     if (nt == 0) break;
-    // 2. own distances and the pair list
+    // 2. own offsets in FP32, certified alpha ranges, the pair list
     for (int i = tid; i < nt; i += blockDim.x) {
-      int lw = tlist[i], l[4];
-      for (int a = 3; a >= 0; a--) {
-        l[a] = lw % W;
-        lw /= W;
-      }
-      double P[4], x[4];
+      int l[4];
+      decode_w(tlist[i], W, l);
+      double P[4];
       for (int a = 0; a < 4; a++) P[a] = site_coord(g, a, (long long)org[a] + l[a]);
-      d2s[i] = dist2_4(g, tself, P, x);
-      nev++;
-      fail[i] = 0;
-      int lo[4], hi[4];
+      float x[4], e[4];
+      eval32_4(g, rself, tself, P, x, e);
+      float bd;
+      d2f[i] = d2_32(x, e, &bd);
+      bdf[i] = bd;
+      int lo[4], hi[4], open = 0;
       for (int a = 0; a < 4; a++) {
-        lo[a] = (x[a] < -g.alpha) ? -1 : 0;
-        hi[a] = (x[a] < -g.alpha) ? 0 : ((x[a] < g.alpha) ? 0 : 1);
+        const float E = e[a] + aerr;
+        // below -alpha: {-1,0}; below alpha: {0}; else {0,1}, each comparison certified
+        const bool below_lo = x[a] + E < -af, above_lo = x[a] - E > -af;
+        const bool below_hi = x[a] + E < af, above_hi = x[a] - E > af;
+        if (below_lo) {
+          lo[a] = -1;
+          hi[a] = 0;
+        } else if (above_lo && below_hi) {
+          lo[a] = 0;
+          hi[a] = 0;
+        } else if (above_hi) {
+          lo[a] = 0;
+          hi[a] = 1;
+        } else {
+          open = 1;
+          lo[a] = hi[a] = 0;
+        }
       }
+      status[i] = open ? ST_OPEN : ST_PASS;
+      if (open) continue;
       int cnt = 0, codes[15];
       for (int o0 = lo[0]; o0 <= hi[0]; o0++)
         for (int o1 = lo[1]; o1 <= hi[1]; o1++)
@@ -469,7 +577,7 @@ __global__ void __launch_bounds__(PERC_THREADS) k4_percolate(G4 g, const double*
     }
     __syncthreads();
     if (ovf) break;
-    // 3. the neighbours' distances at the listed sites
+    // 3. the neighbours' distances at the listed sites, FP32 with bounds
     const int np = npairs;
     for (int j = tid; j < np; j += blockDim.x) {
       const int pr = pairs[j];
@@ -480,34 +588,49 @@ __global__ void __launch_bounds__(PERC_THREADS) k4_percolate(G4 g, const double*
         code /= 3;
       }
       const int mm = (((kl[0] + o[0]) * g.L[1] + (kl[1] + o[1])) * g.L[2] + (kl[2] + o[2])) * g.L[3] + (kl[3] + o[3]);
-      int lw = tlist[i], l[4];
-      for (int a = 3; a >= 0; a--) {
-        l[a] = lw % W;
-        lw /= W;
-      }
+      int l[4];
+      decode_w(tlist[i], W, l);
       double P[4];
       for (int a = 0; a < 4; a++) P[a] = site_coord(g, a, (long long)org[a] + l[a]);
-      nev++;
-      if (dist2_4(g, tay + (size_t)NT4 * mm, P, nullptr) < d2s[i]) fail[i] = 1;
+      float x[4], e[4], bn;
+      eval32_4(g, tay32 + (size_t)NF4 * mm, tay + (size_t)NT4 * mm, P, x, e);
+      const float dn = d2_32(x, e, &bn);
+      const float dm = d2f[i], bm = bdf[i];
+      if (dn + bn < dm - bm)
+        status[i] = ST_FAIL;
+      else if (!(dn - bn > dm + bm))
+        atomicMax(&status[i], ST_OPEN);
     }
     if (tid == 0) ncur = 0;
     __syncthreads();
-    // claims and the next frontier
+    // 4. exact tests where the bounds left them open; FP64 keys; claims
     for (int i = tid; i < nt; i += blockDim.x) {
-      if (fail[i]) continue;
-      int lw = tlist[i], l[4];
-      for (int a = 3; a >= 0; a--) {
-        l[a] = lw % W;
-        lw /= W;
+      const int st = status[i];
+      if (st == ST_FAIL) continue;
+      int l[4];
+      decode_w(tlist[i], W, l);
+      double P[4];
+      long long gs[4];
+      for (int a = 0; a < 4; a++) {
+        gs[a] = (long long)org[a] + l[a];
+        P[a] = site_coord(g, a, gs[a]);
+      }
+      double d2;
+      if (st == ST_OPEN) {
+        if (!passes4(g, kl, tself, tay, P, &d2, nev)) continue;
+      } else {
+        bool in = true;
+        for (int a = 0; a < 4; a++) in = in && gs[a] >= 0 && gs[a] < g.n[a];
+        d2 = in ? dist2_4(g, tself, P, nullptr) : 0.0;  // the key is needed for in-grid sites only
+        nev += in;
       }
       bool in = true;
       long long p = 0;
       for (int a = 0; a < 4; a++) {
-        const long long gs = (long long)org[a] + l[a];
-        in = in && gs >= 0 && gs < g.n[a];
-        p += gs * g.st[a];
+        in = in && gs[a] >= 0 && gs[a] < g.n[a];
+        p += gs[a] * g.st[a];
       }
-      if (in) claim4(key + p, (unsigned long long)__double_as_longlong(d2s[i]), (unsigned long long)m);
+      if (in) claim4(key + p, (unsigned long long)__double_as_longlong(d2), (unsigned long long)m);
       const int idx = atomicAdd(&ncur, 1);
       if (idx < FCAP)
         front[idx] = tlist[i];
@@ -1162,6 +1285,7 @@ struct vm_4d_solver {
   cudaStream_t stream;
   char* ws;
   double *fini, *eta, *f, *el, *tay, *Mpix, *fld, *tab;
+  float* tay32;
   ulonglong2* key;
   int32_t *map, *holes, *cand, *ovf_list;
   uint32_t* big;
@@ -1235,7 +1359,7 @@ int nchunks(const G4& g) {
 }
 
 struct Layout {
-  size_t fini, eta, f, key, map, holes, cand, el, tay, Mpix, fld, gext, part, tab, ovf, big, ds, total;
+  size_t fini, eta, f, key, map, holes, cand, el, tay, tay32, Mpix, fld, gext, part, tab, ovf, big, ds, total;
 };
 
 Layout layout(const G4& g) {
@@ -1256,6 +1380,7 @@ Layout layout(const G4& g) {
   L.cand = take(4 * ns);
   L.el = take(8 * (size_t)NE4 * g.ne);
   L.tay = take(8 * (size_t)NT4 * g.ne);
+  L.tay32 = take(4 * (size_t)NF4 * g.ne);
   L.Mpix = take(8 * (size_t)g.n[0] * g.n[1]);
   L.fld = take(8 * 12 * (size_t)g.n[0] * g.n[1]);
   L.gext = take(16 * (size_t)g.We0 * g.We1);
@@ -1327,11 +1452,11 @@ void prof_end(vm_4d_solver* s, int id, cudaEvent_t a) {
 
 vm_status run_map(vm_4d_solver* s) {
   const G4& g = s->g;
-  K4_LAUNCH(s, K_TAYLOR, k4_taylor<<<blocks(g.ne, 128), 128, 0, s->stream>>>(g, s->el, s->tay));
+  K4_LAUNCH(s, K_TAYLOR, k4_taylor<<<blocks(g.ne, 128), 128, 0, s->stream>>>(g, s->el, s->tay, s->tay32));
   if (cudaMemsetAsync(&s->ds->nholes, 0, sizeof(int32_t), s->stream) != cudaSuccess ||
       cudaMemsetAsync(&s->ds->novf, 0, sizeof(int32_t), s->stream) != cudaSuccess)
     return VM_E_CUDA;
-  K4_LAUNCH(s, K_PERC, k4_percolate<<<g.ne, PERC_THREADS, s->smem, s->stream>>>(g, s->el, s->tay, s->key, s->ovf_list, s->ds));
+  K4_LAUNCH(s, K_PERC, k4_percolate<<<g.ne, PERC_THREADS, s->smem, s->stream>>>(g, s->el, s->tay, s->tay32, s->key, s->ovf_list, s->ds));
   // returns at once when no element left its window
   K4_LAUNCH(s, K_PERC_BIG,
             k4_percolate_big<<<BIG_SLOTS, 256, 0, s->stream>>>(g, s->el, s->tay, s->key, s->ovf_list, s->big, s->ds));
@@ -1420,6 +1545,7 @@ vm_status vm_4d_create(const vm_4d_config* c, void* d_ws, size_t bytes, void* st
   s->cand = (int32_t*)(s->ws + L.cand);
   s->el = (double*)(s->ws + L.el);
   s->tay = (double*)(s->ws + L.tay);
+  s->tay32 = (float*)(s->ws + L.tay32);
   s->Mpix = (double*)(s->ws + L.Mpix);
   s->fld = (double*)(s->ws + L.fld);
   s->gext = (double2*)(s->ws + L.gext);
@@ -1431,7 +1557,7 @@ vm_status vm_4d_create(const vm_4d_config* c, void* d_ws, size_t bytes, void* st
   s->nchunk = nchunks(g);
   const int nwin = g.W * g.W * g.W * g.W;
   const int nwords = (nwin + 31) / 32;
-  s->smem = 4 * (size_t)((nwords + 3) & ~3) + 4 * (size_t)(FCAP + TCAP + PCAP) + 8 * (size_t)TCAP;
+  s->smem = 4 * (size_t)((nwords + 3) & ~3) + 4 * (size_t)(FCAP + TCAP + PCAP + TCAP) + 8 * (size_t)TCAP;
   if (cudaFuncSetAttribute(k4_percolate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem) != cudaSuccess) {
     delete s;
     return VM_E_CUDA;
