@@ -29,14 +29,16 @@
 //                   solves along vy, vx, y, x), k4_reset
 //
 // Every integer decision (start sites, alpha and beta ranges, the d^2
-// comparisons, nearest nodes, spline cells) is taken on FP64 values computed
-// in one fixed order without fused multiply-add (the __d*_rn intrinsics), the
-// order of the FP64 restatement of the method; the map is therefore exactly
-// the one that restatement gives for the same elements.  The reconstruction
-// and the resample use the same order, the spline solve divides by the same
-// pivots, so f and f_ini agree to the last bit with it as well; the pixel
-// masses are block sums (a different order) and the field is summed over
-// blocks, so element trajectories agree to rounding.
+// comparisons of the percolation, the nearest node of the interpolation) is
+// taken on FP64 values computed in one fixed order without fused
+// multiply-add (the __d*_rn intrinsics), the order of the FP64 restatement of
+// the method, or on FP32 values whose rigorous error bound shows the same
+// outcome; the map is therefore exactly the one that restatement gives for
+// the same elements.  Values that feed no such decision (the interpolated f,
+// the Q_r blend, the spline sums) use fused arithmetic and agree with it to
+// rounding; the spline solve divides by the same pivots in the same order;
+// the pixel masses are block sums and the field is summed over blocks, so
+// element trajectories agree to rounding.
 
 #include <cuda_runtime.h>
 #include <math.h>
@@ -132,6 +134,38 @@ __device__ __forceinline__ void qofp4(const double* __restrict__ t, const double
     double c = A_(A_(A_(M_(Ti[4 * a], s[0]), M_(Ti[4 * a + 1], s[1])), M_(Ti[4 * a + 2], s[2])),
                   M_(Ti[4 * a + 3], s[3]));
     dQ[a] = S_(y, M_(0.5, c));
+  }
+}
+
+// The same inverse map with fused multiply-adds, for values that feed no
+// integer decision (or whose decision is re-taken in the exact order near
+// its threshold): about half the FP64 instructions of qofp4.
+__device__ __forceinline__ void qofp4_f(const double* __restrict__ t, const double* P, double* dQ) {
+  double dP[4], s[4];
+  for (int a = 0; a < 4; a++) dP[a] = P[a] - t[a];
+  const double* Ti = t + 4;
+#pragma unroll
+  for (int l = 0; l < 4; l++) {
+    const double* G = t + 20 + 10 * l;
+    double acc = 0.0;
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+      double gb = G[sym4(b, 0)] * dP[0];
+      gb = fma(G[sym4(b, 1)], dP[1], gb);
+      gb = fma(G[sym4(b, 2)], dP[2], gb);
+      gb = fma(G[sym4(b, 3)], dP[3], gb);
+      acc = fma(dP[b], gb, acc);
+    }
+    s[l] = acc;
+  }
+#pragma unroll
+  for (int a = 0; a < 4; a++) {
+    double y = Ti[4 * a] * dP[0], c = Ti[4 * a] * s[0];
+    for (int b = 1; b < 4; b++) {
+      y = fma(Ti[4 * a + b], dP[b], y);
+      c = fma(Ti[4 * a + b], s[b], c);
+    }
+    dQ[a] = fma(-0.5, c, y);
   }
 }
 
@@ -898,6 +932,45 @@ __device__ double qinterp4(const G4& g, const double* __restrict__ F, const doub
   return f;
 }
 
+// The same interpolant with fused arithmetic (stencil chosen from u as above)
+__device__ double qinterp4_f(const G4& g, const double* __restrict__ F, const double* u) {
+  for (int a = 0; a < 4; a++)
+    if (!(u[a] > -2.0 && u[a] < (double)g.n[a] + 1.0)) return 0.0;
+  long long gn[4], gc[4];
+  double dq[4];
+  for (int a = 0; a < 4; a++) {
+    gn[a] = (long long)floor(u[a] + 0.5);
+    gc[a] = (long long)floor(u[a]);
+    dq[a] = u[a] - (double)gn[a];
+  }
+  const double F0 = F4at(g, F, gn);
+  double f = F0 * (1.0 - ((dq[0] * dq[0] + dq[1] * dq[1]) + (dq[2] * dq[2] + dq[3] * dq[3])));
+  for (int a = 0; a < 4; a++) {
+    long long c[4] = {gn[0], gn[1], gn[2], gn[3]};
+    c[a] = gn[a] + 1;
+    const double Fp = F4at(g, F, c);
+    c[a] = gn[a] - 1;
+    const double Fm = F4at(g, F, c);
+    // (Fp dq (1 + dq) + Fm dq (dq - 1)) / 2
+    f = fma(0.5 * dq[a], fma(Fp + Fm, dq[a], Fp - Fm), f);
+  }
+  for (int a = 0; a < 4; a++)
+    for (int b = a + 1; b < 4; b++) {
+      long long c00[4] = {gn[0], gn[1], gn[2], gn[3]};
+      c00[a] = gc[a];
+      c00[b] = gc[b];
+      long long c11[4] = {c00[0], c00[1], c00[2], c00[3]}, c10[4] = {c00[0], c00[1], c00[2], c00[3]},
+                c01[4] = {c00[0], c00[1], c00[2], c00[3]};
+      c11[a] += 1;
+      c11[b] += 1;
+      c10[a] += 1;
+      c01[b] += 1;
+      const double cross = (F4at(g, F, c11) + F4at(g, F, c00)) - (F4at(g, F, c10) + F4at(g, F, c01));
+      f = fma(cross * dq[a], dq[b], f);
+    }
+  return f;
+}
+
 // One block per (x, y) pixel: f(P) = f_ini(Q(P)) at every (vx, vy) site of
 // the pixel through the owner's inverse map, and the pixel mass
 // M = (sum f) dx dy dvx dvy.
@@ -921,9 +994,20 @@ __global__ void __launch_bounds__(256) k4_recon(G4 g, const double* __restrict__
       P[1] = site_coord(g, 1, i1);
       P[2] = site_coord(g, 2, q / g.n[3]);
       P[3] = site_coord(g, 3, q % g.n[3]);
-      qofp4(t, P, dQ);
-      for (int a = 0; a < 4; a++) u[a] = M_(S_(A_(__ldg(t + 60 + a), dQ[a]), g.lo[a]), g.inv_d[a]);
-      fv = qinterp4(g, fini, u);
+      // fused evaluation; the nearest node (the one decision the
+      // interpolant is not continuous across) is re-taken in the exact order
+      // when a coordinate lies within 1e-9 of a half-integer
+      qofp4_f(t, P, dQ);
+      bool tie = false;
+      for (int a = 0; a < 4; a++) {
+        u[a] = ((__ldg(t + 60 + a) + dQ[a]) - g.lo[a]) * g.inv_d[a];
+        tie |= fabs((u[a] - floor(u[a])) - 0.5) < 1e-9;
+      }
+      if (tie) {
+        qofp4(t, P, dQ);
+        for (int a = 0; a < 4; a++) u[a] = M_(S_(A_(__ldg(t + 60 + a), dQ[a]), g.lo[a]), g.inv_d[a]);
+      }
+      fv = qinterp4_f(g, fini, u);
     } else if (m >= g.ne) {
       bad(ds, 43);
     }
@@ -1119,6 +1203,25 @@ __device__ __forceinline__ double W4(double x) {
   return 0.0;
 }
 
+__device__ __forceinline__ double W4f(double x) {
+  if (x <= 1.0) return fma(0.75 * x, x * x, fma(-1.5 * x, x, 1.0));
+  if (x <= 2.0) {
+    const double r = 2.0 - x;
+    return 0.25 * (r * r * r);
+  }
+  return 0.0;
+}
+
+__device__ __forceinline__ double bspline3_f(double t) {
+  t = fabs(t);
+  if (t < 1.0) return fma(0.5 * t, t * t, fma(-t, t, 2.0 / 3.0));
+  if (t < 2.0) {
+    const double r = 2.0 - t;
+    return (r * r * r) * (1.0 / 6.0);
+  }
+  return 0.0;
+}
+
 __device__ __forceinline__ long long ghost4(long long k, int n) {
   if (k >= 0 && k < n) return k;
   if (k == -1) return 1;
@@ -1158,10 +1261,48 @@ __device__ double spline_eval4(const G4& g, const double* __restrict__ eta, cons
   return sum;
 }
 
+// The spline sum with fused arithmetic: it is C2 in u, so the choice of the
+// cell (floor(u)) where u lies on a knot does not change its value.
+__device__ double spline_eval4_f(const G4& g, const double* __restrict__ eta, const double* u) {
+  for (int a = 0; a < 4; a++)
+    if (!(u[a] > -3.0 && u[a] < (double)(g.n[a] + 2))) return 0.0;
+  double B[4][4];
+  long long gk[4][4];
+  for (int a = 0; a < 4; a++) {
+    const long long k0 = (long long)floor(u[a]) - 1;
+    for (int q = 0; q < 4; q++) {
+      B[a][q] = bspline3_f(u[a] - (double)(k0 + q));
+      gk[a][q] = ghost4(k0 + q, g.n[a]);
+    }
+  }
+  double sum = 0.0;
+  for (int q0 = 0; q0 < 4; q0++) {
+    if (gk[0][q0] < 0) continue;
+    for (int q1 = 0; q1 < 4; q1++) {
+      if (gk[1][q1] < 0) continue;
+      const double w01 = B[0][q0] * B[1][q1];
+      for (int q2 = 0; q2 < 4; q2++) {
+        if (gk[2][q2] < 0) continue;
+        const double w012 = w01 * B[2][q2];
+        const long long b012 = gk[0][q0] * g.st[0] + gk[1][q1] * g.st[1] + gk[2][q2] * g.st[2];
+        double part = 0.0;
+        for (int q3 = 0; q3 < 4; q3++) {
+          if (gk[3][q3] < 0) continue;
+          part = fma(__ldg(eta + b012 + gk[3][q3]), B[3][q3], part);
+        }
+        sum = fma(part, w012, sum);
+      }
+    }
+  }
+  return sum;
+}
+
 // f_new(P) = spline[f_ini](Q_r(P)), Q_r = sum W(2 d_m') Q(P, m') / sum W(2 d_m')
 // over the beta set of the owner (per axis below -beta {-1,0}, below beta
 // {-1,0,1}, else {0,1}; an offset with two or more non-zero components is
-// dropped when one of them lies on a {-1,0,1} axis)
+// dropped when one of them lies on a {-1,0,1} axis).  The beta ranges are
+// decided on the owner's offsets in the exact order; the blend and the spline
+// sum, continuous in their inputs, use fused arithmetic.
 __global__ void __launch_bounds__(128) k4_resample(G4 g, const double* __restrict__ tay, const int32_t* __restrict__ map,
                                                   const double* __restrict__ eta, double* __restrict__ fnew, Dev4* ds) {
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1207,26 +1348,28 @@ __global__ void __launch_bounds__(128) k4_resample(G4 g, const double* __restric
             if (!ok) continue;
             const int mm = ((kk[0] * g.L[1] + kk[1]) * g.L[2] + kk[2]) * g.L[3] + kk[3];
             const double* t = tay + (size_t)NT4 * mm;
-            double dQ[4], xl[4];
-            qofp4(t, P, dQ);
-            for (int a = 0; a < 4; a++) xl[a] = M_(dQ[a], g.inv_dm[a]);
-            const double dd =
-                __dsqrt_rn(A_(A_(A_(M_(xl[0], xl[0]), M_(xl[1], xl[1])), M_(xl[2], xl[2])), M_(xl[3], xl[3])));
-            const double w = W4(M_(2.0, dd));
-            for (int a = 0; a < 4; a++) num[a] = A_(num[a], M_(w, A_(__ldg(t + 60 + a), dQ[a])));
-            den = A_(den, w);
+            double dQ[4], dd = 0.0;
+            qofp4_f(t, P, dQ);
+            for (int a = 0; a < 4; a++) {
+              const double xa = dQ[a] * g.inv_dm[a];
+              dd = fma(xa, xa, dd);
+            }
+            const double w = W4f(2.0 * sqrt(dd));
+            for (int a = 0; a < 4; a++) num[a] = fma(w, __ldg(t + 60 + a) + dQ[a], num[a]);
+            den += w;
           }
     double Qr[4];
     if (den > 0.0) {
-      for (int a = 0; a < 4; a++) Qr[a] = __ddiv_rn(num[a], den);
+      const double id = 1.0 / den;
+      for (int a = 0; a < 4; a++) Qr[a] = num[a] * id;
     } else {
       double dQ[4];
-      qofp4(tm, P, dQ);
-      for (int a = 0; a < 4; a++) Qr[a] = A_(__ldg(tm + 60 + a), dQ[a]);
+      qofp4_f(tm, P, dQ);
+      for (int a = 0; a < 4; a++) Qr[a] = __ldg(tm + 60 + a) + dQ[a];
     }
     double u[4];
-    for (int a = 0; a < 4; a++) u[a] = M_(S_(Qr[a], g.lo[a]), g.inv_d[a]);
-    val = spline_eval4(g, eta, u);
+    for (int a = 0; a < 4; a++) u[a] = (Qr[a] - g.lo[a]) * g.inv_d[a];
+    val = spline_eval4_f(g, eta, u);
   } else if (m >= g.ne) {
     bad(ds, 44);
   }
