@@ -14,7 +14,7 @@
 //                   compare-and-swap minimum of (d^2 bits, element index);
 //                   k4_percolate_big fills the elements that left their window
 //                   again over the whole padded lattice (global-memory bits)
-//   k4_map_finish   owner of every site from its key; hole list
+//   k4_map_finish   owner of every site from its slot or record; hole list
 //   k4_holes        Jacobi rounds of the unexplored-site repair (one block)
 //   k4_recon        one block per (x, y) pixel: f at its vx-vy plane by the
 //                   15-point interpolation of f_ini at Q(P); pixel mass by a
@@ -313,39 +313,53 @@ __global__ void __launch_bounds__(128) k4_taylor(G4 g, const double* __restrict_
 
 // FP32 offsets xi of an element at a site with rigorous bounds e_a >=
 // |xi_a - x_a|, x_a the FP64 evaluation's (dQ_a / dm_a in the exact order).
-// Roundings: p (3), products p_b p_c (3 more), coefficients (1), the FMA
-// chain of 14 terms (14): below 23 u = 1.4e-6 of the sum of absolute terms;
-// the FP64 evaluation's own error (under 1e-14 of its absolute terms,
-// bounded by K (sum |p|)^2 and the linear part) and the conversion of the
-// FP64 inputs add the second and third terms.
+// Roundings: products p_b p_c (1), coefficients (1), the FMA chain of 14
+// terms (14): below 17 u = 1.0e-6 of the sum of absolute terms; the bound
+// dp of the inputs p is carried through the linear and quadratic terms; the
+// FP64 evaluation's own error (under 1e-14 of its absolute terms, bounded by
+// K (sum |p|)^2 and the linear part) adds the last term.
 constexpr float kRel4 = 2.0e-6f, kAbs4 = 1.0e-9f;
 
-__device__ __forceinline__ void eval32_4(const G4& g, const float* __restrict__ R, const double* __restrict__ t,
-                                         const double* P, float* xi, float* e) {
-  float p[4], ap[4];
-  for (int b = 0; b < 4; b++) {
-    p[b] = (float)S_(P[b], t[b]) * (float)g.inv_dm[b];
-    ap[b] = fabsf(p[b]);
-  }
-  float pp[10], app[10];
+__device__ __forceinline__ void eval32_4(const float* __restrict__ R, const float* p, const float* dp, float* xi,
+                                         float* e) {
+  float ap[4];
+  for (int b = 0; b < 4; b++) ap[b] = fabsf(p[b]);
+  float pp[10], app[10], dpp[10];
   for (int b = 0; b < 4; b++)
     for (int c = b; c < 4; c++) {
       pp[sym4(b, c)] = p[b] * p[c];
       app[sym4(b, c)] = ap[b] * ap[c];
+      // |p_b p_c - p*_b p*_c| for |p - p*| <= dp
+      dpp[sym4(b, c)] = fmaf(ap[b], dp[c], fmaf(ap[c], dp[b], dp[b] * dp[c]));
     }
   const float S = (ap[0] + ap[1]) + (ap[2] + ap[3]);
   for (int a = 0; a < 4; a++) {
-    float v = 0.f, E = 0.f;
+    float v = 0.f, E = 0.f, Ep = 0.f;
     for (int b = 0; b < 4; b++) {
-      v = fmaf(R[4 * a + b], p[b], v);
-      E = fmaf(fabsf(R[4 * a + b]), ap[b], E);
+      const float r = R[4 * a + b];
+      v = fmaf(r, p[b], v);
+      E = fmaf(fabsf(r), ap[b], E);
+      Ep = fmaf(fabsf(r), dp[b], Ep);
     }
     for (int q = 0; q < 10; q++) {
-      v = fmaf(R[16 + 10 * a + q], pp[q], v);
-      E = fmaf(fabsf(R[16 + 10 * a + q]), app[q], E);
+      const float r = R[16 + 10 * a + q];
+      v = fmaf(r, pp[q], v);
+      E = fmaf(fabsf(r), app[q], E);
+      Ep = fmaf(fabsf(r), dpp[q], Ep);
     }
     xi[a] = v;
-    e[a] = kRel4 * E + kAbs4 * (1.f + E) + 1e-13f * R[56 + a] * (S * S) * 16.f;
+    e[a] = kRel4 * E + kAbs4 * (1.f + E) + 1.00001f * Ep + 1e-13f * R[56 + a] * (S * S) * 16.f;
+  }
+}
+
+// p_b = j_b h_b + r_b (element units) from the integer offset j of the site
+// from a reference site and the element's FP32 offset r of that reference
+// site; dp bounds its distance to the FP64 evaluation's dP_b / dm_b
+__device__ __forceinline__ void p_of(const int* j, const float* h, const float* r, float* p, float* dp) {
+  for (int b = 0; b < 4; b++) {
+    const float jh = (float)j[b] * h[b];
+    p[b] = jh + r[b];
+    dp[b] = 6.0e-8f * (fabsf(r[b]) + 2.f * fabsf(jh) + fabsf(p[b])) + 1e-12f;
   }
 }
 
@@ -391,6 +405,36 @@ __device__ __forceinline__ void claim4(ulonglong2* key, unsigned long long dbits
     if (prev.x == cur.x && prev.y == cur.y) break;
     cur = prev;
   }
+}
+
+// Claim of in-grid site p by element m (Sec. 2.3.1: smaller d, then smaller
+// index).  The site's slot takes m + 1 by an exchange; a first claimant needs
+// nothing more.  A claim that displaces an owner folds the exact FP64 keys of
+// both into the site's 128-bit record: every claimant after the first reaches
+// the record with its own key and its predecessor's, so the record's minimum
+// is the exact winner of a contested site, and FP64 distances are spent on
+// contested sites only.
+__device__ __forceinline__ void claim_site(const G4& g, uint32_t* __restrict__ slot, ulonglong2* __restrict__ key,
+                                           long long p, int m, const double* tm, const double* __restrict__ tay,
+                                           const long long* gs, bool have_d2, double d2, unsigned& nev, Dev4* ds) {
+  const uint32_t old = atomicExch(slot + p, (uint32_t)m + 1u);
+  if (old == 0u) return;
+  double P[4];
+  for (int a = 0; a < 4; a++) P[a] = site_coord(g, a, gs[a]);
+  if (!have_d2) {
+    d2 = dist2_4(g, tm, P, nullptr);
+    nev++;
+  }
+  claim4(key + p, (unsigned long long)__double_as_longlong(d2), (unsigned long long)m);
+  const int o = (int)old - 1;
+  if (o == m) return;
+  if (o < 0 || o >= g.ne) {
+    bad(ds, 45);
+    return;
+  }
+  nev++;
+  const double d2o = dist2_4(g, tay + (size_t)NT4 * o, P, nullptr);
+  claim4(key + p, (unsigned long long)__double_as_longlong(d2o), (unsigned long long)o);
 }
 
 // The percolation test (Sec. 2.3.1): the site passes for m unless an element
@@ -466,7 +510,8 @@ __device__ __forceinline__ void decode_w(int lw, int W, int* l) {
 __global__ void __launch_bounds__(PERC_THREADS) k4_percolate(G4 g, const double* __restrict__ el,
                                                     const double* __restrict__ tay,
                                                     const float* __restrict__ tay32, ulonglong2* __restrict__ key,
-                                                    int32_t* __restrict__ ovf_list, Dev4* ds) {
+                                                    uint32_t* __restrict__ slot, int32_t* __restrict__ ovf_list,
+                                                    Dev4* ds) {
   extern __shared__ uint32_t sm4[];
   const int W = g.W;
   const int nwin = W * W * W * W;
@@ -480,6 +525,7 @@ __global__ void __launch_bounds__(PERC_THREADS) k4_percolate(G4 g, const double*
   float* bdf = d2f + TCAP;                                   // TCAP
   __shared__ double tself[NT4];
   __shared__ float rself[NF4];
+  __shared__ float roff[81][4];  // per offset code: the element's FP32 offset of the start site
   __shared__ int org[4], kk[4];
   __shared__ int go, ncur, ntest, npairs, ovf;
   const int m = blockIdx.x;
@@ -522,6 +568,28 @@ __global__ void __launch_bounds__(PERC_THREADS) k4_percolate(G4 g, const double*
   }
   int kl[4];
   for (int a = 0; a < 4; a++) kl[a] = kk[a];
+  // offsets (start site - P_m') / dm of the element and its 80 neighbours,
+  // in FP64, rounded once to FP32
+  for (int code = tid; code < 81; code += blockDim.x) {
+    int o[4], c = code, ok = 1;
+    for (int a = 3; a >= 0; a--) {
+      o[a] = c % 3 - 1;
+      c /= 3;
+    }
+    int mm = 0;
+    for (int a = 0; a < 4; a++) {
+      const int ka = kl[a] + o[a];
+      ok &= (ka >= 0 && ka < g.L[a]);
+      mm = mm * g.L[a] + ka;
+    }
+    for (int a = 0; a < 4; a++)
+      roff[code][a] = ok ? (float)((site_coord(g, a, (long long)org[a] + g.R) - __ldg(tay + (size_t)NT4 * mm + a)) *
+                                   g.inv_dm[a])
+                         : 0.f;
+  }
+  float h[4];
+  for (int a = 0; a < 4; a++) h[a] = (float)(g.d[a] * g.inv_dm[a]);
+  __syncthreads();
   bool first = true;
   while (true) {
     // 1. expansion of the frontier (the first wave tests the start site only)
@@ -559,10 +627,11 @@ __global__ void __launch_bounds__(PERC_THREADS) k4_percolate(G4 g, const double*
     for (int i = tid; i < nt; i += blockDim.x) {
       int l[4];
       decode_w(tlist[i], W, l);
-      double P[4];
-      for (int a = 0; a < 4; a++) P[a] = site_coord(g, a, (long long)org[a] + l[a]);
-      float x[4], e[4];
-      eval32_4(g, rself, tself, P, x, e);
+      int j[4];
+      for (int a = 0; a < 4; a++) j[a] = l[a] - g.R;
+      float pv[4], dp[4], x[4], e[4];
+      p_of(j, h, roff[40], pv, dp);
+      eval32_4(rself, pv, dp, x, e);
       float bd;
       d2f[i] = d2_32(x, e, &bd);
       bdf[i] = bd;
@@ -622,12 +691,12 @@ __global__ void __launch_bounds__(PERC_THREADS) k4_percolate(G4 g, const double*
         code /= 3;
       }
       const int mm = (((kl[0] + o[0]) * g.L[1] + (kl[1] + o[1])) * g.L[2] + (kl[2] + o[2])) * g.L[3] + (kl[3] + o[3]);
-      int l[4];
+      int l[4], jj[4];
       decode_w(tlist[i], W, l);
-      double P[4];
-      for (int a = 0; a < 4; a++) P[a] = site_coord(g, a, (long long)org[a] + l[a]);
-      float x[4], e[4], bn;
-      eval32_4(g, tay32 + (size_t)NF4 * mm, tay + (size_t)NT4 * mm, P, x, e);
+      for (int a = 0; a < 4; a++) jj[a] = l[a] - g.R;
+      float pv[4], dp[4], x[4], e[4], bn;
+      p_of(jj, h, roff[pr & 127], pv, dp);
+      eval32_4(tay32 + (size_t)NF4 * mm, pv, dp, x, e);
       const float dn = d2_32(x, e, &bn);
       const float dm = d2f[i], bm = bdf[i];
       if (dn + bn < dm - bm)
@@ -637,26 +706,19 @@ __global__ void __launch_bounds__(PERC_THREADS) k4_percolate(G4 g, const double*
     }
     if (tid == 0) ncur = 0;
     __syncthreads();
-    // 4. exact tests where the bounds left them open; FP64 keys; claims
+    // 4. exact tests where the bounds left them open; claims
     for (int i = tid; i < nt; i += blockDim.x) {
       const int st = status[i];
       if (st == ST_FAIL) continue;
       int l[4];
       decode_w(tlist[i], W, l);
-      double P[4];
       long long gs[4];
-      for (int a = 0; a < 4; a++) {
-        gs[a] = (long long)org[a] + l[a];
-        P[a] = site_coord(g, a, gs[a]);
-      }
-      double d2;
+      for (int a = 0; a < 4; a++) gs[a] = (long long)org[a] + l[a];
+      double d2 = 0.0;
       if (st == ST_OPEN) {
+        double P[4];
+        for (int a = 0; a < 4; a++) P[a] = site_coord(g, a, gs[a]);
         if (!passes4(g, kl, tself, tay, P, &d2, nev)) continue;
-      } else {
-        bool in = true;
-        for (int a = 0; a < 4; a++) in = in && gs[a] >= 0 && gs[a] < g.n[a];
-        d2 = in ? dist2_4(g, tself, P, nullptr) : 0.0;  // the key is needed for in-grid sites only
-        nev += in;
       }
       bool in = true;
       long long p = 0;
@@ -664,7 +726,7 @@ __global__ void __launch_bounds__(PERC_THREADS) k4_percolate(G4 g, const double*
         in = in && gs[a] >= 0 && gs[a] < g.n[a];
         p += gs[a] * g.st[a];
       }
-      if (in) claim4(key + p, (unsigned long long)__double_as_longlong(d2), (unsigned long long)m);
+      if (in) claim_site(g, slot, key, p, m, tself, tay, gs, st == ST_OPEN, d2, nev, ds);
       const int idx = atomicAdd(&ncur, 1);
       if (idx < FCAP)
         front[idx] = tlist[i];
@@ -687,6 +749,7 @@ __global__ void __launch_bounds__(PERC_THREADS) k4_percolate(G4 g, const double*
 // frontiers in global memory (one slot per block).
 __global__ void __launch_bounds__(256) k4_percolate_big(G4 g, const double* __restrict__ el,
                                                         const double* __restrict__ tay, ulonglong2* __restrict__ key,
+                                                        uint32_t* __restrict__ slot,
                                                         const int32_t* __restrict__ ovf_list, uint32_t* __restrict__ big,
                                                         Dev4* ds) {
   __shared__ double tself[NT4];
@@ -773,7 +836,7 @@ __global__ void __launch_bounds__(256) k4_percolate_big(G4 g, const double* __re
           in = in && gs[a] >= 0 && gs[a] < g.n[a];
           p += gs[a] * g.st[a];
         }
-        if (in) claim4(key + p, (unsigned long long)__double_as_longlong(d2), (unsigned long long)m);
+        if (in) claim_site(g, slot, key, p, m, tself, tay, gs, true, d2, nev, ds);
         const int idx = atomicAdd(&nnext, 1);
         if (idx < BIG_FCAP)
           fn[idx] = (int32_t)np;
@@ -795,20 +858,27 @@ __global__ void __launch_bounds__(256) k4_percolate_big(G4 g, const double* __re
 
 // owner of every site from its key (the key is emptied for the next map);
 // sites nobody claimed go to the hole list
-__global__ void k4_map_finish(G4 g, ulonglong2* __restrict__ key, int32_t* __restrict__ map,
-                              int32_t* __restrict__ holes, Dev4* ds) {
+__global__ void k4_map_finish(G4 g, ulonglong2* __restrict__ key, uint32_t* __restrict__ slot,
+                              int32_t* __restrict__ map, int32_t* __restrict__ holes, Dev4* ds) {
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= g.nsite) return;
   const ulonglong2 k = key[p];
+  const uint32_t sl = slot[p];
   int owner = -1;
-  if (k.y != KEY_EMPTY) {
+  if (k.y != KEY_EMPTY) {  // contested: the record's minimum
     if (k.x < (unsigned long long)g.ne)
       owner = (int)k.x;
     else
       bad(ds, 41);
+    key[p] = make_ulonglong2(KEY_EMPTY, KEY_EMPTY);
+  } else if (sl != 0u) {  // one claimant
+    if (sl <= (uint32_t)g.ne)
+      owner = (int)sl - 1;
+    else
+      bad(ds, 46);
   }
+  if (sl != 0u) slot[p] = 0u;
   map[p] = owner;
-  key[p] = make_ulonglong2(KEY_EMPTY, KEY_EMPTY);
   if (owner < 0) {
     const int i = atomicAdd(&ds->nholes, 1);
     holes[i] = (int32_t)p;
@@ -1430,6 +1500,7 @@ struct vm_4d_solver {
   double *fini, *eta, *f, *el, *tay, *Mpix, *fld, *tab;
   float* tay32;
   ulonglong2* key;
+  uint32_t* slot;
   int32_t *map, *holes, *cand, *ovf_list;
   uint32_t* big;
   double2 *gext, *part;
@@ -1502,7 +1573,7 @@ int nchunks(const G4& g) {
 }
 
 struct Layout {
-  size_t fini, eta, f, key, map, holes, cand, el, tay, tay32, Mpix, fld, gext, part, tab, ovf, big, ds, total;
+  size_t fini, eta, f, key, slot, map, holes, cand, el, tay, tay32, Mpix, fld, gext, part, tab, ovf, big, ds, total;
 };
 
 Layout layout(const G4& g) {
@@ -1518,6 +1589,7 @@ Layout layout(const G4& g) {
   L.eta = take(8 * ns);
   L.f = take(8 * ns);
   L.key = take(16 * ns);
+  L.slot = take(4 * ns);
   L.map = take(4 * ns);
   L.holes = take(4 * ns);
   L.cand = take(4 * ns);
@@ -1599,11 +1671,12 @@ vm_status run_map(vm_4d_solver* s) {
   if (cudaMemsetAsync(&s->ds->nholes, 0, sizeof(int32_t), s->stream) != cudaSuccess ||
       cudaMemsetAsync(&s->ds->novf, 0, sizeof(int32_t), s->stream) != cudaSuccess)
     return VM_E_CUDA;
-  K4_LAUNCH(s, K_PERC, k4_percolate<<<g.ne, PERC_THREADS, s->smem, s->stream>>>(g, s->el, s->tay, s->tay32, s->key, s->ovf_list, s->ds));
+  K4_LAUNCH(s, K_PERC, k4_percolate<<<g.ne, PERC_THREADS, s->smem, s->stream>>>(g, s->el, s->tay, s->tay32, s->key, s->slot,
+                                                                      s->ovf_list, s->ds));
   // returns at once when no element left its window
   K4_LAUNCH(s, K_PERC_BIG,
-            k4_percolate_big<<<BIG_SLOTS, 256, 0, s->stream>>>(g, s->el, s->tay, s->key, s->ovf_list, s->big, s->ds));
-  K4_LAUNCH(s, K_FINISH, k4_map_finish<<<blocks(g.nsite, 256), 256, 0, s->stream>>>(g, s->key, s->map, s->holes, s->ds));
+            k4_percolate_big<<<BIG_SLOTS, 256, 0, s->stream>>>(g, s->el, s->tay, s->key, s->slot, s->ovf_list, s->big, s->ds));
+  K4_LAUNCH(s, K_FINISH, k4_map_finish<<<blocks(g.nsite, 256), 256, 0, s->stream>>>(g, s->key, s->slot, s->map, s->holes, s->ds));
   K4_LAUNCH(s, K_HOLES, k4_holes<<<1, 1024, 0, s->stream>>>(g, s->tay, s->map, s->holes, s->cand, s->ds));
   return VM_OK;
 }
@@ -1683,6 +1756,7 @@ vm_status vm_4d_create(const vm_4d_config* c, void* d_ws, size_t bytes, void* st
   s->eta = (double*)(s->ws + L.eta);
   s->f = (double*)(s->ws + L.f);
   s->key = (ulonglong2*)(s->ws + L.key);
+  s->slot = (uint32_t*)(s->ws + L.slot);
   s->map = (int32_t*)(s->ws + L.map);
   s->holes = (int32_t*)(s->ws + L.holes);
   s->cand = (int32_t*)(s->ws + L.cand);
@@ -1715,6 +1789,7 @@ vm_status vm_4d_create(const vm_4d_config* c, void* d_ws, size_t bytes, void* st
   vm_status st = VM_OK;
   if (cudaMemcpyAsync(s->tab, tab.data(), 8 * tab.size(), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
       cudaMemsetAsync(s->key, 0xff, 16 * (size_t)g.nsite, s->stream) != cudaSuccess ||
+      cudaMemsetAsync(s->slot, 0, 4 * (size_t)g.nsite, s->stream) != cudaSuccess ||
       cudaMemsetAsync(s->map, 0xff, 4 * (size_t)g.nsite, s->stream) != cudaSuccess ||
       cudaMemsetAsync(s->ds, 0, sizeof(Dev4), s->stream) != cudaSuccess ||
       cudaMemsetAsync(s->Mpix, 0, 8 * (size_t)g.n[0] * g.n[1], s->stream) != cudaSuccess ||
