@@ -55,7 +55,7 @@ namespace {
 
 constexpr int NE4 = 60;  // doubles per element
 constexpr int NT4 = 64;  // doubles per Taylor record
-constexpr int FCAP = 1024;  // frontier capacity of the flood fill (sites per wave)
+constexpr int FCAP = 512;  // frontier capacity of the flood fill (sites per wave)
 constexpr int PERC_THREADS = 64;  // one block of two warps per element
 static_assert(PERC_THREADS >= NT4, "a block loads its element's Taylor record one value per thread");
 constexpr int ERR_NC = 1, ERR_OVF = 2, ERR_INT = 4;
@@ -496,8 +496,8 @@ __device__ bool passes4(const G4& g, const int* k, const double* tself, const do
 // The outcome is the all-FP64 percolation's.  Passing sites are claimed and
 // form the next frontier.  An element whose component would leave the window,
 // or whose lists outgrow their buffers, is listed for k4_percolate_big.
-constexpr int TCAP = 1024;  // sites tested per wave
-constexpr int PCAP = 2048;  // (site, neighbour) pairs per wave
+constexpr int TCAP = 512;  // sites tested per wave
+constexpr int PCAP = 1024;  // (site, neighbour) pairs per wave
 enum : int { ST_PASS = 0, ST_OPEN = 1, ST_FAIL = 2 };
 
 __device__ __forceinline__ void decode_w(int lw, int W, int* l) {
@@ -507,7 +507,7 @@ __device__ __forceinline__ void decode_w(int lw, int W, int* l) {
   }
 }
 
-__global__ void __launch_bounds__(PERC_THREADS) k4_percolate(G4 g, const double* __restrict__ el,
+__global__ void __launch_bounds__(PERC_THREADS, 8) k4_percolate(G4 g, const double* __restrict__ el,
                                                     const double* __restrict__ tay,
                                                     const float* __restrict__ tay32, ulonglong2* __restrict__ key,
                                                     uint32_t* __restrict__ slot, int32_t* __restrict__ ovf_list,
