@@ -96,3 +96,23 @@ def test_binding_refuses_arrays_the_call_would_read_past():
     for bad in (np.zeros((6, 8)), np.zeros((8, 6), dtype=np.float32), np.zeros((8, 12))[:, ::2]):
         with pytest.raises(ValueError):
             V.Solver._arg(fake, bad, (8, 6), "float64")
+
+
+def test_4d_host_only_calls(lib):
+    import ctypes as C
+    from paper_1705_03750_gb300 import inputs4d as I4
+    from paper_1705_03750_gb300 import vlamet4d as V4
+    good = V4.config(I4.HALOS4D_16)
+    n = V4.workspace_bytes(good)
+    assert n > 16 ** 4 * (3 * 8 + 16 + 4 * 4)
+    bad = V4.config(I4.HALOS4D_16.with_(n=(3, 16, 16, 16)))
+    assert V4.workspace_bytes(bad) == 0
+    bad = V4.config(I4.HALOS4D_16.with_(s=9))
+    assert V4.workspace_bytes(bad) == 0
+    h = C.c_void_p()
+    # refused before any device work: a bad config, a misaligned or short workspace
+    assert lib.vm_4d_create(C.byref(bad), C.c_void_p(256), 1 << 30, None, C.byref(h)) == 1
+    assert lib.vm_4d_create(C.byref(good), C.c_void_p(257), n, None, C.byref(h)) == 1
+    assert lib.vm_4d_create(C.byref(good), C.c_void_p(256), 16, None, C.byref(h)) == 2
+    assert lib.vm_4d_kernel_name(2).decode() == "percolate"
+    assert lib.vm_4d_kernel_name(99) is None
