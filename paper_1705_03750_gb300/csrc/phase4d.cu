@@ -1372,8 +1372,11 @@ __device__ double spline_eval4_f(const G4& g, const double* __restrict__ eta, co
 // {-1,0,1}, else {0,1}; an offset with two or more non-zero components is
 // dropped when one of them lies on a {-1,0,1} axis).  The beta ranges are
 // decided on the owner's offsets in the exact order; the blend and the spline
-// sum, continuous in their inputs, use fused arithmetic.
-__global__ void __launch_bounds__(128) k4_resample(G4 g, const double* __restrict__ tay, const int32_t* __restrict__ map,
+// sum, continuous in their inputs, use fused arithmetic; an element whose
+// FP32 distance is certainly at least one element spacing (weight 0) is
+// skipped.
+__global__ void __launch_bounds__(128) k4_resample(G4 g, const double* __restrict__ tay,
+                                                  const float* __restrict__ tay32, const int32_t* __restrict__ map,
                                                   const double* __restrict__ eta, double* __restrict__ fnew, Dev4* ds) {
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= g.nsite) return;
@@ -1418,6 +1421,18 @@ __global__ void __launch_bounds__(128) k4_resample(G4 g, const double* __restric
             if (!ok) continue;
             const int mm = ((kk[0] * g.L[1] + kk[1]) * g.L[2] + kk[2]) * g.L[3] + kk[3];
             const double* t = tay + (size_t)NT4 * mm;
+            {
+              // W(2d) = 0 for d >= 1: skip the FP64 evaluation where the FP32
+              // distance and its bound show d^2 >= 1
+              float pv[4], dp[4], xf[4], ef[4], bd;
+              for (int a = 0; a < 4; a++) {
+                pv[a] = (float)((P[a] - __ldg(t + a)) * g.inv_dm[a]);
+                dp[a] = 1.8e-7f * fabsf(pv[a]) + 1e-12f;
+              }
+              eval32_4(tay32 + (size_t)NF4 * mm, pv, dp, xf, ef);
+              const float d2f = d2_32(xf, ef, &bd);
+              if (d2f - bd >= 1.f) continue;
+            }
             double dQ[4], dd = 0.0;
             qofp4_f(t, P, dQ);
             for (int a = 0; a < 4; a++) {
@@ -1712,7 +1727,7 @@ vm_status run_remap(vm_4d_solver* s) {
   vm_status st = run_map(s);
   if (st) return st;
   // f_ini <- spline(f_ini)(Q_r): the resample reads eta only
-  K4_LAUNCH(s, K_RESAMPLE, k4_resample<<<blocks(g.nsite, 128), 128, 0, s->stream>>>(g, s->tay, s->map, s->eta, s->fini, s->ds));
+  K4_LAUNCH(s, K_RESAMPLE, k4_resample<<<blocks(g.nsite, 128), 128, 0, s->stream>>>(g, s->tay, s->tay32, s->map, s->eta, s->fini, s->ds));
   if (cudaMemcpyAsync(s->eta, s->fini, 8 * (size_t)g.nsite, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess)
     return VM_E_CUDA;
   st = run_spline(s);
