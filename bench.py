@@ -215,6 +215,11 @@ NCU_INSTR = {
 }
 SCHEDULERS = 4 * 152
 
+# The same figures for the 4D phase-space path's dominant kernel, captured on
+# its 64^4 workload (profiles/percolate4d_halos4d64_fp64.md)
+NCU4_TRAFFIC = {"percolate": (230_787_072, "phase4d.cu", "eb26be9e8d28f23c")}
+NCU4_INSTR = {"percolate": (6_204_208_147, "phase4d.cu", "eb26be9e8d28f23c")}
+
 
 def issue_roofline(kernel: str, avg_s: float, sm_mhz):
     """Issue roofline of a kernel with a captured instruction count, or None."""
@@ -534,7 +539,7 @@ def run_native(args, rank: int, world: int, dist):
     if world == 1 and not args.no_serve:
         line["serving"] = serve_sample(args)
     if world == 1 and not args.no_4d:
-        line["phase4d"] = phase4d_run(args, dev, peaks)
+        line["phase4d"] = phase4d_run(args, dev, peaks, clock_mhz=(head["clocks"] or {}).get("sm_mhz"))
     return line
 
 
@@ -606,7 +611,7 @@ FLOP4_D2 = 219
 FLOP4_SITE = 305
 
 
-def phase4d_run(args, dev, peaks, fp64_peak=None) -> dict:
+def phase4d_run(args, dev, peaks, fp64_peak=None, clock_mhz=None) -> dict:
     """The 4D phase-space path (2D space) on its 64^4 halo workload: K steps
     device-timed after the warm-up (remaps at their cadence inside), a
     profiled pass over the same step indices for the kernel shares and the
@@ -655,17 +660,31 @@ def phase4d_run(args, dev, peaks, fp64_peak=None) -> dict:
     dom = max(stats, key=lambda k: stats[k][1])
     nl, tms = stats[dom]
     roof = {"kernel": dom, "launches_per_step": nl / K, "avg_ms": tms / nl, "share_of_step": tms / total}
-    if dom in ("percolate", "reconstruct"):
-        if dom == "percolate":
-            flop = FLOP4_D2 * (ev1 - ev0) / nl
-            per, units = f"{FLOP4_D2} FP64 FLOP per distance evaluation", (ev1 - ev0) / nl
-        else:
-            flop = FLOP4_SITE * sites
-            per, units = f"{FLOP4_SITE} FP64 FLOP per site", sites
+    L4 = 1
+    for a in range(4):
+        L4 *= 2 * ((rc.n[a] - 1 + 2 * rc.s - 1) // (2 * rc.s)) + 3
+    if dom == "percolate":
+        # bound by instruction issue (FP32 tests, integer bookkeeping, atomics;
+        # FP64 only at open decisions and contested claims): the capture's
+        # warp instructions over the launch time against one warp instruction
+        # per scheduler per clock
+        n_instr = _keyed(NCU4_INSTR, "percolate")
+        mhz = clock_mhz or 2070.0
+        peak = SCHEDULERS * mhz * 1e6
+        ach = n_instr / (tms / nl / 1e3) if n_instr else None
+        roof.update({"bound": "alu", "achieved": ach, "peak": peak, "unit": "warp-instr/s",
+                     "frac": (ach / peak) if ach else None, "traffic": _keyed(NCU4_TRAFFIC, "percolate"),
+                     "per_unit": "warp instructions of one launch (ncu capture of this source)",
+                     "units": n_instr, "clock_mhz": mhz,
+                     "peak_kind": "4 schedulers x 152 SMs x the SM clock",
+                     "algorithmic_bytes": 4 * sites + (8 * 64 + 4 * 64) * L4,
+                     "fp64_exact_distances_per_launch": (ev1 - ev0) / nl})
+    elif dom == "reconstruct":
+        flop = FLOP4_SITE * sites
         ach = flop / (tms / nl / 1e3) / 1e12
         roof.update({"bound": "alu", "achieved": ach, "peak": fp64_peak / 1e12, "unit": "TFLOP/s (FP64)",
-                     "frac": ach / (fp64_peak / 1e12), "per_unit": per, "units": units,
-                     "peak_kind": "measured in this run (FP64 FMA chains)"})
+                     "frac": ach / (fp64_peak / 1e12), "per_unit": f"{FLOP4_SITE} FP64 FLOP per site",
+                     "units": sites, "peak_kind": "measured in this run (FP64 FMA chains)"})
     # end to end through the C ABI with host buffers over the same step
     # indices: upload of f0 from pinned host memory, then every timed step
     # reads the pixel masses back to the host
@@ -694,10 +713,14 @@ def phase4d_run(args, dev, peaks, fp64_peak=None) -> dict:
            "value": sites * K / (ms / 1e3), "unit": "cell-updates/s", "ms_per_step": ms / K, "dtype": "f64",
            "gpu_launches": launches, "e2e": e2e, "roofline": roof,
            "kernels": {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in sorted(stats.items(), key=lambda kv: -kv[1][1])}}
-    L4 = 1
-    for a in range(4):
-        L4 *= 2 * ((rc.n[a] - 1 + 2 * rc.s - 1) // (2 * rc.s)) + 3
     out["elements"] = L4
+    rl = stats.get("reconstruct")
+    if rl and rl[0] > 0:
+        # the FP64 reconstruction against the FP64 peak measured in this run
+        a_r = FLOP4_SITE * sites / (rl[1] / rl[0] / 1e3) / 1e12
+        out["reconstruct_roofline"] = {"bound": "alu", "achieved": a_r, "peak": fp64_peak / 1e12,
+                                       "unit": "TFLOP/s (FP64)", "frac": a_r / (fp64_peak / 1e12),
+                                       "per_unit": f"{FLOP4_SITE} FP64 FLOP per site", "avg_ms": rl[1] / rl[0]}
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_4d(rc, f0)
     return out
