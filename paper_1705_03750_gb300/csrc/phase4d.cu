@@ -262,8 +262,9 @@ __device__ void inverse4(const double* A, double* B) {
 // A_ab = T^-1_ab dm_b/dm_a, B_a,bc = -(1/2)(2 - [b=c]) sum_l T^-1_al G_l,bc dm_b dm_c/dm_a
 // (the same polynomial the FP64 evaluation computes in another order), and
 // K_a = (1/2) sum_l |T^-1_al| max_bc |G_l,bc| dm_b dm_c / dm_a (bounds the
-// absolute terms of that FP64 evaluation).  Layout: A[16], B[40], K[4], pad.
-constexpr int NF4 = 64;
+// absolute terms of that FP64 evaluation), nA_a = sum_b |A_ab|,
+// nB_a = sum_bc |B_a,bc|.  Layout: A[16], B[40], K[4], nA[4], nB[4], pad.
+constexpr int NF4 = 72;
 
 __global__ void __launch_bounds__(128) k4_taylor(G4 g, const double* __restrict__ el, double* __restrict__ tay,
                                                  float* __restrict__ tay32) {
@@ -308,7 +309,14 @@ __global__ void __launch_bounds__(128) k4_taylor(G4 g, const double* __restrict_
         r[16 + 10 * a + sym4(b, c)] = (float)(-0.5 * (b == c ? 1.0 : 2.0) * v * g.dm[b] * g.dm[c] * g.inv_dm[a]);
       }
   }
-  for (int q = 60; q < NF4; q++) r[q] = 0.f;
+  for (int a = 0; a < 4; a++) {
+    float na = 0.f, nb = 0.f;
+    for (int b = 0; b < 4; b++) na += fabsf(r[4 * a + b]);
+    for (int q = 0; q < 10; q++) nb += fabsf(r[16 + 10 * a + q]);
+    r[60 + a] = na * 1.000001f;
+    r[64 + a] = nb * 1.000001f;
+  }
+  for (int q = 68; q < NF4; q++) r[q] = 0.f;
 }
 
 // FP32 offsets xi of an element at a site with rigorous bounds e_a >=
@@ -322,32 +330,23 @@ constexpr float kRel4 = 2.0e-6f, kAbs4 = 1.0e-9f;
 
 __device__ __forceinline__ void eval32_4(const float* __restrict__ R, const float* p, const float* dp, float* xi,
                                          float* e) {
-  float ap[4];
-  for (int b = 0; b < 4; b++) ap[b] = fabsf(p[b]);
-  float pp[10], app[10], dpp[10];
+  // the absolute terms bounded by the row norms: |sum A p| <= nA max|p|,
+  // |sum B p p| <= nB max|p|^2, and the input bound likewise
+  const float pm = fmaxf(fmaxf(fabsf(p[0]), fabsf(p[1])), fmaxf(fabsf(p[2]), fabsf(p[3])));
+  const float dm = fmaxf(fmaxf(dp[0], dp[1]), fmaxf(dp[2], dp[3]));
+  const float dpp = fmaf(2.f * pm, dm, dm * dm);
+  const float S = 4.f * pm;
+  float pp[10];
   for (int b = 0; b < 4; b++)
-    for (int c = b; c < 4; c++) {
-      pp[sym4(b, c)] = p[b] * p[c];
-      app[sym4(b, c)] = ap[b] * ap[c];
-      // |p_b p_c - p*_b p*_c| for |p - p*| <= dp
-      dpp[sym4(b, c)] = fmaf(ap[b], dp[c], fmaf(ap[c], dp[b], dp[b] * dp[c]));
-    }
-  const float S = (ap[0] + ap[1]) + (ap[2] + ap[3]);
+    for (int c = b; c < 4; c++) pp[sym4(b, c)] = p[b] * p[c];
   for (int a = 0; a < 4; a++) {
-    float v = 0.f, E = 0.f, Ep = 0.f;
-    for (int b = 0; b < 4; b++) {
-      const float r = R[4 * a + b];
-      v = fmaf(r, p[b], v);
-      E = fmaf(fabsf(r), ap[b], E);
-      Ep = fmaf(fabsf(r), dp[b], Ep);
-    }
-    for (int q = 0; q < 10; q++) {
-      const float r = R[16 + 10 * a + q];
-      v = fmaf(r, pp[q], v);
-      E = fmaf(fabsf(r), app[q], E);
-      Ep = fmaf(fabsf(r), dpp[q], Ep);
-    }
+    float v = 0.f;
+    for (int b = 0; b < 4; b++) v = fmaf(R[4 * a + b], p[b], v);
+    for (int q = 0; q < 10; q++) v = fmaf(R[16 + 10 * a + q], pp[q], v);
     xi[a] = v;
+    const float nA = R[60 + a], nB = R[64 + a];
+    const float E = fmaf(nB, pm * pm, nA * pm);
+    const float Ep = fmaf(nB, dpp, nA * dm);
     e[a] = kRel4 * E + kAbs4 * (1.f + E) + 1.00001f * Ep + 1e-13f * R[56 + a] * (S * S) * 16.f;
   }
 }
@@ -500,12 +499,14 @@ constexpr int TCAP = 512;  // sites tested per wave
 constexpr int PCAP = 1024;  // (site, neighbour) pairs per wave
 enum : int { ST_PASS = 0, ST_OPEN = 1, ST_FAIL = 2 };
 
-__device__ __forceinline__ void decode_w(int lw, int W, int* l) {
-  for (int a = 3; a >= 0; a--) {
-    l[a] = lw % W;
-    lw /= W;
-  }
+// list entries hold a site's four window coordinates, one byte each (W <= 25)
+__device__ __forceinline__ void decode_w(int lw, int /*W*/, int* l) {
+  l[0] = lw & 255;
+  l[1] = (lw >> 8) & 255;
+  l[2] = (lw >> 16) & 255;
+  l[3] = (lw >> 24) & 255;
 }
+__device__ __forceinline__ int pack_w(const int* l) { return l[0] | (l[1] << 8) | (l[2] << 16) | (l[3] << 24); }
 
 __global__ void __launch_bounds__(PERC_THREADS, 8) k4_percolate(G4 g, const double* __restrict__ el,
                                                     const double* __restrict__ tay,
@@ -555,15 +556,16 @@ __global__ void __launch_bounds__(PERC_THREADS, 8) k4_percolate(G4 g, const doub
     ovf = 0;
     // the start site is the first wave's only site to test
     const int c = g.R;
-    const int lw = ((c * W + c) * W + c) * W + c;
-    tlist[0] = lw;
+    const int lc[4] = {c, c, c, c};
+    tlist[0] = pack_w(lc);
     ntest = 1;
     ncur = 0;
   }
   __syncthreads();
   if (!go) return;
   if (tid == 0) {
-    const int lw = tlist[0];
+    const int c = g.R;
+    const int lw = ((c * W + c) * W + c) * W + c;
     stamp[lw >> 5] |= 1u << (lw & 31);
   }
   int kl[4];
@@ -613,7 +615,7 @@ __global__ void __launch_bounds__(PERC_THREADS, 8) k4_percolate(G4 g, const doub
         if (atomicOr(&stamp[nw >> 5], bit) & bit) continue;
         const int idx = atomicAdd(&ntest, 1);
         if (idx < TCAP)
-          tlist[idx] = nw;
+          tlist[idx] = pack_w(l);
         else
           ovf = 1;
       }
