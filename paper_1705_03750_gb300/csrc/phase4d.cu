@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(PERC_THREADS, 8) k4_percolate(G4 g, const doub
   const int tid = threadIdx.x;
   unsigned nev = 0;
   if (tid < NT4) tself[tid] = tay[(size_t)NT4 * m + tid];
-  if (tid < NF4) rself[tid] = tay32[(size_t)NF4 * m + tid];
+  for (int q = tid; q < NF4; q += blockDim.x) rself[q] = tay32[(size_t)NF4 * m + q];
   for (int w = tid; w < nwords; w += blockDim.x) stamp[w] = 0u;
   const float af = (float)g.alpha, aerr = 1e-7f * (1.f + af);
   if (tid == 0) {
