@@ -217,8 +217,8 @@ SCHEDULERS = 4 * 152
 
 # The same figures for the 4D phase-space path's dominant kernel, captured on
 # its 64^4 workload (profiles/percolate4d_halos4d64_fp64.md)
-NCU4_TRAFFIC = {"percolate": (230_787_072, "phase4d.cu", "eb26be9e8d28f23c")}
-NCU4_INSTR = {"percolate": (6_204_208_147, "phase4d.cu", "eb26be9e8d28f23c")}
+NCU4_TRAFFIC = {"percolate": (235_557_120, "phase4d.cu", "2549bf83525dad5b")}
+NCU4_INSTR = {"percolate": (4_326_108_844, "phase4d.cu", "2549bf83525dad5b")}
 
 
 def issue_roofline(kernel: str, avg_s: float, sm_mhz):
