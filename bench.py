@@ -677,7 +677,7 @@ def phase4d_run(args, dev, peaks, fp64_peak=None, clock_mhz=None) -> dict:
                      "per_unit": "warp instructions of one launch (ncu capture of this source)",
                      "units": n_instr, "clock_mhz": mhz,
                      "peak_kind": "4 schedulers x 152 SMs x the SM clock",
-                     "algorithmic_bytes": 4 * sites + (8 * 64 + 4 * 64) * L4,
+                     "algorithmic_bytes": 4 * sites + (8 * 64 + 4 * 72) * L4,
                      "fp64_exact_distances_per_launch": (ev1 - ev0) / nl})
     elif dom == "reconstruct":
         flop = FLOP4_SITE * sites
