@@ -351,14 +351,14 @@ __device__ __forceinline__ void eval32_4(const float* __restrict__ R, const floa
   }
 }
 
-// p_b = j_b h_b + r_b (element units) from the integer offset j of the site
-// from a reference site and the element's FP32 offset r of that reference
-// site; dp bounds its distance to the FP64 evaluation's dP_b / dm_b
-__device__ __forceinline__ void p_of(const int* j, const float* h, const float* r, float* p, float* dp) {
+// p_b = j_b h_b + r_b (element units) from the offset j of the site from a
+// reference site, jh_b = (float)j_b * h_b looked up in a per-block table,
+// and the element's FP32 offset r of that reference site; dp bounds its
+// distance to the FP64 evaluation's dP_b / dm_b
+__device__ __forceinline__ void p_of(const float* jh, const float* r, float* p, float* dp) {
   for (int b = 0; b < 4; b++) {
-    const float jh = (float)j[b] * h[b];
-    p[b] = jh + r[b];
-    dp[b] = 6.0e-8f * (fabsf(r[b]) + 2.f * fabsf(jh) + fabsf(p[b])) + 1e-12f;
+    p[b] = jh[b] + r[b];
+    dp[b] = 6.0e-8f * (fabsf(r[b]) + 2.f * fabsf(jh[b]) + fabsf(p[b])) + 1e-12f;
   }
 }
 
@@ -527,6 +527,8 @@ __global__ void __launch_bounds__(PERC_THREADS, 8) k4_percolate(G4 g, const doub
   __shared__ double tself[NT4];
   __shared__ float rself[NF4];
   __shared__ float roff[81][4];  // per offset code: the element's FP32 offset of the start site
+  __shared__ float jht[4][32];   // (float)(l - R) * h_a for window coordinate l
+  __shared__ double pst[4];      // the start site's coordinates
   __shared__ int org[4], kk[4];
   __shared__ int go, ncur, ntest, npairs, ovf;
   const int m = blockIdx.x;
@@ -570,6 +572,12 @@ __global__ void __launch_bounds__(PERC_THREADS, 8) k4_percolate(G4 g, const doub
   }
   int kl[4];
   for (int a = 0; a < 4; a++) kl[a] = kk[a];
+  if (tid < 4) pst[tid] = site_coord(g, tid, (long long)org[tid] + g.R);
+  for (int q = tid; q < 4 * 32; q += blockDim.x) {
+    const int a = q >> 5, l = q & 31;
+    jht[a][l] = (float)(l - g.R) * (float)(g.d[a] * g.inv_dm[a]);
+  }
+  __syncthreads();
   // offsets (start site - P_m') / dm of the element and its 80 neighbours,
   // in FP64, rounded once to FP32
   for (int code = tid; code < 81; code += blockDim.x) {
@@ -585,12 +593,8 @@ __global__ void __launch_bounds__(PERC_THREADS, 8) k4_percolate(G4 g, const doub
       mm = mm * g.L[a] + ka;
     }
     for (int a = 0; a < 4; a++)
-      roff[code][a] = ok ? (float)((site_coord(g, a, (long long)org[a] + g.R) - __ldg(tay + (size_t)NT4 * mm + a)) *
-                                   g.inv_dm[a])
-                         : 0.f;
+      roff[code][a] = ok ? (float)((pst[a] - __ldg(tay + (size_t)NT4 * mm + a)) * g.inv_dm[a]) : 0.f;
   }
-  float h[4];
-  for (int a = 0; a < 4; a++) h[a] = (float)(g.d[a] * g.inv_dm[a]);
   __syncthreads();
   bool first = true;
   while (true) {
@@ -629,10 +633,10 @@ __global__ void __launch_bounds__(PERC_THREADS, 8) k4_percolate(G4 g, const doub
     for (int i = tid; i < nt; i += blockDim.x) {
       int l[4];
       decode_w(tlist[i], W, l);
-      int j[4];
-      for (int a = 0; a < 4; a++) j[a] = l[a] - g.R;
+      float jh[4];
+      for (int a = 0; a < 4; a++) jh[a] = jht[a][l[a]];
       float pv[4], dp[4], x[4], e[4];
-      p_of(j, h, roff[40], pv, dp);
+      p_of(jh, roff[40], pv, dp);
       eval32_4(rself, pv, dp, x, e);
       float bd;
       d2f[i] = d2_32(x, e, &bd);
@@ -693,11 +697,12 @@ __global__ void __launch_bounds__(PERC_THREADS, 8) k4_percolate(G4 g, const doub
         code /= 3;
       }
       const int mm = (((kl[0] + o[0]) * g.L[1] + (kl[1] + o[1])) * g.L[2] + (kl[2] + o[2])) * g.L[3] + (kl[3] + o[3]);
-      int l[4], jj[4];
+      int l[4];
       decode_w(tlist[i], W, l);
-      for (int a = 0; a < 4; a++) jj[a] = l[a] - g.R;
+      float jh[4];
+      for (int a = 0; a < 4; a++) jh[a] = jht[a][l[a]];
       float pv[4], dp[4], x[4], e[4], bn;
-      p_of(jj, h, roff[pr & 127], pv, dp);
+      p_of(jh, roff[pr & 127], pv, dp);
       eval32_4(tay32 + (size_t)NF4 * mm, pv, dp, x, e);
       const float dn = d2_32(x, e, &bn);
       const float dm = d2f[i], bm = bdf[i];
