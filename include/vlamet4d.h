@@ -58,6 +58,16 @@ typedef struct {
 
 typedef struct vm_4d_solver vm_4d_solver;
 
+typedef struct {
+  double mass;      /* sum f dx dy dvx dvy of the last f */
+  double ekin;      /* (1/2) sum (vx^2 + vy^2) f dx dy dvx dvy */
+  double epot;      /* (1/2) sum_p M_p phi_p, phi_p = 2 G sum_{q != p} M_q ln|r_p - r_q| over the
+                       pixel masses M of the last f (the discrete energy of Sec. 2.5's Poisson
+                       solution in 2D space) */
+  double detT_min;  /* range of det T over the elements (Sec. 2.1, |T| = 1) */
+  double detT_max;
+} vm_4d_diag;
+
 /* Device bytes a solver of config *c needs (0 if *c is invalid). */
 size_t vm_4d_workspace_bytes(const vm_4d_config* c);
 
@@ -106,6 +116,10 @@ vm_status vm_4d_density_force(vm_4d_solver* s, double* M, double* field, int on_
 /* Element state in and out (60 doubles per element, layout above). */
 vm_status vm_4d_get_elements(vm_4d_solver* s, double* out, int on_device);
 vm_status vm_4d_set_elements(vm_4d_solver* s, const double* in, int on_device);
+
+/* Conservation diagnostics of the last f (f0 after vm_4d_set_f, else the last
+ * reconstruction's f(t + dt/2)) and of the elements (synchronises). */
+vm_status vm_4d_diagnostics(vm_4d_solver* s, vm_4d_diag* out);
 
 /* Number of elements, lattice dimensions (L[4]) and kernel launches so far. */
 int32_t vm_4d_num_elements(const vm_4d_solver* s, int32_t* L4);

@@ -1468,6 +1468,72 @@ __global__ void __launch_bounds__(128) k4_resample(G4 g, const double* __restric
   fnew[p] = val;
 }
 
+// Diagnostics: per (x, y) pixel, sum f and sum (vx^2 + vy^2) f of its
+// velocity plane (one block per pixel, sums in a fixed order)
+__global__ void __launch_bounds__(256) k4_diag_pix(G4 g, const double* __restrict__ f, double* __restrict__ out) {
+  __shared__ double r0[8], r1[8];
+  const int pix = blockIdx.x;
+  const int nvel = g.n[2] * g.n[3];
+  const long long base = (long long)pix * nvel;
+  double s0 = 0.0, s1 = 0.0;
+  for (int q = threadIdx.x; q < nvel; q += blockDim.x) {
+    const double fv = f[base + q];
+    const double vx = g.lo[2] + (double)(q / g.n[3]) * g.d[2];
+    const double vy = g.lo[3] + (double)(q % g.n[3]) * g.d[3];
+    s0 += fv;
+    s1 += (vx * vx + vy * vy) * fv;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_down_sync(0xffffffffu, s0, o);
+    s1 += __shfl_down_sync(0xffffffffu, s1, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    r0[threadIdx.x >> 5] = s0;
+    r1[threadIdx.x >> 5] = s1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+      a += r0[w];
+      b += r1[w];
+    }
+    out[2 * pix] = a * g.dV;
+    out[2 * pix + 1] = 0.5 * b * g.dV;
+  }
+}
+
+// potential phi_p = 2 G sum_{q != p} M_q ln|r_p - r_q| at every pixel
+__global__ void k4_diag_phi(G4 g, const double* __restrict__ pm, double* __restrict__ phi) {
+  const int np = g.n[0] * g.n[1];
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  const long long i = p / g.n[1], j = p % g.n[1];
+  double acc = 0.0;
+  for (int q = 0; q < np; q++) {
+    if (q == p) continue;
+    const double rx = (double)(i - q / g.n[1]) * g.d[0], ry = (double)(j - q % g.n[1]) * g.d[1];
+    acc += pm[2 * q] * (0.5 * log(rx * rx + ry * ry));
+  }
+  phi[p] = g.twoG * acc;
+}
+
+__device__ double det4_d(const double* A) {
+  const double s0 = A[0] * A[5] - A[4] * A[1], s1 = A[0] * A[6] - A[4] * A[2];
+  const double s2 = A[0] * A[7] - A[4] * A[3], s3 = A[1] * A[6] - A[5] * A[2];
+  const double s4 = A[1] * A[7] - A[5] * A[3], s5 = A[2] * A[7] - A[6] * A[3];
+  const double c5 = A[10] * A[15] - A[14] * A[11], c4 = A[9] * A[15] - A[13] * A[11];
+  const double c3 = A[9] * A[14] - A[13] * A[10], c2 = A[8] * A[15] - A[12] * A[11];
+  const double c1 = A[8] * A[14] - A[12] * A[10], c0 = A[8] * A[13] - A[12] * A[9];
+  return ((((s0 * c5 - s1 * c4) + s2 * c3) + s3 * c2) - s4 * c1) + s5 * c0;
+}
+
+__global__ void k4_diag_det(G4 g, const double* __restrict__ el, double* __restrict__ det) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= g.ne) return;
+  det[m] = det4_d(el + (size_t)NE4 * m + 4);
+}
+
 // Batched tridiagonal solves of the zero-slope cubic spline along one axis
 // (Sec. 2.2.2), in place on eta, one thread per line.  tab holds, per node i
 // of the axis, the sub-diagonal, the pivot and the eliminated super-diagonal
@@ -1503,10 +1569,10 @@ __global__ void k4_spline_axis(G4 g, int ax, const double* __restrict__ tab, dou
 
 namespace {
 enum K4Id { K_DRIFT, K_TAYLOR, K_PERC, K_PERC_BIG, K_FINISH, K_HOLES, K_RECON, K_ACCEL, K_ACCEL_SUM, K_KICK,
-            K_RESAMPLE, K_SPLINE, K_RESET, K_FIELDS, K_COUNT };
+            K_RESAMPLE, K_SPLINE, K_RESET, K_FIELDS, K_DIAG, K_COUNT };
 const char* const k4_names[K_COUNT] = {"drift", "taylor", "percolate", "percolate_big", "map_finish", "holes",
                                        "reconstruct", "accel", "accel_sum", "kick_drift", "resample", "spline_axis",
-                                       "reset", "node_fields"};
+                                       "reset", "node_fields", "diagnostics"};
 struct ProfRec {
   int id;
   cudaEvent_t a, b;
@@ -1519,7 +1585,7 @@ struct vm_4d_solver {
   std::vector<ProfRec> prof;
   cudaStream_t stream;
   char* ws;
-  double *fini, *eta, *f, *el, *tay, *Mpix, *fld, *tab;
+  double *fini, *eta, *f, *el, *tay, *Mpix, *fld, *tab, *diag;
   float* tay32;
   ulonglong2* key;
   uint32_t* slot;
@@ -1595,7 +1661,7 @@ int nchunks(const G4& g) {
 }
 
 struct Layout {
-  size_t fini, eta, f, key, slot, map, holes, cand, el, tay, tay32, Mpix, fld, gext, part, tab, ovf, big, ds, total;
+  size_t diag, fini, eta, f, key, slot, map, holes, cand, el, tay, tay32, Mpix, fld, gext, part, tab, ovf, big, ds, total;
 };
 
 Layout layout(const G4& g) {
@@ -1607,6 +1673,7 @@ Layout layout(const G4& g) {
     o = up(o + bytes);
     return at;
   };
+  L.diag = take(8 * (3 * (size_t)g.n[0] * g.n[1] + (size_t)g.ne));
   L.fini = take(8 * ns);
   L.eta = take(8 * ns);
   L.f = take(8 * ns);
@@ -1774,6 +1841,7 @@ vm_status vm_4d_create(const vm_4d_config* c, void* d_ws, size_t bytes, void* st
   s->n_s = c->n_s;
   s->stream = (cudaStream_t)stream;
   s->ws = (char*)d_ws;
+  s->diag = (double*)(s->ws + L.diag);
   s->fini = (double*)(s->ws + L.fini);
   s->eta = (double*)(s->ws + L.eta);
   s->f = (double*)(s->ws + L.f);
@@ -1951,6 +2019,39 @@ vm_status vm_4d_map_stats(vm_4d_solver* s, int32_t* out3, int64_t* d2_evals) {
   out3[1] = h.nholes;
   out3[2] = h.rounds;
   if (d2_evals) *d2_evals = (int64_t)h.d2_evals;
+  return VM_OK;
+}
+
+vm_status vm_4d_diagnostics(vm_4d_solver* s, vm_4d_diag* out) {
+  if (!s || !out) return VM_E_INVALID_ARG;
+  const G4& g = s->g;
+  const int np = g.n[0] * g.n[1];
+  double* pm = s->diag;            // 2 per pixel: mass, kinetic energy
+  double* phi = s->diag + 2 * (size_t)np;
+  double* det = s->diag + 3 * (size_t)np;
+  K4_LAUNCH(s, K_DIAG, k4_diag_pix<<<np, 256, 0, s->stream>>>(g, s->f, pm));
+  K4_LAUNCH(s, K_DIAG, k4_diag_phi<<<blocks(np, 128), 128, 0, s->stream>>>(g, pm, phi));
+  K4_LAUNCH(s, K_DIAG, k4_diag_det<<<blocks(g.ne, 128), 128, 0, s->stream>>>(g, s->el, det));
+  std::vector<double> h(3 * (size_t)np + (size_t)g.ne);
+  vm_status st = copy_out(s, h.data(), s->diag, 8 * h.size(), 0);
+  if (st) return st;
+  double mass = 0.0, ek = 0.0, ep = 0.0;
+  for (int p = 0; p < np; p++) {
+    mass += h[2 * (size_t)p];
+    ek += h[2 * (size_t)p + 1];
+    ep += 0.5 * h[2 * (size_t)p] * h[2 * (size_t)np + p];
+  }
+  double lo = INFINITY, hi = -INFINITY;
+  for (int m = 0; m < g.ne; m++) {
+    const double d = h[3 * (size_t)np + m];
+    lo = std::min(lo, d);
+    hi = std::max(hi, d);
+  }
+  out->mass = mass;
+  out->ekin = ek;
+  out->epot = ep;
+  out->detT_min = lo;
+  out->detT_max = hi;
   return VM_OK;
 }
 

@@ -41,7 +41,7 @@ EXPORTS = ["vm_config_default", "vm_workspace_bytes", "vm_create", "vm_destroy",
            "vm_4d_reconstruct", "vm_4d_remap", "vm_4d_read_f", "vm_4d_read_fini", "vm_4d_read_eta",
            "vm_4d_read_map", "vm_4d_density_force", "vm_4d_get_elements", "vm_4d_set_elements",
            "vm_4d_num_elements", "vm_4d_launches", "vm_4d_map_stats", "vm_4d_sync",
-           "vm_4d_profile", "vm_4d_profile_read", "vm_4d_kernel_name"]
+           "vm_4d_profile", "vm_4d_profile_read", "vm_4d_kernel_name", "vm_4d_diagnostics"]
 
 VM_STATIC_FORCE_MAX_NX = 16384
 
@@ -171,6 +171,7 @@ def load() -> C.CDLL:
         "vm_4d_profile": (i32, [vp, i32]),
         "vm_4d_profile_read": (i32, [vp, C.POINTER(i64), dp, i32]),
         "vm_4d_kernel_name": (C.c_char_p, [i32]),
+        "vm_4d_diagnostics": (i32, [vp, vp]),
         "vm_4d_sync": (i32, [vp]),
     }
     for name, (res, args) in sig.items():

@@ -23,6 +23,11 @@ class Vm4dConfig(C.Structure):
     ]
 
 
+class Vm4dDiag(C.Structure):
+    _fields_ = [("mass", C.c_double), ("ekin", C.c_double), ("epot", C.c_double),
+                ("detT_min", C.c_double), ("detT_max", C.c_double)]
+
+
 def config(rc, alpha=math.sqrt(3.0) / 4.0, beta=0.5 * (1.0 - math.sqrt(3.0) / 2.0), pad=0,
            max_hole_rounds=0) -> Vm4dConfig:
     """vm_4d_config of a 4D run configuration (grid, box, stride, dt, n_s, G)."""
@@ -157,6 +162,11 @@ class Solver4D:
             el = np.ascontiguousarray(el, dtype=np.float64)
         p, dev = self._arg(el, (self.ne, 60), "float64")
         V._check(self.L.vm_4d_set_elements(self.h, p, dev), "vm_4d_set_elements")
+
+    def diagnostics(self) -> dict:
+        d = Vm4dDiag()
+        V._check(self.L.vm_4d_diagnostics(self.h, C.byref(d)), "vm_4d_diagnostics")
+        return {k: getattr(d, k) for k, _ in Vm4dDiag._fields_}
 
     def density_force(self) -> dict:
         M = np.empty(self.n[:2])

@@ -163,3 +163,18 @@ def test_full_size_map_and_reconstruction_after_a_cycle():
     fo = o.reconstruct()
     assert (s.read_map() == o.last_map()).all()
     assert np.abs(s.read_f() - fo).max() <= 1e-12 * np.abs(fo).max()
+
+
+def test_diagnostics_match_oracle():
+    rc = I4.HALOS4D_16
+    s, o, f0 = _pair(rc)
+    for k in (0, 3):
+        if k:
+            s.step(k)
+            o.step(k)
+        dg = s.diagnostics()
+        do = o.diagnostics()
+        for key in ("mass", "ekin", "epot"):
+            assert dg[key] == pytest.approx(do[key], rel=1e-10), (k, key)
+        assert dg["detT_min"] == pytest.approx(do["detT_min"], abs=1e-12)
+        assert dg["detT_max"] == pytest.approx(do["detT_max"], abs=1e-12)
