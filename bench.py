@@ -217,8 +217,8 @@ SCHEDULERS = 4 * 152
 
 # The same figures for the 4D phase-space path's dominant kernel, captured on
 # its 64^4 workload (profiles/percolate4d_halos4d64_fp64.md)
-NCU4_TRAFFIC = {"percolate": (235_272_192, "phase4d.cu", "4e86990f6ed6c1e6")}
-NCU4_INSTR = {"percolate": (4_068_069_519, "phase4d.cu", "4e86990f6ed6c1e6")}
+NCU4_TRAFFIC = {"percolate": (236_288_768, "phase4d.cu", "e9b54be3905142c1")}
+NCU4_INSTR = {"percolate": (4_068_047_765, "phase4d.cu", "e9b54be3905142c1")}
 
 
 def issue_roofline(kernel: str, avg_s: float, sm_mhz):
