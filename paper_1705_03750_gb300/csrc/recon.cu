@@ -210,6 +210,67 @@ __device__ __forceinline__ void blended_q(const Grid& g, const double* __restric
   }
 }
 
+// The same blend for the FP64 remap, the beta ranges decided on the owner's
+// offsets in the fixed order (the one integer decision here) and the
+// neighbours' inverse maps, weights and sums in fused FP64: Q_r is continuous
+// in them (W(2d) vanishes at the support's edge), and so is the spline sum
+// it feeds, so the fused values agree with the fixed order to rounding.
+__device__ __forceinline__ void qofp_fused(const double* __restrict__ t, double Px, double Pv, double& dqx,
+                                           double& dqv) {
+  const double dPx = Px - t[TY_X], dPv = Pv - t[TY_V];
+  const double yx = fma(t[TY_TI01], dPv, t[TY_TI00] * dPx), yv = fma(t[TY_TI11], dPv, t[TY_TI10] * dPx);
+  const double sx = fma(dPx, fma(t[TY_GX01], dPv, t[TY_GX00] * dPx), dPv * fma(t[TY_GX11], dPv, t[TY_GX01] * dPx));
+  const double sv = fma(dPx, fma(t[TY_GV01], dPv, t[TY_GV00] * dPx), dPv * fma(t[TY_GV11], dPv, t[TY_GV01] * dPx));
+  dqx = fma(-0.5, fma(t[TY_TI01], sv, t[TY_TI00] * sx), yx);
+  dqv = fma(-0.5, fma(t[TY_TI11], sv, t[TY_TI10] * sx), yv);
+}
+
+__device__ __forceinline__ void blended_q_fused(const Grid& g, const double* __restrict__ tay, int m, double Px,
+                                                double Pv, double& Qx, double& Qv) {
+  double xi, ze;
+  dist2_exact(tay + (size_t)m * TY_N, g, Px, Pv, xi, ze);
+  const double beta = g.beta;
+  const int a0 = (xi < -beta) ? -1 : ((xi < beta) ? -1 : 0);
+  const int a1 = (xi < -beta) ? 0 : 1;
+  const int b0 = (ze < -beta) ? -1 : ((ze < beta) ? -1 : 0);
+  const int b1 = (ze < -beta) ? 0 : 1;
+  const bool full = (a0 == -1 && a1 == 1) || (b0 == -1 && b1 == 1);
+  const int k = m / g.Lv, l = m - k * g.Lv;
+  double nx_ = 0.0, nv_ = 0.0, den = 0.0;
+  for (int a = a0; a <= a1; a++)
+    for (int b = b0; b <= b1; b++) {
+      if (full && a != 0 && b != 0) continue;
+      const int kk = k + a, ll = l + b;
+      if (!elem_exists(g, kk, ll)) continue;
+      const double* t = tay + (size_t)(kk * g.Lv + ll) * TY_N;
+      double dqx, dqv;
+      qofp_fused(t, Px, Pv, dqx, dqv);
+      const double x1 = dqx * g.inv_dxm, z1 = dqv * g.inv_dvm;
+      const double x = 2.0 * sqrt(fma(x1, x1, z1 * z1));
+      double wgt = 0.0;
+      if (x <= 1.0) {
+        wgt = fma(0.75 * x, x * x, fma(-1.5 * x, x, 1.0));
+      } else if (x <= 2.0) {
+        const double r = 2.0 - x;
+        wgt = 0.25 * (r * r * r);
+      }
+      nx_ = fma(wgt, t[TY_QX] + dqx, nx_);
+      nv_ = fma(wgt, t[TY_QV] + dqv, nv_);
+      den += wgt;
+    }
+  if (den > 0.0) {
+    const double id = 1.0 / den;
+    Qx = nx_ * id;
+    Qv = nv_ * id;
+  } else {
+    const double* t = tay + (size_t)m * TY_N;
+    double dqx, dqv;
+    qofp_fused(t, Px, Pv, dqx, dqv);
+    Qx = t[TY_QX] + dqx;
+    Qv = t[TY_QV] + dqv;
+  }
+}
+
 __device__ __forceinline__ long long ghost(long long k, int n) {
   if (k >= 0 && k < n) return k;
   if (k == -1) return 1;
@@ -271,9 +332,9 @@ __device__ __forceinline__ void k_remap64_body(const Grid& g, const uint32_t* __
     double val = 0.0;
     if (m >= 0) {
       double Qx, Qv;
-      blended_q(g, tay, m, Px, site_v(g, j), Qx, Qv);
-      const double u = dmul(dsub(Qx, g.x_lo), g.inv_dx);
-      const double w = dmul(dsub(Qv, g.v_lo), g.inv_dv);
+      blended_q_fused(g, tay, m, Px, site_v(g, j), Qx, Qv);
+      const double u = (Qx - g.x_lo) * g.inv_dx;
+      const double w = (Qv - g.v_lo) * g.inv_dv;
       val = spline_eval(eta, g, u, w);
     }
     out[p] = (R)val;
