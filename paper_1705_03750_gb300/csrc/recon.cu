@@ -6,8 +6,9 @@
 // Q_r blended over the beta set of elements with the Monaghan kernel, then
 // the cubic B-spline of f_ini at Q_r.
 //
-// FP64 path: Q, the node choice and the interpolation in FP64, evaluated in
-// a fixed operation order.  FP32-mixed path: Q from the element's FP32
+// FP64 path: Q, the node choice and the interpolation in FP64, the decisions
+// taken in a fixed operation order (the remap's blend, continuous in its
+// inputs, in fused FP64 once the beta ranges are decided).  FP32-mixed path: Q from the element's FP32
 // record in element units, anchored on the exact lattice position of Q_m, so
 // that only the small offset carries FP32 rounding; the integer decisions
 // (nearest node, containing square, beta ranges) are taken from the FP32
