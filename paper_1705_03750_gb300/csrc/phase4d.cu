@@ -971,45 +971,12 @@ __device__ __forceinline__ double F4at(const G4& g, const double* __restrict__ F
   return __ldg(F + c[0] * g.st[0] + c[1] * g.st[1] + c[2] * g.st[2] + c[3]);
 }
 
-// nearest node, its 9-point cross, and per pair of axes the corner of the
-// square that holds the projection of u (from the integer parts)
-__device__ double qinterp4(const G4& g, const double* __restrict__ F, const double* u) {
-  for (int a = 0; a < 4; a++)
-    if (!(u[a] > -2.0 && u[a] < (double)g.n[a] + 1.0)) return 0.0;
-  long long gn[4], gc[4];
-  double dq[4];
-  for (int a = 0; a < 4; a++) {
-    gn[a] = nearest_i(u[a]);
-    gc[a] = (long long)floor(u[a]);
-    dq[a] = S_(u[a], (double)gn[a]);
-  }
-  const double w0 = S_(S_(S_(S_(1.0, M_(dq[0], dq[0])), M_(dq[1], dq[1])), M_(dq[2], dq[2])), M_(dq[3], dq[3]));
-  double f = M_(F4at(g, F, gn), w0);
-  for (int a = 0; a < 4; a++) {
-    long long c[4] = {gn[0], gn[1], gn[2], gn[3]};
-    c[a] = gn[a] + 1;
-    f = A_(f, M_(M_(M_(0.5, F4at(g, F, c)), dq[a]), A_(1.0, dq[a])));
-    c[a] = gn[a] - 1;
-    f = A_(f, M_(M_(M_(0.5, F4at(g, F, c)), dq[a]), S_(dq[a], 1.0)));
-  }
-  for (int a = 0; a < 4; a++)
-    for (int b = a + 1; b < 4; b++) {
-      long long c00[4] = {gn[0], gn[1], gn[2], gn[3]};
-      c00[a] = gc[a];
-      c00[b] = gc[b];
-      long long c11[4] = {c00[0], c00[1], c00[2], c00[3]}, c10[4] = {c00[0], c00[1], c00[2], c00[3]},
-                c01[4] = {c00[0], c00[1], c00[2], c00[3]};
-      c11[a] += 1;
-      c11[b] += 1;
-      c10[a] += 1;
-      c01[b] += 1;
-      const double cross = S_(S_(A_(F4at(g, F, c11), F4at(g, F, c00)), F4at(g, F, c10)), F4at(g, F, c01));
-      f = A_(f, M_(M_(cross, dq[a]), dq[b]));
-    }
-  return f;
-}
-
-// The same interpolant with fused arithmetic (stencil chosen from u as above)
+// 15-point quadratic interpolation (Sec. 2.2.1) at index coordinates u: the
+// nearest node, its 9-point cross (Lagrange weights on {-1,0,1} per axis),
+// and per pair of axes the corner of the square of that pair's plane through
+// the nearest node that holds the projection of u (from the integer parts);
+// nodes outside the grid read 0.  Values in fused arithmetic; the stencil is
+// chosen from u.
 __device__ double qinterp4_f(const G4& g, const double* __restrict__ F, const double* u) {
   for (int a = 0; a < 4; a++)
     if (!(u[a] > -2.0 && u[a] < (double)g.n[a] + 1.0)) return 0.0;
@@ -1261,25 +1228,7 @@ __global__ void __launch_bounds__(128) k4_kick_drift(G4 g, const double* __restr
 // Secs. 2.2.2 and 2.3.2: remap
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ double bspline3_4(double t) {
-  t = fabs(t);
-  if (t < 1.0) return A_(S_(2.0 / 3.0, M_(t, t)), M_(0.5, M_(M_(t, t), t)));
-  if (t < 2.0) {
-    const double r = S_(2.0, t);
-    return __ddiv_rn(M_(M_(r, r), r), 6.0);
-  }
-  return 0.0;
-}
-
-__device__ __forceinline__ double W4(double x) {
-  if (x <= 1.0) return A_(S_(1.0, M_(1.5, M_(x, x))), M_(0.75, M_(M_(x, x), x)));
-  if (x <= 2.0) {
-    const double r = S_(2.0, x);
-    return M_(0.25, M_(M_(r, r), r));
-  }
-  return 0.0;
-}
-
+// Monaghan M4 kernel W(x), unnormalised (Sec. 2.3.2), fused arithmetic
 __device__ __forceinline__ double W4f(double x) {
   if (x <= 1.0) return fma(0.75 * x, x * x, fma(-1.5 * x, x, 1.0));
   if (x <= 2.0) {
@@ -1289,6 +1238,7 @@ __device__ __forceinline__ double W4f(double x) {
   return 0.0;
 }
 
+// uniform cubic B-spline B(t), support [-2, 2], fused arithmetic
 __device__ __forceinline__ double bspline3_f(double t) {
   t = fabs(t);
   if (t < 1.0) return fma(0.5 * t, t * t, fma(-t, t, 2.0 / 3.0));
@@ -1306,40 +1256,11 @@ __device__ __forceinline__ long long ghost4(long long k, int n) {
   return -1;
 }
 
-// sum over the 4^4 coefficients around u of eta_k prod_a B(u_a - k_a)
-__device__ double spline_eval4(const G4& g, const double* __restrict__ eta, const double* u) {
-  for (int a = 0; a < 4; a++)
-    if (!(u[a] > -3.0 && u[a] < (double)(g.n[a] + 2))) return 0.0;
-  double B[4][4];
-  long long gk[4][4];
-  for (int a = 0; a < 4; a++) {
-    const long long k0 = (long long)floor(u[a]) - 1;
-    for (int q = 0; q < 4; q++) {
-      B[a][q] = bspline3_4(S_(u[a], (double)(k0 + q)));
-      gk[a][q] = ghost4(k0 + q, g.n[a]);
-    }
-  }
-  double sum = 0.0;
-  for (int q0 = 0; q0 < 4; q0++) {
-    if (gk[0][q0] < 0) continue;
-    for (int q1 = 0; q1 < 4; q1++) {
-      if (gk[1][q1] < 0) continue;
-      for (int q2 = 0; q2 < 4; q2++) {
-        if (gk[2][q2] < 0) continue;
-        const long long b012 = gk[0][q0] * g.st[0] + gk[1][q1] * g.st[1] + gk[2][q2] * g.st[2];
-        for (int q3 = 0; q3 < 4; q3++) {
-          if (gk[3][q3] < 0) continue;
-          const double v = __ldg(eta + b012 + gk[3][q3]);
-          sum = A_(sum, M_(M_(M_(M_(v, B[0][q0]), B[1][q1]), B[2][q2]), B[3][q3]));
-        }
-      }
-    }
-  }
-  return sum;
-}
-
-// The spline sum with fused arithmetic: it is C2 in u, so the choice of the
-// cell (floor(u)) where u lies on a knot does not change its value.
+// Cubic B-spline of the coefficients eta at index coordinates u (Sec. 2.2.2):
+// the sum over the 4^4 coefficients around u of eta_k prod_a B(u_a - k_a),
+// with the zero-slope mirror ghosts, zero beyond its support.  Fused
+// arithmetic; the sum is C2 in u, so the choice of the cell (floor(u)) where
+// u lies on a knot does not change its value.
 __device__ double spline_eval4_f(const G4& g, const double* __restrict__ eta, const double* u) {
   for (int a = 0; a < 4; a++)
     if (!(u[a] > -3.0 && u[a] < (double)(g.n[a] + 2))) return 0.0;
