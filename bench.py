@@ -216,9 +216,13 @@ NCU_INSTR = {
 SCHEDULERS = 4 * 152
 
 # The same figures for the 4D phase-space path's dominant kernel, captured on
-# its 64^4 workload (profiles/percolate4d_halos4d64_fp64.md)
-NCU4_TRAFFIC = {"percolate": (236_288_768, "phase4d.cu", "e9b54be3905142c1")}
-NCU4_INSTR = {"percolate": (4_068_047_765, "phase4d.cu", "e9b54be3905142c1")}
+# its 64^4 workload (profiles/percolate4d_halos4d64_fp64.md).  The key hashes
+# the source up to the start of its reconstruction section: the percolation
+# kernels and everything they use come before it in the translation unit, so
+# changes further down cannot change their code.
+PHASE4D_PREFIX_END = "// Sec. 2.2.1: 15-point quadratic interpolation; transport reconstruction"
+NCU4_TRAFFIC = {"percolate": (236_288_768, "phase4d.cu", "908be1a679b46900")}
+NCU4_INSTR = {"percolate": (4_068_047_765, "phase4d.cu", "908be1a679b46900")}
 
 
 def issue_roofline(kernel: str, avg_s: float, sm_mhz):
@@ -236,7 +240,10 @@ def ncu_traffic(kernel: str):
     return _keyed(NCU_TRAFFIC, kernel)
 
 
-def _keyed(table, kernel: str):
+def _keyed(table, kernel: str, prefix_end: str | None = None):
+    """The table's figure for `kernel` if its source still hashes to the
+    captured key (the whole file, or its text before the line `prefix_end`,
+    the start of the section's rule line above it), else None."""
     ent = table.get(kernel)
     if not ent:
         return None
@@ -245,9 +252,15 @@ def _keyed(table, kernel: str):
     path = os.path.join(ROOT, "paper_1705_03750_gb300", "csrc", src)
     try:
         with open(path, "rb") as fh:
-            h = hashlib.sha256(fh.read()).hexdigest()
+            text = fh.read()
     except OSError:
         return None
+    if prefix_end is not None:
+        i = text.find(prefix_end.encode())
+        if i < 0:
+            return None
+        text = text[:text.rindex(b"\n// ----", 0, i)]
+    h = hashlib.sha256(text).hexdigest()
     return nbytes if h.startswith(sha) else None
 
 
@@ -668,12 +681,13 @@ def phase4d_run(args, dev, peaks, fp64_peak=None, clock_mhz=None) -> dict:
         # FP64 only at open decisions and contested claims): the capture's
         # warp instructions over the launch time against one warp instruction
         # per scheduler per clock
-        n_instr = _keyed(NCU4_INSTR, "percolate")
+        n_instr = _keyed(NCU4_INSTR, "percolate", PHASE4D_PREFIX_END)
         mhz = clock_mhz or 2070.0
         peak = SCHEDULERS * mhz * 1e6
         ach = n_instr / (tms / nl / 1e3) if n_instr else None
         roof.update({"bound": "alu", "achieved": ach, "peak": peak, "unit": "warp-instr/s",
-                     "frac": (ach / peak) if ach else None, "traffic": _keyed(NCU4_TRAFFIC, "percolate"),
+                     "frac": (ach / peak) if ach else None,
+                     "traffic": _keyed(NCU4_TRAFFIC, "percolate", PHASE4D_PREFIX_END),
                      "per_unit": "warp instructions of one launch (ncu capture of this source)",
                      "units": n_instr, "clock_mhz": mhz,
                      "peak_kind": "4 schedulers x 152 SMs x the SM clock",

@@ -45,3 +45,22 @@ def test_issue_roofline_counts_one_instruction_per_scheduler_per_clock(monkeypat
     assert r["frac"] == pytest.approx(1e9 / (4 * 152 * 2000e6))
     assert bench.issue_roofline("reconstruct", 1e-3, 2000.0) is None  # source changed
     assert bench.issue_roofline("claim_pair", 1e-3, None) is None     # no clock sample
+
+
+def test_prefix_key_hashes_the_source_before_the_marked_section(monkeypatch):
+    # a key over the translation unit's text before a section stays valid when
+    # only code after it changes, and is void when code before it changes
+    src = os.path.join(bench.ROOT, "paper_1705_03750_gb300", "csrc", "phase4d.cu")
+    with open(src, "rb") as fh:
+        text = fh.read()
+    marker = bench.PHASE4D_PREFIX_END
+    i = text.index(marker.encode())
+    prefix = text[:text.rindex(b"\n// ----", 0, i)]
+    sha = hashlib.sha256(prefix).hexdigest()[:16]
+    monkeypatch.setattr(bench, "NCU4_INSTR", {"percolate": (7, "phase4d.cu", sha),
+                                              "other": (8, "phase4d.cu", "0" * 16)})
+    assert bench._keyed(bench.NCU4_INSTR, "percolate", marker) == 7
+    assert bench._keyed(bench.NCU4_INSTR, "other", marker) is None
+    assert bench._keyed(bench.NCU4_INSTR, "percolate", "no such marker in the file") is None
+    full = hashlib.sha256(text).hexdigest()[:16]
+    assert full != sha and bench._keyed({"k": (9, "phase4d.cu", full)}, "k") == 9
