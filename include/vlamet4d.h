@@ -91,7 +91,8 @@ vm_status vm_4d_set_f(vm_4d_solver* s, const double* f, int on_device);
  * quadratic interpolation (Sec. 2.2.1); pixel masses; the field of the 2D
  * Poisson equation with its gradient and Hessian (Sec. 2.5); kick; half
  * drift; a remap (Sec. 2.3.2: f_ini <- spline(f_ini)(Q_r(P)), new eta,
- * isotropic elements) after every n_s-th step.  Asynchronous. */
+ * isotropic elements) after every n_s-th step.  Asynchronous.  VM_E_STATE
+ * before the first vm_4d_set_f. */
 vm_status vm_4d_step(vm_4d_solver* s, int32_t nsteps);
 
 /* The map and the transport reconstruction (f, pixel masses, field) of the
@@ -129,8 +130,10 @@ int64_t vm_4d_launches(const vm_4d_solver* s);
  * component outgrew the shared-memory flood window of side 2*min(2s, 12)+1
  * and were filled again over the whole padded lattice, out3[1] unexplored
  * sites left by the percolation, out3[2] repair rounds (Sec. 2.3.1);
- * *d2_evals (may be NULL): distance evaluations d^2 = |Q(P) - Q_m|^2 of the
- * percolation tests since creation, 219 FP64 operations each. */
+ * *d2_evals (may be NULL): the FP64 distance evaluations d^2 = |Q(P) - Q_m|^2
+ * in the fixed order since creation (219 FP64 operations each), the ones the
+ * percolation ran where an FP32 bound left a decision open or a site was
+ * claimed by more than one element. */
 vm_status vm_4d_map_stats(vm_4d_solver* s, int32_t* out3, int64_t* d2_evals);
 
 /* Per-kernel timing: while on, CUDA events on the solver's stream bracket
