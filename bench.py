@@ -635,6 +635,8 @@ def phase4d_run(args, dev, peaks, fp64_peak=None, clock_mhz=None) -> dict:
     from paper_1705_03750_gb300 import vlamet as V
     from paper_1705_03750_gb300 import vlamet4d as V4
     rc = I4.HALOS4D_64
+    if args.n4d != rc.n[0]:
+        rc = rc.with_(name=f"halos4d-{args.n4d}^4", n=(args.n4d,) * 4)
     K, W = args.steps4d, max(3, args.warmup4d)
     f0 = I4.initial_f4(rc)
     f0_dev = torch.from_numpy(f0).to(dev)
@@ -1040,6 +1042,7 @@ def main():
     ap.add_argument("--no-4d", action="store_true", help="skip the 4D phase-space sample")
     ap.add_argument("--steps4d", type=int, default=20, help="timed steps of the 4D phase-space sample")
     ap.add_argument("--warmup4d", type=int, default=3)
+    ap.add_argument("--n4d", type=int, default=64, help="nodes per axis of the 4D sample (64: its workload)")
     ap.add_argument("--spin", type=float, default=2.0, help="seconds of untimed steps before the warm-up")
     ap.add_argument("--clock-log", default=None, help="path prefix for the raw clock samples (CSV) of each timed region")
     args = ap.parse_args()
